@@ -1,0 +1,301 @@
+"""Seeded synthetic inputs: face-based quad meshes, boundary tables and case parameters.
+
+This module is the only code shared by the FP64 oracle side and the CUDA side.  It
+holds none of the method's arithmetic: it writes point coordinates, face-to-point
+lists, owner/neighbour arrays and plain case numbers (tau from the Reynolds number,
+dt from the known smallest cell side), nothing that the S-DUGKS step computes.
+
+Mesh convention (the face-based owner/neighbour form of an unstructured FV mesh):
+
+* ``points``   float64 [n_points, 2]
+* ``face_pts`` int64   [n_faces, 2]   the two end points of each straight face
+* ``owner``    int64   [n_faces]      cell on one side
+* ``neighbour`` int64  [n_faces]      cell on the other side, or ``-1 - patch`` on a
+  boundary face of boundary patch ``patch``
+* ``n_cells``  int
+
+Boundary kinds and their three parameters (the same numbers the C-ABI takes):
+
+* PERIODIC     (partner patch, shift_x, shift_y): face centre + shift lands on the partner face
+* WALL         ()                                 no-slip wall at rest
+* MOVING_WALL  (u_x, u_y)                         no-slip wall moving tangentially
+* FARFIELD     (rho, u_x, u_y)                    free stream
+* OUTLET       ()                                 density and velocity from the inner cell
+
+D2Q9 lattice units: c = 1, c_s^2 = 1/3, so tau = 3 nu.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_UNSET, BC_PERIODIC, BC_WALL, BC_MOVING_WALL, BC_FARFIELD, BC_OUTLET = 0, 1, 2, 3, 4, 5
+
+
+@dataclass
+class Mesh:
+    points: np.ndarray
+    face_pts: np.ndarray
+    owner: np.ndarray
+    neighbour: np.ndarray
+    n_cells: int
+    patches: dict
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.face_pts.shape[0])
+
+    @property
+    def n_points(self) -> int:
+        return int(self.points.shape[0])
+
+
+@dataclass
+class Case:
+    """A mesh with its boundary table and flow parameters (lattice units)."""
+    name: str
+    mesh: Mesh
+    bcs: list          # [(patch, kind, (p0, p1, p2))]
+    tau: float
+    dt: float
+    rho0: float = 1.0
+    u0: tuple = (0.0, 0.0)
+    meta: dict = field(default_factory=dict)
+
+
+def _bc_params(*p):
+    q = [float(x) for x in p] + [0.0] * (3 - len(p))
+    return tuple(q[:3])
+
+
+def cartesian(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, *, jitter: float = 0.0,
+              seed: int | None = None) -> Mesh:
+    """Uniform (optionally jittered) nx x ny quad mesh on [0,lx] x [0,ly].
+
+    Patches: 0 bottom (y=0), 1 right (x=lx), 2 top (y=ly), 3 left (x=0).
+    Cell (i, j) has id i + nx*j; point (i, j) has id i + (nx+1)*j.
+    ``jitter`` moves interior points by up to jitter*min(dx,dy) (seeded), which keeps
+    the quads convex for jitter < 0.25.
+    """
+    dx, dy = lx / nx, ly / ny
+    I, J = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    px = (I * dx).astype(np.float64).ravel()
+    py = (J * dy).astype(np.float64).ravel()
+    if jitter:
+        rng = np.random.default_rng(seed)
+        inner = ((I > 0) & (I < nx) & (J > 0) & (J < ny)).ravel()
+        h = jitter * min(dx, dy)
+        px[inner] += rng.uniform(-h, h, inner.sum())
+        py[inner] += rng.uniform(-h, h, inner.sum())
+    points = np.stack([px, py], 1)
+
+    def pid(i, j):
+        return i + (nx + 1) * j
+
+    def cid(i, j):
+        return i + nx * j
+
+    fp, own, nbr = [], [], []
+    # faces of constant x (between cells (i-1, j) and (i, j))
+    for j in range(ny):
+        for i in range(nx + 1):
+            fp.append((pid(i, j), pid(i, j + 1)))
+            if i == 0:
+                own.append(cid(0, j)); nbr.append(-1 - 3)
+            elif i == nx:
+                own.append(cid(nx - 1, j)); nbr.append(-1 - 1)
+            else:
+                own.append(cid(i - 1, j)); nbr.append(cid(i, j))
+    # faces of constant y (between cells (i, j-1) and (i, j))
+    for j in range(ny + 1):
+        for i in range(nx):
+            fp.append((pid(i, j), pid(i + 1, j)))
+            if j == 0:
+                own.append(cid(i, 0)); nbr.append(-1 - 0)
+            elif j == ny:
+                own.append(cid(i, ny - 1)); nbr.append(-1 - 2)
+            else:
+                own.append(cid(i, j - 1)); nbr.append(cid(i, j))
+    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    meta = dict(kind="cartesian", nx=nx, ny=ny, lx=lx, ly=ly, dx=dx, dy=dy,
+                cell_i=ci.ravel(), cell_j=cj.ravel(),
+                cell_xy_nominal=np.stack([(ci.ravel() + 0.5) * dx, (cj.ravel() + 0.5) * dy], 1))
+    return Mesh(points, np.asarray(fp, np.int64), np.asarray(own, np.int64),
+                np.asarray(nbr, np.int64), nx * ny,
+                dict(bottom=0, right=1, top=2, left=3), meta)
+
+
+def o_mesh_ratio(n_r: int, r0: float, first: float, r_far: float) -> float:
+    """Geometric ratio q with r0 + first*(q^n_r - 1)/(q - 1) = r_far (bisection)."""
+    lo, hi = 1.0 + 1e-12, 2.0
+    span = r_far - r0
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        s = first * (q ** n_r - 1.0) / (q - 1.0)
+        lo, hi = (q, hi) if s < span else (lo, q)
+    return 0.5 * (lo + hi)
+
+
+def o_mesh(n_theta: int, n_r: int, *, diameter: float = 1.0, first: float = 0.005,
+           r_far: float = 50.0) -> Mesh:
+    """Body-fitted O-mesh around a circular cylinder centred at the origin.
+
+    n_theta cells around, n_r cells out, radii geometric from D/2 with first cell
+    thickness ``first`` (in units of D) out to ``r_far`` (in units of D).
+    Patches: 0 cylinder wall, 1 far field.  Cell (i, k) has id i + n_theta*k.
+    """
+    r0 = 0.5 * diameter
+    q = o_mesh_ratio(n_r, r0, first * diameter, r_far * diameter)
+    radii = np.empty(n_r + 1)
+    radii[0] = r0
+    h = first * diameter
+    for k in range(n_r):
+        radii[k + 1] = radii[k] + h
+        h *= q
+    radii[-1] = r_far * diameter
+    th = 2.0 * np.pi * np.arange(n_theta) / n_theta
+    R, T = np.meshgrid(radii, th, indexing="ij")          # [n_r+1, n_theta]
+    points = np.stack([(R * np.cos(T)).ravel(), (R * np.sin(T)).ravel()], 1)
+
+    def pid(i, k):
+        return (i % n_theta) + n_theta * k
+
+    def cid(i, k):
+        return (i % n_theta) + n_theta * k
+
+    fp, own, nbr = [], [], []
+    # radial faces at angle th_i, between cells (i-1, k) and (i, k)
+    for k in range(n_r):
+        for i in range(n_theta):
+            fp.append((pid(i, k), pid(i, k + 1)))
+            own.append(cid(i - 1, k)); nbr.append(cid(i, k))
+    # circumferential faces at radius r_k, between cells (i, k-1) and (i, k)
+    for k in range(n_r + 1):
+        for i in range(n_theta):
+            fp.append((pid(i, k), pid(i + 1, k)))
+            if k == 0:
+                own.append(cid(i, 0)); nbr.append(-1 - 0)
+            elif k == n_r:
+                own.append(cid(i, n_r - 1)); nbr.append(-1 - 1)
+            else:
+                own.append(cid(i, k - 1)); nbr.append(cid(i, k))
+    ci, ck = np.meshgrid(np.arange(n_theta), np.arange(n_r), indexing="xy")
+    meta = dict(kind="o_mesh", n_theta=n_theta, n_r=n_r, ratio=q, radii=radii,
+                cell_i=ci.ravel(), cell_k=ck.ravel(), diameter=diameter, first=first * diameter)
+    return Mesh(points, np.asarray(fp, np.int64), np.asarray(own, np.int64),
+                np.asarray(nbr, np.int64), n_theta * n_r, dict(wall=0, farfield=1), meta)
+
+
+def shuffled(mesh: Mesh, seed: int) -> Mesh:
+    """Same mesh with cell ids, face ids and each face's point order permuted (seeded)."""
+    rng = np.random.default_rng(seed)
+    cperm = rng.permutation(mesh.n_cells)          # new id of old cell c is cperm[c]
+    fperm = rng.permutation(mesh.n_faces)          # new face k is old face fperm[k]
+    flip = rng.integers(0, 2, mesh.n_faces).astype(bool)
+    own = cperm[mesh.owner[fperm]]
+    nb_old = mesh.neighbour[fperm]
+    nbr = np.where(nb_old >= 0, cperm[np.maximum(nb_old, 0)], nb_old)
+    fp = mesh.face_pts[fperm].copy()
+    fp[flip] = fp[flip][:, ::-1]
+    meta = dict(mesh.meta)
+    inv = np.empty_like(cperm)
+    inv[cperm] = np.arange(mesh.n_cells)
+    for key, val in mesh.meta.items():
+        if isinstance(val, np.ndarray) and val.shape[:1] == (mesh.n_cells,):
+            meta[key] = val[inv]
+    meta["cell_perm"] = cperm
+    return Mesh(mesh.points.copy(), fp, own, nbr, mesh.n_cells, dict(mesh.patches), meta)
+
+
+# ----------------------------------------------------------------------------- cases
+
+def couette(ny: int = 64, nx: int = 4, *, U: float = 0.1, Re: float = 10.0, cfl: float = 0.5,
+            height: float = 1.0) -> Case:
+    """Plane Couette flow: nx x ny square cells, unit height, periodic in x,
+    bottom wall at rest, top wall moving at U; nu = U*H/Re."""
+    dy = height / ny
+    m = cartesian(nx, ny, nx * dy, height)
+    w = nx * dy
+    bcs = [(m.patches["left"], BC_PERIODIC, _bc_params(m.patches["right"], w, 0.0)),
+           (m.patches["right"], BC_PERIODIC, _bc_params(m.patches["left"], -w, 0.0)),
+           (m.patches["bottom"], BC_WALL, _bc_params()),
+           (m.patches["top"], BC_MOVING_WALL, _bc_params(U, 0.0))]
+    nu = U * height / Re
+    return Case(f"couette_{nx}x{ny}", m, bcs, tau=3.0 * nu, dt=cfl * dy / math.sqrt(2.0),
+                meta=dict(U=U, Re=Re, cfl=cfl, height=height))
+
+
+def cavity(n: int = 256, *, U: float = 0.1, Re: float = 1000.0, cfl: float = 0.5) -> Case:
+    """Lid-driven square cavity of n x n unit cells (L = n), lid (top) moving at U."""
+    m = cartesian(n, n, float(n), float(n))
+    bcs = [(m.patches["bottom"], BC_WALL, _bc_params()),
+           (m.patches["right"], BC_WALL, _bc_params()),
+           (m.patches["left"], BC_WALL, _bc_params()),
+           (m.patches["top"], BC_MOVING_WALL, _bc_params(U, 0.0))]
+    nu = U * n / Re
+    return Case(f"cavity_{n}", m, bcs, tau=3.0 * nu, dt=cfl * 1.0 / math.sqrt(2.0),
+                meta=dict(U=U, Re=Re, cfl=cfl, L=float(n)))
+
+
+def cylinder(n_theta: int = 512, n_r: int = 256, *, U: float = 0.1, Re: float = 40.0,
+             cfl: float = 0.5, first: float = 0.005, r_far: float = 50.0,
+             shuffle_seed: int | None = 0) -> Case:
+    """Flow past a circular cylinder of diameter 1 on an O-mesh; far field at r_far."""
+    m = o_mesh(n_theta, n_r, first=first, r_far=r_far)
+    if shuffle_seed is not None:
+        m = shuffled(m, shuffle_seed)
+    bcs = [(m.patches["wall"], BC_WALL, _bc_params()),
+           (m.patches["farfield"], BC_FARFIELD, _bc_params(1.0, U, 0.0))]
+    nu = U * 1.0 / Re
+    # the smallest cell side is the first radial spacing (the circumferential side
+    # of the first ring, pi*D/n_theta, is longer for n_theta <= 628)
+    dmin = min(first, math.pi / n_theta)
+    return Case(f"cylinder_{n_theta}x{n_r}", m, bcs, tau=3.0 * nu, dt=cfl * dmin / math.sqrt(2.0),
+                u0=(U, 0.0), meta=dict(U=U, Re=Re, cfl=cfl))
+
+
+def periodic_box(nx: int, ny: int, *, lx: float | None = None, ly: float | None = None,
+                 jitter: float = 0.0, seed: int | None = None, tau: float = 0.05,
+                 dt: float = 0.1) -> Case:
+    """Fully periodic nx x ny box (no walls): for fixed-point and conservation checks."""
+    lx = float(nx) if lx is None else lx
+    ly = float(ny) if ly is None else ly
+    m = cartesian(nx, ny, lx, ly, jitter=jitter, seed=seed)
+    bcs = [(3, BC_PERIODIC, _bc_params(1, lx, 0.0)), (1, BC_PERIODIC, _bc_params(3, -lx, 0.0)),
+           (0, BC_PERIODIC, _bc_params(2, 0.0, ly)), (2, BC_PERIODIC, _bc_params(0, 0.0, -ly))]
+    return Case(f"periodic_{nx}x{ny}", m, bcs, tau=tau, dt=dt)
+
+
+def smooth_field(case: Case, seed: int, amp_rho: float = 0.05, amp_u: float = 0.05):
+    """Seeded smooth initial (rho [N], u [N,2]) on a Cartesian-generated case, built from
+    low Fourier modes of the nominal cell centres (periodic in the box)."""
+    rng = np.random.default_rng(seed)
+    xy = case.mesh.meta["cell_xy_nominal"]
+    lx, ly = case.mesh.meta["lx"], case.mesh.meta["ly"]
+    X = 2 * np.pi * xy[:, 0] / lx
+    Y = 2 * np.pi * xy[:, 1] / ly
+
+    def field_():
+        out = np.zeros(len(X))
+        for kx in range(0, 3):
+            for ky in range(0, 3):
+                a, b = rng.normal(size=2)
+                out += a * np.cos(kx * X + ky * Y) + b * np.sin(kx * X + ky * Y)
+        return out / 9.0
+
+    rho = 1.0 + amp_rho * field_()
+    u = np.stack([amp_u * field_(), amp_u * field_()], 1)
+    return rho, u
+
+
+def batch_cavities(count: int = 256, *, seed: int = 1, n_lo: int = 32, n_hi: int = 512,
+                   re_lo: float = 100.0, re_hi: float = 5000.0, U: float = 0.1, cfl: float = 0.5):
+    """Sizes and Reynolds numbers of a batch of lid-driven cavities, drawn log-uniformly (seeded)."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))
+    ns = np.clip(np.rint(ns).astype(int), n_lo, n_hi)
+    res = np.exp(rng.uniform(math.log(re_lo), math.log(re_hi), count))
+    return [(int(n), float(re)) for n, re in zip(ns, res)]
