@@ -1,0 +1,328 @@
+"""Benchmark of the S-DUGKS D2Q9 step on one GB300 (or N replicas, one per GPU).
+
+Workload (default): the lid-driven cavity of 256 x 256 unit cells, Re 1000, lid
+U = 0.1, CFL 0.5, f stored in FP32, started from rest.  One benchmark step is one
+residual interval: 1000 fused S-DUGKS time steps (steps 1-11 of Sec. II, each one
+kernel launch, replayed from a captured CUDA graph) followed by the FP64 residual
+and mass reduction of Sec. IV.  The default --warmup 3 --steps 17 therefore runs
+exactly the 20,000 steps of that case.
+
+Metric: MLUPS = cells x 9 velocities x time steps / s / 1e6 ("cell-Q updates").
+The device-timed region starts with f, W resident in HBM; L2 is flushed (a 256 MB
+buffer is rewritten) before every timed step, outside its events.  The state of
+this case is 9.4 MB, so inside a step the 1000 launches run from L2.
+
+e2e: the same metric through the C-ABI from pinned host buffers: each step uploads
+the full state (f, W, W_next in FP64), advances 1000 steps, runs the residual and
+reads rho and u back.
+
+--impl reference: the FP64 C oracle, as it stands, on the host cores, on bounded
+samples of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2007_07347_gb300 import meshes as M  # noqa: E402
+
+INTERVAL = 1000
+STATE_BYTES = {"fp64": 240, "fp32": 144, "bf16dev": 108}   # f r+w, W^n and W^{n+1} read, W^{n+2} written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=17)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
+    ap.add_argument("--n", type=int, default=256, help="cavity cells per side")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    return M.cavity(args.n, U=0.1, Re=1000.0, cfl=0.5)
+
+
+def config(args, case):
+    return {"workload": f"lid-driven cavity {args.n}x{args.n}, Re 1000, lid 0.1, CFL 0.5, from rest",
+            "cells": case.mesh.n_cells, "velocities": 9, "time_steps_per_step": INTERVAL,
+            "storage": args.precision, "tau": case.tau, "dt": case.dt,
+            "l2": "flushed (256 MB rewrite) before each timed step; the 9.4 MB state is L2-resident within a step",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2007_07347_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kernel_key)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(case, seconds: float):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample: as many
+    10-step chunks of the workload as fit in about `seconds`."""
+    import oracle as O
+    threads = O.set_threads(0)
+    st = O.init(case.mesh.n_cells)
+    O.run(case, st, 1)                       # geometry warm-up, untimed
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        O.run(case, st, 10)
+        steps += 10
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    mlups = case.mesh.n_cells * 9 * steps / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} time steps of the same {case.mesh.n_cells}-cell cavity from rest "
+                      f"({el:.1f} s, {threads} OpenMP threads, FP64)"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    case = workload(args)
+    threads = O.set_threads(0)
+    st = O.init(case.mesh.n_cells)
+    sample = 10                              # time steps per benchmark step
+    for _ in range(args.warmup):
+        O.run(case, st, sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.run(case, st, sample)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    mlups = case.mesh.n_cells * 9 * sample * args.steps / tot / 1e6
+    line = {"impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(config(args, case), time_steps_per_step=sample,
+                                                l2="n/a (CPU)", parallelism="host cores"),
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} time steps per benchmark step, {threads} OpenMP threads"},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2007_07347_gb300 import sdugks as S
+    S.lib()
+    case = workload(args)
+    n = case.mesh.n_cells
+    stream = torch.cuda.Stream()
+    s = S.Solver.from_case(case, args.precision, stream=stream)
+    s.init()
+    info = s.info()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            s.step(INTERVAL)
+            s.residual()
+        barrier()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        eps_hist = []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                s.step(INTERVAL)
+                ev[k][1].record(stream)
+                eps_hist.append(s.residual())
+                ev[k][2].record(stream)
+            barrier()
+        step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+        kern_ms = [e[0].elapsed_time(e[1]) / INTERVAL for e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells_q = n * 9 * INTERVAL * args.steps * world
+    value = cells_q / (total_ms / 1e3) / 1e6
+
+    # ---- e2e through the C-ABI with pinned host buffers
+    f_h = torch.empty((n, 9), dtype=torch.float64).pin_memory().numpy()
+    W_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    Wn_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    rho_h = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    u_h = torch.empty((n, 2), dtype=torch.float64).pin_memory().numpy()
+    s.get_state_into(f_h, W_h, Wn_h)
+    e2e_steps = max(3, min(args.steps, 10))
+    import ctypes as C
+    L = S.lib()
+    P = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        S._ck(L.sdugks_set_state(s._h, P(f_h), P(W_h), P(Wn_h)), "set_state")
+        S._ck(L.sdugks_step(s._h, INTERVAL), "step")
+        s.residual()
+        S._ck(L.sdugks_get_macros(s._h, P(rho_h), P(u_h)), "get_macros")
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = n * 9 * INTERVAL * e2e_steps * world / e2e_s / 1e6
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    alg_bytes = STATE_BYTES[args.precision] * n
+    kern_avg_s = float(np.mean(kern_ms)) / 1e3
+    achieved = alg_bytes / kern_avg_s / 1e9
+    key = f"k_step_tiled_{args.precision}_cavity{args.n}"
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16dev": "f32 (bf16 storage)"}[args.precision],
+        "data": "synthetic", "config": config(args, case),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(key),
+                     "kernel": "k_step_tiled", "algorithmic_bytes_per_launch": alg_bytes,
+                     "avg_launch_us": kern_avg_s * 1e6, "peak_kind": f"{peak_kind} (hbm_gbs)"},
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": n * 15 * 8,
+                "d2h_bytes_per_step": n * 3 * 8 + 32, "steps": e2e_steps},
+        "gpu_launches": args.steps * (INTERVAL + 2),
+        "residual_last": eps_hist[-1][0], "mass_last": eps_hist[-1][1],
+        "solver": {k: info[k] for k in ("n_tiles", "halo_cells", "mesh_bytes_per_cell_step", "kernel")},
+        "mcell_steps_per_s": value / 9,
+    }
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds)
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * sdugks.h -- C-ABI of libsdugks: the simplified discrete unified gas kinetic scheme
+ * (S-DUGKS, arXiv:2007.07347) D2Q9 time step on finite-volume quad meshes, run by
+ * hand-written CUDA kernels on one GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Status.     Every int-returning call returns SDUGKS_OK (0) or a negative
+ *             SDUGKS_ERR_* code; sdugks_last_error() then holds a one-line message
+ *             (thread-local, valid until the next failing call on that thread).
+ *             No call aborts the process or traps the device.
+ * Ownership.  Input arrays are caller-owned and only read during the call (the mesh
+ *             is copied).  Handles are library-owned: create/destroy pairs.
+ *             Host output arrays are caller-owned and must hold the stated size.
+ * Memory.     "host" pointers are ordinary (pageable or pinned) CPU memory; "device"
+ *             pointers are CUDA global memory of the solver's device.
+ * Streams.    A solver issues all its work on the CUDA stream given at creation
+ *             (NULL = legacy default stream).  Calls marked "async" return before the
+ *             GPU is done; calls that write host memory synchronise that stream.
+ * Threads.    One solver must not be used from two threads at once; distinct
+ *             solvers are independent.
+ * Lattice.    D2Q9, c = 1, c_s^2 = 1/3.  Velocity index a = 0..8:
+ *             (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1),
+ *             weights 4/9, 1/9 (a = 1..4), 1/36 (a = 5..8).
+ * Layouts.    Cell-major, in the caller's cell numbering: f[n_cells][9],
+ *             W[n_cells][3] = (rho, rho*u_x, rho*u_y), u[n_cells][2].
+ */
+#ifndef SDUGKS_H
+#define SDUGKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------- */
+#define SDUGKS_OK 0
+#define SDUGKS_ERR_INVALID_ARG (-1)  /* NULL handle/pointer, size or value out of range */
+#define SDUGKS_ERR_INVALID_MESH (-2) /* inconsistent face/cell arrays, open or degenerate cell */
+#define SDUGKS_ERR_BAD_BC (-3)       /* missing boundary condition, unmatched periodic face */
+#define SDUGKS_ERR_OOM (-4)          /* device or host allocation failed */
+#define SDUGKS_ERR_DIVERGED (-5)     /* non-finite value found by the residual reduction */
+#define SDUGKS_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
+#define SDUGKS_ERR_CUDA (-7)         /* any other CUDA runtime error (message has the name) */
+#define SDUGKS_ERR_STATE (-8)        /* call out of order, e.g. step before init */
+
+/* ---- boundary kinds (Sec. III) ------------------------------------------------- */
+#define SDUGKS_BC_UNSET 0
+#define SDUGKS_BC_PERIODIC 1    /* params: partner patch, shift_x, shift_y             */
+#define SDUGKS_BC_WALL 2        /* no-slip wall at rest; params unused                 */
+#define SDUGKS_BC_MOVING_WALL 3 /* no-slip wall moving at (u_x, u_y); params: u_x, u_y */
+#define SDUGKS_BC_FARFIELD 4    /* inlet / free stream; params: rho_inf, u_x, u_y      */
+#define SDUGKS_BC_OUTLET 5      /* rho and u of the inner cell; params unused          */
+
+/* ---- storage/compute precision of f ------------------------------------------- */
+#define SDUGKS_FP64 0          /* f stored and computed in FP64                          */
+#define SDUGKS_FP32 1          /* f stored and computed in FP32                          */
+#define SDUGKS_FP32_BF16DEV 2  /* f stored as bf16 d = (f - feq(W)) / w, computed in FP32 */
+/* W (and the macroscopic-flux accumulation, residual and mass) is FP64 in every mode. */
+
+/* ---- kernel selection ---------------------------------------------------------- */
+#define SDUGKS_KERNEL_AUTO 0      /* Cartesian kernel when the mesh is a uniform grid  */
+#define SDUGKS_KERNEL_TILED 1     /* unstructured tiled kernel on any quad mesh        */
+#define SDUGKS_KERNEL_CARTESIAN 2 /* structured kernel; INVALID_ARG if not a grid      */
+
+typedef struct sdugks_mesh sdugks_mesh;
+typedef struct sdugks_solver sdugks_solver;
+
+/* Flow and launch parameters.  tau = nu / c_s^2 = 3 nu; dt is the time step
+ * (sdugks_mesh_cfl_dt gives a CFL-limited value). */
+typedef struct sdugks_params {
+    double tau;          /* relaxation time, > 0                                   */
+    double dt;           /* time step, > 0                                         */
+    int32_t precision;   /* SDUGKS_FP64 | SDUGKS_FP32 | SDUGKS_FP32_BF16DEV         */
+    int32_t kernel;      /* SDUGKS_KERNEL_*                                        */
+    int32_t tile_cells;  /* tiled kernel: interior cells per tile (32..256), 0 = auto */
+    int32_t graph_steps; /* steps per captured CUDA graph in sdugks_step, 0 = auto, <0 = off */
+} sdugks_params;
+
+/* What a solver chose and holds (sdugks_solver_info). */
+typedef struct sdugks_info {
+    int64_t n_cells, n_faces;     /* after periodic faces are merged pairwise          */
+    int64_t n_tiles;              /* CTAs per step                                     */
+    int64_t halo_cells;           /* summed over tiles (ring 1 + ring 2)               */
+    int64_t steps_done;           /* steps since init / set_state                      */
+    int64_t device_bytes;         /* device memory held by the solver                  */
+    double state_bytes_per_cell_step; /* f, W read and written once per cell and step */
+    double mesh_bytes_per_cell_step;  /* mesh data the kernel reads per cell and step  */
+    int32_t kernel;               /* SDUGKS_KERNEL_TILED or SDUGKS_KERNEL_CARTESIAN    */
+    int32_t precision;
+    int32_t tile_cells;
+    int32_t nx, ny;               /* Cartesian kernel: grid size, else 0               */
+} sdugks_info;
+
+/* ---- mesh ---------------------------------------------------------------------- */
+
+/* Build a 2-D finite-volume mesh from face-based owner/neighbour arrays (the
+ * unstructured FV form the paper's cases use, Sec. IV).
+ *   xy[n_points][2]        point coordinates (host)
+ *   face_pts[n_faces][2]   end points of each straight face (host)
+ *   owner[n_faces]         cell on one side, 0 <= owner < n_cells (host)
+ *   neighbour[n_faces]     cell on the other side, or -1 - patch for a face of
+ *                          boundary patch `patch` (0 <= patch < 64) (host)
+ * Every cell must be a closed convex polygon with 3 or 4 faces.  Geometry (face
+ * normals, areas, centroids) is computed here in FP64.  Errors: INVALID_ARG,
+ * INVALID_MESH (open cell, repeated point, more than 4 faces), OOM. */
+int sdugks_mesh_create(int64_t n_points, const double *xy, int64_t n_faces, const int64_t *face_pts,
+                       const int64_t *owner, const int64_t *neighbour, int64_t n_cells,
+                       sdugks_mesh **out);
+
+/* Boundary condition of one patch (Sec. III: no-slip/moving wall and inlet by
+ * non-equilibrium extrapolation, outlet, periodic).  params[3] as listed with the
+ * SDUGKS_BC_* kinds (host; may be NULL for WALL and OUTLET).  A PERIODIC patch
+ * must name a PERIODIC partner whose faces sit at this patch's face centres plus
+ * (shift_x, shift_y); pairing is checked when a solver is created.
+ * Errors: INVALID_ARG (patch or kind out of range). */
+int sdugks_set_bc(sdugks_mesh *mesh, int32_t patch, int32_t kind, const double *params);
+
+/* CFL time step dt = cfl * dx_min / |xi|_max with |xi|_max = sqrt(2) (the diagonal
+ * D2Q9 velocity) and dx_min = min over cells of area / longest face (Sec. I: the
+ * step is limited only by the CFL condition). */
+int sdugks_mesh_cfl_dt(const sdugks_mesh *mesh, double cfl, double *dt);
+
+/* Number of cells and faces as given, and the number of boundary patches used. */
+int sdugks_mesh_sizes(const sdugks_mesh *mesh, int64_t *n_cells, int64_t *n_faces, int32_t *n_patches);
+
+void sdugks_mesh_destroy(sdugks_mesh *mesh);
+
+/* ---- solver -------------------------------------------------------------------- */
+
+/* Create a solver on the current CUDA device: pairs periodic faces, builds the LLSR
+ * normal matrices of Sec. II, orders cells into tiles and uploads everything.
+ * `stream` is a cudaStream_t (NULL = default stream).  The mesh may be destroyed
+ * afterwards.  Errors: INVALID_ARG, BAD_BC, INVALID_MESH, OOM, CUDA. */
+int sdugks_solver_create(const sdugks_mesh *mesh, const sdugks_params *params, void *stream,
+                         sdugks_solver **out);
+
+/* Initial state: W = (rho, rho u), f = feq(W) and zero macroscopic flux.
+ * rho[n_cells], u[n_cells][2] (host); NULL rho means 1, NULL u means 0.
+ * Also takes the residual snapshot.  Synchronises the stream. */
+int sdugks_init(sdugks_solver *s, const double *rho, const double *u);
+
+/* Advance n >= 0 steps (Sec. II, the eleven-step update; async).  Long runs replay
+ * a captured CUDA graph of params.graph_steps steps.  Errors: STATE before init. */
+int sdugks_step(sdugks_solver *s, int64_t n);
+
+/* Macroscopic fields at the current step: rho[n_cells], u[n_cells][2] (host;
+ * synchronises).  Either pointer may be NULL. */
+int sdugks_get_macros(sdugks_solver *s, double *rho, double *u);
+
+/* Same into device memory (async): d_rho[n_cells], d_u[n_cells][2], FP64. */
+int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double *d_u);
+
+/* Convergence residual of Sec. IV against the snapshot taken at the previous call
+ * (or at init/set_state):
+ *   eps = sqrt(sum_i (U_i - U0_i)^2 + (V_i - V0_i)^2) / sqrt(sum_i U0_i^2 + V0_i^2)
+ * with U, V = rho u / rho; +inf when the snapshot is at rest.  *mass = sum_i V_i rho_i.
+ * Then the snapshot is refreshed.  FP64 device reduction with a fixed order.
+ * Synchronises.  Returns DIVERGED (with eps = NaN) if any W is not finite. */
+int sdugks_residual(sdugks_solver *s, double *eps, double *mass);
+
+/* Checkpoint of the state at t_n (host, FP64, caller's cell order):
+ *   f[n_cells][9]      cell distribution
+ *   W[n_cells][3]      conserved variables at t_n
+ *   W_next[n_cells][3] W at t_{n+1} = W - dt/V F_macro^n (Eq. MacroUpdate, computed
+ *                      one step ahead; the macroscopic flux is kept in this form)
+ * get synchronises; set replaces the state (f is rounded to the storage precision)
+ * and refreshes the residual snapshot.  A run resumed from a checkpoint equals the
+ * uninterrupted run bit for bit in FP64 and FP32 storage. */
+int sdugks_get_state(sdugks_solver *s, double *f, double *W, double *W_next);
+int sdugks_set_state(sdugks_solver *s, const double *f, const double *W, const double *W_next);
+
+int sdugks_solver_info(const sdugks_solver *s, sdugks_info *out);
+
+void sdugks_solver_destroy(sdugks_solver *s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *sdugks_last_error(void);
+
+/* Library version string, e.g. "sdugks 0.1 sm_103a". */
+const char *sdugks_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDUGKS_H */

@@ -1,0 +1,74 @@
+// d2q9.cuh -- D2Q9 lattice constants, the discrete equilibrium and the storage
+// codecs of f shared by the CUDA translation units.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+#include "sdugks_internal.h"
+
+namespace sdugks {
+
+// Velocity a: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+__host__ __device__ constexpr int EX(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0); }
+__host__ __device__ constexpr int EY(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
+
+template <class R> __device__ __forceinline__ R wq(int a) {
+    return a == 0 ? R(4) / R(9) : (a < 5 ? R(1) / R(9) : R(1) / R(36));
+}
+template <class R> __device__ __forceinline__ R inv_wq(int a) {
+    return a == 0 ? R(9) / R(4) : (a < 5 ? R(9) : R(36));
+}
+
+// xi_a . v with the lattice components folded in at compile time.
+template <class R> __device__ __forceinline__ R xdot(int a, R vx, R vy) {
+    const int ex = EX(a), ey = EY(a);
+    R s = R(0);
+    if (ex == 1) s = vx; else if (ex == -1) s = -vx;
+    if (ey == 1) s = (ex == 0) ? vy : s + vy;
+    else if (ey == -1) s = (ex == 0) ? -vy : s - vy;
+    return s;
+}
+
+// Discrete equilibrium (second-order Hermite expansion of the Maxwellian, Eq. Feq on
+// the nine-velocity lattice): w rho [1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 |u|^2].
+template <class R> __device__ __forceinline__ void feq9(R rho, R ux, R uy, R out[NQ]) {
+    const R base = R(1) - R(1.5) * (ux * ux + uy * uy);
+#pragma unroll
+    for (int a = 0; a < NQ; a++) {
+        const R eu = xdot<R>(a, ux, uy);
+        out[a] = wq<R>(a) * rho * (base + eu * (R(3) + R(4.5) * eu));
+    }
+}
+
+// Storage codecs.  FP64/FP32 store f itself.  BF16DEV stores the scaled deviation
+// d = (f - feq(W)) / w from the equilibrium of the same time level.
+template <int P> struct Store;
+template <> struct Store<P_FP64> {
+    using T = double; using R = double;
+    static __device__ __forceinline__ R dec(T v, R, int) { return v; }
+    static __device__ __forceinline__ T enc(R f, R, int) { return f; }
+};
+template <> struct Store<P_FP32> {
+    using T = float; using R = float;
+    static __device__ __forceinline__ R dec(T v, R, int) { return v; }
+    static __device__ __forceinline__ T enc(R f, R, int) { return f; }
+};
+template <> struct Store<P_BF16DEV> {
+    using T = __nv_bfloat16; using R = float;
+    static __device__ __forceinline__ R dec(T v, R feq, int a) { return feq + wq<R>(a) * __bfloat162float(v); }
+    static __device__ __forceinline__ T enc(R f, R feq, int a) { return __float2bfloat16_rn((f - feq) * inv_wq<R>(a)); }
+};
+
+// Conserved variables (rho, rho u) -> (rho, u) in the compute precision.
+template <class R> __device__ __forceinline__ void macro_of(double w0, double w1, double w2, R &rho, R &ux, R &uy) {
+    rho = R(w0);
+    ux = R(w1) / rho;
+    uy = R(w2) / rho;
+}
+template <> __device__ __forceinline__ void macro_of<double>(double w0, double w1, double w2, double &rho, double &ux,
+                                                             double &uy) {
+    rho = w0;
+    ux = w1 / w0;
+    uy = w2 / w0;
+}
+
+}  // namespace sdugks

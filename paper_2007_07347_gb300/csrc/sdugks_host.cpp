@@ -1,0 +1,943 @@
+// sdugks_host.cpp -- host side of libsdugks: mesh geometry and validation, periodic
+// pairing, LLSR normal matrices, the tile partition with its halo rings, device
+// upload, stepping (with captured CUDA graphs) and the C-ABI of include/sdugks.h.
+#include "sdugks.h"
+#include "sdugks_internal.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace sdugks;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? SDUGKS_ERR_OOM : SDUGKS_ERR_CUDA,       \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__);     \
+    } while (0)
+
+// ------------------------------------------------------------------ mesh
+
+struct sdugks_mesh {
+    int64_t np = 0, nf = 0, nc = 0;
+    std::vector<double> xy;
+    std::vector<int64_t> fpts, own, nbr;
+    int32_t npatch = 0;
+    std::array<int32_t, MAXPATCH> bc_kind{};
+    std::array<std::array<double, 3>, MAXPATCH> bc_par{};
+    // geometry (FP64)
+    std::vector<double> vol, xc, xf, nl;   // nl: out of the owner
+    std::vector<int64_t> cs, cl;           // cell -> faces
+};
+
+// Area and centroid from the outward face normals (divergence theorem on straight
+// edges: V = 1/2 sum x_f . n l; int x dA = sum n_x l (x0^2 + x0 x1 + x1^2) / 6).
+static int build_geometry(sdugks_mesh &m)
+{
+    const int64_t nc = m.nc, nf = m.nf;
+    m.cs.assign(nc + 1, 0);
+    for (int64_t f = 0; f < nf; f++) {
+        m.cs[m.own[f] + 1]++;
+        if (m.nbr[f] >= 0) m.cs[m.nbr[f] + 1]++;
+    }
+    for (int64_t c = 0; c < nc; c++) m.cs[c + 1] += m.cs[c];
+    m.cl.assign(m.cs[nc], 0);
+    {
+        std::vector<int64_t> fill(nc, 0);
+        for (int64_t f = 0; f < nf; f++) {
+            m.cl[m.cs[m.own[f]] + fill[m.own[f]]++] = f;
+            if (m.nbr[f] >= 0) m.cl[m.cs[m.nbr[f]] + fill[m.nbr[f]]++] = f;
+        }
+    }
+    // vertex mean of each cell (inside a convex cell) for orienting the normals
+    std::vector<double> vm(2 * nc, 0.0);
+    for (int64_t c = 0; c < nc; c++) {
+        const int64_t k = m.cs[c + 1] - m.cs[c];
+        if (k < 3 || k > MAXF) return fail(SDUGKS_ERR_INVALID_MESH, "cell %lld has %lld faces (3 or 4 supported)",
+                                           (long long)c, (long long)k);
+        for (int64_t e = m.cs[c]; e < m.cs[c + 1]; e++) {
+            const int64_t f = m.cl[e];
+            for (int q = 0; q < 2; q++) {
+                vm[2 * c] += m.xy[2 * m.fpts[2 * f + q]];
+                vm[2 * c + 1] += m.xy[2 * m.fpts[2 * f + q] + 1];
+            }
+        }
+        vm[2 * c] /= 2.0 * k;
+        vm[2 * c + 1] /= 2.0 * k;
+    }
+    m.xf.assign(2 * nf, 0.0);
+    m.nl.assign(2 * nf, 0.0);
+    for (int64_t f = 0; f < nf; f++) {
+        const double x0 = m.xy[2 * m.fpts[2 * f]], y0 = m.xy[2 * m.fpts[2 * f] + 1];
+        const double x1 = m.xy[2 * m.fpts[2 * f + 1]], y1 = m.xy[2 * m.fpts[2 * f + 1] + 1];
+        double nx = y1 - y0, ny = x0 - x1;
+        const double mx = 0.5 * (x0 + x1), my = 0.5 * (y0 + y1);
+        if ((mx - vm[2 * m.own[f]]) * nx + (my - vm[2 * m.own[f] + 1]) * ny < 0.0) { nx = -nx; ny = -ny; }
+        if (nx == 0.0 && ny == 0.0) return fail(SDUGKS_ERR_INVALID_MESH, "face %lld has zero length", (long long)f);
+        m.xf[2 * f] = mx; m.xf[2 * f + 1] = my;
+        m.nl[2 * f] = nx; m.nl[2 * f + 1] = ny;
+    }
+    m.vol.assign(nc, 0.0);
+    m.xc.assign(2 * nc, 0.0);
+    for (int64_t c = 0; c < nc; c++) {
+        double v2 = 0, ix = 0, iy = 0, sx = 0, sy = 0, per = 0;
+        for (int64_t e = m.cs[c]; e < m.cs[c + 1]; e++) {
+            const int64_t f = m.cl[e];
+            const double sg = m.own[f] == c ? 1.0 : -1.0;
+            const double nx = sg * m.nl[2 * f], ny = sg * m.nl[2 * f + 1];
+            const double x0 = m.xy[2 * m.fpts[2 * f]], y0 = m.xy[2 * m.fpts[2 * f] + 1];
+            const double x1 = m.xy[2 * m.fpts[2 * f + 1]], y1 = m.xy[2 * m.fpts[2 * f + 1] + 1];
+            v2 += m.xf[2 * f] * nx + m.xf[2 * f + 1] * ny;
+            ix += nx * (x0 * x0 + x0 * x1 + x1 * x1);
+            iy += ny * (y0 * y0 + y0 * y1 + y1 * y1);
+            sx += nx; sy += ny;
+            per += std::hypot(nx, ny);
+        }
+        const double V = 0.5 * v2;
+        if (!(V > 0.0)) return fail(SDUGKS_ERR_INVALID_MESH, "cell %lld has area %g", (long long)c, V);
+        if (std::hypot(sx, sy) > 1e-12 * per)
+            return fail(SDUGKS_ERR_INVALID_MESH, "cell %lld is not closed (|sum n l| = %g)", (long long)c, std::hypot(sx, sy));
+        m.vol[c] = V;
+        m.xc[2 * c] = ix / (6.0 * V);
+        m.xc[2 * c + 1] = iy / (6.0 * V);
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_mesh_create(int64_t n_points, const double *xy, int64_t n_faces, const int64_t *face_pts,
+                                  const int64_t *owner, const int64_t *neighbour, int64_t n_cells, sdugks_mesh **out)
+{
+    if (!out) return fail(SDUGKS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_points <= 0 || n_faces <= 0 || n_cells <= 0 || !xy || !face_pts || !owner || !neighbour)
+        return fail(SDUGKS_ERR_INVALID_ARG, "empty mesh or NULL array");
+    if (n_cells > INT32_MAX / 2 || n_faces > INT32_MAX / 2)
+        return fail(SDUGKS_ERR_INVALID_ARG, "mesh too large (%lld cells, %lld faces)", (long long)n_cells, (long long)n_faces);
+    sdugks_mesh *m = new (std::nothrow) sdugks_mesh;
+    if (!m) return fail(SDUGKS_ERR_OOM, "host allocation failed");
+    try {
+        m->np = n_points; m->nf = n_faces; m->nc = n_cells;
+        m->xy.assign(xy, xy + 2 * n_points);
+        m->fpts.assign(face_pts, face_pts + 2 * n_faces);
+        m->own.assign(owner, owner + n_faces);
+        m->nbr.assign(neighbour, neighbour + n_faces);
+    } catch (...) {
+        delete m;
+        return fail(SDUGKS_ERR_OOM, "host allocation failed");
+    }
+    for (int64_t k = 0; k < 2 * n_points; k++)
+        if (!std::isfinite(m->xy[k])) { delete m; return fail(SDUGKS_ERR_INVALID_MESH, "non-finite point coordinate"); }
+    int32_t npatch = 0;
+    for (int64_t f = 0; f < n_faces; f++) {
+        const int64_t p0 = m->fpts[2 * f], p1 = m->fpts[2 * f + 1];
+        if (p0 < 0 || p0 >= n_points || p1 < 0 || p1 >= n_points || p0 == p1) {
+            delete m;
+            return fail(SDUGKS_ERR_INVALID_MESH, "face %lld has bad points (%lld, %lld)", (long long)f, (long long)p0, (long long)p1);
+        }
+        const int64_t o = m->own[f], k = m->nbr[f];
+        if (o < 0 || o >= n_cells || k >= n_cells || k == o) {
+            delete m;
+            return fail(SDUGKS_ERR_INVALID_MESH, "face %lld has bad owner/neighbour (%lld, %lld)", (long long)f, (long long)o, (long long)k);
+        }
+        if (k < 0) {
+            const int64_t p = -1 - k;
+            if (p >= MAXPATCH) { delete m; return fail(SDUGKS_ERR_INVALID_MESH, "patch %lld >= %d", (long long)p, MAXPATCH); }
+            npatch = std::max<int32_t>(npatch, (int32_t)p + 1);
+        }
+    }
+    m->npatch = npatch;
+    int rc = build_geometry(*m);
+    if (rc) { delete m; return rc; }
+    *out = m;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_set_bc(sdugks_mesh *m, int32_t patch, int32_t kind, const double *params)
+{
+    if (!m) return fail(SDUGKS_ERR_INVALID_ARG, "mesh is NULL");
+    if (patch < 0 || patch >= MAXPATCH) return fail(SDUGKS_ERR_INVALID_ARG, "patch %d out of range", patch);
+    if (kind < SDUGKS_BC_PERIODIC || kind > SDUGKS_BC_OUTLET) return fail(SDUGKS_ERR_INVALID_ARG, "unknown kind %d", kind);
+    const bool need = kind == SDUGKS_BC_PERIODIC || kind == SDUGKS_BC_MOVING_WALL || kind == SDUGKS_BC_FARFIELD;
+    if (need && !params) return fail(SDUGKS_ERR_INVALID_ARG, "kind %d needs params", kind);
+    for (int k = 0; k < 3; k++) {
+        const double v = params ? params[k] : 0.0;
+        if (!std::isfinite(v)) return fail(SDUGKS_ERR_INVALID_ARG, "non-finite boundary parameter");
+        m->bc_par[patch][k] = v;
+    }
+    if (kind == SDUGKS_BC_FARFIELD && !(params[0] > 0)) return fail(SDUGKS_ERR_INVALID_ARG, "far-field density must be > 0");
+    m->bc_kind[patch] = kind;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_mesh_cfl_dt(const sdugks_mesh *m, double cfl, double *dt)
+{
+    if (!m || !dt || !(cfl > 0)) return fail(SDUGKS_ERR_INVALID_ARG, "bad argument");
+    double dmin = INFINITY;
+    for (int64_t c = 0; c < m->nc; c++) {
+        double lmax = 0;
+        for (int64_t e = m->cs[c]; e < m->cs[c + 1]; e++) {
+            const int64_t f = m->cl[e];
+            lmax = std::max(lmax, std::hypot(m->nl[2 * f], m->nl[2 * f + 1]));
+        }
+        dmin = std::min(dmin, m->vol[c] / lmax);
+    }
+    *dt = cfl * dmin / std::sqrt(2.0);
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_mesh_sizes(const sdugks_mesh *m, int64_t *n_cells, int64_t *n_faces, int32_t *n_patches)
+{
+    if (!m) return fail(SDUGKS_ERR_INVALID_ARG, "mesh is NULL");
+    if (n_cells) *n_cells = m->nc;
+    if (n_faces) *n_faces = m->nf;
+    if (n_patches) *n_patches = m->npatch;
+    return SDUGKS_OK;
+}
+
+extern "C" void sdugks_mesh_destroy(sdugks_mesh *m) { delete m; }
+
+// ------------------------------------------------------------------ solver build
+
+namespace {
+
+// Faces after periodic pairs are merged into interior faces.
+struct Faces {
+    int64_t nf = 0;
+    std::vector<int64_t> own, nbr;        // nbr: cell or -1 - patch
+    std::vector<double> nl, ro, rk;       // [nf][2]
+};
+
+int merge_periodic(const sdugks_mesh &m, Faces &F)
+{
+    const int64_t nf = m.nf;
+    std::vector<int64_t> partner(nf, -1);
+    for (int32_t p = 0; p < m.npatch; p++) {
+        if (m.bc_kind[p] != SDUGKS_BC_PERIODIC) continue;
+        const int32_t q = (int32_t)m.bc_par[p][0];
+        if (q < 0 || q >= MAXPATCH || q == p || m.bc_kind[q] != SDUGKS_BC_PERIODIC)
+            return fail(SDUGKS_ERR_BAD_BC, "periodic patch %d names partner %d which is not periodic", p, q);
+        if ((int32_t)m.bc_par[q][0] != p) return fail(SDUGKS_ERR_BAD_BC, "periodic patches %d and %d are not partners of each other", p, q);
+        const double sx = m.bc_par[p][1], sy = m.bc_par[p][2];
+        if (std::hypot(sx + m.bc_par[q][1], sy + m.bc_par[q][2]) > 1e-9 * std::max(1.0, std::hypot(sx, sy)))
+            return fail(SDUGKS_ERR_BAD_BC, "periodic shifts of patches %d and %d do not cancel", p, q);
+        // faces of q sorted along their centres for matching
+        std::vector<int64_t> fq;
+        for (int64_t g = 0; g < nf; g++)
+            if (m.nbr[g] == -1 - q) fq.push_back(g);
+        std::sort(fq.begin(), fq.end(), [&](int64_t a, int64_t b) {
+            return m.xf[2 * a] != m.xf[2 * b] ? m.xf[2 * a] < m.xf[2 * b] : m.xf[2 * a + 1] < m.xf[2 * b + 1];
+        });
+        for (int64_t f = 0; f < nf; f++) {
+            if (m.nbr[f] != -1 - p) continue;
+            const double len = std::hypot(m.nl[2 * f], m.nl[2 * f + 1]);
+            const double tx = m.xf[2 * f] + sx, ty = m.xf[2 * f + 1] + sy, tol = 1e-9 * len;
+            auto it = std::lower_bound(fq.begin(), fq.end(), tx - tol, [&](int64_t g, double v) { return m.xf[2 * g] < v; });
+            int64_t hit = -1;
+            for (; it != fq.end() && m.xf[2 * *it] <= tx + tol; ++it)
+                if (std::hypot(m.xf[2 * *it] - tx, m.xf[2 * *it + 1] - ty) <= tol) { hit = *it; break; }
+            if (hit < 0) return fail(SDUGKS_ERR_BAD_BC, "periodic face %lld of patch %d has no partner on patch %d", (long long)f, p, q);
+            partner[f] = hit;
+        }
+    }
+    std::vector<int64_t> newid(nf, -1);
+    for (int64_t f = 0; f < nf; f++) {
+        if (m.nbr[f] < 0) {
+            const int32_t p = (int32_t)(-1 - m.nbr[f]);
+            if (m.bc_kind[p] == SDUGKS_BC_UNSET) return fail(SDUGKS_ERR_BAD_BC, "boundary patch %d has no boundary condition", p);
+            if (m.bc_kind[p] == SDUGKS_BC_PERIODIC) {
+                const int64_t g = partner[f];
+                if (partner[g] != f) return fail(SDUGKS_ERR_BAD_BC, "periodic faces %lld and %lld do not pair both ways", (long long)f, (long long)g);
+                if (g < f) continue;      // the pair is kept once, at the lower face id
+            }
+        }
+        newid[f] = F.nf++;
+    }
+    F.own.resize(F.nf); F.nbr.resize(F.nf);
+    F.nl.resize(2 * F.nf); F.ro.resize(2 * F.nf); F.rk.resize(2 * F.nf);
+    for (int64_t f = 0; f < nf; f++) {
+        const int64_t k = newid[f];
+        if (k < 0) continue;
+        const int64_t o = m.own[f];
+        F.own[k] = o;
+        F.nl[2 * k] = m.nl[2 * f]; F.nl[2 * k + 1] = m.nl[2 * f + 1];
+        F.ro[2 * k] = m.xf[2 * f] - m.xc[2 * o]; F.ro[2 * k + 1] = m.xf[2 * f + 1] - m.xc[2 * o + 1];
+        if (m.nbr[f] >= 0) {
+            const int64_t nb = m.nbr[f];
+            F.nbr[k] = nb;
+            F.rk[2 * k] = m.xf[2 * f] - m.xc[2 * nb]; F.rk[2 * k + 1] = m.xf[2 * f + 1] - m.xc[2 * nb + 1];
+        } else if (partner[f] >= 0) {
+            const int64_t g = partner[f], nb = m.own[g];
+            F.nbr[k] = nb;
+            // the same face seen from the far cell: its own copy of the face centre
+            F.rk[2 * k] = m.xf[2 * g] - m.xc[2 * nb]; F.rk[2 * k + 1] = m.xf[2 * g + 1] - m.xc[2 * nb + 1];
+        } else {
+            F.nbr[k] = m.nbr[f];
+            F.rk[2 * k] = 0.0; F.rk[2 * k + 1] = 0.0;
+        }
+    }
+    return SDUGKS_OK;
+}
+
+// Recursive coordinate bisection of the cell centroids into tiles of <= cap cells.
+void rcb(const std::vector<double> &xc, std::vector<int32_t> &ids, size_t lo, size_t hi, size_t cap,
+         std::vector<std::pair<size_t, size_t>> &tiles)
+{
+    if (hi - lo <= cap) { tiles.push_back({lo, hi}); return; }
+    double mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+    for (size_t i = lo; i < hi; i++)
+        for (int d = 0; d < 2; d++) {
+            mn[d] = std::min(mn[d], xc[2 * ids[i] + d]);
+            mx[d] = std::max(mx[d], xc[2 * ids[i] + d]);
+        }
+    const int ax = (mx[0] - mn[0] >= mx[1] - mn[1]) ? 0 : 1;
+    // split so the left part is a whole number of full tiles where possible
+    const size_t n = hi - lo, ntile = (n + cap - 1) / cap;
+    const size_t mid = lo + ((ntile / 2) * n + ntile / 2) / ntile;
+    std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi, [&](int32_t a, int32_t b) {
+        const double va = xc[2 * a + ax], vb = xc[2 * b + ax];
+        if (va != vb) return va < vb;
+        const double wa = xc[2 * a + 1 - ax], wb = xc[2 * b + 1 - ax];
+        return wa != wb ? wa < wb : a < b;
+    });
+    rcb(xc, ids, lo, mid, cap, tiles);
+    rcb(xc, ids, mid, hi, cap, tiles);
+}
+
+struct Arena {
+    char *base = nullptr;
+    size_t used = 0, cap = 0;
+    template <class T> T *take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + off) : nullptr;
+    }
+};
+
+}  // namespace
+
+struct sdugks_solver {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    sdugks_params p{};
+    Coefs coefs{};
+    int64_t n = 0, npad = 0, nf = 0, fpad = 0;
+    int32_t n_tiles = 0;
+    int64_t halo_cells = 0;
+    int32_t kernel = SDUGKS_KERNEL_TILED;
+    TiledMesh tm{};
+    // device buffers
+    char *dmem = nullptr;
+    size_t dbytes = 0;
+    int32_t *perm = nullptr;        // internal -> user
+    double *vol = nullptr, *snap = nullptr, *partial = nullptr, *red = nullptr;
+    State st{};
+    int n_red_blocks = 1;
+    double *staging = nullptr;      // [n][15] FP64, allocated on first use
+    double *h_red = nullptr;        // pinned [4]
+    bool initialised = false;
+    int cur = 0, w0 = 0;            // f buffer holding f^n; W buffer holding W^n
+    int64_t steps_done = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_len = 0;
+    double mesh_bytes = 0.0;
+};
+
+static int prepare(int prec)
+{
+    return prec == P_FP64 ? (int)prepare_tiled_fp64() : (int)prepare_tiled_fp32(prec);
+}
+
+static cudaError_t launch_one(sdugks_solver *s, cudaStream_t st)
+{
+    const int a = s->cur, b = s->w0;
+    const void *fin = s->st.f[a];
+    void *fout = s->st.f[1 - a];
+    const double *Wn = s->st.W[b], *Wn1 = s->st.W[(b + 1) % 3];
+    double *Wn2 = s->st.W[(b + 2) % 3];
+    cudaError_t e;
+    if (s->p.precision == P_FP64) e = launch_step_tiled_fp64(s->tm, s->coefs, fin, fout, Wn, Wn1, Wn2, st);
+    else e = launch_step_tiled_fp32(s->p.precision, s->tm, s->coefs, fin, fout, Wn, Wn1, Wn2, st);
+    s->cur = 1 - a;
+    s->w0 = (b + 1) % 3;
+    return e;
+}
+
+extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *prm, void *stream, sdugks_solver **out)
+{
+    if (!out) return fail(SDUGKS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!m || !prm) return fail(SDUGKS_ERR_INVALID_ARG, "mesh or params is NULL");
+    if (!(prm->tau > 0) || !(prm->dt > 0) || !std::isfinite(prm->tau) || !std::isfinite(prm->dt))
+        return fail(SDUGKS_ERR_INVALID_ARG, "tau and dt must be finite and > 0");
+    if (prm->precision < SDUGKS_FP64 || prm->precision > SDUGKS_FP32_BF16DEV)
+        return fail(SDUGKS_ERR_INVALID_ARG, "unknown precision %d", prm->precision);
+    if (prm->kernel == SDUGKS_KERNEL_CARTESIAN)
+        return fail(SDUGKS_ERR_INVALID_ARG, "the Cartesian kernel is not available in this build");
+    if (prm->kernel < SDUGKS_KERNEL_AUTO || prm->kernel > SDUGKS_KERNEL_CARTESIAN)
+        return fail(SDUGKS_ERR_INVALID_ARG, "unknown kernel %d", prm->kernel);
+    if (prm->tile_cells != 0 && (prm->tile_cells < 16 || prm->tile_cells > TILE_MAX))
+        return fail(SDUGKS_ERR_INVALID_ARG, "tile_cells must be 0 or in [16, %d]", TILE_MAX);
+
+    Faces F;
+    int rc = merge_periodic(*m, F);
+    if (rc) return rc;
+    const int64_t n = m->nc;
+
+    // cell -> faces over the merged faces (ascending merged face id)
+    std::vector<std::array<int64_t, MAXF>> slots(n);
+    std::vector<int> nslot(n, 0);
+    for (int64_t f = 0; f < F.nf; f++) {
+        for (int side = 0; side < 2; side++) {
+            const int64_t c = side == 0 ? F.own[f] : F.nbr[f];
+            if (c < 0) continue;
+            if (nslot[c] >= MAXF) return fail(SDUGKS_ERR_INVALID_MESH, "cell %lld has more than %d faces", (long long)c, MAXF);
+            slots[c][nslot[c]++] = f;
+        }
+    }
+    // LLSR normal matrix per cell: d = (face - own centre) - (face - other centre)
+    std::vector<double> nbd(n * MAXF * 2, 0.0), ainv(3 * n, 0.0);
+    for (int64_t c = 0; c < n; c++) {
+        double axx = 0, axy = 0, ayy = 0;
+        for (int sl = 0; sl < nslot[c]; sl++) {
+            const int64_t f = slots[c][sl];
+            if (F.nbr[f] < 0) continue;
+            const bool mine = F.own[f] == c;
+            const double *rme = mine ? &F.ro[2 * f] : &F.rk[2 * f];
+            const double *rot = mine ? &F.rk[2 * f] : &F.ro[2 * f];
+            const double dx = rme[0] - rot[0], dy = rme[1] - rot[1];
+            nbd[(c * MAXF + sl) * 2] = dx;
+            nbd[(c * MAXF + sl) * 2 + 1] = dy;
+            axx += dx * dx; axy += dx * dy; ayy += dy * dy;
+        }
+        const double det = axx * ayy - axy * axy, tr = axx + ayy;
+        if (det > 1e-14 * tr * tr) {
+            ainv[3 * c] = ayy / det; ainv[3 * c + 1] = -axy / det; ainv[3 * c + 2] = axx / det;
+        }
+    }
+
+    // ---- tiles: RCB, then halo rings; tiles whose halo overflows are split again
+    const size_t cap0 = prm->tile_cells ? (size_t)prm->tile_cells : (size_t)TILE_MAX;
+    std::vector<int32_t> ids(n);
+    std::iota(ids.begin(), ids.end(), 0);
+    std::vector<std::pair<size_t, size_t>> tiles;
+    rcb(m->xc, ids, 0, (size_t)n, cap0, tiles);
+
+    auto other_of = [&](int64_t c, int sl) -> int64_t {
+        const int64_t f = slots[c][sl];
+        if (F.nbr[f] < 0) return -1;
+        return F.own[f] == c ? F.nbr[f] : F.own[f];
+    };
+    std::vector<int32_t> stamp(n, -1), local(n, 0);
+    struct TileHalo { std::vector<int32_t> r1, r2; };
+    std::vector<TileHalo> halos;
+    std::vector<std::pair<size_t, size_t>> final_tiles;
+    int32_t tag = 0;
+    for (size_t ti = 0; ti < tiles.size(); ti++) {
+        const auto [lo, hi] = tiles[ti];
+        tag++;
+        for (size_t i = lo; i < hi; i++) stamp[ids[i]] = tag;
+        TileHalo h;
+        for (size_t i = lo; i < hi; i++)
+            for (int sl = 0; sl < nslot[ids[i]]; sl++) {
+                const int64_t k = other_of(ids[i], sl);
+                if (k >= 0 && stamp[k] != tag) { stamp[k] = tag; h.r1.push_back((int32_t)k); }
+            }
+        for (int32_t c1 : h.r1)
+            for (int sl = 0; sl < nslot[c1]; sl++) {
+                const int64_t k = other_of(c1, sl);
+                if (k >= 0 && stamp[k] != tag) { stamp[k] = tag; h.r2.push_back((int32_t)k); }
+            }
+        const size_t nint = hi - lo;
+        if (nint + h.r1.size() + h.r2.size() > (size_t)LOC_MAX || nint + h.r1.size() > (size_t)SIG_MAX) {
+            if (nint <= 8) return fail(SDUGKS_ERR_INVALID_MESH, "halo of a %zu-cell tile does not fit", nint);
+            std::vector<std::pair<size_t, size_t>> sub;
+            rcb(m->xc, ids, lo, hi, (nint + 1) / 2, sub);
+            tiles.insert(tiles.begin() + ti + 1, sub.begin(), sub.end());
+            continue;
+        }
+        final_tiles.push_back(tiles[ti]);
+        halos.push_back(std::move(h));
+    }
+    const int32_t nt = (int32_t)final_tiles.size();
+    // internal order: tiles in RCB order
+    std::vector<int32_t> perm(n), iperm(n);
+    {
+        int64_t k = 0;
+        for (auto &t : final_tiles)
+            for (size_t i = t.first; i < t.second; i++) perm[k++] = ids[i];
+        for (int64_t i = 0; i < n; i++) iperm[perm[i]] = (int32_t)i;
+    }
+    // faces renumbered by the smaller internal id of their cells (locality)
+    std::vector<int64_t> forder(F.nf);
+    std::iota(forder.begin(), forder.end(), 0);
+    auto fkey = [&](int64_t f) {
+        int64_t a = iperm[F.own[f]];
+        if (F.nbr[f] >= 0) a = std::min<int64_t>(a, iperm[F.nbr[f]]);
+        return a;
+    };
+    std::stable_sort(forder.begin(), forder.end(), [&](int64_t a, int64_t b) { return fkey(a) < fkey(b); });
+    std::vector<int64_t> fnew(F.nf);
+    for (int64_t k = 0; k < F.nf; k++) fnew[forder[k]] = k;
+
+    const int64_t npad = (n + 31) / 32 * 32, fpad = (F.nf + 31) / 32 * 32;
+    std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), halo;
+    std::vector<uint16_t> sig_nb;
+    std::vector<int32_t> cface(MAXF * npad, -1);
+    std::vector<uint16_t> fo_local(MAXF * npad, NO_LOCAL);
+    // per internal cell: slots re-sorted by new face id, with nbd permuted alongside
+    std::vector<std::array<int64_t, MAXF>> islot(n);
+    std::vector<int> insl(n);
+    std::vector<double> inbd(MAXF * 2 * npad, 0.0);
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t c = perm[i];
+        std::array<int, MAXF> ord{0, 1, 2, 3};
+        std::sort(ord.begin(), ord.begin() + nslot[c], [&](int x, int y) { return fnew[slots[c][x]] < fnew[slots[c][y]]; });
+        insl[i] = nslot[c];
+        for (int sl = 0; sl < nslot[c]; sl++) {
+            islot[i][sl] = slots[c][ord[sl]];
+            cface[sl * npad + i] = (int32_t)fnew[slots[c][ord[sl]]];
+            inbd[(2 * sl) * npad + i] = nbd[(c * MAXF + ord[sl]) * 2];
+            inbd[(2 * sl + 1) * npad + i] = nbd[(c * MAXF + ord[sl]) * 2 + 1];
+        }
+    }
+    int64_t halo_total = 0;
+    {
+        int32_t c0 = 0, hoff = 0, soff = 0;
+        for (int32_t t = 0; t < nt; t++) {
+            const int32_t nint = (int32_t)(final_tiles[t].second - final_tiles[t].first);
+            tile_c0[t] = c0; tile_h0[t] = hoff; tile_s0[t] = soff;
+            std::vector<int32_t> r1, r2;
+            for (int32_t c : halos[t].r1) r1.push_back(iperm[c]);
+            for (int32_t c : halos[t].r2) r2.push_back(iperm[c]);
+            std::sort(r1.begin(), r1.end());
+            std::sort(r2.begin(), r2.end());
+            tile_nh1[t] = (int32_t)r1.size();
+            // local numbering: interior, ring 1, ring 2
+            for (int32_t i = 0; i < nint; i++) local[c0 + i] = i;
+            for (size_t k = 0; k < r1.size(); k++) local[r1[k]] = nint + (int32_t)k;
+            for (size_t k = 0; k < r2.size(); k++) local[r2[k]] = nint + (int32_t)(r1.size() + k);
+            halo.insert(halo.end(), r1.begin(), r1.end());
+            halo.insert(halo.end(), r2.begin(), r2.end());
+            auto push_sig = [&](int32_t i) {
+                std::array<uint16_t, MAXF> row;
+                row.fill(NO_LOCAL);
+                for (int sl = 0; sl < insl[i]; sl++) {
+                    const int64_t f = islot[i][sl];
+                    if (F.nbr[f] < 0) continue;
+                    const int64_t c = perm[i];
+                    const int64_t k = F.own[f] == c ? F.nbr[f] : F.own[f];
+                    row[sl] = (uint16_t)local[iperm[k]];
+                }
+                sig_nb.insert(sig_nb.end(), row.begin(), row.end());
+            };
+            for (int32_t i = 0; i < nint; i++) push_sig(c0 + i);
+            for (int32_t c : r1) push_sig(c);
+            for (int32_t i = 0; i < nint; i++) {
+                const int32_t g = c0 + i;
+                for (int sl = 0; sl < insl[g]; sl++) {
+                    const int64_t f = islot[g][sl];
+                    if (F.nbr[f] < 0) continue;
+                    const int64_t c = perm[g];
+                    const int64_t k = F.own[f] == c ? F.nbr[f] : F.own[f];
+                    fo_local[sl * npad + g] = (uint16_t)local[iperm[k]];
+                }
+            }
+            c0 += nint;
+            hoff += (int32_t)(r1.size() + r2.size());
+            soff += nint + (int32_t)r1.size();
+            halo_total += (int64_t)(r1.size() + r2.size());
+        }
+        tile_c0[nt] = c0; tile_h0[nt] = hoff; tile_s0[nt] = soff;
+    }
+    // face arrays in new order, internal cell ids
+    std::vector<int32_t> fown(F.nf), fnbr(F.nf);
+    std::vector<double> fnl(2 * fpad, 0.0), fro(2 * fpad, 0.0), frk(2 * fpad, 0.0);
+    for (int64_t f = 0; f < F.nf; f++) {
+        const int64_t k = fnew[f];
+        fown[k] = iperm[F.own[f]];
+        fnbr[k] = F.nbr[f] >= 0 ? iperm[F.nbr[f]] : (int32_t)F.nbr[f];
+        fnl[k] = F.nl[2 * f]; fnl[fpad + k] = F.nl[2 * f + 1];
+        fro[k] = F.ro[2 * f]; fro[fpad + k] = F.ro[2 * f + 1];
+        frk[k] = F.rk[2 * f]; frk[fpad + k] = F.rk[2 * f + 1];
+    }
+    // ---- every index the kernel dereferences is checked here, on the host
+    for (int32_t t = 0; t < nt; t++) {
+        const int32_t nint = tile_c0[t + 1] - tile_c0[t];
+        const int32_t nloc = nint + (tile_h0[t + 1] - tile_h0[t]);
+        const int32_t nsig = nint + tile_nh1[t];
+        if (nint < 1 || nint > TILE_MAX || nloc > LOC_MAX || nsig > SIG_MAX || tile_s0[t + 1] - tile_s0[t] != nsig)
+            return fail(SDUGKS_ERR_INVALID_MESH, "internal: tile %d sizes out of range", t);
+        for (int32_t k = tile_h0[t]; k < tile_h0[t + 1]; k++)
+            if (halo[k] < 0 || halo[k] >= n) return fail(SDUGKS_ERR_INVALID_MESH, "internal: halo id out of range");
+        for (int64_t k = (int64_t)tile_s0[t] * MAXF; k < (int64_t)tile_s0[t + 1] * MAXF; k++)
+            if (sig_nb[k] != NO_LOCAL && sig_nb[k] >= nloc)
+                return fail(SDUGKS_ERR_INVALID_MESH, "internal: gradient neighbour outside the tile's cells");
+        for (int32_t g = tile_c0[t]; g < tile_c0[t + 1]; g++) {
+            bool ended = false;
+            for (int sl = 0; sl < MAXF; sl++) {
+                const int32_t f = cface[sl * npad + g];
+                if (f < 0) { ended = true; continue; }
+                if (ended || f >= F.nf || (sl > 0 && f <= cface[(sl - 1) * npad + g]))
+                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: face slots of a cell out of order");
+                if (fown[f] != g && fnbr[f] != g) return fail(SDUGKS_ERR_INVALID_MESH, "internal: face not on its cell");
+                if (fnbr[f] >= 0) {
+                    if (fo_local[sl * npad + g] >= nsig) return fail(SDUGKS_ERR_INVALID_MESH, "internal: face neighbour outside ring 1");
+                } else {
+                    const int32_t p = -1 - fnbr[f];
+                    if (p >= MAXPATCH || m->bc_kind[p] == SDUGKS_BC_UNSET || m->bc_kind[p] == SDUGKS_BC_PERIODIC)
+                        return fail(SDUGKS_ERR_BAD_BC, "internal: boundary face without a usable condition");
+                }
+            }
+        }
+    }
+
+    std::vector<double> ivol(npad, 1.0), idtv(npad, 0.0), iainv(3 * npad, 0.0);
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t c = perm[i];
+        ivol[i] = m->vol[c];
+        idtv[i] = prm->dt / m->vol[c];
+        for (int d = 0; d < 3; d++) iainv[d * npad + i] = ainv[3 * c + d];
+    }
+
+    // ---- device allocation (one arena) and upload
+    sdugks_solver *s = new (std::nothrow) sdugks_solver;
+    if (!s) return fail(SDUGKS_ERR_OOM, "host allocation failed");
+    s->p = *prm;
+    if (s->p.graph_steps == 0) s->p.graph_steps = 60;
+    if (s->p.graph_steps > 0) s->p.graph_steps = std::max(6, s->p.graph_steps / 6 * 6);
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->n = n; s->npad = npad; s->nf = F.nf; s->fpad = fpad; s->n_tiles = nt; s->halo_cells = halo_total;
+    s->kernel = SDUGKS_KERNEL_TILED;
+    const int prec = prm->precision;
+    const size_t rs = prec == P_FP64 ? sizeof(double) : sizeof(float);
+    const size_t fs = prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2);
+    s->n_red_blocks = residual_blocks(n);
+
+    auto layout = [&](Arena &A) {
+        s->perm = A.take<int32_t>(npad);
+        s->vol = A.take<double>(npad);
+        s->snap = A.take<double>(2 * npad);
+        s->partial = A.take<double>(4 * (size_t)s->n_red_blocks);
+        s->red = A.take<double>(4);
+        for (int b = 0; b < 2; b++) s->st.f[b] = A.take<char>(NQ * npad * fs);
+        for (int b = 0; b < 3; b++) s->st.W[b] = A.take<double>(3 * npad);
+        s->tm.tile_c0 = A.take<int32_t>(nt + 1);
+        s->tm.tile_h0 = A.take<int32_t>(nt + 1);
+        s->tm.tile_nh1 = A.take<int32_t>(nt);
+        s->tm.tile_s0 = A.take<int32_t>(nt + 1);
+        s->tm.halo = A.take<int32_t>(std::max<size_t>(1, halo.size()));
+        s->tm.sig_nb = A.take<uint16_t>(sig_nb.size());
+        s->tm.cface = A.take<int32_t>(MAXF * npad);
+        s->tm.fo_local = A.take<uint16_t>(MAXF * npad);
+        s->tm.fown = A.take<int32_t>(fpad);
+        s->tm.fnbr = A.take<int32_t>(fpad);
+        s->tm.dtV = A.take<double>(npad);
+        s->tm.vol = s->vol;
+        s->tm.nbd = A.take<char>(MAXF * 2 * npad * rs);
+        s->tm.ainv = A.take<char>(3 * npad * rs);
+        s->tm.nl = A.take<char>(2 * fpad * rs);
+        s->tm.ro = A.take<char>(2 * fpad * rs);
+        s->tm.rk = A.take<char>(2 * fpad * rs);
+    };
+    Arena A0;
+    layout(A0);
+    s->dbytes = A0.used + 256;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dmem, s->dbytes);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail(e == cudaErrorMemoryAllocation ? SDUGKS_ERR_OOM : SDUGKS_ERR_CUDA, "cudaMalloc(%zu): %s",
+                    A0.used, cudaGetErrorString(e));
+    }
+    Arena A{s->dmem, 0, s->dbytes};
+    layout(A);
+    s->tm.n_tiles = nt; s->tm.n = n; s->tm.npad = npad; s->tm.nf = F.nf; s->tm.fpad = fpad;
+
+    auto conv = [&](const std::vector<double> &v) {
+        std::vector<char> out(v.size() * rs);
+        if (prec == P_FP64) std::memcpy(out.data(), v.data(), out.size());
+        else {
+            float *o = reinterpret_cast<float *>(out.data());
+            for (size_t k = 0; k < v.size(); k++) o[k] = (float)v[k];
+        }
+        return out;
+    };
+    std::vector<int32_t> permpad(npad, 0);
+    std::copy(perm.begin(), perm.end(), permpad.begin());
+    std::vector<int32_t> fownp(fpad, 0), fnbrp(fpad, -1);
+    std::copy(fown.begin(), fown.end(), fownp.begin());
+    std::copy(fnbr.begin(), fnbr.end(), fnbrp.begin());
+    auto up = [&](const void *dst, const void *src, size_t bytes) {
+        return cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
+    };
+    const std::vector<char> gnbd = conv(inbd), gainv = conv(iainv), gnl = conv(fnl), gro = conv(fro), grk = conv(frk);
+    int rc2 = SDUGKS_OK;
+    auto chk = [&](cudaError_t ee, const char *what) {
+        if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
+    };
+    chk(cudaMemset(s->dmem, 0, s->dbytes), "memset");
+    chk(up(s->perm, permpad.data(), npad * 4), "upload perm");
+    chk(up(s->vol, ivol.data(), npad * 8), "upload vol");
+    chk(up(s->tm.tile_c0, tile_c0.data(), (nt + 1) * 4), "upload tiles");
+    chk(up(s->tm.tile_h0, tile_h0.data(), (nt + 1) * 4), "upload tiles");
+    chk(up(s->tm.tile_nh1, tile_nh1.data(), nt * 4), "upload tiles");
+    chk(up(s->tm.tile_s0, tile_s0.data(), (nt + 1) * 4), "upload tiles");
+    if (!halo.empty()) chk(up(s->tm.halo, halo.data(), halo.size() * 4), "upload halo");
+    chk(up(s->tm.sig_nb, sig_nb.data(), sig_nb.size() * 2), "upload sig_nb");
+    chk(up(s->tm.cface, cface.data(), cface.size() * 4), "upload cface");
+    chk(up(s->tm.fo_local, fo_local.data(), fo_local.size() * 2), "upload fo_local");
+    chk(up(s->tm.fown, fownp.data(), fpad * 4), "upload fown");
+    chk(up(s->tm.fnbr, fnbrp.data(), fpad * 4), "upload fnbr");
+    chk(up(s->tm.dtV, idtv.data(), npad * 8), "upload dtV");
+    chk(up(s->tm.nbd, gnbd.data(), gnbd.size()), "upload nbd");
+    chk(up(s->tm.ainv, gainv.data(), gainv.size()), "upload ainv");
+    chk(up(s->tm.nl, gnl.data(), gnl.size()), "upload nl");
+    chk(up(s->tm.ro, gro.data(), gro.size()), "upload ro");
+    chk(up(s->tm.rk, grk.data(), grk.size()), "upload rk");
+    chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
+    chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    chk((cudaError_t)prepare(prec), "kernel attributes");
+    if (rc2) { sdugks_solver_destroy(s); return rc2; }
+
+    // coefficients
+    Coefs &c = s->coefs;
+    const double tau = prm->tau, dt = prm->dt;
+    c.a_plus = (2.0 * tau - dt) / (2.0 * tau);
+    c.b_plus = dt / (2.0 * tau);
+    c.c_face = 2.0 * tau / (2.0 * tau + dt);
+    c.r = dt / tau;
+    c.inv1r = 1.0 / (1.0 + dt / tau);
+    c.dt = dt;
+    c.tie = 1e-12;
+    for (int q = 0; q < MAXPATCH; q++) {
+        c.bc_kind[q] = m->bc_kind[q];
+        for (int k = 0; k < 3; k++) c.bc_par[q][k] = m->bc_par[q][k];
+    }
+    // mesh bytes read per cell and step by the tiled kernel (interior cells): slot data,
+    // LLSR data for interior and ring-1 cells, halo ids, face data (read by both sides)
+    {
+        const double sigc = (double)(n + [&] { int64_t a = 0; for (int t = 0; t < nt; t++) a += tile_nh1[t]; return a; }()) / n;
+        const double per_face = 4 + 4 + 6 * rs;   // fown, fnbr, nl, ro, rk
+        s->mesh_bytes = MAXF * (4 + 2) + 8 + sigc * (MAXF * (2 + 2 * rs) + 3 * rs) + (double)halo_total / n * 4 +
+                        2.0 * F.nf / n * per_face;
+    }
+    *out = s;
+    return SDUGKS_OK;
+}
+
+static int ensure_staging(sdugks_solver *s)
+{
+    if (s->staging) return SDUGKS_OK;
+    CUDA_TRY(cudaSetDevice(s->device));
+    CUDA_TRY(cudaMalloc(&s->staging, sizeof(double) * 15 * (size_t)std::max<int64_t>(s->n, 1)));
+    return SDUGKS_OK;
+}
+
+static int snapshot(sdugks_solver *s, double *eps, double *mass)
+{
+    CUDA_TRY(launch_residual(s->n, s->npad, s->st.W[s->w0], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
+                             s->stream));
+    CUDA_TRY(cudaMemcpyAsync(s->h_red, s->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    const double num = s->h_red[0], den = s->h_red[1];
+    if (mass) *mass = s->h_red[2];
+    if (s->h_red[3] != 0.0) {
+        if (eps) *eps = NAN;
+        return fail(SDUGKS_ERR_DIVERGED, "%g cells hold non-finite or zero-density W after %lld steps", s->h_red[3],
+                    (long long)s->steps_done);
+    }
+    if (eps) *eps = den > 0.0 ? std::sqrt(num) / std::sqrt(den) : INFINITY;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_init(sdugks_solver *s, const double *rho, const double *u)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    CUDA_TRY(cudaSetDevice(s->device));
+    int rc = ensure_staging(s);
+    if (rc) return rc;
+    double *d_rho = rho ? s->staging : nullptr;
+    double *d_u = u ? s->staging + s->n : nullptr;
+    if (rho) CUDA_TRY(cudaMemcpyAsync(d_rho, rho, sizeof(double) * s->n, cudaMemcpyHostToDevice, s->stream));
+    if (u) CUDA_TRY(cudaMemcpyAsync(d_u, u, sizeof(double) * 2 * s->n, cudaMemcpyHostToDevice, s->stream));
+    s->cur = 0; s->w0 = 0; s->steps_done = 0;
+    CUDA_TRY(launch_init_state(s->p.precision, s->n, s->npad, s->perm, d_rho, d_u, s->st.f[0], s->st.W[0], s->st.W[1],
+                               s->stream));
+    s->initialised = true;
+    return snapshot(s, nullptr, nullptr);
+}
+
+static int ensure_graph(sdugks_solver *s)
+{
+    if (s->graph) return SDUGKS_OK;
+    const int G = s->p.graph_steps;
+    const int cur0 = s->cur, w00 = s->w0;
+    s->cur = 0; s->w0 = 0;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < G && e == cudaSuccess; k++) e = launch_one(s, s->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+    s->cur = cur0; s->w0 = w00;
+    CUDA_TRY(e);
+    CUDA_TRY(e2);
+    e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    s->graph_len = G;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_step(sdugks_solver *s, int64_t n)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (n < 0) return fail(SDUGKS_ERR_INVALID_ARG, "negative step count");
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "step before init or set_state");
+    CUDA_TRY(cudaSetDevice(s->device));
+    int64_t left = n;
+    const int G = s->p.graph_steps;
+    if (G > 0 && left >= 2 * G) {
+        while (left > 0 && (s->steps_done % 6) != 0) {
+            CUDA_TRY(launch_one(s, s->stream));
+            s->steps_done++; left--;
+        }
+        int rc = ensure_graph(s);
+        if (rc) return rc;
+        while (left >= G) {
+            CUDA_TRY(cudaGraphLaunch(s->graph, s->stream));
+            s->steps_done += G; left -= G;
+            // a graph of G (multiple of 6) steps leaves the buffer phase unchanged
+        }
+    }
+    while (left > 0) {
+        CUDA_TRY(launch_one(s, s->stream));
+        s->steps_done++; left--;
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double *d_u)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_macros before init");
+    CUDA_TRY(cudaSetDevice(s->device));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->w0], d_rho, d_u, s->stream));
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_get_macros(sdugks_solver *s, double *rho, double *u)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_macros before init");
+    CUDA_TRY(cudaSetDevice(s->device));
+    int rc = ensure_staging(s);
+    if (rc) return rc;
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->w0], s->staging, s->staging + s->n, s->stream));
+    if (rho) CUDA_TRY(cudaMemcpyAsync(rho, s->staging, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+    if (u) CUDA_TRY(cudaMemcpyAsync(u, s->staging + s->n, sizeof(double) * 2 * s->n, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_residual(sdugks_solver *s, double *eps, double *mass)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "residual before init");
+    CUDA_TRY(cudaSetDevice(s->device));
+    return snapshot(s, eps, mass);
+}
+
+extern "C" int sdugks_get_state(sdugks_solver *s, double *f, double *W, double *W_next)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_state before init");
+    CUDA_TRY(cudaSetDevice(s->device));
+    int rc = ensure_staging(s);
+    if (rc) return rc;
+    double *df = s->staging, *dW = s->staging + 9 * s->n, *dWn = s->staging + 12 * s->n;
+    CUDA_TRY(launch_pack_state(s->p.precision, s->n, s->npad, s->perm, s->st.f[s->cur], s->st.W[s->w0],
+                               s->st.W[(s->w0 + 1) % 3], df, dW, dWn, s->stream));
+    if (f) CUDA_TRY(cudaMemcpyAsync(f, df, sizeof(double) * 9 * s->n, cudaMemcpyDeviceToHost, s->stream));
+    if (W) CUDA_TRY(cudaMemcpyAsync(W, dW, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
+    if (W_next) CUDA_TRY(cudaMemcpyAsync(W_next, dWn, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_set_state(sdugks_solver *s, const double *f, const double *W, const double *W_next)
+{
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (!f || !W || !W_next) return fail(SDUGKS_ERR_INVALID_ARG, "f, W and W_next are required");
+    CUDA_TRY(cudaSetDevice(s->device));
+    int rc = ensure_staging(s);
+    if (rc) return rc;
+    double *df = s->staging, *dW = s->staging + 9 * s->n, *dWn = s->staging + 12 * s->n;
+    CUDA_TRY(cudaMemcpyAsync(df, f, sizeof(double) * 9 * s->n, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(dW, W, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(dWn, W_next, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
+    s->cur = 0; s->w0 = 0; s->steps_done = 0;
+    CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, df, dW, dWn, s->st.f[0], s->st.W[0],
+                                 s->st.W[1], s->stream));
+    s->initialised = true;
+    return snapshot(s, nullptr, nullptr);
+}
+
+extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
+{
+    if (!s || !o) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    std::memset(o, 0, sizeof *o);
+    o->n_cells = s->n;
+    o->n_faces = s->nf;
+    o->n_tiles = s->n_tiles;
+    o->halo_cells = s->halo_cells;
+    o->steps_done = s->steps_done;
+    o->device_bytes = (int64_t)s->dbytes + (s->staging ? (int64_t)(15 * sizeof(double) * s->n) : 0);
+    const double fb = s->p.precision == P_FP64 ? 8 : (s->p.precision == P_FP32 ? 4 : 2);
+    o->state_bytes_per_cell_step = 2 * NQ * fb + 3 * 3 * 8;   // f read + write; W^n, W^{n+1} read, W^{n+2} write
+    o->mesh_bytes_per_cell_step = s->mesh_bytes;
+    o->kernel = s->kernel;
+    o->precision = s->p.precision;
+    o->tile_cells = s->p.tile_cells ? s->p.tile_cells : TILE_MAX;
+    return SDUGKS_OK;
+}
+
+extern "C" void sdugks_solver_destroy(sdugks_solver *s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->staging) cudaFree(s->staging);
+    if (s->h_red) cudaFreeHost(s->h_red);
+    if (s->dmem) cudaFree(s->dmem);
+    delete s;
+}
+
+extern "C" const char *sdugks_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *sdugks_version(void) { return "sdugks 0.1 sm_103a"; }

@@ -1,0 +1,107 @@
+// sdugks_internal.h -- launch interface between the host library (sdugks_host.cpp)
+// and the CUDA translation units.  Plain structs of device pointers and sizes.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sdugks {
+
+constexpr int NQ = 9;
+constexpr int MAXF = 4;         // faces per cell (quads and triangles)
+constexpr int MAXPATCH = 64;    // boundary patches
+constexpr uint16_t NO_LOCAL = 0xFFFF;
+
+// Tiled kernel shape: one CTA per tile, one thread per interior cell.
+constexpr int TILE_MAX = 128;   // interior cells per tile (= threads per CTA)
+constexpr int LOC_MAX = 416;    // interior + two halo rings
+constexpr int SIG_MAX = 272;    // interior + first halo ring (cells whose gradient is needed)
+
+enum Prec : int32_t { P_FP64 = 0, P_FP32 = 1, P_BF16DEV = 2 };
+
+enum BcKind : int32_t { BK_UNSET = 0, BK_PERIODIC = 1, BK_WALL = 2, BK_MOVING_WALL = 3,
+                        BK_FARFIELD = 4, BK_OUTLET = 5 };
+
+// Scalars of one step (host-computed in FP64 from tau and dt).
+struct Coefs {
+    double a_plus;   // (2 tau - dt) / (2 tau)
+    double b_plus;   // dt / (2 tau)
+    double c_face;   // 2 tau / (2 tau + dt)
+    double r;        // dt / tau
+    double inv1r;    // 1 / (1 + dt / tau)
+    double dt;
+    double tie;      // |xi . n l| <= tie counts as tangential
+    int32_t bc_kind[MAXPATCH];
+    double bc_par[MAXPATCH][3];
+};
+
+// Unstructured tiled mesh on the device.  Cells are in internal (tile-contiguous)
+// order; arrays indexed by cell are padded to npad, by face to fpad.
+struct TiledMesh {
+    int32_t n_tiles;
+    int64_t n, npad, nf, fpad;
+    const int32_t *tile_c0;   // [n_tiles+1] interior cell range of each tile
+    const int32_t *tile_h0;   // [n_tiles+1] range into halo
+    const int32_t *tile_nh1;  // [n_tiles]   cells of ring 1 (first in the tile's halo)
+    const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb
+    const int32_t *halo;      // internal ids of ring 1 then ring 2 of each tile
+    const uint16_t *sig_nb;   // [sum n_sig][MAXF] local index of each face neighbour
+    const int32_t *cface;     // [MAXF][npad] face id per slot (ascending), -1 = none
+    const uint16_t *fo_local; // [MAXF][npad] local index of the cell across an interior face
+    const int32_t *fown;      // [nf] owner (internal id)
+    const int32_t *fnbr;      // [nf] neighbour (internal id) or -1 - patch
+    const double *dtV;        // [npad] dt / V
+    const double *vol;        // [npad] V
+    // geometry in FP64 and FP32 (each kernel reads its own precision)
+    const void *nbd;          // [MAXF][2][npad] x_k - x_j per slot
+    const void *ainv;         // [3][npad] LLSR inverse (xx, xy, yy)
+    const void *nl;           // [2][fpad] normal * length, out of the owner
+    const void *ro;           // [2][fpad] face centre - owner centre
+    const void *rk;           // [2][fpad] face centre - neighbour centre (periodic image)
+};
+
+// Uniform Cartesian grid: cell (i, j) -> internal id i + nx j.
+struct CartMesh {
+    int32_t nx, ny;
+    int64_t n, npad;
+    double dx, dy;
+    int32_t side_patch[4];    // patch of the bottom, right, top, left side (-1 = periodic)
+    bool periodic_x, periodic_y;
+};
+
+// Device state of one solver.  f: [2][NQ][npad] (element type by precision).
+// W: three rotating [3][npad] FP64 buffers holding W^n, W^{n+1}, W^{n+2}.
+struct State {
+    void *f[2];
+    double *W[3];
+};
+
+// fused step kernels (k_step_fp64.cu, k_step_fp32.cu); prepare_* sets the kernel
+// attributes on the current device and is called once per solver creation
+cudaError_t prepare_tiled(int prec);
+cudaError_t launch_step_tiled(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
+                              const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st);
+cudaError_t prepare_tiled_fp64();
+cudaError_t launch_step_tiled_fp64(const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
+                                   const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st);
+cudaError_t prepare_tiled_fp32(int prec);
+cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
+                                   const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st);
+
+// state conversions between the caller's cell-major FP64 layout (user cell order)
+// and the internal SoA layout; perm[internal] = user id.
+cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *rho,
+                              const double *u, void *f, double *W0, double *W1, cudaStream_t st);
+cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const void *f,
+                              const double *W, const double *Wn1, double *f_out, double *W_out,
+                              double *Wn1_out, cudaStream_t st);
+cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *f_in,
+                                const double *W_in, const double *Wn1_in, void *f, double *W, double *Wn1,
+                                cudaStream_t st);
+cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const double *W, double *rho,
+                          double *u, cudaStream_t st);
+// residual: snap [2][npad] (U0, V0); partial [blocks][4]; out[4] = (num, den, mass, nonfinite)
+cudaError_t launch_residual(int64_t n, int64_t npad, const double *W, const double *vol, double *snap,
+                            double *partial, int n_blocks, double *out, cudaStream_t st);
+int residual_blocks(int64_t n);
+
+}  // namespace sdugks

@@ -1,0 +1,227 @@
+"""ctypes binding of libsdugks (include/sdugks.h): argument marshalling only.
+
+Every step of the S-DUGKS update runs in the library's CUDA kernels; this module
+converts numpy arrays and torch tensors to pointers and raises ``SdugksError`` on a
+non-zero status.  There is no fallback: if the library cannot be built or loaded,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+from . import meshes as _meshes
+
+_lock = threading.Lock()
+_lib = None
+
+FP64, FP32, FP32_BF16DEV = 0, 1, 2
+KERNEL_AUTO, KERNEL_TILED, KERNEL_CARTESIAN = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16dev": FP32_BF16DEV}
+ERRORS = {-1: "INVALID_ARG", -2: "INVALID_MESH", -3: "BAD_BC", -4: "OOM", -5: "DIVERGED", -6: "TIMEOUT",
+          -7: "CUDA", -8: "STATE"}
+
+
+class SdugksError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        super().__init__(f"{what}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class Params(C.Structure):
+    _fields_ = [("tau", C.c_double), ("dt", C.c_double), ("precision", C.c_int32), ("kernel", C.c_int32),
+                ("tile_cells", C.c_int32), ("graph_steps", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_tiles", C.c_int64), ("halo_cells", C.c_int64),
+                ("steps_done", C.c_int64), ("device_bytes", C.c_int64), ("state_bytes_per_cell_step", C.c_double),
+                ("mesh_bytes_per_cell_step", C.c_double), ("kernel", C.c_int32), ("precision", C.c_int32),
+                ("tile_cells", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/sdugks.h."""
+    with open(os.path.join(_build.INCLUDE, "sdugks.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdugks_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Build (if stale) and load libsdugks; raises if that is not possible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            P, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+            sig = {
+                "sdugks_mesh_create": [i64, P, i64, P, P, P, i64, P],
+                "sdugks_set_bc": [P, i32, i32, P],
+                "sdugks_mesh_cfl_dt": [P, dbl, P],
+                "sdugks_mesh_sizes": [P, P, P, P],
+                "sdugks_solver_create": [P, P, P, P],
+                "sdugks_init": [P, P, P],
+                "sdugks_step": [P, i64],
+                "sdugks_get_macros": [P, P, P],
+                "sdugks_get_macros_device": [P, P, P],
+                "sdugks_residual": [P, P, P],
+                "sdugks_get_state": [P, P, P, P],
+                "sdugks_set_state": [P, P, P, P],
+                "sdugks_solver_info": [P, P],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.sdugks_mesh_destroy.argtypes = [P]
+            L.sdugks_mesh_destroy.restype = None
+            L.sdugks_solver_destroy.argtypes = [P]
+            L.sdugks_solver_destroy.restype = None
+            L.sdugks_last_error.restype = C.c_char_p
+            L.sdugks_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _ck(rc: int, what: str):
+    if rc != 0:
+        raise SdugksError(rc, what, lib().sdugks_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Mesh:
+    """sdugks_mesh: geometry from a face-based owner/neighbour mesh plus boundary table."""
+
+    def __init__(self, mesh: _meshes.Mesh, bcs=()):
+        L = lib()
+        self._h = C.c_void_p()
+        xy = _f64(mesh.points)
+        fp = np.ascontiguousarray(mesh.face_pts, np.int64)
+        own = np.ascontiguousarray(mesh.owner, np.int64)
+        nbr = np.ascontiguousarray(mesh.neighbour, np.int64)
+        _ck(L.sdugks_mesh_create(xy.shape[0], _ptr(xy), fp.shape[0], _ptr(fp), _ptr(own), _ptr(nbr),
+                                 int(mesh.n_cells), C.byref(self._h)), "sdugks_mesh_create")
+        self.n_cells = int(mesh.n_cells)
+        for patch, kind, par in bcs:
+            self.set_bc(patch, kind, par)
+
+    def set_bc(self, patch: int, kind: int, params=(0.0, 0.0, 0.0)):
+        p = _f64(list(params) + [0.0] * (3 - len(params)))
+        _ck(lib().sdugks_set_bc(self._h, int(patch), int(kind), _ptr(p)), "sdugks_set_bc")
+
+    def cfl_dt(self, cfl: float) -> float:
+        out = C.c_double()
+        _ck(lib().sdugks_mesh_cfl_dt(self._h, float(cfl), C.byref(out)), "sdugks_mesh_cfl_dt")
+        return out.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sdugks_mesh_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """sdugks_solver on the current CUDA device; ``stream`` is a torch.cuda.Stream,
+    a raw cudaStream_t integer, or None for the default stream."""
+
+    def __init__(self, mesh: Mesh, tau: float, dt: float, precision="fp32", *, kernel=KERNEL_AUTO,
+                 tile_cells=0, graph_steps=0, stream=None):
+        L = lib()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.params = Params(float(tau), float(dt), prec, int(kernel), int(tile_cells), int(graph_steps))
+        sh = getattr(stream, "cuda_stream", stream)
+        self._h = C.c_void_p()
+        _ck(L.sdugks_solver_create(mesh._h, C.byref(self.params), C.c_void_p(sh or 0), C.byref(self._h)),
+            "sdugks_solver_create")
+        self.n = mesh.n_cells
+
+    @classmethod
+    def from_case(cls, case: _meshes.Case, precision="fp32", **kw):
+        m = Mesh(case.mesh, case.bcs)
+        s = cls(m, case.tau, case.dt, precision, **kw)
+        s._mesh = m
+        return s
+
+    def init(self, rho=None, u=None):
+        r = None if rho is None else _f64(rho, (self.n,))
+        v = None if u is None else _f64(u, (self.n, 2))
+        _ck(lib().sdugks_init(self._h, _ptr(r), _ptr(v)), "sdugks_init")
+        return self
+
+    def step(self, n: int = 1):
+        _ck(lib().sdugks_step(self._h, int(n)), "sdugks_step")
+        return self
+
+    def macros(self):
+        rho = np.empty(self.n)
+        u = np.empty((self.n, 2))
+        _ck(lib().sdugks_get_macros(self._h, _ptr(rho), _ptr(u)), "sdugks_get_macros")
+        return rho, u
+
+    def macros_device(self, rho_t=None, u_t=None):
+        """Write rho [n] and u [n, 2] (FP64 torch CUDA tensors) on the solver's stream."""
+        _ck(lib().sdugks_get_macros_device(self._h, C.c_void_p(rho_t.data_ptr() if rho_t is not None else 0),
+                                           C.c_void_p(u_t.data_ptr() if u_t is not None else 0)),
+            "sdugks_get_macros_device")
+
+    def residual(self):
+        eps, mass = C.c_double(), C.c_double()
+        _ck(lib().sdugks_residual(self._h, C.byref(eps), C.byref(mass)), "sdugks_residual")
+        return eps.value, mass.value
+
+    def get_state(self):
+        f = np.empty((self.n, 9)); W = np.empty((self.n, 3)); Wn = np.empty((self.n, 3))
+        _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W), _ptr(Wn)), "sdugks_get_state")
+        return f, W, Wn
+
+    def get_state_into(self, f, W, Wn):
+        """Like get_state into caller-provided (e.g. pinned) float64 arrays."""
+        _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W), _ptr(Wn)), "sdugks_get_state")
+
+    def set_state(self, f, W, Wn):
+        f = _f64(f, (self.n, 9)); W = _f64(W, (self.n, 3)); Wn = _f64(Wn, (self.n, 3))
+        _ck(lib().sdugks_set_state(self._h, _ptr(f), _ptr(W), _ptr(Wn)), "sdugks_set_state")
+        return self
+
+    def info(self) -> dict:
+        out = Info()
+        _ck(lib().sdugks_solver_info(self._h, C.byref(out)), "sdugks_solver_info")
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sdugks_solver_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,92 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every function that
+include/sdugks.h declares, and its host-only entry points (mesh geometry, boundary
+table, CFL time step, argument validation) behave as documented.  No kernel runs."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+from paper_2007_07347_gb300 import meshes as M
+from paper_2007_07347_gb300 import sdugks as S
+
+
+def test_library_exports_every_declared_function():
+    L = S.lib()
+    names = S.header_functions()
+    assert "sdugks_step" in names and "sdugks_mesh_create" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert L.sdugks_version().decode().startswith("sdugks")
+
+
+def test_mesh_create_and_cfl_dt():
+    case = M.cavity(8)
+    m = S.Mesh(case.mesh, case.bcs)
+    # dx_min = 1 (unit squares): dt = cfl / sqrt(2)
+    assert abs(m.cfl_dt(0.5) - 0.5 / math.sqrt(2)) < 1e-15
+    cyl = M.cylinder(64, 32, first=0.01, r_far=10.0)
+    m2 = S.Mesh(cyl.mesh, cyl.bcs)
+    dt = m2.cfl_dt(0.5)
+    # area / longest face of the first ring is just under its radial thickness 0.01
+    assert 0.5 * 0.0098 / math.sqrt(2) < dt <= 0.5 * 0.01 / math.sqrt(2)
+
+
+def test_mesh_sizes():
+    case = M.couette(16)
+    m = S.Mesh(case.mesh, case.bcs)
+    nc, nf, npch = C.c_int64(), C.c_int64(), C.c_int32()
+    S._ck(S.lib().sdugks_mesh_sizes(m._h, C.byref(nc), C.byref(nf), C.byref(npch)), "sizes")
+    assert (nc.value, nf.value, npch.value) == (64, case.mesh.n_faces, 4)
+
+
+def test_invalid_mesh_rejected():
+    mesh = M.cartesian(3, 3)
+    bad = M.Mesh(mesh.points, mesh.face_pts.copy(), mesh.owner.copy(), mesh.neighbour.copy(), mesh.n_cells,
+                 mesh.patches)
+    bad.face_pts[4] = [0, 0]                      # degenerate face
+    with pytest.raises(S.SdugksError) as e:
+        S.Mesh(bad)
+    assert e.value.name == "INVALID_MESH"
+    open_cell = M.Mesh(mesh.points, mesh.face_pts[1:], mesh.owner[1:], mesh.neighbour[1:], mesh.n_cells, mesh.patches)
+    with pytest.raises(S.SdugksError) as e:
+        S.Mesh(open_cell)                         # cell 0 lost a face: 3 faces, not closed
+    assert e.value.name == "INVALID_MESH"
+
+
+def test_bad_bc_arguments():
+    m = S.Mesh(M.cartesian(2, 2))
+    with pytest.raises(S.SdugksError) as e:
+        m.set_bc(70, M.BC_WALL)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(S.SdugksError):
+        m.set_bc(0, 99)
+    with pytest.raises(S.SdugksError):
+        m.set_bc(0, M.BC_FARFIELD, (0.0, 0.1, 0.0))
+
+
+def test_solver_create_validates_before_touching_the_device():
+    case = M.cavity(4)
+    m = S.Mesh(case.mesh, [])                      # no boundary conditions
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver(m, 0.1, 0.1)
+    assert e.value.name in ("BAD_BC",)
+    m2 = S.Mesh(case.mesh, case.bcs)
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver(m2, -1.0, 0.1)
+    assert e.value.name == "INVALID_ARG"
+    # a periodic patch whose faces do not match its partner's
+    c = M.periodic_box(3, 3)
+    bcs = list(c.bcs)
+    bcs[0] = (3, M.BC_PERIODIC, (1, 2.0, 0.0))     # wrong shift
+    m3 = S.Mesh(c.mesh, bcs)
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver(m3, 0.1, 0.1)
+    assert e.value.name == "BAD_BC"
+
+
+def test_last_error_message_is_set():
+    with pytest.raises(S.SdugksError) as e:
+        S.Mesh(M.Mesh(np.zeros((0, 2)), np.zeros((0, 2), np.int64), np.zeros(0, np.int64),
+                      np.zeros(0, np.int64), 0, {}))
+    assert "empty" in str(e.value)

@@ -1,0 +1,225 @@
+"""GPU parity of the CUDA S-DUGKS step (through the C-ABI) with the FP64 oracle.
+
+Tolerances (written next to each check):
+* FP64 mode: max |gpu - oracle| / max |oracle| <= 1e-12 for f, W and W^{n+1}.  Both
+  sides evaluate the same sums in FP64 but in different orders (and the library's
+  geometry is computed by a different formula), so agreement is to rounding.
+* FP32 mode: relative L2 error of u against the FP64 oracle <= 1e-4 after the
+  stated steps (FP32 round-off of ~6e-8 per operation accumulated over the run,
+  with headroom), and max |rho - rho_oracle| <= 1e-5.
+* BF16-deviation storage: relative L2 error of u <= 1e-2.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_07347_gb300 import meshes as M
+
+pytestmark = pytest.mark.gpu
+
+
+def _S():
+    from paper_2007_07347_gb300 import sdugks as S
+    return S
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def rel_l2(a, b):
+    return np.sqrt(np.sum((a - b) ** 2) / max(np.sum(b ** 2), 1e-300))
+
+
+def run_both(case, steps, precision="fp64", rho=None, u=None, **kw):
+    S = _S()
+    s = S.Solver.from_case(case, precision, **kw)
+    s.init(rho, u)
+    s.step(steps)
+    g = s.get_state()
+    st = O.init(case.mesh.n_cells, rho=rho, u=u)
+    O.run(case, st, steps)
+    return s, g, st
+
+
+def _mixed3():
+    mesh = M.cartesian(3, 3, 3.0, 1.5)
+    bcs = [(0, M.BC_WALL, (0, 0, 0)), (2, M.BC_MOVING_WALL, (0.1, 0, 0)), (3, M.BC_FARFIELD, (1, 0.05, 0)),
+           (1, M.BC_OUTLET, (0, 0, 0))]
+    return M.Case("mixed3", mesh, bcs, tau=0.1, dt=0.25)
+
+
+def _random_state(case, seed, amp=0.03):
+    rng = np.random.default_rng(seed)
+    n = case.mesh.n_cells
+    return 1.0 + amp * rng.uniform(-1, 1, n), amp * rng.uniform(-1, 1, (n, 2))
+
+
+FP64_CASES = {
+    "couette_4x64": (lambda: M.couette(64), 2000, None),
+    "cavity_48": (lambda: M.cavity(48, Re=400.0), 1000, None),
+    "mixed_bc_3x3": (_mixed3, 40, 7),
+    "periodic_jittered": (lambda: M.periodic_box(24, 20, jitter=0.2, seed=4, tau=0.05, dt=0.2), 300, "smooth"),
+    "cylinder_64x32_shuffled": (lambda: M.cylinder(64, 32, first=0.01, r_far=10.0, shuffle_seed=3), 400, None),
+}
+
+
+@pytest.mark.parametrize("name", list(FP64_CASES))
+def test_fp64_matches_oracle(name):
+    make, steps, init = FP64_CASES[name]
+    case = make()
+    rho = u = None
+    if init == "smooth":
+        rho, u = M.smooth_field(case, seed=3)
+    elif isinstance(init, int):
+        rho, u = _random_state(case, init)
+    elif case.u0 != (0.0, 0.0):
+        u = np.tile(case.u0, (case.mesh.n_cells, 1))
+    s, (f, W, Wn), st = run_both(case, steps, "fp64", rho, u)
+    assert relmax(f, st.f) <= 1e-12
+    assert relmax(W, st.W) <= 1e-12
+    assert relmax(Wn, O.macro_update(case, st)) <= 1e-12
+    assert np.abs(st.W[:, 1:]).max() > 0 or name == "couette_4x64"
+
+
+def test_fp64_full_size_cylinder_and_cavity():
+    """The configs' full meshes (512 x 256 shuffled O-mesh, 256^2 cavity), a few steps."""
+    for case, steps in ((M.cylinder(512, 256), 12), (M.cavity(256), 30)):
+        u = np.tile(case.u0, (case.mesh.n_cells, 1)) if case.u0 != (0.0, 0.0) else None
+        s, (f, W, Wn), st = run_both(case, steps, "fp64", None, u)
+        assert relmax(f, st.f) <= 1e-12
+        assert relmax(W, st.W) <= 1e-12
+        assert relmax(Wn, O.macro_update(case, st)) <= 1e-12
+
+
+def test_fp64_couette_steady_state():
+    """Couette config (4 x 64, U = 0.1, Re = 10, CFL 0.5) run to residual < 1e-10 on the GPU:
+    the analytic linear profile (Sec. IV) and the oracle's steady state."""
+    S = _S()
+    case = M.couette(64)
+    s = S.Solver.from_case(case, "fp64").init()
+    steps = 0
+    while steps < 200000:
+        s.step(1000)
+        steps += 1000
+        eps, _ = s.residual()
+        if eps < 1e-10:
+            break
+    assert eps < 1e-10
+    rho, u = s.macros()
+    y = case.mesh.meta["cell_xy_nominal"][:, 1]
+    assert rel_l2(u[:, 0], 0.1 * y) < 1e-8
+    assert np.abs(u[:, 1]).max() < 1e-12
+    st = O.init(case.mesh.n_cells)
+    O.run(case, st, steps)
+    assert relmax(u, st.u) <= 1e-9
+
+
+def test_tile_size_and_graphs_do_not_change_results():
+    """Each cell's sums run in a fixed order whatever the tiling, and a captured graph
+    replays the same launches: FP64 results are bit-identical."""
+    S = _S()
+    case = M.cylinder(96, 48, first=0.01, r_far=10.0, shuffle_seed=1)
+    u = np.tile(case.u0, (case.mesh.n_cells, 1))
+    out = []
+    for tile, graph in ((128, -1), (32, -1), (64, 12)):
+        s = S.Solver.from_case(case, "fp64", tile_cells=tile, graph_steps=graph).init(None, u)
+        s.step(150)
+        out.append(s.get_state())
+    for o in out[1:]:
+        for a, b in zip(o, out[0]):
+            np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(precision):
+    S = _S()
+    case = M.cavity(40, Re=400.0)
+    a = S.Solver.from_case(case, precision).init()
+    a.step(100)
+    ck = a.get_state()
+    a.step(130)
+    ref = a.get_state()
+    b = S.Solver.from_case(case, precision).set_state(*ck)
+    b.step(130)
+    for x, y in zip(b.get_state(), ref):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_fp32_cavity_full_size_against_oracle():
+    """256^2 cavity (Re 1000, lid 0.1) in FP32: 1000 steps against the FP64 oracle."""
+    case = M.cavity(256)
+    s, (f, W, Wn), st = run_both(case, 1000, "fp32")
+    rho, u = s.macros()
+    assert rel_l2(u, st.u) <= 1e-4
+    assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
+
+
+def test_fp32_cylinder_against_oracle():
+    case = M.cylinder(128, 64, first=0.01, r_far=20.0)
+    u0 = np.tile(case.u0, (case.mesh.n_cells, 1))
+    s, (f, W, Wn), st = run_both(case, 1500, "fp32", None, u0)
+    rho, u = s.macros()
+    assert rel_l2(u, st.u) <= 1e-4
+    assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
+
+
+def test_bf16dev_cylinder_against_oracle():
+    case = M.cylinder(128, 64, first=0.01, r_far=20.0)
+    u0 = np.tile(case.u0, (case.mesh.n_cells, 1))
+    s, (f, W, Wn), st = run_both(case, 1500, "bf16dev", None, u0)
+    rho, u = s.macros()
+    assert rel_l2(u, st.u) <= 1e-2
+
+
+def test_residual_matches_oracle():
+    S = _S()
+    case = M.cavity(32, Re=100.0)
+    s = S.Solver.from_case(case, "fp64").init()
+    st = O.init(case.mesh.n_cells)
+    vol = O.geometry(case.mesh, case.bcs)["vol"]
+    for _ in range(3):
+        Ws = st.W.copy()
+        s.step(200)
+        O.run(case, st, 200)
+        eps, mass = s.residual()
+        eps_o, mass_o = O.residual(st.W, Ws, vol)
+        assert abs(eps - eps_o) <= 1e-10 * eps_o
+        assert abs(mass - mass_o) <= 1e-12 * mass_o
+
+
+def test_fp32_mass_conservation_periodic():
+    """Fully periodic box: W accumulates the telescoping face fluxes in FP64."""
+    S = _S()
+    case = M.periodic_box(64, 48, jitter=0.2, seed=2, tau=0.05, dt=0.2)
+    rho0, u0 = M.smooth_field(case, seed=5)
+    s = S.Solver.from_case(case, "fp32").init(rho0, u0)
+    _, m0 = s.residual()
+    s.step(3000)
+    _, m1 = s.residual()
+    assert abs(m1 - m0) <= 1e-9 * m0
+
+
+def test_errors_are_status_codes_not_faults():
+    S = _S()
+    case = M.cavity(16)
+    s = S.Solver.from_case(case, "fp32")
+    with pytest.raises(S.SdugksError) as e:
+        s.step(1)
+    assert e.value.name == "STATE"
+    s.init()
+    f, W, Wn = s.get_state()
+    W[3, 0] = np.nan
+    with pytest.raises(S.SdugksError) as e:
+        s.set_state(f, W, Wn)       # set_state takes the residual snapshot, which sees the NaN
+    assert e.value.name == "DIVERGED"
+    s.step(5)                       # NaN propagates through values only, never into indices
+    with pytest.raises(S.SdugksError) as e:
+        s.residual()
+    assert e.value.name == "DIVERGED"
+    s.init()                        # the solver stays usable
+    s.step(5)
+    eps, mass = s.residual()
+    assert np.isfinite(mass)
