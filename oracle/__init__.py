@@ -5,8 +5,7 @@ this.  It builds ``sdugks_oracle.c`` with gcc (FP64, ``-ffp-contract=off``, Open
 over independent cell and face loops) and wraps it with ctypes.  It shares no code
 with the CUDA library.
 
-Every routine is pinned by CPU tests (tests/test_oracle_pins.py and
-tests/test_oracle_handstep.py).
+Every routine is pinned by the CPU tests in tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 
@@ -51,8 +50,8 @@ def _load():
             lib.oracle_feq.argtypes = [dbl, dbl, dbl, P]
             lib.oracle_geometry.argtypes = mesh_args + [P, P, P, P, P, P]
             lib.oracle_gradient.argtypes = mesh_args + [P, P]
-            lib.oracle_run.argtypes = mesh_args + [dbl, dbl, i64, P, P, P]
-            lib.oracle_init.argtypes = [i64, P, P, P, P, P]
+            lib.oracle_run.argtypes = mesh_args + [dbl, dbl, i64, P, P]
+            lib.oracle_init.argtypes = [i64, P, P, P, P]
             lib.oracle_residual.argtypes = [i64, P, P, P, P, P]
             lib.oracle_set_threads.argtypes = [i32]
             for fn in ("oracle_feq", "oracle_geometry", "oracle_gradient", "oracle_run",
@@ -119,13 +118,13 @@ def gradient(mesh, bcs, phi):
 
 
 class State:
-    """Oracle state at t_n: f [N,9], W [N,3] = (rho, rho u), M [N,3] = F_macro^n."""
+    """Oracle state at t_n: f [N,9], W [N,3] = (rho, rho u)."""
 
-    def __init__(self, f, W, M):
-        self.f, self.W, self.M = f, W, M
+    def __init__(self, f, W):
+        self.f, self.W = f, W
 
     def copy(self):
-        return State(self.f.copy(), self.W.copy(), self.M.copy())
+        return State(self.f.copy(), self.W.copy())
 
     @property
     def rho(self):
@@ -139,26 +138,20 @@ class State:
 def init(n_cells: int, rho=None, u=None, rho0: float = 1.0, u0=(0.0, 0.0)) -> State:
     rho = np.full(n_cells, rho0) if rho is None else np.ascontiguousarray(rho, np.float64)
     u = np.tile(np.asarray(u0, float), (n_cells, 1)) if u is None else np.ascontiguousarray(u, np.float64)
-    f = np.empty((n_cells, NQ)); W = np.empty((n_cells, 3)); M = np.empty((n_cells, 3))
-    _check(_load().oracle_init(n_cells, _p(rho), _p(u), _p(f), _p(W), _p(M)), "init")
-    return State(f, W, M)
+    f = np.empty((n_cells, NQ)); W = np.empty((n_cells, 3))
+    _check(_load().oracle_init(n_cells, _p(rho), _p(u), _p(f), _p(W)), "init")
+    return State(f, W)
 
 
 def run(case, state: State, n_steps: int, *, tau=None, dt=None) -> State:
     """Advance ``state`` in place by n_steps steps of the case's mesh/BCs."""
     m = _MeshArgs(case.mesh, case.bcs)
-    for a in (state.f, state.W, state.M):
+    for a in (state.f, state.W):
         assert a.flags.c_contiguous and a.dtype == np.float64
     _check(_load().oracle_run(*m.args(), float(case.tau if tau is None else tau),
                               float(case.dt if dt is None else dt), int(n_steps),
-                              _p(state.f), _p(state.W), _p(state.M)), "run")
+                              _p(state.f), _p(state.W)), "run")
     return state
-
-
-def macro_update(case, state: State) -> np.ndarray:
-    """W^{n+1} = W^n - dt/V F_macro^n (Eq. MacroUpdate) for the given state."""
-    vol = geometry(case.mesh, case.bcs)["vol"]
-    return state.W - (case.dt / vol)[:, None] * state.M
 
 
 def residual(W, Ws, vol=None):

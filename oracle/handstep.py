@@ -9,8 +9,9 @@ polynomial D2Q9 equilibrium every quantity of the step is rational, so this resu
 is exact and the FP64 oracle must agree with it to rounding.
 
 Readings shared with the oracle (they are readings of the paper, not code): D2Q9 with
-c_s^2 = 1/3, F_macro^n = moments of the previous step's mesoscopic flux (zero at
-start), upwind by the sign of xi.n with the two-sided mean for tangential
+c_s^2 = 1/3, the macroscopic flux of Eq. MacroUpdate = moments of the same step's
+mesoscopic flux (the moment of Eq. Integration), upwind by the sign of xi.n with the
+two-sided mean for tangential
 velocities, wall/far-field/outlet by non-equilibrium extrapolation for incoming
 velocities and interior reconstruction with the boundary Maxwellian otherwise.
 """
@@ -66,13 +67,12 @@ class Grid:
         return out
 
 
-def step(g: Grid, tau, dt, f, W, M):
-    """One step; f[c][9], W[c][3], M[c][3] lists of Fractions.  Returns new (f, W, M)."""
+def step(g: Grid, tau, dt, f, W):
+    """One step; f[c][9], W[c][3] lists of Fractions.  Returns the new (f, W)."""
     tau, dt = Fr(tau), Fr(dt)
     n = g.nx * g.ny
     vol = g.dx * g.dy
     ap, bp, cf, r = (2 * tau - dt) / (2 * tau), dt / (2 * tau), 2 * tau / (2 * tau + dt), dt / tau
-    Wn1 = [[W[c][d] - dt / vol * M[c][d] for d in range(3)] for c in range(n)]
     feqn = [feq_W(W[c]) for c in range(n)]
     fbp = [[ap * f[c][a] + bp * feqn[c][a] for a in range(9)] for c in range(n)]
     # least-squares gradient: solve (sum d d^T) sigma = sum d (phi_k - phi_j)
@@ -185,21 +185,21 @@ def step(g: Grid, tau, dt, f, W, M):
                 c = g.cid(i, g.ny - 1)
                 add_flux(c, nl, boundary_face(c, g.centre(i, g.ny - 1), xb, nl, "top"))
 
-    f_new, M_new = [], []
+    f_new, W_new = [], []
     for c in range(n):
-        fe1 = feq_W(Wn1[c])
+        mac = [sum(F[c]), sum(XI[a][0] * F[c][a] for a in range(9)), sum(XI[a][1] * F[c][a] for a in range(9))]
+        w1 = [W[c][d] - dt / vol * mac[d] for d in range(3)]
+        fe1 = feq_W(w1)
         f_new.append([(f[c][a] - dt / vol * F[c][a] + r * fe1[a]) / (1 + r) for a in range(9)])
-        M_new.append([sum(F[c]), sum(XI[a][0] * F[c][a] for a in range(9)),
-                      sum(XI[a][1] * F[c][a] for a in range(9))])
-    return f_new, Wn1, M_new
+        W_new.append(w1)
+    return f_new, W_new
 
 
 def run(g: Grid, tau, dt, rho, u, n_steps):
-    """Start from f = feq(rho, u), M = 0 and take n_steps steps; returns (f, W, M)."""
+    """Start from f = feq(rho, u) and take n_steps steps; returns (f, W)."""
     n = g.nx * g.ny
     W = [[Fr(rho[c]), Fr(rho[c]) * Fr(u[c][0]), Fr(rho[c]) * Fr(u[c][1])] for c in range(n)]
     f = [feq(Fr(rho[c]), Fr(u[c][0]), Fr(u[c][1])) for c in range(n)]
-    M = [[Fr(0)] * 3 for _ in range(n)]
     for _ in range(n_steps):
-        f, W, M = step(g, tau, dt, f, W, M)
-    return f, W, M
+        f, W = step(g, tau, dt, f, W)
+    return f, W

@@ -19,7 +19,7 @@
  *   xy[n_points][2], face_pts[n_faces][2], owner[n_faces], neighbour[n_faces]
  *   (neighbour < 0 means boundary patch -1-neighbour),
  *   bc_kind[n_patches], bc_par[n_patches][3],
- *   f[n_cells][9], W[n_cells][3] = (rho, rho*u_x, rho*u_y), M[n_cells][3].
+ *   f[n_cells][9], W[n_cells][3] = (rho, rho*u_x, rho*u_y).
  */
 #include <math.h>
 #include <stdint.h>
@@ -343,27 +343,24 @@ static void boundary_macros(int kind, const double *par, const double Wo[3], dou
 }
 
 typedef struct {
-    double *Wn1, *feqn, *fbp, *sig, *fb, *F;
+    double *feqn, *fbp, *sig, *fb, *F;
 } owork;
 
-/* One S-DUGKS step, the eleven steps of Sec. II in the paper's order.
- * State at t_n: f (cell-centred distribution), W (conserved variables) and
- * M = F_macro^n (reading A3: the macroscopic flux of the interface distribution at
- * t_n, i.e. the moments of the previous step's mesoscopic flux; zero at start). */
-static void one_step(const omesh *m, double tau, double dt, double *f, double *W, double *M,
-                     owork *w)
+/* One S-DUGKS step, the eleven steps of Sec. II.  State at t_n: f (cell-centred
+ * distribution) and W (conserved variables).
+ * Reading A3 of the macroscopic flux in Eq. MacroUpdate: Eq. MacroUpdate is the
+ * moment psi = (1, xi) of Eq. Integration, whose flux is F_meso^{n+1}, so the
+ * macroscopic flux is the moment of the mesoscopic flux of this same step, built
+ * from the interface distribution f(x_b, t_{n+1}) of step 7.  It is therefore
+ * evaluated with step 8 and applied in step 9.  (A lagged reading that uses the
+ * previous step's interface distribution diverges on the cavity at dt = 10 tau,
+ * where the paper reports converged runs.) */
+static void one_step(const omesh *m, double tau, double dt, double *f, double *W, owork *w)
 {
     const int64_t nc = m->nc, nf = m->nf;
     const double a_plus = (2.0 * tau - dt) / (2.0 * tau);  /* Eq. fbarplus */
     const double b_plus = dt / (2.0 * tau);
     const double c_face = 2.0 * tau / (2.0 * tau + dt);    /* Eq. f_t_n+1 */
-
-    /* Step 1 + Eq. MacroUpdate, evaluated now and applied in step 9:
-     * W^{n+1} = W^n - dt/V F_macro^n. */
-#pragma omp parallel for schedule(static)
-    for (int64_t j = 0; j < nc; j++)
-        for (int d = 0; d < 3; d++)
-            w->Wn1[3 * j + d] = W[3 * j + d] - dt / m->vol[j] * M[3 * j + d];
 
     /* Step 2, Eq. fbarplus at the cell centre: fbar+ = (2tau-dt)/(2tau) f + dt/(2tau) feq(W^n). */
 #pragma omp parallel for schedule(static)
@@ -450,60 +447,55 @@ static void one_step(const omesh *m, double tau, double dt, double *f, double *W
         for (int a = 0; a < NQ; a++) w->F[NQ * j + a] = Fj[a];
     }
 
-    /* Steps 9-11 and the macroscopic flux for the next step. */
+    /* Steps 1 and 9 (Eqs. MacroFlux, MacroUpdate), 10 and 11 (Eq. fn+1). */
     const double r = dt / tau;
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < nc; j++) {
-        double feq1[NQ];
-        for (int d = 0; d < 3; d++) W[3 * j + d] = w->Wn1[3 * j + d];      /* step 9 */
-        feq_of_W(&W[3 * j], feq1);                                        /* step 10 */
-        double Mj[3] = {0, 0, 0};
-        for (int a = 0; a < NQ; a++) {
+        double Mj[3] = {0, 0, 0}, feq1[NQ];
+        for (int a = 0; a < NQ; a++) {          /* macroscopic flux: moments psi = (1, xi) */
             double Fa = w->F[NQ * j + a];
-            /* step 11, Eq. fn+1 */
-            f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * Fa + r * feq1[a]) / (1.0 + r);
-            /* Eq. MacroFlux at t_{n+1}: moments psi = (1, xi) of the mesoscopic flux */
             Mj[0] += Fa;
             Mj[1] += XI[a][0] * Fa;
             Mj[2] += XI[a][1] * Fa;
         }
-        for (int d = 0; d < 3; d++) M[3 * j + d] = Mj[d];
+        for (int d = 0; d < 3; d++) W[3 * j + d] = W[3 * j + d] - dt / m->vol[j] * Mj[d];   /* step 9 */
+        feq_of_W(&W[3 * j], feq1);                                                          /* step 10 */
+        for (int a = 0; a < NQ; a++)                                                        /* step 11 */
+            f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * w->F[NQ * j + a] + r * feq1[a]) / (1.0 + r);
     }
 }
 
-/* Run n_steps steps in place on (f, W, M). */
+/* Run n_steps steps in place on (f, W). */
 int oracle_run(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, const int64_t *own,
                const int64_t *nbr, int64_t nc, int npatch, const int32_t *bck, const double *bcp,
-               double tau, double dt, int64_t n_steps, double *f, double *W, double *M)
+               double tau, double dt, int64_t n_steps, double *f, double *W)
 {
-    if (!(tau > 0) || !(dt > 0) || n_steps < 0 || !f || !W || !M) return OR_ERR_ARG;
+    if (!(tau > 0) || !(dt > 0) || n_steps < 0 || !f || !W) return OR_ERR_ARG;
     omesh m;
     int rc = omesh_build(&m, np, xy, nf, fpts, own, nbr, nc, npatch, bck, bcp);
     if (rc) return rc;
     owork w;
-    w.Wn1 = malloc(sizeof(double) * 3 * nc);
     w.feqn = malloc(sizeof(double) * NQ * nc);
     w.fbp = malloc(sizeof(double) * NQ * nc);
     w.sig = malloc(sizeof(double) * 2 * NQ * nc);
     w.fb = malloc(sizeof(double) * NQ * nf);
     w.F = malloc(sizeof(double) * NQ * nc);
-    if (!w.Wn1 || !w.feqn || !w.fbp || !w.sig || !w.fb || !w.F) rc = OR_ERR_NOMEM;
-    for (int64_t s = 0; s < n_steps && !rc; s++) one_step(&m, tau, dt, f, W, M, &w);
-    free(w.Wn1); free(w.feqn); free(w.fbp); free(w.sig); free(w.fb); free(w.F);
+    if (!w.feqn || !w.fbp || !w.sig || !w.fb || !w.F) rc = OR_ERR_NOMEM;
+    for (int64_t s = 0; s < n_steps && !rc; s++) one_step(&m, tau, dt, f, W, &w);
+    free(w.feqn); free(w.fbp); free(w.sig); free(w.fb); free(w.F);
     omesh_free(&m);
     return rc;
 }
 
-/* Initial state: f = feq(W0), M = 0 (reading A4). */
-int oracle_init(int64_t nc, const double *rho, const double *u, double *f, double *W, double *M)
+/* Initial state: W = (rho, rho u), f = feq(W). */
+int oracle_init(int64_t nc, const double *rho, const double *u, double *f, double *W)
 {
-    if (nc <= 0 || !rho || !u || !f || !W || !M) return OR_ERR_ARG;
+    if (nc <= 0 || !rho || !u || !f || !W) return OR_ERR_ARG;
     for (int64_t j = 0; j < nc; j++) {
         W[3 * j] = rho[j];
         W[3 * j + 1] = rho[j] * u[2 * j];
         W[3 * j + 2] = rho[j] * u[2 * j + 1];
         feq_of(rho[j], u[2 * j], u[2 * j + 1], &f[NQ * j]);
-        M[3 * j] = M[3 * j + 1] = M[3 * j + 2] = 0.0;
     }
     return OR_OK;
 }
