@@ -13,8 +13,8 @@ buffer is rewritten) before every timed step, outside its events.  The state of
 this case is 9.4 MB, so inside a step the 1000 launches run from L2.
 
 e2e: the same metric through the C-ABI from pinned host buffers: each step uploads
-the full state (f, W, W_next in FP64), advances 1000 steps, runs the residual and
-reads rho and u back.
+the full state (f, W in FP64), advances 1000 steps, runs the residual and reads rho
+and u back.
 
 --impl reference: the FP64 C oracle, as it stands, on the host cores, on bounded
 samples of the same workload (rank 0 only).
@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 from paper_2007_07347_gb300 import meshes as M  # noqa: E402
 
 INTERVAL = 1000
-STATE_BYTES = {"fp64": 240, "fp32": 144, "bf16dev": 108}   # f r+w, W^n and W^{n+1} read, W^{n+2} written
+STATE_BYTES = {"fp64": 192, "fp32": 120, "bf16dev": 84}    # f and W (FP64) each read and written once
 
 
 def parse():
@@ -265,10 +265,9 @@ def run_ours(args):
     # ---- e2e through the C-ABI with pinned host buffers
     f_h = torch.empty((n, 9), dtype=torch.float64).pin_memory().numpy()
     W_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-    Wn_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     rho_h = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
     u_h = torch.empty((n, 2), dtype=torch.float64).pin_memory().numpy()
-    s.get_state_into(f_h, W_h, Wn_h)
+    s.get_state_into(f_h, W_h)
     e2e_steps = max(3, min(args.steps, 10))
     import ctypes as C
     L = S.lib()
@@ -276,7 +275,7 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        S._ck(L.sdugks_set_state(s._h, P(f_h), P(W_h), P(Wn_h)), "set_state")
+        S._ck(L.sdugks_set_state(s._h, P(f_h), P(W_h)), "set_state")
         S._ck(L.sdugks_step(s._h, INTERVAL), "step")
         s.residual()
         S._ck(L.sdugks_get_macros(s._h, P(rho_h), P(u_h)), "get_macros")
@@ -301,7 +300,7 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": profiled_traffic(key),
                      "kernel": "k_step_tiled", "algorithmic_bytes_per_launch": alg_bytes,
                      "avg_launch_us": kern_avg_s * 1e6, "peak_kind": f"{peak_kind} (hbm_gbs)"},
-        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": n * 15 * 8,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": n * 12 * 8,
                 "d2h_bytes_per_step": n * 3 * 8 + 32, "steps": e2e_steps},
         "gpu_launches": args.steps * (INTERVAL + 2),
         "residual_last": eps_hist[-1][0], "mass_last": eps_hist[-1][1],

@@ -85,7 +85,7 @@ typedef struct sdugks_info {
     int64_t halo_cells;           /* summed over tiles (ring 1 + ring 2)               */
     int64_t steps_done;           /* steps since init / set_state                      */
     int64_t device_bytes;         /* device memory held by the solver                  */
-    double state_bytes_per_cell_step; /* f, W read and written once per cell and step */
+    double state_bytes_per_cell_step; /* f and W read and written once per cell and step */
     double mesh_bytes_per_cell_step;  /* mesh data the kernel reads per cell and step  */
     int32_t kernel;               /* SDUGKS_KERNEL_TILED or SDUGKS_KERNEL_CARTESIAN    */
     int32_t precision;
@@ -136,7 +136,7 @@ void sdugks_mesh_destroy(sdugks_mesh *mesh);
 int sdugks_solver_create(const sdugks_mesh *mesh, const sdugks_params *params, void *stream,
                          sdugks_solver **out);
 
-/* Initial state: W = (rho, rho u), f = feq(W) and zero macroscopic flux.
+/* Initial state: W = (rho, rho u), f = feq(W).
  * rho[n_cells], u[n_cells][2] (host); NULL rho means 1, NULL u means 0.
  * Also takes the residual snapshot.  Synchronises the stream. */
 int sdugks_init(sdugks_solver *s, const double *rho, const double *u);
@@ -161,15 +161,13 @@ int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double *d_u);
 int sdugks_residual(sdugks_solver *s, double *eps, double *mass);
 
 /* Checkpoint of the state at t_n (host, FP64, caller's cell order):
- *   f[n_cells][9]      cell distribution
- *   W[n_cells][3]      conserved variables at t_n
- *   W_next[n_cells][3] W at t_{n+1} = W - dt/V F_macro^n (Eq. MacroUpdate, computed
- *                      one step ahead; the macroscopic flux is kept in this form)
+ *   f[n_cells][9]  cell distribution
+ *   W[n_cells][3]  conserved variables
  * get synchronises; set replaces the state (f is rounded to the storage precision)
  * and refreshes the residual snapshot.  A run resumed from a checkpoint equals the
- * uninterrupted run bit for bit in FP64 and FP32 storage. */
-int sdugks_get_state(sdugks_solver *s, double *f, double *W, double *W_next);
-int sdugks_set_state(sdugks_solver *s, const double *f, const double *W, const double *W_next);
+ * uninterrupted run bit for bit with FP64 and FP32 storage. */
+int sdugks_get_state(sdugks_solver *s, double *f, double *W);
+int sdugks_set_state(sdugks_solver *s, const double *f, const double *W);
 
 int sdugks_solver_info(const sdugks_solver *s, sdugks_info *out);
 

@@ -10,10 +10,10 @@ cudaError_t prepare_tiled_fp32(int prec)
 }
 
 cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
-                                   const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st)
+                                   const double *W_in, double *W_out, cudaStream_t st)
 {
-    if (prec == P_BF16DEV) return launch_tiled_p<P_BF16DEV>(m, c, f_in, f_out, Wn, Wn1, Wn2, st);
-    return launch_tiled_p<P_FP32>(m, c, f_in, f_out, Wn, Wn1, Wn2, st);
+    if (prec == P_BF16DEV) return launch_tiled_p<P_BF16DEV>(m, c, f_in, f_out, W_in, W_out, st);
+    return launch_tiled_p<P_FP32>(m, c, f_in, f_out, W_in, W_out, st);
 }
 
 }  // namespace sdugks

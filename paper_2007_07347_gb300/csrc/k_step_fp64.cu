@@ -8,9 +8,9 @@ namespace sdugks {
 cudaError_t prepare_tiled_fp64() { return prepare_tiled_p<P_FP64>(); }
 
 cudaError_t launch_step_tiled_fp64(const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
-                                   const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st)
+                                   const double *W_in, double *W_out, cudaStream_t st)
 {
-    return launch_tiled_p<P_FP64>(m, c, f_in, f_out, Wn, Wn1, Wn2, st);
+    return launch_tiled_p<P_FP64>(m, c, f_in, f_out, W_in, W_out, st);
 }
 
 }  // namespace sdugks

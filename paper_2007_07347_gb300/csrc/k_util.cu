@@ -13,8 +13,7 @@ __device__ void feq9_d(double rho, double ux, double uy, double out[NQ]) { feq9<
 
 template <int P>
 __global__ void k_init(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const double *__restrict__ rho_in,
-                       const double *__restrict__ u_in, typename Store<P>::T *__restrict__ f, double *__restrict__ W0,
-                       double *__restrict__ W1)
+                       const double *__restrict__ u_in, typename Store<P>::T *__restrict__ f, double *__restrict__ W)
 {
     using R = typename Store<P>::R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -22,8 +21,7 @@ __global__ void k_init(int64_t n, int64_t npad, const int32_t *__restrict__ perm
         const double rho = rho_in ? rho_in[p] : 1.0;
         const double ux = u_in ? u_in[2 * p] : 0.0, uy = u_in ? u_in[2 * p + 1] : 0.0;
         const double w0 = rho, w1 = rho * ux, w2 = rho * uy;
-        W0[i] = w0; W0[npad + i] = w1; W0[2 * npad + i] = w2;
-        W1[i] = w0; W1[npad + i] = w1; W1[2 * npad + i] = w2;
+        W[i] = w0; W[npad + i] = w1; W[2 * npad + i] = w2;
         double fe[NQ];
         feq9_d(rho, ux, uy, fe);
         R r, x, y, feR[NQ];
@@ -36,8 +34,7 @@ __global__ void k_init(int64_t n, int64_t npad, const int32_t *__restrict__ perm
 
 template <int P>
 __global__ void k_pack(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const typename Store<P>::T *__restrict__ f,
-                       const double *__restrict__ W, const double *__restrict__ Wn1, double *__restrict__ f_out,
-                       double *__restrict__ W_out, double *__restrict__ Wn1_out)
+                       const double *__restrict__ W, double *__restrict__ f_out, double *__restrict__ W_out)
 {
     using R = typename Store<P>::R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -51,23 +48,17 @@ __global__ void k_pack(int64_t n, int64_t npad, const int32_t *__restrict__ perm
         }
         if (W_out)
             for (int d = 0; d < 3; d++) W_out[3 * p + d] = W[d * npad + i];
-        if (Wn1_out)
-            for (int d = 0; d < 3; d++) Wn1_out[3 * p + d] = Wn1[d * npad + i];
     }
 }
 
 template <int P>
 __global__ void k_unpack(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const double *__restrict__ f_in,
-                         const double *__restrict__ W_in, const double *__restrict__ Wn1_in,
-                         typename Store<P>::T *__restrict__ f, double *__restrict__ W, double *__restrict__ Wn1)
+                         const double *__restrict__ W_in, typename Store<P>::T *__restrict__ f, double *__restrict__ W)
 {
     using R = typename Store<P>::R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = perm[i];
-        for (int d = 0; d < 3; d++) {
-            W[d * npad + i] = W_in[3 * p + d];
-            Wn1[d * npad + i] = Wn1_in[3 * p + d];
-        }
+        for (int d = 0; d < 3; d++) W[d * npad + i] = W_in[3 * p + d];
         R r, x, y, fe[NQ];
         macro_of<R>(W_in[3 * p], W_in[3 * p + 1], W_in[3 * p + 2], r, x, y);
         feq9<R>(r, x, y, fe);
@@ -149,39 +140,38 @@ int grid_for(int64_t n) {
 }  // namespace
 
 cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *rho,
-                              const double *u, void *f, double *W0, double *W1, cudaStream_t st)
+                              const double *u, void *f, double *W, cudaStream_t st)
 {
     const int g = grid_for(n);
-    if (prec == P_FP64) k_init<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (double *)f, W0, W1);
-    else if (prec == P_FP32) k_init<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (float *)f, W0, W1);
-    else k_init<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (__nv_bfloat16 *)f, W0, W1);
+    if (prec == P_FP64) k_init<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (double *)f, W);
+    else if (prec == P_FP32) k_init<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (float *)f, W);
+    else k_init<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (__nv_bfloat16 *)f, W);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const void *f, const double *W,
-                              const double *Wn1, double *f_out, double *W_out, double *Wn1_out, cudaStream_t st)
+                              double *f_out, double *W_out, cudaStream_t st)
 {
     const int g = grid_for(n);
     if (prec == P_FP64)
-        k_pack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, (const double *)f, W, Wn1, f_out, W_out, Wn1_out);
+        k_pack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, (const double *)f, W, f_out, W_out);
     else if (prec == P_FP32)
-        k_pack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, (const float *)f, W, Wn1, f_out, W_out, Wn1_out);
+        k_pack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, (const float *)f, W, f_out, W_out);
     else
-        k_pack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, (const __nv_bfloat16 *)f, W, Wn1, f_out, W_out, Wn1_out);
+        k_pack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, (const __nv_bfloat16 *)f, W, f_out, W_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *f_in,
-                                const double *W_in, const double *Wn1_in, void *f, double *W, double *Wn1,
-                                cudaStream_t st)
+                                const double *W_in, void *f, double *W, cudaStream_t st)
 {
     const int g = grid_for(n);
     if (prec == P_FP64)
-        k_unpack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, Wn1_in, (double *)f, W, Wn1);
+        k_unpack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, (double *)f, W);
     else if (prec == P_FP32)
-        k_unpack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, Wn1_in, (float *)f, W, Wn1);
+        k_unpack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, (float *)f, W);
     else
-        k_unpack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, Wn1_in, (__nv_bfloat16 *)f, W, Wn1);
+        k_unpack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, (__nv_bfloat16 *)f, W);
     return cudaGetLastError();
 }
 

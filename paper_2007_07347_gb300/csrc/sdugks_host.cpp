@@ -360,7 +360,7 @@ struct sdugks_solver {
     double *staging = nullptr;      // [n][15] FP64, allocated on first use
     double *h_red = nullptr;        // pinned [4]
     bool initialised = false;
-    int cur = 0, w0 = 0;            // f buffer holding f^n; W buffer holding W^n
+    int cur = 0;                    // buffer (f and W) holding the state at t_n
     int64_t steps_done = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_len = 0;
@@ -374,16 +374,14 @@ static int prepare(int prec)
 
 static cudaError_t launch_one(sdugks_solver *s, cudaStream_t st)
 {
-    const int a = s->cur, b = s->w0;
-    const void *fin = s->st.f[a];
-    void *fout = s->st.f[1 - a];
-    const double *Wn = s->st.W[b], *Wn1 = s->st.W[(b + 1) % 3];
-    double *Wn2 = s->st.W[(b + 2) % 3];
+    const int a = s->cur;
     cudaError_t e;
-    if (s->p.precision == P_FP64) e = launch_step_tiled_fp64(s->tm, s->coefs, fin, fout, Wn, Wn1, Wn2, st);
-    else e = launch_step_tiled_fp32(s->p.precision, s->tm, s->coefs, fin, fout, Wn, Wn1, Wn2, st);
+    if (s->p.precision == P_FP64)
+        e = launch_step_tiled_fp64(s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
+    else
+        e = launch_step_tiled_fp32(s->p.precision, s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a],
+                                   s->st.W[1 - a], st);
     s->cur = 1 - a;
-    s->w0 = (b + 1) % 3;
     return e;
 }
 
@@ -629,7 +627,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     if (!s) return fail(SDUGKS_ERR_OOM, "host allocation failed");
     s->p = *prm;
     if (s->p.graph_steps == 0) s->p.graph_steps = 60;
-    if (s->p.graph_steps > 0) s->p.graph_steps = std::max(6, s->p.graph_steps / 6 * 6);
+    if (s->p.graph_steps > 0) s->p.graph_steps = std::max(2, s->p.graph_steps / 2 * 2);
     s->stream = static_cast<cudaStream_t>(stream);
     s->n = n; s->npad = npad; s->nf = F.nf; s->fpad = fpad; s->n_tiles = nt; s->halo_cells = halo_total;
     s->kernel = SDUGKS_KERNEL_TILED;
@@ -645,7 +643,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->partial = A.take<double>(4 * (size_t)s->n_red_blocks);
         s->red = A.take<double>(4);
         for (int b = 0; b < 2; b++) s->st.f[b] = A.take<char>(NQ * npad * fs);
-        for (int b = 0; b < 3; b++) s->st.W[b] = A.take<double>(3 * npad);
+        for (int b = 0; b < 2; b++) s->st.W[b] = A.take<double>(3 * npad);
         s->tm.tile_c0 = A.take<int32_t>(nt + 1);
         s->tm.tile_h0 = A.take<int32_t>(nt + 1);
         s->tm.tile_nh1 = A.take<int32_t>(nt);
@@ -754,13 +752,13 @@ static int ensure_staging(sdugks_solver *s)
 {
     if (s->staging) return SDUGKS_OK;
     CUDA_TRY(cudaSetDevice(s->device));
-    CUDA_TRY(cudaMalloc(&s->staging, sizeof(double) * 15 * (size_t)std::max<int64_t>(s->n, 1)));
+    CUDA_TRY(cudaMalloc(&s->staging, sizeof(double) * 12 * (size_t)std::max<int64_t>(s->n, 1)));
     return SDUGKS_OK;
 }
 
 static int snapshot(sdugks_solver *s, double *eps, double *mass)
 {
-    CUDA_TRY(launch_residual(s->n, s->npad, s->st.W[s->w0], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
+    CUDA_TRY(launch_residual(s->n, s->npad, s->st.W[s->cur], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
                              s->stream));
     CUDA_TRY(cudaMemcpyAsync(s->h_red, s->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -785,9 +783,8 @@ extern "C" int sdugks_init(sdugks_solver *s, const double *rho, const double *u)
     double *d_u = u ? s->staging + s->n : nullptr;
     if (rho) CUDA_TRY(cudaMemcpyAsync(d_rho, rho, sizeof(double) * s->n, cudaMemcpyHostToDevice, s->stream));
     if (u) CUDA_TRY(cudaMemcpyAsync(d_u, u, sizeof(double) * 2 * s->n, cudaMemcpyHostToDevice, s->stream));
-    s->cur = 0; s->w0 = 0; s->steps_done = 0;
-    CUDA_TRY(launch_init_state(s->p.precision, s->n, s->npad, s->perm, d_rho, d_u, s->st.f[0], s->st.W[0], s->st.W[1],
-                               s->stream));
+    s->cur = 0; s->steps_done = 0;
+    CUDA_TRY(launch_init_state(s->p.precision, s->n, s->npad, s->perm, d_rho, d_u, s->st.f[0], s->st.W[0], s->stream));
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);
 }
@@ -796,14 +793,14 @@ static int ensure_graph(sdugks_solver *s)
 {
     if (s->graph) return SDUGKS_OK;
     const int G = s->p.graph_steps;
-    const int cur0 = s->cur, w00 = s->w0;
-    s->cur = 0; s->w0 = 0;
+    const int cur0 = s->cur;
+    s->cur = 0;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < G && e == cudaSuccess; k++) e = launch_one(s, s->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
-    s->cur = cur0; s->w0 = w00;
+    s->cur = cur0;
     CUDA_TRY(e);
     CUDA_TRY(e2);
     e = cudaGraphInstantiate(&s->graph, g, 0);
@@ -822,7 +819,7 @@ extern "C" int sdugks_step(sdugks_solver *s, int64_t n)
     int64_t left = n;
     const int G = s->p.graph_steps;
     if (G > 0 && left >= 2 * G) {
-        while (left > 0 && (s->steps_done % 6) != 0) {
+        while (left > 0 && s->cur != 0) {
             CUDA_TRY(launch_one(s, s->stream));
             s->steps_done++; left--;
         }
@@ -831,7 +828,7 @@ extern "C" int sdugks_step(sdugks_solver *s, int64_t n)
         while (left >= G) {
             CUDA_TRY(cudaGraphLaunch(s->graph, s->stream));
             s->steps_done += G; left -= G;
-            // a graph of G (multiple of 6) steps leaves the buffer phase unchanged
+            // a graph of G (even) steps leaves the buffer phase unchanged
         }
     }
     while (left > 0) {
@@ -846,7 +843,7 @@ extern "C" int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double 
     if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
     if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_macros before init");
     CUDA_TRY(cudaSetDevice(s->device));
-    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->w0], d_rho, d_u, s->stream));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->cur], d_rho, d_u, s->stream));
     return SDUGKS_OK;
 }
 
@@ -857,7 +854,7 @@ extern "C" int sdugks_get_macros(sdugks_solver *s, double *rho, double *u)
     CUDA_TRY(cudaSetDevice(s->device));
     int rc = ensure_staging(s);
     if (rc) return rc;
-    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->w0], s->staging, s->staging + s->n, s->stream));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->cur], s->staging, s->staging + s->n, s->stream));
     if (rho) CUDA_TRY(cudaMemcpyAsync(rho, s->staging, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
     if (u) CUDA_TRY(cudaMemcpyAsync(u, s->staging + s->n, sizeof(double) * 2 * s->n, cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -872,37 +869,34 @@ extern "C" int sdugks_residual(sdugks_solver *s, double *eps, double *mass)
     return snapshot(s, eps, mass);
 }
 
-extern "C" int sdugks_get_state(sdugks_solver *s, double *f, double *W, double *W_next)
+extern "C" int sdugks_get_state(sdugks_solver *s, double *f, double *W)
 {
     if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
     if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_state before init");
     CUDA_TRY(cudaSetDevice(s->device));
     int rc = ensure_staging(s);
     if (rc) return rc;
-    double *df = s->staging, *dW = s->staging + 9 * s->n, *dWn = s->staging + 12 * s->n;
-    CUDA_TRY(launch_pack_state(s->p.precision, s->n, s->npad, s->perm, s->st.f[s->cur], s->st.W[s->w0],
-                               s->st.W[(s->w0 + 1) % 3], df, dW, dWn, s->stream));
+    double *df = s->staging, *dW = s->staging + 9 * s->n;
+    CUDA_TRY(launch_pack_state(s->p.precision, s->n, s->npad, s->perm, s->st.f[s->cur], s->st.W[s->cur], df, dW,
+                               s->stream));
     if (f) CUDA_TRY(cudaMemcpyAsync(f, df, sizeof(double) * 9 * s->n, cudaMemcpyDeviceToHost, s->stream));
     if (W) CUDA_TRY(cudaMemcpyAsync(W, dW, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
-    if (W_next) CUDA_TRY(cudaMemcpyAsync(W_next, dWn, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     return SDUGKS_OK;
 }
 
-extern "C" int sdugks_set_state(sdugks_solver *s, const double *f, const double *W, const double *W_next)
+extern "C" int sdugks_set_state(sdugks_solver *s, const double *f, const double *W)
 {
     if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
-    if (!f || !W || !W_next) return fail(SDUGKS_ERR_INVALID_ARG, "f, W and W_next are required");
+    if (!f || !W) return fail(SDUGKS_ERR_INVALID_ARG, "f and W are required");
     CUDA_TRY(cudaSetDevice(s->device));
     int rc = ensure_staging(s);
     if (rc) return rc;
-    double *df = s->staging, *dW = s->staging + 9 * s->n, *dWn = s->staging + 12 * s->n;
+    double *df = s->staging, *dW = s->staging + 9 * s->n;
     CUDA_TRY(cudaMemcpyAsync(df, f, sizeof(double) * 9 * s->n, cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaMemcpyAsync(dW, W, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(cudaMemcpyAsync(dWn, W_next, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
-    s->cur = 0; s->w0 = 0; s->steps_done = 0;
-    CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, df, dW, dWn, s->st.f[0], s->st.W[0],
-                                 s->st.W[1], s->stream));
+    s->cur = 0; s->steps_done = 0;
+    CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, df, dW, s->st.f[0], s->st.W[0], s->stream));
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);
 }
@@ -916,9 +910,9 @@ extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
     o->n_tiles = s->n_tiles;
     o->halo_cells = s->halo_cells;
     o->steps_done = s->steps_done;
-    o->device_bytes = (int64_t)s->dbytes + (s->staging ? (int64_t)(15 * sizeof(double) * s->n) : 0);
+    o->device_bytes = (int64_t)s->dbytes + (s->staging ? (int64_t)(12 * sizeof(double) * s->n) : 0);
     const double fb = s->p.precision == P_FP64 ? 8 : (s->p.precision == P_FP32 ? 4 : 2);
-    o->state_bytes_per_cell_step = 2 * NQ * fb + 3 * 3 * 8;   // f read + write; W^n, W^{n+1} read, W^{n+2} write
+    o->state_bytes_per_cell_step = 2 * NQ * fb + 2 * 3 * 8;   // f and W (FP64) read and written once
     o->mesh_bytes_per_cell_step = s->mesh_bytes;
     o->kernel = s->kernel;
     o->precision = s->p.precision;

@@ -68,35 +68,30 @@ struct CartMesh {
     bool periodic_x, periodic_y;
 };
 
-// Device state of one solver.  f: [2][NQ][npad] (element type by precision).
-// W: three rotating [3][npad] FP64 buffers holding W^n, W^{n+1}, W^{n+2}.
+// Device state of one solver, ping-pong: f [2][NQ][npad] (element type by
+// precision), W [2][3][npad] FP64.
 struct State {
     void *f[2];
-    double *W[3];
+    double *W[2];
 };
 
 // fused step kernels (k_step_fp64.cu, k_step_fp32.cu); prepare_* sets the kernel
 // attributes on the current device and is called once per solver creation
-cudaError_t prepare_tiled(int prec);
-cudaError_t launch_step_tiled(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
-                              const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st);
 cudaError_t prepare_tiled_fp64();
 cudaError_t launch_step_tiled_fp64(const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
-                                   const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st);
+                                   const double *W_in, double *W_out, cudaStream_t st);
 cudaError_t prepare_tiled_fp32(int prec);
 cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
-                                   const double *Wn, const double *Wn1, double *Wn2, cudaStream_t st);
+                                   const double *W_in, double *W_out, cudaStream_t st);
 
 // state conversions between the caller's cell-major FP64 layout (user cell order)
 // and the internal SoA layout; perm[internal] = user id.
 cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *rho,
-                              const double *u, void *f, double *W0, double *W1, cudaStream_t st);
+                              const double *u, void *f, double *W, cudaStream_t st);
 cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const void *f,
-                              const double *W, const double *Wn1, double *f_out, double *W_out,
-                              double *Wn1_out, cudaStream_t st);
+                              const double *W, double *f_out, double *W_out, cudaStream_t st);
 cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *f_in,
-                                const double *W_in, const double *Wn1_in, void *f, double *W, double *Wn1,
-                                cudaStream_t st);
+                                const double *W_in, void *f, double *W, cudaStream_t st);
 cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const double *W, double *rho,
                           double *u, cudaStream_t st);
 // residual: snap [2][npad] (U0, V0); partial [blocks][4]; out[4] = (num, den, mass, nonfinite)

@@ -5,11 +5,11 @@
 // two halo rings (Eq. fbarplus), then the LLSR gradient of its cells and of the
 // first ring, then every thread reconstructs the interface distribution on the
 // faces of its own cell along the characteristic (Eqs. fbpsource, fbar, Macro at the
-// face, Feq, f_t_n+1), sums the mesoscopic flux (Eq. MesoFlux) and updates f
-// (Eq. fn+1).  The macroscopic flux of the new interface values (Eq. MacroFlux) is
-// accumulated in FP64 and folded straight into W^{n+2} = W^{n+1} - dt/V F_macro^{n+1}
-// (Eq. MacroUpdate of the next step), so W rotates through three FP64 buffers and no
-// separate flux array is stored.
+// face, Feq, f_t_n+1) and sums the mesoscopic flux (Eq. MesoFlux).  Its moments, the
+// macroscopic flux (Eq. MacroFlux), are accumulated in FP64 into
+// W^{n+1} = W^n - dt/V F_macro (Eq. MacroUpdate, the moment of Eq. Integration), whose
+// equilibrium then closes the implicit cell update of f (Eq. fn+1).  f and W
+// ping-pong between two buffers each; nothing else is stored between steps.
 //
 // An interior face is evaluated by the threads of both cells with identical operands
 // in the same order, so both see the same interface values and the face fluxes
@@ -23,7 +23,7 @@ template <int P>
 __global__ void __launch_bounds__(TILE_MAX)
 k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__restrict__ fin,
              typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn,
-             const double *__restrict__ Wn1, double *__restrict__ Wn2)
+             double *__restrict__ Wout)
 {
     using R = typename Store<P>::R;
     using SP = Store<P>;
@@ -162,28 +162,31 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         }
     }
 
-    // ---- cell update: f^{n+1} (Eq. fn+1) with feq(W^{n+1}); W^{n+2} from the new flux
-    const double W0 = Wn1[g], W1 = Wn1[np + g], W2 = Wn1[2 * np + g];
+    // ---- macroscopic flux (FP64 moments of F) -> W^{n+1}; cell update f^{n+1} (Eq. fn+1)
+    double M0 = 0.0, M1 = 0.0, M2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < NQ; a++) {
+        const double Fa = (double)F[a];
+        M0 += Fa;
+        if (EX(a) == 1) M1 += Fa; else if (EX(a) == -1) M1 -= Fa;
+        if (EY(a) == 1) M2 += Fa; else if (EY(a) == -1) M2 -= Fa;
+    }
     const double dtv = m.dtV[g];
+    const double W0 = Wn[g] - dtv * M0, W1 = Wn[np + g] - dtv * M1, W2 = Wn[2 * np + g] - dtv * M2;
+    Wout[g] = W0;
+    Wout[np + g] = W1;
+    Wout[2 * np + g] = W2;
     R rho1, ux1, uy1, feq1[NQ];
     macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
     feq9<R>(rho1, ux1, uy1, feq1);
     const R r = R(c.r), dtvr = R(dtv);
-    double M0 = 0.0, M1 = 0.0, M2 = 0.0;
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         R fnew;
         if constexpr (P == P_FP64) fnew = (fn[a] - dtvr * F[a] + r * feq1[a]) / (R(1) + r);
         else fnew = (fn[a] - dtvr * F[a] + r * feq1[a]) * R(c.inv1r);
         fout[a * np + g] = SP::enc(fnew, feq1[a], a);
-        const double Fa = (double)F[a];
-        M0 += Fa;
-        if (EX(a) == 1) M1 += Fa; else if (EX(a) == -1) M1 -= Fa;
-        if (EY(a) == 1) M2 += Fa; else if (EY(a) == -1) M2 -= Fa;
     }
-    Wn2[g] = W0 - dtv * M0;
-    Wn2[np + g] = W1 - dtv * M1;
-    Wn2[2 * np + g] = W2 - dtv * M2;
 }
 
 template <int P> constexpr size_t tiled_smem() {
@@ -196,13 +199,13 @@ template <int P> cudaError_t prepare_tiled_p() {
 
 template <int P>
 cudaError_t launch_tiled_p(const TiledMesh &m, const Coefs &c, const void *fin, void *fout, const double *Wn,
-                           const double *Wn1, double *Wn2, cudaStream_t st)
+                           double *Wout, cudaStream_t st)
 {
     using T = typename Store<P>::T;
     const size_t smem = tiled_smem<P>();
     if (m.n_tiles <= 0) return cudaSuccess;
     k_step_tiled<P><<<m.n_tiles, TILE_MAX, smem, st>>>(m, c, static_cast<const T *>(fin), static_cast<T *>(fout),
-                                                        Wn, Wn1, Wn2);
+                                                        Wn, Wout);
     return cudaGetLastError();
 }
 

@@ -76,8 +76,8 @@ def lib():
                 "sdugks_get_macros": [P, P, P],
                 "sdugks_get_macros_device": [P, P, P],
                 "sdugks_residual": [P, P, P],
-                "sdugks_get_state": [P, P, P, P],
-                "sdugks_set_state": [P, P, P, P],
+                "sdugks_get_state": [P, P, P],
+                "sdugks_set_state": [P, P, P],
                 "sdugks_solver_info": [P, P],
             }
             for name, args in sig.items():
@@ -197,17 +197,17 @@ class Solver:
         return eps.value, mass.value
 
     def get_state(self):
-        f = np.empty((self.n, 9)); W = np.empty((self.n, 3)); Wn = np.empty((self.n, 3))
-        _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W), _ptr(Wn)), "sdugks_get_state")
-        return f, W, Wn
+        f = np.empty((self.n, 9)); W = np.empty((self.n, 3))
+        _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W)), "sdugks_get_state")
+        return f, W
 
-    def get_state_into(self, f, W, Wn):
+    def get_state_into(self, f, W):
         """Like get_state into caller-provided (e.g. pinned) float64 arrays."""
-        _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W), _ptr(Wn)), "sdugks_get_state")
+        _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W)), "sdugks_get_state")
 
-    def set_state(self, f, W, Wn):
-        f = _f64(f, (self.n, 9)); W = _f64(W, (self.n, 3)); Wn = _f64(Wn, (self.n, 3))
-        _ck(lib().sdugks_set_state(self._h, _ptr(f), _ptr(W), _ptr(Wn)), "sdugks_set_state")
+    def set_state(self, f, W):
+        f = _f64(f, (self.n, 9)); W = _f64(W, (self.n, 3))
+        _ck(lib().sdugks_set_state(self._h, _ptr(f), _ptr(W)), "sdugks_set_state")
         return self
 
     def info(self) -> dict:

@@ -1,7 +1,7 @@
 """GPU parity of the CUDA S-DUGKS step (through the C-ABI) with the FP64 oracle.
 
 Tolerances (written next to each check):
-* FP64 mode: max |gpu - oracle| / max |oracle| <= 1e-12 for f, W and W^{n+1}.  Both
+* FP64 mode: max |gpu - oracle| / max |oracle| <= 1e-12 for f and W.  Both
   sides evaluate the same sums in FP64 but in different orders (and the library's
   geometry is computed by a different formula), so agreement is to rounding.
 * FP32 mode: relative L2 error of u against the FP64 oracle <= 1e-4 after the
@@ -77,21 +77,19 @@ def test_fp64_matches_oracle(name):
         rho, u = _random_state(case, init)
     elif case.u0 != (0.0, 0.0):
         u = np.tile(case.u0, (case.mesh.n_cells, 1))
-    s, (f, W, Wn), st = run_both(case, steps, "fp64", rho, u)
+    s, (f, W), st = run_both(case, steps, "fp64", rho, u)
     assert relmax(f, st.f) <= 1e-12
     assert relmax(W, st.W) <= 1e-12
-    assert relmax(Wn, O.macro_update(case, st)) <= 1e-12
-    assert np.abs(st.W[:, 1:]).max() > 0 or name == "couette_4x64"
+    assert np.abs(st.W[:, 1:]).max() > 0
 
 
 def test_fp64_full_size_cylinder_and_cavity():
     """The configs' full meshes (512 x 256 shuffled O-mesh, 256^2 cavity), a few steps."""
     for case, steps in ((M.cylinder(512, 256), 12), (M.cavity(256), 30)):
         u = np.tile(case.u0, (case.mesh.n_cells, 1)) if case.u0 != (0.0, 0.0) else None
-        s, (f, W, Wn), st = run_both(case, steps, "fp64", None, u)
+        s, (f, W), st = run_both(case, steps, "fp64", None, u)
         assert relmax(f, st.f) <= 1e-12
         assert relmax(W, st.W) <= 1e-12
-        assert relmax(Wn, O.macro_update(case, st)) <= 1e-12
 
 
 def test_fp64_couette_steady_state():
@@ -151,7 +149,7 @@ def test_checkpoint_resume_is_bitwise(precision):
 def test_fp32_cavity_full_size_against_oracle():
     """256^2 cavity (Re 1000, lid 0.1) in FP32: 1000 steps against the FP64 oracle."""
     case = M.cavity(256)
-    s, (f, W, Wn), st = run_both(case, 1000, "fp32")
+    s, (f, W), st = run_both(case, 1000, "fp32")
     rho, u = s.macros()
     assert rel_l2(u, st.u) <= 1e-4
     assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
@@ -160,7 +158,7 @@ def test_fp32_cavity_full_size_against_oracle():
 def test_fp32_cylinder_against_oracle():
     case = M.cylinder(128, 64, first=0.01, r_far=20.0)
     u0 = np.tile(case.u0, (case.mesh.n_cells, 1))
-    s, (f, W, Wn), st = run_both(case, 1500, "fp32", None, u0)
+    s, (f, W), st = run_both(case, 1500, "fp32", None, u0)
     rho, u = s.macros()
     assert rel_l2(u, st.u) <= 1e-4
     assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
@@ -169,7 +167,7 @@ def test_fp32_cylinder_against_oracle():
 def test_bf16dev_cylinder_against_oracle():
     case = M.cylinder(128, 64, first=0.01, r_far=20.0)
     u0 = np.tile(case.u0, (case.mesh.n_cells, 1))
-    s, (f, W, Wn), st = run_both(case, 1500, "bf16dev", None, u0)
+    s, (f, W), st = run_both(case, 1500, "bf16dev", None, u0)
     rho, u = s.macros()
     assert rel_l2(u, st.u) <= 1e-2
 
@@ -210,10 +208,10 @@ def test_errors_are_status_codes_not_faults():
         s.step(1)
     assert e.value.name == "STATE"
     s.init()
-    f, W, Wn = s.get_state()
+    f, W = s.get_state()
     W[3, 0] = np.nan
     with pytest.raises(S.SdugksError) as e:
-        s.set_state(f, W, Wn)       # set_state takes the residual snapshot, which sees the NaN
+        s.set_state(f, W)       # set_state takes the residual snapshot, which sees the NaN
     assert e.value.name == "DIVERGED"
     s.step(5)                       # NaN propagates through values only, never into indices
     with pytest.raises(S.SdugksError) as e:
