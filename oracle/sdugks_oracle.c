@@ -127,18 +127,21 @@ static int cell_polygon(const omesh *m, int64_t c, double *area, double cen[2])
         loop[k] = next;
     }
     if (loop[n] != loop[0]) return OR_ERR_MESH;
+    /* shoelace in coordinates relative to the first vertex (the same sums, without
+     * the cancellation of large absolute coordinates) */
+    const double ox = m->xy[2 * loop[0]], oy = m->xy[2 * loop[0] + 1];
     double a2 = 0, cx = 0, cy = 0;
     for (int64_t k = 0; k < n; k++) {
-        double x0 = m->xy[2 * loop[k]], y0 = m->xy[2 * loop[k] + 1];
-        double x1 = m->xy[2 * loop[k + 1]], y1 = m->xy[2 * loop[k + 1] + 1];
+        double x0 = m->xy[2 * loop[k]] - ox, y0 = m->xy[2 * loop[k] + 1] - oy;
+        double x1 = m->xy[2 * loop[k + 1]] - ox, y1 = m->xy[2 * loop[k + 1] + 1] - oy;
         double cr = x0 * y1 - x1 * y0;
         a2 += cr;
         cx += (x0 + x1) * cr;
         cy += (y0 + y1) * cr;
     }
     if (a2 == 0.0) return OR_ERR_MESH;
-    cen[0] = cx / (3.0 * a2);
-    cen[1] = cy / (3.0 * a2);
+    cen[0] = ox + cx / (3.0 * a2);
+    cen[1] = oy + cy / (3.0 * a2);
     *area = fabs(0.5 * a2);
     return OR_OK;
 }

@@ -101,17 +101,20 @@ static int build_geometry(sdugks_mesh &m)
         m.xf[2 * f] = mx; m.xf[2 * f + 1] = my;
         m.nl[2 * f] = nx; m.nl[2 * f + 1] = ny;
     }
+    // the sums run in coordinates relative to the cell's vertex mean, so that cells
+    // far from the origin keep their digits
     m.vol.assign(nc, 0.0);
     m.xc.assign(2 * nc, 0.0);
     for (int64_t c = 0; c < nc; c++) {
+        const double ox = vm[2 * c], oy = vm[2 * c + 1];
         double v2 = 0, ix = 0, iy = 0, sx = 0, sy = 0, per = 0;
         for (int64_t e = m.cs[c]; e < m.cs[c + 1]; e++) {
             const int64_t f = m.cl[e];
             const double sg = m.own[f] == c ? 1.0 : -1.0;
             const double nx = sg * m.nl[2 * f], ny = sg * m.nl[2 * f + 1];
-            const double x0 = m.xy[2 * m.fpts[2 * f]], y0 = m.xy[2 * m.fpts[2 * f] + 1];
-            const double x1 = m.xy[2 * m.fpts[2 * f + 1]], y1 = m.xy[2 * m.fpts[2 * f + 1] + 1];
-            v2 += m.xf[2 * f] * nx + m.xf[2 * f + 1] * ny;
+            const double x0 = m.xy[2 * m.fpts[2 * f]] - ox, y0 = m.xy[2 * m.fpts[2 * f] + 1] - oy;
+            const double x1 = m.xy[2 * m.fpts[2 * f + 1]] - ox, y1 = m.xy[2 * m.fpts[2 * f + 1] + 1] - oy;
+            v2 += 0.5 * ((x0 + x1) * nx + (y0 + y1) * ny);
             ix += nx * (x0 * x0 + x0 * x1 + x1 * x1);
             iy += ny * (y0 * y0 + y0 * y1 + y1 * y1);
             sx += nx; sy += ny;
@@ -122,8 +125,8 @@ static int build_geometry(sdugks_mesh &m)
         if (std::hypot(sx, sy) > 1e-12 * per)
             return fail(SDUGKS_ERR_INVALID_MESH, "cell %lld is not closed (|sum n l| = %g)", (long long)c, std::hypot(sx, sy));
         m.vol[c] = V;
-        m.xc[2 * c] = ix / (6.0 * V);
-        m.xc[2 * c + 1] = iy / (6.0 * V);
+        m.xc[2 * c] = ox + ix / (6.0 * V);
+        m.xc[2 * c + 1] = oy + iy / (6.0 * V);
     }
     return SDUGKS_OK;
 }
