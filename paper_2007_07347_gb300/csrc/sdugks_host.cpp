@@ -348,7 +348,7 @@ struct sdugks_solver {
     cudaStream_t cap_stream = nullptr;
     sdugks_params p{};
     Coefs coefs{};
-    int64_t n = 0, npad = 0, nf = 0, fpad = 0;
+    int64_t n = 0, npad = 0, nf = 0;
     int32_t n_tiles = 0;
     int64_t halo_cells = 0;
     int32_t kernel = SDUGKS_KERNEL_TILED;
@@ -409,7 +409,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     if (rc) return rc;
     const int64_t n = m->nc;
 
-    // cell -> faces over the merged faces (ascending merged face id)
+    // cell -> faces over the merged faces; slots in ascending merged face id, which
+    // keeps the caller's face order, so per-cell sums do not depend on the tiling
     std::vector<std::array<int64_t, MAXF>> slots(n);
     std::vector<int> nslot(n, 0);
     for (int64_t f = 0; f < F.nf; f++) {
@@ -420,20 +421,29 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
             slots[c][nslot[c]++] = f;
         }
     }
-    // LLSR normal matrix per cell: d = (face - own centre) - (face - other centre)
-    std::vector<double> nbd(n * MAXF * 2, 0.0), ainv(3 * n, 0.0);
+    // per cell and slot: n l out of the cell, x_f - x_j, x_f - x_k; LLSR inverse from
+    // d = x_k - x_j = (x_f - x_j) - (x_f - x_k)
+    std::vector<double> sgeo((size_t)n * MAXF * 6, 0.0), ainv(3 * n, 0.0);
+    std::vector<uint8_t> skind((size_t)n * MAXF, SK_NONE);
     for (int64_t c = 0; c < n; c++) {
         double axx = 0, axy = 0, ayy = 0;
         for (int sl = 0; sl < nslot[c]; sl++) {
             const int64_t f = slots[c][sl];
-            if (F.nbr[f] < 0) continue;
+            double *G = &sgeo[((size_t)c * MAXF + sl) * 6];
             const bool mine = F.own[f] == c;
+            const double sg = mine ? 1.0 : -1.0;
+            G[0] = sg * F.nl[2 * f]; G[1] = sg * F.nl[2 * f + 1];
             const double *rme = mine ? &F.ro[2 * f] : &F.rk[2 * f];
             const double *rot = mine ? &F.rk[2 * f] : &F.ro[2 * f];
-            const double dx = rme[0] - rot[0], dy = rme[1] - rot[1];
-            nbd[(c * MAXF + sl) * 2] = dx;
-            nbd[(c * MAXF + sl) * 2 + 1] = dy;
-            axx += dx * dx; axy += dx * dy; ayy += dy * dy;
+            G[2] = rme[0]; G[3] = rme[1];
+            if (F.nbr[f] >= 0) {
+                skind[(size_t)c * MAXF + sl] = SK_INTERIOR;
+                G[4] = rot[0]; G[5] = rot[1];
+                const double dx = rme[0] - rot[0], dy = rme[1] - rot[1];
+                axx += dx * dx; axy += dx * dy; ayy += dy * dy;
+            } else {
+                skind[(size_t)c * MAXF + sl] = (uint8_t)(-1 - F.nbr[f]);
+            }
         }
         const double det = axx * ayy - axy * axy, tr = axx + ayy;
         if (det > 1e-14 * tr * tr) {
@@ -465,13 +475,13 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         TileHalo h;
         for (size_t i = lo; i < hi; i++)
             for (int sl = 0; sl < nslot[ids[i]]; sl++) {
-                const int64_t k = other_of(ids[i], sl);
-                if (k >= 0 && stamp[k] != tag) { stamp[k] = tag; h.r1.push_back((int32_t)k); }
+                const int64_t kc = other_of(ids[i], sl);
+                if (kc >= 0 && stamp[kc] != tag) { stamp[kc] = tag; h.r1.push_back((int32_t)kc); }
             }
         for (int32_t c1 : h.r1)
             for (int sl = 0; sl < nslot[c1]; sl++) {
-                const int64_t k = other_of(c1, sl);
-                if (k >= 0 && stamp[k] != tag) { stamp[k] = tag; h.r2.push_back((int32_t)k); }
+                const int64_t kc = other_of(c1, sl);
+                if (kc >= 0 && stamp[kc] != tag) { stamp[kc] = tag; h.r2.push_back((int32_t)kc); }
             }
         const size_t nint = hi - lo;
         if (nint + h.r1.size() + h.r2.size() > (size_t)LOC_MAX || nint + h.r1.size() > (size_t)SIG_MAX) {
@@ -488,45 +498,28 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     // internal order: tiles in RCB order
     std::vector<int32_t> perm(n), iperm(n);
     {
-        int64_t k = 0;
+        int64_t q = 0;
         for (auto &t : final_tiles)
-            for (size_t i = t.first; i < t.second; i++) perm[k++] = ids[i];
+            for (size_t i = t.first; i < t.second; i++) perm[q++] = ids[i];
         for (int64_t i = 0; i < n; i++) iperm[perm[i]] = (int32_t)i;
     }
-    // faces renumbered by the smaller internal id of their cells (locality)
-    std::vector<int64_t> forder(F.nf);
-    std::iota(forder.begin(), forder.end(), 0);
-    auto fkey = [&](int64_t f) {
-        int64_t a = iperm[F.own[f]];
-        if (F.nbr[f] >= 0) a = std::min<int64_t>(a, iperm[F.nbr[f]]);
-        return a;
-    };
-    std::stable_sort(forder.begin(), forder.end(), [&](int64_t a, int64_t b) { return fkey(a) < fkey(b); });
-    std::vector<int64_t> fnew(F.nf);
-    for (int64_t k = 0; k < F.nf; k++) fnew[forder[k]] = k;
 
-    const int64_t npad = (n + 31) / 32 * 32, fpad = (F.nf + 31) / 32 * 32;
+    const int64_t npad = (n + 31) / 32 * 32;
     std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), halo;
     std::vector<uint16_t> sig_nb;
-    std::vector<int32_t> cface(MAXF * npad, -1);
-    std::vector<uint16_t> fo_local(MAXF * npad, NO_LOCAL);
-    // per internal cell: slots re-sorted by new face id, with nbd permuted alongside
-    std::vector<std::array<int64_t, MAXF>> islot(n);
-    std::vector<int> insl(n);
-    std::vector<double> inbd(MAXF * 2 * npad, 0.0);
+    std::vector<uint8_t> islk((size_t)MAXF * npad, SK_NONE);
+    std::vector<double> igeo((size_t)MAXF * 6 * npad, 0.0), iainv(3 * npad, 0.0), ivol(npad, 1.0), idtv(npad, 0.0);
     for (int64_t i = 0; i < n; i++) {
         const int64_t c = perm[i];
-        std::array<int, MAXF> ord{0, 1, 2, 3};
-        std::sort(ord.begin(), ord.begin() + nslot[c], [&](int x, int y) { return fnew[slots[c][x]] < fnew[slots[c][y]]; });
-        insl[i] = nslot[c];
-        for (int sl = 0; sl < nslot[c]; sl++) {
-            islot[i][sl] = slots[c][ord[sl]];
-            cface[sl * npad + i] = (int32_t)fnew[slots[c][ord[sl]]];
-            inbd[(2 * sl) * npad + i] = nbd[(c * MAXF + ord[sl]) * 2];
-            inbd[(2 * sl + 1) * npad + i] = nbd[(c * MAXF + ord[sl]) * 2 + 1];
+        for (int sl = 0; sl < MAXF; sl++) {
+            islk[(size_t)sl * npad + i] = skind[(size_t)c * MAXF + sl];
+            for (int q = 0; q < 6; q++) igeo[((size_t)sl * 6 + q) * npad + i] = sgeo[((size_t)c * MAXF + sl) * 6 + q];
         }
+        for (int d = 0; d < 3; d++) iainv[d * npad + i] = ainv[3 * c + d];
+        ivol[i] = m->vol[c];
+        idtv[i] = prm->dt / m->vol[c];
     }
-    int64_t halo_total = 0;
+    int64_t halo_total = 0, sig_total = 0;
     {
         int32_t c0 = 0, hoff = 0, soff = 0;
         for (int32_t t = 0; t < nt; t++) {
@@ -540,52 +533,31 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
             tile_nh1[t] = (int32_t)r1.size();
             // local numbering: interior, ring 1, ring 2
             for (int32_t i = 0; i < nint; i++) local[c0 + i] = i;
-            for (size_t k = 0; k < r1.size(); k++) local[r1[k]] = nint + (int32_t)k;
-            for (size_t k = 0; k < r2.size(); k++) local[r2[k]] = nint + (int32_t)(r1.size() + k);
+            for (size_t q = 0; q < r1.size(); q++) local[r1[q]] = nint + (int32_t)q;
+            for (size_t q = 0; q < r2.size(); q++) local[r2[q]] = nint + (int32_t)(r1.size() + q);
             halo.insert(halo.end(), r1.begin(), r1.end());
             halo.insert(halo.end(), r2.begin(), r2.end());
             auto push_sig = [&](int32_t i) {
                 std::array<uint16_t, MAXF> row;
                 row.fill(NO_LOCAL);
-                for (int sl = 0; sl < insl[i]; sl++) {
-                    const int64_t f = islot[i][sl];
-                    if (F.nbr[f] < 0) continue;
-                    const int64_t c = perm[i];
-                    const int64_t k = F.own[f] == c ? F.nbr[f] : F.own[f];
-                    row[sl] = (uint16_t)local[iperm[k]];
+                const int64_t c = perm[i];
+                for (int sl = 0; sl < nslot[c]; sl++) {
+                    const int64_t kc = other_of(c, sl);
+                    if (kc >= 0) row[sl] = (uint16_t)local[iperm[kc]];
                 }
                 sig_nb.insert(sig_nb.end(), row.begin(), row.end());
             };
             for (int32_t i = 0; i < nint; i++) push_sig(c0 + i);
             for (int32_t c : r1) push_sig(c);
-            for (int32_t i = 0; i < nint; i++) {
-                const int32_t g = c0 + i;
-                for (int sl = 0; sl < insl[g]; sl++) {
-                    const int64_t f = islot[g][sl];
-                    if (F.nbr[f] < 0) continue;
-                    const int64_t c = perm[g];
-                    const int64_t k = F.own[f] == c ? F.nbr[f] : F.own[f];
-                    fo_local[sl * npad + g] = (uint16_t)local[iperm[k]];
-                }
-            }
             c0 += nint;
             hoff += (int32_t)(r1.size() + r2.size());
             soff += nint + (int32_t)r1.size();
             halo_total += (int64_t)(r1.size() + r2.size());
+            sig_total += nint + (int64_t)r1.size();
         }
         tile_c0[nt] = c0; tile_h0[nt] = hoff; tile_s0[nt] = soff;
     }
-    // face arrays in new order, internal cell ids
-    std::vector<int32_t> fown(F.nf), fnbr(F.nf);
-    std::vector<double> fnl(2 * fpad, 0.0), fro(2 * fpad, 0.0), frk(2 * fpad, 0.0);
-    for (int64_t f = 0; f < F.nf; f++) {
-        const int64_t k = fnew[f];
-        fown[k] = iperm[F.own[f]];
-        fnbr[k] = F.nbr[f] >= 0 ? iperm[F.nbr[f]] : (int32_t)F.nbr[f];
-        fnl[k] = F.nl[2 * f]; fnl[fpad + k] = F.nl[2 * f + 1];
-        fro[k] = F.ro[2 * f]; fro[fpad + k] = F.ro[2 * f + 1];
-        frk[k] = F.rk[2 * f]; frk[fpad + k] = F.rk[2 * f + 1];
-    }
+
     // ---- every index the kernel dereferences is checked here, on the host
     for (int32_t t = 0; t < nt; t++) {
         const int32_t nint = tile_c0[t + 1] - tile_c0[t];
@@ -593,46 +565,34 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         const int32_t nsig = nint + tile_nh1[t];
         if (nint < 1 || nint > TILE_MAX || nloc > LOC_MAX || nsig > SIG_MAX || tile_s0[t + 1] - tile_s0[t] != nsig)
             return fail(SDUGKS_ERR_INVALID_MESH, "internal: tile %d sizes out of range", t);
-        for (int32_t k = tile_h0[t]; k < tile_h0[t + 1]; k++)
-            if (halo[k] < 0 || halo[k] >= n) return fail(SDUGKS_ERR_INVALID_MESH, "internal: halo id out of range");
-        for (int64_t k = (int64_t)tile_s0[t] * MAXF; k < (int64_t)tile_s0[t + 1] * MAXF; k++)
-            if (sig_nb[k] != NO_LOCAL && sig_nb[k] >= nloc)
-                return fail(SDUGKS_ERR_INVALID_MESH, "internal: gradient neighbour outside the tile's cells");
-        for (int32_t g = tile_c0[t]; g < tile_c0[t + 1]; g++) {
-            bool ended = false;
+        for (int32_t q = tile_h0[t]; q < tile_h0[t + 1]; q++)
+            if (halo[q] < 0 || halo[q] >= n) return fail(SDUGKS_ERR_INVALID_MESH, "internal: halo id out of range");
+        for (int32_t i = 0; i < nsig; i++) {
+            const int32_t g = i < nint ? tile_c0[t] + i : halo[tile_h0[t] + i - nint];
             for (int sl = 0; sl < MAXF; sl++) {
-                const int32_t f = cface[sl * npad + g];
-                if (f < 0) { ended = true; continue; }
-                if (ended || f >= F.nf || (sl > 0 && f <= cface[(sl - 1) * npad + g]))
-                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: face slots of a cell out of order");
-                if (fown[f] != g && fnbr[f] != g) return fail(SDUGKS_ERR_INVALID_MESH, "internal: face not on its cell");
-                if (fnbr[f] >= 0) {
-                    if (fo_local[sl * npad + g] >= nsig) return fail(SDUGKS_ERR_INVALID_MESH, "internal: face neighbour outside ring 1");
-                } else {
-                    const int32_t p = -1 - fnbr[f];
-                    if (p >= MAXPATCH || m->bc_kind[p] == SDUGKS_BC_UNSET || m->bc_kind[p] == SDUGKS_BC_PERIODIC)
-                        return fail(SDUGKS_ERR_BAD_BC, "internal: boundary face without a usable condition");
-                }
+                const uint16_t v = sig_nb[((size_t)tile_s0[t] + i) * MAXF + sl];
+                const uint8_t kd = islk[(size_t)sl * npad + g];
+                if (v != NO_LOCAL && v >= nloc)
+                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: gradient neighbour outside the tile's cells");
+                if ((kd == SK_INTERIOR) != (v != NO_LOCAL))
+                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: slot kind and neighbour disagree");
+                if (i < nint && kd == SK_INTERIOR && v >= nsig)
+                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: face neighbour outside ring 1");
+                if (kd != SK_INTERIOR && kd != SK_NONE &&
+                    (kd >= MAXPATCH || m->bc_kind[kd] == SDUGKS_BC_UNSET || m->bc_kind[kd] == SDUGKS_BC_PERIODIC))
+                    return fail(SDUGKS_ERR_BAD_BC, "internal: boundary face without a usable condition");
             }
         }
-    }
-
-    std::vector<double> ivol(npad, 1.0), idtv(npad, 0.0), iainv(3 * npad, 0.0);
-    for (int64_t i = 0; i < n; i++) {
-        const int64_t c = perm[i];
-        ivol[i] = m->vol[c];
-        idtv[i] = prm->dt / m->vol[c];
-        for (int d = 0; d < 3; d++) iainv[d * npad + i] = ainv[3 * c + d];
     }
 
     // ---- device allocation (one arena) and upload
     sdugks_solver *s = new (std::nothrow) sdugks_solver;
     if (!s) return fail(SDUGKS_ERR_OOM, "host allocation failed");
     s->p = *prm;
-    if (s->p.graph_steps == 0) s->p.graph_steps = 60;
+    if (s->p.graph_steps == 0) s->p.graph_steps = 64;
     if (s->p.graph_steps > 0) s->p.graph_steps = std::max(2, s->p.graph_steps / 2 * 2);
     s->stream = static_cast<cudaStream_t>(stream);
-    s->n = n; s->npad = npad; s->nf = F.nf; s->fpad = fpad; s->n_tiles = nt; s->halo_cells = halo_total;
+    s->n = n; s->npad = npad; s->nf = F.nf; s->n_tiles = nt; s->halo_cells = halo_total;
     s->kernel = SDUGKS_KERNEL_TILED;
     const int prec = prm->precision;
     const size_t rs = prec == P_FP64 ? sizeof(double) : sizeof(float);
@@ -653,17 +613,11 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->tm.tile_s0 = A.take<int32_t>(nt + 1);
         s->tm.halo = A.take<int32_t>(std::max<size_t>(1, halo.size()));
         s->tm.sig_nb = A.take<uint16_t>(sig_nb.size());
-        s->tm.cface = A.take<int32_t>(MAXF * npad);
-        s->tm.fo_local = A.take<uint16_t>(MAXF * npad);
-        s->tm.fown = A.take<int32_t>(fpad);
-        s->tm.fnbr = A.take<int32_t>(fpad);
-        s->tm.dtV = A.take<double>(npad);
-        s->tm.vol = s->vol;
-        s->tm.nbd = A.take<char>(MAXF * 2 * npad * rs);
+        s->tm.sl_kind = A.take<uint8_t>(islk.size());
+        s->tm.sl_geo = A.take<char>(igeo.size() * rs);
         s->tm.ainv = A.take<char>(3 * npad * rs);
-        s->tm.nl = A.take<char>(2 * fpad * rs);
-        s->tm.ro = A.take<char>(2 * fpad * rs);
-        s->tm.rk = A.take<char>(2 * fpad * rs);
+        s->tm.dtV = A.take<char>(npad * rs);
+        s->tm.vol = s->vol;
     };
     Arena A0;
     layout(A0);
@@ -677,26 +631,23 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     }
     Arena A{s->dmem, 0, s->dbytes};
     layout(A);
-    s->tm.n_tiles = nt; s->tm.n = n; s->tm.npad = npad; s->tm.nf = F.nf; s->tm.fpad = fpad;
+    s->tm.n_tiles = nt; s->tm.n = n; s->tm.npad = npad;
 
     auto conv = [&](const std::vector<double> &v) {
-        std::vector<char> out(v.size() * rs);
-        if (prec == P_FP64) std::memcpy(out.data(), v.data(), out.size());
+        std::vector<char> o(v.size() * rs);
+        if (prec == P_FP64) std::memcpy(o.data(), v.data(), o.size());
         else {
-            float *o = reinterpret_cast<float *>(out.data());
-            for (size_t k = 0; k < v.size(); k++) o[k] = (float)v[k];
+            float *q = reinterpret_cast<float *>(o.data());
+            for (size_t i = 0; i < v.size(); i++) q[i] = (float)v[i];
         }
-        return out;
+        return o;
     };
     std::vector<int32_t> permpad(npad, 0);
     std::copy(perm.begin(), perm.end(), permpad.begin());
-    std::vector<int32_t> fownp(fpad, 0), fnbrp(fpad, -1);
-    std::copy(fown.begin(), fown.end(), fownp.begin());
-    std::copy(fnbr.begin(), fnbr.end(), fnbrp.begin());
     auto up = [&](const void *dst, const void *src, size_t bytes) {
         return cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
     };
-    const std::vector<char> gnbd = conv(inbd), gainv = conv(iainv), gnl = conv(fnl), gro = conv(fro), grk = conv(frk);
+    const std::vector<char> ggeo = conv(igeo), gainv = conv(iainv), gdtv = conv(idtv);
     int rc2 = SDUGKS_OK;
     auto chk = [&](cudaError_t ee, const char *what) {
         if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
@@ -710,16 +661,10 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     chk(up(s->tm.tile_s0, tile_s0.data(), (nt + 1) * 4), "upload tiles");
     if (!halo.empty()) chk(up(s->tm.halo, halo.data(), halo.size() * 4), "upload halo");
     chk(up(s->tm.sig_nb, sig_nb.data(), sig_nb.size() * 2), "upload sig_nb");
-    chk(up(s->tm.cface, cface.data(), cface.size() * 4), "upload cface");
-    chk(up(s->tm.fo_local, fo_local.data(), fo_local.size() * 2), "upload fo_local");
-    chk(up(s->tm.fown, fownp.data(), fpad * 4), "upload fown");
-    chk(up(s->tm.fnbr, fnbrp.data(), fpad * 4), "upload fnbr");
-    chk(up(s->tm.dtV, idtv.data(), npad * 8), "upload dtV");
-    chk(up(s->tm.nbd, gnbd.data(), gnbd.size()), "upload nbd");
+    chk(up(s->tm.sl_kind, islk.data(), islk.size()), "upload slot kinds");
+    chk(up(s->tm.sl_geo, ggeo.data(), ggeo.size()), "upload slot geometry");
     chk(up(s->tm.ainv, gainv.data(), gainv.size()), "upload ainv");
-    chk(up(s->tm.nl, gnl.data(), gnl.size()), "upload nl");
-    chk(up(s->tm.ro, gro.data(), gro.size()), "upload ro");
-    chk(up(s->tm.rk, grk.data(), grk.size()), "upload rk");
+    chk(up(s->tm.dtV, gdtv.data(), gdtv.size()), "upload dtV");
     chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
     chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     chk((cudaError_t)prepare(prec), "kernel attributes");
@@ -735,17 +680,21 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     c.inv1r = 1.0 / (1.0 + dt / tau);
     c.dt = dt;
     c.tie = 1e-12;
+    c.fa_plus = (float)c.a_plus; c.fb_plus = (float)c.b_plus; c.fc_face = (float)c.c_face; c.fr = (float)c.r;
+    c.finv1r = (float)c.inv1r; c.fdt = (float)c.dt; c.ftie = (float)c.tie; c.fpad_ = 0.0f;
     for (int q = 0; q < MAXPATCH; q++) {
         c.bc_kind[q] = m->bc_kind[q];
-        for (int k = 0; k < 3; k++) c.bc_par[q][k] = m->bc_par[q][k];
+        for (int d = 0; d < 3; d++) {
+            c.bc_par[q][d] = m->bc_par[q][d];
+            c.fbc_par[q][d] = (float)m->bc_par[q][d];
+        }
     }
-    // mesh bytes read per cell and step by the tiled kernel (interior cells): slot data,
-    // LLSR data for interior and ring-1 cells, halo ids, face data (read by both sides)
+    // mesh bytes the tiled kernel reads per interior cell and step: slot kinds and
+    // geometry (4 x 6 values) of its own cell, gradient data (d vectors, inverse,
+    // neighbour indices) of interior and ring-1 cells, halo ids and dt/V
     {
-        const double sigc = (double)(n + [&] { int64_t a = 0; for (int t = 0; t < nt; t++) a += tile_nh1[t]; return a; }()) / n;
-        const double per_face = 4 + 4 + 6 * rs;   // fown, fnbr, nl, ro, rk
-        s->mesh_bytes = MAXF * (4 + 2) + 8 + sigc * (MAXF * (2 + 2 * rs) + 3 * rs) + (double)halo_total / n * 4 +
-                        2.0 * F.nf / n * per_face;
+        const double sigc = (double)sig_total / n;
+        s->mesh_bytes = MAXF * (1 + 6 * rs) + sigc * (MAXF * (2 + 2 * rs) + 3 * rs) + (double)halo_total / n * 4 + rs;
     }
     *out = s;
     return SDUGKS_OK;

@@ -21,7 +21,8 @@ enum Prec : int32_t { P_FP64 = 0, P_FP32 = 1, P_BF16DEV = 2 };
 enum BcKind : int32_t { BK_UNSET = 0, BK_PERIODIC = 1, BK_WALL = 2, BK_MOVING_WALL = 3,
                         BK_FARFIELD = 4, BK_OUTLET = 5 };
 
-// Scalars of one step (host-computed in FP64 from tau and dt).
+// Scalars of one step (host-computed in FP64 from tau and dt; FP32 copies for the
+// FP32-compute kernels so that no thread converts them).
 struct Coefs {
     double a_plus;   // (2 tau - dt) / (2 tau)
     double b_plus;   // dt / (2 tau)
@@ -30,33 +31,34 @@ struct Coefs {
     double inv1r;    // 1 / (1 + dt / tau)
     double dt;
     double tie;      // |xi . n l| <= tie counts as tangential
+    float fa_plus, fb_plus, fc_face, fr, finv1r, fdt, ftie, fpad_;
     int32_t bc_kind[MAXPATCH];
     double bc_par[MAXPATCH][3];
+    float fbc_par[MAXPATCH][3];
 };
 
+// Slot kinds of a cell's faces (slots in ascending face id).
+constexpr uint8_t SK_NONE = 0xFE;      // cell has fewer faces than MAXF
+constexpr uint8_t SK_INTERIOR = 0xFF;  // face shared with another cell (periodic pairs included)
+                                       // any other value: boundary patch id
+
 // Unstructured tiled mesh on the device.  Cells are in internal (tile-contiguous)
-// order; arrays indexed by cell are padded to npad, by face to fpad.
+// order; arrays indexed by cell are padded to npad.
 struct TiledMesh {
     int32_t n_tiles;
-    int64_t n, npad, nf, fpad;
+    int64_t n, npad;
     const int32_t *tile_c0;   // [n_tiles+1] interior cell range of each tile
     const int32_t *tile_h0;   // [n_tiles+1] range into halo
     const int32_t *tile_nh1;  // [n_tiles]   cells of ring 1 (first in the tile's halo)
     const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb
     const int32_t *halo;      // internal ids of ring 1 then ring 2 of each tile
-    const uint16_t *sig_nb;   // [sum n_sig][MAXF] local index of each face neighbour
-    const int32_t *cface;     // [MAXF][npad] face id per slot (ascending), -1 = none
-    const uint16_t *fo_local; // [MAXF][npad] local index of the cell across an interior face
-    const int32_t *fown;      // [nf] owner (internal id)
-    const int32_t *fnbr;      // [nf] neighbour (internal id) or -1 - patch
-    const double *dtV;        // [npad] dt / V
-    const double *vol;        // [npad] V
-    // geometry in FP64 and FP32 (each kernel reads its own precision)
-    const void *nbd;          // [MAXF][2][npad] x_k - x_j per slot
+    const uint16_t *sig_nb;   // [sum n_sig][MAXF] tile-local index of the cell across each slot
+    const uint8_t *sl_kind;   // [MAXF][npad] SK_* or boundary patch
+    const void *sl_geo;       // [MAXF][6][npad] per slot: n l out of the cell (2),
+                              //   x_f - x_j (2), x_f - x_k with x_k the far cell (2)
     const void *ainv;         // [3][npad] LLSR inverse (xx, xy, yy)
-    const void *nl;           // [2][fpad] normal * length, out of the owner
-    const void *ro;           // [2][fpad] face centre - owner centre
-    const void *rk;           // [2][fpad] face centre - neighbour centre (periodic image)
+    const void *dtV;          // [npad] dt / V (compute precision)
+    const double *vol;        // [npad] V
 };
 
 // Uniform Cartesian grid: cell (i, j) -> internal id i + nx j.

@@ -6,24 +6,36 @@
 // first ring, then every thread reconstructs the interface distribution on the
 // faces of its own cell along the characteristic (Eqs. fbpsource, fbar, Macro at the
 // face, Feq, f_t_n+1) and sums the mesoscopic flux (Eq. MesoFlux).  Its moments, the
-// macroscopic flux (Eq. MacroFlux), are accumulated in FP64 into
+// macroscopic flux (Eq. MacroFlux), update the FP64 conserved variables
 // W^{n+1} = W^n - dt/V F_macro (Eq. MacroUpdate, the moment of Eq. Integration), whose
 // equilibrium then closes the implicit cell update of f (Eq. fn+1).  f and W
 // ping-pong between two buffers each; nothing else is stored between steps.
 //
-// An interior face is evaluated by the threads of both cells with identical operands
-// in the same order, so both see the same interface values and the face fluxes
-// cancel exactly in the sum over cells.
+// Face data is stored per cell and slot (normal, face centre relative to this cell
+// and to the far cell), so an interior face is evaluated by the threads of both its
+// cells with the same operands in the same order: both get the same interface
+// values, and the face fluxes cancel exactly in the sum over the two cells.
 #pragma once
 #include "d2q9.cuh"
 
 namespace sdugks {
 
+template <class R> struct CoefR;
+template <> struct CoefR<double> {
+    double a, b, c, r, dt, tie;
+    __device__ CoefR(const Coefs &k) : a(k.a_plus), b(k.b_plus), c(k.c_face), r(k.r), dt(k.dt), tie(k.tie) {}
+    __device__ static double par(const Coefs &k, int p, int i) { return k.bc_par[p][i]; }
+};
+template <> struct CoefR<float> {
+    float a, b, c, r, dt, tie;
+    __device__ CoefR(const Coefs &k) : a(k.fa_plus), b(k.fb_plus), c(k.fc_face), r(k.fr), dt(k.fdt), tie(k.ftie) {}
+    __device__ static float par(const Coefs &k, int p, int i) { return k.fbc_par[p][i]; }
+};
+
 template <int P>
 __global__ void __launch_bounds__(TILE_MAX)
 k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__restrict__ fin,
-             typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn,
-             double *__restrict__ Wout)
+             typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn, double *__restrict__ Wout)
 {
     using R = typename Store<P>::R;
     using SP = Store<P>;
@@ -38,26 +50,25 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int n_loc = n_int + (m.tile_h0[t + 1] - h0);
     const int n_sig = n_int + m.tile_nh1[t];
     const int s0 = m.tile_s0[t];
-    const int64_t np = m.npad, fp = m.fpad;
-    const R a_plus = R(c.a_plus), b_plus = R(c.b_plus), c_face = R(c.c_face), dt = R(c.dt), tie = R(c.tie);
-    const R *nbd = static_cast<const R *>(m.nbd);
+    const int64_t np = m.npad;
+    const CoefR<R> k(c);
+    const R *geo = static_cast<const R *>(m.sl_geo);
     const R *ainv = static_cast<const R *>(m.ainv);
-    const R *nl = static_cast<const R *>(m.nl);
-    const R *ro = static_cast<const R *>(m.ro);
-    const R *rk = static_cast<const R *>(m.rk);
 
     // ---- phase 1: fbar+ = a f^n + b feq(W^n) for own cells (kept in registers) and halos
     const bool active = tid < n_int;
     const int64_t g = c0 + tid;
     R fn[NQ], feqn[NQ];
     R rho_n = R(1), ux_n = R(0), uy_n = R(0);
+    double w0n = 1.0, w1n = 0.0, w2n = 0.0;
     if (active) {
-        macro_of<R>(Wn[g], Wn[np + g], Wn[2 * np + g], rho_n, ux_n, uy_n);
+        w0n = Wn[g]; w1n = Wn[np + g]; w2n = Wn[2 * np + g];
+        macro_of<R>(w0n, w1n, w2n, rho_n, ux_n, uy_n);
         feq9<R>(rho_n, ux_n, uy_n, feqn);
 #pragma unroll
         for (int a = 0; a < NQ; a++) {
             fn[a] = SP::dec(fin[a * np + g], feqn[a], a);
-            s_fbp[a * LOC_MAX + tid] = a_plus * fn[a] + b_plus * feqn[a];
+            s_fbp[a * LOC_MAX + tid] = k.a * fn[a] + k.b * feqn[a];
         }
     }
     for (int i = n_int + tid; i < n_loc; i += blockDim.x) {
@@ -67,11 +78,11 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         feq9<R>(rho, ux, uy, fe);
 #pragma unroll
         for (int a = 0; a < NQ; a++)
-            s_fbp[a * LOC_MAX + i] = a_plus * SP::dec(fin[a * np + gh], fe[a], a) + b_plus * fe[a];
+            s_fbp[a * LOC_MAX + i] = k.a * SP::dec(fin[a * np + gh], fe[a], a) + k.b * fe[a];
     }
     __syncthreads();
 
-    // ---- phase 2: LLSR gradient sigma = A^{-1} sum_k d_k (fbar+_k - fbar+_j)
+    // ---- phase 2: LLSR gradient sigma = A^{-1} sum_k d_k (fbar+_k - fbar+_j), d = x_k - x_j
     for (int i = tid; i < n_sig; i += blockDim.x) {
         const int64_t gi = i < n_int ? (int64_t)c0 + i : (int64_t)m.halo[h0 + i - n_int];
         const uint16_t *nb = m.sig_nb + (int64_t)(s0 + i) * MAXF;
@@ -80,12 +91,13 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         for (int a = 0; a < NQ; a++) { bx[a] = R(0); by[a] = R(0); }
 #pragma unroll
         for (int sl = 0; sl < MAXF; sl++) {
-            const int k = nb[sl];
-            if (k == NO_LOCAL) continue;
-            const R dx = nbd[(2 * sl) * np + gi], dy = nbd[(2 * sl + 1) * np + gi];
+            const int kk = nb[sl];
+            if (kk == NO_LOCAL) continue;
+            const R *G = geo + (int64_t)(6 * sl) * np + gi;
+            const R dx = G[2 * np] - G[4 * np], dy = G[3 * np] - G[5 * np];
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
-                const R d = s_fbp[a * LOC_MAX + k] - s_fbp[a * LOC_MAX + i];
+                const R d = s_fbp[a * LOC_MAX + kk] - s_fbp[a * LOC_MAX + i];
                 bx[a] += dx * d;
                 by[a] += dy * d;
             }
@@ -104,27 +116,26 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     R F[NQ];
 #pragma unroll
     for (int a = 0; a < NQ; a++) F[a] = R(0);
+    const uint16_t *my_nb = m.sig_nb + (int64_t)(s0 + tid) * MAXF;
+#pragma unroll
     for (int sl = 0; sl < MAXF; sl++) {
-        const int fid = m.cface[sl * np + g];
-        if (fid < 0) break;
-        const int own = m.fown[fid], nbr = m.fnbr[fid];
-        const bool mine = (own == (int)g);
-        R nx = nl[fid], ny = nl[fp + fid];
-        if (!mine) { nx = -nx; ny = -ny; }
-        if (nbr >= 0) {
-            const int o = m.fo_local[sl * np + g];
-            R rmx = ro[fid], rmy = ro[fp + fid], rox = rk[fid], roy = rk[fp + fid];
-            if (!mine) { R tx = rmx, ty = rmy; rmx = rox; rmy = roy; rox = tx; roy = ty; }
+        const int kind = m.sl_kind[sl * np + g];
+        if (kind == SK_NONE) continue;
+        const R *G = geo + (int64_t)(6 * sl) * np + g;
+        const R nx = G[0], ny = G[np], rmx = G[2 * np], rmy = G[3 * np];
+        if (kind == SK_INTERIOR) {
+            const R rox = G[4 * np], roy = G[5 * np];
+            const int o = my_nb[sl];
             R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
-                const R ex = R(EX(a)) * dt, ey = R(EY(a)) * dt;
+                const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
                 const R A = s_fbp[a * LOC_MAX + tid] + (rmx - ex) * s_sig[(2 * a) * SIG_MAX + tid] +
                             (rmy - ey) * s_sig[(2 * a + 1) * SIG_MAX + tid];
                 const R B = s_fbp[a * LOC_MAX + o] + (rox - ex) * s_sig[(2 * a) * SIG_MAX + o] +
                             (roy - ey) * s_sig[(2 * a + 1) * SIG_MAX + o];
-                fbar[a] = s > tie ? A : (s < -tie ? B : R(0.5) * (A + B));
+                fbar[a] = s > k.tie ? A : (s < -k.tie ? B : R(0.5) * (A + B));
                 w0 += fbar[a];
                 if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
@@ -134,57 +145,62 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
-                F[a] += s * ((fbar[a] + b_plus * feqb[a]) * c_face);
+                F[a] += s * ((fbar[a] + k.b * feqb[a]) * k.c);
             }
         } else {
-            const int p = -1 - nbr;
-            const int kind = c.bc_kind[p];
+            const int p = kind;
+            const int bk = c.bc_kind[p];
             R rb = rho_n, ubx = R(0), uby = R(0);
-            if (kind == BK_MOVING_WALL) { ubx = R(c.bc_par[p][0]); uby = R(c.bc_par[p][1]); }
-            else if (kind == BK_FARFIELD) { rb = R(c.bc_par[p][0]); ubx = R(c.bc_par[p][1]); uby = R(c.bc_par[p][2]); }
-            else if (kind == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
+            if (bk == BK_MOVING_WALL) { ubx = CoefR<R>::par(c, p, 0); uby = CoefR<R>::par(c, p, 1); }
+            else if (bk == BK_FARFIELD) { rb = CoefR<R>::par(c, p, 0); ubx = CoefR<R>::par(c, p, 1); uby = CoefR<R>::par(c, p, 2); }
+            else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
             R feqb[NQ];
             feq9<R>(rb, ubx, uby, feqb);
-            const R rmx = ro[fid], rmy = ro[fp + fid];
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
                 R fb;
-                if (s < -tie) {
+                if (s < -k.tie) {
                     fb = feqb[a] + (fn[a] - feqn[a]);     // non-equilibrium extrapolation
                 } else {
-                    const R A = s_fbp[a * LOC_MAX + tid] + (rmx - R(EX(a)) * dt) * s_sig[(2 * a) * SIG_MAX + tid] +
-                                (rmy - R(EY(a)) * dt) * s_sig[(2 * a + 1) * SIG_MAX + tid];
-                    fb = (A + b_plus * feqb[a]) * c_face;
+                    const R A = s_fbp[a * LOC_MAX + tid] + (rmx - R(EX(a)) * k.dt) * s_sig[(2 * a) * SIG_MAX + tid] +
+                                (rmy - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * SIG_MAX + tid];
+                    fb = (A + k.b * feqb[a]) * k.c;
                 }
                 F[a] += s * fb;
             }
         }
     }
 
-    // ---- macroscopic flux (FP64 moments of F) -> W^{n+1}; cell update f^{n+1} (Eq. fn+1)
-    double M0 = 0.0, M1 = 0.0, M2 = 0.0;
+    // ---- macroscopic flux (moments of F) -> W^{n+1} in FP64; cell update f^{n+1} (Eq. fn+1)
+    const R dtv = static_cast<const R *>(m.dtV)[g];
+    R M0 = R(0), M1 = R(0), M2 = R(0);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
-        const double Fa = (double)F[a];
-        M0 += Fa;
-        if (EX(a) == 1) M1 += Fa; else if (EX(a) == -1) M1 -= Fa;
-        if (EY(a) == 1) M2 += Fa; else if (EY(a) == -1) M2 -= Fa;
+        M0 += F[a];
+        if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
+        if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
     }
-    const double dtv = m.dtV[g];
-    const double W0 = Wn[g] - dtv * M0, W1 = Wn[np + g] - dtv * M1, W2 = Wn[2 * np + g] - dtv * M2;
+    const R d0 = dtv * M0, d1 = dtv * M1, d2 = dtv * M2;
+    const double W0 = w0n - (double)d0, W1 = w1n - (double)d1, W2 = w2n - (double)d2;
     Wout[g] = W0;
     Wout[np + g] = W1;
     Wout[2 * np + g] = W2;
     R rho1, ux1, uy1, feq1[NQ];
-    macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
+    if constexpr (P == P_FP64) {
+        macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
+    } else {
+        // FP32 compute: W^{n+1} in FP32 from the FP32 copies already at hand
+        rho1 = R(w0n) - d0;
+        ux1 = (R(w1n) - d1) / rho1;
+        uy1 = (R(w2n) - d2) / rho1;
+    }
     feq9<R>(rho1, ux1, uy1, feq1);
-    const R r = R(c.r), dtvr = R(dtv);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         R fnew;
-        if constexpr (P == P_FP64) fnew = (fn[a] - dtvr * F[a] + r * feq1[a]) / (R(1) + r);
-        else fnew = (fn[a] - dtvr * F[a] + r * feq1[a]) * R(c.inv1r);
+        if constexpr (P == P_FP64) fnew = (fn[a] - dtv * F[a] + k.r * feq1[a]) / (R(1) + k.r);
+        else fnew = (fn[a] - dtv * F[a] + k.r * feq1[a]) * c.finv1r;
         fout[a * np + g] = SP::enc(fnew, feq1[a], a);
     }
 }
@@ -202,10 +218,9 @@ cudaError_t launch_tiled_p(const TiledMesh &m, const Coefs &c, const void *fin, 
                            double *Wout, cudaStream_t st)
 {
     using T = typename Store<P>::T;
-    const size_t smem = tiled_smem<P>();
     if (m.n_tiles <= 0) return cudaSuccess;
-    k_step_tiled<P><<<m.n_tiles, TILE_MAX, smem, st>>>(m, c, static_cast<const T *>(fin), static_cast<T *>(fout),
-                                                        Wn, Wout);
+    k_step_tiled<P><<<m.n_tiles, TILE_MAX, tiled_smem<P>(), st>>>(m, c, static_cast<const T *>(fin),
+                                                                  static_cast<T *>(fout), Wn, Wout);
     return cudaGetLastError();
 }
 

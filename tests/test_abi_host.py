@@ -90,3 +90,21 @@ def test_last_error_message_is_set():
         S.Mesh(M.Mesh(np.zeros((0, 2)), np.zeros((0, 2), np.int64), np.zeros(0, np.int64),
                       np.zeros(0, np.int64), 0, {}))
     assert "empty" in str(e.value)
+
+
+@pytest.mark.parametrize("tile", [0, 32])
+@pytest.mark.parametrize("make", [lambda: M.couette(64), lambda: M.cavity(64),
+                                  lambda: M.cylinder(128, 64, first=0.01, r_far=10.0),
+                                  lambda: M.periodic_box(24, 20, jitter=0.2, seed=4)])
+def test_tile_construction_passes_host_index_checks(make, tile):
+    """solver_create builds the tiles, halo rings and slot tables and checks every
+    index the kernel will use before it touches the device: without a GPU it must get
+    as far as the device allocation (CUDA error), never to an INVALID_MESH."""
+    import torch
+    case = make()
+    try:
+        s = S.Solver.from_case(case, "fp32", tile_cells=tile)
+    except S.SdugksError as e:
+        assert e.name == "CUDA" and not torch.cuda.is_available(), str(e)
+    else:
+        assert s.info()["n_tiles"] >= 1
