@@ -24,10 +24,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_UNITS = {
     "k_step_fp64.cu": ["--fmad=false"],
     "k_step_fp32.cu": [],
+    "k_cart_fp64.cu": ["--fmad=false"],
+    "k_cart.cu": [],
     "k_util.cu": [],
 }
 CXX_UNITS = ["sdugks_host.cpp"]
-HEADERS = ["sdugks_internal.h", "d2q9.cuh", "step_tiled.cuh"]
+HEADERS = ["sdugks_internal.h", "d2q9.cuh", "step_tiled.cuh", "step_cart.cuh"]
 
 
 def _sources():

@@ -12,12 +12,13 @@ constexpr int UT = 256;
 __device__ void feq9_d(double rho, double ux, double uy, double out[NQ]) { feq9<double>(rho, ux, uy, out); }
 
 template <int P>
-__global__ void k_init(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const double *__restrict__ rho_in,
+__global__ void k_init(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const int32_t *__restrict__ loc,
+                       const double *__restrict__ rho_in,
                        const double *__restrict__ u_in, typename Store<P>::T *__restrict__ f, double *__restrict__ W)
 {
     using R = typename Store<P>::R;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = perm[i];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = perm[q], i = loc ? loc[q] : q;
         const double rho = rho_in ? rho_in[p] : 1.0;
         const double ux = u_in ? u_in[2 * p] : 0.0, uy = u_in ? u_in[2 * p + 1] : 0.0;
         const double w0 = rho, w1 = rho * ux, w2 = rho * uy;
@@ -33,12 +34,13 @@ __global__ void k_init(int64_t n, int64_t npad, const int32_t *__restrict__ perm
 }
 
 template <int P>
-__global__ void k_pack(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const typename Store<P>::T *__restrict__ f,
+__global__ void k_pack(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const int32_t *__restrict__ loc,
+                       const typename Store<P>::T *__restrict__ f,
                        const double *__restrict__ W, double *__restrict__ f_out, double *__restrict__ W_out)
 {
     using R = typename Store<P>::R;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = perm[i];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = perm[q], i = loc ? loc[q] : q;
         R r, x, y, fe[NQ];
         macro_of<R>(W[i], W[npad + i], W[2 * npad + i], r, x, y);
         feq9<R>(r, x, y, fe);
@@ -52,12 +54,13 @@ __global__ void k_pack(int64_t n, int64_t npad, const int32_t *__restrict__ perm
 }
 
 template <int P>
-__global__ void k_unpack(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const double *__restrict__ f_in,
+__global__ void k_unpack(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const int32_t *__restrict__ loc,
+                         const double *__restrict__ f_in,
                          const double *__restrict__ W_in, typename Store<P>::T *__restrict__ f, double *__restrict__ W)
 {
     using R = typename Store<P>::R;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = perm[i];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = perm[q], i = loc ? loc[q] : q;
         for (int d = 0; d < 3; d++) W[d * npad + i] = W_in[3 * p + d];
         R r, x, y, fe[NQ];
         macro_of<R>(W_in[3 * p], W_in[3 * p + 1], W_in[3 * p + 2], r, x, y);
@@ -67,11 +70,12 @@ __global__ void k_unpack(int64_t n, int64_t npad, const int32_t *__restrict__ pe
     }
 }
 
-__global__ void k_macros(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const double *__restrict__ W,
+__global__ void k_macros(int64_t n, int64_t npad, const int32_t *__restrict__ perm, const int32_t *__restrict__ loc,
+                         const double *__restrict__ W,
                          double *__restrict__ rho, double *__restrict__ u)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = perm[i];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = perm[q], i = loc ? loc[q] : q;
         const double w0 = W[i];
         if (rho) rho[p] = w0;
         if (u) {
@@ -104,12 +108,14 @@ __device__ void block_sum4(double v[4], double *out)
 
 // Residual terms per block: sum (U-U0)^2+(V-V0)^2, sum U0^2+V0^2, sum V rho, and a
 // count of non-finite W; refreshes the snapshot (U0, V0) <- (U, V).
-__global__ void __launch_bounds__(UT) k_resid_partial(int64_t n, int64_t npad, const double *__restrict__ W,
+__global__ void __launch_bounds__(UT) k_resid_partial(int64_t n, int64_t npad, const int32_t *__restrict__ loc,
+                                                      const double *__restrict__ W,
                                                       const double *__restrict__ vol, double *__restrict__ snap,
                                                       double *__restrict__ partial)
 {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t i = blockIdx.x * (int64_t)UT + threadIdx.x; i < n; i += (int64_t)gridDim.x * UT) {
+    for (int64_t q = blockIdx.x * (int64_t)UT + threadIdx.x; q < n; q += (int64_t)gridDim.x * UT) {
+        const int64_t i = loc ? loc[q] : q;
         const double w0 = W[i], w1 = W[npad + i], w2 = W[2 * npad + i];
         const double U = w1 / w0, V = w2 / w0;
         const double U0 = snap[i], V0 = snap[npad + i];
@@ -139,46 +145,46 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *rho,
-                              const double *u, void *f, double *W, cudaStream_t st)
+cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc,
+                              const double *rho, const double *u, void *f, double *W, cudaStream_t st)
 {
     const int g = grid_for(n);
-    if (prec == P_FP64) k_init<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (double *)f, W);
-    else if (prec == P_FP32) k_init<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (float *)f, W);
-    else k_init<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, rho, u, (__nv_bfloat16 *)f, W);
+    if (prec == P_FP64) k_init<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (double *)f, W);
+    else if (prec == P_FP32) k_init<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (float *)f, W);
+    else k_init<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (__nv_bfloat16 *)f, W);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const void *f, const double *W,
-                              double *f_out, double *W_out, cudaStream_t st)
-{
-    const int g = grid_for(n);
-    if (prec == P_FP64)
-        k_pack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, (const double *)f, W, f_out, W_out);
-    else if (prec == P_FP32)
-        k_pack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, (const float *)f, W, f_out, W_out);
-    else
-        k_pack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, (const __nv_bfloat16 *)f, W, f_out, W_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *f_in,
-                                const double *W_in, void *f, double *W, cudaStream_t st)
+cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc, const void *f,
+                              const double *W, double *f_out, double *W_out, cudaStream_t st)
 {
     const int g = grid_for(n);
     if (prec == P_FP64)
-        k_unpack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, (double *)f, W);
+        k_pack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, loc, (const double *)f, W, f_out, W_out);
     else if (prec == P_FP32)
-        k_unpack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, (float *)f, W);
+        k_pack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, loc, (const float *)f, W, f_out, W_out);
     else
-        k_unpack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, f_in, W_in, (__nv_bfloat16 *)f, W);
+        k_pack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, (const __nv_bfloat16 *)f, W, f_out, W_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const double *W, double *rho, double *u,
-                          cudaStream_t st)
+cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc,
+                                const double *f_in, const double *W_in, void *f, double *W, cudaStream_t st)
 {
-    k_macros<<<grid_for(n), UT, 0, st>>>(n, npad, perm, W, rho, u);
+    const int g = grid_for(n);
+    if (prec == P_FP64)
+        k_unpack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (double *)f, W);
+    else if (prec == P_FP32)
+        k_unpack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (float *)f, W);
+    else
+        k_unpack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (__nv_bfloat16 *)f, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc, const double *W, double *rho,
+                          double *u, cudaStream_t st)
+{
+    k_macros<<<grid_for(n), UT, 0, st>>>(n, npad, perm, loc, W, rho, u);
     return cudaGetLastError();
 }
 
@@ -187,10 +193,10 @@ int residual_blocks(int64_t n) {
     return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
-cudaError_t launch_residual(int64_t n, int64_t npad, const double *W, const double *vol, double *snap,
+cudaError_t launch_residual(int64_t n, int64_t npad, const int32_t *loc, const double *W, const double *vol, double *snap,
                             double *partial, int n_blocks, double *out, cudaStream_t st)
 {
-    k_resid_partial<<<n_blocks, UT, 0, st>>>(n, npad, W, vol, snap, partial);
+    k_resid_partial<<<n_blocks, UT, 0, st>>>(n, npad, loc, W, vol, snap, partial);
     k_resid_final<<<1, UT, 0, st>>>(n_blocks, partial, out);
     return cudaGetLastError();
 }

@@ -356,7 +356,9 @@ struct sdugks_solver {
     // device buffers
     char *dmem = nullptr;
     size_t dbytes = 0;
-    int32_t *perm = nullptr;        // internal -> user
+    int32_t *perm = nullptr;        // q-th listed cell -> user id
+    int32_t *loc = nullptr;         // q-th listed cell -> internal offset (nullptr: q)
+    CartMesh cm{};
     double *vol = nullptr, *snap = nullptr, *partial = nullptr, *red = nullptr;
     State st{};
     int n_red_blocks = 1;
@@ -370,8 +372,9 @@ struct sdugks_solver {
     double mesh_bytes = 0.0;
 };
 
-static int prepare(int prec)
+static int prepare(int prec, int kernel)
 {
+    if (kernel == SDUGKS_KERNEL_CARTESIAN) return (int)prepare_cart(prec);
     return prec == P_FP64 ? (int)prepare_tiled_fp64() : (int)prepare_tiled_fp32(prec);
 }
 
@@ -379,13 +382,208 @@ static cudaError_t launch_one(sdugks_solver *s, cudaStream_t st)
 {
     const int a = s->cur;
     cudaError_t e;
-    if (s->p.precision == P_FP64)
+    if (s->kernel == SDUGKS_KERNEL_CARTESIAN)
+        e = launch_step_cart(s->p.precision, s->cm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
+    else if (s->p.precision == P_FP64)
         e = launch_step_tiled_fp64(s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
     else
         e = launch_step_tiled_fp32(s->p.precision, s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a],
                                    s->st.W[1 - a], st);
     s->cur = 1 - a;
     return e;
+}
+
+static void fill_coefs(Coefs &c, const sdugks_mesh &m, double tau, double dt)
+{
+    c.a_plus = (2.0 * tau - dt) / (2.0 * tau);
+    c.b_plus = dt / (2.0 * tau);
+    c.c_face = 2.0 * tau / (2.0 * tau + dt);
+    c.r = dt / tau;
+    c.inv1r = 1.0 / (1.0 + dt / tau);
+    c.dt = dt;
+    c.tie = 1e-12;
+    c.fa_plus = (float)c.a_plus; c.fb_plus = (float)c.b_plus; c.fc_face = (float)c.c_face; c.fr = (float)c.r;
+    c.finv1r = (float)c.inv1r; c.fdt = (float)c.dt; c.ftie = (float)c.tie; c.fpad_ = 0.0f;
+    for (int q = 0; q < MAXPATCH; q++) {
+        c.bc_kind[q] = m.bc_kind[q];
+        for (int d = 0; d < 3; d++) {
+            c.bc_par[q][d] = m.bc_par[q][d];
+            c.fbc_par[q][d] = (float)m.bc_par[q][d];
+        }
+    }
+}
+
+namespace {
+
+// A mesh recognised as a uniform nx x ny grid of dx x dy rectangles.
+struct CartGrid {
+    int32_t nx = 0, ny = 0;
+    double dx = 0, dy = 0;
+    int32_t side_patch[4] = {-1, -1, -1, -1};   // bottom, right, top, left
+    bool px = false, py = false;
+    std::vector<int32_t> ci, cj;                  // lattice position of each user cell
+    std::string why;
+};
+
+bool detect_cart(const sdugks_mesh &m, CartGrid &g)
+{
+    double dx = -1, dy = -1;
+    for (int64_t f = 0; f < m.nf; f++) {
+        const double nx = m.nl[2 * f], ny = m.nl[2 * f + 1], len = std::hypot(nx, ny);
+        double *h;
+        if (std::fabs(ny) <= 1e-12 * len) h = &dy;          // face of constant x, length dy
+        else if (std::fabs(nx) <= 1e-12 * len) h = &dx;     // face of constant y, length dx
+        else { g.why = "a face is not axis-aligned"; return false; }
+        if (*h < 0) *h = len;
+        else if (std::fabs(*h - len) > 1e-12 * len) { g.why = "faces of different lengths"; return false; }
+    }
+    if (dx <= 0 || dy <= 0) { g.why = "no faces in one direction"; return false; }
+    for (int64_t c = 0; c < m.nc; c++)
+        if (m.cs[c + 1] - m.cs[c] != 4) { g.why = "a cell without four faces"; return false; }
+    double x0 = INFINITY, y0 = INFINITY;
+    for (int64_t p = 0; p < m.np; p++) { x0 = std::min(x0, m.xy[2 * p]); y0 = std::min(y0, m.xy[2 * p + 1]); }
+    g.ci.resize(m.nc); g.cj.resize(m.nc);
+    int64_t mi = 0, mj = 0;
+    for (int64_t c = 0; c < m.nc; c++) {
+        const double fi = (m.xc[2 * c] - x0) / dx - 0.5, fj = (m.xc[2 * c + 1] - y0) / dy - 0.5;
+        const long long i = std::llround(fi), j = std::llround(fj);
+        if (std::fabs(fi - i) > 1e-6 || std::fabs(fj - j) > 1e-6 || i < 0 || j < 0 || i > INT32_MAX / 4 || j > INT32_MAX / 4) {
+            g.why = "cell centres are not on a lattice";
+            return false;
+        }
+        g.ci[c] = (int32_t)i; g.cj[c] = (int32_t)j;
+        mi = std::max<int64_t>(mi, i); mj = std::max<int64_t>(mj, j);
+    }
+    const int64_t nx = mi + 1, ny = mj + 1;
+    if (nx * ny != m.nc || nx < 2 || ny < 2) { g.why = "cells do not fill an nx x ny grid (nx, ny >= 2)"; return false; }
+    {
+        std::vector<char> seen(m.nc, 0);
+        for (int64_t c = 0; c < m.nc; c++) {
+            char &v = seen[g.ci[c] + nx * g.cj[c]];
+            if (v) { g.why = "two cells on one lattice site"; return false; }
+            v = 1;
+        }
+    }
+    for (int64_t f = 0; f < m.nf; f++) {
+        const int64_t o = m.own[f], k = m.nbr[f];
+        const double nx_ = m.nl[2 * f], ny_ = m.nl[2 * f + 1];
+        const int sx = std::fabs(nx_) > std::fabs(ny_) ? (nx_ > 0 ? 1 : -1) : 0;
+        const int sy = sx == 0 ? (ny_ > 0 ? 1 : -1) : 0;
+        if (k >= 0) {
+            if (g.ci[k] - g.ci[o] != sx || g.cj[k] - g.cj[o] != sy) { g.why = "an interior face joins non-adjacent cells"; return false; }
+            continue;
+        }
+        int side;
+        if (sx == 1 && g.ci[o] == nx - 1) side = 1;
+        else if (sx == -1 && g.ci[o] == 0) side = 3;
+        else if (sy == 1 && g.cj[o] == ny - 1) side = 2;
+        else if (sy == -1 && g.cj[o] == 0) side = 0;
+        else { g.why = "a boundary face inside the grid"; return false; }
+        const int32_t patch = (int32_t)(-1 - k);
+        if (g.side_patch[side] < 0) g.side_patch[side] = patch;
+        else if (g.side_patch[side] != patch) { g.why = "one grid side carries two patches"; return false; }
+    }
+    // periodic sides must pair left/right and bottom/top with the grid period as shift
+    const double W = nx * dx, H = ny * dy;
+    const int opp[4] = {2, 3, 0, 1};
+    const double shx[4] = {0, -W, 0, W}, shy[4] = {H, 0, -H, 0};
+    for (int side = 0; side < 4; side++) {
+        const int32_t p = g.side_patch[side];
+        if (p < 0) { g.why = "a grid side has no boundary faces"; return false; }
+        const bool per = m.bc_kind[p] == SDUGKS_BC_PERIODIC;
+        if (!per) continue;
+        if ((int32_t)m.bc_par[p][0] != g.side_patch[opp[side]] ||
+            std::fabs(m.bc_par[p][1] - shx[side]) > 1e-9 * dx || std::fabs(m.bc_par[p][2] - shy[side]) > 1e-9 * dy) {
+            g.why = "a periodic side does not pair with the opposite side";
+            return false;
+        }
+    }
+    auto periodic = [&](int side) { return m.bc_kind[g.side_patch[side]] == SDUGKS_BC_PERIODIC; };
+    g.px = periodic(1) && periodic(3);
+    g.py = periodic(0) && periodic(2);
+    if (periodic(1) != periodic(3) || periodic(0) != periodic(2)) { g.why = "one-sided periodic grid"; return false; }
+    for (int side = 0; side < 4; side++)
+        for (int other = 0; other < 4; other++)
+            if (other != side && g.side_patch[other] == g.side_patch[side] && periodic(side)) {
+                g.why = "a periodic patch on two sides"; return false;
+            }
+    g.nx = (int32_t)nx; g.ny = (int32_t)ny; g.dx = dx; g.dy = dy;
+    return true;
+}
+
+}  // namespace
+
+static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_params *prm, void *stream, sdugks_solver **out)
+{
+    const int64_t n = m.nc;
+    const int32_t pitch = (g.nx + 31) / 32 * 32;
+    const int64_t npad = ((int64_t)pitch * g.ny + 31) / 32 * 32;
+    const int prec = prm->precision;
+    const size_t fs = prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2);
+    sdugks_solver *s = new (std::nothrow) sdugks_solver;
+    if (!s) return fail(SDUGKS_ERR_OOM, "host allocation failed");
+    s->p = *prm;
+    if (s->p.graph_steps == 0) s->p.graph_steps = 64;
+    if (s->p.graph_steps > 0) s->p.graph_steps = std::max(2, s->p.graph_steps / 2 * 2);
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->n = n; s->npad = npad; s->nf = m.nf;
+    s->kernel = SDUGKS_KERNEL_CARTESIAN;
+    constexpr int TX = 32, TY = 8;
+    s->n_tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    s->halo_cells = (int64_t)s->n_tiles * ((TX + 4) * (TY + 4) - TX * TY);
+    s->n_red_blocks = residual_blocks(n);
+    s->mesh_bytes = 0.0;
+    CartMesh &cm = s->cm;
+    cm.nx = g.nx; cm.ny = g.ny; cm.pitch = pitch; cm.periodic_x = g.px; cm.periodic_y = g.py;
+    for (int k = 0; k < 4; k++) cm.side_patch[k] = g.side_patch[k];
+    cm.npad = npad; cm.dx = g.dx; cm.dy = g.dy;
+    cm.dtV = prm->dt / (g.dx * g.dy);
+    cm.fdtV = (float)cm.dtV;
+
+    auto layout = [&](Arena &A) {
+        s->perm = A.take<int32_t>(n);
+        s->loc = A.take<int32_t>(n);
+        s->vol = A.take<double>(npad);
+        s->snap = A.take<double>(2 * npad);
+        s->partial = A.take<double>(4 * (size_t)s->n_red_blocks);
+        s->red = A.take<double>(4);
+        for (int b = 0; b < 2; b++) s->st.f[b] = A.take<char>(NQ * npad * fs);
+        for (int b = 0; b < 2; b++) s->st.W[b] = A.take<double>(3 * npad);
+    };
+    Arena A0;
+    layout(A0);
+    s->dbytes = A0.used + 256;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dmem, s->dbytes);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail(e == cudaErrorMemoryAllocation ? SDUGKS_ERR_OOM : SDUGKS_ERR_CUDA, "cudaMalloc(%zu): %s", A0.used,
+                    cudaGetErrorString(e));
+    }
+    Arena A{s->dmem, 0, s->dbytes};
+    layout(A);
+    std::vector<int32_t> perm(n), loc(n);
+    std::vector<double> vol(npad, 1.0);
+    for (int64_t c = 0; c < n; c++) {
+        perm[c] = (int32_t)c;
+        loc[c] = g.ci[c] + pitch * g.cj[c];
+        vol[loc[c]] = m.vol[c];
+    }
+    int rc2 = SDUGKS_OK;
+    auto chk = [&](cudaError_t ee, const char *what) {
+        if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
+    };
+    chk(cudaMemset(s->dmem, 0, s->dbytes), "memset");
+    chk(cudaMemcpy(s->perm, perm.data(), n * 4, cudaMemcpyHostToDevice), "upload perm");
+    chk(cudaMemcpy(s->loc, loc.data(), n * 4, cudaMemcpyHostToDevice), "upload loc");
+    chk(cudaMemcpy(s->vol, vol.data(), npad * 8, cudaMemcpyHostToDevice), "upload vol");
+    chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
+    chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    chk((cudaError_t)prepare(prec, SDUGKS_KERNEL_CARTESIAN), "kernel attributes");
+    if (rc2) { sdugks_solver_destroy(s); return rc2; }
+    fill_coefs(s->coefs, m, prm->tau, prm->dt);
+    *out = s;
+    return SDUGKS_OK;
 }
 
 extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *prm, void *stream, sdugks_solver **out)
@@ -397,8 +595,6 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         return fail(SDUGKS_ERR_INVALID_ARG, "tau and dt must be finite and > 0");
     if (prm->precision < SDUGKS_FP64 || prm->precision > SDUGKS_FP32_BF16DEV)
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown precision %d", prm->precision);
-    if (prm->kernel == SDUGKS_KERNEL_CARTESIAN)
-        return fail(SDUGKS_ERR_INVALID_ARG, "the Cartesian kernel is not available in this build");
     if (prm->kernel < SDUGKS_KERNEL_AUTO || prm->kernel > SDUGKS_KERNEL_CARTESIAN)
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown kernel %d", prm->kernel);
     if (prm->tile_cells != 0 && (prm->tile_cells < 16 || prm->tile_cells > TILE_MAX))
@@ -408,6 +604,12 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     int rc = merge_periodic(*m, F);
     if (rc) return rc;
     const int64_t n = m->nc;
+    if (prm->kernel != SDUGKS_KERNEL_TILED) {
+        CartGrid cg;
+        if (detect_cart(*m, cg)) return create_cart(*m, cg, prm, stream, out);
+        if (prm->kernel == SDUGKS_KERNEL_CARTESIAN)
+            return fail(SDUGKS_ERR_INVALID_ARG, "not a uniform Cartesian grid: %s", cg.why.c_str());
+    }
 
     // cell -> faces over the merged faces; slots in ascending merged face id, which
     // keeps the caller's face order, so per-cell sums do not depend on the tiling
@@ -667,28 +869,10 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     chk(up(s->tm.dtV, gdtv.data(), gdtv.size()), "upload dtV");
     chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
     chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
-    chk((cudaError_t)prepare(prec), "kernel attributes");
+    chk((cudaError_t)prepare(prec, SDUGKS_KERNEL_TILED), "kernel attributes");
     if (rc2) { sdugks_solver_destroy(s); return rc2; }
 
-    // coefficients
-    Coefs &c = s->coefs;
-    const double tau = prm->tau, dt = prm->dt;
-    c.a_plus = (2.0 * tau - dt) / (2.0 * tau);
-    c.b_plus = dt / (2.0 * tau);
-    c.c_face = 2.0 * tau / (2.0 * tau + dt);
-    c.r = dt / tau;
-    c.inv1r = 1.0 / (1.0 + dt / tau);
-    c.dt = dt;
-    c.tie = 1e-12;
-    c.fa_plus = (float)c.a_plus; c.fb_plus = (float)c.b_plus; c.fc_face = (float)c.c_face; c.fr = (float)c.r;
-    c.finv1r = (float)c.inv1r; c.fdt = (float)c.dt; c.ftie = (float)c.tie; c.fpad_ = 0.0f;
-    for (int q = 0; q < MAXPATCH; q++) {
-        c.bc_kind[q] = m->bc_kind[q];
-        for (int d = 0; d < 3; d++) {
-            c.bc_par[q][d] = m->bc_par[q][d];
-            c.fbc_par[q][d] = (float)m->bc_par[q][d];
-        }
-    }
+    fill_coefs(s->coefs, *m, prm->tau, prm->dt);
     // mesh bytes the tiled kernel reads per interior cell and step: slot kinds and
     // geometry (4 x 6 values) of its own cell, gradient data (d vectors, inverse,
     // neighbour indices) of interior and ring-1 cells, halo ids and dt/V
@@ -710,7 +894,7 @@ static int ensure_staging(sdugks_solver *s)
 
 static int snapshot(sdugks_solver *s, double *eps, double *mass)
 {
-    CUDA_TRY(launch_residual(s->n, s->npad, s->st.W[s->cur], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
+    CUDA_TRY(launch_residual(s->n, s->npad, s->loc, s->st.W[s->cur], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
                              s->stream));
     CUDA_TRY(cudaMemcpyAsync(s->h_red, s->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -736,7 +920,7 @@ extern "C" int sdugks_init(sdugks_solver *s, const double *rho, const double *u)
     if (rho) CUDA_TRY(cudaMemcpyAsync(d_rho, rho, sizeof(double) * s->n, cudaMemcpyHostToDevice, s->stream));
     if (u) CUDA_TRY(cudaMemcpyAsync(d_u, u, sizeof(double) * 2 * s->n, cudaMemcpyHostToDevice, s->stream));
     s->cur = 0; s->steps_done = 0;
-    CUDA_TRY(launch_init_state(s->p.precision, s->n, s->npad, s->perm, d_rho, d_u, s->st.f[0], s->st.W[0], s->stream));
+    CUDA_TRY(launch_init_state(s->p.precision, s->n, s->npad, s->perm, s->loc, d_rho, d_u, s->st.f[0], s->st.W[0], s->stream));
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);
 }
@@ -795,7 +979,7 @@ extern "C" int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double 
     if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
     if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_macros before init");
     CUDA_TRY(cudaSetDevice(s->device));
-    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->cur], d_rho, d_u, s->stream));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->loc, s->st.W[s->cur], d_rho, d_u, s->stream));
     return SDUGKS_OK;
 }
 
@@ -806,7 +990,7 @@ extern "C" int sdugks_get_macros(sdugks_solver *s, double *rho, double *u)
     CUDA_TRY(cudaSetDevice(s->device));
     int rc = ensure_staging(s);
     if (rc) return rc;
-    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->st.W[s->cur], s->staging, s->staging + s->n, s->stream));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->loc, s->st.W[s->cur], s->staging, s->staging + s->n, s->stream));
     if (rho) CUDA_TRY(cudaMemcpyAsync(rho, s->staging, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
     if (u) CUDA_TRY(cudaMemcpyAsync(u, s->staging + s->n, sizeof(double) * 2 * s->n, cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -829,7 +1013,7 @@ extern "C" int sdugks_get_state(sdugks_solver *s, double *f, double *W)
     int rc = ensure_staging(s);
     if (rc) return rc;
     double *df = s->staging, *dW = s->staging + 9 * s->n;
-    CUDA_TRY(launch_pack_state(s->p.precision, s->n, s->npad, s->perm, s->st.f[s->cur], s->st.W[s->cur], df, dW,
+    CUDA_TRY(launch_pack_state(s->p.precision, s->n, s->npad, s->perm, s->loc, s->st.f[s->cur], s->st.W[s->cur], df, dW,
                                s->stream));
     if (f) CUDA_TRY(cudaMemcpyAsync(f, df, sizeof(double) * 9 * s->n, cudaMemcpyDeviceToHost, s->stream));
     if (W) CUDA_TRY(cudaMemcpyAsync(W, dW, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
@@ -848,7 +1032,7 @@ extern "C" int sdugks_set_state(sdugks_solver *s, const double *f, const double 
     CUDA_TRY(cudaMemcpyAsync(df, f, sizeof(double) * 9 * s->n, cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaMemcpyAsync(dW, W, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
     s->cur = 0; s->steps_done = 0;
-    CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, df, dW, s->st.f[0], s->st.W[0], s->stream));
+    CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, s->loc, df, dW, s->st.f[0], s->st.W[0], s->stream));
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);
 }
@@ -868,7 +1052,9 @@ extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
     o->mesh_bytes_per_cell_step = s->mesh_bytes;
     o->kernel = s->kernel;
     o->precision = s->p.precision;
-    o->tile_cells = s->p.tile_cells ? s->p.tile_cells : TILE_MAX;
+    o->tile_cells = s->kernel == SDUGKS_KERNEL_CARTESIAN ? 256 : (s->p.tile_cells ? s->p.tile_cells : TILE_MAX);
+    o->nx = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->cm.nx : 0;
+    o->ny = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->cm.ny : 0;
     return SDUGKS_OK;
 }
 

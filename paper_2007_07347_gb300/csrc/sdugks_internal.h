@@ -61,13 +61,14 @@ struct TiledMesh {
     const double *vol;        // [npad] V
 };
 
-// Uniform Cartesian grid: cell (i, j) -> internal id i + nx j.
+// Uniform Cartesian grid of nx x ny rectangles dx x dy: cell (i, j) at i + pitch j.
 struct CartMesh {
-    int32_t nx, ny;
-    int64_t n, npad;
-    double dx, dy;
-    int32_t side_patch[4];    // patch of the bottom, right, top, left side (-1 = periodic)
-    bool periodic_x, periodic_y;
+    int32_t nx, ny, pitch;
+    int32_t periodic_x, periodic_y;
+    int32_t side_patch[4];    // patch of the bottom, right, top, left side (unused if periodic)
+    int64_t npad;             // >= pitch * ny, multiple of 32
+    double dx, dy, dtV;       // dtV = dt / (dx dy)
+    float fdtV;
 };
 
 // Device state of one solver, ping-pong: f [2][NQ][npad] (element type by
@@ -83,21 +84,26 @@ cudaError_t prepare_tiled_fp64();
 cudaError_t launch_step_tiled_fp64(const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
                                    const double *W_in, double *W_out, cudaStream_t st);
 cudaError_t prepare_tiled_fp32(int prec);
+cudaError_t prepare_cart(int prec);
+cudaError_t launch_step_cart(int prec, const CartMesh &m, const Coefs &c, const void *f_in, void *f_out,
+                             const double *W_in, double *W_out, cudaStream_t st);
 cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
                                    const double *W_in, double *W_out, cudaStream_t st);
 
 // state conversions between the caller's cell-major FP64 layout (user cell order)
-// and the internal SoA layout; perm[internal] = user id.
-cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *rho,
-                              const double *u, void *f, double *W, cudaStream_t st);
-cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const void *f,
+// and the internal SoA layout: the q-th listed cell is user cell perm[q] stored at
+// internal offset loc[q] (loc == nullptr: offset q).
+cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc,
+                              const double *rho, const double *u, void *f, double *W, cudaStream_t st);
+cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc, const void *f,
                               const double *W, double *f_out, double *W_out, cudaStream_t st);
-cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const double *f_in,
-                                const double *W_in, void *f, double *W, cudaStream_t st);
-cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const double *W, double *rho,
+cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc,
+                                const double *f_in, const double *W_in, void *f, double *W, cudaStream_t st);
+cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc, const double *W, double *rho,
                           double *u, cudaStream_t st);
-// residual: snap [2][npad] (U0, V0); partial [blocks][4]; out[4] = (num, den, mass, nonfinite)
-cudaError_t launch_residual(int64_t n, int64_t npad, const double *W, const double *vol, double *snap,
+// residual over the listed cells: snap [2][npad] (U0, V0); partial [blocks][4];
+// out[4] = (num, den, mass, non-finite count)
+cudaError_t launch_residual(int64_t n, int64_t npad, const int32_t *loc, const double *W, const double *vol, double *snap,
                             double *partial, int n_blocks, double *out, cudaStream_t st);
 int residual_blocks(int64_t n);
 
