@@ -289,7 +289,8 @@ def run_ours(args):
     alg_bytes = STATE_BYTES[args.precision] * n
     kern_avg_s = float(np.mean(kern_ms)) / 1e3
     achieved = alg_bytes / kern_avg_s / 1e9
-    key = f"k_step_tiled_{args.precision}_cavity{args.n}"
+    kname = {1: "k_step_tiled", 2: "k_step_cart"}[info["kernel"]]
+    key = f"{kname}_{args.precision}_cavity{args.n}"
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -298,7 +299,7 @@ def run_ours(args):
         "data": "synthetic", "config": config(args, case),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(key),
-                     "kernel": "k_step_tiled", "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes,
                      "avg_launch_us": kern_avg_s * 1e6, "peak_kind": f"{peak_kind} (hbm_gbs)"},
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": n * 12 * 8,
                 "d2h_bytes_per_step": n * 3 * 8 + 32, "steps": e2e_steps},

@@ -39,6 +39,35 @@ template <class R> __device__ __forceinline__ void feq9(R rho, R ux, R uy, R out
     }
 }
 
+// The same equilibrium with the shared terms factored out of the nine velocities
+// (opposite velocities share w rho [1 - 1.5 |u|^2 + 4.5 (xi.u)^2] and differ in the
+// sign of 3 w rho xi.u).  Used by the hot kernels.
+template <class R> __device__ __forceinline__ R recip(R x) { return R(1) / x; }
+template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+
+template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R out[NQ]) {
+    const R base = rho - R(1.5) * rho * (ux * ux + uy * uy);
+    const R r3 = R(3) * rho, r45 = R(4.5) * rho;
+    const R w0 = R(4) / R(9), w1 = R(1) / R(9), w5 = R(1) / R(36);
+    out[0] = w0 * base;
+    {
+        const R t = base + r45 * ux * ux, l = r3 * ux;
+        out[1] = w1 * (t + l); out[3] = w1 * (t - l);
+    }
+    {
+        const R t = base + r45 * uy * uy, l = r3 * uy;
+        out[2] = w1 * (t + l); out[4] = w1 * (t - l);
+    }
+    {
+        const R e = ux + uy, t = base + r45 * e * e, l = r3 * e;
+        out[5] = w5 * (t + l); out[7] = w5 * (t - l);
+    }
+    {
+        const R e = uy - ux, t = base + r45 * e * e, l = r3 * e;
+        out[6] = w5 * (t + l); out[8] = w5 * (t - l);
+    }
+}
+
 // Storage codecs.  FP64/FP32 store f itself.  BF16DEV stores the scaled deviation
 // d = (f - feq(W)) / w from the equilibrium of the same time level.
 template <int P> struct Store;

@@ -4,7 +4,7 @@
 
 namespace sdugks {
 
-constexpr int CTX = 32, CTY = 8;
+constexpr int CTX = 16, CTY = 16;
 
 cudaError_t prepare_cart_fp64();
 cudaError_t launch_cart_fp64(const CartMesh &m, const Coefs &c, const void *f_in, void *f_out, const double *W_in,

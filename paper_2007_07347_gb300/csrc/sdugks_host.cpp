@@ -528,7 +528,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     s->stream = static_cast<cudaStream_t>(stream);
     s->n = n; s->npad = npad; s->nf = m.nf;
     s->kernel = SDUGKS_KERNEL_CARTESIAN;
-    constexpr int TX = 32, TY = 8;
+    constexpr int TX = 16, TY = 16;
     s->n_tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     s->halo_cells = (int64_t)s->n_tiles * ((TX + 4) * (TY + 4) - TX * TY);
     s->n_red_blocks = residual_blocks(n);

@@ -2,11 +2,16 @@
 //
 // The same update as the tiled kernel (Eqs. fbarplus, fbpsource, fbar, Macro, Feq,
 // f_t_n+1, MesoFlux, MacroFlux, MacroUpdate, fn+1), specialised to nx x ny
-// rectangles of one size: cell (i, j) sits at i + pitch j, a CTA owns a TX x TY
-// block and stages it with a two-cell halo, the LLSR gradient reduces to central
-// (or, next to a wall, one-sided) differences, and on every face the upwind side of
-// each velocity is known at compile time.  No mesh arrays are read.  Each grid side
-// is either one boundary patch or periodic with the opposite side.
+// rectangles of one size: cell (i, j) sits at i + pitch j and a CTA owns a TX x TY
+// block, staged with a two-cell halo.  The LLSR gradient reduces to central (or,
+// next to a wall, one-sided) differences, and on every face the upwind side of each
+// velocity is known at compile time.  No mesh arrays are read.  Each grid side is one
+// boundary patch or periodic with the opposite side.
+//
+// Phases: (1) fbar+ of the block and halo into shared memory; (2) gradients of the
+// block and its first ring; (3) every interior face of the block once, its six
+// non-zero fluxes (xi.n l f_b for the velocities that cross it) into shared memory;
+// (4) per cell: boundary faces, the flux sum, W^{n+1} in FP64 and f^{n+1}.
 #pragma once
 #include "d2q9.cuh"
 #include "step_tiled.cuh"   // CoefR
@@ -17,77 +22,104 @@ template <int TX, int TY> struct CartShape {
     static constexpr int LX = TX + 4, LY = TY + 4;   // staged block with a two-cell halo
     static constexpr int GX = TX + 2, GY = TY + 2;   // cells whose gradient is needed
     static constexpr int NT = TX * TY;
+    static constexpr int NFX = (TX + 1) * TY;        // faces of constant x inside/around the block
+    static constexpr int NFY = TX * (TY + 1);        // faces of constant y
 };
 
 template <int P, int TX, int TY> constexpr size_t cart_smem() {
     using S = CartShape<TX, TY>;
-    return sizeof(typename Store<P>::R) * (size_t)(NQ * S::LX * S::LY + 2 * NQ * S::GX * S::GY);
+    return sizeof(typename Store<P>::R) *
+           (size_t)(NQ * S::LX * S::LY + 2 * NQ * S::GX * S::GY + 6 * (S::NFX + S::NFY));
 }
 
-// Face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y): returns the flux
-// contribution (xi . n l) f_b for every velocity in F.
-template <int D, class R>
-__device__ __forceinline__ void cart_face(R F[NQ], const R *s_fbp, const R *s_sig, int lme, int loth, int gme,
-                                          int goth, bool interior, int patch, const Coefs &c, const CoefR<R> &k,
-                                          const R fn[NQ], const R feqn[NQ], R rho_n, R ux_n, R uy_n, R hx, R hy,
-                                          int LXY, int GXY)
+// Velocities crossing a face of constant x (xi_x != 0) and of constant y, in slot order.
+__device__ constexpr int XSLOT_A(int k) { return k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
+__device__ constexpr int YSLOT_A(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
+
+// (u_x, u_y) from rho, rho u in the compute precision
+template <class R> __device__ __forceinline__ void vel_of(R rho, R m1, R m2, R &ux, R &uy) {
+    const R inv = recip<R>(rho);
+    ux = m1 * inv;
+    uy = m2 * inv;
+}
+template <> __device__ __forceinline__ void vel_of<double>(double rho, double m1, double m2, double &ux, double &uy) {
+    ux = m1 / rho;
+    uy = m2 / rho;
+}
+
+// Interface distribution on a face between cell L (below/left) and R (above/right),
+// along axis AX (0: face of constant x, 1: of constant y), from the staged fbar+ and
+// gradients; writes (xi . n_+ l) f_b of the six crossing velocities (n_+ = +x or +y).
+template <int AX, class R>
+__device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, const R *s_sig, int lL, int lR, int gL,
+                                                   int gR, const CoefR<R> &k, R hx, R hy, int LXY, int GXY)
 {
-    // outward normal * length, and x_f - x_j (x_f - x_k is its negative)
+    // x_f - x_L = +h/2 along the axis, x_f - x_R = -h/2
+    const R hl = AX == 0 ? R(0.5) * hx : R(0.5) * hy;
+    R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
+#pragma unroll
+    for (int a = 0; a < NQ; a++) {
+        const int sg = AX == 0 ? EX(a) : EY(a);      // sign of xi . n_+
+        const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
+        // (x_f - xi dt - x_u) for u = L and u = R
+        const R pxL = AX == 0 ? hl - ex : -ex, pyL = AX == 0 ? -ey : hl - ey;
+        const R pxR = AX == 0 ? -hl - ex : -ex, pyR = AX == 0 ? -ey : -hl - ey;
+        R A = R(0), B = R(0);
+        if (sg >= 0)
+            A = s_fbp[a * LXY + lL] + pxL * s_sig[(2 * a) * GXY + gL] + pyL * s_sig[(2 * a + 1) * GXY + gL];
+        if (sg <= 0)
+            B = s_fbp[a * LXY + lR] + pxR * s_sig[(2 * a) * GXY + gR] + pyR * s_sig[(2 * a + 1) * GXY + gR];
+        fbar[a] = sg > 0 ? A : (sg < 0 ? B : R(0.5) * (A + B));
+        w0 += fbar[a];
+        if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
+        if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+    }
+    R ux, uy, feqb[NQ];
+    vel_of<R>(w0, w1, w2, ux, uy);
+    feq9f<R>(w0, ux, uy, feqb);
+    const R len = AX == 0 ? hy : hx;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        const int a = AX == 0 ? XSLOT_A(q) : YSLOT_A(q);
+        const int sg = AX == 0 ? EX(a) : EY(a);
+        const R s = sg > 0 ? len : -len;
+        flux[q] = s * ((fbar[a] + k.b * feqb[a]) * k.c);
+    }
+}
+
+// Boundary face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y): adds the
+// outward flux (xi . n l) f_b of every crossing velocity to F (Sec. III rules).
+template <int D, class R>
+__device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, const R *s_sig, int lme, int gme, int patch,
+                                                   const Coefs &c, const CoefR<R> &k, const R fn[NQ], const R feqn[NQ],
+                                                   R rho_n, R ux_n, R uy_n, R hx, R hy, int LXY, int GXY)
+{
     const R nx = D == 0 ? hy : (D == 1 ? -hy : R(0));
     const R ny = D == 2 ? hx : (D == 3 ? -hx : R(0));
     const R rx = D == 0 ? R(0.5) * hx : (D == 1 ? R(-0.5) * hx : R(0));
     const R ry = D == 2 ? R(0.5) * hy : (D == 3 ? R(-0.5) * hy : R(0));
-    if (interior) {
-        R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
+    const int bk = c.bc_kind[patch];
+    R rb = rho_n, ubx = R(0), uby = R(0);
+    if (bk == BK_MOVING_WALL) { ubx = CoefR<R>::par(c, patch, 0); uby = CoefR<R>::par(c, patch, 1); }
+    else if (bk == BK_FARFIELD) {
+        rb = CoefR<R>::par(c, patch, 0); ubx = CoefR<R>::par(c, patch, 1); uby = CoefR<R>::par(c, patch, 2);
+    } else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
+    R feqb[NQ];
+    feq9f<R>(rb, ubx, uby, feqb);
 #pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            // sign of xi . n, fixed per velocity and direction
-            const int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));
-            const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
-            R A = R(0), B = R(0);
-            if (sg >= 0)
-                A = s_fbp[a * LXY + lme] + (rx - ex) * s_sig[(2 * a) * GXY + gme] + (ry - ey) * s_sig[(2 * a + 1) * GXY + gme];
-            if (sg <= 0)
-                B = s_fbp[a * LXY + loth] + (-rx - ex) * s_sig[(2 * a) * GXY + goth] +
-                    (-ry - ey) * s_sig[(2 * a + 1) * GXY + goth];
-            fbar[a] = sg > 0 ? A : (sg < 0 ? B : R(0.5) * (A + B));
-            w0 += fbar[a];
-            if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
-            if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+    for (int a = 0; a < NQ; a++) {
+        const int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));
+        if (sg == 0) continue;
+        const R s = xdot<R>(a, nx, ny);
+        R fb;
+        if (sg < 0) {
+            fb = feqb[a] + (fn[a] - feqn[a]);          // non-equilibrium extrapolation
+        } else {
+            const R A = s_fbp[a * LXY + lme] + (rx - R(EX(a)) * k.dt) * s_sig[(2 * a) * GXY + gme] +
+                        (ry - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * GXY + gme];
+            fb = (A + k.b * feqb[a]) * k.c;
         }
-        R feqb[NQ];
-        feq9<R>(w0, w1 / w0, w2 / w0, feqb);
-#pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            const int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));
-            if (sg == 0) continue;
-            const R s = xdot<R>(a, nx, ny);
-            F[a] += s * ((fbar[a] + k.b * feqb[a]) * k.c);
-        }
-    } else {
-        const int bk = c.bc_kind[patch];
-        R rb = rho_n, ubx = R(0), uby = R(0);
-        if (bk == BK_MOVING_WALL) { ubx = CoefR<R>::par(c, patch, 0); uby = CoefR<R>::par(c, patch, 1); }
-        else if (bk == BK_FARFIELD) {
-            rb = CoefR<R>::par(c, patch, 0); ubx = CoefR<R>::par(c, patch, 1); uby = CoefR<R>::par(c, patch, 2);
-        } else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
-        R feqb[NQ];
-        feq9<R>(rb, ubx, uby, feqb);
-#pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            const int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));
-            if (sg == 0) continue;
-            const R s = xdot<R>(a, nx, ny);
-            R fb;
-            if (sg < 0) {
-                fb = feqb[a] + (fn[a] - feqn[a]);          // non-equilibrium extrapolation
-            } else {
-                const R A = s_fbp[a * LXY + lme] + (rx - R(EX(a)) * k.dt) * s_sig[(2 * a) * GXY + gme] +
-                            (ry - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * GXY + gme];
-                fb = (A + k.b * feqb[a]) * k.c;
-            }
-            F[a] += s * fb;
-        }
+        F[a] += s * fb;
     }
 }
 
@@ -103,6 +135,8 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][LX]
     R *s_sig = s_fbp + NQ * LXY;                     // [2 NQ][GY][GX]
+    R *s_fx = s_sig + 2 * NQ * GXY;                  // [6][NFX] fluxes through faces of constant x
+    R *s_fy = s_fx + 6 * S::NFX;                     // [6][NFY]
 
     const int ntx = (m.nx + TX - 1) / TX;
     const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
@@ -111,8 +145,9 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     const CoefR<R> k(c);
     const R hx = R(m.dx), hy = R(m.dy);
 
-    // domain cell of a staged position (periodic sides wrap), or -1 outside
-    auto cell_of = [&](int gi, int gj) -> int64_t {
+    // domain cell of a block-relative position (periodic sides wrap), or -1 outside
+    auto cell_of = [&](int bi, int bj) -> int64_t {
+        int gi = x0 + bi, gj = y0 + bj;
         if (gi < 0 || gi >= m.nx) {
             if (!m.periodic_x) return -1;
             gi = (gi + m.nx) % m.nx;
@@ -123,8 +158,17 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         }
         return gi + pitch * gj;
     };
+    auto stage = [&](int64_t gc, R &rho, R &ux, R &uy, R fe[NQ], double &w0, double &w1, double &w2) {
+        w0 = Wn[gc]; w1 = Wn[np + gc]; w2 = Wn[2 * np + gc];
+        rho = R(w0);
+        if constexpr (P == P_FP64) vel_of<R>(w0, w1, w2, ux, uy);
+        else vel_of<R>(rho, R(w1), R(w2), ux, uy);
+        feq9f<R>(rho, ux, uy, fe);
+    };
 
-    // ---- phase 1: fbar+ of the own cell (kept in registers) and of the halo
+    // ---- phase 1: fbar+ = a f^n + b feq(W^n): own cell (kept in registers), then the
+    // rest of the staged area (the two-cell ring, and block positions without an own
+    // cell: past the grid edge, holding wrapped cells on periodic sides)
     const int gi = x0 + ti, gj = y0 + tj;
     const bool active = gi < m.nx && gj < m.ny;
     const int64_t g = (int64_t)gi + pitch * gj;
@@ -133,26 +177,21 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     R rho_n = R(1), ux_n = R(0), uy_n = R(0);
     double w0n = 1.0, w1n = 0.0, w2n = 0.0;
     if (active) {
-        w0n = Wn[g]; w1n = Wn[np + g]; w2n = Wn[2 * np + g];
-        macro_of<R>(w0n, w1n, w2n, rho_n, ux_n, uy_n);
-        feq9<R>(rho_n, ux_n, uy_n, feqn);
+        stage(g, rho_n, ux_n, uy_n, feqn, w0n, w1n, w2n);
 #pragma unroll
         for (int a = 0; a < NQ; a++) {
             fn[a] = SP::dec(fin[a * np + g], feqn[a], a);
             s_fbp[a * LXY + lme] = k.a * fn[a] + k.b * feqn[a];
         }
     }
-    // every other staged position: the two-cell ring, and block positions without an
-    // own cell (past the grid edge; they hold wrapped cells on periodic sides)
     for (int q = tid; q < LXY; q += S::NT) {
-        const int li = q % S::LX, lj = q / S::LX;
-        const int bi = li - 2, bj = lj - 2;
+        const int bi = q % S::LX - 2, bj = q / S::LX - 2;
         if (bi >= 0 && bi < TX && bj >= 0 && bj < TY && x0 + bi < m.nx && y0 + bj < m.ny) continue;
-        const int64_t gh = cell_of(x0 + bi, y0 + bj);
+        const int64_t gh = cell_of(bi, bj);
         if (gh < 0) continue;
         R rho, ux, uy, fe[NQ];
-        macro_of<R>(Wn[gh], Wn[np + gh], Wn[2 * np + gh], rho, ux, uy);
-        feq9<R>(rho, ux, uy, fe);
+        double a0, a1, a2;
+        stage(gh, rho, ux, uy, fe, a0, a1, a2);
 #pragma unroll
         for (int a = 0; a < NQ; a++) s_fbp[a * LXY + q] = k.a * SP::dec(fin[a * np + gh], fe[a], a) + k.b * fe[a];
     }
@@ -161,58 +200,92 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     // ---- phase 2: gradient on the block and its first ring.  LLSR over the existing
     // face neighbours of a uniform grid: sigma_x = sum_k dx_k (phi_k - phi) / sum_k dx_k^2
     for (int q = tid; q < GXY; q += S::NT) {
-        const int gx = q % S::GX, gy = q / S::GX;
-        const int ci = x0 + gx - 1, cj = y0 + gy - 1;
-        if (cell_of(ci, cj) < 0) continue;
+        const int bi = q % S::GX - 1, bj = q / S::GX - 1;
+        if (cell_of(bi, bj) < 0) continue;
+        const int ci = x0 + bi, cj = y0 + bj;
         const bool hasE = m.periodic_x || ci + 1 < m.nx, hasW = m.periodic_x || ci - 1 >= 0;
         const bool hasN = m.periodic_y || cj + 1 < m.ny, hasS = m.periodic_y || cj - 1 >= 0;
-        const int l = (gy + 1) * S::LX + (gx + 1);
+        const int l = (bj + 2) * S::LX + (bi + 2);
         const R nxk = R((hasE ? 1 : 0) + (hasW ? 1 : 0)), nyk = R((hasN ? 1 : 0) + (hasS ? 1 : 0));
         const bool singular = nxk == R(0) || nyk == R(0);
         const R ax = singular ? R(0) : R(1) / (nxk * hx * hx), ay = singular ? R(0) : R(1) / (nyk * hy * hy);
+        const R cE = hasE ? hx : R(0), cW = hasW ? hx : R(0), cN = hasN ? hy : R(0), cS = hasS ? hy : R(0);
+        const int oE = hasE ? 1 : 0, oW = hasW ? -1 : 0, oN = hasN ? S::LX : 0, oS = hasS ? -S::LX : 0;
 #pragma unroll
         for (int a = 0; a < NQ; a++) {
             const R *f = s_fbp + a * LXY;
             const R p = f[l];
-            R bx = R(0), by = R(0);
-            if (hasE) bx += hx * (f[l + 1] - p);
-            if (hasW) bx += -hx * (f[l - 1] - p);
-            if (hasN) by += hy * (f[l + S::LX] - p);
-            if (hasS) by += -hy * (f[l - S::LX] - p);
+            const R bx = cE * (f[l + oE] - p) - cW * (f[l + oW] - p);
+            const R by = cN * (f[l + oN] - p) - cS * (f[l + oS] - p);
             s_sig[(2 * a) * GXY + q] = ax * bx;
             s_sig[(2 * a + 1) * GXY + q] = ay * by;
         }
     }
     __syncthreads();
+
+    // ---- phase 3: interior faces of the block, each once
+    for (int q = tid; q < S::NFX + S::NFY; q += S::NT) {
+        if (q < S::NFX) {
+            // face of constant x between block columns fi-1 (L) and fi (R), row fj
+            const int fi = q % (TX + 1), fj = q / (TX + 1);
+            if (cell_of(fi - 1, fj) < 0 || cell_of(fi, fj) < 0) continue;   // boundary or outside
+            const int lL = (fj + 2) * S::LX + (fi + 1), gL = (fj + 1) * S::GX + fi;
+            R fl[6];
+            cart_interior_face<0, R>(fl, s_fbp, s_sig, lL, lL + 1, gL, gL + 1, k, hx, hy, LXY, GXY);
+#pragma unroll
+            for (int r = 0; r < 6; r++) s_fx[r * S::NFX + q] = fl[r];
+        } else {
+            // face of constant y between block rows fj-1 (below) and fj (above), column fi
+            const int qq = q - S::NFX, fi = qq % TX, fj = qq / TX;
+            if (cell_of(fi, fj - 1) < 0 || cell_of(fi, fj) < 0) continue;
+            const int lB = (fj + 1) * S::LX + (fi + 2), gB = fj * S::GX + (fi + 1);
+            R fl[6];
+            cart_interior_face<1, R>(fl, s_fbp, s_sig, lB, lB + S::LX, gB, gB + S::GX, k, hx, hy, LXY, GXY);
+#pragma unroll
+            for (int r = 0; r < 6; r++) s_fy[r * S::NFY + qq] = fl[r];
+        }
+    }
+    __syncthreads();
     if (!active) return;
 
-    // ---- phase 3: the four faces of the own cell (order -x, +x, -y, +y)
+    // ---- phase 4: flux sum over the own cell's faces (order -x, +x, -y, +y)
     R F[NQ];
 #pragma unroll
     for (int a = 0; a < NQ; a++) F[a] = R(0);
     const int gme = (tj + 1) * S::GX + (ti + 1);
-    {
-        const bool in = m.periodic_x || gi - 1 >= 0;
-        cart_face<1, R>(F, s_fbp, s_sig, lme, lme - 1, gme, gme - 1, in, m.side_patch[3], c, k, fn, feqn, rho_n, ux_n,
-                        uy_n, hx, hy, LXY, GXY);
+    const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
+    const bool inW = m.periodic_x || gi - 1 >= 0, inE = m.periodic_x || gi + 1 < m.nx;
+    const bool inS = m.periodic_y || gj - 1 >= 0, inN = m.periodic_y || gj + 1 < m.ny;
+    if (inW) {
+#pragma unroll
+        for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
+    } else {
+        cart_boundary_face<1, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[3], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
+                                 LXY, GXY);
     }
-    {
-        const bool in = m.periodic_x || gi + 1 < m.nx;
-        cart_face<0, R>(F, s_fbp, s_sig, lme, lme + 1, gme, gme + 1, in, m.side_patch[1], c, k, fn, feqn, rho_n, ux_n,
-                        uy_n, hx, hy, LXY, GXY);
+    if (inE) {
+#pragma unroll
+        for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NFX + fW + 1];
+    } else {
+        cart_boundary_face<0, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[1], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
+                                 LXY, GXY);
     }
-    {
-        const bool in = m.periodic_y || gj - 1 >= 0;
-        cart_face<3, R>(F, s_fbp, s_sig, lme, lme - S::LX, gme, gme - S::GX, in, m.side_patch[0], c, k, fn, feqn, rho_n,
-                        ux_n, uy_n, hx, hy, LXY, GXY);
+    if (inS) {
+#pragma unroll
+        for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NFY + fS];
+    } else {
+        cart_boundary_face<3, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[0], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
+                                 LXY, GXY);
     }
-    {
-        const bool in = m.periodic_y || gj + 1 < m.ny;
-        cart_face<2, R>(F, s_fbp, s_sig, lme, lme + S::LX, gme, gme + S::GX, in, m.side_patch[2], c, k, fn, feqn, rho_n,
-                        ux_n, uy_n, hx, hy, LXY, GXY);
+    if (inN) {
+#pragma unroll
+        for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NFY + fS + TX];
+    } else {
+        cart_boundary_face<2, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[2], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
+                                 LXY, GXY);
     }
 
-    // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1}
+    // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)
     const R dtv = P == P_FP64 ? R(m.dtV) : R(m.fdtV);
     R M0 = R(0), M1 = R(0), M2 = R(0);
 #pragma unroll
@@ -228,13 +301,13 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     Wout[2 * np + g] = W2;
     R rho1, ux1, uy1, feq1[NQ];
     if constexpr (P == P_FP64) {
-        macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
+        rho1 = W0;
+        vel_of<R>(W0, W1, W2, ux1, uy1);
     } else {
         rho1 = R(w0n) - d0;
-        ux1 = (R(w1n) - d1) / rho1;
-        uy1 = (R(w2n) - d2) / rho1;
+        vel_of<R>(rho1, R(w1n) - d1, R(w2n) - d2, ux1, uy1);
     }
-    feq9<R>(rho1, ux1, uy1, feq1);
+    feq9f<R>(rho1, ux1, uy1, feq1);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         R fnew;
