@@ -68,6 +68,18 @@ template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R ou
     }
 }
 
+// (u_x, u_y) from rho, rho u in the compute precision (FP32: one correctly rounded
+// reciprocal; FP64: two IEEE divisions).
+template <class R> __device__ __forceinline__ void vel_of(R rho, R m1, R m2, R &ux, R &uy) {
+    const R inv = recip<R>(rho);
+    ux = m1 * inv;
+    uy = m2 * inv;
+}
+template <> __device__ __forceinline__ void vel_of<double>(double rho, double m1, double m2, double &ux, double &uy) {
+    ux = m1 / rho;
+    uy = m2 / rho;
+}
+
 // Storage codecs.  FP64/FP32 store f itself.  BF16DEV stores the scaled deviation
 // d = (f - feq(W)) / w from the equilibrium of the same time level.
 template <int P> struct Store;
@@ -87,11 +99,45 @@ template <> struct Store<P_BF16DEV> {
     static __device__ __forceinline__ T enc(R f, R feq, int a) { return __float2bfloat16_rn((f - feq) * inv_wq<R>(a)); }
 };
 
+// IEEE-754 format conversions by field arithmetic on the integer pipe (the FP64 unit of
+// this GPU is narrow, and the FP32 kernels only need FP32 copies of the FP64 W).
+// binary64 -> binary32, mantissa truncated (error < 1 ulp of binary32); magnitudes
+// below the binary32 normal range become signed zero, above it infinity; NaN stays NaN.
+__device__ __forceinline__ float d2f_fields(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int ef = (int)((hi >> 20) & 0x7ffu);
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const int e = ef - 1023 + 127;
+    if (ef == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+// binary32 -> binary64, exact for normal numbers, zero, infinity and NaN; binary32
+// subnormals (below 1.2e-38) become signed zero.
+__device__ __forceinline__ double f2d_fields(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u, ef = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi;
+    if (ef == 0) hi = sign;
+    else if (ef == 0xff) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    else hi = sign | ((ef - 127u + 1023u) << 20) | (m >> 3);
+    const unsigned lo = (ef == 0 || ef == 0xff) ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+template <class R> __device__ __forceinline__ R from_f64(double d) { return R(d); }
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return d2f_fields(d); }
+template <class R> __device__ __forceinline__ double to_f64(R x) { return double(x); }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_fields(x); }
+
 // Conserved variables (rho, rho u) -> (rho, u) in the compute precision.
 template <class R> __device__ __forceinline__ void macro_of(double w0, double w1, double w2, R &rho, R &ux, R &uy) {
-    rho = R(w0);
-    ux = R(w1) / rho;
-    uy = R(w2) / rho;
+    rho = from_f64<R>(w0);
+    vel_of<R>(rho, from_f64<R>(w1), from_f64<R>(w2), ux, uy);
 }
 template <> __device__ __forceinline__ void macro_of<double>(double w0, double w1, double w2, double &rho, double &ux,
                                                              double &uy) {

@@ -36,17 +36,6 @@ template <int P, int TX, int TY> constexpr size_t cart_smem() {
 __device__ constexpr int XSLOT_A(int k) { return k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
 __device__ constexpr int YSLOT_A(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
 
-// (u_x, u_y) from rho, rho u in the compute precision
-template <class R> __device__ __forceinline__ void vel_of(R rho, R m1, R m2, R &ux, R &uy) {
-    const R inv = recip<R>(rho);
-    ux = m1 * inv;
-    uy = m2 * inv;
-}
-template <> __device__ __forceinline__ void vel_of<double>(double rho, double m1, double m2, double &ux, double &uy) {
-    ux = m1 / rho;
-    uy = m2 / rho;
-}
-
 // Interface distribution on a face between cell L (below/left) and R (above/right),
 // along axis AX (0: face of constant x, 1: of constant y), from the staged fbar+ and
 // gradients; writes (xi . n_+ l) f_b of the six crossing velocities (n_+ = +x or +y).
@@ -160,9 +149,9 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     };
     auto stage = [&](int64_t gc, R &rho, R &ux, R &uy, R fe[NQ], double &w0, double &w1, double &w2) {
         w0 = Wn[gc]; w1 = Wn[np + gc]; w2 = Wn[2 * np + gc];
-        rho = R(w0);
+        rho = from_f64<R>(w0);
         if constexpr (P == P_FP64) vel_of<R>(w0, w1, w2, ux, uy);
-        else vel_of<R>(rho, R(w1), R(w2), ux, uy);
+        else vel_of<R>(rho, from_f64<R>(w1), from_f64<R>(w2), ux, uy);
         feq9f<R>(rho, ux, uy, fe);
     };
 
@@ -295,7 +284,7 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
     }
     const R d0 = dtv * M0, d1 = dtv * M1, d2 = dtv * M2;
-    const double W0 = w0n - (double)d0, W1 = w1n - (double)d1, W2 = w2n - (double)d2;
+    const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
     Wout[g] = W0;
     Wout[np + g] = W1;
     Wout[2 * np + g] = W2;
@@ -304,8 +293,8 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         rho1 = W0;
         vel_of<R>(W0, W1, W2, ux1, uy1);
     } else {
-        rho1 = R(w0n) - d0;
-        vel_of<R>(rho1, R(w1n) - d1, R(w2n) - d2, ux1, uy1);
+        rho1 = rho_n - d0;
+        vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
     }
     feq9f<R>(rho1, ux1, uy1, feq1);
 #pragma unroll

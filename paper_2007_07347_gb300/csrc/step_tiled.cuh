@@ -64,7 +64,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     if (active) {
         w0n = Wn[g]; w1n = Wn[np + g]; w2n = Wn[2 * np + g];
         macro_of<R>(w0n, w1n, w2n, rho_n, ux_n, uy_n);
-        feq9<R>(rho_n, ux_n, uy_n, feqn);
+        feq9f<R>(rho_n, ux_n, uy_n, feqn);
 #pragma unroll
         for (int a = 0; a < NQ; a++) {
             fn[a] = SP::dec(fin[a * np + g], feqn[a], a);
@@ -75,7 +75,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         const int64_t gh = m.halo[h0 + i - n_int];
         R rho, ux, uy, fe[NQ];
         macro_of<R>(Wn[gh], Wn[np + gh], Wn[2 * np + gh], rho, ux, uy);
-        feq9<R>(rho, ux, uy, fe);
+        feq9f<R>(rho, ux, uy, fe);
 #pragma unroll
         for (int a = 0; a < NQ; a++)
             s_fbp[a * LOC_MAX + i] = k.a * SP::dec(fin[a * np + gh], fe[a], a) + k.b * fe[a];
@@ -140,8 +140,9 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
             }
-            R feqb[NQ];
-            feq9<R>(w0, w1 / w0, w2 / w0, feqb);
+            R ux, uy, feqb[NQ];
+            vel_of<R>(w0, w1, w2, ux, uy);
+            feq9f<R>(w0, ux, uy, feqb);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
@@ -155,7 +156,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
             else if (bk == BK_FARFIELD) { rb = CoefR<R>::par(c, p, 0); ubx = CoefR<R>::par(c, p, 1); uby = CoefR<R>::par(c, p, 2); }
             else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
             R feqb[NQ];
-            feq9<R>(rb, ubx, uby, feqb);
+            feq9f<R>(rb, ubx, uby, feqb);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
@@ -182,7 +183,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
     }
     const R d0 = dtv * M0, d1 = dtv * M1, d2 = dtv * M2;
-    const double W0 = w0n - (double)d0, W1 = w1n - (double)d1, W2 = w2n - (double)d2;
+    const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
     Wout[g] = W0;
     Wout[np + g] = W1;
     Wout[2 * np + g] = W2;
@@ -191,11 +192,10 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
     } else {
         // FP32 compute: W^{n+1} in FP32 from the FP32 copies already at hand
-        rho1 = R(w0n) - d0;
-        ux1 = (R(w1n) - d1) / rho1;
-        uy1 = (R(w2n) - d2) / rho1;
+        rho1 = rho_n - d0;
+        vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
     }
-    feq9<R>(rho1, ux1, uy1, feq1);
+    feq9f<R>(rho1, ux1, uy1, feq1);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         R fnew;
