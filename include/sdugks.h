@@ -169,6 +169,33 @@ int sdugks_residual(sdugks_solver *s, double *eps, double *mass);
 int sdugks_get_state(sdugks_solver *s, double *f, double *W);
 int sdugks_set_state(sdugks_solver *s, const double *f, const double *W);
 
+/* The residual and mass reduction of sdugks_residual, for callers that may not
+ * allocate device memory: over caller-owned device arrays, with the reduction's
+ * scratch (per-block partial sums) in a fixed array inside the library instead of
+ * memory it allocates.  This is a facility of this library; the paper has no
+ * counterpart.  It is for code that must not call cudaMalloc or any allocating
+ * routine -- a loop whose device memory is owned and budgeted by another runtime,
+ * or a latency-critical path that must not enter the allocator.
+ *   n          number of cells, 1 <= n <= 4,194,304 (larger n: INVALID_ARG; the
+ *              fixed scratch holds one partial row per 1024 cells, 4096 rows)
+ *   d_W        device, [n][3] FP64 (rho, rho u_x, rho u_y)            (read)
+ *   d_vol      device, [n] FP64 cell areas                            (read)
+ *   d_snap     device, [n][2] FP64 (U0, V0) snapshot: read, then overwritten
+ *              with the current (U, V), as sdugks_residual refreshes its own
+ *   d_out      device, [3] FP64: eps (+inf when the snapshot is at rest), the mass
+ *              sum V rho, and the count of cells with non-finite or zero-density W
+ *   stream     cudaStream_t (NULL = default stream); the call is asynchronous
+ * No memory is allocated and nothing is freed.  The scratch is 128 KiB of device
+ * memory held on every GPU that loads the library until the process exits.  The
+ * first call on a device (with that device current) looks up the scratch's device
+ * address; make that first call before any stream capture on that device.  All calls
+ * share the scratch, and every call overwrites the rows it uses before reading them,
+ * so calls that run one after another need no clearing; calls that overlap on the
+ * GPU (different streams, no ordering) race on the scratch and give wrong results.
+ * Errors: INVALID_ARG, CUDA (message in sdugks_last_error()). */
+int sdugks_residual_noalloc(int64_t n, const double *d_W, const double *d_vol, double *d_snap, double *d_out,
+                            void *stream);
+
 int sdugks_solver_info(const sdugks_solver *s, sdugks_info *out);
 
 void sdugks_solver_destroy(sdugks_solver *s);

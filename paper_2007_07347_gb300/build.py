@@ -27,6 +27,7 @@ CU_UNITS = {
     "k_cart_fp64.cu": ["--fmad=false"],
     "k_cart.cu": [],
     "k_util.cu": [],
+    "k_residual_noalloc.cu": [],
 }
 CXX_UNITS = ["sdugks_host.cpp"]
 HEADERS = ["sdugks_internal.h", "d2q9.cuh", "step_tiled.cuh", "step_cart.cuh"]

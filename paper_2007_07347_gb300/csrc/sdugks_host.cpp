@@ -32,6 +32,12 @@ static int fail(int code, const char *fmt, ...)
     return code;
 }
 
+int sdugks::set_error(int code, const char *msg)
+{
+    g_err = msg;
+    return code;
+}
+
 #define CUDA_TRY(expr)                                                                           \
     do {                                                                                         \
         cudaError_t e_ = (expr);                                                                 \

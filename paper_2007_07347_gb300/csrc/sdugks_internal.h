@@ -107,4 +107,7 @@ cudaError_t launch_residual(int64_t n, int64_t npad, const int32_t *loc, const d
                             double *partial, int n_blocks, double *out, cudaStream_t st);
 int residual_blocks(int64_t n);
 
+// records msg as the calling thread's sdugks_last_error() and returns code
+int set_error(int code, const char *msg);
+
 }  // namespace sdugks
