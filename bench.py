@@ -135,10 +135,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+STEP_SOURCES = ["d2q9.cuh", "sdugks_internal.h", "step_cart.cuh", "step_tiled.cuh", "k_cart.cu", "k_step_fp32.cu"]
+
+
 def kernel_source_hash():
+    """Hash of the sources the step kernels are compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2007_07347_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STEP_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
