@@ -112,8 +112,16 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, cons
     }
 }
 
+// Threads per CTA: one per interior face of the block (>= cells, >= staged positions).
+template <int TX, int TY> __host__ __device__ constexpr int cart_threads() {
+    constexpr int nf = CartShape<TX, TY>::NFX + CartShape<TX, TY>::NFY;
+    constexpr int nl = CartShape<TX, TY>::LX * CartShape<TX, TY>::LY;
+    constexpr int m = nf > nl ? nf : nl;
+    return (m + 31) / 32 * 32;
+}
+
 template <int P, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : 2)
 k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restrict__ fin,
             typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn, double *__restrict__ Wout)
 {
@@ -121,6 +129,7 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     using SP = Store<P>;
     using S = CartShape<TX, TY>;
     constexpr int LXY = S::LX * S::LY, GXY = S::GX * S::GY;
+    constexpr int NTH = cart_threads<TX, TY>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][LX]
     R *s_sig = s_fbp + NQ * LXY;                     // [2 NQ][GY][GX]
@@ -129,7 +138,7 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
 
     const int ntx = (m.nx + TX - 1) / TX;
     const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
-    const int tid = threadIdx.x, ti = tid % TX, tj = tid / TX;
+    const int tid = threadIdx.x;
     const int64_t np = m.npad, pitch = m.pitch;
     const CoefR<R> k(c);
     const R hx = R(m.dx), hy = R(m.dy);
@@ -147,48 +156,67 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         }
         return gi + pitch * gj;
     };
-    auto stage = [&](int64_t gc, R &rho, R &ux, R &uy, R fe[NQ], double &w0, double &w1, double &w2) {
-        w0 = Wn[gc]; w1 = Wn[np + gc]; w2 = Wn[2 * np + gc];
+    auto macro = [&](double w0, double w1, double w2, R &rho, R &ux, R &uy) {
         rho = from_f64<R>(w0);
         if constexpr (P == P_FP64) vel_of<R>(w0, w1, w2, ux, uy);
         else vel_of<R>(rho, from_f64<R>(w1), from_f64<R>(w2), ux, uy);
-        feq9f<R>(rho, ux, uy, fe);
     };
 
-    // ---- phase 1: fbar+ = a f^n + b feq(W^n): own cell (kept in registers), then the
-    // rest of the staged area (the two-cell ring, and block positions without an own
-    // cell: past the grid edge, holding wrapped cells on periodic sides)
+    // ---- phase 1: fbar+ = a f^n + b feq(W^n) of every staged position, one round.
+    // Threads 0..NT-1 take the block (their own cell, kept in registers), the others
+    // the two-cell ring.
+    const bool cell_thread = tid < S::NT;
+    const int ti = tid % TX, tj = tid / TX;
     const int gi = x0 + ti, gj = y0 + tj;
-    const bool active = gi < m.nx && gj < m.ny;
+    const bool active = cell_thread && gi < m.nx && gj < m.ny;
     const int64_t g = (int64_t)gi + pitch * gj;
     const int lme = (tj + 2) * S::LX + (ti + 2);
-    R fn[NQ], feqn[NQ];
+    R fn[NQ];
     R rho_n = R(1), ux_n = R(0), uy_n = R(0);
     double w0n = 1.0, w1n = 0.0, w2n = 0.0;
-    if (active) {
-        stage(g, rho_n, ux_n, uy_n, feqn, w0n, w1n, w2n);
-#pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            fn[a] = SP::dec(fin[a * np + g], feqn[a], a);
-            s_fbp[a * LXY + lme] = k.a * fn[a] + k.b * feqn[a];
+    {
+        int64_t gs = -1;
+        int ls = 0;
+        if (cell_thread) {
+            ls = lme;
+            gs = active ? g : cell_of(ti, tj);          // past the grid edge: a wrapped cell or none
+        } else if (tid < LXY) {
+            // ring position r: two rows below, two above, then two columns left and right
+            const int r = tid - S::NT;
+            int li, lj;
+            if (r < 2 * S::LX) { li = r % S::LX; lj = r / S::LX; }
+            else if (r < 4 * S::LX) { li = (r - 2 * S::LX) % S::LX; lj = S::LY - 2 + (r - 2 * S::LX) / S::LX; }
+            else { const int q = r - 4 * S::LX; lj = 2 + q / 4; const int cc = q % 4; li = cc < 2 ? cc : S::LX - 4 + cc; }
+            ls = lj * S::LX + li;
+            gs = cell_of(li - 2, lj - 2);
         }
-    }
-    for (int q = tid; q < LXY; q += S::NT) {
-        const int bi = q % S::LX - 2, bj = q / S::LX - 2;
-        if (bi >= 0 && bi < TX && bj >= 0 && bj < TY && x0 + bi < m.nx && y0 + bj < m.ny) continue;
-        const int64_t gh = cell_of(bi, bj);
-        if (gh < 0) continue;
-        R rho, ux, uy, fe[NQ];
-        double a0, a1, a2;
-        stage(gh, rho, ux, uy, fe, a0, a1, a2);
+        if (gs >= 0) {
+            double a0 = Wn[gs], a1 = Wn[np + gs], a2 = Wn[2 * np + gs];
+            R rho, ux, uy, fe[NQ], fv[NQ];
 #pragma unroll
-        for (int a = 0; a < NQ; a++) s_fbp[a * LXY + q] = k.a * SP::dec(fin[a * np + gh], fe[a], a) + k.b * fe[a];
+            for (int a = 0; a < NQ; a++) fv[a] = SP::dec(fin[a * np + gs], R(0), a);
+            macro(a0, a1, a2, rho, ux, uy);
+            feq9f<R>(rho, ux, uy, fe);
+#pragma unroll
+            for (int a = 0; a < NQ; a++) {
+                if constexpr (P == P_BF16DEV) fv[a] += fe[a];       // decode the deviation
+                s_fbp[a * LXY + ls] = k.a * fv[a] + k.b * fe[a];
+            }
+            if (active) {
+#pragma unroll
+                for (int a = 0; a < NQ; a++) fn[a] = fv[a];
+                rho_n = rho; ux_n = ux; uy_n = uy;
+                w0n = a0; w1n = a1; w2n = a2;
+            }
+        }
     }
     __syncthreads();
 
-    // ---- phase 2: gradient on the block and its first ring.  LLSR over the existing
-    // face neighbours of a uniform grid: sigma_x = sum_k dx_k (phi_k - phi) / sum_k dx_k^2
-    for (int q = tid; q < GXY; q += S::NT) {
+    // ---- phase 2: gradient on the block and its first ring, one item per position and
+    // velocity triple.  LLSR over the existing face neighbours of a uniform grid:
+    // sigma_x = sum_k dx_k (phi_k - phi) / sum_k dx_k^2.
+    for (int it = tid; it < 3 * GXY; it += NTH) {
+        const int q = it % GXY, grp = it / GXY;
         const int bi = q % S::GX - 1, bj = q / S::GX - 1;
         if (cell_of(bi, bj) < 0) continue;
         const int ci = x0 + bi, cj = y0 + bj;
@@ -201,7 +229,8 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         const R cE = hasE ? hx : R(0), cW = hasW ? hx : R(0), cN = hasN ? hy : R(0), cS = hasS ? hy : R(0);
         const int oE = hasE ? 1 : 0, oW = hasW ? -1 : 0, oN = hasN ? S::LX : 0, oS = hasS ? -S::LX : 0;
 #pragma unroll
-        for (int a = 0; a < NQ; a++) {
+        for (int u = 0; u < 3; u++) {
+            const int a = 3 * grp + u;
             const R *f = s_fbp + a * LXY;
             const R p = f[l];
             const R bx = cE * (f[l + oE] - p) - cW * (f[l + oW] - p);
@@ -212,21 +241,21 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     }
     __syncthreads();
 
-    // ---- phase 3: interior faces of the block, each once
-    for (int q = tid; q < S::NFX + S::NFY; q += S::NT) {
-        if (q < S::NFX) {
-            // face of constant x between block columns fi-1 (L) and fi (R), row fj
-            const int fi = q % (TX + 1), fj = q / (TX + 1);
-            if (cell_of(fi - 1, fj) < 0 || cell_of(fi, fj) < 0) continue;   // boundary or outside
+    // ---- phase 3: every interior face of the block once, one per thread
+    if (tid < S::NFX) {
+        // face of constant x between block columns fi-1 (L) and fi (R), row fj
+        const int fi = tid % (TX + 1), fj = tid / (TX + 1);
+        if (cell_of(fi - 1, fj) >= 0 && cell_of(fi, fj) >= 0) {
             const int lL = (fj + 2) * S::LX + (fi + 1), gL = (fj + 1) * S::GX + fi;
             R fl[6];
             cart_interior_face<0, R>(fl, s_fbp, s_sig, lL, lL + 1, gL, gL + 1, k, hx, hy, LXY, GXY);
 #pragma unroll
-            for (int r = 0; r < 6; r++) s_fx[r * S::NFX + q] = fl[r];
-        } else {
-            // face of constant y between block rows fj-1 (below) and fj (above), column fi
-            const int qq = q - S::NFX, fi = qq % TX, fj = qq / TX;
-            if (cell_of(fi, fj - 1) < 0 || cell_of(fi, fj) < 0) continue;
+            for (int r = 0; r < 6; r++) s_fx[r * S::NFX + tid] = fl[r];
+        }
+    } else if (tid < S::NFX + S::NFY) {
+        // face of constant y between block rows fj-1 (below) and fj (above), column fi
+        const int qq = tid - S::NFX, fi = qq % TX, fj = qq / TX;
+        if (cell_of(fi, fj - 1) >= 0 && cell_of(fi, fj) >= 0) {
             const int lB = (fj + 1) * S::LX + (fi + 2), gB = fj * S::GX + (fi + 1);
             R fl[6];
             cart_interior_face<1, R>(fl, s_fbp, s_sig, lB, lB + S::LX, gB, gB + S::GX, k, hx, hy, LXY, GXY);
@@ -245,6 +274,8 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
     const bool inW = m.periodic_x || gi - 1 >= 0, inE = m.periodic_x || gi + 1 < m.nx;
     const bool inS = m.periodic_y || gj - 1 >= 0, inN = m.periodic_y || gj + 1 < m.ny;
+    R feqn[NQ];
+    if (!(inW && inE && inS && inN)) feq9f<R>(rho_n, ux_n, uy_n, feqn);   // boundary cells only
     if (inW) {
 #pragma unroll
         for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
@@ -317,7 +348,7 @@ cudaError_t launch_cart_p(const CartMesh &m, const Coefs &c, const void *fin, vo
 {
     using T = typename Store<P>::T;
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
-    k_step_cart<P, TX, TY><<<ntx * nty, TX * TY, cart_smem<P, TX, TY>(), st>>>(
+    k_step_cart<P, TX, TY><<<ntx * nty, cart_threads<TX, TY>(), cart_smem<P, TX, TY>(), st>>>(
         m, c, static_cast<const T *>(fin), static_cast<T *>(fout), Wn, Wout);
     return cudaGetLastError();
 }
