@@ -1,0 +1,40 @@
+"""Profiling driver: N separate step launches (no graph) of one case.
+
+    python -m paper_2007_07347_gb300.profile_step CASE [PRECISION] [STEPS] [TILE]
+
+CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh).  Used
+under ncu with ``-k regex:k_step`` to capture single step launches.
+"""
+import sys
+
+import numpy as np
+import torch
+
+from . import meshes as M
+from . import sdugks as S
+
+CASES = {
+    "cavity128": lambda: M.cavity(128),
+    "cavity256": lambda: M.cavity(256),
+    "cavity1024": lambda: M.cavity(1024),
+    "cylinder": lambda: M.cylinder(512, 256),
+}
+
+
+def main(argv):
+    name = argv[1] if len(argv) > 1 else "cavity256"
+    prec = argv[2] if len(argv) > 2 else "fp32"
+    nsteps = int(argv[3]) if len(argv) > 3 else 10
+    tile = int(argv[4]) if len(argv) > 4 else 0
+    case = CASES[name]()
+    torch.cuda.set_device(0)
+    s = S.Solver.from_case(case, prec, graph_steps=-1, tile_cells=tile)
+    u = None if case.u0 == (0.0, 0.0) else np.tile(case.u0, (case.mesh.n_cells, 1))
+    s.init(None, u)
+    s.step(nsteps)
+    torch.cuda.synchronize()
+    print("info", s.info())
+
+
+if __name__ == "__main__":
+    main(sys.argv)
