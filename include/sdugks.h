@@ -44,6 +44,7 @@ extern "C" {
 #define SDUGKS_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
 #define SDUGKS_ERR_CUDA (-7)         /* any other CUDA runtime error (message has the name) */
 #define SDUGKS_ERR_STATE (-8)        /* call out of order, e.g. step before init */
+#define SDUGKS_ERR_FULL (-9)         /* a batch has no room (device memory or instance slots) */
 
 /* ---- boundary kinds (Sec. III) ------------------------------------------------- */
 #define SDUGKS_BC_UNSET 0
@@ -197,6 +198,74 @@ int sdugks_residual_noalloc(int64_t n, const double *d_W, const double *d_vol, d
                             void *stream);
 
 int sdugks_solver_info(const sdugks_solver *s, sdugks_info *out);
+
+/* ---- batched solves ----------------------------------------------------------- */
+/* Many independent uniform-grid solves (cavities, channels) of different sizes and
+ * Reynolds numbers advanced together: every step is one launch of a fixed grid of
+ * CTAs walking the (instance, 16x16 block) work list of all instances, with the
+ * S-DUGKS update of Sec. II per block; steps replay a captured CUDA graph.  Each
+ * instance's arithmetic is the same as a single solver's Cartesian kernel on the
+ * same mesh, so its results do not depend on what else is in the batch.  Instances
+ * are admitted while the batch's device pool has room for their state (admission
+ * by device-memory footprint) and can be removed at any step boundary, which frees
+ * their memory for new ones (continuous batching). */
+typedef struct sdugks_batch sdugks_batch;
+
+typedef struct sdugks_batch_status {
+    int64_t instances;       /* active instances                                    */
+    int64_t cells;           /* cells over active instances                         */
+    int64_t items;           /* (instance, block) work items per step               */
+    int64_t pool_bytes;      /* device pool size                                    */
+    int64_t pool_used;       /* bytes held by active instances                      */
+    int64_t steps;           /* batch steps since creation                          */
+    int32_t grid;            /* CTAs per step launch                                */
+    int32_t ctas_per_sm;     /* resident CTAs per SM of the batched kernel          */
+    int32_t graph_steps;     /* steps per captured graph                            */
+    int32_t precision;
+} sdugks_batch_status;
+
+/* Create a batch with a device pool of pool_bytes and room for max_instances
+ * instances.  precision: SDUGKS_FP32 or SDUGKS_FP32_BF16DEV.  stream as for
+ * solvers.  Errors: INVALID_ARG, OOM, CUDA. */
+int sdugks_batch_create(int64_t pool_bytes, int32_t precision, int32_t max_instances, void *stream,
+                        sdugks_batch **out);
+
+/* Bytes of pool an instance on this mesh would take (state f, W and the residual
+ * snapshot, padded).  INVALID_ARG if the mesh is not a uniform Cartesian grid. */
+int sdugks_batch_footprint(const sdugks_batch *b, const sdugks_mesh *mesh, int64_t *bytes);
+
+/* Admit a solve on a uniform Cartesian grid (sides: walls, moving walls, far field,
+ * outlet or periodic pairs) with relaxation time tau and time step dt, started from
+ * rho[nx*ny], u[nx*ny][2] (host, cell order of the mesh; NULL = 1 and 0).  *id is
+ * its handle.  FULL when the pool or the instance table has no room; INVALID_ARG if
+ * the mesh is not a uniform grid.  The residual snapshot is taken at admission. */
+int sdugks_batch_add(sdugks_batch *b, const sdugks_mesh *mesh, double tau, double dt, const double *rho,
+                     const double *u, int64_t *id);
+
+/* Remove an instance (its memory returns to the pool).  INVALID_ARG for an unknown id. */
+int sdugks_batch_remove(sdugks_batch *b, int64_t id);
+
+/* Advance every active instance by n steps (async). */
+int sdugks_batch_step(sdugks_batch *b, int64_t n);
+
+/* Residual and mass of every active instance against its snapshot, which is then
+ * refreshed (as sdugks_residual).  ids, eps, mass: host arrays of at least
+ * max_instances entries (any may be NULL); *count = active instances.  Steps taken
+ * by instance ids[k] since admission go to steps[k] if steps is not NULL.
+ * Synchronises.  Non-finite states are reported as eps = NaN (no error). */
+int sdugks_batch_residual(sdugks_batch *b, int64_t *ids, double *eps, double *mass, int64_t *steps, int64_t *count);
+
+/* rho[nx*ny], u[nx*ny][2] of one instance (host; synchronises). */
+int sdugks_batch_get_macros(sdugks_batch *b, int64_t id, double *rho, double *u);
+
+/* Time `steps` steps at each candidate grid (1, 2 and 4 times the resident CTAs
+ * per step) and keep the fastest (see sdugks_batch_status.grid).  Call with instances
+ * admitted. */
+int sdugks_batch_autotune(sdugks_batch *b, int64_t steps);
+
+int sdugks_batch_info(const sdugks_batch *b, sdugks_batch_status *out);
+
+void sdugks_batch_destroy(sdugks_batch *b);
 
 void sdugks_solver_destroy(sdugks_solver *s);
 

@@ -28,6 +28,7 @@ CU_UNITS = {
     "k_cart.cu": [],
     "k_util.cu": [],
     "k_residual_noalloc.cu": [],
+    "k_batch.cu": [],
 }
 CXX_UNITS = ["sdugks_host.cpp"]
 HEADERS = ["sdugks_internal.h", "d2q9.cuh", "step_tiled.cuh", "step_cart.cuh"]

@@ -1,0 +1,175 @@
+// k_batch.cu -- batched uniform-grid solves: the fused step over an (instance,
+// block) work list, the per-instance residual/mass reduction, and per-instance state
+// set-up and read-out.
+#include "step_cart.cuh"
+
+namespace sdugks {
+
+namespace {
+
+constexpr int BTX = 16, BTY = 16;
+constexpr int RT = 256;                    // residual block = one 16x16 block of cells
+
+template <int P> cudaError_t prep_p() {
+    return cudaFuncSetAttribute(k_step_batch<P, BTX, BTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cart_smem<P, BTX, BTY>());
+}
+
+template <int P> int occ_p() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<P, BTX, BTY>, cart_threads<BTX, BTY>(),
+                                                      cart_smem<P, BTX, BTY>()) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+__device__ void bsum4(double v[4], double *out)
+{
+    __shared__ double sh[RT / 32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < 4; k++) sh[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            double x = lane < RT / 32 ? sh[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) out[k] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// per item: sums over the block's cells of (U-U0)^2+(V-V0)^2, U0^2+V0^2, V rho and
+// non-finite W; refreshes the snapshot
+__global__ void __launch_bounds__(RT) k_bresid_partial(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
+                                                       const int *__restrict__ n_items, int par,
+                                                       double *__restrict__ partial)
+{
+    const int n = *n_items;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int2 it = items[w];
+        const CartInst &m = insts[it.x];
+        const int ntx = (m.nx + BTX - 1) / BTX;
+        const int i = (it.y % ntx) * BTX + threadIdx.x % BTX, j = (it.y / ntx) * BTY + threadIdx.x / BTX;
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (i < m.nx && j < m.ny) {
+            const int64_t g = i + (int64_t)m.pitch * j, np = m.npad;
+            const double *W = m.W[par];
+            const double w0 = W[g], w1 = W[np + g], w2 = W[2 * np + g];
+            const double U = w1 / w0, V = w2 / w0, U0 = m.snap[g], V0 = m.snap[np + g];
+            v[0] = (U - U0) * (U - U0) + (V - V0) * (V - V0);
+            v[1] = U0 * U0 + V0 * V0;
+            v[2] = m.dx * m.dy * w0;
+            v[3] = (isfinite(w0) && isfinite(w1) && isfinite(w2) && w0 != 0.0) ? 0.0 : 1.0;
+            m.snap[g] = U;
+            m.snap[np + g] = V;
+        }
+        bsum4(v, partial + 4 * (int64_t)w);
+    }
+}
+
+// one block per instance: fixed-order sum of its items' partials
+__global__ void __launch_bounds__(RT) k_bresid_final(const CartInst *__restrict__ insts, int n_inst,
+                                                     const double *__restrict__ partial, double *__restrict__ out)
+{
+    for (int q = blockIdx.x; q < n_inst; q += gridDim.x) {
+        const CartInst &m = insts[q];
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (m.n_items > 0)
+            for (int w = threadIdx.x; w < m.n_items; w += RT)
+                for (int k = 0; k < 4; k++) v[k] += partial[4 * (int64_t)(m.item0 + w) + k];
+        bsum4(v, out + 4 * (int64_t)q);
+    }
+}
+
+template <int P>
+__global__ void k_binit(const CartInst *__restrict__ mp, int par, const double *__restrict__ rho,
+                        const double *__restrict__ u)
+{
+    using R = typename Store<P>::R;
+    using T = typename Store<P>::T;
+    const CartInst &m = *mp;
+    const int64_t n = (int64_t)m.nx * m.ny, np = m.npad;
+    T *f = static_cast<T *>(m.f[par]);
+    double *W = m.W[par];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = q % m.nx + (int64_t)m.pitch * (q / m.nx);
+        const double r = rho ? rho[q] : 1.0, ux = u ? u[2 * q] : 0.0, uy = u ? u[2 * q + 1] : 0.0;
+        W[g] = r; W[np + g] = r * ux; W[2 * np + g] = r * uy;
+        m.snap[g] = ux; m.snap[np + g] = uy;
+        double fe[NQ];
+        feq9<double>(r, ux, uy, fe);
+        R rr, x, y, feR[NQ];
+        macro_of<R>(r, r * ux, r * uy, rr, x, y);
+        feq9f<R>(rr, x, y, feR);
+#pragma unroll
+        for (int a = 0; a < NQ; a++) f[a * np + g] = Store<P>::enc(R(fe[a]), feR[a], a);
+    }
+}
+
+__global__ void k_bmacros(const CartInst *__restrict__ mp, int par, double *__restrict__ rho, double *__restrict__ u)
+{
+    const CartInst &m = *mp;
+    const int64_t n = (int64_t)m.nx * m.ny, np = m.npad;
+    const double *W = m.W[par];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = q % m.nx + (int64_t)m.pitch * (q / m.nx);
+        const double w0 = W[g];
+        if (rho) rho[q] = w0;
+        if (u) { u[2 * q] = W[np + g] / w0; u[2 * q + 1] = W[2 * np + g] / w0; }
+    }
+}
+
+int grid_of(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 2048 ? 2048 : b)); }
+
+}  // namespace
+
+cudaError_t prepare_batch(int prec)
+{
+    return prec == P_BF16DEV ? prep_p<P_BF16DEV>() : prep_p<P_FP32>();
+}
+
+int batch_ctas_per_sm(int prec) { return prec == P_BF16DEV ? occ_p<P_BF16DEV>() : occ_p<P_FP32>(); }
+
+cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,
+                              int parity, cudaStream_t st)
+{
+    if (prec == P_BF16DEV)
+        k_step_batch<P_BF16DEV, BTX, BTY><<<grid, cart_threads<BTX, BTY>(), cart_smem<P_BF16DEV, BTX, BTY>(), st>>>(
+            insts, items, n_items, parity);
+    else
+        k_step_batch<P_FP32, BTX, BTY><<<grid, cart_threads<BTX, BTY>(), cart_smem<P_FP32, BTX, BTY>(), st>>>(
+            insts, items, n_items, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_residual(const CartInst *insts, int n_inst, const int2 *items, const int *n_items, int grid,
+                                  int parity, double *partial, double *out, cudaStream_t st)
+{
+    k_bresid_partial<<<grid, RT, 0, st>>>(insts, items, n_items, parity, partial);
+    if (n_inst > 0) k_bresid_final<<<n_inst < 1024 ? n_inst : 1024, RT, 0, st>>>(insts, n_inst, partial, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init(int prec, const CartInst *inst_host, const CartInst *inst_dev, int parity,
+                              const double *rho, const double *u, cudaStream_t st)
+{
+    const int g = grid_of((int64_t)inst_host->nx * inst_host->ny);
+    if (prec == P_BF16DEV) k_binit<P_BF16DEV><<<g, 256, 0, st>>>(inst_dev, parity, rho, u);
+    else k_binit<P_FP32><<<g, 256, 0, st>>>(inst_dev, parity, rho, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_macros(const CartInst *inst_host, const CartInst *inst_dev, int parity, double *rho, double *u,
+                                cudaStream_t st)
+{
+    k_bmacros<<<grid_of((int64_t)inst_host->nx * inst_host->ny), 256, 0, st>>>(inst_dev, parity, rho, u);
+    return cudaGetLastError();
+}
+
+}  // namespace sdugks

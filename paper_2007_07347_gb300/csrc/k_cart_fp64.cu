@@ -5,10 +5,9 @@ namespace sdugks {
 
 cudaError_t prepare_cart_fp64() { return prepare_cart_p<P_FP64, 16, 16>(); }
 
-cudaError_t launch_cart_fp64(const CartMesh &m, const Coefs &c, const void *f_in, void *f_out, const double *W_in,
-                             double *W_out, cudaStream_t st)
+cudaError_t launch_cart_fp64(const CartInst &m, int parity, cudaStream_t st)
 {
-    return launch_cart_p<P_FP64, 16, 16>(m, c, f_in, f_out, W_in, W_out, st);
+    return launch_cart_p<P_FP64, 16, 16>(m, parity, st);
 }
 
 }  // namespace sdugks

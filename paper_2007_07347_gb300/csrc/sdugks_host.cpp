@@ -364,7 +364,7 @@ struct sdugks_solver {
     size_t dbytes = 0;
     int32_t *perm = nullptr;        // q-th listed cell -> user id
     int32_t *loc = nullptr;         // q-th listed cell -> internal offset (nullptr: q)
-    CartMesh cm{};
+    CartInst ci{};
     double *vol = nullptr, *snap = nullptr, *partial = nullptr, *red = nullptr;
     State st{};
     int n_red_blocks = 1;
@@ -389,7 +389,7 @@ static cudaError_t launch_one(sdugks_solver *s, cudaStream_t st)
     const int a = s->cur;
     cudaError_t e;
     if (s->kernel == SDUGKS_KERNEL_CARTESIAN)
-        e = launch_step_cart(s->p.precision, s->cm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
+        e = launch_step_cart(s->p.precision, s->ci, a, st);
     else if (s->p.precision == P_FP64)
         e = launch_step_tiled_fp64(s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
     else
@@ -519,6 +519,34 @@ bool detect_cart(const sdugks_mesh &m, CartGrid &g)
 
 }  // namespace
 
+// Grid, side rules and coefficients of a uniform-grid solve (state pointers are set
+// by the caller).
+static void fill_cart_inst(CartInst &ci, const sdugks_mesh &m, const CartGrid &g, double tau, double dt, int32_t pitch,
+                           int64_t npad)
+{
+    std::memset(&ci, 0, sizeof ci);
+    ci.nx = g.nx; ci.ny = g.ny; ci.pitch = pitch; ci.periodic_x = g.px; ci.periodic_y = g.py;
+    for (int k = 0; k < 4; k++) {
+        const int32_t p = g.side_patch[k];
+        ci.side_kind[k] = m.bc_kind[p];
+        for (int d = 0; d < 3; d++) {
+            ci.side_par[k][d] = m.bc_par[p][d];
+            ci.fside_par[k][d] = (float)m.bc_par[p][d];
+        }
+    }
+    ci.npad = npad;
+    ci.dx = g.dx; ci.dy = g.dy; ci.dtV = dt / (g.dx * g.dy);
+    ci.a = (2.0 * tau - dt) / (2.0 * tau);
+    ci.b = dt / (2.0 * tau);
+    ci.c = 2.0 * tau / (2.0 * tau + dt);
+    ci.r = dt / tau;
+    ci.dt = dt;
+    ci.fdx = (float)ci.dx; ci.fdy = (float)ci.dy; ci.fdtV = (float)ci.dtV;
+    ci.fa = (float)ci.a; ci.fb = (float)ci.b; ci.fc = (float)ci.c; ci.fr = (float)ci.r;
+    ci.finv1r = (float)(1.0 / (1.0 + dt / tau));
+    ci.fdt = (float)dt;
+}
+
 static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_params *prm, void *stream, sdugks_solver **out)
 {
     const int64_t n = m.nc;
@@ -539,13 +567,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     s->halo_cells = (int64_t)s->n_tiles * ((TX + 4) * (TY + 4) - TX * TY);
     s->n_red_blocks = residual_blocks(n);
     s->mesh_bytes = 0.0;
-    CartMesh &cm = s->cm;
-    cm.nx = g.nx; cm.ny = g.ny; cm.pitch = pitch; cm.periodic_x = g.px; cm.periodic_y = g.py;
-    for (int k = 0; k < 4; k++) cm.side_patch[k] = g.side_patch[k];
-    cm.npad = npad; cm.dx = g.dx; cm.dy = g.dy;
-    cm.dtV = prm->dt / (g.dx * g.dy);
-    cm.fdtV = (float)cm.dtV;
-
+    fill_cart_inst(s->ci, m, g, prm->tau, prm->dt, pitch, npad);
     auto layout = [&](Arena &A) {
         s->perm = A.take<int32_t>(n);
         s->loc = A.take<int32_t>(n);
@@ -568,6 +590,8 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     }
     Arena A{s->dmem, 0, s->dbytes};
     layout(A);
+    for (int b = 0; b < 2; b++) { s->ci.f[b] = s->st.f[b]; s->ci.W[b] = s->st.W[b]; }
+    s->ci.snap = s->snap;
     std::vector<int32_t> perm(n), loc(n);
     std::vector<double> vol(npad, 1.0);
     for (int64_t c = 0; c < n; c++) {
@@ -1059,8 +1083,8 @@ extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
     o->kernel = s->kernel;
     o->precision = s->p.precision;
     o->tile_cells = s->kernel == SDUGKS_KERNEL_CARTESIAN ? 256 : (s->p.tile_cells ? s->p.tile_cells : TILE_MAX);
-    o->nx = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->cm.nx : 0;
-    o->ny = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->cm.ny : 0;
+    o->nx = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.nx : 0;
+    o->ny = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.ny : 0;
     return SDUGKS_OK;
 }
 
@@ -1079,3 +1103,411 @@ extern "C" void sdugks_solver_destroy(sdugks_solver *s)
 extern "C" const char *sdugks_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char *sdugks_version(void) { return "sdugks 0.1 sm_103a"; }
+
+// ------------------------------------------------------------------ batched solves
+
+namespace {
+
+// First-fit allocator over [0, cap) in 256-byte units, with coalescing on free.
+class PoolAlloc {
+  public:
+    explicit PoolAlloc(size_t cap = 0) { reset(cap); }
+    void reset(size_t cap) { free_.clear(); if (cap) free_.push_back({0, cap}); cap_ = cap; used_ = 0; }
+    bool alloc(size_t bytes, size_t &off) {
+        bytes = (bytes + 255) & ~size_t(255);
+        for (size_t k = 0; k < free_.size(); k++) {
+            if (free_[k].second < bytes) continue;
+            off = free_[k].first;
+            free_[k].first += bytes;
+            free_[k].second -= bytes;
+            if (free_[k].second == 0) free_.erase(free_.begin() + k);
+            used_ += bytes;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        auto it = std::lower_bound(free_.begin(), free_.end(), std::make_pair(off, size_t(0)));
+        it = free_.insert(it, {off, bytes});
+        // merge with the next and the previous block
+        if (it + 1 != free_.end() && it->first + it->second == (it + 1)->first) {
+            it->second += (it + 1)->second;
+            free_.erase(it + 1);
+        }
+        if (it != free_.begin() && (it - 1)->first + (it - 1)->second == it->first) {
+            (it - 1)->second += it->second;
+            free_.erase(it);
+        }
+        used_ -= bytes;
+    }
+    size_t used() const { return used_; }
+    size_t cap() const { return cap_; }
+
+  private:
+    std::vector<std::pair<size_t, size_t>> free_;   // (offset, size), sorted by offset
+    size_t cap_ = 0, used_ = 0;
+};
+
+struct BatchInst {
+    int64_t id;
+    CartInst ci;
+    size_t off, bytes;
+    int64_t admitted_at;            // batch step at admission
+    int64_t ntiles;
+    std::vector<int64_t> lattice;   // caller's cell c -> lattice position i + nx j
+};
+
+int64_t cart_npad(int32_t pitch, int32_t ny) { return ((int64_t)pitch * ny + 31) / 32 * 32; }
+
+size_t inst_bytes(int prec, int64_t npad)
+{
+    const size_t fs = prec == P_BF16DEV ? 2 : 4;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    return 2 * up(NQ * npad * fs) + 2 * up(3 * npad * 8) + up(2 * npad * 8);
+}
+
+}  // namespace
+
+struct sdugks_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int32_t prec = P_FP32;
+    int32_t max_inst = 0;
+    char *pool = nullptr;
+    PoolAlloc alloc;
+    std::vector<BatchInst> inst;        // active instances, in work-list order
+    int64_t next_id = 1;
+    int64_t steps = 0;
+    int cur = 0;
+    // device tables (fixed addresses, sized for max_inst and max_items)
+    CartInst *d_inst = nullptr;
+    int2 *d_items = nullptr;
+    int *d_nitems = nullptr;
+    double *d_partial = nullptr, *d_out = nullptr;
+    double *h_out = nullptr;            // pinned [max_inst][4]
+    double *d_stage = nullptr;          // [max_cells_one][3] staging for add/get
+    int64_t stage_cells = 0;
+    int64_t max_items = 0, n_items = 0;
+    int grid = 0, ctas_per_sm = 1, n_sm = 1;
+    int graph_steps = 64;
+    cudaGraphExec_t graph = nullptr;
+};
+
+static int batch_upload_tables(sdugks_batch *b)
+{
+    std::vector<CartInst> h;
+    std::vector<int2> items;
+    h.reserve(b->inst.size());
+    for (size_t q = 0; q < b->inst.size(); q++) {
+        CartInst ci = b->inst[q].ci;
+        ci.item0 = (int32_t)items.size();
+        ci.n_items = (int32_t)b->inst[q].ntiles;
+        for (int64_t t = 0; t < b->inst[q].ntiles; t++) items.push_back(make_int2((int)q, (int)t));
+        b->inst[q].ci.item0 = ci.item0;
+        b->inst[q].ci.n_items = ci.n_items;
+        h.push_back(ci);
+    }
+    if ((int64_t)items.size() > b->max_items) return fail(SDUGKS_ERR_FULL, "batch work list full");
+    b->n_items = (int64_t)items.size();
+    const int ni = (int)b->n_items;
+    if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(b->d_inst, h.data(), h.size() * sizeof(CartInst), cudaMemcpyHostToDevice, b->stream));
+    if (!items.empty()) CUDA_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(b->d_nitems, &ni, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));   // the host vectors go out of scope
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_create(int64_t pool_bytes, int32_t precision, int32_t max_instances, void *stream,
+                                   sdugks_batch **out)
+{
+    if (!out) return fail(SDUGKS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (pool_bytes <= 0 || max_instances <= 0 || max_instances > (1 << 20))
+        return fail(SDUGKS_ERR_INVALID_ARG, "pool_bytes must be > 0 and max_instances in [1, 2^20]");
+    if (precision != SDUGKS_FP32 && precision != SDUGKS_FP32_BF16DEV)
+        return fail(SDUGKS_ERR_INVALID_ARG, "batches run in FP32 or FP32_BF16DEV");
+    sdugks_batch *b = new (std::nothrow) sdugks_batch;
+    if (!b) return fail(SDUGKS_ERR_OOM, "host allocation failed");
+    b->prec = precision;
+    b->max_inst = max_instances;
+    b->stream = static_cast<cudaStream_t>(stream);
+    // the work list can hold one item per 64 pool cells plus one per instance
+    b->max_items = pool_bytes / (64 * 100) + max_instances + 1024;
+    auto cleanup = [&](int rc) { sdugks_batch_destroy(b); return rc; };
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMalloc(&b->pool, (size_t)pool_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(CartInst) * (size_t)max_instances);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * (size_t)b->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_nitems, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_partial, sizeof(double) * 4 * (size_t)b->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_out, sizeof(double) * 4 * (size_t)max_instances);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, sizeof(double) * 4 * (size_t)max_instances);
+    if (e == cudaSuccess) e = cudaMemset(b->d_nitems, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = prepare_batch(precision);
+    if (e != cudaSuccess)
+        return cleanup(fail(e == cudaErrorMemoryAllocation ? SDUGKS_ERR_OOM : SDUGKS_ERR_CUDA, "batch create: %s",
+                            cudaGetErrorString(e)));
+    b->alloc.reset((size_t)pool_bytes);
+    b->ctas_per_sm = batch_ctas_per_sm(precision);
+    b->grid = b->n_sm * b->ctas_per_sm;
+    *out = b;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_footprint(const sdugks_batch *b, const sdugks_mesh *m, int64_t *bytes)
+{
+    if (!b || !m || !bytes) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    CartGrid g;
+    if (!detect_cart(*m, g)) return fail(SDUGKS_ERR_INVALID_ARG, "not a uniform Cartesian grid: %s", g.why.c_str());
+    const int32_t pitch = (g.nx + 31) / 32 * 32;
+    *bytes = (int64_t)inst_bytes(b->prec, cart_npad(pitch, g.ny));
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_add(sdugks_batch *b, const sdugks_mesh *m, double tau, double dt, const double *rho,
+                                const double *u, int64_t *id)
+{
+    if (!b || !m || !id) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    if (!(tau > 0) || !(dt > 0) || !std::isfinite(tau) || !std::isfinite(dt))
+        return fail(SDUGKS_ERR_INVALID_ARG, "tau and dt must be finite and > 0");
+    Faces F;
+    int rc = merge_periodic(*m, F);       // boundary table checks
+    if (rc) return rc;
+    CartGrid g;
+    if (!detect_cart(*m, g)) return fail(SDUGKS_ERR_INVALID_ARG, "not a uniform Cartesian grid: %s", g.why.c_str());
+    if ((int32_t)b->inst.size() >= b->max_inst) return fail(SDUGKS_ERR_FULL, "batch instance table full");
+    const int32_t pitch = (g.nx + 31) / 32 * 32;
+    const int64_t npad = cart_npad(pitch, g.ny);
+    const size_t bytes = inst_bytes(b->prec, npad);
+    size_t off = 0;
+    if (!b->alloc.alloc(bytes, off)) return fail(SDUGKS_ERR_FULL, "batch pool has no room for %zu bytes", bytes);
+    CUDA_TRY(cudaSetDevice(b->device));
+    BatchInst bi;
+    bi.id = b->next_id++;
+    bi.off = off;
+    bi.bytes = bytes;
+    bi.admitted_at = b->steps;
+    bi.ntiles = (int64_t)((g.nx + 15) / 16) * ((g.ny + 15) / 16);
+    fill_cart_inst(bi.ci, *m, g, tau, dt, pitch, npad);
+    {
+        auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+        const size_t fs = b->prec == P_BF16DEV ? 2 : 4;
+        char *p = b->pool + off;
+        for (int k = 0; k < 2; k++) { bi.ci.f[k] = p; p += up(NQ * npad * fs); }
+        for (int k = 0; k < 2; k++) { bi.ci.W[k] = reinterpret_cast<double *>(p); p += up(3 * npad * 8); }
+        bi.ci.snap = reinterpret_cast<double *>(p);
+    }
+    // initial state into the current buffer, through a staging slot of the instance table
+    const int64_t n = (int64_t)g.nx * g.ny;
+    if (b->stage_cells < n) {
+        if (b->d_stage) cudaFree(b->d_stage);
+        b->d_stage = nullptr;
+        b->stage_cells = 0;
+        cudaError_t e = cudaMalloc(&b->d_stage, sizeof(double) * 3 * (size_t)n);
+        if (e != cudaSuccess) { b->alloc.release(off, bytes); return fail(SDUGKS_ERR_OOM, "batch staging: %s", cudaGetErrorString(e)); }
+        b->stage_cells = n;
+    }
+    // user cell c -> lattice position; the staging arrays are in lattice order i + nx j
+    bi.lattice.resize(n);
+    for (int64_t c = 0; c < n; c++) bi.lattice[c] = g.ci[c] + (int64_t)g.nx * g.cj[c];
+    std::vector<double> r_l, u_l;
+    if (rho || u) {
+        r_l.assign(n, 1.0);
+        u_l.assign(2 * n, 0.0);
+        for (int64_t c = 0; c < n; c++) {
+            const int64_t q = bi.lattice[c];
+            if (rho) r_l[q] = rho[c];
+            if (u) { u_l[2 * q] = u[2 * c]; u_l[2 * q + 1] = u[2 * c + 1]; }
+        }
+    }
+    CartInst *slot = b->d_inst + b->inst.size();        // the new instance's table entry
+    CUDA_TRY(cudaMemcpyAsync(slot, &bi.ci, sizeof(CartInst), cudaMemcpyHostToDevice, b->stream));
+    double *dr = nullptr, *du = nullptr;
+    if (rho) { dr = b->d_stage; CUDA_TRY(cudaMemcpyAsync(dr, r_l.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream)); }
+    if (u) { du = b->d_stage + n; CUDA_TRY(cudaMemcpyAsync(du, u_l.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice, b->stream)); }
+    CUDA_TRY(launch_batch_init(b->prec, &bi.ci, slot, b->cur, dr, du, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->inst.push_back(std::move(bi));
+    rc = batch_upload_tables(b);
+    if (rc) { b->inst.pop_back(); b->alloc.release(off, bytes); return rc; }
+    *id = b->inst.back().id;
+    return SDUGKS_OK;
+}
+
+static int batch_find(const sdugks_batch *b, int64_t id)
+{
+    for (size_t q = 0; q < b->inst.size(); q++)
+        if (b->inst[q].id == id) return (int)q;
+    return -1;
+}
+
+extern "C" int sdugks_batch_remove(sdugks_batch *b, int64_t id)
+{
+    if (!b) return fail(SDUGKS_ERR_INVALID_ARG, "batch is NULL");
+    const int q = batch_find(b, id);
+    if (q < 0) return fail(SDUGKS_ERR_INVALID_ARG, "no instance %lld in the batch", (long long)id);
+    CUDA_TRY(cudaSetDevice(b->device));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));        // no step may still read its memory
+    b->alloc.release(b->inst[q].off, b->inst[q].bytes);
+    b->inst.erase(b->inst.begin() + q);
+    return batch_upload_tables(b);
+}
+
+static int batch_ensure_graph(sdugks_batch *b)
+{
+    if (b->graph) return SDUGKS_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->graph_steps && e == cudaSuccess; k++)
+        e = launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, b->grid, k & 1, b->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    CUDA_TRY(e);
+    CUDA_TRY(e2);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_step(sdugks_batch *b, int64_t n)
+{
+    if (!b) return fail(SDUGKS_ERR_INVALID_ARG, "batch is NULL");
+    if (n < 0) return fail(SDUGKS_ERR_INVALID_ARG, "negative step count");
+    CUDA_TRY(cudaSetDevice(b->device));
+    int64_t left = n;
+    if (left >= 2 * b->graph_steps) {
+        if (b->cur != 0) {
+            CUDA_TRY(launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, b->grid, b->cur, b->stream));
+            b->cur ^= 1; b->steps++; left--;
+        }
+        int rc = batch_ensure_graph(b);
+        if (rc) return rc;
+        while (left >= b->graph_steps) {
+            CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+            b->steps += b->graph_steps; left -= b->graph_steps;
+        }
+    }
+    while (left > 0) {
+        CUDA_TRY(launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, b->grid, b->cur, b->stream));
+        b->cur ^= 1; b->steps++; left--;
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_residual(sdugks_batch *b, int64_t *ids, double *eps, double *mass, int64_t *steps,
+                                     int64_t *count)
+{
+    if (!b) return fail(SDUGKS_ERR_INVALID_ARG, "batch is NULL");
+    CUDA_TRY(cudaSetDevice(b->device));
+    const int ni = (int)b->inst.size();
+    if (count) *count = ni;
+    if (ni == 0) return SDUGKS_OK;
+    CUDA_TRY(launch_batch_residual(b->d_inst, ni, b->d_items, b->d_nitems, b->grid, b->cur, b->d_partial, b->d_out,
+                                   b->stream));
+    CUDA_TRY(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * 4 * ni, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (int q = 0; q < ni; q++) {
+        const double *o = b->h_out + 4 * q;
+        if (ids) ids[q] = b->inst[q].id;
+        if (eps) eps[q] = o[3] != 0.0 ? NAN : (o[1] > 0.0 ? std::sqrt(o[0]) / std::sqrt(o[1]) : INFINITY);
+        if (mass) mass[q] = o[2];
+        if (steps) steps[q] = b->steps - b->inst[q].admitted_at;
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_get_macros(sdugks_batch *b, int64_t id, double *rho, double *u)
+{
+    if (!b) return fail(SDUGKS_ERR_INVALID_ARG, "batch is NULL");
+    const int q = batch_find(b, id);
+    if (q < 0) return fail(SDUGKS_ERR_INVALID_ARG, "no instance %lld in the batch", (long long)id);
+    CUDA_TRY(cudaSetDevice(b->device));
+    const CartInst &ci = b->inst[q].ci;
+    const int64_t n = (int64_t)ci.nx * ci.ny;
+    if (b->stage_cells < n) return fail(SDUGKS_ERR_STATE, "internal: staging smaller than an instance");
+    CUDA_TRY(launch_batch_macros(&ci, b->d_inst + q, b->cur, b->d_stage, b->d_stage + n, b->stream));
+    std::vector<double> r(n), v(2 * n);
+    CUDA_TRY(cudaMemcpyAsync(r.data(), b->d_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(v.data(), b->d_stage + n, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    const std::vector<int64_t> &lat = b->inst[q].lattice;       // back to the caller's cell order
+    for (int64_t c = 0; c < n; c++) {
+        if (rho) rho[c] = r[lat[c]];
+        if (u) { u[2 * c] = v[2 * lat[c]]; u[2 * c + 1] = v[2 * lat[c] + 1]; }
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_autotune(sdugks_batch *b, int64_t steps)
+{
+    if (!b || steps <= 0) return fail(SDUGKS_ERR_INVALID_ARG, "bad argument");
+    if (b->inst.empty()) return fail(SDUGKS_ERR_STATE, "autotune needs admitted instances");
+    CUDA_TRY(cudaSetDevice(b->device));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int base = b->n_sm * b->ctas_per_sm;
+    int best = base;
+    float best_ms = 1e30f;
+    for (int mult : {1, 2, 4}) {
+        const int grid = base * mult;
+        // steps in pairs so that the buffer parity is unchanged
+        for (int64_t k = 0; k < 2; k++) launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, (b->cur + k) & 1, b->stream);
+        cudaEventRecord(e0, b->stream);
+        for (int64_t k = 0; k < 2 * steps; k++)
+            launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, (b->cur + k) & 1, b->stream);
+        cudaEventRecord(e1, b->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return fail(SDUGKS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e)); }
+        b->steps += 2 + 2 * steps;
+        if (ms < best_ms) { best_ms = ms; best = grid; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best != b->grid) {
+        b->grid = best;
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_batch_info(const sdugks_batch *b, sdugks_batch_status *o)
+{
+    if (!b || !o) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    std::memset(o, 0, sizeof *o);
+    o->instances = (int64_t)b->inst.size();
+    for (const auto &i : b->inst) o->cells += (int64_t)i.ci.nx * i.ci.ny;
+    o->items = b->n_items;
+    o->pool_bytes = (int64_t)b->alloc.cap();
+    o->pool_used = (int64_t)b->alloc.used();
+    o->steps = b->steps;
+    o->grid = b->grid;
+    o->ctas_per_sm = b->ctas_per_sm;
+    o->graph_steps = b->graph_steps;
+    o->precision = b->prec;
+    return SDUGKS_OK;
+}
+
+extern "C" void sdugks_batch_destroy(sdugks_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->pool);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_items);
+    cudaFree(b->d_nitems);
+    cudaFree(b->d_partial);
+    cudaFree(b->d_out);
+    cudaFree(b->d_stage);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    delete b;
+}

@@ -61,14 +61,23 @@ struct TiledMesh {
     const double *vol;        // [npad] V
 };
 
-// Uniform Cartesian grid of nx x ny rectangles dx x dy: cell (i, j) at i + pitch j.
-struct CartMesh {
-    int32_t nx, ny, pitch;
-    int32_t periodic_x, periodic_y;
-    int32_t side_patch[4];    // patch of the bottom, right, top, left side (unused if periodic)
+// One uniform-grid solve as the Cartesian kernels see it: nx x ny rectangles
+// dx x dy, cell (i, j) at i + pitch j; side boundary rules; step coefficients; and
+// its ping-pong state f[2] ([NQ][npad]), W[2] ([3][npad] FP64).  Buffer p holds
+// t_n when the launch parity is p.
+struct CartInst {
+    int32_t nx, ny, pitch, periodic_x, periodic_y;
+    int32_t side_kind[4];     // BK_* of the bottom, right, top, left side (unused if periodic)
+    int32_t item0, n_items;   // batched runs: this instance's range in the work list
     int64_t npad;             // >= pitch * ny, multiple of 32
     double dx, dy, dtV;       // dtV = dt / (dx dy)
-    float fdtV;
+    double a, b, c, r, dt;    // (2tau-dt)/2tau, dt/2tau, 2tau/(2tau+dt), dt/tau, dt
+    double side_par[4][3];
+    float fdx, fdy, fdtV, fa, fb, fc, fr, finv1r, fdt, fpad_;
+    float fside_par[4][3];
+    void *f[2];
+    double *W[2];
+    double *snap;             // [2][npad] residual snapshot (U0, V0)
 };
 
 // Device state of one solver, ping-pong: f [2][NQ][npad] (element type by
@@ -85,8 +94,19 @@ cudaError_t launch_step_tiled_fp64(const TiledMesh &m, const Coefs &c, const voi
                                    const double *W_in, double *W_out, cudaStream_t st);
 cudaError_t prepare_tiled_fp32(int prec);
 cudaError_t prepare_cart(int prec);
-cudaError_t launch_step_cart(int prec, const CartMesh &m, const Coefs &c, const void *f_in, void *f_out,
-                             const double *W_in, double *W_out, cudaStream_t st);
+cudaError_t launch_step_cart(int prec, const CartInst &m, int parity, cudaStream_t st);
+// batched: every (instance, tile) item of the list, grid-stride over a fixed grid
+cudaError_t prepare_batch(int prec);
+cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,
+                              int parity, cudaStream_t st);
+int batch_ctas_per_sm(int prec);
+// batched residual: partial [max_items][4] per tile, out [n_inst][4] = (num, den, mass, non-finite)
+cudaError_t launch_batch_residual(const CartInst *insts, int n_inst, const int2 *items, const int *n_items, int grid,
+                                  int parity, double *partial, double *out, cudaStream_t st);
+cudaError_t launch_batch_init(int prec, const CartInst *inst_host, const CartInst *inst_dev, int parity,
+                              const double *rho, const double *u, cudaStream_t st);
+cudaError_t launch_batch_macros(const CartInst *inst_host, const CartInst *inst_dev, int parity, double *rho, double *u,
+                                cudaStream_t st);
 cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
                                    const double *W_in, double *W_out, cudaStream_t st);
 

@@ -1,4 +1,4 @@
-// step_cart.cuh -- fused S-DUGKS step on a uniform Cartesian grid.
+// step_cart.cuh -- fused S-DUGKS step on uniform Cartesian grids.
 //
 // The same update as the tiled kernel (Eqs. fbarplus, fbpsource, fbar, Macro, Feq,
 // f_t_n+1, MesoFlux, MacroFlux, MacroUpdate, fn+1), specialised to nx x ny
@@ -6,15 +6,17 @@
 // block, staged with a two-cell halo.  The LLSR gradient reduces to central (or,
 // next to a wall, one-sided) differences, and on every face the upwind side of each
 // velocity is known at compile time.  No mesh arrays are read.  Each grid side is one
-// boundary patch or periodic with the opposite side.
+// boundary rule or periodic with the opposite side.
 //
-// Phases: (1) fbar+ of the block and halo into shared memory; (2) gradients of the
-// block and its first ring; (3) every interior face of the block once, its six
-// non-zero fluxes (xi.n l f_b for the velocities that cross it) into shared memory;
-// (4) per cell: boundary faces, the flux sum, W^{n+1} in FP64 and f^{n+1}.
+// Phases of one block: (1) fbar+ of the block and halo into shared memory, one
+// position per thread; (2) gradients of the block and its first ring, one item per
+// position and velocity triple; (3) every interior face of the block once, one per
+// thread, its six non-zero fluxes (xi.n l f_b of the velocities that cross it) into
+// shared memory; (4) per cell: boundary faces, the flux sum, W^{n+1} in FP64 and
+// f^{n+1}.  `cart_tile` does one block; `k_step_cart` runs it for every block of one
+// grid and `k_step_batch` for every (instance, block) item of a batch.
 #pragma once
 #include "d2q9.cuh"
-#include "step_tiled.cuh"   // CoefR
 
 namespace sdugks {
 
@@ -26,6 +28,14 @@ template <int TX, int TY> struct CartShape {
     static constexpr int NFY = TX * (TY + 1);        // faces of constant y
 };
 
+// Threads per CTA: one per interior face of the block (>= cells, >= staged positions).
+template <int TX, int TY> __host__ __device__ constexpr int cart_threads() {
+    constexpr int nf = CartShape<TX, TY>::NFX + CartShape<TX, TY>::NFY;
+    constexpr int nl = CartShape<TX, TY>::LX * CartShape<TX, TY>::LY;
+    constexpr int m = nf > nl ? nf : nl;
+    return (m + 31) / 32 * 32;
+}
+
 template <int P, int TX, int TY> constexpr size_t cart_smem() {
     using S = CartShape<TX, TY>;
     return sizeof(typename Store<P>::R) *
@@ -36,15 +46,28 @@ template <int P, int TX, int TY> constexpr size_t cart_smem() {
 __device__ constexpr int XSLOT_A(int k) { return k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
 __device__ constexpr int YSLOT_A(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
 
+// Step coefficients in the compute precision.
+template <class R> struct CartK;
+template <> struct CartK<double> {
+    double a, b, c, r, dt, dtV, hx, hy;
+    __device__ explicit CartK(const CartInst &m) : a(m.a), b(m.b), c(m.c), r(m.r), dt(m.dt), dtV(m.dtV), hx(m.dx), hy(m.dy) {}
+    __device__ static double par(const CartInst &m, int side, int i) { return m.side_par[side][i]; }
+};
+template <> struct CartK<float> {
+    float a, b, c, r, dt, dtV, hx, hy;
+    __device__ explicit CartK(const CartInst &m) : a(m.fa), b(m.fb), c(m.fc), r(m.fr), dt(m.fdt), dtV(m.fdtV), hx(m.fdx), hy(m.fdy) {}
+    __device__ static float par(const CartInst &m, int side, int i) { return m.fside_par[side][i]; }
+};
+
 // Interface distribution on a face between cell L (below/left) and R (above/right),
 // along axis AX (0: face of constant x, 1: of constant y), from the staged fbar+ and
 // gradients; writes (xi . n_+ l) f_b of the six crossing velocities (n_+ = +x or +y).
 template <int AX, class R>
 __device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, const R *s_sig, int lL, int lR, int gL,
-                                                   int gR, const CoefR<R> &k, R hx, R hy, int LXY, int GXY)
+                                                   int gR, const CartK<R> &k, int LXY, int GXY)
 {
     // x_f - x_L = +h/2 along the axis, x_f - x_R = -h/2
-    const R hl = AX == 0 ? R(0.5) * hx : R(0.5) * hy;
+    const R hl = AX == 0 ? R(0.5) * k.hx : R(0.5) * k.hy;
     R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
@@ -66,7 +89,7 @@ __device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, co
     R ux, uy, feqb[NQ];
     vel_of<R>(w0, w1, w2, ux, uy);
     feq9f<R>(w0, ux, uy, feqb);
-    const R len = AX == 0 ? hy : hx;
+    const R len = AX == 0 ? k.hy : k.hx;
 #pragma unroll
     for (int q = 0; q < 6; q++) {
         const int a = AX == 0 ? XSLOT_A(q) : YSLOT_A(q);
@@ -76,22 +99,23 @@ __device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, co
     }
 }
 
-// Boundary face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y): adds the
-// outward flux (xi . n l) f_b of every crossing velocity to F (Sec. III rules).
+// Boundary face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y) on grid side
+// `side`: adds the outward flux (xi . n l) f_b of every crossing velocity to F
+// (Sec. III rules).
 template <int D, class R>
-__device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, const R *s_sig, int lme, int gme, int patch,
-                                                   const Coefs &c, const CoefR<R> &k, const R fn[NQ], const R feqn[NQ],
-                                                   R rho_n, R ux_n, R uy_n, R hx, R hy, int LXY, int GXY)
+__device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, const R *s_sig, int lme, int gme,
+                                                   const CartInst &m, int side, const CartK<R> &k, const R fn[NQ],
+                                                   const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY, int GXY)
 {
-    const R nx = D == 0 ? hy : (D == 1 ? -hy : R(0));
-    const R ny = D == 2 ? hx : (D == 3 ? -hx : R(0));
-    const R rx = D == 0 ? R(0.5) * hx : (D == 1 ? R(-0.5) * hx : R(0));
-    const R ry = D == 2 ? R(0.5) * hy : (D == 3 ? R(-0.5) * hy : R(0));
-    const int bk = c.bc_kind[patch];
+    const R nx = D == 0 ? k.hy : (D == 1 ? -k.hy : R(0));
+    const R ny = D == 2 ? k.hx : (D == 3 ? -k.hx : R(0));
+    const R rx = D == 0 ? R(0.5) * k.hx : (D == 1 ? R(-0.5) * k.hx : R(0));
+    const R ry = D == 2 ? R(0.5) * k.hy : (D == 3 ? R(-0.5) * k.hy : R(0));
+    const int bk = m.side_kind[side];
     R rb = rho_n, ubx = R(0), uby = R(0);
-    if (bk == BK_MOVING_WALL) { ubx = CoefR<R>::par(c, patch, 0); uby = CoefR<R>::par(c, patch, 1); }
+    if (bk == BK_MOVING_WALL) { ubx = CartK<R>::par(m, side, 0); uby = CartK<R>::par(m, side, 1); }
     else if (bk == BK_FARFIELD) {
-        rb = CoefR<R>::par(c, patch, 0); ubx = CoefR<R>::par(c, patch, 1); uby = CoefR<R>::par(c, patch, 2);
+        rb = CartK<R>::par(m, side, 0); ubx = CartK<R>::par(m, side, 1); uby = CartK<R>::par(m, side, 2);
     } else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
     R feqb[NQ];
     feq9f<R>(rb, ubx, uby, feqb);
@@ -112,47 +136,43 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, cons
     }
 }
 
-// Threads per CTA: one per interior face of the block (>= cells, >= staged positions).
-template <int TX, int TY> __host__ __device__ constexpr int cart_threads() {
-    constexpr int nf = CartShape<TX, TY>::NFX + CartShape<TX, TY>::NFY;
-    constexpr int nl = CartShape<TX, TY>::LX * CartShape<TX, TY>::LY;
-    constexpr int m = nf > nl ? nf : nl;
-    return (m + 31) / 32 * 32;
-}
-
+// One TX x TY block (block coordinates tbx, tby) of one grid: reads buffer `par`,
+// writes buffer 1 - par.  All threads of the CTA must call it (it synchronises).
 template <int P, int TX, int TY>
-__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : 2)
-k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restrict__ fin,
-            typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn, double *__restrict__ Wout)
+__device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, int tby, unsigned char *smem_raw)
 {
     using R = typename Store<P>::R;
+    using T = typename Store<P>::T;
     using SP = Store<P>;
     using S = CartShape<TX, TY>;
     constexpr int LXY = S::LX * S::LY, GXY = S::GX * S::GY;
     constexpr int NTH = cart_threads<TX, TY>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][LX]
     R *s_sig = s_fbp + NQ * LXY;                     // [2 NQ][GY][GX]
     R *s_fx = s_sig + 2 * NQ * GXY;                  // [6][NFX] fluxes through faces of constant x
     R *s_fy = s_fx + 6 * S::NFX;                     // [6][NFY]
 
-    const int ntx = (m.nx + TX - 1) / TX;
-    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const T *__restrict__ fin = static_cast<const T *>(m.f[par]);
+    T *__restrict__ fout = static_cast<T *>(m.f[1 - par]);
+    const double *__restrict__ Wn = m.W[par];
+    double *__restrict__ Wout = m.W[1 - par];
+    const int x0 = tbx * TX, y0 = tby * TY;
     const int tid = threadIdx.x;
     const int64_t np = m.npad, pitch = m.pitch;
-    const CoefR<R> k(c);
-    const R hx = R(m.dx), hy = R(m.dy);
+    const int nx = m.nx, ny = m.ny;
+    const bool px = m.periodic_x != 0, py = m.periodic_y != 0;
+    const CartK<R> k(m);
 
     // domain cell of a block-relative position (periodic sides wrap), or -1 outside
     auto cell_of = [&](int bi, int bj) -> int64_t {
         int gi = x0 + bi, gj = y0 + bj;
-        if (gi < 0 || gi >= m.nx) {
-            if (!m.periodic_x) return -1;
-            gi = (gi + m.nx) % m.nx;
+        if (gi < 0 || gi >= nx) {
+            if (!px) return -1;
+            gi = (gi + nx) % nx;
         }
-        if (gj < 0 || gj >= m.ny) {
-            if (!m.periodic_y) return -1;
-            gj = (gj + m.ny) % m.ny;
+        if (gj < 0 || gj >= ny) {
+            if (!py) return -1;
+            gj = (gj + ny) % ny;
         }
         return gi + pitch * gj;
     };
@@ -168,7 +188,7 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
     const bool cell_thread = tid < S::NT;
     const int ti = tid % TX, tj = tid / TX;
     const int gi = x0 + ti, gj = y0 + tj;
-    const bool active = cell_thread && gi < m.nx && gj < m.ny;
+    const bool active = cell_thread && gi < nx && gj < ny;
     const int64_t g = (int64_t)gi + pitch * gj;
     const int lme = (tj + 2) * S::LX + (ti + 2);
     R fn[NQ];
@@ -191,7 +211,7 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
             gs = cell_of(li - 2, lj - 2);
         }
         if (gs >= 0) {
-            double a0 = Wn[gs], a1 = Wn[np + gs], a2 = Wn[2 * np + gs];
+            const double a0 = Wn[gs], a1 = Wn[np + gs], a2 = Wn[2 * np + gs];
             R rho, ux, uy, fe[NQ], fv[NQ];
 #pragma unroll
             for (int a = 0; a < NQ; a++) fv[a] = SP::dec(fin[a * np + gs], R(0), a);
@@ -220,13 +240,13 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         const int bi = q % S::GX - 1, bj = q / S::GX - 1;
         if (cell_of(bi, bj) < 0) continue;
         const int ci = x0 + bi, cj = y0 + bj;
-        const bool hasE = m.periodic_x || ci + 1 < m.nx, hasW = m.periodic_x || ci - 1 >= 0;
-        const bool hasN = m.periodic_y || cj + 1 < m.ny, hasS = m.periodic_y || cj - 1 >= 0;
+        const bool hasE = px || ci + 1 < nx, hasW = px || ci - 1 >= 0;
+        const bool hasN = py || cj + 1 < ny, hasS = py || cj - 1 >= 0;
         const int l = (bj + 2) * S::LX + (bi + 2);
         const R nxk = R((hasE ? 1 : 0) + (hasW ? 1 : 0)), nyk = R((hasN ? 1 : 0) + (hasS ? 1 : 0));
         const bool singular = nxk == R(0) || nyk == R(0);
-        const R ax = singular ? R(0) : R(1) / (nxk * hx * hx), ay = singular ? R(0) : R(1) / (nyk * hy * hy);
-        const R cE = hasE ? hx : R(0), cW = hasW ? hx : R(0), cN = hasN ? hy : R(0), cS = hasS ? hy : R(0);
+        const R ax = singular ? R(0) : R(1) / (nxk * k.hx * k.hx), ay = singular ? R(0) : R(1) / (nyk * k.hy * k.hy);
+        const R cE = hasE ? k.hx : R(0), cW = hasW ? k.hx : R(0), cN = hasN ? k.hy : R(0), cS = hasS ? k.hy : R(0);
         const int oE = hasE ? 1 : 0, oW = hasW ? -1 : 0, oN = hasN ? S::LX : 0, oS = hasS ? -S::LX : 0;
 #pragma unroll
         for (int u = 0; u < 3; u++) {
@@ -248,7 +268,7 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         if (cell_of(fi - 1, fj) >= 0 && cell_of(fi, fj) >= 0) {
             const int lL = (fj + 2) * S::LX + (fi + 1), gL = (fj + 1) * S::GX + fi;
             R fl[6];
-            cart_interior_face<0, R>(fl, s_fbp, s_sig, lL, lL + 1, gL, gL + 1, k, hx, hy, LXY, GXY);
+            cart_interior_face<0, R>(fl, s_fbp, s_sig, lL, lL + 1, gL, gL + 1, k, LXY, GXY);
 #pragma unroll
             for (int r = 0; r < 6; r++) s_fx[r * S::NFX + tid] = fl[r];
         }
@@ -258,82 +278,105 @@ k_step_cart(const CartMesh m, const Coefs c, const typename Store<P>::T *__restr
         if (cell_of(fi, fj - 1) >= 0 && cell_of(fi, fj) >= 0) {
             const int lB = (fj + 1) * S::LX + (fi + 2), gB = fj * S::GX + (fi + 1);
             R fl[6];
-            cart_interior_face<1, R>(fl, s_fbp, s_sig, lB, lB + S::LX, gB, gB + S::GX, k, hx, hy, LXY, GXY);
+            cart_interior_face<1, R>(fl, s_fbp, s_sig, lB, lB + S::LX, gB, gB + S::GX, k, LXY, GXY);
 #pragma unroll
             for (int r = 0; r < 6; r++) s_fy[r * S::NFY + qq] = fl[r];
         }
     }
     __syncthreads();
-    if (!active) return;
 
-    // ---- phase 4: flux sum over the own cell's faces (order -x, +x, -y, +y)
-    R F[NQ];
+    if (active) {
+        // ---- phase 4: flux sum over the own cell's faces (order -x, +x, -y, +y)
+        R F[NQ];
 #pragma unroll
-    for (int a = 0; a < NQ; a++) F[a] = R(0);
-    const int gme = (tj + 1) * S::GX + (ti + 1);
-    const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
-    const bool inW = m.periodic_x || gi - 1 >= 0, inE = m.periodic_x || gi + 1 < m.nx;
-    const bool inS = m.periodic_y || gj - 1 >= 0, inN = m.periodic_y || gj + 1 < m.ny;
-    R feqn[NQ];
-    if (!(inW && inE && inS && inN)) feq9f<R>(rho_n, ux_n, uy_n, feqn);   // boundary cells only
-    if (inW) {
+        for (int a = 0; a < NQ; a++) F[a] = R(0);
+        const int gme = (tj + 1) * S::GX + (ti + 1);
+        const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
+        const bool inW = px || gi - 1 >= 0, inE = px || gi + 1 < nx;
+        const bool inS = py || gj - 1 >= 0, inN = py || gj + 1 < ny;
+        R feqn[NQ];
+        if (!(inW && inE && inS && inN)) feq9f<R>(rho_n, ux_n, uy_n, feqn);   // boundary cells only
+        if (inW) {
 #pragma unroll
-        for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
-    } else {
-        cart_boundary_face<1, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[3], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
-                                 LXY, GXY);
-    }
-    if (inE) {
+            for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
+        } else {
+            cart_boundary_face<1, R>(F, s_fbp, s_sig, lme, gme, m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+        }
+        if (inE) {
 #pragma unroll
-        for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NFX + fW + 1];
-    } else {
-        cart_boundary_face<0, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[1], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
-                                 LXY, GXY);
-    }
-    if (inS) {
+            for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NFX + fW + 1];
+        } else {
+            cart_boundary_face<0, R>(F, s_fbp, s_sig, lme, gme, m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+        }
+        if (inS) {
 #pragma unroll
-        for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NFY + fS];
-    } else {
-        cart_boundary_face<3, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[0], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
-                                 LXY, GXY);
-    }
-    if (inN) {
+            for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NFY + fS];
+        } else {
+            cart_boundary_face<3, R>(F, s_fbp, s_sig, lme, gme, m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+        }
+        if (inN) {
 #pragma unroll
-        for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NFY + fS + TX];
-    } else {
-        cart_boundary_face<2, R>(F, s_fbp, s_sig, lme, gme, m.side_patch[2], c, k, fn, feqn, rho_n, ux_n, uy_n, hx, hy,
-                                 LXY, GXY);
-    }
+            for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NFY + fS + TX];
+        } else {
+            cart_boundary_face<2, R>(F, s_fbp, s_sig, lme, gme, m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+        }
 
-    // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)
-    const R dtv = P == P_FP64 ? R(m.dtV) : R(m.fdtV);
-    R M0 = R(0), M1 = R(0), M2 = R(0);
+        // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)
+        R M0 = R(0), M1 = R(0), M2 = R(0);
 #pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        M0 += F[a];
-        if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
-        if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
-    }
-    const R d0 = dtv * M0, d1 = dtv * M1, d2 = dtv * M2;
-    const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
-    Wout[g] = W0;
-    Wout[np + g] = W1;
-    Wout[2 * np + g] = W2;
-    R rho1, ux1, uy1, feq1[NQ];
-    if constexpr (P == P_FP64) {
-        rho1 = W0;
-        vel_of<R>(W0, W1, W2, ux1, uy1);
-    } else {
-        rho1 = rho_n - d0;
-        vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
-    }
-    feq9f<R>(rho1, ux1, uy1, feq1);
+        for (int a = 0; a < NQ; a++) {
+            M0 += F[a];
+            if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
+            if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
+        }
+        const R d0 = k.dtV * M0, d1 = k.dtV * M1, d2 = k.dtV * M2;
+        const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
+        Wout[g] = W0;
+        Wout[np + g] = W1;
+        Wout[2 * np + g] = W2;
+        R rho1, ux1, uy1, feq1[NQ];
+        if constexpr (P == P_FP64) {
+            rho1 = W0;
+            vel_of<R>(W0, W1, W2, ux1, uy1);
+        } else {
+            rho1 = rho_n - d0;
+            vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
+        }
+        feq9f<R>(rho1, ux1, uy1, feq1);
 #pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        R fnew;
-        if constexpr (P == P_FP64) fnew = (fn[a] - dtv * F[a] + k.r * feq1[a]) / (R(1) + k.r);
-        else fnew = (fn[a] - dtv * F[a] + k.r * feq1[a]) * c.finv1r;
-        fout[a * np + g] = SP::enc(fnew, feq1[a], a);
+        for (int a = 0; a < NQ; a++) {
+            R fnew;
+            if constexpr (P == P_FP64) fnew = (fn[a] - k.dtV * F[a] + k.r * feq1[a]) / (R(1) + k.r);
+            else fnew = (fn[a] - k.dtV * F[a] + k.r * feq1[a]) * m.finv1r;
+            fout[a * np + g] = SP::enc(fnew, feq1[a], a);
+        }
+    }
+}
+
+template <int P, int TX, int TY>
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : 2)
+k_step_cart(const CartInst m, int par)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ntx = (m.nx + TX - 1) / TX;
+    cart_tile<P, TX, TY>(m, par, blockIdx.x % ntx, blockIdx.x / ntx, smem_raw);
+}
+
+// Batched: a fixed grid walks the (instance, block) work list; the item count is in
+// device memory so that a captured graph stays valid while instances come and go.
+template <int P, int TX, int TY>
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), 2)
+k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items, const int *__restrict__ n_items,
+             int par)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = *n_items;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int2 it = items[w];
+        const CartInst &m = insts[it.x];
+        const int ntx = (m.nx + TX - 1) / TX;
+        cart_tile<P, TX, TY>(m, par, it.y % ntx, it.y / ntx, smem_raw);
+        __syncthreads();                                 // shared memory is reused by the next item
     }
 }
 
@@ -343,13 +386,10 @@ template <int P, int TX, int TY> cudaError_t prepare_cart_p() {
 }
 
 template <int P, int TX, int TY>
-cudaError_t launch_cart_p(const CartMesh &m, const Coefs &c, const void *fin, void *fout, const double *Wn, double *Wout,
-                          cudaStream_t st)
+cudaError_t launch_cart_p(const CartInst &m, int par, cudaStream_t st)
 {
-    using T = typename Store<P>::T;
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
-    k_step_cart<P, TX, TY><<<ntx * nty, cart_threads<TX, TY>(), cart_smem<P, TX, TY>(), st>>>(
-        m, c, static_cast<const T *>(fin), static_cast<T *>(fout), Wn, Wout);
+    k_step_cart<P, TX, TY><<<ntx * nty, cart_threads<TX, TY>(), cart_smem<P, TX, TY>(), st>>>(m, par);
     return cudaGetLastError();
 }
 

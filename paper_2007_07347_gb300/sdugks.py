@@ -24,7 +24,7 @@ FP64, FP32, FP32_BF16DEV = 0, 1, 2
 KERNEL_AUTO, KERNEL_TILED, KERNEL_CARTESIAN = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16dev": FP32_BF16DEV}
 ERRORS = {-1: "INVALID_ARG", -2: "INVALID_MESH", -3: "BAD_BC", -4: "OOM", -5: "DIVERGED", -6: "TIMEOUT",
-          -7: "CUDA", -8: "STATE"}
+          -7: "CUDA", -8: "STATE", -9: "FULL"}
 
 
 class SdugksError(RuntimeError):
@@ -79,6 +79,16 @@ def lib():
                 "sdugks_get_state": [P, P, P],
                 "sdugks_set_state": [P, P, P],
                 "sdugks_solver_info": [P, P],
+                "sdugks_residual_noalloc": [i64, P, P, P, P, P],
+                "sdugks_batch_create": [i64, i32, i32, P, P],
+                "sdugks_batch_footprint": [P, P, P],
+                "sdugks_batch_add": [P, P, dbl, dbl, P, P, P],
+                "sdugks_batch_remove": [P, i64],
+                "sdugks_batch_step": [P, i64],
+                "sdugks_batch_residual": [P, P, P, P, P, P],
+                "sdugks_batch_get_macros": [P, i64, P, P],
+                "sdugks_batch_autotune": [P, i64],
+                "sdugks_batch_info": [P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -88,6 +98,8 @@ def lib():
             L.sdugks_mesh_destroy.restype = None
             L.sdugks_solver_destroy.argtypes = [P]
             L.sdugks_solver_destroy.restype = None
+            L.sdugks_batch_destroy.argtypes = [P]
+            L.sdugks_batch_destroy.restype = None
             L.sdugks_last_error.restype = C.c_char_p
             L.sdugks_version.restype = C.c_char_p
             _lib = L
@@ -218,6 +230,90 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().sdugks_solver_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchStatus(C.Structure):
+    _fields_ = [("instances", C.c_int64), ("cells", C.c_int64), ("items", C.c_int64), ("pool_bytes", C.c_int64),
+                ("pool_used", C.c_int64), ("steps", C.c_int64), ("grid", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("graph_steps", C.c_int32), ("precision", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Batch:
+    """sdugks_batch: many uniform-grid solves advanced by one batched kernel per step."""
+
+    def __init__(self, pool_bytes: int, precision="fp32", max_instances: int = 1024, stream=None):
+        L = lib()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        sh = getattr(stream, "cuda_stream", stream)
+        self._h = C.c_void_p()
+        _ck(L.sdugks_batch_create(int(pool_bytes), prec, int(max_instances), C.c_void_p(sh or 0), C.byref(self._h)),
+            "sdugks_batch_create")
+        self.max_instances = int(max_instances)
+        self.n_cells = {}
+
+    def footprint(self, mesh: Mesh) -> int:
+        out = C.c_int64()
+        _ck(lib().sdugks_batch_footprint(self._h, mesh._h, C.byref(out)), "sdugks_batch_footprint")
+        return out.value
+
+    def add(self, mesh: Mesh, tau: float, dt: float, rho=None, u=None) -> int:
+        r = None if rho is None else _f64(rho, (mesh.n_cells,))
+        v = None if u is None else _f64(u, (mesh.n_cells, 2))
+        out = C.c_int64()
+        _ck(lib().sdugks_batch_add(self._h, mesh._h, float(tau), float(dt), _ptr(r), _ptr(v), C.byref(out)),
+            "sdugks_batch_add")
+        self.n_cells[out.value] = mesh.n_cells
+        return out.value
+
+    def add_case(self, case: _meshes.Case, rho=None, u=None) -> int:
+        m = Mesh(case.mesh, case.bcs)
+        return self.add(m, case.tau, case.dt, rho, u)
+
+    def remove(self, ident: int):
+        _ck(lib().sdugks_batch_remove(self._h, int(ident)), "sdugks_batch_remove")
+        self.n_cells.pop(ident, None)
+
+    def step(self, n: int = 1):
+        _ck(lib().sdugks_batch_step(self._h, int(n)), "sdugks_batch_step")
+        return self
+
+    def residual(self) -> dict:
+        """{id: (eps, mass, steps since admission)} for every active instance."""
+        m = self.max_instances
+        ids = np.empty(m, np.int64); eps = np.empty(m); mass = np.empty(m); steps = np.empty(m, np.int64)
+        cnt = C.c_int64()
+        _ck(lib().sdugks_batch_residual(self._h, _ptr(ids), _ptr(eps), _ptr(mass), _ptr(steps), C.byref(cnt)),
+            "sdugks_batch_residual")
+        k = cnt.value
+        return {int(i): (float(e), float(ms), int(st)) for i, e, ms, st in zip(ids[:k], eps[:k], mass[:k], steps[:k])}
+
+    def macros(self, ident: int):
+        n = self.n_cells[ident]
+        rho = np.empty(n); u = np.empty((n, 2))
+        _ck(lib().sdugks_batch_get_macros(self._h, int(ident), _ptr(rho), _ptr(u)), "sdugks_batch_get_macros")
+        return rho, u
+
+    def autotune(self, steps: int = 20):
+        _ck(lib().sdugks_batch_autotune(self._h, int(steps)), "sdugks_batch_autotune")
+
+    def info(self) -> dict:
+        out = BatchStatus()
+        _ck(lib().sdugks_batch_info(self._h, C.byref(out)), "sdugks_batch_info")
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sdugks_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

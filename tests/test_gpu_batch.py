@@ -1,0 +1,129 @@
+"""Batched solves (sdugks_batch): one kernel launch per step over the (instance, block)
+work list of many uniform-grid solves of different sizes and Reynolds numbers.
+
+Each instance runs the same device code on its own data as the single-solver
+Cartesian kernel, so its results are compared bit for bit with a single solver of the
+same case, alone and in a mix, including instances admitted mid-run.  One instance is
+also checked against the FP64 oracle with the FP32 tolerance of the parity tests.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_07347_gb300 import meshes as M
+
+pytestmark = pytest.mark.gpu
+
+
+def _S():
+    from paper_2007_07347_gb300 import sdugks as S
+    return S
+
+
+def _single(case, steps, precision="fp32"):
+    S = _S()
+    s = S.Solver.from_case(case, precision).init()
+    s.step(steps)
+    return s.macros()
+
+
+MIX = [lambda: M.cavity(40, Re=400.0), lambda: M.cavity(100, Re=1000.0), lambda: M.couette(64),
+       lambda: M.cavity(64, Re=100.0)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev"])
+def test_batch_instances_equal_single_solvers(precision):
+    S = _S()
+    b = S.Batch(256 << 20, precision, max_instances=16)
+    cases = [mk() for mk in MIX]
+    ids = [b.add_case(c) for c in cases]
+    b.step(300)                                   # graph of 64 steps + single launches
+    for ident, case in zip(ids, cases):
+        rho, u = b.macros(ident)
+        rho1, u1 = _single(case, 300, precision)
+        np.testing.assert_array_equal(rho, rho1)
+        np.testing.assert_array_equal(u, u1)
+
+
+def test_result_same_alone_and_in_the_mix_and_late_admission():
+    S = _S()
+    case = M.cavity(48, Re=400.0)
+    alone = S.Batch(64 << 20, "fp32", max_instances=4)
+    a = alone.add_case(case)
+    alone.step(201)
+    mix = S.Batch(256 << 20, "fp32", max_instances=8)
+    others = [mix.add_case(mk()) for mk in MIX[:2]]
+    mix.step(37)                                  # odd step count: the buffer parity flips
+    late = mix.add_case(case)
+    mix.add_case(MIX[2]())
+    mix.step(201)
+    np.testing.assert_array_equal(alone.macros(a)[1], mix.macros(late)[1])
+    res = mix.residual()
+    assert res[late][2] == 201 and res[others[0]][2] == 238
+
+
+def test_batch_against_oracle():
+    S = _S()
+    case = M.cavity(32, Re=100.0)
+    b = S.Batch(32 << 20, "fp32", max_instances=2)
+    ident = b.add_case(case)
+    b.step(500)
+    rho, u = b.macros(ident)
+    st = O.init(case.mesh.n_cells)
+    O.run(case, st, 500)
+    assert np.sqrt(np.sum((u - st.u) ** 2) / np.sum(st.u ** 2)) <= 1e-4
+    assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
+
+
+def test_batch_residual_matches_single_solver():
+    S = _S()
+    case = M.cavity(64, Re=100.0)
+    b = S.Batch(64 << 20, "fp32", max_instances=2)
+    ident = b.add_case(case)
+    s = S.Solver.from_case(case, "fp32").init()
+    for k in range(2):
+        b.step(128)
+        s.step(128)
+        eps_b, mass_b, _ = b.residual()[ident]
+        eps_s, mass_s = s.residual()
+        if k == 0:
+            assert np.isinf(eps_b) and np.isinf(eps_s)
+        else:
+            assert abs(eps_b - eps_s) <= 1e-12 * eps_s
+        assert abs(mass_b - mass_s) <= 1e-12 * mass_s
+
+
+def test_admission_by_footprint_and_reuse():
+    S = _S()
+    probe = S.Batch(1 << 20, "fp32", max_instances=4)
+    mesh = S.Mesh(M.cavity(64).mesh, M.cavity(64).bcs)
+    fp = probe.footprint(mesh)
+    assert fp > 64 * 64 * 120
+    b = S.Batch(2 * fp, "fp32", max_instances=8)
+    c = M.cavity(64, Re=100.0)
+    i1 = b.add_case(c)
+    i2 = b.add_case(c)
+    with pytest.raises(S.SdugksError) as e:
+        b.add_case(c)
+    assert e.value.name == "FULL"
+    b.step(10)
+    b.remove(i1)
+    i3 = b.add_case(c)                           # the freed block is reused
+    b.step(10)
+    info = b.info()
+    assert info["instances"] == 2 and info["pool_used"] == 2 * fp
+    assert set(b.residual()) == {i2, i3}
+    with pytest.raises(S.SdugksError):
+        b.add_case(M.cylinder(32, 16, first=0.02, r_far=10.0))   # not a uniform grid
+
+
+def test_autotune_keeps_results():
+    S = _S()
+    b = S.Batch(256 << 20, "fp32", max_instances=8)
+    ids = [b.add_case(mk()) for mk in MIX]
+    b.autotune(4)
+    done = b.residual()[ids[0]][2]
+    b.step(64)
+    rho, u = b.macros(ids[1])
+    rho1, u1 = _single(MIX[1](), done + 64)
+    np.testing.assert_array_equal(u, u1)
