@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="cavity cells per side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve"],
+                    help="cavity: the headline single solve; batch: 256 cavities in one batch against the plain "
+                         "one-at-a-time path; serve: the continuous-batching request loop")
+    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
     return ap.parse_args()
 
 
@@ -320,10 +325,89 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def run_batch(args):
+    """256 lid-driven cavities (N ~ logU[32, 512], Re ~ logU[100, 5000], seed 1, lid 0.1,
+    CFL 0.5, FP32) advanced together, against the plain path (each solved alone)."""
+    import torch
+    from paper_2007_07347_gb300 import sdugks as S
+    torch.cuda.set_device(0)
+    specs = M.batch_cavities(256, seed=1)
+    cases = [M.cavity(n, Re=re) for n, re in specs]
+    cells = sum(c.mesh.n_cells for c in cases)
+    stream = torch.cuda.Stream()
+    probe = S.Batch(1 << 20, args.precision, 4)
+    need = sum(probe.footprint(S.Mesh(c.mesh, c.bcs)) for c in cases)
+    b = S.Batch(need + (64 << 20), args.precision, 512, stream=stream)
+    for c in cases:
+        b.add_case(c)
+    b.autotune(2)
+    interval = 100
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            b.step(interval)
+            b.residual()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.step(interval)
+            b.residual()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    batch_mlups = cells * 9 * interval * args.steps / t_batch / 1e6
+    # plain path: each instance alone (same kernel family, one solver per case), 2 x 64 steps each
+    plain_steps = 128
+    t_plain = 0.0
+    with torch.cuda.stream(stream):
+        for c in cases:
+            s = S.Solver.from_case(c, args.precision, stream=stream).init()
+            s.step(64)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.step(plain_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_plain += e0.elapsed_time(e1) / 1e3
+            s.close()
+    plain_mlups = cells * 9 * plain_steps / t_plain / 1e6
+    info = b.info()
+    print(json.dumps({"metric": "MLUPS", "value": batch_mlups, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
+                      "dtype": args.precision, "data": "synthetic",
+                      "config": {"workload": "batch of 256 lid-driven cavities, N~logU[32,512], Re~logU[100,5000], "
+                                             "seed 1, FP32", "cells": cells, "time_steps_per_step": interval},
+                      "plain_path_mlups": plain_mlups, "batched_over_plain": batch_mlups / plain_mlups,
+                      "batch": info}))
+
+
+def run_serve(args):
+    """Continuous-batching request loop on the config-shaped request mix (seed 2)."""
+    import torch
+    from paper_2007_07347_gb300 import serve as V
+    torch.cuda.set_device(0)
+    wl = V.Workload(n_requests=args.requests)
+    reqs = wl.requests()
+    srv = V.Server(pool_bytes=16 << 30, precision=args.precision, target=1e-6, check_every=500,
+                   step_cap=args.step_cap)
+    sb, ss = torch.cuda.Stream(), torch.cuda.Stream()
+    out = srv.run(reqs, stream_batch=sb, stream_solvers=ss)
+    out["cell_steps_per_s"] = out["cell_steps"] / out["wall_s"]
+    out["mlups"] = 9 * out["cell_steps_per_s"] / 1e6
+    out["config"] = {"workload": f"{args.requests} Poisson requests (200/s, seed 2), 60/30/10 cavities 64^2-1024^2 "
+                                 f"Re 100-5000 / Couette 4x64-4x1024 Re 10 / cylinders 128x64-512x256 Re 10-100, "
+                                 f"target 1e-6, cap {args.step_cap} steps", "precision": args.precision}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
