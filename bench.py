@@ -131,6 +131,19 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- helpers
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest value over all ranks (each rank's timed-region duration); the
+    process group must be initialised when world > 1."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -263,11 +276,7 @@ def run_ours(args):
             barrier()
         step_ms = [e[0].elapsed_time(e[2]) for e in ev]
         kern_ms = [e[0].elapsed_time(e[1]) / INTERVAL for e in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world)
     cells_q = n * 9 * INTERVAL * args.steps * world
     value = cells_q / (total_ms / 1e3) / 1e6
 

@@ -146,6 +146,16 @@ int sdugks_init(sdugks_solver *s, const double *rho, const double *u);
  * a captured CUDA graph of params.graph_steps steps.  Errors: STATE before init. */
 int sdugks_step(sdugks_solver *s, int64_t n);
 
+/* One step (as sdugks_step(s, 1)) that also returns the force on every boundary
+ * patch: force[2 p], force[2 p + 1] (host, [64][2]) = the momentum leaving the fluid
+ * through the faces of patch p in that step, sum over its faces of
+ * sum_a xi_a (xi_a . n l) f_b,a (n out of the fluid), per unit depth and time in the
+ * solver's units.  For a wall this is the force of the fluid on it, from which drag
+ * and lift coefficients follow (C = F / (0.5 rho U^2 D), Sec. IV).  Periodic patches
+ * read 0.  Synchronises.  The FP64 sums use atomics, so the last bits can vary from
+ * run to run; the state update itself is unchanged. */
+int sdugks_step_forces(sdugks_solver *s, double *force);
+
 /* Macroscopic fields at the current step: rho[n_cells], u[n_cells][2] (host;
  * synchronises).  Either pointer may be NULL. */
 int sdugks_get_macros(sdugks_solver *s, double *rho, double *u);

@@ -376,6 +376,8 @@ struct sdugks_solver {
     cudaGraphExec_t graph = nullptr;
     int graph_len = 0;
     double mesh_bytes = 0.0;
+    double *d_force = nullptr;      // [MAXPATCH][2] (allocated on first force step)
+    int32_t side_patch[4] = {-1, -1, -1, -1};   // Cartesian: patch of each grid side
 };
 
 static int prepare(int prec, int kernel)
@@ -568,6 +570,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     s->n_red_blocks = residual_blocks(n);
     s->mesh_bytes = 0.0;
     fill_cart_inst(s->ci, m, g, prm->tau, prm->dt, pitch, npad);
+    for (int k = 0; k < 4; k++) s->side_patch[k] = g.side_patch[k];
     auto layout = [&](Arena &A) {
         s->perm = A.take<int32_t>(n);
         s->loc = A.take<int32_t>(n);
@@ -1004,6 +1007,47 @@ extern "C" int sdugks_step(sdugks_solver *s, int64_t n)
     return SDUGKS_OK;
 }
 
+extern "C" int sdugks_step_forces(sdugks_solver *s, double *force)
+{
+    if (!s || !force) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "step before init or set_state");
+    CUDA_TRY(cudaSetDevice(s->device));
+    if (!s->d_force) CUDA_TRY(cudaMalloc(&s->d_force, sizeof(double) * 2 * MAXPATCH));
+    CUDA_TRY(cudaMemsetAsync(s->d_force, 0, sizeof(double) * 2 * MAXPATCH, s->stream));
+    cudaError_t e;
+    if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
+        CartInst ci = s->ci;
+        ci.force = s->d_force;                 // per grid side
+        e = launch_step_cart(s->p.precision, ci, s->cur, s->stream);
+    } else {
+        TiledMesh tm = s->tm;
+        tm.force = s->d_force;                 // per patch
+        const int a = s->cur;
+        e = s->p.precision == P_FP64
+                ? launch_step_tiled_fp64(tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], s->stream)
+                : launch_step_tiled_fp32(s->p.precision, tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a],
+                                         s->st.W[1 - a], s->stream);
+    }
+    CUDA_TRY(e);
+    s->cur = 1 - s->cur;
+    s->steps_done++;
+    double h[2 * MAXPATCH];
+    CUDA_TRY(cudaMemcpyAsync(h, s->d_force, sizeof h, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    for (int q = 0; q < 2 * MAXPATCH; q++) force[q] = 0.0;
+    if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
+        for (int side = 0; side < 4; side++) {
+            const int p = s->side_patch[side];
+            if (p < 0 || s->coefs.bc_kind[p] == SDUGKS_BC_PERIODIC) continue;
+            force[2 * p] += h[2 * side];
+            force[2 * p + 1] += h[2 * side + 1];
+        }
+    } else {
+        for (int q = 0; q < 2 * MAXPATCH; q++) force[q] = h[q];
+    }
+    return SDUGKS_OK;
+}
+
 extern "C" int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double *d_u)
 {
     if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
@@ -1095,6 +1139,7 @@ extern "C" void sdugks_solver_destroy(sdugks_solver *s)
     if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->staging) cudaFree(s->staging);
+    if (s->d_force) cudaFree(s->d_force);
     if (s->h_red) cudaFreeHost(s->h_red);
     if (s->dmem) cudaFree(s->dmem);
     delete s;

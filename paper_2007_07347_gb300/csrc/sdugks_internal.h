@@ -59,6 +59,7 @@ struct TiledMesh {
     const void *ainv;         // [3][npad] LLSR inverse (xx, xy, yy)
     const void *dtV;          // [npad] dt / V (compute precision)
     const double *vol;        // [npad] V
+    double *force;            // nullptr, or [MAXPATCH][2]: momentum flux out of the fluid per boundary patch
 };
 
 // One uniform-grid solve as the Cartesian kernels see it: nx x ny rectangles
@@ -78,6 +79,7 @@ struct CartInst {
     void *f[2];
     double *W[2];
     double *snap;             // [2][npad] residual snapshot (U0, V0)
+    double *force;            // nullptr, or [4][2]: momentum flux out of the fluid per grid side
 };
 
 // Device state of one solver, ping-pong: f [2][NQ][npad] (element type by

@@ -102,7 +102,7 @@ __device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, co
 // Boundary face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y) on grid side
 // `side`: adds the outward flux (xi . n l) f_b of every crossing velocity to F
 // (Sec. III rules).
-template <int D, class R>
+template <int D, class R, bool DIAG>
 __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, const R *s_sig, int lme, int gme,
                                                    const CartInst &m, int side, const CartK<R> &k, const R fn[NQ],
                                                    const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY, int GXY)
@@ -119,6 +119,7 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, cons
     } else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
     R feqb[NQ];
     feq9f<R>(rb, ubx, uby, feqb);
+    R px_ = R(0), py_ = R(0);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         const int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));
@@ -133,12 +134,19 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, cons
             fb = (A + k.b * feqb[a]) * k.c;
         }
         F[a] += s * fb;
+        px_ += R(EX(a)) * (s * fb);
+        py_ += R(EY(a)) * (s * fb);
+    }
+    if (DIAG && m.force) {       // diagnostic steps only: momentum leaving the fluid through this side
+        atomicAdd(&m.force[2 * side], to_f64<R>(px_));
+        atomicAdd(&m.force[2 * side + 1], to_f64<R>(py_));
     }
 }
 
 // One TX x TY block (block coordinates tbx, tby) of one grid: reads buffer `par`,
 // writes buffer 1 - par.  All threads of the CTA must call it (it synchronises).
-template <int P, int TX, int TY>
+// DIAG compiles in the optional wall-force accumulation.
+template <int P, int TX, int TY, bool DIAG>
 __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, int tby, unsigned char *smem_raw)
 {
     using R = typename Store<P>::R;
@@ -300,25 +308,25 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
         } else {
-            cart_boundary_face<1, R>(F, s_fbp, s_sig, lme, gme, m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<1, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
         }
         if (inE) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NFX + fW + 1];
         } else {
-            cart_boundary_face<0, R>(F, s_fbp, s_sig, lme, gme, m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<0, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
         }
         if (inS) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NFY + fS];
         } else {
-            cart_boundary_face<3, R>(F, s_fbp, s_sig, lme, gme, m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<3, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
         }
         if (inN) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NFY + fS + TX];
         } else {
-            cart_boundary_face<2, R>(F, s_fbp, s_sig, lme, gme, m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<2, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
         }
 
         // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)
@@ -359,7 +367,7 @@ k_step_cart(const CartInst m, int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ntx = (m.nx + TX - 1) / TX;
-    cart_tile<P, TX, TY>(m, par, blockIdx.x % ntx, blockIdx.x / ntx, smem_raw);
+    cart_tile<P, TX, TY, true>(m, par, blockIdx.x % ntx, blockIdx.x / ntx, smem_raw);
 }
 
 // Batched: a fixed grid walks the (instance, block) work list; the item count is in
@@ -375,7 +383,7 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
         const int2 it = items[w];
         const CartInst &m = insts[it.x];
         const int ntx = (m.nx + TX - 1) / TX;
-        cart_tile<P, TX, TY>(m, par, it.y % ntx, it.y / ntx, smem_raw);
+        cart_tile<P, TX, TY, false>(m, par, it.y % ntx, it.y / ntx, smem_raw);
         __syncthreads();                                 // shared memory is reused by the next item
     }
 }

@@ -157,6 +157,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
             else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
             R feqb[NQ];
             feq9f<R>(rb, ubx, uby, feqb);
+            R px_ = R(0), py_ = R(0);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
@@ -169,6 +170,12 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                     fb = (A + k.b * feqb[a]) * k.c;
                 }
                 F[a] += s * fb;
+                px_ += R(EX(a)) * (s * fb);
+                py_ += R(EY(a)) * (s * fb);
+            }
+            if (m.force) {       // diagnostic steps only: momentum leaving the fluid through this patch
+                atomicAdd(&m.force[2 * p], to_f64<R>(px_));
+                atomicAdd(&m.force[2 * p + 1], to_f64<R>(py_));
             }
         }
     }

@@ -92,40 +92,26 @@ def cartesian(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, *, jitter: flo
         py[inner] += rng.uniform(-h, h, inner.sum())
     points = np.stack([px, py], 1)
 
-    def pid(i, j):
-        return i + (nx + 1) * j
-
-    def cid(i, j):
-        return i + nx * j
-
-    fp, own, nbr = [], [], []
-    # faces of constant x (between cells (i-1, j) and (i, j))
-    for j in range(ny):
-        for i in range(nx + 1):
-            fp.append((pid(i, j), pid(i, j + 1)))
-            if i == 0:
-                own.append(cid(0, j)); nbr.append(-1 - 3)
-            elif i == nx:
-                own.append(cid(nx - 1, j)); nbr.append(-1 - 1)
-            else:
-                own.append(cid(i - 1, j)); nbr.append(cid(i, j))
+    # faces of constant x (between cells (i-1, j) and (i, j)), row by row
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx + 1), indexing="ij")
+    ii, jj = ii.ravel(), jj.ravel()
+    fpx = np.stack([ii + (nx + 1) * jj, ii + (nx + 1) * (jj + 1)], 1)
+    ownx = np.where(ii == 0, jj * nx, ii - 1 + nx * jj)
+    nbrx = np.where(ii == 0, -1 - 3, np.where(ii == nx, -1 - 1, ii + nx * jj))
     # faces of constant y (between cells (i, j-1) and (i, j))
-    for j in range(ny + 1):
-        for i in range(nx):
-            fp.append((pid(i, j), pid(i + 1, j)))
-            if j == 0:
-                own.append(cid(i, 0)); nbr.append(-1 - 0)
-            elif j == ny:
-                own.append(cid(i, ny - 1)); nbr.append(-1 - 2)
-            else:
-                own.append(cid(i, j - 1)); nbr.append(cid(i, j))
+    jj, ii = np.meshgrid(np.arange(ny + 1), np.arange(nx), indexing="ij")
+    ii, jj = ii.ravel(), jj.ravel()
+    fpy = np.stack([ii + (nx + 1) * jj, ii + 1 + (nx + 1) * jj], 1)
+    owny = np.where(jj == 0, ii, ii + nx * (jj - 1))
+    nbry = np.where(jj == 0, -1 - 0, np.where(jj == ny, -1 - 2, ii + nx * jj))
+    fp = np.concatenate([fpx, fpy]).astype(np.int64)
+    own = np.concatenate([ownx, owny]).astype(np.int64)
+    nbr = np.concatenate([nbrx, nbry]).astype(np.int64)
     ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
     meta = dict(kind="cartesian", nx=nx, ny=ny, lx=lx, ly=ly, dx=dx, dy=dy,
                 cell_i=ci.ravel(), cell_j=cj.ravel(),
                 cell_xy_nominal=np.stack([(ci.ravel() + 0.5) * dx, (cj.ravel() + 0.5) * dy], 1))
-    return Mesh(points, np.asarray(fp, np.int64), np.asarray(own, np.int64),
-                np.asarray(nbr, np.int64), nx * ny,
-                dict(bottom=0, right=1, top=2, left=3), meta)
+    return Mesh(points, fp, own, nbr, nx * ny, dict(bottom=0, right=1, top=2, left=3), meta)
 
 
 def o_mesh_ratio(n_r: int, r0: float, first: float, r_far: float) -> float:
@@ -160,33 +146,25 @@ def o_mesh(n_theta: int, n_r: int, *, diameter: float = 1.0, first: float = 0.00
     R, T = np.meshgrid(radii, th, indexing="ij")          # [n_r+1, n_theta]
     points = np.stack([(R * np.cos(T)).ravel(), (R * np.sin(T)).ravel()], 1)
 
-    def pid(i, k):
-        return (i % n_theta) + n_theta * k
-
-    def cid(i, k):
-        return (i % n_theta) + n_theta * k
-
-    fp, own, nbr = [], [], []
-    # radial faces at angle th_i, between cells (i-1, k) and (i, k)
-    for k in range(n_r):
-        for i in range(n_theta):
-            fp.append((pid(i, k), pid(i, k + 1)))
-            own.append(cid(i - 1, k)); nbr.append(cid(i, k))
+    # radial faces at angle th_i, between cells (i-1, k) and (i, k), ring by ring
+    kk, ii = np.meshgrid(np.arange(n_r), np.arange(n_theta), indexing="ij")
+    ii, kk = ii.ravel(), kk.ravel()
+    fpr = np.stack([ii + n_theta * kk, ii + n_theta * (kk + 1)], 1)
+    ownr = (ii - 1) % n_theta + n_theta * kk
+    nbrr = ii + n_theta * kk
     # circumferential faces at radius r_k, between cells (i, k-1) and (i, k)
-    for k in range(n_r + 1):
-        for i in range(n_theta):
-            fp.append((pid(i, k), pid(i + 1, k)))
-            if k == 0:
-                own.append(cid(i, 0)); nbr.append(-1 - 0)
-            elif k == n_r:
-                own.append(cid(i, n_r - 1)); nbr.append(-1 - 1)
-            else:
-                own.append(cid(i, k - 1)); nbr.append(cid(i, k))
+    kk, ii = np.meshgrid(np.arange(n_r + 1), np.arange(n_theta), indexing="ij")
+    ii, kk = ii.ravel(), kk.ravel()
+    fpc = np.stack([ii + n_theta * kk, (ii + 1) % n_theta + n_theta * kk], 1)
+    ownc = np.where(kk == 0, ii, np.where(kk == n_r, ii + n_theta * (n_r - 1), ii + n_theta * (kk - 1)))
+    nbrc = np.where(kk == 0, -1 - 0, np.where(kk == n_r, -1 - 1, ii + n_theta * kk))
+    fp = np.concatenate([fpr, fpc]).astype(np.int64)
+    own = np.concatenate([ownr, ownc]).astype(np.int64)
+    nbr = np.concatenate([nbrr, nbrc]).astype(np.int64)
     ci, ck = np.meshgrid(np.arange(n_theta), np.arange(n_r), indexing="xy")
     meta = dict(kind="o_mesh", n_theta=n_theta, n_r=n_r, ratio=q, radii=radii,
                 cell_i=ci.ravel(), cell_k=ck.ravel(), diameter=diameter, first=first * diameter)
-    return Mesh(points, np.asarray(fp, np.int64), np.asarray(own, np.int64),
-                np.asarray(nbr, np.int64), n_theta * n_r, dict(wall=0, farfield=1), meta)
+    return Mesh(points, fp, own, nbr, n_theta * n_r, dict(wall=0, farfield=1), meta)
 
 
 def shuffled(mesh: Mesh, seed: int) -> Mesh:

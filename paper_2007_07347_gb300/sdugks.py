@@ -79,6 +79,7 @@ def lib():
                 "sdugks_get_state": [P, P, P],
                 "sdugks_set_state": [P, P, P],
                 "sdugks_solver_info": [P, P],
+                "sdugks_step_forces": [P, P],
                 "sdugks_residual_noalloc": [i64, P, P, P, P, P],
                 "sdugks_batch_create": [i64, i32, i32, P, P],
                 "sdugks_batch_footprint": [P, P, P],
@@ -190,6 +191,12 @@ class Solver:
     def step(self, n: int = 1):
         _ck(lib().sdugks_step(self._h, int(n)), "sdugks_step")
         return self
+
+    def step_forces(self) -> np.ndarray:
+        """One step; returns [64, 2]: the force of the fluid on each boundary patch."""
+        out = np.zeros((64, 2))
+        _ck(lib().sdugks_step_forces(self._h, _ptr(out)), "sdugks_step_forces")
+        return out
 
     def macros(self):
         rho = np.empty(self.n)
