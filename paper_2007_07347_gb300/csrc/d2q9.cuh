@@ -101,32 +101,26 @@ template <> struct Store<P_BF16DEV> {
 
 // IEEE-754 format conversions by field arithmetic on the integer pipe (the FP64 unit of
 // this GPU is narrow, and the FP32 kernels only need FP32 copies of the FP64 W).
-// binary64 -> binary32, mantissa truncated (error < 1 ulp of binary32); magnitudes
-// below the binary32 normal range become signed zero, above it infinity; NaN stays NaN.
+// binary64 -> binary32: the exponent field is rebiased by 896 and the mantissa is
+// truncated to 23 bits (error < 1 ulp of binary32); magnitudes below the binary32
+// normal range become signed zero.  Intended for the finite, normal-range conserved
+// variables: NaN and values beyond the binary32 range give unspecified finite results
+// (the FP64 W they come from keeps the NaN, which the residual reduction reports).
 __device__ __forceinline__ float d2f_fields(double d)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    const unsigned sign = hi & 0x80000000u;
-    const int ef = (int)((hi >> 20) & 0x7ffu);
-    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const int e = ef - 1023 + 127;
-    if (ef == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
-    if (e <= 0) return __uint_as_float(sign);
-    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
-    return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned s = hi & 0x80000000u, a = hi & 0x7fffffffu;
+    const unsigned m = ((a - 0x38000000u) << 3) | (lo >> 29);
+    return __uint_as_float(a < 0x38100000u ? s : (s | m));
 }
 // binary32 -> binary64, exact for normal numbers, zero, infinity and NaN; binary32
 // subnormals (below 1.2e-38) become signed zero.
 __device__ __forceinline__ double f2d_fields(float f)
 {
-    const unsigned u = __float_as_uint(f);
-    const unsigned sign = u & 0x80000000u, ef = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-    unsigned hi;
-    if (ef == 0) hi = sign;
-    else if (ef == 0xff) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
-    else hi = sign | ((ef - 127u + 1023u) << 20) | (m >> 3);
-    const unsigned lo = (ef == 0 || ef == 0xff) ? 0u : (m << 29);
+    const unsigned u = __float_as_uint(f), s = u & 0x80000000u, a = u & 0x7fffffffu;
+    unsigned hi = s | ((a >> 3) + 0x38000000u), lo = a << 29;
+    if (a < 0x00800000u) { hi = s; lo = 0u; }
+    if (a >= 0x7f800000u) { hi = s | 0x7ff00000u | (a > 0x7f800000u ? 0x80000u : 0u); lo = 0u; }
     return __hiloint2double((int)hi, (int)lo);
 }
 template <class R> __device__ __forceinline__ R from_f64(double d) { return R(d); }

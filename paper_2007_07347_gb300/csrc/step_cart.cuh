@@ -9,11 +9,12 @@
 // boundary rule or periodic with the opposite side.
 //
 // Phases of one block: (1) fbar+ of the block and halo into shared memory, one
-// position per thread; (2) gradients of the block and its first ring, one item per
-// position and velocity triple; (3) every interior face of the block once, one per
-// thread, its six non-zero fluxes (xi.n l f_b of the velocities that cross it) into
-// shared memory; (4) per cell: boundary faces, the flux sum, W^{n+1} in FP64 and
-// f^{n+1}.  `cart_tile` does one block; `k_step_cart` runs it for every block of one
+// position per thread; (2) every interior face of the block once, one per thread:
+// the characteristic reconstruction from the upwind cell, with that cell's LLSR
+// gradient evaluated on the spot as the two-point difference it reduces to on a
+// uniform grid, and the six non-zero fluxes (xi.n l f_b of the velocities that cross
+// the face) into shared memory; (3) per cell: boundary faces, the flux sum, W^{n+1}
+// in FP64 and f^{n+1}.  `cart_tile` does one block; `k_step_cart` runs it for every block of one
 // grid and `k_step_batch` for every (instance, block) item of a batch.
 #pragma once
 #include "d2q9.cuh"
@@ -38,8 +39,7 @@ template <int TX, int TY> __host__ __device__ constexpr int cart_threads() {
 
 template <int P, int TX, int TY> constexpr size_t cart_smem() {
     using S = CartShape<TX, TY>;
-    return sizeof(typename Store<P>::R) *
-           (size_t)(NQ * S::LX * S::LY + 2 * NQ * S::GX * S::GY + 6 * (S::NFX + S::NFY));
+    return sizeof(typename Store<P>::R) * (size_t)(NQ * S::LX * S::LY + 6 * (S::NFX + S::NFY));
 }
 
 // Velocities crossing a face of constant x (xi_x != 0) and of constant y, in slot order.
@@ -49,43 +49,68 @@ __device__ constexpr int YSLOT_A(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 
 // Step coefficients in the compute precision.
 template <class R> struct CartK;
 template <> struct CartK<double> {
-    double a, b, c, r, dt, dtV, hx, hy;
-    __device__ explicit CartK(const CartInst &m) : a(m.a), b(m.b), c(m.c), r(m.r), dt(m.dt), dtV(m.dtV), hx(m.dx), hy(m.dy) {}
+    double a, b, c, r, dt, dtV, hx, hy, ihx, ihy;
+    __device__ explicit CartK(const CartInst &m)
+        : a(m.a), b(m.b), c(m.c), r(m.r), dt(m.dt), dtV(m.dtV), hx(m.dx), hy(m.dy), ihx(1.0 / m.dx), ihy(1.0 / m.dy) {}
     __device__ static double par(const CartInst &m, int side, int i) { return m.side_par[side][i]; }
 };
 template <> struct CartK<float> {
-    float a, b, c, r, dt, dtV, hx, hy;
-    __device__ explicit CartK(const CartInst &m) : a(m.fa), b(m.fb), c(m.fc), r(m.fr), dt(m.fdt), dtV(m.fdtV), hx(m.fdx), hy(m.fdy) {}
+    float a, b, c, r, dt, dtV, hx, hy, ihx, ihy;
+    __device__ explicit CartK(const CartInst &m)
+        : a(m.fa), b(m.fb), c(m.fc), r(m.fr), dt(m.fdt), dtV(m.fdtV), hx(m.fdx), hy(m.fdy),
+          ihx((float)(1.0 / m.dx)), ihy((float)(1.0 / m.dy)) {}
     __device__ static float par(const CartInst &m, int side, int i) { return m.fside_par[side][i]; }
 };
 
+// LLSR gradient stencil of one staged cell on a uniform grid.  Over the face
+// neighbours that exist, sum_k d_k (phi_k - phi) / sum_k d_k^2 is the central
+// difference (phi_E - phi_W) / 2h when both exist and the one-sided difference
+// otherwise; oE/oW/oN/oS are the staged offsets (0 for a missing neighbour) and ax, ay
+// the factors 1/(2h) or 1/h.
+template <class R> struct Sten {
+    int oE, oW, oN, oS;
+    R ax, ay;
+};
+
+// fbar+_j + (x_f - xi dt - x_j) . sigma_j for velocity a from staged cell l, with
+// (px, py) = x_f - xi dt - x_j; UX / UY drop a component whose factor is zero
+template <int a, bool UX, bool UY, class R>
+__device__ __forceinline__ R cart_extrap(const R *s_fbp, int l, const Sten<R> &st, R px, R py, int LXY)
+{
+    const R *f = s_fbp + a * LXY;
+    R v = f[l];
+    if (UX) v += (px * st.ax) * (f[l + st.oE] - f[l + st.oW]);
+    if (UY) v += (py * st.ay) * (f[l + st.oN] - f[l + st.oS]);
+    return v;
+}
+
 // Interface distribution on a face between cell L (below/left) and R (above/right),
-// along axis AX (0: face of constant x, 1: of constant y), from the staged fbar+ and
-// gradients; writes (xi . n_+ l) f_b of the six crossing velocities (n_+ = +x or +y).
+// along axis AX (0: face of constant x, 1: of constant y), from the staged fbar+ of
+// the two cells and their neighbours; writes (xi . n_+ l) f_b of the six crossing
+// velocities (n_+ = +x or +y).
 template <int AX, class R>
-__device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, const R *s_sig, int lL, int lR, int gL,
-                                                   int gR, const CartK<R> &k, int LXY, int GXY)
+__device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, int lL, int lR, const Sten<R> &sL,
+                                                   const Sten<R> &sR, const CartK<R> &k, int LXY)
 {
     // x_f - x_L = +h/2 along the axis, x_f - x_R = -h/2
     const R hl = AX == 0 ? R(0.5) * k.hx : R(0.5) * k.hy;
     R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
-#pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        const int sg = AX == 0 ? EX(a) : EY(a);      // sign of xi . n_+
-        const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
-        // (x_f - xi dt - x_u) for u = L and u = R
-        const R pxL = AX == 0 ? hl - ex : -ex, pyL = AX == 0 ? -ey : hl - ey;
-        const R pxR = AX == 0 ? -hl - ex : -ex, pyR = AX == 0 ? -ey : -hl - ey;
-        R A = R(0), B = R(0);
-        if (sg >= 0)
-            A = s_fbp[a * LXY + lL] + pxL * s_sig[(2 * a) * GXY + gL] + pyL * s_sig[(2 * a + 1) * GXY + gL];
-        if (sg <= 0)
-            B = s_fbp[a * LXY + lR] + pxR * s_sig[(2 * a) * GXY + gR] + pyR * s_sig[(2 * a + 1) * GXY + gR];
-        fbar[a] = sg > 0 ? A : (sg < 0 ? B : R(0.5) * (A + B));
-        w0 += fbar[a];
-        if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
-        if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+#define SDUGKS_FACE_ALPHA(a)                                                                        \
+    {                                                                                               \
+        constexpr int sg = AX == 0 ? EX(a) : EY(a);   /* sign of xi . n_+ */                        \
+        const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;                                         \
+        R A = R(0), B = R(0);                                                                       \
+        constexpr bool ux = AX == 0 || EX(a) != 0, uy = AX == 1 || EY(a) != 0;                     \
+        if (sg >= 0) A = cart_extrap<a, ux, uy, R>(s_fbp, lL, sL, AX == 0 ? hl - ex : -ex, AX == 0 ? -ey : hl - ey, LXY); \
+        if (sg <= 0) B = cart_extrap<a, ux, uy, R>(s_fbp, lR, sR, AX == 0 ? -hl - ex : -ex, AX == 0 ? -ey : -hl - ey, LXY); \
+        fbar[a] = sg > 0 ? A : (sg < 0 ? B : R(0.5) * (A + B));                                     \
+        w0 += fbar[a];                                                                              \
+        if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];                         \
+        if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];                         \
     }
+    SDUGKS_FACE_ALPHA(0) SDUGKS_FACE_ALPHA(1) SDUGKS_FACE_ALPHA(2) SDUGKS_FACE_ALPHA(3) SDUGKS_FACE_ALPHA(4)
+    SDUGKS_FACE_ALPHA(5) SDUGKS_FACE_ALPHA(6) SDUGKS_FACE_ALPHA(7) SDUGKS_FACE_ALPHA(8)
+#undef SDUGKS_FACE_ALPHA
     R ux, uy, feqb[NQ];
     vel_of<R>(w0, w1, w2, ux, uy);
     feq9f<R>(w0, ux, uy, feqb);
@@ -103,9 +128,9 @@ __device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, co
 // `side`: adds the outward flux (xi . n l) f_b of every crossing velocity to F
 // (Sec. III rules).
 template <int D, class R, bool DIAG>
-__device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, const R *s_sig, int lme, int gme,
+__device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int lme, const Sten<R> &st,
                                                    const CartInst &m, int side, const CartK<R> &k, const R fn[NQ],
-                                                   const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY, int GXY)
+                                                   const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY)
 {
     const R nx = D == 0 ? k.hy : (D == 1 ? -k.hy : R(0));
     const R ny = D == 2 ? k.hx : (D == 3 ? -k.hx : R(0));
@@ -120,23 +145,27 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, cons
     R feqb[NQ];
     feq9f<R>(rb, ubx, uby, feqb);
     R px_ = R(0), py_ = R(0);
-#pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        const int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));
-        if (sg == 0) continue;
-        const R s = xdot<R>(a, nx, ny);
-        R fb;
-        if (sg < 0) {
-            fb = feqb[a] + (fn[a] - feqn[a]);          // non-equilibrium extrapolation
-        } else {
-            const R A = s_fbp[a * LXY + lme] + (rx - R(EX(a)) * k.dt) * s_sig[(2 * a) * GXY + gme] +
-                        (ry - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * GXY + gme];
-            fb = (A + k.b * feqb[a]) * k.c;
-        }
-        F[a] += s * fb;
-        px_ += R(EX(a)) * (s * fb);
-        py_ += R(EY(a)) * (s * fb);
+#define SDUGKS_BFACE_ALPHA(a)                                                                       \
+    {                                                                                               \
+        constexpr int sg = (D < 2) ? (D == 0 ? EX(a) : -EX(a)) : (D == 2 ? EY(a) : -EY(a));         \
+        if (sg != 0) {                                                                              \
+            const R s = xdot<R>(a, nx, ny);                                                         \
+            R fb;                                                                                   \
+            if (sg < 0) {                                                                           \
+                fb = feqb[a] + (fn[a] - feqn[a]);   /* non-equilibrium extrapolation */             \
+            } else {                                                                                \
+                constexpr bool ux = D < 2 || EX(a) != 0, uy = D >= 2 || EY(a) != 0;                 \
+                const R A = cart_extrap<a, ux, uy, R>(s_fbp, lme, st, rx - R(EX(a)) * k.dt, ry - R(EY(a)) * k.dt, LXY); \
+                fb = (A + k.b * feqb[a]) * k.c;                                                     \
+            }                                                                                       \
+            F[a] += s * fb;                                                                         \
+            px_ += R(EX(a)) * (s * fb);                                                             \
+            py_ += R(EY(a)) * (s * fb);                                                             \
+        }                                                                                           \
     }
+    SDUGKS_BFACE_ALPHA(0) SDUGKS_BFACE_ALPHA(1) SDUGKS_BFACE_ALPHA(2) SDUGKS_BFACE_ALPHA(3) SDUGKS_BFACE_ALPHA(4)
+    SDUGKS_BFACE_ALPHA(5) SDUGKS_BFACE_ALPHA(6) SDUGKS_BFACE_ALPHA(7) SDUGKS_BFACE_ALPHA(8)
+#undef SDUGKS_BFACE_ALPHA
     if (DIAG && m.force) {       // diagnostic steps only: momentum leaving the fluid through this side
         atomicAdd(&m.force[2 * side], to_f64<R>(px_));
         atomicAdd(&m.force[2 * side + 1], to_f64<R>(py_));
@@ -153,11 +182,9 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     using T = typename Store<P>::T;
     using SP = Store<P>;
     using S = CartShape<TX, TY>;
-    constexpr int LXY = S::LX * S::LY, GXY = S::GX * S::GY;
-    constexpr int NTH = cart_threads<TX, TY>();
+    constexpr int LXY = S::LX * S::LY;
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][LX]
-    R *s_sig = s_fbp + NQ * LXY;                     // [2 NQ][GY][GX]
-    R *s_fx = s_sig + 2 * NQ * GXY;                  // [6][NFX] fluxes through faces of constant x
+    R *s_fx = s_fbp + NQ * LXY;                      // [6][NFX] fluxes through faces of constant x
     R *s_fy = s_fx + 6 * S::NFX;                     // [6][NFY]
 
     const T *__restrict__ fin = static_cast<const T *>(m.f[par]);
@@ -183,6 +210,17 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             gj = (gj + ny) % ny;
         }
         return gi + pitch * gj;
+    };
+    // gradient stencil of the staged cell at block position (bi, bj) (a domain cell)
+    auto sten = [&](int bi, int bj) {
+        const int ci = x0 + bi, cj = y0 + bj;
+        const bool hE = px || ci + 1 < nx, hW = px || ci - 1 >= 0;
+        const bool hN = py || cj + 1 < ny, hS = py || cj - 1 >= 0;
+        Sten<R> st;
+        st.oE = hE ? 1 : 0; st.oW = hW ? -1 : 0; st.oN = hN ? S::LX : 0; st.oS = hS ? -S::LX : 0;
+        st.ax = (hE && hW) ? R(0.5) * k.ihx : k.ihx;
+        st.ay = (hN && hS) ? R(0.5) * k.ihy : k.ihy;
+        return st;
     };
     auto macro = [&](double w0, double w1, double w2, R &rho, R &ux, R &uy) {
         rho = from_f64<R>(w0);
@@ -240,43 +278,14 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     }
     __syncthreads();
 
-    // ---- phase 2: gradient on the block and its first ring, one item per position and
-    // velocity triple.  LLSR over the existing face neighbours of a uniform grid:
-    // sigma_x = sum_k dx_k (phi_k - phi) / sum_k dx_k^2.
-    for (int it = tid; it < 3 * GXY; it += NTH) {
-        const int q = it % GXY, grp = it / GXY;
-        const int bi = q % S::GX - 1, bj = q / S::GX - 1;
-        if (cell_of(bi, bj) < 0) continue;
-        const int ci = x0 + bi, cj = y0 + bj;
-        const bool hasE = px || ci + 1 < nx, hasW = px || ci - 1 >= 0;
-        const bool hasN = py || cj + 1 < ny, hasS = py || cj - 1 >= 0;
-        const int l = (bj + 2) * S::LX + (bi + 2);
-        const R nxk = R((hasE ? 1 : 0) + (hasW ? 1 : 0)), nyk = R((hasN ? 1 : 0) + (hasS ? 1 : 0));
-        const bool singular = nxk == R(0) || nyk == R(0);
-        const R ax = singular ? R(0) : R(1) / (nxk * k.hx * k.hx), ay = singular ? R(0) : R(1) / (nyk * k.hy * k.hy);
-        const R cE = hasE ? k.hx : R(0), cW = hasW ? k.hx : R(0), cN = hasN ? k.hy : R(0), cS = hasS ? k.hy : R(0);
-        const int oE = hasE ? 1 : 0, oW = hasW ? -1 : 0, oN = hasN ? S::LX : 0, oS = hasS ? -S::LX : 0;
-#pragma unroll
-        for (int u = 0; u < 3; u++) {
-            const int a = 3 * grp + u;
-            const R *f = s_fbp + a * LXY;
-            const R p = f[l];
-            const R bx = cE * (f[l + oE] - p) - cW * (f[l + oW] - p);
-            const R by = cN * (f[l + oN] - p) - cS * (f[l + oS] - p);
-            s_sig[(2 * a) * GXY + q] = ax * bx;
-            s_sig[(2 * a + 1) * GXY + q] = ay * by;
-        }
-    }
-    __syncthreads();
-
-    // ---- phase 3: every interior face of the block once, one per thread
+    // ---- phase 2: every interior face of the block once, one per thread
     if (tid < S::NFX) {
         // face of constant x between block columns fi-1 (L) and fi (R), row fj
         const int fi = tid % (TX + 1), fj = tid / (TX + 1);
         if (cell_of(fi - 1, fj) >= 0 && cell_of(fi, fj) >= 0) {
-            const int lL = (fj + 2) * S::LX + (fi + 1), gL = (fj + 1) * S::GX + fi;
+            const int lL = (fj + 2) * S::LX + (fi + 1);
             R fl[6];
-            cart_interior_face<0, R>(fl, s_fbp, s_sig, lL, lL + 1, gL, gL + 1, k, LXY, GXY);
+            cart_interior_face<0, R>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
 #pragma unroll
             for (int r = 0; r < 6; r++) s_fx[r * S::NFX + tid] = fl[r];
         }
@@ -284,9 +293,9 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         // face of constant y between block rows fj-1 (below) and fj (above), column fi
         const int qq = tid - S::NFX, fi = qq % TX, fj = qq / TX;
         if (cell_of(fi, fj - 1) >= 0 && cell_of(fi, fj) >= 0) {
-            const int lB = (fj + 1) * S::LX + (fi + 2), gB = fj * S::GX + (fi + 1);
+            const int lB = (fj + 1) * S::LX + (fi + 2);
             R fl[6];
-            cart_interior_face<1, R>(fl, s_fbp, s_sig, lB, lB + S::LX, gB, gB + S::GX, k, LXY, GXY);
+            cart_interior_face<1, R>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
 #pragma unroll
             for (int r = 0; r < 6; r++) s_fy[r * S::NFY + qq] = fl[r];
         }
@@ -294,11 +303,10 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     __syncthreads();
 
     if (active) {
-        // ---- phase 4: flux sum over the own cell's faces (order -x, +x, -y, +y)
+        // ---- phase 3: flux sum over the own cell's faces (order -x, +x, -y, +y)
         R F[NQ];
 #pragma unroll
         for (int a = 0; a < NQ; a++) F[a] = R(0);
-        const int gme = (tj + 1) * S::GX + (ti + 1);
         const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
         const bool inW = px || gi - 1 >= 0, inE = px || gi + 1 < nx;
         const bool inS = py || gj - 1 >= 0, inN = py || gj + 1 < ny;
@@ -308,25 +316,25 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
         } else {
-            cart_boundary_face<1, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inE) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NFX + fW + 1];
         } else {
-            cart_boundary_face<0, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inS) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NFY + fS];
         } else {
-            cart_boundary_face<3, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inN) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NFY + fS + TX];
         } else {
-            cart_boundary_face<2, R, DIAG>(F, s_fbp, s_sig, lme, gme, m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY, GXY);
+            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
 
         // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)
