@@ -196,9 +196,16 @@ def cpu_baseline(case, seconds: float):
         if el >= seconds:
             break
     mlups = case.mesh.n_cells * 9 * steps / el / 1e6
+    # the same oracle on one thread, a short sample
+    O.set_threads(1)
+    t0 = time.perf_counter()
+    O.run(case, st, 2)
+    el1 = time.perf_counter() - t0
+    O.set_threads(threads)
     return {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
             "sample": f"{steps} time steps of the same {case.mesh.n_cells}-cell cavity from rest "
-                      f"({el:.1f} s, {threads} OpenMP threads, FP64)"}
+                      f"({el:.1f} s, {threads} OpenMP threads, FP64)",
+            "single_thread_value": case.mesh.n_cells * 9 * 2 / el1 / 1e6}
 
 
 # ----------------------------------------------------------------------------- arms
