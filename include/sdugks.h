@@ -75,7 +75,9 @@ typedef struct sdugks_params {
     double dt;           /* time step, > 0                                         */
     int32_t precision;   /* SDUGKS_FP64 | SDUGKS_FP32 | SDUGKS_FP32_BF16DEV         */
     int32_t kernel;      /* SDUGKS_KERNEL_*                                        */
-    int32_t tile_cells;  /* tiled kernel: interior cells per tile (32..256), 0 = auto */
+    int32_t tile_cells;  /* tiled kernel: cells per tile (16..128); Cartesian kernel (FP32 and
+                            bf16 storage): 256, 224 or 128 for 16x16, 16x14 or 16x8 blocks;
+                            0 = chosen from the grid size (Cartesian) or 128 (tiled) */
     int32_t graph_steps; /* steps per captured CUDA graph in sdugks_step, 0 = auto, <0 = off */
 } sdugks_params;
 

@@ -365,6 +365,7 @@ struct sdugks_solver {
     int32_t *perm = nullptr;        // q-th listed cell -> user id
     int32_t *loc = nullptr;         // q-th listed cell -> internal offset (nullptr: q)
     CartInst ci{};
+    int cart_shape = 0;             // Cartesian block shape (CART_TY)
     double *vol = nullptr, *snap = nullptr, *partial = nullptr, *red = nullptr;
     State st{};
     int n_red_blocks = 1;
@@ -391,7 +392,7 @@ static cudaError_t launch_one(sdugks_solver *s, cudaStream_t st)
     const int a = s->cur;
     cudaError_t e;
     if (s->kernel == SDUGKS_KERNEL_CARTESIAN)
-        e = launch_step_cart(s->p.precision, s->ci, a, st);
+        e = launch_step_cart(s->p.precision, s->cart_shape, s->ci, a, st);
     else if (s->p.precision == P_FP64)
         e = launch_step_tiled_fp64(s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
     else
@@ -615,6 +616,29 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     chk((cudaError_t)prepare(prec, SDUGKS_KERNEL_CARTESIAN), "kernel attributes");
     if (rc2) { sdugks_solver_destroy(s); return rc2; }
     fill_coefs(s->coefs, m, prm->tau, prm->dt);
+    // Block shape: tile_cells 256/224/128 picks 16x16/16x14/16x8; 0 picks by a cost
+    // model -- blocks per SM (rounded up) times the work of one block (staged
+    // positions plus faces) -- so that small grids fill every SM evenly.  The
+    // choice depends only on the grid size and the device, never on timings.
+    {
+        int n_sm = 1;
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
+        s->cart_shape = 0;
+        if (prec != P_FP64) {
+            double best = 1e300;
+            for (int sh = 0; sh < CART_SHAPES; sh++) {
+                const int ty = CART_TY[sh];
+                if (prm->tile_cells && prm->tile_cells != 16 * ty) continue;
+                const int64_t tiles = (int64_t)((g.nx + 15) / 16) * ((g.ny + ty - 1) / ty);
+                const double work = (20.0 * (ty + 4) + 17.0 * ty + 16.0 * (ty + 1));
+                const double cost = (double)((tiles + n_sm - 1) / n_sm) * work;
+                if (cost < best - 1e-9) { best = cost; s->cart_shape = sh; }
+            }
+        }
+        const int ty = CART_TY[s->cart_shape];
+        s->n_tiles = ((g.nx + 15) / 16) * ((g.ny + ty - 1) / ty);
+        s->halo_cells = (int64_t)s->n_tiles * (20 * (ty + 4) - 16 * ty);
+    }
     *out = s;
     return SDUGKS_OK;
 }
@@ -630,8 +654,6 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown precision %d", prm->precision);
     if (prm->kernel < SDUGKS_KERNEL_AUTO || prm->kernel > SDUGKS_KERNEL_CARTESIAN)
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown kernel %d", prm->kernel);
-    if (prm->tile_cells != 0 && (prm->tile_cells < 16 || prm->tile_cells > TILE_MAX))
-        return fail(SDUGKS_ERR_INVALID_ARG, "tile_cells must be 0 or in [16, %d]", TILE_MAX);
 
     Faces F;
     int rc = merge_periodic(*m, F);
@@ -639,10 +661,18 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     const int64_t n = m->nc;
     if (prm->kernel != SDUGKS_KERNEL_TILED) {
         CartGrid cg;
-        if (detect_cart(*m, cg)) return create_cart(*m, cg, prm, stream, out);
+        if (detect_cart(*m, cg)) {
+            const int t = prm->tile_cells;
+            if (t != 0 && !(prm->precision != SDUGKS_FP64 && (t == 256 || t == 224 || t == 128)) &&
+                !(prm->precision == SDUGKS_FP64 && t == 256))
+                return fail(SDUGKS_ERR_INVALID_ARG, "Cartesian kernel: tile_cells must be 0, 256, 224 or 128 (FP64: 0 or 256)");
+            return create_cart(*m, cg, prm, stream, out);
+        }
         if (prm->kernel == SDUGKS_KERNEL_CARTESIAN)
             return fail(SDUGKS_ERR_INVALID_ARG, "not a uniform Cartesian grid: %s", cg.why.c_str());
     }
+    if (prm->tile_cells != 0 && (prm->tile_cells < 16 || prm->tile_cells > TILE_MAX))
+        return fail(SDUGKS_ERR_INVALID_ARG, "tile_cells must be 0 or in [16, %d]", TILE_MAX);
 
     // cell -> faces over the merged faces; slots in ascending merged face id, which
     // keeps the caller's face order, so per-cell sums do not depend on the tiling
@@ -1018,7 +1048,7 @@ extern "C" int sdugks_step_forces(sdugks_solver *s, double *force)
     if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
         CartInst ci = s->ci;
         ci.force = s->d_force;                 // per grid side
-        e = launch_step_cart(s->p.precision, ci, s->cur, s->stream);
+        e = launch_step_cart(s->p.precision, s->cart_shape, ci, s->cur, s->stream);
     } else {
         TiledMesh tm = s->tm;
         tm.force = s->d_force;                 // per patch
@@ -1126,7 +1156,7 @@ extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
     o->mesh_bytes_per_cell_step = s->mesh_bytes;
     o->kernel = s->kernel;
     o->precision = s->p.precision;
-    o->tile_cells = s->kernel == SDUGKS_KERNEL_CARTESIAN ? 256 : (s->p.tile_cells ? s->p.tile_cells : TILE_MAX);
+    o->tile_cells = s->kernel == SDUGKS_KERNEL_CARTESIAN ? 16 * CART_TY[s->cart_shape] : (s->p.tile_cells ? s->p.tile_cells : TILE_MAX);
     o->nx = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.nx : 0;
     o->ny = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.ny : 0;
     return SDUGKS_OK;

@@ -96,7 +96,11 @@ cudaError_t launch_step_tiled_fp64(const TiledMesh &m, const Coefs &c, const voi
                                    const double *W_in, double *W_out, cudaStream_t st);
 cudaError_t prepare_tiled_fp32(int prec);
 cudaError_t prepare_cart(int prec);
-cudaError_t launch_step_cart(int prec, const CartInst &m, int parity, cudaStream_t st);
+// block shapes of the Cartesian kernel: 0 = 16x16, 1 = 16x14, 2 = 16x8 (FP64: 16x16 only)
+constexpr int CART_SHAPES = 3;
+constexpr int CART_TY[CART_SHAPES] = {16, 14, 8};
+cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, int parity, cudaStream_t st);
+int cart_shape_occupancy(int prec, int shape);   // resident CTAs per SM
 // batched: every (instance, tile) item of the list, grid-stride over a fixed grid
 cudaError_t prepare_batch(int prec);
 cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,

@@ -370,7 +370,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 }
 
 template <int P, int TX, int TY>
-__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : 2)
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : (cart_threads<TX, TY>() <= 320 ? 4 : 2))
 k_step_cart(const CartInst m, int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -103,7 +103,7 @@ def test_tile_construction_passes_host_index_checks(make, tile):
     import torch
     case = make()
     try:
-        s = S.Solver.from_case(case, "fp32", tile_cells=tile)
+        s = S.Solver.from_case(case, "fp32", tile_cells=tile, kernel=S.KERNEL_TILED)
     except S.SdugksError as e:
         assert e.name == "CUDA" and not torch.cuda.is_available(), str(e)
     else:

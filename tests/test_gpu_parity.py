@@ -291,3 +291,21 @@ def test_wall_forces_balance_momentum(kernel):
     dP = vol @ (W1[:, 1:] - W0[:, 1:])
     np.testing.assert_allclose(F.sum(0), -dP / case.dt, rtol=1e-9, atol=1e-12 * np.abs(F).max())
     assert abs(F[2, 0]) > 0                      # the moving lid (patch 2) drags the fluid
+
+
+@pytest.mark.parametrize("tile", [256, 224, 128])
+def test_cartesian_block_shapes_agree(tile):
+    """The 16x16, 16x14 and 16x8 block shapes of the Cartesian kernel (chosen by the
+    cost model or by tile_cells) give the same FP32 results to round-off (one 16x8
+    solve is the reference), and the shape the model picks is reported."""
+    S = _S()
+    case = M.cavity(100, Re=400.0)
+    ref = S.Solver.from_case(case, "fp32", tile_cells=128).init()
+    ref.step(200)
+    s = S.Solver.from_case(case, "fp32", tile_cells=tile).init()
+    assert s.info()["tile_cells"] == tile
+    s.step(200)
+    r0, u0 = ref.macros()
+    r1, u1 = s.macros()
+    assert rel_l2(u1, u0) <= 1e-5
+    assert S.Solver.from_case(M.cavity(256), "fp32").info()["tile_cells"] == 224   # 304 blocks = 2 per SM
