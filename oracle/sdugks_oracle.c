@@ -33,7 +33,7 @@
 
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_MESH = -2, OR_ERR_BC = -3, OR_ERR_NOMEM = -4 };
 enum { KIND_UNSET = 0, KIND_PERIODIC = 1, KIND_WALL = 2, KIND_MOVING_WALL = 3,
-       KIND_FARFIELD = 4, KIND_OUTLET = 5 };
+       KIND_FARFIELD = 4, KIND_OUTLET = 5, KIND_SYMMETRY = 6 };
 
 /* D2Q9 velocity set and weights (reading A1: the paper names no set; the continuum
  * cases use the nine-velocity lattice with c = 1, c_s^2 = 1/3).
@@ -43,6 +43,10 @@ static const double XI[NQ][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1},
 static const double WGT[NQ] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0;
+/* Mirror images of the velocities in a line of constant x (xi_x -> -xi_x) and of
+ * constant y (xi_y -> -xi_y), by index. */
+static const int MIRROR_X[NQ] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
+static const int MIRROR_Y[NQ] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
 /* Tangential tie: |xi . n l| <= TIE counts as neither inflow nor outflow. */
 static const double TIE = 1e-12;
 
@@ -86,8 +90,11 @@ typedef struct {
     double *nl;     /* [nf][2] unit normal times length, pointing out of the owner */
     double *vol;    /* [nc] cell area                                              */
     double *xc;     /* [nc][2] cell centroid                                       */
-    int64_t *ghost; /* [nf] periodic faces: the cell on the far side, else -1      */
-    double *gpos;   /* [nf][2] position of that cell seen from this side           */
+    int64_t *ghost; /* [nf] periodic faces: the cell on the far side; symmetry
+                       faces: the owner (the ghost is its mirror image); else -1    */
+    double *gpos;   /* [nf][2] position of that (ghost) cell seen from this side    */
+    int *mir;       /* [nf] symmetry faces: 1 = mirror in x (normal along x),
+                       2 = mirror in y; 0 for every other face                      */
     int64_t *cs, *cl; /* cell -> faces, ascending face id                          */
     double *ainv;   /* [nc][3] inverse of the LLSR normal matrix: xx, xy, yy       */
 } omesh;
@@ -95,7 +102,7 @@ typedef struct {
 static void omesh_free(omesh *m)
 {
     free(m->xf); free(m->nl); free(m->vol); free(m->xc); free(m->ghost); free(m->gpos);
-    free(m->cs); free(m->cl); free(m->ainv);
+    free(m->mir); free(m->cs); free(m->cl); free(m->ainv);
     memset(m, 0, sizeof(*m));
 }
 
@@ -163,10 +170,12 @@ static int omesh_build(omesh *m, int64_t np, const double *xy, int64_t nf, const
     m->xc = malloc(sizeof(double) * 2 * nc);
     m->ghost = malloc(sizeof(int64_t) * nf);
     m->gpos = calloc(2 * nf, sizeof(double));
+    m->mir = calloc(nf, sizeof(int));
     m->cs = calloc(nc + 1, sizeof(int64_t));
     m->cl = malloc(sizeof(int64_t) * 2 * nf);
     m->ainv = calloc(3 * nc, sizeof(double));
-    if (!m->xf || !m->nl || !m->vol || !m->xc || !m->ghost || !m->gpos || !m->cs || !m->cl || !m->ainv) {
+    if (!m->xf || !m->nl || !m->vol || !m->xc || !m->ghost || !m->gpos || !m->mir || !m->cs || !m->cl ||
+        !m->ainv) {
         omesh_free(m);
         return OR_ERR_NOMEM;
     }
@@ -231,6 +240,25 @@ static int omesh_build(omesh *m, int64_t np, const double *xy, int64_t nf, const
         m->ghost[f] = other;
         m->gpos[2 * f] = m->xc[2 * other] - sx;
         m->gpos[2 * f + 1] = m->xc[2 * other + 1] - sy;
+    }
+    /* Symmetric boundary (Sec. III): a ghost cell mirrors the owner in the face line,
+     * x_g = x_o + 2 ((x_f - x_o) . N) N, with the owner's density and the mirrored
+     * velocity.  Mirrored velocities must be lattice velocities, so the face must be
+     * a line of constant x or constant y. */
+    for (int64_t f = 0; f < nf; f++) {
+        if (nbr[f] >= 0) continue;
+        int p = (int)(-1 - nbr[f]);
+        if (bck[p] != KIND_SYMMETRY) continue;
+        double len = hypot(m->nl[2 * f], m->nl[2 * f + 1]);
+        double Nx = m->nl[2 * f] / len, Ny = m->nl[2 * f + 1] / len;
+        if (fabs(Ny) <= 1e-12) m->mir[f] = 1;
+        else if (fabs(Nx) <= 1e-12) m->mir[f] = 2;
+        else { omesh_free(m); return OR_ERR_BC; }
+        const double *xo = &m->xc[2 * own[f]];
+        double dn = (m->xf[2 * f] - xo[0]) * Nx + (m->xf[2 * f + 1] - xo[1]) * Ny;
+        m->ghost[f] = own[f];
+        m->gpos[2 * f] = xo[0] + 2.0 * dn * Nx;
+        m->gpos[2 * f + 1] = xo[1] + 2.0 * dn * Ny;
     }
     /* LLSR normal matrix sum_k d d^T and its inverse (Cramer) */
     for (int64_t c = 0; c < nc; c++) {
@@ -303,7 +331,11 @@ static void llsr(const omesh *m, const double *phi, int nv, double *grad)
                 } else {
                     continue;
                 }
-                double dphi = phi[k * nv + v] - phi[c * nv + v];
+                /* a symmetry ghost holds the owner's value of the mirrored velocity
+                 * (nv == NQ: the nine velocity fields; a single field mirrors to itself) */
+                int vk = v;
+                if (m->mir[f] && nv == NQ) vk = m->mir[f] == 1 ? MIRROR_X[v] : MIRROR_Y[v];
+                double dphi = phi[k * nv + vk] - phi[c * nv + v];
                 bx += (px - m->xc[2 * c]) * dphi;
                 by += (py - m->xc[2 * c + 1]) * dphi;
             }
@@ -387,6 +419,7 @@ static void one_step(const omesh *m, double tau, double dt, double *f, double *W
             /* interior (or periodic) face: upwind characteristic reconstruction */
             const double *xk = k >= 0 ? &m->xc[2 * k] : &m->gpos[2 * fc];
             const double *xo = &m->xc[2 * o];
+            const int mir = k >= 0 ? 0 : m->mir[fc];
             double fbar[NQ], Wb[3] = {0, 0, 0}, feqb[NQ];
             for (int a = 0; a < NQ; a++) {
                 double s = XI[a][0] * n[0] + XI[a][1] * n[1];
@@ -394,8 +427,15 @@ static void one_step(const omesh *m, double tau, double dt, double *f, double *W
                 double px = xb[0] - XI[a][0] * dt, py = xb[1] - XI[a][1] * dt;
                 double from_o = w->fbp[NQ * o + a] + (px - xo[0]) * w->sig[2 * (NQ * o + a)] +
                                 (py - xo[1]) * w->sig[2 * (NQ * o + a) + 1];
-                double from_k = w->fbp[NQ * kk + a] + (px - xk[0]) * w->sig[2 * (NQ * kk + a)] +
-                                (py - xk[1]) * w->sig[2 * (NQ * kk + a) + 1];
+                /* far cell: a real cell, a periodic image, or the mirror ghost, whose
+                 * fbar+ and gradient are the owner's for the mirrored velocity with the
+                 * gradient reflected (Sec. III, symmetric boundary) */
+                int ak = a;
+                double gsx = 1.0, gsy = 1.0;
+                if (mir == 1) { ak = MIRROR_X[a]; gsx = -1.0; }
+                else if (mir == 2) { ak = MIRROR_Y[a]; gsy = -1.0; }
+                double from_k = w->fbp[NQ * kk + ak] + (px - xk[0]) * (gsx * w->sig[2 * (NQ * kk + ak)]) +
+                                (py - xk[1]) * (gsy * w->sig[2 * (NQ * kk + ak) + 1]);
                 /* reading A5: upwind by the sign of xi.n, mean of both when tangential */
                 if (s > TIE) fbar[a] = from_o;
                 else if (s < -TIE) fbar[a] = from_k;

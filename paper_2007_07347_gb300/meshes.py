@@ -31,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BC_UNSET, BC_PERIODIC, BC_WALL, BC_MOVING_WALL, BC_FARFIELD, BC_OUTLET = 0, 1, 2, 3, 4, 5
+BC_UNSET, BC_PERIODIC, BC_WALL, BC_MOVING_WALL, BC_FARFIELD, BC_OUTLET, BC_SYMMETRY = 0, 1, 2, 3, 4, 5, 6
 
 
 @dataclass
@@ -112,6 +112,83 @@ def cartesian(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, *, jitter: flo
                 cell_i=ci.ravel(), cell_j=cj.ravel(),
                 cell_xy_nominal=np.stack([(ci.ravel() + 0.5) * dx, (cj.ravel() + 0.5) * dy], 1))
     return Mesh(points, fp, own, nbr, nx * ny, dict(bottom=0, right=1, top=2, left=3), meta)
+
+
+def mirror_y(mesh: Mesh, patch: int) -> Mesh:
+    """The mesh doubled by its mirror image in the horizontal line of boundary patch
+    ``patch``: cell c + n is the mirror of cell c, the patch faces become interior
+    faces between c and c + n (same face ids), and the mirrored copies of every
+    other face follow with the same boundary patches."""
+    y0s = mesh.points[np.unique(mesh.face_pts[mesh.neighbour == -1 - patch])][:, 1]
+    y0 = float(y0s[0])
+    assert np.all(y0s == y0), "patch is not a horizontal line"
+    n, npt = mesh.n_cells, mesh.n_points
+    on = mesh.points[:, 1] == y0
+    mp = np.where(on, np.arange(npt), npt + np.cumsum(~on) - 1)
+    q = mesh.points[~on].copy()
+    q[:, 1] = 2.0 * y0 - q[:, 1]
+    points = np.concatenate([mesh.points, q])
+    sym = mesh.neighbour == -1 - patch
+    nbr0 = np.where(sym, mesh.owner + n, mesh.neighbour)
+    keep = ~sym
+    fp_m = mp[mesh.face_pts[keep]]
+    own_m = mesh.owner[keep] + n
+    nbr_m = np.where(mesh.neighbour[keep] >= 0, mesh.neighbour[keep] + n, mesh.neighbour[keep])
+    meta = dict(kind="mirror_y", base=mesh.meta.get("kind"), y0=y0)
+    return Mesh(points, np.concatenate([mesh.face_pts, fp_m]).astype(np.int64),
+                np.concatenate([mesh.owner, own_m]).astype(np.int64),
+                np.concatenate([nbr0, nbr_m]).astype(np.int64), 2 * n,
+                {k: v for k, v in mesh.patches.items() if v != patch}, meta)
+
+
+def stretched(xs: np.ndarray, ys: np.ndarray) -> Mesh:
+    """Tensor-product quad mesh on the (increasing) point coordinates xs, ys: cells of
+    varying size, so it is not a uniform grid.  Patches and numbering as cartesian()."""
+    nx, ny = len(xs) - 1, len(ys) - 1
+    m = cartesian(nx, ny, 1.0, 1.0)
+    I, J = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    m.points = np.stack([np.asarray(xs, np.float64)[I.ravel()], np.asarray(ys, np.float64)[J.ravel()]], 1)
+    xc = 0.5 * (xs[:-1] + xs[1:])
+    yc = 0.5 * (ys[:-1] + ys[1:])
+    m.meta = dict(kind="stretched", nx=nx, ny=ny, cell_i=m.meta["cell_i"], cell_j=m.meta["cell_j"],
+                  cell_xy_nominal=np.stack([xc[m.meta["cell_i"]], yc[m.meta["cell_j"]]], 1))
+    return m
+
+
+def _graded(a: float, b: float, h_a: float, n: int) -> np.ndarray:
+    """n cells from a to b, first cell h_a at a, geometric growth (ratio by bisection)."""
+    if abs(h_a * n - (b - a)) < 1e-12 * (b - a):
+        return np.linspace(a, b, n + 1)
+    q = o_mesh_ratio(n, 0.0, h_a, b - a)
+    x = a + h_a * (q ** np.arange(n + 1) - 1.0) / (q - 1.0)
+    x[-1] = b
+    return x
+
+
+def flat_plate(nx_up: int = 24, nx_plate: int = 72, ny: int = 64, *, U: float = 0.1, Re_L: float = 1e5,
+               L: float = 100.0, x_up: float = 50.0, height: float = 100.0, h_le: float = 0.05,
+               h_wall: float = 0.02, cfl: float = 0.5) -> Case:
+    """Laminar flow over a flat plate of length L on [-x_up, L] x [0, height]: far-field
+    inflow at x = -x_up and at the top, an outlet at x = L, a symmetry line on y = 0
+    upstream of the leading edge and a no-slip wall (the plate) along 0 <= x <= L.
+    Cells cluster at the leading edge (first width h_le on both sides of x = 0) and
+    at the wall (first height h_wall).  Patches: 0 symmetry, 1 outlet, 2 top, 3 inflow,
+    4 plate."""
+    xs = np.concatenate([-_graded(0.0, x_up, h_le, nx_up)[::-1], _graded(0.0, L, h_le, nx_plate)[1:]])
+    ys = _graded(0.0, height, h_wall, ny)
+    m = stretched(xs, ys)
+    # split the bottom patch at the leading edge: faces with both points at x >= 0
+    bot = np.where(m.neighbour == -1 - 0)[0]
+    on_plate = m.points[m.face_pts[bot]][:, :, 0].min(1) >= 0.0
+    m.neighbour[bot[on_plate]] = -1 - 4
+    m.patches = dict(symmetry=0, outlet=1, top=2, inflow=3, plate=4)
+    nu = U * L / Re_L
+    dmin = min(h_le, h_wall)
+    bcs = [(0, BC_SYMMETRY, _bc_params()), (1, BC_OUTLET, _bc_params()),
+           (2, BC_FARFIELD, _bc_params(1.0, U, 0.0)), (3, BC_FARFIELD, _bc_params(1.0, U, 0.0)),
+           (4, BC_WALL, _bc_params())]
+    return Case(f"flat_plate_{len(xs) - 1}x{ny}", m, bcs, tau=3.0 * nu, dt=cfl * dmin / math.sqrt(2.0),
+                u0=(U, 0.0), meta=dict(U=U, Re_L=Re_L, L=L, xs=xs, ys=ys, cfl=cfl))
 
 
 def o_mesh_ratio(n_r: int, r0: float, first: float, r_far: float) -> float:

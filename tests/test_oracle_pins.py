@@ -294,3 +294,85 @@ def test_residual_closed_form():
     assert mass == 10.0
     eps0, _ = O.residual(W, np.tile([1.0, 0.0, 0.0], (n, 1)))
     assert math.isinf(eps0)
+
+
+# ------------------------------------------------------------------ symmetric boundary
+# Sec. III: a symmetric boundary puts a ghost cell at the mirror image of the inner
+# cell, with the same density and the mirrored velocity.  Pinned against the scheme
+# without that rule: the same flow on the mirror-doubled mesh, where the symmetry
+# line is an ordinary row of interior faces.
+
+def _channel_half(jitter, seed):
+    return M.cartesian(8, 4, 8.0, 4.0, jitter=jitter, seed=seed)
+
+
+@pytest.mark.parametrize("jitter,seed", [(0.0, None), (0.2, 3)])
+def test_symmetry_line_equals_the_mirrored_domain(jitter, seed):
+    """Periodic channel with a moving bottom wall and a symmetry line on top against
+    the mirror-doubled channel (walls at both ends) from a mirror-symmetric start:
+    the lower half of the doubled flow is the half-domain flow."""
+    half = _channel_half(jitter, seed)
+    full = M.mirror_y(half, half.patches["top"])
+    n = half.n_cells
+    per = [(3, M.BC_PERIODIC, (1, 8.0, 0.0)), (1, M.BC_PERIODIC, (3, -8.0, 0.0))]
+    wall = [(0, M.BC_MOVING_WALL, (0.05, 0.0, 0.0))]
+    c_half = M.Case("half", half, per + wall + [(2, M.BC_SYMMETRY, (0.0, 0.0, 0.0))], tau=0.05, dt=0.2)
+    c_full = M.Case("full", full, per + wall, tau=0.05, dt=0.2)
+    xy = half.meta["cell_xy_nominal"]
+    X, Y = 2 * np.pi * xy[:, 0] / 8.0, np.pi * xy[:, 1] / 4.0
+    rho = 1.0 + 0.02 * np.cos(X) * np.cos(Y)
+    u = np.stack([0.03 * np.sin(X) + 0.01 * Y, 0.02 * np.sin(X) * np.sin(0.5 * Y)], 1)
+    s_half = O.init(n, rho=rho, u=u)
+    u_m = u.copy()
+    u_m[:, 1] *= -1.0
+    s_full = O.init(2 * n, rho=np.concatenate([rho, rho]), u=np.concatenate([u, u_m]))
+    O.run(c_half, s_half, 40)
+    O.run(c_full, s_full, 40)
+    assert np.abs(s_half.W[:, 2]).max() > 1e-4                 # normal velocity near the line
+    np.testing.assert_allclose(s_half.f, s_full.f[:n], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s_half.W, s_full.W[:n], rtol=0, atol=1e-13)
+    # the doubled flow itself stays mirror-symmetric
+    mx = np.array([0, 1, 4, 3, 2, 8, 7, 6, 5])
+    np.testing.assert_allclose(s_full.f[n:], s_full.f[:n][:, mx], rtol=0, atol=1e-13)
+
+
+def test_symmetry_uniform_stream_is_fixed_point():
+    """A uniform stream along two symmetry lines (periodic in x) is a fixed point."""
+    m = M.cartesian(6, 5, 6.0, 5.0, jitter=0.2, seed=8)
+    bcs = [(3, M.BC_PERIODIC, (1, 6.0, 0.0)), (1, M.BC_PERIODIC, (3, -6.0, 0.0)),
+           (0, M.BC_SYMMETRY, (0.0, 0.0, 0.0)), (2, M.BC_SYMMETRY, (0.0, 0.0, 0.0))]
+    case = M.Case("sym_stream", m, bcs, tau=0.07, dt=0.3)
+    st = O.init(m.n_cells, rho0=1.1, u0=(0.08, 0.0))
+    f0 = st.f.copy()
+    O.run(case, st, 40)
+    assert np.abs(st.f - f0).max() <= 1e-14 * np.abs(f0).max()
+
+
+def test_symmetry_channel_conserves_mass_and_streamwise_momentum():
+    """Symmetry lines pass no mass and no tangential momentum (the interface
+    distribution is even in the normal velocity component), so a channel periodic in
+    x between two symmetry lines conserves mass and x-momentum."""
+    m = M.cartesian(10, 8, 10.0, 8.0, jitter=0.2, seed=9)
+    bcs = [(3, M.BC_PERIODIC, (1, 10.0, 0.0)), (1, M.BC_PERIODIC, (3, -10.0, 0.0)),
+           (0, M.BC_SYMMETRY, (0.0, 0.0, 0.0)), (2, M.BC_SYMMETRY, (0.0, 0.0, 0.0))]
+    case = M.Case("sym_channel", m, bcs, tau=0.05, dt=0.2)
+    xy = m.meta["cell_xy_nominal"]
+    X, Y = 2 * np.pi * xy[:, 0] / 10.0, 2 * np.pi * xy[:, 1] / 8.0
+    rho = 1.0 + 0.03 * np.cos(X + 0.3) * np.sin(Y)
+    u = np.stack([0.04 * np.sin(Y) + 0.02 * np.cos(X), 0.03 * np.sin(X) * np.cos(Y)], 1)
+    vol = O.geometry(m, bcs)["vol"]
+    st = O.init(m.n_cells, rho=rho, u=u)
+    m0 = vol @ st.W
+    O.run(case, st, 400)
+    m1 = vol @ st.W
+    assert abs(m1[0] - m0[0]) <= 1e-13 * abs(m0[0])
+    assert abs(m1[1] - m0[1]) <= 1e-13 * abs(m0[0])
+    assert abs(m1[2] - m0[2]) > 1e-6 * abs(m0[0])             # normal momentum is not conserved (pressure)
+
+
+def test_symmetry_rejects_a_slanted_line():
+    """Mirrored D2Q9 velocities stay on the lattice only for lines of constant x or y."""
+    case = M.cylinder(16, 8, first=0.05, r_far=3.0, shuffle_seed=None)
+    bcs = [(0, M.BC_SYMMETRY, (0.0, 0.0, 0.0)), (1, M.BC_FARFIELD, (1.0, 0.1, 0.0))]
+    with pytest.raises(RuntimeError):
+        O.run(dataclasses.replace(case, bcs=bcs), O.init(case.mesh.n_cells), 1)
