@@ -191,6 +191,74 @@ def flat_plate(nx_up: int = 24, nx_plate: int = 72, ny: int = 64, *, U: float = 
                 u0=(U, 0.0), meta=dict(U=U, Re_L=Re_L, L=L, xs=xs, ys=ys, cfl=cfl))
 
 
+def from_polygons(points: np.ndarray, cells: list, side_of) -> Mesh:
+    """Face-based mesh from cell polygons (vertex lists, either orientation): every
+    edge becomes one face, owned by the first cell that lists it; an edge of one cell
+    only is a boundary face of patch side_of(midpoint)."""
+    edge = {}
+    fpts, own, nbr = [], [], []
+    for c, poly in enumerate(cells):
+        k = len(poly)
+        for q in range(k):
+            a, b = int(poly[q]), int(poly[(q + 1) % k])
+            key = (a, b) if a < b else (b, a)
+            f = edge.get(key)
+            if f is None:
+                edge[key] = len(fpts)
+                fpts.append((a, b)); own.append(c); nbr.append(-1)
+            else:
+                assert nbr[f] == -1, "edge shared by more than two cells"
+                nbr[f] = c
+    fpts = np.asarray(fpts, np.int64)
+    own = np.asarray(own, np.int64)
+    nbr = np.asarray(nbr, np.int64)
+    mid = 0.5 * (points[fpts[:, 0]] + points[fpts[:, 1]])
+    for f in np.where(nbr == -1)[0]:
+        nbr[f] = -1 - int(side_of(mid[f]))
+    return Mesh(np.asarray(points, np.float64), fpts, own, nbr, len(cells), {})
+
+
+def hybrid(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, *, tri_from: float = 0.5, jitter: float = 0.0,
+           seed: int | None = None, quad_rows: int = 0) -> Mesh:
+    """Quad/triangle hybrid mesh on [0,lx] x [0,ly]: the quads of the uniform (optionally
+    jittered) nx x ny grid whose column index is >= tri_from * nx are each split into
+    two triangles (diagonals alternating in a checkerboard), except in the quad_rows
+    rows next to the bottom and to the top (a layer of quads along walls, as hybrid
+    meshes keep at solid boundaries).  Patches and point numbering as cartesian(); the
+    cell order is row by row, a split quad giving its lower then its upper triangle."""
+    base = cartesian(nx, ny, lx, ly, jitter=jitter, seed=seed)
+    P = base.points
+    pid = lambda i, j: i + (nx + 1) * j  # noqa: E731
+    cells, n_tri = [], 0
+    for j in range(ny):
+        for i in range(nx):
+            a, b, c, d = pid(i, j), pid(i + 1, j), pid(i + 1, j + 1), pid(i, j + 1)
+            if i >= tri_from * nx and quad_rows <= j < ny - quad_rows:
+                if (i + j) % 2 == 0:
+                    cells += [[a, b, c], [a, c, d]]
+                else:
+                    cells += [[a, b, d], [b, c, d]]
+                n_tri += 2
+            else:
+                cells.append([a, b, c, d])
+    eps = 1e-9 * max(lx, ly)
+
+    def side_of(x):
+        if abs(x[1]) <= eps:
+            return 0
+        if abs(x[0] - lx) <= eps:
+            return 1
+        if abs(x[1] - ly) <= eps:
+            return 2
+        return 3
+
+    m = from_polygons(P, cells, side_of)
+    m.patches = dict(bottom=0, right=1, top=2, left=3)
+    m.meta = dict(kind="hybrid", nx=nx, ny=ny, lx=lx, ly=ly, n_triangles=n_tri,
+                  cell_xy_nominal=np.array([P[c].mean(0) for c in cells]))
+    return m
+
+
 def o_mesh_ratio(n_r: int, r0: float, first: float, r_far: float) -> float:
     """Geometric ratio q with r0 + first*(q^n_r - 1)/(q - 1) = r_far (bisection)."""
     lo, hi = 1.0 + 1e-12, 2.0
