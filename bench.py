@@ -48,27 +48,54 @@ def parse():
     ap.add_argument("--steps", type=int, default=17)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16dev"],
+                    help="storage of f (default: fp32; bf16dev for the cylinder)")
     ap.add_argument("--n", type=int, default=256, help="cavity cells per side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve"],
-                    help="cavity: the headline single solve; batch: 256 cavities in one batch against the plain "
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "cylinder", "batch", "serve"],
+                    help="cavity: the headline single solve; cylinder: the 512 x 256 O-mesh (shuffled, "
+                         "unstructured kernel); batch: 256 cavities in one batch against the plain "
                          "one-at-a-time path; serve: the continuous-batching request loop")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "bf16dev" if args.workload == "cylinder" else "fp32"
+    return args
 
 
 def workload(args):
+    if args.workload == "cylinder":
+        return M.cylinder(512, 256)
     return M.cavity(args.n, U=0.1, Re=1000.0, cfl=0.5)
 
 
+def workload_name(args):
+    if args.workload == "cylinder":
+        return ("cylinder O-mesh 512x256 (r 0.5-50, first cell 0.005), Re 40, U 0.1, far field + no-slip wall, "
+                "cell ids shuffled (seed 0), from uniform flow")
+    return f"lid-driven cavity {args.n}x{args.n}, Re 1000, lid 0.1, CFL 0.5, from rest"
+
+
+def workload_tag(args):
+    return "cylinder512x256" if args.workload == "cylinder" else f"cavity{args.n}"
+
+
+def initial_u(case):
+    """Uniform initial velocity of the case (None: at rest)."""
+    if tuple(case.u0) == (0.0, 0.0):
+        return None
+    return np.tile(np.asarray(case.u0, dtype=np.float64), (case.mesh.n_cells, 1))
+
+
 def config(args, case):
-    return {"workload": f"lid-driven cavity {args.n}x{args.n}, Re 1000, lid 0.1, CFL 0.5, from rest",
+    state_mb = STATE_BYTES[args.precision] * case.mesh.n_cells / 1e6
+    return {"workload": workload_name(args),
             "cells": case.mesh.n_cells, "velocities": 9, "time_steps_per_step": INTERVAL,
             "storage": args.precision, "tau": case.tau, "dt": case.dt,
-            "l2": "flushed (256 MB rewrite) before each timed step; the 9.4 MB state is L2-resident within a step",
+            "l2": f"flushed (256 MB rewrite) before each timed step; the {state_mb:.1f} MB state is L2-resident "
+                  f"within a step",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -186,7 +213,7 @@ def cpu_baseline(case, seconds: float):
     10-step chunks of the workload as fit in about `seconds`."""
     import oracle as O
     threads = O.set_threads(0)
-    st = O.init(case.mesh.n_cells)
+    st = O.init(case.mesh.n_cells, u=initial_u(case))
     O.run(case, st, 1)                       # geometry warm-up, untimed
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -203,7 +230,7 @@ def cpu_baseline(case, seconds: float):
     el1 = time.perf_counter() - t0
     O.set_threads(threads)
     return {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": f"{steps} time steps of the same {case.mesh.n_cells}-cell cavity from rest "
+            "sample": f"{steps} time steps of the same {case.mesh.n_cells}-cell workload "
                       f"({el:.1f} s, {threads} OpenMP threads, FP64)",
             "single_thread_value": case.mesh.n_cells * 9 * 2 / el1 / 1e6}
 
@@ -217,7 +244,7 @@ def run_reference(args):
     import oracle as O
     case = workload(args)
     threads = O.set_threads(0)
-    st = O.init(case.mesh.n_cells)
+    st = O.init(case.mesh.n_cells, u=initial_u(case))
     sample = 10                              # time steps per benchmark step
     for _ in range(args.warmup):
         O.run(case, st, sample)
@@ -256,7 +283,7 @@ def run_ours(args):
     n = case.mesh.n_cells
     stream = torch.cuda.Stream()
     s = S.Solver.from_case(case, args.precision, stream=stream)
-    s.init()
+    s.init(None, initial_u(case))
     info = s.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -311,11 +338,14 @@ def run_ours(args):
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
-    alg_bytes = STATE_BYTES[args.precision] * n
+    # algorithmic bytes per launch: the state (f and W read and written once) and, on
+    # an unstructured mesh, the mesh data the step must read
+    mesh_b = info["mesh_bytes_per_cell_step"] if info["kernel"] == 1 else 0.0
+    alg_bytes = (STATE_BYTES[args.precision] + mesh_b) * n
     kern_avg_s = float(np.mean(kern_ms)) / 1e3
     achieved = alg_bytes / kern_avg_s / 1e9
     kname = {1: "k_step_tiled", 2: "k_step_cart"}[info["kernel"]]
-    key = f"{kname}_{args.precision}_cavity{args.n}"
+    key = f"{kname}_{args.precision}_{workload_tag(args)}"
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -425,7 +455,7 @@ def main():
     elif args.workload == "serve":
         run_serve(args)
     else:
-        run_ours(args)
+        run_ours(args)           # cavity or cylinder
 
 
 if __name__ == "__main__":

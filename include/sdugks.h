@@ -53,6 +53,8 @@ extern "C" {
 #define SDUGKS_BC_MOVING_WALL 3 /* no-slip wall moving at (u_x, u_y); params: u_x, u_y */
 #define SDUGKS_BC_FARFIELD 4    /* inlet / free stream; params: rho_inf, u_x, u_y      */
 #define SDUGKS_BC_OUTLET 5      /* rho and u of the inner cell; params unused          */
+#define SDUGKS_BC_SYMMETRY 6    /* mirror ghost cell (same rho, mirrored u); the patch's
+                                   faces must be lines of constant x or y; params unused */
 
 /* ---- storage/compute precision of f ------------------------------------------- */
 #define SDUGKS_FP64 0          /* f stored and computed in FP64                          */
@@ -113,8 +115,11 @@ int sdugks_mesh_create(int64_t n_points, const double *xy, int64_t n_faces, cons
                        sdugks_mesh **out);
 
 /* Boundary condition of one patch (Sec. III: no-slip/moving wall and inlet by
- * non-equilibrium extrapolation, outlet, periodic).  params[3] as listed with the
- * SDUGKS_BC_* kinds (host; may be NULL for WALL and OUTLET).  A PERIODIC patch
+ * non-equilibrium extrapolation, outlet, symmetric, periodic).  params[3] as listed
+ * with the SDUGKS_BC_* kinds (host; may be NULL for WALL, OUTLET and SYMMETRY).  A
+ * SYMMETRY face acts as an interior face to the mirror image of its cell (fbar+ of
+ * the mirrored velocity, reflected gradient, also a neighbour in the cell's LLSR);
+ * a slanted symmetry face is rejected with BAD_BC when a solver is created.  A PERIODIC patch
  * must name a PERIODIC partner whose faces sit at this patch's face centres plus
  * (shift_x, shift_y); pairing is checked when a solver is created.
  * Errors: INVALID_ARG (patch or kind out of range). */

@@ -11,6 +11,14 @@ namespace sdugks {
 __host__ __device__ constexpr int EX(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0); }
 __host__ __device__ constexpr int EY(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
 
+// Mirror image of velocity a in a line of constant x (xi_x -> -xi_x) and of constant y.
+__host__ __device__ constexpr int MIRROR_X(int a) {
+    return a == 1 ? 3 : a == 3 ? 1 : a == 5 ? 6 : a == 6 ? 5 : a == 7 ? 8 : a == 8 ? 7 : a;
+}
+__host__ __device__ constexpr int MIRROR_Y(int a) {
+    return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
+}
+
 template <class R> __device__ __forceinline__ R wq(int a) {
     return a == 0 ? R(4) / R(9) : (a < 5 ? R(1) / R(9) : R(1) / R(36));
 }

@@ -189,7 +189,7 @@ extern "C" int sdugks_set_bc(sdugks_mesh *m, int32_t patch, int32_t kind, const 
 {
     if (!m) return fail(SDUGKS_ERR_INVALID_ARG, "mesh is NULL");
     if (patch < 0 || patch >= MAXPATCH) return fail(SDUGKS_ERR_INVALID_ARG, "patch %d out of range", patch);
-    if (kind < SDUGKS_BC_PERIODIC || kind > SDUGKS_BC_OUTLET) return fail(SDUGKS_ERR_INVALID_ARG, "unknown kind %d", kind);
+    if (kind < SDUGKS_BC_PERIODIC || kind > SDUGKS_BC_SYMMETRY) return fail(SDUGKS_ERR_INVALID_ARG, "unknown kind %d", kind);
     const bool need = kind == SDUGKS_BC_PERIODIC || kind == SDUGKS_BC_MOVING_WALL || kind == SDUGKS_BC_FARFIELD;
     if (need && !params) return fail(SDUGKS_ERR_INVALID_ARG, "kind %d needs params", kind);
     for (int k = 0; k < 3; k++) {
@@ -544,7 +544,9 @@ static void fill_cart_inst(CartInst &ci, const sdugks_mesh &m, const CartGrid &g
     ci.c = 2.0 * tau / (2.0 * tau + dt);
     ci.r = dt / tau;
     ci.dt = dt;
+    ci.ihx = 1.0 / g.dx; ci.ihy = 1.0 / g.dy;
     ci.fdx = (float)ci.dx; ci.fdy = (float)ci.dy; ci.fdtV = (float)ci.dtV;
+    ci.fihx = (float)ci.ihx; ci.fihy = (float)ci.ihy;
     ci.fa = (float)ci.a; ci.fb = (float)ci.b; ci.fc = (float)ci.c; ci.fr = (float)ci.r;
     ci.finv1r = (float)(1.0 / (1.0 + dt / tau));
     ci.fdt = (float)dt;
@@ -679,6 +681,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     std::vector<std::array<int64_t, MAXF>> slots(n);
     std::vector<int> nslot(n, 0);
     for (int64_t f = 0; f < F.nf; f++) {
+        if (F.own[f] == F.nbr[f])
+            return fail(SDUGKS_ERR_INVALID_MESH, "periodic pair joins cell %lld to itself", (long long)F.own[f]);
         for (int side = 0; side < 2; side++) {
             const int64_t c = side == 0 ? F.own[f] : F.nbr[f];
             if (c < 0) continue;
@@ -707,7 +711,20 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                 const double dx = rme[0] - rot[0], dy = rme[1] - rot[1];
                 axx += dx * dx; axy += dx * dy; ayy += dy * dy;
             } else {
-                skind[(size_t)c * MAXF + sl] = (uint8_t)(-1 - F.nbr[f]);
+                const int p = (int)(-1 - F.nbr[f]);
+                skind[(size_t)c * MAXF + sl] = (uint8_t)p;
+                if (m->bc_kind[p] == SDUGKS_BC_SYMMETRY) {
+                    // the mirror ghost: x_f - x_g is x_f - x_j reflected in the face line,
+                    // and the ghost is an LLSR neighbour at d = x_g - x_j
+                    const double ax = std::fabs(G[0]), ay = std::fabs(G[1]);
+                    if (ay > 1e-12 * ax && ax > 1e-12 * ay)
+                        return fail(SDUGKS_ERR_BAD_BC, "symmetry face %lld is not a line of constant x or y", (long long)f);
+                    const bool nx_axis = ax > ay;
+                    G[4] = nx_axis ? -rme[0] : rme[0];
+                    G[5] = nx_axis ? rme[1] : -rme[1];
+                    const double dx = rme[0] - G[4], dy = rme[1] - G[5];
+                    axx += dx * dx; axy += dx * dy; ayy += dy * dy;
+                }
             }
         }
         const double det = axx * ayy - axy * axy, tr = axx + ayy;
@@ -728,7 +745,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         if (F.nbr[f] < 0) return -1;
         return F.own[f] == c ? F.nbr[f] : F.own[f];
     };
-    std::vector<int32_t> stamp(n, -1), local(n, 0);
+    std::vector<int32_t> stamp(n, -1), local(n, 0), fstamp(F.nf, -1);
     struct TileHalo { std::vector<int32_t> r1, r2; };
     std::vector<TileHalo> halos;
     std::vector<std::pair<size_t, size_t>> final_tiles;
@@ -738,10 +755,13 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         tag++;
         for (size_t i = lo; i < hi; i++) stamp[ids[i]] = tag;
         TileHalo h;
+        size_t n_faces = 0;
         for (size_t i = lo; i < hi; i++)
             for (int sl = 0; sl < nslot[ids[i]]; sl++) {
                 const int64_t kc = other_of(ids[i], sl);
                 if (kc >= 0 && stamp[kc] != tag) { stamp[kc] = tag; h.r1.push_back((int32_t)kc); }
+                const int64_t f = slots[ids[i]][sl];
+                if (fstamp[f] != tag) { fstamp[f] = tag; n_faces++; }
             }
         for (int32_t c1 : h.r1)
             for (int sl = 0; sl < nslot[c1]; sl++) {
@@ -749,7 +769,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                 if (kc >= 0 && stamp[kc] != tag) { stamp[kc] = tag; h.r2.push_back((int32_t)kc); }
             }
         const size_t nint = hi - lo;
-        if (nint + h.r1.size() + h.r2.size() > (size_t)LOC_MAX || nint + h.r1.size() > (size_t)SIG_MAX) {
+        if (nint + h.r1.size() + h.r2.size() > (size_t)LOC_MAX || nint + h.r1.size() > (size_t)SIG_MAX ||
+            n_faces > (size_t)LF_MAX) {
             if (nint <= 8) return fail(SDUGKS_ERR_INVALID_MESH, "halo of a %zu-cell tile does not fit", nint);
             std::vector<std::pair<size_t, size_t>> sub;
             rcb(m->xc, ids, lo, hi, (nint + 1) / 2, sub);
@@ -770,21 +791,41 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     }
 
     const int64_t npad = (n + 31) / 32 * 32;
-    std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), halo;
-    std::vector<uint16_t> sig_nb;
+    std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), tile_f0(nt + 1), halo;
+    std::vector<uint16_t> sig_nb, cell_lf((size_t)MAXF * npad, LF_NONE);
+    std::vector<uint32_t> lf_ab;
+    std::vector<double> lf_geo;   // [n_lf][6], transposed at upload
     std::vector<uint8_t> islk((size_t)MAXF * npad, SK_NONE);
-    std::vector<double> igeo((size_t)MAXF * 6 * npad, 0.0), iainv(3 * npad, 0.0), ivol(npad, 1.0), idtv(npad, 0.0);
+    std::vector<double> iainv(3 * npad, 0.0), ivol(npad, 1.0), idtv(npad, 0.0);
+    // x_k - x_j across each interior slot, formed in the compute precision from the
+    // two face-centre offsets as they are stored for the kernel
+    const int prec = prm->precision;
+    const size_t rs = prec == P_FP64 ? sizeof(double) : sizeof(float);
+    std::vector<char> isld((size_t)MAXF * 2 * npad * rs, 0);
     for (int64_t i = 0; i < n; i++) {
         const int64_t c = perm[i];
         for (int sl = 0; sl < MAXF; sl++) {
-            islk[(size_t)sl * npad + i] = skind[(size_t)c * MAXF + sl];
-            for (int q = 0; q < 6; q++) igeo[((size_t)sl * 6 + q) * npad + i] = sgeo[((size_t)c * MAXF + sl) * 6 + q];
+            const uint8_t kd = skind[(size_t)c * MAXF + sl];
+            islk[(size_t)sl * npad + i] = kd;
+            if (kd != SK_INTERIOR && !(kd < MAXPATCH && m->bc_kind[kd] == SDUGKS_BC_SYMMETRY)) continue;
+            const double *G = &sgeo[((size_t)c * MAXF + sl) * 6];
+            for (int q = 0; q < 2; q++) {
+                const size_t at = ((size_t)(2 * sl + q) * npad + i) * rs;
+                if (prec == P_FP64) {
+                    const double v = G[2 + q] - G[4 + q];
+                    std::memcpy(&isld[at], &v, rs);
+                } else {
+                    const float v = (float)G[2 + q] - (float)G[4 + q];
+                    std::memcpy(&isld[at], &v, rs);
+                }
+            }
         }
         for (int d = 0; d < 3; d++) iainv[d * npad + i] = ainv[3 * c + d];
         ivol[i] = m->vol[c];
         idtv[i] = prm->dt / m->vol[c];
     }
     int64_t halo_total = 0, sig_total = 0;
+    std::vector<int32_t> flocal(F.nf, 0);
     {
         int32_t c0 = 0, hoff = 0, soff = 0;
         for (int32_t t = 0; t < nt; t++) {
@@ -809,18 +850,45 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                 for (int sl = 0; sl < nslot[c]; sl++) {
                     const int64_t kc = other_of(c, sl);
                     if (kc >= 0) row[sl] = (uint16_t)local[iperm[kc]];
+                    const uint8_t kd = skind[(size_t)c * MAXF + sl];
+                    if (kd != SK_INTERIOR && m->bc_kind[kd] == SDUGKS_BC_SYMMETRY) {
+                        const double *G = &sgeo[((size_t)c * MAXF + sl) * 6];
+                        row[sl] = std::fabs(G[0]) > std::fabs(G[1]) ? SYM_X : SYM_Y;
+                    }
                 }
                 sig_nb.insert(sig_nb.end(), row.begin(), row.end());
             };
             for (int32_t i = 0; i < nint; i++) push_sig(c0 + i);
             for (int32_t c : r1) push_sig(c);
+            // local faces, in order of first appearance over the tile's cells and slots;
+            // oriented from the merged face's owner to its neighbour (or boundary)
+            tile_f0[t] = (int32_t)lf_ab.size();
+            for (int32_t i = 0; i < nint; i++) {
+                const int64_t c = perm[c0 + i];
+                for (int sl = 0; sl < nslot[c]; sl++) {
+                    const int64_t f = slots[c][sl];
+                    if (fstamp[f] != -2 - t) {
+                        fstamp[f] = -2 - t;
+                        flocal[f] = (int32_t)lf_ab.size() - tile_f0[t];
+                        const uint32_t a = (uint32_t)local[iperm[F.own[f]]];
+                        const uint32_t b = F.nbr[f] >= 0 ? (uint32_t)local[iperm[F.nbr[f]]]
+                                                         : (LF_BOUNDARY | (uint32_t)(-1 - F.nbr[f]));
+                        lf_ab.push_back(a | (b << 16));
+                        const double q6[6] = {F.nl[2 * f], F.nl[2 * f + 1], F.ro[2 * f], F.ro[2 * f + 1],
+                                              F.rk[2 * f], F.rk[2 * f + 1]};
+                        lf_geo.insert(lf_geo.end(), q6, q6 + 6);
+                    }
+                    const bool second = F.own[f] != c;
+                    cell_lf[(size_t)sl * npad + c0 + i] = (uint16_t)(flocal[f] | (second ? LF_SECOND : 0));
+                }
+            }
             c0 += nint;
             hoff += (int32_t)(r1.size() + r2.size());
             soff += nint + (int32_t)r1.size();
             halo_total += (int64_t)(r1.size() + r2.size());
             sig_total += nint + (int64_t)r1.size();
         }
-        tile_c0[nt] = c0; tile_h0[nt] = hoff; tile_s0[nt] = soff;
+        tile_c0[nt] = c0; tile_h0[nt] = hoff; tile_s0[nt] = soff; tile_f0[nt] = (int32_t)lf_ab.size();
     }
 
     // ---- every index the kernel dereferences is checked here, on the host
@@ -837,17 +905,44 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
             for (int sl = 0; sl < MAXF; sl++) {
                 const uint16_t v = sig_nb[((size_t)tile_s0[t] + i) * MAXF + sl];
                 const uint8_t kd = islk[(size_t)sl * npad + g];
-                if (v != NO_LOCAL && v >= nloc)
+                const bool sym = kd != SK_INTERIOR && kd != SK_NONE && kd < MAXPATCH &&
+                                 m->bc_kind[kd] == SDUGKS_BC_SYMMETRY;
+                if (sym != (v == SYM_X || v == SYM_Y))
+                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: symmetry slot without its mirror code");
+                if (!sym && v != NO_LOCAL && v >= nloc)
                     return fail(SDUGKS_ERR_INVALID_MESH, "internal: gradient neighbour outside the tile's cells");
-                if ((kd == SK_INTERIOR) != (v != NO_LOCAL))
+                if ((kd == SK_INTERIOR) != (!sym && v != NO_LOCAL))
                     return fail(SDUGKS_ERR_INVALID_MESH, "internal: slot kind and neighbour disagree");
                 if (i < nint && kd == SK_INTERIOR && v >= nsig)
                     return fail(SDUGKS_ERR_INVALID_MESH, "internal: face neighbour outside ring 1");
-                if (kd != SK_INTERIOR && kd != SK_NONE &&
-                    (kd >= MAXPATCH || m->bc_kind[kd] == SDUGKS_BC_UNSET || m->bc_kind[kd] == SDUGKS_BC_PERIODIC))
+            }
+        }
+        const int32_t nlf = tile_f0[t + 1] - tile_f0[t];
+        if (nlf < 1 || nlf > LF_MAX) return fail(SDUGKS_ERR_INVALID_MESH, "internal: tile %d face count out of range", t);
+        for (int32_t q = tile_f0[t]; q < tile_f0[t + 1]; q++) {
+            const uint32_t a = lf_ab[q] & 0xFFFFu, b = lf_ab[q] >> 16;
+            if ((b & LF_SECOND) == 0) {
+                if (a >= (uint32_t)nsig || b >= (uint32_t)nsig || (a >= (uint32_t)nint && b >= (uint32_t)nint))
+                    return fail(SDUGKS_ERR_INVALID_MESH, "internal: face sides outside the tile's gradient cells");
+            } else {
+                const uint32_t p = b & 0xFFu;
+                if ((b & ~0xFFu) != LF_BOUNDARY || a >= (uint32_t)nint || p >= MAXPATCH ||
+                    m->bc_kind[p] == SDUGKS_BC_UNSET || m->bc_kind[p] == SDUGKS_BC_PERIODIC)
                     return fail(SDUGKS_ERR_BAD_BC, "internal: boundary face without a usable condition");
             }
         }
+        for (int32_t i = 0; i < nint; i++)
+            for (int sl = 0; sl < MAXF; sl++) {
+                const uint16_t v = cell_lf[(size_t)sl * npad + tile_c0[t] + i];
+                const bool none = islk[(size_t)sl * npad + tile_c0[t] + i] == SK_NONE;
+                if (none != (v == LF_NONE)) return fail(SDUGKS_ERR_INVALID_MESH, "internal: slot without its face");
+                if (none) continue;
+                const int32_t lf = v & (LF_SECOND - 1);
+                if (lf >= nlf) return fail(SDUGKS_ERR_INVALID_MESH, "internal: local face out of range");
+                const uint32_t ab = lf_ab[tile_f0[t] + lf];
+                const uint32_t side = (v & LF_SECOND) ? ab >> 16 : ab & 0xFFFFu;
+                if (side != (uint32_t)i) return fail(SDUGKS_ERR_INVALID_MESH, "internal: face side is not the cell");
+            }
     }
 
     // ---- device allocation (one arena) and upload
@@ -859,8 +954,6 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     s->stream = static_cast<cudaStream_t>(stream);
     s->n = n; s->npad = npad; s->nf = F.nf; s->n_tiles = nt; s->halo_cells = halo_total;
     s->kernel = SDUGKS_KERNEL_TILED;
-    const int prec = prm->precision;
-    const size_t rs = prec == P_FP64 ? sizeof(double) : sizeof(float);
     const size_t fs = prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2);
     s->n_red_blocks = residual_blocks(n);
 
@@ -878,8 +971,11 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->tm.tile_s0 = A.take<int32_t>(nt + 1);
         s->tm.halo = A.take<int32_t>(std::max<size_t>(1, halo.size()));
         s->tm.sig_nb = A.take<uint16_t>(sig_nb.size());
-        s->tm.sl_kind = A.take<uint8_t>(islk.size());
-        s->tm.sl_geo = A.take<char>(igeo.size() * rs);
+        s->tm.tile_f0 = A.take<int32_t>(nt + 1);
+        s->tm.sl_d = A.take<char>(isld.size());
+        s->tm.cell_lf = A.take<uint16_t>(cell_lf.size());
+        s->tm.lf_ab = A.take<uint32_t>(lf_ab.size());
+        s->tm.lf_geo = A.take<char>(lf_geo.size() * rs);
         s->tm.ainv = A.take<char>(3 * npad * rs);
         s->tm.dtV = A.take<char>(npad * rs);
         s->tm.vol = s->vol;
@@ -896,7 +992,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     }
     Arena A{s->dmem, 0, s->dbytes};
     layout(A);
-    s->tm.n_tiles = nt; s->tm.n = n; s->tm.npad = npad;
+    s->tm.n_tiles = nt; s->tm.n = n; s->tm.npad = npad; s->tm.n_lf = (int64_t)lf_ab.size();
 
     auto conv = [&](const std::vector<double> &v) {
         std::vector<char> o(v.size() * rs);
@@ -912,7 +1008,13 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     auto up = [&](const void *dst, const void *src, size_t bytes) {
         return cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
     };
-    const std::vector<char> ggeo = conv(igeo), gainv = conv(iainv), gdtv = conv(idtv);
+    std::vector<double> lgeo_t(lf_geo.size());
+    {
+        const size_t nlf = lf_ab.size();
+        for (size_t q = 0; q < nlf; q++)
+            for (int d = 0; d < 6; d++) lgeo_t[d * nlf + q] = lf_geo[q * 6 + d];
+    }
+    const std::vector<char> ggeo = conv(lgeo_t), gainv = conv(iainv), gdtv = conv(idtv);
     int rc2 = SDUGKS_OK;
     auto chk = [&](cudaError_t ee, const char *what) {
         if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
@@ -926,8 +1028,11 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     chk(up(s->tm.tile_s0, tile_s0.data(), (nt + 1) * 4), "upload tiles");
     if (!halo.empty()) chk(up(s->tm.halo, halo.data(), halo.size() * 4), "upload halo");
     chk(up(s->tm.sig_nb, sig_nb.data(), sig_nb.size() * 2), "upload sig_nb");
-    chk(up(s->tm.sl_kind, islk.data(), islk.size()), "upload slot kinds");
-    chk(up(s->tm.sl_geo, ggeo.data(), ggeo.size()), "upload slot geometry");
+    chk(up(s->tm.tile_f0, tile_f0.data(), (nt + 1) * 4), "upload tiles");
+    chk(up(s->tm.sl_d, isld.data(), isld.size()), "upload slot offsets");
+    chk(up(s->tm.cell_lf, cell_lf.data(), cell_lf.size() * 2), "upload cell faces");
+    chk(up(s->tm.lf_ab, lf_ab.data(), lf_ab.size() * 4), "upload face sides");
+    chk(up(s->tm.lf_geo, ggeo.data(), ggeo.size()), "upload face geometry");
     chk(up(s->tm.ainv, gainv.data(), gainv.size()), "upload ainv");
     chk(up(s->tm.dtV, gdtv.data(), gdtv.size()), "upload dtV");
     chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
@@ -936,12 +1041,14 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     if (rc2) { sdugks_solver_destroy(s); return rc2; }
 
     fill_coefs(s->coefs, *m, prm->tau, prm->dt);
-    // mesh bytes the tiled kernel reads per interior cell and step: slot kinds and
-    // geometry (4 x 6 values) of its own cell, gradient data (d vectors, inverse,
-    // neighbour indices) of interior and ring-1 cells, halo ids and dt/V
+    // mesh bytes the tiled kernel reads per interior cell and step: the slot list of
+    // its own cell, the tile's local faces (sides and 6 geometry values), gradient
+    // data (d vectors, inverse, neighbour indices) of interior and ring-1 cells, halo
+    // ids and dt/V
     {
-        const double sigc = (double)sig_total / n;
-        s->mesh_bytes = MAXF * (1 + 6 * rs) + sigc * (MAXF * (2 + 2 * rs) + 3 * rs) + (double)halo_total / n * 4 + rs;
+        const double sigc = (double)sig_total / n, lfc = (double)lf_ab.size() / n;
+        s->mesh_bytes = MAXF * 2 + lfc * (4 + 6 * rs) + sigc * (MAXF * (2 + 2 * rs) + 3 * rs) +
+                        (double)halo_total / n * 4 + rs;
     }
     *out = s;
     return SDUGKS_OK;

@@ -10,16 +10,21 @@ constexpr int NQ = 9;
 constexpr int MAXF = 4;         // faces per cell (quads and triangles)
 constexpr int MAXPATCH = 64;    // boundary patches
 constexpr uint16_t NO_LOCAL = 0xFFFF;
+// LLSR neighbour codes of a symmetry slot: the mirror image of the cell itself in a
+// line of constant x (SYM_X) or constant y (SYM_Y)
+constexpr uint16_t SYM_X = 0xFFFD, SYM_Y = 0xFFFE;
 
-// Tiled kernel shape: one CTA per tile, one thread per interior cell.
-constexpr int TILE_MAX = 128;   // interior cells per tile (= threads per CTA)
+// Tiled kernel shape: one CTA per tile of up to TILE_MAX cells.
+constexpr int TILE_MAX = 128;   // interior cells per tile
+constexpr int TILED_THREADS = 256;
 constexpr int LOC_MAX = 416;    // interior + two halo rings
 constexpr int SIG_MAX = 272;    // interior + first halo ring (cells whose gradient is needed)
+constexpr int LF_MAX = 320;     // faces with at least one interior cell of the tile
 
 enum Prec : int32_t { P_FP64 = 0, P_FP32 = 1, P_BF16DEV = 2 };
 
 enum BcKind : int32_t { BK_UNSET = 0, BK_PERIODIC = 1, BK_WALL = 2, BK_MOVING_WALL = 3,
-                        BK_FARFIELD = 4, BK_OUTLET = 5 };
+                        BK_FARFIELD = 4, BK_OUTLET = 5, BK_SYMMETRY = 6 };
 
 // Scalars of one step (host-computed in FP64 from tau and dt; FP32 copies for the
 // FP32-compute kernels so that no thread converts them).
@@ -43,24 +48,34 @@ constexpr uint8_t SK_INTERIOR = 0xFF;  // face shared with another cell (periodi
                                        // any other value: boundary patch id
 
 // Unstructured tiled mesh on the device.  Cells are in internal (tile-contiguous)
-// order; arrays indexed by cell are padded to npad.
+// order; arrays indexed by cell are padded to npad.  Each tile lists the faces that
+// touch its interior cells ("local faces", evaluated once per tile), oriented from
+// their first side (the face owner) to the second.
 struct TiledMesh {
     int32_t n_tiles;
     int64_t n, npad;
+    int64_t n_lf;             // local faces of all tiles (stride of lf_geo)
     const int32_t *tile_c0;   // [n_tiles+1] interior cell range of each tile
     const int32_t *tile_h0;   // [n_tiles+1] range into halo
     const int32_t *tile_nh1;  // [n_tiles]   cells of ring 1 (first in the tile's halo)
     const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb
+    const int32_t *tile_f0;   // [n_tiles+1] range of local faces
     const int32_t *halo;      // internal ids of ring 1 then ring 2 of each tile
     const uint16_t *sig_nb;   // [sum n_sig][MAXF] tile-local index of the cell across each slot
-    const uint8_t *sl_kind;   // [MAXF][npad] SK_* or boundary patch
-    const void *sl_geo;       // [MAXF][6][npad] per slot: n l out of the cell (2),
-                              //   x_f - x_j (2), x_f - x_k with x_k the far cell (2)
+    const void *sl_d;         // [MAXF][2][npad] x_k - x_j across each interior slot
+    const uint16_t *cell_lf;  // [MAXF][npad] local face of each slot, | LF_SECOND when the cell
+                              //   is the face's second side; LF_NONE for no face
+    const uint32_t *lf_ab;    // [n_lf] tile-local first side | second side << 16; a boundary
+                              //   face's second side is LF_BOUNDARY | patch
+    const void *lf_geo;       // [6][n_lf] n l from the first side to the second (2),
+                              //   x_f - x_first (2), x_f - x_second (2)
     const void *ainv;         // [3][npad] LLSR inverse (xx, xy, yy)
     const void *dtV;          // [npad] dt / V (compute precision)
     const double *vol;        // [npad] V
     double *force;            // nullptr, or [MAXPATCH][2]: momentum flux out of the fluid per boundary patch
 };
+constexpr uint16_t LF_SECOND = 0x8000, LF_NONE = 0xFFFF;
+constexpr uint32_t LF_BOUNDARY = 0xC000;
 
 // One uniform-grid solve as the Cartesian kernels see it: nx x ny rectangles
 // dx x dy, cell (i, j) at i + pitch j; side boundary rules; step coefficients; and
@@ -72,9 +87,10 @@ struct CartInst {
     int32_t item0, n_items;   // batched runs: this instance's range in the work list
     int64_t npad;             // >= pitch * ny, multiple of 32
     double dx, dy, dtV;       // dtV = dt / (dx dy)
+    double ihx, ihy;          // 1 / dx, 1 / dy
     double a, b, c, r, dt;    // (2tau-dt)/2tau, dt/2tau, 2tau/(2tau+dt), dt/tau, dt
     double side_par[4][3];
-    float fdx, fdy, fdtV, fa, fb, fc, fr, finv1r, fdt, fpad_;
+    float fdx, fdy, fdtV, fa, fb, fc, fr, finv1r, fdt, fihx, fihy;
     float fside_par[4][3];
     void *f[2];
     double *W[2];

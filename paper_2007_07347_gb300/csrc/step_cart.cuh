@@ -17,6 +17,7 @@
 // in FP64 and f^{n+1}.  `cart_tile` does one block; `k_step_cart` runs it for every block of one
 // grid and `k_step_batch` for every (instance, block) item of a batch.
 #pragma once
+#include <climits>
 #include "d2q9.cuh"
 
 namespace sdugks {
@@ -51,14 +52,14 @@ template <class R> struct CartK;
 template <> struct CartK<double> {
     double a, b, c, r, dt, dtV, hx, hy, ihx, ihy;
     __device__ explicit CartK(const CartInst &m)
-        : a(m.a), b(m.b), c(m.c), r(m.r), dt(m.dt), dtV(m.dtV), hx(m.dx), hy(m.dy), ihx(1.0 / m.dx), ihy(1.0 / m.dy) {}
+        : a(m.a), b(m.b), c(m.c), r(m.r), dt(m.dt), dtV(m.dtV), hx(m.dx), hy(m.dy), ihx(m.ihx), ihy(m.ihy) {}
     __device__ static double par(const CartInst &m, int side, int i) { return m.side_par[side][i]; }
 };
 template <> struct CartK<float> {
     float a, b, c, r, dt, dtV, hx, hy, ihx, ihy;
     __device__ explicit CartK(const CartInst &m)
         : a(m.fa), b(m.fb), c(m.fc), r(m.fr), dt(m.fdt), dtV(m.fdtV), hx(m.fdx), hy(m.fdy),
-          ihx((float)(1.0 / m.dx)), ihy((float)(1.0 / m.dy)) {}
+          ihx(m.fihx), ihy(m.fihy) {}
     __device__ static float par(const CartInst &m, int side, int i) { return m.fside_par[side][i]; }
 };
 
@@ -198,24 +199,45 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     const bool px = m.periodic_x != 0, py = m.periodic_y != 0;
     const CartK<R> k(m);
 
-    // domain cell of a block-relative position (periodic sides wrap), or -1 outside
-    auto cell_of = [&](int bi, int bj) -> int64_t {
+    // Symmetry sides (Sec. III): beyond them sit mirror ghosts of the inner cells
+    // (same fbar+ for the mirrored velocity), staged like any other position, so a
+    // symmetry face is an ordinary face between a cell and its ghost.
+    const bool symL = !px && m.side_kind[3] == BK_SYMMETRY, symR = !px && m.side_kind[1] == BK_SYMMETRY;
+    const bool symB = !py && m.side_kind[0] == BK_SYMMETRY, symT = !py && m.side_kind[2] == BK_SYMMETRY;
+    // a grid column / row exists (a domain cell, a periodic image or a mirror ghost)
+    // iff it lies in [xlo, xhi) x [ylo, yhi)
+    const int xlo = px ? INT_MIN : (symL ? -nx : 0), xhi = px ? INT_MAX : (symR ? 2 * nx : nx);
+    const int ylo = py ? INT_MIN : (symB ? -ny : 0), yhi = py ? INT_MAX : (symT ? 2 * ny : ny);
+    auto has_x = [&](int ci) { return ci >= xlo && ci < xhi; };
+    auto has_y = [&](int cj) { return cj >= ylo && cj < yhi; };
+    // domain cell of a block-relative position (periodic sides wrap, symmetry sides
+    // reflect: mir bit 0 / 1 for a reflection in x / y), or -1 outside
+    auto cell_of = [&](int bi, int bj, int &mir) -> int64_t {
         int gi = x0 + bi, gj = y0 + bj;
+        mir = 0;
         if (gi < 0 || gi >= nx) {
-            if (!px) return -1;
-            gi = (gi + nx) % nx;
+            if (px) gi = (gi + nx) % nx;
+            else if (gi < 0 ? symL : symR) {
+                gi = gi < 0 ? -1 - gi : 2 * nx - 1 - gi;
+                mir |= 1;
+                if (gi < 0 || gi >= nx) return -1;
+            } else return -1;
         }
         if (gj < 0 || gj >= ny) {
-            if (!py) return -1;
-            gj = (gj + ny) % ny;
+            if (py) gj = (gj + ny) % ny;
+            else if (gj < 0 ? symB : symT) {
+                gj = gj < 0 ? -1 - gj : 2 * ny - 1 - gj;
+                mir |= 2;
+                if (gj < 0 || gj >= ny) return -1;
+            } else return -1;
         }
         return gi + pitch * gj;
     };
-    // gradient stencil of the staged cell at block position (bi, bj) (a domain cell)
+    // gradient stencil of the staged cell at block position (bi, bj)
     auto sten = [&](int bi, int bj) {
         const int ci = x0 + bi, cj = y0 + bj;
-        const bool hE = px || ci + 1 < nx, hW = px || ci - 1 >= 0;
-        const bool hN = py || cj + 1 < ny, hS = py || cj - 1 >= 0;
+        const bool hE = has_x(ci + 1), hW = has_x(ci - 1);
+        const bool hN = has_y(cj + 1), hS = has_y(cj - 1);
         Sten<R> st;
         st.oE = hE ? 1 : 0; st.oW = hW ? -1 : 0; st.oN = hN ? S::LX : 0; st.oS = hS ? -S::LX : 0;
         st.ax = (hE && hW) ? R(0.5) * k.ihx : k.ihx;
@@ -242,10 +264,10 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     double w0n = 1.0, w1n = 0.0, w2n = 0.0;
     {
         int64_t gs = -1;
-        int ls = 0;
+        int ls = 0, mir = 0;
         if (cell_thread) {
             ls = lme;
-            gs = active ? g : cell_of(ti, tj);          // past the grid edge: a wrapped cell or none
+            gs = active ? g : cell_of(ti, tj, mir);     // past the grid edge: a wrapped cell, a ghost or none
         } else if (tid < LXY) {
             // ring position r: two rows below, two above, then two columns left and right
             const int r = tid - S::NT;
@@ -254,7 +276,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             else if (r < 4 * S::LX) { li = (r - 2 * S::LX) % S::LX; lj = S::LY - 2 + (r - 2 * S::LX) / S::LX; }
             else { const int q = r - 4 * S::LX; lj = 2 + q / 4; const int cc = q % 4; li = cc < 2 ? cc : S::LX - 4 + cc; }
             ls = lj * S::LX + li;
-            gs = cell_of(li - 2, lj - 2);
+            gs = cell_of(li - 2, lj - 2, mir);
         }
         if (gs >= 0) {
             const double a0 = Wn[gs], a1 = Wn[np + gs], a2 = Wn[2 * np + gs];
@@ -264,9 +286,19 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             macro(a0, a1, a2, rho, ux, uy);
             feq9f<R>(rho, ux, uy, fe);
 #pragma unroll
-            for (int a = 0; a < NQ; a++) {
+            for (int a = 0; a < NQ; a++)
                 if constexpr (P == P_BF16DEV) fv[a] += fe[a];       // decode the deviation
-                s_fbp[a * LXY + ls] = k.a * fv[a] + k.b * fe[a];
+            if (mir == 0) {
+#pragma unroll
+                for (int a = 0; a < NQ; a++) s_fbp[a * LXY + ls] = k.a * fv[a] + k.b * fe[a];
+            } else {
+                // mirror ghost: fbar+ of the mirrored velocity
+                R fb[NQ];
+#pragma unroll
+                for (int a = 0; a < NQ; a++) fb[a] = k.a * fv[a] + k.b * fe[a];
+#pragma unroll
+                for (int a = 0; a < NQ; a++)
+                    s_fbp[a * LXY + ls] = mir == 1 ? fb[MIRROR_X(a)] : (mir == 2 ? fb[MIRROR_Y(a)] : fb[MIRROR_X(MIRROR_Y(a))]);
             }
             if (active) {
 #pragma unroll
@@ -282,7 +314,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     if (tid < S::NFX) {
         // face of constant x between block columns fi-1 (L) and fi (R), row fj
         const int fi = tid % (TX + 1), fj = tid / (TX + 1);
-        if (cell_of(fi - 1, fj) >= 0 && cell_of(fi, fj) >= 0) {
+        if (has_x(x0 + fi - 1) && has_x(x0 + fi) && has_y(y0 + fj)) {
             const int lL = (fj + 2) * S::LX + (fi + 1);
             R fl[6];
             cart_interior_face<0, R>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
@@ -292,7 +324,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     } else if (tid < S::NFX + S::NFY) {
         // face of constant y between block rows fj-1 (below) and fj (above), column fi
         const int qq = tid - S::NFX, fi = qq % TX, fj = qq / TX;
-        if (cell_of(fi, fj - 1) >= 0 && cell_of(fi, fj) >= 0) {
+        if (has_y(y0 + fj - 1) && has_y(y0 + fj) && has_x(x0 + fi)) {
             const int lB = (fj + 1) * S::LX + (fi + 2);
             R fl[6];
             cart_interior_face<1, R>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
@@ -308,8 +340,8 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 #pragma unroll
         for (int a = 0; a < NQ; a++) F[a] = R(0);
         const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
-        const bool inW = px || gi - 1 >= 0, inE = px || gi + 1 < nx;
-        const bool inS = py || gj - 1 >= 0, inN = py || gj + 1 < ny;
+        const bool inW = has_x(gi - 1), inE = has_x(gi + 1);
+        const bool inS = has_y(gj - 1), inN = has_y(gj + 1);
         R feqn[NQ];
         if (!(inW && inE && inS && inN)) feq9f<R>(rho_n, ux_n, uy_n, feqn);   // boundary cells only
         if (inW) {

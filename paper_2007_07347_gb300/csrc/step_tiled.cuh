@@ -1,20 +1,24 @@
 // step_tiled.cuh -- fused S-DUGKS step on an unstructured quad mesh.
 //
-// One CTA per tile of up to TILE_MAX cells (one thread per interior cell).  The tile
-// stages in shared memory the transformed distribution fbar+ of its cells and of
-// two halo rings (Eq. fbarplus), then the LLSR gradient of its cells and of the
-// first ring, then every thread reconstructs the interface distribution on the
-// faces of its own cell along the characteristic (Eqs. fbpsource, fbar, Macro at the
-// face, Feq, f_t_n+1) and sums the mesoscopic flux (Eq. MesoFlux).  Its moments, the
-// macroscopic flux (Eq. MacroFlux), update the FP64 conserved variables
-// W^{n+1} = W^n - dt/V F_macro (Eq. MacroUpdate, the moment of Eq. Integration), whose
-// equilibrium then closes the implicit cell update of f (Eq. fn+1).  f and W
-// ping-pong between two buffers each; nothing else is stored between steps.
+// One CTA per tile of up to TILE_MAX cells.  The tile stages in shared memory the
+// transformed distribution fbar+ of its cells and of two halo rings (Eq. fbarplus),
+// then the LLSR gradient of its cells and of the first ring.  Each face that touches
+// a cell of the tile is then evaluated once, by one thread: the interface
+// distribution is reconstructed along the characteristic from the upwind side (Eqs.
+// fbpsource, fbar), its moments give the interface equilibrium (Macro at the face,
+// Feq), and the interface f (Eq. f_t_n+1) times xi . n l is the face's mesoscopic
+// flux, oriented from its first side to its second, kept in shared memory.  Each cell
+// thread sums the fluxes of its faces in ascending face id with the sign of its side
+// (Eq. MesoFlux); their moments, the macroscopic flux (Eq. MacroFlux), update the FP64
+// conserved variables W^{n+1} = W^n - dt/V F_macro (Eq. MacroUpdate, the moment of
+// Eq. Integration), whose equilibrium closes the implicit cell update of f (Eq.
+// fn+1).  f and W ping-pong between two buffers each; nothing else is stored between
+// steps.
 //
-// Face data is stored per cell and slot (normal, face centre relative to this cell
-// and to the far cell), so an interior face is evaluated by the threads of both its
-// cells with the same operands in the same order: both get the same interface
-// values, and the face fluxes cancel exactly in the sum over the two cells.
+// A face on the border of two tiles is evaluated by both, with the same operands in
+// the same order, so both get the same flux; within a tile the two cells of a face
+// add and subtract the same value, and the face fluxes cancel exactly in the sum over
+// the cells.
 #pragma once
 #include "d2q9.cuh"
 
@@ -32,8 +36,26 @@ template <> struct CoefR<float> {
     __device__ static float par(const Coefs &k, int p, int i) { return k.fbc_par[p][i]; }
 };
 
+// fbar+ = a f^n + b feq(W^n) of one cell (Eq. fbarplus), with f^n and feq(W^n) returned.
 template <int P>
-__global__ void __launch_bounds__(TILE_MAX)
+__device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict__ fin, const double *__restrict__ Wn,
+                                         int64_t g, int64_t np, const CoefR<typename Store<P>::R> &k,
+                                         typename Store<P>::R fn[NQ], typename Store<P>::R fe[NQ],
+                                         typename Store<P>::R fbp[NQ])
+{
+    using R = typename Store<P>::R;
+    R rho, ux, uy;
+    macro_of<R>(Wn[g], Wn[np + g], Wn[2 * np + g], rho, ux, uy);
+    feq9f<R>(rho, ux, uy, fe);
+#pragma unroll
+    for (int a = 0; a < NQ; a++) {
+        fn[a] = Store<P>::dec(fin[a * np + g], fe[a], a);
+        fbp[a] = k.a * fn[a] + k.b * fe[a];
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(TILED_THREADS, P == P_FP64 ? 1 : 4)
 k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__restrict__ fin,
              typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn, double *__restrict__ Wout)
 {
@@ -42,6 +64,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LOC_MAX]
     R *s_sig = s_fbp + NQ * LOC_MAX;                 // [2 NQ][SIG_MAX]
+    R *s_flux = s_sig + 2 * NQ * SIG_MAX;            // [NQ][LF_MAX]
 
     const int t = blockIdx.x, tid = threadIdx.x;
     const int c0 = m.tile_c0[t];
@@ -50,40 +73,34 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int n_loc = n_int + (m.tile_h0[t + 1] - h0);
     const int n_sig = n_int + m.tile_nh1[t];
     const int s0 = m.tile_s0[t];
-    const int64_t np = m.npad;
+    const int f0 = m.tile_f0[t];
+    const int n_lf = m.tile_f0[t + 1] - f0;
+    const int64_t np = m.npad, nlf = m.n_lf;
     const CoefR<R> k(c);
-    const R *geo = static_cast<const R *>(m.sl_geo);
+    const R *sld = static_cast<const R *>(m.sl_d);
+    const R *geo = static_cast<const R *>(m.lf_geo);
     const R *ainv = static_cast<const R *>(m.ainv);
 
-    // ---- phase 1: fbar+ = a f^n + b feq(W^n) for own cells (kept in registers) and halos
+    // ---- phase 1: fbar+ of the tile's cells and both halo rings; a thread keeps f^n of
+    // its own cell (cell tid) in registers for the update
     const bool active = tid < n_int;
     const int64_t g = c0 + tid;
-    R fn[NQ], feqn[NQ];
-    R rho_n = R(1), ux_n = R(0), uy_n = R(0);
-    double w0n = 1.0, w1n = 0.0, w2n = 0.0;
-    if (active) {
-        w0n = Wn[g]; w1n = Wn[np + g]; w2n = Wn[2 * np + g];
-        macro_of<R>(w0n, w1n, w2n, rho_n, ux_n, uy_n);
-        feq9f<R>(rho_n, ux_n, uy_n, feqn);
+    R fn[NQ];
+    for (int i = tid; i < n_loc; i += TILED_THREADS) {
+        const int64_t gi = i < n_int ? (int64_t)c0 + i : (int64_t)m.halo[h0 + i - n_int];
+        R fx[NQ], fe[NQ], fb[NQ];
+        cell_fbp<P>(fin, Wn, gi, np, k, fx, fe, fb);
 #pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            fn[a] = SP::dec(fin[a * np + g], feqn[a], a);
-            s_fbp[a * LOC_MAX + tid] = k.a * fn[a] + k.b * feqn[a];
+        for (int a = 0; a < NQ; a++) s_fbp[a * LOC_MAX + i] = fb[a];
+        if (i == tid) {
+#pragma unroll
+            for (int a = 0; a < NQ; a++) fn[a] = fx[a];
         }
-    }
-    for (int i = n_int + tid; i < n_loc; i += blockDim.x) {
-        const int64_t gh = m.halo[h0 + i - n_int];
-        R rho, ux, uy, fe[NQ];
-        macro_of<R>(Wn[gh], Wn[np + gh], Wn[2 * np + gh], rho, ux, uy);
-        feq9f<R>(rho, ux, uy, fe);
-#pragma unroll
-        for (int a = 0; a < NQ; a++)
-            s_fbp[a * LOC_MAX + i] = k.a * SP::dec(fin[a * np + gh], fe[a], a) + k.b * fe[a];
     }
     __syncthreads();
 
     // ---- phase 2: LLSR gradient sigma = A^{-1} sum_k d_k (fbar+_k - fbar+_j), d = x_k - x_j
-    for (int i = tid; i < n_sig; i += blockDim.x) {
+    for (int i = tid; i < n_sig; i += TILED_THREADS) {
         const int64_t gi = i < n_int ? (int64_t)c0 + i : (int64_t)m.halo[h0 + i - n_int];
         const uint16_t *nb = m.sig_nb + (int64_t)(s0 + i) * MAXF;
         R bx[NQ], by[NQ];
@@ -93,13 +110,23 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         for (int sl = 0; sl < MAXF; sl++) {
             const int kk = nb[sl];
             if (kk == NO_LOCAL) continue;
-            const R *G = geo + (int64_t)(6 * sl) * np + gi;
-            const R dx = G[2 * np] - G[4 * np], dy = G[3 * np] - G[5 * np];
+            const R dx = sld[(2 * sl) * np + gi], dy = sld[(2 * sl + 1) * np + gi];
+            if (kk < SYM_X) {
 #pragma unroll
-            for (int a = 0; a < NQ; a++) {
-                const R d = s_fbp[a * LOC_MAX + kk] - s_fbp[a * LOC_MAX + i];
-                bx[a] += dx * d;
-                by[a] += dy * d;
+                for (int a = 0; a < NQ; a++) {
+                    const R d = s_fbp[a * LOC_MAX + kk] - s_fbp[a * LOC_MAX + i];
+                    bx[a] += dx * d;
+                    by[a] += dy * d;
+                }
+            } else {
+                // symmetry ghost: the cell's own fbar+ of the mirrored velocity (Sec. III)
+                const bool mx = kk == SYM_X;
+#pragma unroll
+                for (int a = 0; a < NQ; a++) {
+                    const R d = s_fbp[(mx ? MIRROR_X(a) : MIRROR_Y(a)) * LOC_MAX + i] - s_fbp[a * LOC_MAX + i];
+                    bx[a] += dx * d;
+                    by[a] += dy * d;
+                }
             }
         }
         const R axx = ainv[gi], axy = ainv[np + gi], ayy = ainv[2 * np + gi];
@@ -110,32 +137,25 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         }
     }
     __syncthreads();
-    if (!active) return;
 
-    // ---- phase 3: faces of the own cell, mesoscopic flux
-    R F[NQ];
-#pragma unroll
-    for (int a = 0; a < NQ; a++) F[a] = R(0);
-    const uint16_t *my_nb = m.sig_nb + (int64_t)(s0 + tid) * MAXF;
-#pragma unroll
-    for (int sl = 0; sl < MAXF; sl++) {
-        const int kind = m.sl_kind[sl * np + g];
-        if (kind == SK_NONE) continue;
-        const R *G = geo + (int64_t)(6 * sl) * np + g;
-        const R nx = G[0], ny = G[np], rmx = G[2 * np], rmy = G[3 * np];
-        if (kind == SK_INTERIOR) {
-            const R rox = G[4 * np], roy = G[5 * np];
-            const int o = my_nb[sl];
+    // ---- phase 3: every local face once; flux s f_b from the first side to the second
+    for (int lf = tid; lf < n_lf; lf += TILED_THREADS) {
+        const uint32_t ab = m.lf_ab[f0 + lf];
+        const int A = (int)(ab & 0xFFFFu), B = (int)(ab >> 16);
+        const R *G = geo + f0 + lf;
+        const R nx = G[0], ny = G[nlf], rax = G[2 * nlf], ray = G[3 * nlf];
+        if (!(B & LF_SECOND)) {
+            const R rbx = G[4 * nlf], rby = G[5 * nlf];
             R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
                 const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
-                const R A = s_fbp[a * LOC_MAX + tid] + (rmx - ex) * s_sig[(2 * a) * SIG_MAX + tid] +
-                            (rmy - ey) * s_sig[(2 * a + 1) * SIG_MAX + tid];
-                const R B = s_fbp[a * LOC_MAX + o] + (rox - ex) * s_sig[(2 * a) * SIG_MAX + o] +
-                            (roy - ey) * s_sig[(2 * a + 1) * SIG_MAX + o];
-                fbar[a] = s > k.tie ? A : (s < -k.tie ? B : R(0.5) * (A + B));
+                const R FA = s_fbp[a * LOC_MAX + A] + (rax - ex) * s_sig[(2 * a) * SIG_MAX + A] +
+                             (ray - ey) * s_sig[(2 * a + 1) * SIG_MAX + A];
+                const R FB = s_fbp[a * LOC_MAX + B] + (rbx - ex) * s_sig[(2 * a) * SIG_MAX + B] +
+                             (rby - ey) * s_sig[(2 * a + 1) * SIG_MAX + B];
+                fbar[a] = s > k.tie ? FA : (s < -k.tie ? FB : R(0.5) * (FA + FB));
                 w0 += fbar[a];
                 if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
@@ -146,15 +166,56 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
-                F[a] += s * ((fbar[a] + k.b * feqb[a]) * k.c);
+                s_flux[a * LF_MAX + lf] = s * ((fbar[a] + k.b * feqb[a]) * k.c);
+            }
+        } else if (c.bc_kind[B & 0xFF] == BK_SYMMETRY) {
+            // symmetry face of cell A: the far side is A's mirror ghost, whose
+            // reconstruction of xi is A's own reconstruction of the mirrored velocity
+            // (same fbar+, reflected gradient and offset); tangential velocities are
+            // their own mirror images.  Then as on an interior face.
+            const bool mx = (nx < R(0) ? -nx : nx) > (ny < R(0) ? -ny : ny);
+            R rec[NQ];
+#pragma unroll
+            for (int a = 0; a < NQ; a++)
+                rec[a] = s_fbp[a * LOC_MAX + A] + (rax - R(EX(a)) * k.dt) * s_sig[(2 * a) * SIG_MAX + A] +
+                         (ray - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * SIG_MAX + A];
+            R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
+#pragma unroll
+            for (int a = 0; a < NQ; a++) {
+                const R s = xdot<R>(a, nx, ny);
+                fbar[a] = s < -k.tie ? (mx ? rec[MIRROR_X(a)] : rec[MIRROR_Y(a)]) : rec[a];
+                w0 += fbar[a];
+                if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
+                if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+            }
+            R ux, uy, feqb[NQ];
+            vel_of<R>(w0, w1, w2, ux, uy);
+            feq9f<R>(w0, ux, uy, feqb);
+            R px_ = R(0), py_ = R(0);
+#pragma unroll
+            for (int a = 0; a < NQ; a++) {
+                const R s = xdot<R>(a, nx, ny);
+                const R fl = s * ((fbar[a] + k.b * feqb[a]) * k.c);
+                s_flux[a * LF_MAX + lf] = fl;
+                px_ += R(EX(a)) * fl;
+                py_ += R(EY(a)) * fl;
+            }
+            if (m.force) {
+                atomicAdd(&m.force[2 * (B & 0xFF)], to_f64<R>(px_));
+                atomicAdd(&m.force[2 * (B & 0xFF) + 1], to_f64<R>(py_));
             }
         } else {
-            const int p = kind;
+            // boundary face of cell A (an interior cell of the tile): Sec. III rules
+            const int p = B & 0xFF;
             const int bk = c.bc_kind[p];
-            R rb = rho_n, ubx = R(0), uby = R(0);
+            const int64_t gA = (int64_t)c0 + A;
+            R fnA[NQ], feqA[NQ], fbA[NQ], rhoA, uxA, uyA;
+            cell_fbp<P>(fin, Wn, gA, np, k, fnA, feqA, fbA);
+            macro_of<R>(Wn[gA], Wn[np + gA], Wn[2 * np + gA], rhoA, uxA, uyA);
+            R rb = rhoA, ubx = R(0), uby = R(0);
             if (bk == BK_MOVING_WALL) { ubx = CoefR<R>::par(c, p, 0); uby = CoefR<R>::par(c, p, 1); }
             else if (bk == BK_FARFIELD) { rb = CoefR<R>::par(c, p, 0); ubx = CoefR<R>::par(c, p, 1); uby = CoefR<R>::par(c, p, 2); }
-            else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
+            else if (bk == BK_OUTLET) { ubx = uxA; uby = uyA; }
             R feqb[NQ];
             feq9f<R>(rb, ubx, uby, feqb);
             R px_ = R(0), py_ = R(0);
@@ -163,13 +224,13 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 const R s = xdot<R>(a, nx, ny);
                 R fb;
                 if (s < -k.tie) {
-                    fb = feqb[a] + (fn[a] - feqn[a]);     // non-equilibrium extrapolation
+                    fb = feqb[a] + (fnA[a] - feqA[a]);     // non-equilibrium extrapolation
                 } else {
-                    const R A = s_fbp[a * LOC_MAX + tid] + (rmx - R(EX(a)) * k.dt) * s_sig[(2 * a) * SIG_MAX + tid] +
-                                (rmy - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * SIG_MAX + tid];
-                    fb = (A + k.b * feqb[a]) * k.c;
+                    const R FA = s_fbp[a * LOC_MAX + A] + (rax - R(EX(a)) * k.dt) * s_sig[(2 * a) * SIG_MAX + A] +
+                                 (ray - R(EY(a)) * k.dt) * s_sig[(2 * a + 1) * SIG_MAX + A];
+                    fb = (FA + k.b * feqb[a]) * k.c;
                 }
-                F[a] += s * fb;
+                s_flux[a * LF_MAX + lf] = s * fb;
                 px_ += R(EX(a)) * (s * fb);
                 py_ += R(EY(a)) * (s * fb);
             }
@@ -179,8 +240,29 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
             }
         }
     }
+    __syncthreads();
+    if (!active) return;
+
+    // ---- mesoscopic flux of the own cell (Eq. MesoFlux), ascending face id
+    R F[NQ];
+#pragma unroll
+    for (int a = 0; a < NQ; a++) F[a] = R(0);
+#pragma unroll
+    for (int sl = 0; sl < MAXF; sl++) {
+        const unsigned v = m.cell_lf[sl * np + g];
+        if (v == LF_NONE) continue;
+        const int lf = (int)(v & (LF_SECOND - 1u));
+        if (v & LF_SECOND) {
+#pragma unroll
+            for (int a = 0; a < NQ; a++) F[a] -= s_flux[a * LF_MAX + lf];
+        } else {
+#pragma unroll
+            for (int a = 0; a < NQ; a++) F[a] += s_flux[a * LF_MAX + lf];
+        }
+    }
 
     // ---- macroscopic flux (moments of F) -> W^{n+1} in FP64; cell update f^{n+1} (Eq. fn+1)
+    const double w0n = Wn[g], w1n = Wn[np + g], w2n = Wn[2 * np + g];
     const R dtv = static_cast<const R *>(m.dtV)[g];
     R M0 = R(0), M1 = R(0), M2 = R(0);
 #pragma unroll
@@ -198,8 +280,8 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     if constexpr (P == P_FP64) {
         macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
     } else {
-        // FP32 compute: W^{n+1} in FP32 from the FP32 copies already at hand
-        rho1 = rho_n - d0;
+        // FP32 compute: W^{n+1} in FP32 from the FP32 copies of W^n
+        rho1 = from_f64<R>(w0n) - d0;
         vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
     }
     feq9f<R>(rho1, ux1, uy1, feq1);
@@ -213,11 +295,16 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 }
 
 template <int P> constexpr size_t tiled_smem() {
-    return sizeof(typename Store<P>::R) * (size_t)(NQ * LOC_MAX + 2 * NQ * SIG_MAX);
+    return sizeof(typename Store<P>::R) * (size_t)(NQ * LOC_MAX + 2 * NQ * SIG_MAX + NQ * LF_MAX);
 }
 
 template <int P> cudaError_t prepare_tiled_p() {
-    return cudaFuncSetAttribute(k_step_tiled<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_smem<P>());
+    cudaError_t e = cudaFuncSetAttribute(k_step_tiled<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_smem<P>());
+    // all of the unified L1/shared array as shared memory: four FP32 tiles per SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step_tiled<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 template <int P>
@@ -226,7 +313,7 @@ cudaError_t launch_tiled_p(const TiledMesh &m, const Coefs &c, const void *fin, 
 {
     using T = typename Store<P>::T;
     if (m.n_tiles <= 0) return cudaSuccess;
-    k_step_tiled<P><<<m.n_tiles, TILE_MAX, tiled_smem<P>(), st>>>(m, c, static_cast<const T *>(fin),
+    k_step_tiled<P><<<m.n_tiles, TILED_THREADS, tiled_smem<P>(), st>>>(m, c, static_cast<const T *>(fin),
                                                                   static_cast<T *>(fout), Wn, Wout);
     return cudaGetLastError();
 }

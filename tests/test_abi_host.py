@@ -95,7 +95,8 @@ def test_last_error_message_is_set():
 @pytest.mark.parametrize("tile", [0, 32])
 @pytest.mark.parametrize("make", [lambda: M.couette(64), lambda: M.cavity(64),
                                   lambda: M.cylinder(128, 64, first=0.01, r_far=10.0),
-                                  lambda: M.periodic_box(24, 20, jitter=0.2, seed=4)])
+                                  lambda: M.periodic_box(24, 20, jitter=0.2, seed=4),
+                                  lambda: M.flat_plate(8, 24, 16, Re_L=2e3, h_le=0.5, h_wall=0.2)])
 def test_tile_construction_passes_host_index_checks(make, tile):
     """solver_create builds the tiles, halo rings and slot tables and checks every
     index the kernel will use before it touches the device: without a GPU it must get
@@ -108,3 +109,15 @@ def test_tile_construction_passes_host_index_checks(make, tile):
         assert e.name == "CUDA" and not torch.cuda.is_available(), str(e)
     else:
         assert s.info()["n_tiles"] >= 1
+
+
+def test_slanted_symmetry_line_is_rejected_on_the_host():
+    """Mirror images of D2Q9 velocities are lattice velocities only in lines of
+    constant x or y: a symmetry patch on the cylinder wall is BAD_BC, found before
+    any device work."""
+    import dataclasses
+    case = M.cylinder(32, 16, first=0.05, r_far=4.0)
+    bcs = [(0, M.BC_SYMMETRY, (0.0, 0.0, 0.0)), (1, M.BC_FARFIELD, (1.0, 0.1, 0.0))]
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver.from_case(dataclasses.replace(case, bcs=bcs), "fp32")
+    assert e.value.name == "BAD_BC"

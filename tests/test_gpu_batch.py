@@ -7,7 +7,9 @@ instance admitted mid-run.  Against the single-solver Cartesian kernel (the same
 device function inlined into another kernel, where the compiler may contract
 products and sums differently) the results agree within the FP32 parity tolerance
 that both meet against the FP64 oracle: relative L2 of u <= 1e-4 (1e-3 for bf16
-storage), max |rho| difference <= 1e-5.  One instance is also checked against the
+storage), max |rho| difference <= 1e-5 (1e-4 for bf16 storage, which keeps 8
+significant bits of the scaled deviation (f - feq)/w: two kernels that round a
+product differently drift apart by a few 1e-5 in rho over 300 steps).  One instance is also checked against the
 FP64 oracle with the FP32 tolerance of the parity tests.
 """
 import numpy as np
@@ -31,9 +33,9 @@ def _single(case, steps, precision="fp32"):
     return s.macros()
 
 
-def _close_to_single(rho, u, rho1, u1, tol_u=1e-4):
+def _close_to_single(rho, u, rho1, u1, tol_u=1e-4, tol_rho=1e-5):
     assert np.sqrt(np.sum((u - u1) ** 2) / np.sum(u1 ** 2)) <= tol_u
-    assert np.abs(rho - rho1).max() <= 1e-5
+    assert np.abs(rho - rho1).max() <= tol_rho
 
 
 MIX = [lambda: M.cavity(40, Re=400.0), lambda: M.cavity(100, Re=1000.0), lambda: M.couette(64),
@@ -50,7 +52,7 @@ def test_batch_instances_equal_single_solvers(precision):
     for ident, case in zip(ids, cases):
         rho, u = b.macros(ident)
         rho1, u1 = _single(case, 300, precision)
-        _close_to_single(rho, u, rho1, u1, 1e-4 if precision == "fp32" else 1e-3)
+        _close_to_single(rho, u, rho1, u1, *((1e-4, 1e-5) if precision == "fp32" else (1e-3, 1e-4)))
 
 
 def test_result_same_alone_and_in_the_mix_and_late_admission():

@@ -57,7 +57,48 @@ def _random_state(case, seed, amp=0.03):
     return 1.0 + amp * rng.uniform(-1, 1, n), amp * rng.uniform(-1, 1, (n, 2))
 
 
+def _sym_channel():
+    """Ragged uniform grid: symmetry on the left and top, moving wall below, outlet right."""
+    mesh = M.cartesian(37, 23, 37.0, 23.0)
+    bcs = [(0, M.BC_MOVING_WALL, (0.05, 0.0, 0.0)), (1, M.BC_OUTLET, (0, 0, 0)),
+           (2, M.BC_SYMMETRY, (0, 0, 0)), (3, M.BC_SYMMETRY, (0, 0, 0))]
+    return M.Case("sym_channel", mesh, bcs, tau=0.05, dt=0.25)
+
+
+def _sym_box():
+    """Symmetry lines on all four sides (mirror ghosts of ghosts at the corners)."""
+    mesh = M.cartesian(20, 18, 20.0, 18.0)
+    bcs = [(p, M.BC_SYMMETRY, (0, 0, 0)) for p in range(4)]
+    return M.Case("sym_box", mesh, bcs, tau=0.06, dt=0.3)
+
+
+def _sym_half_jittered():
+    mesh = M.cartesian(16, 8, 16.0, 8.0, jitter=0.2, seed=5)
+    bcs = [(3, M.BC_PERIODIC, (1, 16.0, 0.0)), (1, M.BC_PERIODIC, (3, -16.0, 0.0)),
+           (0, M.BC_MOVING_WALL, (0.05, 0.0, 0.0)), (2, M.BC_SYMMETRY, (0, 0, 0))]
+    return M.Case("sym_half", mesh, bcs, tau=0.05, dt=0.2)
+
+
+def _hybrid_periodic():
+    mesh = M.hybrid(24, 20, 24.0, 20.0, tri_from=0.3, jitter=0.2, seed=4)
+    bcs = [(3, M.BC_PERIODIC, (1, 24.0, 0.0)), (1, M.BC_PERIODIC, (3, -24.0, 0.0)),
+           (0, M.BC_PERIODIC, (2, 0.0, 20.0)), (2, M.BC_PERIODIC, (0, 0.0, -20.0))]
+    return M.Case("hybrid_periodic", mesh, bcs, tau=0.05, dt=0.1)
+
+
+def _hybrid_couette():
+    base = M.couette(32)
+    mesh = M.hybrid(4, 32, 4.0 / 32, 1.0, tri_from=0.0, jitter=0.1, seed=5, quad_rows=1)
+    return dataclasses.replace(base, mesh=mesh, dt=0.5 * base.dt)
+
+
 FP64_CASES = {
+    "hybrid_periodic_jittered": (_hybrid_periodic, 300, 14),
+    "hybrid_couette_4x32": (_hybrid_couette, 2000, None),
+    "symmetry_channel_37x23": (_sym_channel, 300, 11),
+    "symmetry_box_20x18": (_sym_box, 300, 12),
+    "symmetry_half_channel_jittered": (_sym_half_jittered, 300, 13),
+    "flat_plate_32x16": (lambda: M.flat_plate(8, 24, 16, Re_L=2e3, h_le=0.5, h_wall=0.2), 400, None),
     "couette_4x64": (lambda: M.couette(64), 2000, None),
     "cavity_48": (lambda: M.cavity(48, Re=400.0), 1000, None),
     "mixed_bc_3x3": (_mixed3, 40, 7),
