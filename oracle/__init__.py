@@ -54,8 +54,13 @@ def _load():
             lib.oracle_init.argtypes = [i64, P, P, P, P]
             lib.oracle_residual.argtypes = [i64, P, P, P, P, P]
             lib.oracle_set_threads.argtypes = [i32]
+            lib.oracle_dvm_grid.argtypes = [i32, dbl, P, P]
+            lib.oracle_dvm_maxwell.argtypes = [dbl, dbl, dbl, dbl, i32, P, P, P]
+            lib.oracle_dvm_init.argtypes = [i64, i32, P, P, P, P, P, P, P]
+            lib.oracle_dvm_run.argtypes = mesh_args + [i32, P, P, dbl, dbl, dbl, i64, P, P]
             for fn in ("oracle_feq", "oracle_geometry", "oracle_gradient", "oracle_run",
-                       "oracle_init", "oracle_residual", "oracle_set_threads"):
+                       "oracle_init", "oracle_residual", "oracle_set_threads", "oracle_dvm_grid",
+                       "oracle_dvm_maxwell", "oracle_dvm_init", "oracle_dvm_run"):
                 getattr(lib, fn).restype = C.c_int
             _lib = lib
     return _lib
@@ -166,3 +171,62 @@ def residual(W, Ws, vol=None):
 def set_threads(n: int = 0) -> int:
     """Set (n > 0) and return the OpenMP thread count the oracle uses."""
     return int(_load().oracle_set_threads(int(n)))
+
+
+# ---------------------------------------------------------------- rarefied (discrete velocity grid)
+
+def dvm_grid(nv: int, vmax: float):
+    """Velocity nodes xi [Q, 2] (x fastest) and weights w [Q] of the nv x nv midpoint grid on
+    [-vmax, vmax]^2."""
+    xi = np.empty((nv * nv, 2)); w = np.empty(nv * nv)
+    _check(_load().oracle_dvm_grid(nv, vmax, _p(xi), _p(w)), "dvm_grid")
+    return xi, w
+
+
+def dvm_maxwell(rho, ux, uy, RT, xi, w) -> np.ndarray:
+    xi = np.ascontiguousarray(xi, np.float64); w = np.ascontiguousarray(w, np.float64)
+    out = np.empty(len(w))
+    _check(_load().oracle_dvm_maxwell(rho, ux, uy, RT, len(w), _p(xi), _p(w), _p(out)), "dvm_maxwell")
+    return out
+
+
+class DvmState:
+    """Rarefied oracle state: f [N, Q] (weighted), W [N, 4] = (rho, rho u, rho E)."""
+
+    def __init__(self, f, W):
+        self.f, self.W = f, W
+
+    @property
+    def rho(self):
+        return self.W[:, 0]
+
+    @property
+    def u(self):
+        return self.W[:, 1:3] / self.W[:, :1]
+
+    @property
+    def RT(self):
+        u = self.u
+        return self.W[:, 3] / self.W[:, 0] - 0.5 * (u ** 2).sum(1)
+
+
+def dvm_init(n_cells, xi, w, rho=None, u=None, RT=None, rho0=1.0, u0=(0.0, 0.0), RT0=0.5) -> DvmState:
+    xi = np.ascontiguousarray(xi, np.float64); w = np.ascontiguousarray(w, np.float64)
+    rho = np.full(n_cells, rho0) if rho is None else np.ascontiguousarray(rho, np.float64)
+    u = np.tile(np.asarray(u0, float), (n_cells, 1)) if u is None else np.ascontiguousarray(u, np.float64)
+    RT = np.full(n_cells, RT0) if RT is None else np.ascontiguousarray(RT, np.float64)
+    Q = len(w)
+    f = np.empty((n_cells, Q)); W = np.empty((n_cells, 4))
+    _check(_load().oracle_dvm_init(n_cells, Q, _p(xi), _p(w), _p(rho), _p(u), _p(RT), _p(f), _p(W)), "dvm_init")
+    return DvmState(f, W)
+
+
+def dvm_run(mesh, bcs, state: DvmState, xi, w, RT_wall: float, tau: float, dt: float, n_steps: int) -> DvmState:
+    """Advance the rarefied state in place (diffuse walls at R T_wall, periodic faces)."""
+    m = _MeshArgs(mesh, bcs)
+    xi = np.ascontiguousarray(xi, np.float64); w = np.ascontiguousarray(w, np.float64)
+    for a in (state.f, state.W):
+        assert a.flags.c_contiguous and a.dtype == np.float64
+    _check(_load().oracle_dvm_run(*m.args(), len(w), _p(xi), _p(w), RT_wall, tau, dt, n_steps,
+                                  _p(state.f), _p(state.W)), "dvm_run")
+    return state

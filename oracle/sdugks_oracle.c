@@ -21,6 +21,7 @@
  *   bc_kind[n_patches], bc_par[n_patches][3],
  *   f[n_cells][9], W[n_cells][3] = (rho, rho*u_x, rho*u_y).
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -562,6 +563,232 @@ int oracle_residual(int64_t nc, const double *W, const double *Ws, const double 
     *eps = den > 0 ? sqrt(num) / sqrt(den) : INFINITY;
     if (mass) *mass = ms;
     return OR_OK;
+}
+
+/* ===================================================================== rarefied
+ * The same scheme on a discrete velocity grid for rarefied flow (Sec. IV, micro
+ * cavity): Q velocities xi_q with quadrature weights w_q; the state is the
+ * weighted distribution f_q = w_q f(xi_q) (so moments are plain sums), and
+ * W = (rho, rho u, rho E) with psi = (1, xi, xi^2/2) of Eq. Macro.  Readings:
+ *  - the velocity grid: nv x nv nodes at the midpoints of a uniform partition of
+ *    [-vmax, vmax]^2, weights (2 vmax / nv)^2 (midpoint rule);
+ *  - the equilibrium: the Maxwellian of Eq. Feq with the exponent written as
+ *    |xi - u|^2 / (2 R T) in D = 2 dimensions, sampled at the nodes;
+ *  - the temperature from W: R T = (rho E - rho |u|^2 / 2) / rho (two translational
+ *    degrees of freedom);
+ *  - the relaxation time tau is a constant of the run;
+ *  - walls scatter diffusely (Sec. III, diffuse boundary): velocities entering the
+ *    gas (xi . N < 0) take the wall Maxwellian rho_w g(xi; u_w, R T_w) (Eq. 6001);
+ *    velocities leaving it take the characteristic reconstruction from the inner
+ *    cell with the wall Maxwellian as interface equilibrium (as reading A8); rho_w
+ *    makes the wall pass no mass (the balance of Eq. 6002, solved in closed form
+ *    because the outgoing values depend linearly on rho_w).
+ * Periodic faces work as in the continuum scheme; other boundary kinds are
+ * rejected. */
+
+int oracle_dvm_grid(int nv, double vmax, double *xi, double *w)
+{
+    if (nv <= 0 || !(vmax > 0) || !xi || !w) return OR_ERR_ARG;
+    const double h = 2.0 * vmax / nv;
+    for (int i = 0; i < nv; i++)          /* q = i + nv * j: x fastest */
+        for (int j = 0; j < nv; j++) {
+            const int q = j + nv * i;
+            xi[2 * q] = -vmax + (j + 0.5) * h;
+            xi[2 * q + 1] = -vmax + (i + 0.5) * h;
+            w[q] = h * h;
+        }
+    return OR_OK;
+}
+
+/* Weighted Maxwellian of Eq. Feq (D = 2) at every node. */
+static void dvm_maxwell(double rho, double ux, double uy, double RT, int Q, const double *xi, const double *w,
+                        double *out)
+{
+    const double pre = rho / (2.0 * M_PI * RT);
+    for (int q = 0; q < Q; q++) {
+        double cx = xi[2 * q] - ux, cy = xi[2 * q + 1] - uy;
+        out[q] = w[q] * pre * exp(-(cx * cx + cy * cy) / (2.0 * RT));
+    }
+}
+
+static void dvm_maxwell_W(const double W[4], int Q, const double *xi, const double *w, double *out)
+{
+    double rho = W[0], ux = W[1] / rho, uy = W[2] / rho;
+    double RT = W[3] / rho - 0.5 * (ux * ux + uy * uy);
+    dvm_maxwell(rho, ux, uy, RT, Q, xi, w, out);
+}
+
+/* Moments psi = (1, xi, xi^2/2) of a weighted distribution. */
+static void dvm_moments(int Q, const double *xi, const double *g, double W[4])
+{
+    W[0] = W[1] = W[2] = W[3] = 0.0;
+    for (int q = 0; q < Q; q++) {
+        double x = xi[2 * q], y = xi[2 * q + 1];
+        W[0] += g[q];
+        W[1] += x * g[q];
+        W[2] += y * g[q];
+        W[3] += 0.5 * (x * x + y * y) * g[q];
+    }
+}
+
+int oracle_dvm_maxwell(double rho, double ux, double uy, double RT, int Q, const double *xi, const double *w,
+                       double *out)
+{
+    if (Q <= 0 || !(rho > 0) || !(RT > 0) || !xi || !w || !out) return OR_ERR_ARG;
+    dvm_maxwell(rho, ux, uy, RT, Q, xi, w, out);
+    return OR_OK;
+}
+
+/* Initial state W = (rho, rho u, rho (|u|^2/2 + R T)) and f = feq(W) (as the continuum
+ * scheme starts from f = feq(W^0)). */
+int oracle_dvm_init(int64_t nc, int Q, const double *xi, const double *w, const double *rho, const double *u,
+                    const double *RT, double *f, double *W)
+{
+    if (nc <= 0 || Q <= 0 || !xi || !w || !rho || !u || !RT || !f || !W) return OR_ERR_ARG;
+    for (int64_t j = 0; j < nc; j++) {
+        double ux = u[2 * j], uy = u[2 * j + 1];
+        W[4 * j] = rho[j];
+        W[4 * j + 1] = rho[j] * ux;
+        W[4 * j + 2] = rho[j] * uy;
+        W[4 * j + 3] = rho[j] * (0.5 * (ux * ux + uy * uy) + RT[j]);
+        dvm_maxwell_W(&W[4 * j], Q, xi, w, &f[(size_t)Q * j]);
+    }
+    return OR_OK;
+}
+
+typedef struct {
+    double *fbp, *sig, *fb, *F;
+} dwork;
+
+/* One step of the scheme (Sec. II, steps in the paper's order, as in one_step) on
+ * the velocity grid; RTw is the wall temperature R T_w. */
+static void dvm_step(const omesh *m, int Q, const double *xi, const double *w, double RTw, double tau, double dt,
+                     double *f, double *W, dwork *k)
+{
+    const int64_t nc = m->nc, nf = m->nf;
+    const double a_plus = (2.0 * tau - dt) / (2.0 * tau);
+    const double b_plus = dt / (2.0 * tau);
+    const double c_face = 2.0 * tau / (2.0 * tau + dt);
+
+    /* step 2, Eq. fbarplus */
+#pragma omp parallel
+    {
+        double *fe = malloc(sizeof(double) * Q);
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < nc; j++) {
+            dvm_maxwell_W(&W[4 * j], Q, xi, w, fe);
+            for (int q = 0; q < Q; q++)
+                k->fbp[(size_t)Q * j + q] = a_plus * f[(size_t)Q * j + q] + b_plus * fe[q];
+        }
+        free(fe);
+    }
+    /* step 3, LLSR gradient of every velocity's fbar+ */
+    llsr(m, k->fbp, Q, k->sig);
+
+    /* steps 3-7 at every face */
+#pragma omp parallel
+    {
+        double *fbar = malloc(sizeof(double) * Q), *g = malloc(sizeof(double) * Q);
+#pragma omp for schedule(static)
+        for (int64_t fc = 0; fc < nf; fc++) {
+            int64_t o = m->own[fc], kc = m->nbr[fc];
+            const double *n = &m->nl[2 * fc], *xb = &m->xf[2 * fc];
+            const double *xo = &m->xc[2 * o];
+            double *fbf = &k->fb[(size_t)Q * fc];
+            int64_t kk = kc >= 0 ? kc : m->ghost[fc];
+            if (kk >= 0) {
+                const double *xk = kc >= 0 ? &m->xc[2 * kc] : &m->gpos[2 * fc];
+                for (int q = 0; q < Q; q++) {
+                    double s = xi[2 * q] * n[0] + xi[2 * q + 1] * n[1];
+                    double px = xb[0] - xi[2 * q] * dt, py = xb[1] - xi[2 * q + 1] * dt;
+                    const double *so = &k->sig[2 * ((size_t)Q * o + q)], *sk = &k->sig[2 * ((size_t)Q * kk + q)];
+                    double from_o = k->fbp[(size_t)Q * o + q] + (px - xo[0]) * so[0] + (py - xo[1]) * so[1];
+                    double from_k = k->fbp[(size_t)Q * kk + q] + (px - xk[0]) * sk[0] + (py - xk[1]) * sk[1];
+                    fbar[q] = s > TIE ? from_o : (s < -TIE ? from_k : 0.5 * (from_o + from_k));
+                }
+                double Wb[4];
+                dvm_moments(Q, xi, fbar, Wb);               /* step 5 */
+                dvm_maxwell_W(Wb, Q, xi, w, g);             /* step 6 */
+                for (int q = 0; q < Q; q++) fbf[q] = (fbar[q] + b_plus * g[q]) * c_face;   /* step 7 */
+            } else {
+                int p = (int)(-1 - kc);
+                double uwx = 0.0, uwy = 0.0;
+                if (m->bck[p] == KIND_MOVING_WALL) { uwx = m->bcp[3 * p]; uwy = m->bcp[3 * p + 1]; }
+                dvm_maxwell(1.0, uwx, uwy, RTw, Q, xi, w, g);
+                double S_out = 0.0, G_out = 0.0, G_in = 0.0;
+                for (int q = 0; q < Q; q++) {
+                    double s = xi[2 * q] * n[0] + xi[2 * q + 1] * n[1];
+                    if (s < -TIE) {
+                        G_in += s * g[q];
+                    } else {
+                        double px = xb[0] - xi[2 * q] * dt, py = xb[1] - xi[2 * q + 1] * dt;
+                        const double *so = &k->sig[2 * ((size_t)Q * o + q)];
+                        fbar[q] = k->fbp[(size_t)Q * o + q] + (px - xo[0]) * so[0] + (py - xo[1]) * so[1];
+                        S_out += s * fbar[q];
+                        G_out += s * g[q];
+                    }
+                }
+                double rho_w = -c_face * S_out / (c_face * b_plus * G_out + G_in);
+                for (int q = 0; q < Q; q++) {
+                    double s = xi[2 * q] * n[0] + xi[2 * q + 1] * n[1];
+                    fbf[q] = s < -TIE ? rho_w * g[q] : (fbar[q] + b_plus * rho_w * g[q]) * c_face;
+                }
+            }
+        }
+        free(fbar); free(g);
+    }
+
+    /* step 8 and steps 1, 9-11 per cell */
+    const double r = dt / tau;
+#pragma omp parallel
+    {
+        double *Fj = malloc(sizeof(double) * Q), *fe = malloc(sizeof(double) * Q);
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < nc; j++) {
+            for (int q = 0; q < Q; q++) Fj[q] = 0.0;
+            for (int64_t e = m->cs[j]; e < m->cs[j + 1]; e++) {
+                int64_t fc = m->cl[e];
+                double sg = (m->own[fc] == j) ? 1.0 : -1.0;
+                for (int q = 0; q < Q; q++) {
+                    double s = xi[2 * q] * m->nl[2 * fc] + xi[2 * q + 1] * m->nl[2 * fc + 1];
+                    Fj[q] += sg * s * k->fb[(size_t)Q * fc + q];
+                }
+            }
+            double Mj[4];
+            dvm_moments(Q, xi, Fj, Mj);
+            for (int d = 0; d < 4; d++) W[4 * j + d] -= dt / m->vol[j] * Mj[d];
+            dvm_maxwell_W(&W[4 * j], Q, xi, w, fe);
+            for (int q = 0; q < Q; q++)
+                f[(size_t)Q * j + q] = (f[(size_t)Q * j + q] - dt / m->vol[j] * Fj[q] + r * fe[q]) / (1.0 + r);
+        }
+        free(Fj); free(fe);
+    }
+}
+
+int oracle_dvm_run(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, const int64_t *own,
+                   const int64_t *nbr, int64_t nc, int npatch, const int32_t *bck, const double *bcp,
+                   int Q, const double *xi, const double *w, double RTw, double tau, double dt, int64_t n_steps,
+                   double *f, double *W)
+{
+    if (Q <= 0 || !xi || !w || !(RTw > 0) || !(tau > 0) || !(dt > 0) || n_steps < 0 || !f || !W) return OR_ERR_ARG;
+    omesh m;
+    int rc = omesh_build(&m, np, xy, nf, fpts, own, nbr, nc, npatch, bck, bcp);
+    if (rc) return rc;
+    for (int64_t fc = 0; fc < nf && !rc; fc++) {
+        if (nbr[fc] >= 0) continue;
+        int kd = bck[-1 - nbr[fc]];
+        if (kd != KIND_PERIODIC && kd != KIND_WALL && kd != KIND_MOVING_WALL) rc = OR_ERR_BC;
+    }
+    dwork k;
+    k.fbp = malloc(sizeof(double) * Q * nc);
+    k.sig = malloc(sizeof(double) * 2 * Q * nc);
+    k.fb = malloc(sizeof(double) * Q * nf);
+    k.F = NULL;
+    if (!k.fbp || !k.sig || !k.fb) rc = rc ? rc : OR_ERR_NOMEM;
+    for (int64_t s = 0; s < n_steps && !rc; s++) dvm_step(&m, Q, xi, w, RTw, tau, dt, f, W, &k);
+    free(k.fbp); free(k.sig); free(k.fb);
+    omesh_free(&m);
+    return rc;
 }
 
 int oracle_set_threads(int n)

@@ -380,6 +380,23 @@ def cylinder(n_theta: int = 512, n_r: int = 256, *, U: float = 0.1, Re: float = 
                 u0=(U, 0.0), meta=dict(U=U, Re=Re, cfl=cfl))
 
 
+def micro_cavity(n: int = 40, Kn: float = 1.0, *, U: float = 0.1, L: float = 1.0, nv: int = 100,
+                 vmax: float = 2.0, RT0: float = 0.5, cfl: float = 0.5) -> Case:
+    """Rarefied lid-driven micro cavity (Sec. IV): n x n cells on an L x L square,
+    diffuse walls at R T0, lid moving at U, on an nv x nv velocity grid over
+    [-vmax, vmax]^2.  The relaxation time follows from the Knudsen number with the
+    mean free path lambda = (mu / p) sqrt(pi R T0 / 2): tau = Kn L sqrt(2 / (pi R T0));
+    dt = cfl * (L / n) / (largest node speed)."""
+    m = cartesian(n, n, L, L)
+    bcs = [(m.patches["bottom"], BC_WALL, _bc_params()), (m.patches["right"], BC_WALL, _bc_params()),
+           (m.patches["left"], BC_WALL, _bc_params()), (m.patches["top"], BC_MOVING_WALL, _bc_params(U, 0.0))]
+    tau = Kn * L * math.sqrt(2.0 / (math.pi * RT0))
+    h = 2.0 * vmax / nv
+    vfast = math.sqrt(2.0) * (vmax - 0.5 * h)
+    return Case(f"micro_cavity_{n}_Kn{Kn:g}", m, bcs, tau=tau, dt=cfl * (L / n) / vfast,
+                meta=dict(U=U, Kn=Kn, nv=nv, vmax=vmax, RT0=RT0, L=L, cfl=cfl))
+
+
 def periodic_box(nx: int, ny: int, *, lx: float | None = None, ly: float | None = None,
                  jitter: float = 0.0, seed: int | None = None, tau: float = 0.05,
                  dt: float = 0.1) -> Case:

@@ -1,0 +1,119 @@
+"""CPU pins of the rarefied (discrete velocity grid) oracle.
+
+The rarefied variant runs the same scheme on a Q-node velocity grid with the
+Maxwellian of Eq. Feq and diffuse walls (Sec. III).  Pinned against: closed-form
+truncated Gaussian integrals of the grid (error bound of the midpoint rule), the
+uniform equilibrium as a fixed point, exact conservation of mass, momentum and
+energy on periodic meshes, the zero mass flux of a diffuse wall, and the
+collisionless Couette flow between diffuse plates, whose steady state is known in
+closed form on any velocity grid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_07347_gb300 import meshes as M
+
+
+def _erf_mass(a, b, mu, s):
+    """int_a^b N(x; mu, s^2) dx."""
+    return 0.5 * (math.erf((b - mu) / (s * math.sqrt(2))) - math.erf((a - mu) / (s * math.sqrt(2))))
+
+
+@pytest.mark.parametrize("nv,vmax,ux,uy,RT", [(100, 2.0, 0.1, 0.0, 0.5), (40, 3.0, -0.2, 0.15, 0.4)])
+def test_grid_and_maxwellian_against_truncated_gaussian(nv, vmax, ux, uy, RT):
+    """Eq. Feq on the midpoint grid: the discrete mass and mean velocity equal the
+    Gaussian integrals over the truncated square within the midpoint-rule bound
+    (h^2/24) * (2 vmax) * max|g''| per dimension."""
+    xi, w = O.dvm_grid(nv, vmax)
+    h = 2 * vmax / nv
+    assert np.allclose(w, h * h)
+    assert abs(xi[:, 0].min() + vmax - h / 2) < 1e-15 and abs(xi[:, 0].max() - vmax + h / 2) < 1e-15
+    g = O.dvm_maxwell(1.3, ux, uy, RT, xi, w)
+    s = math.sqrt(RT)
+    Ix, Iy = _erf_mass(-vmax, vmax, ux, s), _erf_mass(-vmax, vmax, uy, s)
+    bound = (h * h / 24) * (2 * vmax) / (s ** 3 * math.sqrt(2 * math.pi))     # max|g''| = 1/(s^3 sqrt(2 pi))
+    rho = g.sum()
+    assert abs(rho / 1.3 - Ix * Iy) <= 2.5 * bound
+    # first moment along x: int x N dx = mu I + s^2 (N(a) - N(b))
+    na = math.exp(-(-vmax - ux) ** 2 / (2 * RT)) / (s * math.sqrt(2 * math.pi))
+    nb = math.exp(-(vmax - ux) ** 2 / (2 * RT)) / (s * math.sqrt(2 * math.pi))
+    mx = ux * Ix + RT * (na - nb)
+    assert abs((xi[:, 0] * g).sum() / 1.3 - mx * Iy) <= 2.5 * bound * (vmax + 2)
+
+
+def _periodic(lx, ly):
+    return [(3, M.BC_PERIODIC, (1, lx, 0.0)), (1, M.BC_PERIODIC, (3, -lx, 0.0)),
+            (0, M.BC_PERIODIC, (2, 0.0, ly)), (2, M.BC_PERIODIC, (0, 0.0, -ly))]
+
+
+def test_uniform_equilibrium_is_fixed_point():
+    xi, w = O.dvm_grid(12, 2.0)
+    m = M.cartesian(4, 3, 1.0, 0.75, jitter=0.2, seed=2)
+    st = O.dvm_init(m.n_cells, xi, w, rho0=1.1, u0=(0.1, -0.05), RT0=0.45)
+    f0 = st.f.copy(); W0 = st.W.copy()
+    O.dvm_run(m, _periodic(1.0, 0.75), st, xi, w, 0.5, tau=0.05, dt=0.02, n_steps=30)
+    assert np.abs(st.f - f0).max() <= 1e-14 * np.abs(f0).max()
+    assert np.abs(st.W - W0).max() <= 1e-14
+
+
+def test_conservation_periodic():
+    """Mass, momentum and energy move only through face fluxes (Eq. MacroUpdate)."""
+    xi, w = O.dvm_grid(10, 2.5)
+    m = M.cartesian(6, 5, 1.2, 1.0, jitter=0.2, seed=3)
+    xy = m.meta["cell_xy_nominal"]
+    X, Y = 2 * np.pi * xy[:, 0] / 1.2, 2 * np.pi * xy[:, 1]
+    st = O.dvm_init(m.n_cells, xi, w, rho=1 + 0.05 * np.sin(X), u=np.stack([0.1 * np.cos(Y), 0.05 * np.sin(X)], 1),
+                    RT=0.5 + 0.03 * np.cos(X + Y))
+    vol = O.geometry(m, _periodic(1.2, 1.0))["vol"]
+    W0 = vol @ st.W
+    O.dvm_run(m, _periodic(1.2, 1.0), st, xi, w, 0.5, tau=0.02, dt=0.01, n_steps=60)
+    W1 = vol @ st.W
+    assert np.abs(W1 - W0).max() <= 1e-13 * abs(W0[0])
+    assert np.abs(st.W[:, 1]).std() > 1e-4
+
+
+def test_diffuse_walls_pass_no_mass():
+    """A closed box with diffuse walls (one moving) keeps its mass to round-off."""
+    xi, w = O.dvm_grid(16, 2.0)
+    m = M.cartesian(6, 6, 1.0, 1.0, jitter=0.15, seed=4)
+    bcs = [(0, M.BC_WALL, (0, 0, 0)), (1, M.BC_WALL, (0, 0, 0)), (3, M.BC_WALL, (0, 0, 0)),
+           (2, M.BC_MOVING_WALL, (0.1, 0, 0))]
+    st = O.dvm_init(m.n_cells, xi, w)
+    vol = O.geometry(m, bcs)["vol"]
+    m0 = vol @ st.W[:, 0]
+    O.dvm_run(m, bcs, st, xi, w, 0.5, tau=0.1, dt=0.01, n_steps=300)
+    assert abs(vol @ st.W[:, 0] - m0) <= 1e-13 * m0
+    assert np.abs(st.u).max() > 1e-3
+
+
+def test_collisionless_couette_closed_form():
+    """Free-molecular Couette flow between diffuse plates (bottom at rest, top moving
+    at U, periodic in x): every velocity keeps the Maxwellian of the wall it left, so
+    the steady state is uniform across the channel, f = A g_bottom for xi_y > 0 and
+    f = B g_top for xi_y < 0, with A and B fixed by zero net mass flux at each wall and
+    the total mass."""
+    nv, vmax, RT, U = 8, 2.0, 0.5, 0.2
+    xi, w = O.dvm_grid(nv, vmax)
+    m = M.cartesian(2, 6, 1.0 / 3, 1.0)
+    bcs = [(3, M.BC_PERIODIC, (1, 1.0 / 3, 0.0)), (1, M.BC_PERIODIC, (3, -1.0 / 3, 0.0)),
+           (0, M.BC_WALL, (0, 0, 0)), (2, M.BC_MOVING_WALL, (U, 0, 0))]
+    st = O.dvm_init(m.n_cells, xi, w, RT0=RT)
+    mass0 = st.W[:, 0].mean()
+    for _ in range(60):
+        O.dvm_run(m, bcs, st, xi, w, RT, tau=1e12, dt=0.02, n_steps=500)
+    gb = O.dvm_maxwell(1.0, 0.0, 0.0, RT, xi, w)
+    gt = O.dvm_maxwell(1.0, U, 0.0, RT, xi, w)
+    up, dn = xi[:, 1] > 0, xi[:, 1] < 0
+    # bottom wall re-emits what arrives from the top: A sum_up xi_y gb = B sum_dn |xi_y| gt
+    ratio = (np.abs(xi[dn, 1]) * gt[dn]).sum() / (xi[up, 1] * gb[up]).sum()
+    f_shape = np.where(up, ratio * gb, gt)
+    f_exact = f_shape * (st.f[0].sum() / f_shape.sum())
+    assert np.abs(st.f - f_exact).max() <= 1e-10 * f_exact.max()
+    # W moves by the same face fluxes as f: with no collisions its momentum is the
+    # momentum of f (both start at zero); its mass stays at the initial mass
+    np.testing.assert_allclose(st.W[:, 1], (xi[:, 0] * f_exact).sum(), rtol=1e-9)
+    np.testing.assert_allclose(st.W[:, 2], 0.0, atol=1e-12)
+    assert abs(st.W[:, 0].mean() - mass0) < 1e-12
