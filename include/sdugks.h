@@ -286,6 +286,53 @@ void sdugks_batch_destroy(sdugks_batch *b);
 
 void sdugks_solver_destroy(sdugks_solver *s);
 
+/* ---- rarefied flow on a discrete velocity grid (Sec. IV, micro cavity) ----------
+ * The same step (Sec. II) with the D2Q9 lattice replaced by nv x nv velocity nodes at
+ * the midpoints of a uniform partition of [-vmax, vmax]^2 (weights (2 vmax/nv)^2),
+ * the Maxwellian of Eq. Feq (exponent |xi - u|^2 / (2 R T), two dimensions) and
+ * W = (rho, rho u, rho E) with psi = (1, xi, xi^2/2) (Eq. Macro), R T = E - |u|^2/2.
+ * Boundary faces must be PERIODIC (paired), WALL or MOVING_WALL; walls scatter
+ * diffusely (Sec. III): velocities entering the gas take the wall Maxwellian at
+ * R T_wall with the density that makes the wall pass no mass (Eqs. 6001-6002),
+ * leaving ones the characteristic reconstruction from the inner cell.  Any other
+ * boundary kind gives BAD_BC at creation.  f is stored [cell][velocity] (weighted
+ * values f_q = w_q f(xi_q)), W [cell][4] in FP64.  Device memory: about
+ * 4 x (2 n_cells + n_faces) x Q bytes (FP32). */
+typedef struct sdugks_dvm sdugks_dvm;
+
+typedef struct {
+    int32_t nv;          /* velocity nodes per axis (Q = nv^2), 2..1024 */
+    double vmax;         /* the grid spans [-vmax, vmax]^2 */
+    double RT_wall;      /* R T of the walls (and the default initial state) */
+    double tau, dt;      /* relaxation time and time step (lattice units) */
+    int32_t precision;   /* SDUGKS_FP64 or SDUGKS_FP32 (f and the scratch arrays) */
+    int32_t graph_steps; /* steps per captured CUDA graph: 0 = 32, < 0 = no graphs */
+} sdugks_dvm_params;
+
+/* Create on the current device; stream may be NULL (legacy default stream).
+ * Errors: INVALID_ARG (NULL, nv out of range, non-positive vmax/RT_wall/tau/dt,
+ * precision), INVALID_MESH (more than 4 faces per cell), BAD_BC, OOM, CUDA. */
+int sdugks_dvm_create(const sdugks_mesh *mesh, const sdugks_dvm_params *params, void *stream, sdugks_dvm **out);
+
+/* Initial state W = (rho, rho u, rho (|u|^2/2 + R T)), f = feq(W).  rho[n], u[n][2],
+ * RT[n] host arrays in user cell order; NULL gives 1, (0, 0) and RT_wall. */
+int sdugks_dvm_init(sdugks_dvm *d, const double *rho, const double *u, const double *RT);
+
+/* n steps, asynchronous on the solver's stream. */
+int sdugks_dvm_step(sdugks_dvm *d, int64_t n);
+
+/* rho[n], u[n][2], RT[n] from W (host; any may be NULL; synchronises). */
+int sdugks_dvm_get_macros(sdugks_dvm *d, double *rho, double *u, double *RT);
+
+/* f[n][Q] (weighted, FP64) and W[n][4] (host; either may be NULL; synchronises). */
+int sdugks_dvm_get_state(sdugks_dvm *d, double *f, double *W);
+
+/* Sizes: cells, faces (periodic pairs merged), Q, device bytes. */
+int sdugks_dvm_sizes(const sdugks_dvm *d, int64_t *n_cells, int64_t *n_faces, int64_t *n_velocities,
+                     int64_t *device_bytes);
+
+void sdugks_dvm_destroy(sdugks_dvm *d);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *sdugks_last_error(void);
 

@@ -29,6 +29,7 @@ CU_UNITS = {
     "k_util.cu": [],
     "k_residual_noalloc.cu": [],
     "k_batch.cu": [],
+    "k_dvm.cu": [],
 }
 CXX_UNITS = ["sdugks_host.cpp"]
 HEADERS = ["sdugks_internal.h", "d2q9.cuh", "step_tiled.cuh", "step_cart.cuh"]

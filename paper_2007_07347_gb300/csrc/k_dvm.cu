@@ -1,0 +1,371 @@
+// k_dvm.cu -- the S-DUGKS step on a discrete velocity grid (rarefied flow, Sec. IV
+// micro cavity; diffuse walls of Sec. III).
+//
+// The mesh is small and the velocity grid large (10^4 nodes), so the work is spread
+// over velocities: one CTA per cell or per face walks all Q velocities with its
+// threads, and the moments a step needs (the interface W of every face, the
+// macroscopic flux of every cell) are block reductions in a fixed order.  Three
+// launches per step:
+//   k_dvm_fbp   per cell: fbar+ = a f + b feq(W^n)                      (Eq. fbarplus)
+//   k_dvm_face  per face: characteristic reconstruction from the upwind cell with its
+//               LLSR gradient evaluated on the spot (Eqs. fbpsource, fbar), interface
+//               moments and Maxwellian (Eqs. Macro, Feq), f_b (Eq. f_t_n+1); walls by
+//               diffuse scattering; writes xi . n l f_b per face and velocity
+//   k_dvm_cell  per cell: F = sum of its faces' fluxes (Eq. MesoFlux), its moments
+//               (Eq. MacroFlux) update W in FP64 (Eq. MacroUpdate), then f (Eq. fn+1)
+// W = (rho, rho u, rho E) per cell in FP64; f and the scratch arrays in the compute
+// precision.  The Maxwellian is that of Eq. Feq with exponent |xi - u|^2 / (2 R T),
+// D = 2, sampled at the nodes and multiplied by the node weights.
+#include "sdugks_internal.h"
+
+#include <cuda_runtime.h>
+
+namespace sdugks {
+namespace {
+
+template <class R> struct DvmR;
+template <> struct DvmR<double> {
+    double a, b, c, r, dt, tie, inv1r;
+    __device__ explicit DvmR(const Coefs &k) : a(k.a_plus), b(k.b_plus), c(k.c_face), r(k.r), dt(k.dt), tie(k.tie),
+                                               inv1r(k.inv1r) {}
+};
+template <> struct DvmR<float> {
+    float a, b, c, r, dt, tie, inv1r;
+    __device__ explicit DvmR(const Coefs &k) : a(k.fa_plus), b(k.fb_plus), c(k.fc_face), r(k.fr), dt(k.fdt),
+                                               tie(k.ftie), inv1r(k.finv1r) {}
+};
+
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+
+// Maxwellian parameters of one state, computed once per CTA in FP64.
+struct MaxP {
+    double pre, ux, uy, inv2RT;
+};
+__device__ __forceinline__ MaxP max_params(double rho, double mx, double my, double rE)
+{
+    MaxP p;
+    p.ux = mx / rho;
+    p.uy = my / rho;
+    const double RT = rE / rho - 0.5 * (p.ux * p.ux + p.uy * p.uy);
+    p.pre = rho / (2.0 * 3.14159265358979323846 * RT);
+    p.inv2RT = 1.0 / (2.0 * RT);
+    return p;
+}
+
+template <class R>
+__device__ __forceinline__ R maxwell(const R *sp, R x, R y, R w)
+{
+    // sp = {pre, ux, uy, inv2RT} in the compute precision
+    const R cx = x - sp[1], cy = y - sp[2];
+    return w * sp[0] * dexp(-(cx * cx + cy * cy) * sp[3]);
+}
+
+// Fixed-order block sum of NV per-thread values: warp sums by shuffles in the
+// compute precision, the per-warp results combined in FP64 by one thread; the result
+// in out[] on every thread.  Uses scratch[32 * NV] shared doubles.
+template <int NV, class R>
+__device__ __forceinline__ void block_sum(R v[NV], double *scratch, double out[NV])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        R x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) scratch[k * 32 + warp] = double(x);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double t = 0.0;
+            for (int w = 0; w < nw; w++) t += scratch[k * 32 + w];
+            scratch[k * 32] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) out[k] = scratch[k * 32];
+    __syncthreads();
+}
+
+// fbar+ of the cell's velocity q plus (r - xi dt) . sigma, sigma its LLSR gradient
+template <class R>
+__device__ __forceinline__ R reconstruct(const DvmMesh &m, const R *fbp, int64_t c, int64_t q, R rx, R ry, R xx,
+                                         R xy, R dt, const int32_t *nb, const R *d, const R *ai)
+{
+    const int64_t Q = m.Q;
+    const R v0 = fbp[c * Q + q];
+    R bx = R(0), by = R(0);
+#pragma unroll
+    for (int sl = 0; sl < MAXF; sl++) {
+        if (nb[sl] < 0) continue;
+        const R dv = fbp[(int64_t)nb[sl] * Q + q] - v0;
+        bx += d[2 * sl] * dv;
+        by += d[2 * sl + 1] * dv;
+    }
+    const R sx = ai[0] * bx + ai[1] * by, sy = ai[1] * bx + ai[2] * by;
+    return v0 + (rx - xx * dt) * sx + (ry - xy * dt) * sy;
+}
+
+template <class R>
+__global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
+                                                         const double *__restrict__ W, R *__restrict__ fbp)
+{
+    __shared__ R sp[4];
+    const int64_t c = blockIdx.x, Q = m.Q;
+    if (threadIdx.x == 0) {
+        const MaxP p = max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]);
+        sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
+    }
+    __syncthreads();
+    const DvmR<R> k(cf);
+    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
+#pragma unroll 2
+    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+        const R fe = maxwell<R>(sp, xi[2 * q], xi[2 * q + 1], wq[q]);
+        fbp[c * Q + q] = k.a * f[c * Q + q] + k.b * fe;
+    }
+}
+
+// SMEM: the interface distribution of the face between the two passes over the
+// velocities stays in shared memory (Q values); otherwise in the flux array itself.
+template <class R, bool SMEM>
+__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 4 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+                                                          const R *__restrict__ fbp, R *__restrict__ flux)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ double red[32 * 4];
+    __shared__ R sp[4];
+    __shared__ int32_t nb[2][MAXF];
+    __shared__ R dd[2][2 * MAXF], ai[2][3];
+    const int64_t fc = blockIdx.x, Q = m.Q;
+    const DvmR<R> k(cf);
+    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
+    const R *G = static_cast<const R *>(m.face_geo) + 6 * fc;
+    const R nx = G[0], ny = G[1], rox = G[2], roy = G[3], rkx = G[4], rky = G[5];
+    const int64_t o = m.face_own[fc];
+    const int32_t kn = m.face_nbr[fc];
+    const bool interior = kn >= 0;
+    if (threadIdx.x < 2 * MAXF) {
+        const int side = threadIdx.x / MAXF, sl = threadIdx.x % MAXF;
+        const int64_t cc = side == 0 ? o : (interior ? (int64_t)kn : o);
+        nb[side][sl] = m.cell_nb[cc * MAXF + sl];
+        dd[side][2 * sl] = static_cast<const R *>(m.cell_d)[(cc * MAXF + sl) * 2];
+        dd[side][2 * sl + 1] = static_cast<const R *>(m.cell_d)[(cc * MAXF + sl) * 2 + 1];
+        if (sl < 3) ai[side][sl] = static_cast<const R *>(m.ainv)[cc * 3 + sl];
+    }
+    __syncthreads();
+    R *out = flux + fc * Q;
+    R *fbuf = SMEM ? reinterpret_cast<R *>(dyn) : out;
+
+    if (interior) {
+        R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
+        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+            const R x = xi[2 * q], y = xi[2 * q + 1];
+            const R s = x * nx + y * ny;
+            R fb;
+            if (s > k.tie) fb = reconstruct<R>(m, fbp, o, q, rox, roy, x, y, k.dt, nb[0], dd[0], ai[0]);
+            else if (s < -k.tie) fb = reconstruct<R>(m, fbp, kn, q, rkx, rky, x, y, k.dt, nb[1], dd[1], ai[1]);
+            else fb = R(0.5) * (reconstruct<R>(m, fbp, o, q, rox, roy, x, y, k.dt, nb[0], dd[0], ai[0]) +
+                                reconstruct<R>(m, fbp, kn, q, rkx, rky, x, y, k.dt, nb[1], dd[1], ai[1]));
+            fbuf[q] = fb;
+            p0 += fb; p1 += x * fb; p2 += y * fb; p3 += R(0.5) * (x * x + y * y) * fb;
+        }
+        R part[4] = {p0, p1, p2, p3};
+        double Wb[4];
+        block_sum<4, R>(part, red, Wb);
+        if (threadIdx.x == 0) {
+            const MaxP p = max_params(Wb[0], Wb[1], Wb[2], Wb[3]);
+            sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
+        }
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+            const R x = xi[2 * q], y = xi[2 * q + 1];
+            const R s = x * nx + y * ny;
+            const R g = maxwell<R>(sp, x, y, wq[q]);
+            out[q] = s * ((fbuf[q] + k.b * g) * k.c);
+        }
+    } else {
+        // diffuse wall (Sec. III): entering velocities take rho_w g(u_w, R T_w), leaving
+        // ones the reconstruction with the wall Maxwellian; rho_w so that no mass passes
+        const int p = -1 - kn;
+        const int bk = cf.bc_kind[p];
+        const double uwx = bk == BK_MOVING_WALL ? cf.bc_par[p][0] : 0.0;
+        const double uwy = bk == BK_MOVING_WALL ? cf.bc_par[p][1] : 0.0;
+        if (threadIdx.x == 0) {
+            sp[0] = R(1.0 / (2.0 * 3.14159265358979323846 * RTw)); sp[1] = R(uwx); sp[2] = R(uwy);
+            sp[3] = R(1.0 / (2.0 * RTw));
+        }
+        __syncthreads();
+        R so = R(0), go = R(0), gi = R(0);
+        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+            const R x = xi[2 * q], y = xi[2 * q + 1];
+            const R s = x * nx + y * ny;
+            const R g = maxwell<R>(sp, x, y, wq[q]);
+            if (s < -k.tie) {
+                gi += s * g;
+            } else {
+                const R fb = reconstruct<R>(m, fbp, o, q, rox, roy, x, y, k.dt, nb[0], dd[0], ai[0]);
+                fbuf[q] = fb;
+                so += s * fb;
+                go += s * g;
+            }
+        }
+        R part[3] = {so, go, gi};
+        double tot[3];
+        block_sum<3, R>(part, red, tot);
+        const double rho_w = -double(k.c) * tot[0] / (double(k.c) * double(k.b) * tot[1] + tot[2]);
+        const R rw = R(rho_w);
+        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+            const R x = xi[2 * q], y = xi[2 * q + 1];
+            const R s = x * nx + y * ny;
+            const R g = maxwell<R>(sp, x, y, wq[q]);
+            out[q] = s < -k.tie ? s * (rw * g) : s * ((fbuf[q] + k.b * (rw * g)) * k.c);
+        }
+    }
+}
+
+// SMEM: the cell's flux sum F (Q values) is kept in shared memory between the two
+// passes; otherwise it is summed again from the face fluxes.
+template <class R, bool SMEM>
+__global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
+                                                          double *__restrict__ W, const R *__restrict__ flux)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    R *Fbuf = reinterpret_cast<R *>(dyn);
+    __shared__ double red[32 * 4];
+    __shared__ R sp[4];
+    __shared__ int32_t fid[MAXF];
+    const int64_t c = blockIdx.x, Q = m.Q;
+    const DvmR<R> k(cf);
+    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
+    if (threadIdx.x < MAXF) fid[threadIdx.x] = m.cell_face[c * MAXF + threadIdx.x];
+    __syncthreads();
+    auto F_of = [&](int64_t q) {
+        R F = R(0);
+#pragma unroll
+        for (int sl = 0; sl < MAXF; sl++) {
+            const int32_t v = fid[sl];
+            if (v < 0) continue;
+            const R x = flux[(int64_t)(v & (DVM_SECOND - 1)) * Q + q];
+            if (v & DVM_SECOND) F -= x; else F += x;
+        }
+        return F;
+    };
+    R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
+#pragma unroll 2
+    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+        const R x = xi[2 * q], y = xi[2 * q + 1];
+        const R F = F_of(q);
+        if (SMEM) Fbuf[q] = F;
+        p0 += F; p1 += x * F; p2 += y * F; p3 += R(0.5) * (x * x + y * y) * F;
+    }
+    R part[4] = {p0, p1, p2, p3};
+    double M[4];
+    block_sum<4, R>(part, red, M);
+    const double dtv = m.dtV[c];
+    if (threadIdx.x == 0) {
+        double Wn[4];
+        for (int d = 0; d < 4; d++) {
+            Wn[d] = W[4 * c + d] - dtv * M[d];
+            W[4 * c + d] = Wn[d];
+        }
+        const MaxP p = max_params(Wn[0], Wn[1], Wn[2], Wn[3]);
+        sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
+    }
+    __syncthreads();
+    const R rdtv = R(dtv);
+#pragma unroll 2
+    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
+        const R x = xi[2 * q], y = xi[2 * q + 1];
+        const R F = SMEM ? Fbuf[q] : F_of(q);
+        const R fe = maxwell<R>(sp, x, y, wq[q]);
+        const R num = f[c * Q + q] - rdtv * F + k.r * fe;
+        f[c * Q + q] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
+    }
+}
+
+// f = feq(W) per cell (the initial state)
+template <class R>
+__global__ void __launch_bounds__(DVM_THREADS) k_dvm_init(const DvmMesh m, const double *__restrict__ W,
+                                                          R *__restrict__ f)
+{
+    __shared__ R sp[4];
+    const int64_t c = blockIdx.x, Q = m.Q;
+    if (threadIdx.x == 0) {
+        const MaxP p = max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]);
+        sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
+    }
+    __syncthreads();
+    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
+    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) f[c * Q + q] = maxwell<R>(sp, xi[2 * q], xi[2 * q + 1], wq[q]);
+}
+
+// Largest per-velocity buffer kept in shared memory (bytes).
+constexpr size_t DVM_SMEM_MAX = 160 * 1024;
+
+template <class R> bool dvm_use_smem(int64_t Q) { return (size_t)Q * sizeof(R) <= DVM_SMEM_MAX; }
+
+template <class R>
+cudaError_t prepare_p(int64_t Q)
+{
+    if (!dvm_use_smem<R>(Q)) return cudaSuccess;
+    const int bytes = (int)((size_t)Q * sizeof(R));
+    cudaError_t e = cudaFuncSetAttribute(k_dvm_face<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dvm_cell<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dvm_face<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dvm_cell<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <class R>
+cudaError_t step_p(const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp, void *flux,
+                   cudaStream_t st)
+{
+    if (m.nc <= 0) return cudaSuccess;
+    k_dvm_fbp<R><<<(unsigned)m.nc, DVM_THREADS, 0, st>>>(m, c, static_cast<const R *>(f), W, static_cast<R *>(fbp));
+    if (dvm_use_smem<R>(m.Q)) {
+        const size_t bytes = (size_t)m.Q * sizeof(R);
+        k_dvm_face<R, true><<<(unsigned)m.nf, DVM_THREADS, bytes, st>>>(m, c, RTw, static_cast<const R *>(fbp),
+                                                                          static_cast<R *>(flux));
+        k_dvm_cell<R, true><<<(unsigned)m.nc, DVM_THREADS, bytes, st>>>(m, c, static_cast<R *>(f), W,
+                                                                          static_cast<const R *>(flux));
+    } else {
+        k_dvm_face<R, false><<<(unsigned)m.nf, DVM_THREADS, 0, st>>>(m, c, RTw, static_cast<const R *>(fbp),
+                                                                       static_cast<R *>(flux));
+        k_dvm_cell<R, false><<<(unsigned)m.nc, DVM_THREADS, 0, st>>>(m, c, static_cast<R *>(f), W,
+                                                                       static_cast<const R *>(flux));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_dvm_step(int prec, const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp,
+                            void *flux, cudaStream_t st)
+{
+    return prec == P_FP64 ? step_p<double>(m, c, RTw, f, W, fbp, flux, st)
+                          : step_p<float>(m, c, RTw, f, W, fbp, flux, st);
+}
+
+cudaError_t prepare_dvm(int prec, int64_t Q)
+{
+    return prec == P_FP64 ? prepare_p<double>(Q) : prepare_p<float>(Q);
+}
+
+cudaError_t launch_dvm_init(int prec, const DvmMesh &m, const double *W, void *f, cudaStream_t st)
+{
+    if (m.nc <= 0) return cudaSuccess;
+    if (prec == P_FP64) k_dvm_init<double><<<(unsigned)m.nc, DVM_THREADS, 0, st>>>(m, W, static_cast<double *>(f));
+    else k_dvm_init<float><<<(unsigned)m.nc, DVM_THREADS, 0, st>>>(m, W, static_cast<float *>(f));
+    return cudaGetLastError();
+}
+
+}  // namespace sdugks

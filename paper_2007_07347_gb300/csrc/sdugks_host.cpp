@@ -1693,3 +1693,287 @@ extern "C" void sdugks_batch_destroy(sdugks_batch *b)
     if (b->h_out) cudaFreeHost(b->h_out);
     delete b;
 }
+
+// ------------------------------------------------------------------ rarefied (discrete velocity grid)
+
+struct sdugks_dvm {
+    sdugks_dvm_params p{};
+    int prec = P_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int64_t n = 0, nf = 0, Q = 0;
+    size_t rs = 4, dbytes = 0;
+    char *dmem = nullptr;
+    DvmMesh dm{};
+    Coefs coefs{};
+    void *f = nullptr, *fbp = nullptr, *flux = nullptr;
+    double *W = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_len = 0;
+    bool initialised = false;
+};
+
+extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *prm, void *stream, sdugks_dvm **out)
+{
+    if (!out) return fail(SDUGKS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!m || !prm) return fail(SDUGKS_ERR_INVALID_ARG, "mesh or params is NULL");
+    if (prm->nv < 2 || prm->nv > 1024) return fail(SDUGKS_ERR_INVALID_ARG, "nv must be in [2, 1024]");
+    if (!(prm->vmax > 0) || !(prm->RT_wall > 0) || !(prm->tau > 0) || !(prm->dt > 0) || !std::isfinite(prm->vmax) ||
+        !std::isfinite(prm->RT_wall) || !std::isfinite(prm->tau) || !std::isfinite(prm->dt))
+        return fail(SDUGKS_ERR_INVALID_ARG, "vmax, RT_wall, tau and dt must be finite and > 0");
+    if (prm->precision != SDUGKS_FP64 && prm->precision != SDUGKS_FP32)
+        return fail(SDUGKS_ERR_INVALID_ARG, "precision must be FP64 or FP32");
+    for (int64_t f = 0; f < m->nf; f++) {
+        if (m->nbr[f] >= 0) continue;
+        const int k = m->bc_kind[-1 - m->nbr[f]];
+        if (k != SDUGKS_BC_PERIODIC && k != SDUGKS_BC_WALL && k != SDUGKS_BC_MOVING_WALL)
+            return fail(SDUGKS_ERR_BAD_BC, "rarefied solver: boundary kind %d (only periodic and diffuse walls)", k);
+    }
+    Faces F;
+    int rc = merge_periodic(*m, F);
+    if (rc) return rc;
+    const int64_t n = m->nc, nf = F.nf, Q = (int64_t)prm->nv * prm->nv;
+    for (int64_t f = 0; f < nf; f++)
+        if (F.own[f] == F.nbr[f]) return fail(SDUGKS_ERR_INVALID_MESH, "periodic pair joins a cell to itself");
+
+    // cell slots in ascending merged face id; LLSR neighbours, offsets and inverse
+    std::vector<int32_t> cface((size_t)n * MAXF, -1), cnb((size_t)n * MAXF, -1);
+    std::vector<double> cd((size_t)n * MAXF * 2, 0.0), ainv((size_t)n * 3, 0.0), dtv(n);
+    std::vector<int> ns(n, 0);
+    for (int64_t f = 0; f < nf; f++)
+        for (int side = 0; side < 2; side++) {
+            const int64_t c = side == 0 ? F.own[f] : F.nbr[f];
+            if (c < 0) continue;
+            if (ns[c] >= MAXF) return fail(SDUGKS_ERR_INVALID_MESH, "cell %lld has more than %d faces", (long long)c, MAXF);
+            const int sl = ns[c]++;
+            cface[(size_t)c * MAXF + sl] = (int32_t)f | (side ? DVM_SECOND : 0);
+            const int64_t k = side == 0 ? F.nbr[f] : F.own[f];
+            if (k >= 0) {
+                cnb[(size_t)c * MAXF + sl] = (int32_t)k;
+                const double *rme = side == 0 ? &F.ro[2 * f] : &F.rk[2 * f];
+                const double *rot = side == 0 ? &F.rk[2 * f] : &F.ro[2 * f];
+                cd[((size_t)c * MAXF + sl) * 2] = rme[0] - rot[0];
+                cd[((size_t)c * MAXF + sl) * 2 + 1] = rme[1] - rot[1];
+            }
+        }
+    for (int64_t c = 0; c < n; c++) {
+        double axx = 0, axy = 0, ayy = 0;
+        for (int sl = 0; sl < MAXF; sl++) {
+            if (cnb[(size_t)c * MAXF + sl] < 0) continue;
+            const double dx = cd[((size_t)c * MAXF + sl) * 2], dy = cd[((size_t)c * MAXF + sl) * 2 + 1];
+            axx += dx * dx; axy += dx * dy; ayy += dy * dy;
+        }
+        const double det = axx * ayy - axy * axy, tr = axx + ayy;
+        if (det > 1e-14 * tr * tr) {
+            ainv[3 * c] = ayy / det; ainv[3 * c + 1] = -axy / det; ainv[3 * c + 2] = axx / det;
+        }
+        dtv[c] = prm->dt / m->vol[c];
+    }
+    std::vector<double> fgeo((size_t)nf * 6);
+    std::vector<int32_t> fown(nf), fnbr(nf);
+    for (int64_t f = 0; f < nf; f++) {
+        fown[f] = (int32_t)F.own[f];
+        fnbr[f] = (int32_t)F.nbr[f];
+        const double g6[6] = {F.nl[2 * f], F.nl[2 * f + 1], F.ro[2 * f], F.ro[2 * f + 1], F.rk[2 * f], F.rk[2 * f + 1]};
+        std::copy(g6, g6 + 6, &fgeo[(size_t)f * 6]);
+    }
+    // velocity nodes: midpoints of a uniform nv x nv partition of [-vmax, vmax]^2, x fastest
+    std::vector<double> xi((size_t)Q * 2), wq(Q);
+    {
+        const double h = 2.0 * prm->vmax / prm->nv;
+        for (int i = 0; i < prm->nv; i++)
+            for (int j = 0; j < prm->nv; j++) {
+                const size_t q = (size_t)j + (size_t)prm->nv * i;
+                xi[2 * q] = -prm->vmax + (j + 0.5) * h;
+                xi[2 * q + 1] = -prm->vmax + (i + 0.5) * h;
+                wq[q] = h * h;
+            }
+    }
+
+    sdugks_dvm *d = new (std::nothrow) sdugks_dvm;
+    if (!d) return fail(SDUGKS_ERR_OOM, "host allocation failed");
+    d->p = *prm;
+    if (d->p.graph_steps == 0) d->p.graph_steps = 32;
+    d->prec = prm->precision;
+    d->rs = d->prec == P_FP64 ? 8 : 4;
+    d->stream = static_cast<cudaStream_t>(stream);
+    d->n = n; d->nf = nf; d->Q = Q;
+    const size_t rs = d->rs;
+    auto layout = [&](Arena &A) {
+        d->f = A.take<char>((size_t)n * Q * rs);
+        d->fbp = A.take<char>((size_t)n * Q * rs);
+        d->flux = A.take<char>((size_t)nf * Q * rs);
+        d->W = A.take<double>((size_t)n * 4);
+        d->dm.cell_face = A.take<int32_t>(cface.size());
+        d->dm.cell_nb = A.take<int32_t>(cnb.size());
+        d->dm.cell_d = A.take<char>(cd.size() * rs);
+        d->dm.ainv = A.take<char>(ainv.size() * rs);
+        d->dm.dtV = A.take<double>(n);
+        d->dm.face_own = A.take<int32_t>(nf);
+        d->dm.face_nbr = A.take<int32_t>(nf);
+        d->dm.face_geo = A.take<char>(fgeo.size() * rs);
+        d->dm.xi = A.take<char>(xi.size() * rs);
+        d->dm.wq = A.take<char>(wq.size() * rs);
+    };
+    Arena A0;
+    layout(A0);
+    d->dbytes = A0.used + 256;
+    cudaError_t e = cudaGetDevice(&d->device);
+    if (e == cudaSuccess) e = cudaMalloc(&d->dmem, d->dbytes);
+    if (e != cudaSuccess) {
+        delete d;
+        return fail(e == cudaErrorMemoryAllocation ? SDUGKS_ERR_OOM : SDUGKS_ERR_CUDA, "cudaMalloc(%zu): %s",
+                    A0.used, cudaGetErrorString(e));
+    }
+    Arena A{d->dmem, 0, d->dbytes};
+    layout(A);
+    d->dm.nc = n; d->dm.nf = nf; d->dm.Q = Q;
+    auto conv = [&](const std::vector<double> &v) {
+        std::vector<char> o(v.size() * rs);
+        if (rs == 8) std::memcpy(o.data(), v.data(), o.size());
+        else {
+            float *q = reinterpret_cast<float *>(o.data());
+            for (size_t i = 0; i < v.size(); i++) q[i] = (float)v[i];
+        }
+        return o;
+    };
+    int rc2 = SDUGKS_OK;
+    auto up = [&](const void *dst, const void *src, size_t bytes, const char *what) {
+        const cudaError_t ee = cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
+        if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
+    };
+    const auto gcd = conv(cd), gai = conv(ainv), gfg = conv(fgeo), gxi = conv(xi), gwq = conv(wq);
+    up(d->dm.cell_face, cface.data(), cface.size() * 4, "upload cell faces");
+    up(d->dm.cell_nb, cnb.data(), cnb.size() * 4, "upload neighbours");
+    up(d->dm.cell_d, gcd.data(), gcd.size(), "upload offsets");
+    up(d->dm.ainv, gai.data(), gai.size(), "upload LLSR inverse");
+    up(d->dm.dtV, dtv.data(), dtv.size() * 8, "upload dt/V");
+    up(d->dm.face_own, fown.data(), fown.size() * 4, "upload owners");
+    up(d->dm.face_nbr, fnbr.data(), fnbr.size() * 4, "upload neighbours");
+    up(d->dm.face_geo, gfg.data(), gfg.size(), "upload face geometry");
+    up(d->dm.xi, gxi.data(), gxi.size(), "upload velocity nodes");
+    up(d->dm.wq, gwq.data(), gwq.size(), "upload weights");
+    if (rc2 == SDUGKS_OK) {
+        cudaError_t ee = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
+        if (ee == cudaSuccess) ee = prepare_dvm(d->prec, Q);
+        if (ee != cudaSuccess) rc2 = fail(SDUGKS_ERR_CUDA, "stream / kernel attributes: %s", cudaGetErrorString(ee));
+    }
+    if (rc2) { sdugks_dvm_destroy(d); return rc2; }
+    fill_coefs(d->coefs, *m, prm->tau, prm->dt);
+    *out = d;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_dvm_init(sdugks_dvm *d, const double *rho, const double *u, const double *RT)
+{
+    if (!d) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    std::vector<double> W((size_t)d->n * 4);
+    for (int64_t c = 0; c < d->n; c++) {
+        const double r = rho ? rho[c] : 1.0, ux = u ? u[2 * c] : 0.0, uy = u ? u[2 * c + 1] : 0.0;
+        const double t = RT ? RT[c] : d->p.RT_wall;
+        if (!(r > 0) || !(t > 0) || !std::isfinite(ux) || !std::isfinite(uy))
+            return fail(SDUGKS_ERR_INVALID_ARG, "initial state of cell %lld: rho and RT must be > 0", (long long)c);
+        W[4 * c] = r; W[4 * c + 1] = r * ux; W[4 * c + 2] = r * uy; W[4 * c + 3] = r * (0.5 * (ux * ux + uy * uy) + t);
+    }
+    CUDA_TRY(cudaSetDevice(d->device));
+    CUDA_TRY(cudaMemcpyAsync(d->W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, d->stream));
+    CUDA_TRY(launch_dvm_init(d->prec, d->dm, d->W, d->f, d->stream));
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    d->initialised = true;
+    return SDUGKS_OK;
+}
+
+static int dvm_ensure_graph(sdugks_dvm *d)
+{
+    if (d->graph) return SDUGKS_OK;
+    const int G = d->p.graph_steps;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < G && e == cudaSuccess; k++)
+        e = launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, d->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(d->cap_stream, &g);
+    CUDA_TRY(e);
+    CUDA_TRY(e2);
+    e = cudaGraphInstantiate(&d->graph, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    d->graph_len = G;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_dvm_step(sdugks_dvm *d, int64_t n)
+{
+    if (!d) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (n < 0) return fail(SDUGKS_ERR_INVALID_ARG, "negative step count");
+    if (!d->initialised) return fail(SDUGKS_ERR_STATE, "step before init");
+    CUDA_TRY(cudaSetDevice(d->device));
+    int64_t left = n;
+    const int G = d->p.graph_steps;
+    if (G > 0 && left >= G) {
+        int rc = dvm_ensure_graph(d);
+        if (rc) return rc;
+        for (; left >= G; left -= G) CUDA_TRY(cudaGraphLaunch(d->graph, d->stream));
+    }
+    for (; left > 0; left--)
+        CUDA_TRY(launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, d->stream));
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_dvm_get_macros(sdugks_dvm *d, double *rho, double *u, double *RT)
+{
+    if (!d) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    std::vector<double> W((size_t)d->n * 4);
+    CUDA_TRY(cudaSetDevice(d->device));
+    CUDA_TRY(cudaMemcpyAsync(W.data(), d->W, W.size() * 8, cudaMemcpyDeviceToHost, d->stream));
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    for (int64_t c = 0; c < d->n; c++) {
+        const double r = W[4 * c], ux = W[4 * c + 1] / r, uy = W[4 * c + 2] / r;
+        if (rho) rho[c] = r;
+        if (u) { u[2 * c] = ux; u[2 * c + 1] = uy; }
+        if (RT) RT[c] = W[4 * c + 3] / r - 0.5 * (ux * ux + uy * uy);
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_dvm_get_state(sdugks_dvm *d, double *f, double *W)
+{
+    if (!d) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    CUDA_TRY(cudaSetDevice(d->device));
+    if (W) CUDA_TRY(cudaMemcpyAsync(W, d->W, (size_t)d->n * 4 * 8, cudaMemcpyDeviceToHost, d->stream));
+    if (f) {
+        const size_t cnt = (size_t)d->n * d->Q;
+        if (d->prec == P_FP64) {
+            CUDA_TRY(cudaMemcpyAsync(f, d->f, cnt * 8, cudaMemcpyDeviceToHost, d->stream));
+        } else {
+            std::vector<float> tmp(cnt);
+            CUDA_TRY(cudaMemcpyAsync(tmp.data(), d->f, cnt * 4, cudaMemcpyDeviceToHost, d->stream));
+            CUDA_TRY(cudaStreamSynchronize(d->stream));
+            for (size_t i = 0; i < cnt; i++) f[i] = tmp[i];
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_dvm_sizes(const sdugks_dvm *d, int64_t *n_cells, int64_t *n_faces, int64_t *n_velocities,
+                                int64_t *device_bytes)
+{
+    if (!d) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
+    if (n_cells) *n_cells = d->n;
+    if (n_faces) *n_faces = d->nf;
+    if (n_velocities) *n_velocities = d->Q;
+    if (device_bytes) *device_bytes = (int64_t)d->dbytes;
+    return SDUGKS_OK;
+}
+
+extern "C" void sdugks_dvm_destroy(sdugks_dvm *d)
+{
+    if (!d) return;
+    cudaSetDevice(d->device);
+    if (d->graph) cudaGraphExecDestroy(d->graph);
+    if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+    if (d->dmem) cudaFree(d->dmem);
+    delete d;
+}

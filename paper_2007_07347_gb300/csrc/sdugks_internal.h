@@ -132,6 +132,28 @@ cudaError_t launch_batch_macros(const CartInst *inst_host, const CartInst *inst_
 cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
                                    const double *W_in, double *W_out, cudaStream_t st);
 
+// Rarefied solver on a discrete velocity grid (Q nodes): any face-based mesh, f and
+// the scratch arrays cell- (or face-) major with the Q velocities contiguous.
+struct DvmMesh {
+    int64_t nc, nf, Q;
+    const int32_t *cell_face;  // [nc][MAXF] face id, | DVM_SECOND when the cell is the face's
+                               //   second side; -1 for no face
+    const int32_t *cell_nb;    // [nc][MAXF] LLSR neighbour (periodic partners included), -1 none
+    const void *cell_d;        // [nc][MAXF][2] x_k - x_j (compute precision)
+    const void *ainv;          // [nc][3] LLSR inverse (xx, xy, yy)
+    const double *dtV;         // [nc] dt / V
+    const int32_t *face_own, *face_nbr;   // face_nbr: cell, or -1 - patch
+    const void *face_geo;      // [nf][6] n l (first -> second side), x_f - x_first, x_f - x_second
+    const void *xi;            // [Q][2] velocity nodes
+    const void *wq;            // [Q] quadrature weights
+};
+constexpr int32_t DVM_SECOND = int32_t(0x40000000);
+constexpr int DVM_THREADS = 256;
+cudaError_t launch_dvm_step(int prec, const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp,
+                            void *flux, cudaStream_t st);
+cudaError_t launch_dvm_init(int prec, const DvmMesh &m, const double *W, void *f, cudaStream_t st);
+cudaError_t prepare_dvm(int prec, int64_t Q);   // kernel attributes on the current device
+
 // state conversions between the caller's cell-major FP64 layout (user cell order)
 // and the internal SoA layout: the q-th listed cell is user cell perm[q] stored at
 // internal offset loc[q] (loc == nullptr: offset q).

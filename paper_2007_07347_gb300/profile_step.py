@@ -2,8 +2,10 @@
 
     python -m paper_2007_07347_gb300.profile_step CASE [PRECISION] [STEPS] [TILE]
 
-CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh).  Used
-under ncu with ``-k regex:k_step`` to capture single step launches.
+CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh), or
+microcavity (the rarefied solver: 40 x 40 cells, 100 x 100 velocities, Kn 1).  Used
+under ncu with ``-k regex:k_step`` (``regex:k_dvm`` for the rarefied kernels) to
+capture single step launches.
 """
 import sys
 
@@ -26,8 +28,14 @@ def main(argv):
     prec = argv[2] if len(argv) > 2 else "fp32"
     nsteps = int(argv[3]) if len(argv) > 3 else 10
     tile = int(argv[4]) if len(argv) > 4 else 0
-    case = CASES[name]()
     torch.cuda.set_device(0)
+    if name == "microcavity":
+        d = S.Dvm.from_case(M.micro_cavity(40, Kn=1.0), "fp64" if prec == "fp64" else "fp32", graph_steps=-1).init()
+        d.step(nsteps)
+        torch.cuda.synchronize()
+        print("sizes", d.sizes())
+        return
+    case = CASES[name]()
     s = S.Solver.from_case(case, prec, graph_steps=-1, tile_cells=tile)
     u = None if case.u0 == (0.0, 0.0) else np.tile(case.u0, (case.mesh.n_cells, 1))
     s.init(None, u)

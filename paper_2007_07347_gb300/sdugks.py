@@ -90,6 +90,12 @@ def lib():
                 "sdugks_batch_get_macros": [P, i64, P, P],
                 "sdugks_batch_autotune": [P, i64],
                 "sdugks_batch_info": [P, P],
+                "sdugks_dvm_create": [P, P, P, P],
+                "sdugks_dvm_init": [P, P, P, P],
+                "sdugks_dvm_step": [P, i64],
+                "sdugks_dvm_get_macros": [P, P, P, P],
+                "sdugks_dvm_get_state": [P, P, P],
+                "sdugks_dvm_sizes": [P, P, P, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -101,6 +107,8 @@ def lib():
             L.sdugks_solver_destroy.restype = None
             L.sdugks_batch_destroy.argtypes = [P]
             L.sdugks_batch_destroy.restype = None
+            L.sdugks_dvm_destroy.argtypes = [P]
+            L.sdugks_dvm_destroy.restype = None
             L.sdugks_last_error.restype = C.c_char_p
             L.sdugks_version.restype = C.c_char_p
             _lib = L
@@ -321,6 +329,69 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().sdugks_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DvmParams(C.Structure):
+    _fields_ = [("nv", C.c_int32), ("vmax", C.c_double), ("RT_wall", C.c_double), ("tau", C.c_double),
+                ("dt", C.c_double), ("precision", C.c_int32), ("graph_steps", C.c_int32)]
+
+
+class Dvm:
+    """sdugks_dvm: the rarefied solver on an nv x nv velocity grid (diffuse walls)."""
+
+    def __init__(self, mesh: Mesh, nv: int, vmax: float, RT_wall: float, tau: float, dt: float, precision="fp32",
+                 graph_steps: int = 0, stream=None):
+        L = lib()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        prm = DvmParams(int(nv), float(vmax), float(RT_wall), float(tau), float(dt), prec, int(graph_steps))
+        sh = getattr(stream, "cuda_stream", stream)
+        self._h = C.c_void_p()
+        _ck(L.sdugks_dvm_create(mesh._h, C.byref(prm), C.c_void_p(sh or 0), C.byref(self._h)), "sdugks_dvm_create")
+        self.mesh = mesh
+        self.n = mesh.n_cells
+        self.Q = int(nv) * int(nv)
+
+    @classmethod
+    def from_case(cls, case: _meshes.Case, precision="fp32", **kw):
+        """A micro-cavity-style case (meta: nv, vmax, RT0)."""
+        mt = case.meta
+        return cls(Mesh(case.mesh, case.bcs), mt["nv"], mt["vmax"], mt["RT0"], case.tau, case.dt, precision, **kw)
+
+    def init(self, rho=None, u=None, RT=None):
+        r = None if rho is None else _f64(rho, (self.n,))
+        v = None if u is None else _f64(u, (self.n, 2))
+        t = None if RT is None else _f64(RT, (self.n,))
+        _ck(lib().sdugks_dvm_init(self._h, _ptr(r), _ptr(v), _ptr(t)), "sdugks_dvm_init")
+        return self
+
+    def step(self, n: int = 1):
+        _ck(lib().sdugks_dvm_step(self._h, int(n)), "sdugks_dvm_step")
+
+    def macros(self):
+        rho = np.empty(self.n); u = np.empty((self.n, 2)); RT = np.empty(self.n)
+        _ck(lib().sdugks_dvm_get_macros(self._h, _ptr(rho), _ptr(u), _ptr(RT)), "sdugks_dvm_get_macros")
+        return rho, u, RT
+
+    def get_state(self):
+        f = np.empty((self.n, self.Q)); W = np.empty((self.n, 4))
+        _ck(lib().sdugks_dvm_get_state(self._h, _ptr(f), _ptr(W)), "sdugks_dvm_get_state")
+        return f, W
+
+    def sizes(self):
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _ck(lib().sdugks_dvm_sizes(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "sdugks_dvm_sizes")
+        return {"n_cells": a.value, "n_faces": b.value, "Q": c.value, "device_bytes": d.value}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sdugks_dvm_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

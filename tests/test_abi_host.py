@@ -121,3 +121,21 @@ def test_slanted_symmetry_line_is_rejected_on_the_host():
     with pytest.raises(S.SdugksError) as e:
         S.Solver.from_case(dataclasses.replace(case, bcs=bcs), "fp32")
     assert e.value.name == "BAD_BC"
+
+
+def test_rarefied_solver_checks_its_boundaries_on_the_host():
+    """The rarefied solver takes periodic faces and diffuse walls only; other kinds
+    are BAD_BC before any device work, and bad grid parameters INVALID_ARG."""
+    import torch
+    case = M.flat_plate(8, 24, 16, Re_L=2e3, h_le=0.5, h_wall=0.2)
+    with pytest.raises(S.SdugksError) as e:
+        S.Dvm(S.Mesh(case.mesh, case.bcs), 8, 2.0, 0.5, 0.1, 0.01)
+    assert e.value.name == "BAD_BC"
+    mc = M.micro_cavity(8, nv=8)
+    with pytest.raises(S.SdugksError) as e:
+        S.Dvm(S.Mesh(mc.mesh, mc.bcs), 1, 2.0, 0.5, 0.1, 0.01)
+    assert e.value.name == "INVALID_ARG"
+    try:
+        S.Dvm.from_case(mc)
+    except S.SdugksError as e:
+        assert e.name == "CUDA" and not torch.cuda.is_available(), str(e)
