@@ -140,12 +140,10 @@ cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items
                               int parity, cudaStream_t st)
 {
     if (prec == P_BF16DEV)
-        k_step_batch<P_BF16DEV, BTX, BTY><<<grid, cart_threads<BTX, BTY>(), cart_smem<P_BF16DEV, BTX, BTY>(), st>>>(
-            insts, items, n_items, parity);
-    else
-        k_step_batch<P_FP32, BTX, BTY><<<grid, cart_threads<BTX, BTY>(), cart_smem<P_FP32, BTX, BTY>(), st>>>(
-            insts, items, n_items, parity);
-    return cudaGetLastError();
+        return launch_step_kernel(k_step_batch<P_BF16DEV, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
+                                  cart_smem<P_BF16DEV, BTX, BTY>(), st, insts, items, n_items, parity);
+    return launch_step_kernel(k_step_batch<P_FP32, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
+                              cart_smem<P_FP32, BTX, BTY>(), st, insts, items, n_items, parity);
 }
 
 cudaError_t launch_batch_residual(const CartInst *insts, int n_inst, const int2 *items, const int *n_items, int grid,

@@ -113,6 +113,7 @@ template <class R>
 __global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
                                                          const double *__restrict__ W, R *__restrict__ fbp)
 {
+    step_dependency_wait();
     __shared__ R sp[4];
     const int64_t c = blockIdx.x, Q = m.Q;
     if (threadIdx.x == 0) {
@@ -135,6 +136,7 @@ template <class R, bool SMEM>
 __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 4 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
+    step_dependency_wait();
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ double red[32 * 4];
     __shared__ R sp[4];
@@ -233,6 +235,7 @@ template <class R, bool SMEM>
 __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
                                                           double *__restrict__ W, const R *__restrict__ flux)
 {
+    step_dependency_wait();
     extern __shared__ __align__(16) unsigned char dyn[];
     R *Fbuf = reinterpret_cast<R *>(dyn);
     __shared__ double red[32 * 4];
@@ -330,20 +333,21 @@ cudaError_t step_p(const DvmMesh &m, const Coefs &c, double RTw, void *f, double
                    cudaStream_t st)
 {
     if (m.nc <= 0) return cudaSuccess;
-    k_dvm_fbp<R><<<(unsigned)m.nc, DVM_THREADS, 0, st>>>(m, c, static_cast<const R *>(f), W, static_cast<R *>(fbp));
+    const dim3 cells((unsigned)m.nc), faces((unsigned)m.nf), blk(DVM_THREADS);
+    const R *cf = static_cast<const R *>(f);
+    R *pf = static_cast<R *>(f), *pfbp = static_cast<R *>(fbp), *pflux = static_cast<R *>(flux);
+    const R *cfbp = pfbp, *cflux = pflux;
+    cudaError_t e = launch_step_kernel(k_dvm_fbp<R>, cells, blk, 0, st, m, c, cf, (const double *)W, pfbp);
+    if (e != cudaSuccess) return e;
     if (dvm_use_smem<R>(m.Q)) {
         const size_t bytes = (size_t)m.Q * sizeof(R);
-        k_dvm_face<R, true><<<(unsigned)m.nf, DVM_THREADS, bytes, st>>>(m, c, RTw, static_cast<const R *>(fbp),
-                                                                          static_cast<R *>(flux));
-        k_dvm_cell<R, true><<<(unsigned)m.nc, DVM_THREADS, bytes, st>>>(m, c, static_cast<R *>(f), W,
-                                                                          static_cast<const R *>(flux));
+        e = launch_step_kernel(k_dvm_face<R, true>, faces, blk, bytes, st, m, c, RTw, cfbp, pflux);
+        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, true>, cells, blk, bytes, st, m, c, pf, W, cflux);
     } else {
-        k_dvm_face<R, false><<<(unsigned)m.nf, DVM_THREADS, 0, st>>>(m, c, RTw, static_cast<const R *>(fbp),
-                                                                       static_cast<R *>(flux));
-        k_dvm_cell<R, false><<<(unsigned)m.nc, DVM_THREADS, 0, st>>>(m, c, static_cast<R *>(f), W,
-                                                                       static_cast<const R *>(flux));
+        e = launch_step_kernel(k_dvm_face<R, false>, faces, blk, 0, st, m, c, RTw, cfbp, pflux);
+        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, false>, cells, blk, 0, st, m, c, pf, W, cflux);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace

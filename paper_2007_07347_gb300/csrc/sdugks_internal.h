@@ -132,6 +132,37 @@ cudaError_t launch_batch_macros(const CartInst *inst_host, const CartInst *inst_
 cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c, const void *f_in, void *f_out,
                                    const double *W_in, double *W_out, cudaStream_t st);
 
+// Programmatic dependent launch of the step kernels: each step kernel lets the next
+// launch in its stream be scheduled as soon as all of its CTAs are running
+// (griddepcontrol.launch_dependents) and, before it touches global memory, waits
+// until the previous grid has completed and its writes are visible
+// (griddepcontrol.wait; a no-op when the launch did not allow an early start).  The
+// next step's CTAs therefore take the SM slots the moment the current step's CTAs
+// retire, instead of after the launch latency.
+#ifdef __CUDACC__
+__device__ __forceinline__ void step_dependency_wait()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <class... P, class... A>
+cudaError_t launch_step_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
+#endif
+
 // Rarefied solver on a discrete velocity grid (Q nodes): any face-based mesh, f and
 // the scratch arrays cell- (or face-) major with the Q velocities contiguous.
 struct DvmMesh {

@@ -175,8 +175,11 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int 
 
 // One TX x TY block (block coordinates tbx, tby) of one grid: reads buffer `par`,
 // writes buffer 1 - par.  All threads of the CTA must call it (it synchronises).
-// DIAG compiles in the optional wall-force accumulation.
-template <int P, int TX, int TY, bool DIAG>
+// DIAG compiles in the optional wall-force accumulation.  INTERIOR: the block and its
+// two-cell halo lie inside the grid (no side, wrap or ghost within reach), so every
+// stencil is the central difference and every face of a cell is interior; the
+// existence tests and stencil choices are compile-time constants.
+template <int P, int TX, int TY, bool DIAG, bool INTERIOR>
 __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, int tby, unsigned char *smem_raw)
 {
     using R = typename Store<P>::R;
@@ -208,13 +211,14 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     // iff it lies in [xlo, xhi) x [ylo, yhi)
     const int xlo = px ? INT_MIN : (symL ? -nx : 0), xhi = px ? INT_MAX : (symR ? 2 * nx : nx);
     const int ylo = py ? INT_MIN : (symB ? -ny : 0), yhi = py ? INT_MAX : (symT ? 2 * ny : ny);
-    auto has_x = [&](int ci) { return ci >= xlo && ci < xhi; };
-    auto has_y = [&](int cj) { return cj >= ylo && cj < yhi; };
+    auto has_x = [&](int ci) { return INTERIOR || (ci >= xlo && ci < xhi); };
+    auto has_y = [&](int cj) { return INTERIOR || (cj >= ylo && cj < yhi); };
     // domain cell of a block-relative position (periodic sides wrap, symmetry sides
     // reflect: mir bit 0 / 1 for a reflection in x / y), or -1 outside
     auto cell_of = [&](int bi, int bj, int &mir) -> int64_t {
         int gi = x0 + bi, gj = y0 + bj;
         mir = 0;
+        if (INTERIOR) return gi + pitch * gj;
         if (gi < 0 || gi >= nx) {
             if (px) gi = (gi + nx) % nx;
             else if (gi < 0 ? symL : symR) {
@@ -235,6 +239,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     };
     // gradient stencil of the staged cell at block position (bi, bj)
     auto sten = [&](int bi, int bj) {
+        if (INTERIOR) return Sten<R>{1, -1, S::LX, -S::LX, R(0.5) * k.ihx, R(0.5) * k.ihy};
         const int ci = x0 + bi, cj = y0 + bj;
         const bool hE = has_x(ci + 1), hW = has_x(ci - 1);
         const bool hN = has_y(cj + 1), hS = has_y(cj - 1);
@@ -401,13 +406,24 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     }
 }
 
+// The block and its two-cell halo lie inside the grid.
+template <int TX, int TY>
+__device__ __forceinline__ bool cart_block_interior(const CartInst &m, int tbx, int tby)
+{
+    const int x0 = tbx * TX, y0 = tby * TY;
+    return x0 >= 2 && x0 + TX + 2 <= m.nx && y0 >= 2 && y0 + TY + 2 <= m.ny;
+}
+
 template <int P, int TX, int TY>
 __global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : (cart_threads<TX, TY>() <= 320 ? 4 : 2))
 k_step_cart(const CartInst m, int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_dependency_wait();
     const int ntx = (m.nx + TX - 1) / TX;
-    cart_tile<P, TX, TY, true>(m, par, blockIdx.x % ntx, blockIdx.x / ntx, smem_raw);
+    const int tbx = blockIdx.x % ntx, tby = blockIdx.x / ntx;
+    if (cart_block_interior<TX, TY>(m, tbx, tby)) cart_tile<P, TX, TY, false, true>(m, par, tbx, tby, smem_raw);
+    else cart_tile<P, TX, TY, true, false>(m, par, tbx, tby, smem_raw);
 }
 
 // Batched: a fixed grid walks the (instance, block) work list; the item count is in
@@ -418,12 +434,13 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
              int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_dependency_wait();
     const int n = *n_items;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int2 it = items[w];
         const CartInst &m = insts[it.x];
         const int ntx = (m.nx + TX - 1) / TX;
-        cart_tile<P, TX, TY, false>(m, par, it.y % ntx, it.y / ntx, smem_raw);
+        cart_tile<P, TX, TY, false, false>(m, par, it.y % ntx, it.y / ntx, smem_raw);
         __syncthreads();                                 // shared memory is reused by the next item
     }
 }
@@ -437,8 +454,8 @@ template <int P, int TX, int TY>
 cudaError_t launch_cart_p(const CartInst &m, int par, cudaStream_t st)
 {
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
-    k_step_cart<P, TX, TY><<<ntx * nty, cart_threads<TX, TY>(), cart_smem<P, TX, TY>(), st>>>(m, par);
-    return cudaGetLastError();
+    return launch_step_kernel(k_step_cart<P, TX, TY>, dim3(ntx * nty), dim3(cart_threads<TX, TY>()),
+                              cart_smem<P, TX, TY>(), st, m, par);
 }
 
 }  // namespace sdugks

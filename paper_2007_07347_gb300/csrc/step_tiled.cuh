@@ -65,6 +65,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LOC_MAX]
     R *s_sig = s_fbp + NQ * LOC_MAX;                 // [2 NQ][SIG_MAX]
     R *s_flux = s_sig + 2 * NQ * SIG_MAX;            // [NQ][LF_MAX]
+    step_dependency_wait();
 
     const int t = blockIdx.x, tid = threadIdx.x;
     const int c0 = m.tile_c0[t];
@@ -313,9 +314,8 @@ cudaError_t launch_tiled_p(const TiledMesh &m, const Coefs &c, const void *fin, 
 {
     using T = typename Store<P>::T;
     if (m.n_tiles <= 0) return cudaSuccess;
-    k_step_tiled<P><<<m.n_tiles, TILED_THREADS, tiled_smem<P>(), st>>>(m, c, static_cast<const T *>(fin),
-                                                                  static_cast<T *>(fout), Wn, Wout);
-    return cudaGetLastError();
+    return launch_step_kernel(k_step_tiled<P>, dim3(m.n_tiles), dim3(TILED_THREADS), tiled_smem<P>(), st, m, c,
+                              static_cast<const T *>(fin), static_cast<T *>(fout), Wn, Wout);
 }
 
 }  // namespace sdugks
