@@ -58,6 +58,8 @@ def parse():
                          "unstructured kernel); batch: 256 cavities in one batch against the plain "
                          "one-at-a-time path; serve: the continuous-batching request loop; rarefied: the "
                          "40x40 micro cavity on a 100x100 velocity grid (Kn 1)")
+    ap.add_argument("--tile-cells", type=int, default=0,
+                    help="block / tile size of the solver (0: the solver's own choice)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
     args = ap.parse_args()
@@ -283,7 +285,7 @@ def run_ours(args):
     case = workload(args)
     n = case.mesh.n_cells
     stream = torch.cuda.Stream()
-    s = S.Solver.from_case(case, args.precision, stream=stream)
+    s = S.Solver.from_case(case, args.precision, stream=stream, tile_cells=args.tile_cells)
     s.init(None, initial_u(case))
     info = s.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

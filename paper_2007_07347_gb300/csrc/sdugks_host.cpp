@@ -619,9 +619,11 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     if (rc2) { sdugks_solver_destroy(s); return rc2; }
     fill_coefs(s->coefs, m, prm->tau, prm->dt);
     // Block shape: tile_cells 256/224/128 picks 16x16/16x14/16x8; 0 picks by a cost
-    // model -- blocks per SM (rounded up) times the work of one block (staged
-    // positions plus faces) -- so that small grids fill every SM evenly.  The
-    // choice depends only on the grid size and the device, never on timings.
+    // model: waves of resident blocks (rounded up) times the work one SM does per
+    // wave (resident blocks x staged positions plus faces of a block), with the
+    // shapes that fit four blocks per SM credited 1.21x for hiding latency better (the
+    // ratio measured on GB300 between the 16x8 and 16x16 shapes on a 1024^2 grid).
+    // The choice depends only on the grid size and the device, never on timings.
     {
         int n_sm = 1;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -631,9 +633,12 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
             for (int sh = 0; sh < CART_SHAPES; sh++) {
                 const int ty = CART_TY[sh];
                 if (prm->tile_cells && prm->tile_cells != 16 * ty) continue;
+                const int occ = std::max(1, cart_shape_occupancy(prec, sh));
                 const int64_t tiles = (int64_t)((g.nx + 15) / 16) * ((g.ny + ty - 1) / ty);
+                const int64_t slots = (int64_t)n_sm * occ;
                 const double work = (20.0 * (ty + 4) + 17.0 * ty + 16.0 * (ty + 1));
-                const double cost = (double)((tiles + n_sm - 1) / n_sm) * work;
+                const double eff = occ >= 4 ? 1.21 : 1.0;
+                const double cost = (double)((tiles + slots - 1) / slots) * occ * work / eff;
                 if (cost < best - 1e-9) { best = cost; s->cart_shape = sh; }
             }
         }

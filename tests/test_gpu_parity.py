@@ -350,3 +350,4 @@ def test_cartesian_block_shapes_agree(tile):
     r1, u1 = s.macros()
     assert rel_l2(u1, u0) <= 1e-5
     assert S.Solver.from_case(M.cavity(256), "fp32").info()["tile_cells"] == 224   # 304 blocks = 2 per SM
+    assert S.Solver.from_case(M.cavity(1024), "fp32").info()["tile_cells"] == 128  # many waves: 4 blocks per SM
