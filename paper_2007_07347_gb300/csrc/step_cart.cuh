@@ -125,6 +125,95 @@ __device__ __forceinline__ void cart_interior_face(R flux[6], const R *s_fbp, in
     }
 }
 
+// FP32 specialisation of cart_interior_face with paired arithmetic: on this GPU one
+// FFMA2/FMUL2 instruction does two independent FP32 operations (each rounded as the
+// scalar operation), so the reconstructions are evaluated two velocities at a time,
+// paired so that each pair is also a pair of the six face fluxes; the values are
+// those of the scalar routine with its products and sums contracted to FMAs.
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+
+// fbar+ of velocity plane a at l plus cx (E - W) [plus cy (N - S)], for two
+// (plane, position, stencil) triples at once
+template <bool UX, bool UY>
+__device__ __forceinline__ float2 extrap2(const float *s_fbp, int LXY, int ax_, int lx, const Sten<float> &sx,
+                                          int ay_, int ly, const Sten<float> &sy, float2 cx, float2 cy)
+{
+    const float *fx = s_fbp + ax_ * LXY, *fy = s_fbp + ay_ * LXY;
+    float2 v = p2(fx[lx], fy[ly]);
+    if (UX) {
+        const float2 dx = p2(fx[lx + sx.oE] - fx[lx + sx.oW], fy[ly + sy.oE] - fy[ly + sy.oW]);
+        v = __ffma2_rn(cx, dx, v);
+    }
+    if (UY) {
+        const float2 dy = p2(fx[lx + sx.oN] - fx[lx + sx.oS], fy[ly + sy.oN] - fy[ly + sy.oS]);
+        v = __ffma2_rn(cy, dy, v);
+    }
+    return v;
+}
+
+template <int AX>
+__device__ __forceinline__ void cart_interior_face_f32x2(float flux[6], const float *s_fbp, int lL, int lR,
+                                                         const Sten<float> &sL, const Sten<float> &sR,
+                                                         const CartK<float> &k, int LXY)
+{
+    const float hl = AX == 0 ? 0.5f * k.hx : 0.5f * k.hy, dt = k.dt;
+    float fbar[NQ];
+    float2 v01, v23, v45;     // reconstructions of the flux pairs (slots 0-1, 2-3, 4-5)
+    if (AX == 0) {
+        // x-face, left L / right R; x_f - x_L = (hl, 0), x_f - x_R = (-hl, 0)
+        const float2 ax2 = p2(sL.ax, sR.ax), ay2 = p2(sL.ay, sR.ay);
+        const float2 kb = __fmul2_rn(p2(hl - dt, -hl + dt), ax2);      // velocities with xi_x = +-1
+        const float2 k0 = __fmul2_rn(p2(hl, -hl), ax2);                // xi_x = 0
+        const float2 kc = __fmul2_rn(p2(-dt, -dt), ay2), kd = __fmul2_rn(p2(dt, dt), ay2);
+        v01 = extrap2<true, false>(s_fbp, LXY, 1, lL, sL, 3, lR, sR, kb, kb);                       // (A1, B3)
+        v23 = extrap2<true, true>(s_fbp, LXY, 5, lL, sL, 6, lR, sR, kb, kc);                        // (A5, B6)
+        v45 = extrap2<true, true>(s_fbp, LXY, 7, lR, sR, 8, lL, sL, p2(kb.y, kb.x), p2(kd.y, kd.x)); // (B7, A8)
+        const float2 t0 = extrap2<true, false>(s_fbp, LXY, 0, lL, sL, 0, lR, sR, k0, k0);           // (A0, B0)
+        const float2 t2 = extrap2<true, true>(s_fbp, LXY, 2, lL, sL, 2, lR, sR, k0, kc);            // (A2, B2)
+        const float2 t4 = extrap2<true, true>(s_fbp, LXY, 4, lL, sL, 4, lR, sR, k0, kd);            // (A4, B4)
+        fbar[0] = 0.5f * (t0.x + t0.y); fbar[1] = v01.x; fbar[2] = 0.5f * (t2.x + t2.y); fbar[3] = v01.y;
+        fbar[4] = 0.5f * (t4.x + t4.y); fbar[5] = v23.x; fbar[6] = v23.y; fbar[7] = v45.x; fbar[8] = v45.y;
+    } else {
+        // y-face, below L / above R; x_f - x_L = (0, hl), x_f - x_R = (0, -hl)
+        const float2 kyb = __fmul2_rn(p2(hl - dt, -hl + dt), p2(sL.ay, sR.ay));   // (A2, B4)
+        v01 = extrap2<false, true>(s_fbp, LXY, 2, lL, sL, 4, lR, sR, p2(0.f, 0.f), kyb);
+        const float kyL = (hl - dt) * sL.ay, kyR = (-hl + dt) * sR.ay;
+        v23 = extrap2<true, true>(s_fbp, LXY, 5, lL, sL, 6, lL, sL, __fmul2_rn(p2(-dt, dt), p2(sL.ax, sL.ax)),
+                            p2(kyL, kyL));                                                      // (A5, A6)
+        v45 = extrap2<true, true>(s_fbp, LXY, 7, lR, sR, 8, lR, sR, __fmul2_rn(p2(dt, -dt), p2(sR.ax, sR.ax)),
+                            p2(kyR, kyR));                                                      // (B7, B8)
+        const float2 ky0 = __fmul2_rn(p2(hl, -hl), p2(sL.ay, sR.ay));
+        const float2 ax2 = p2(sL.ax, sR.ax);
+        const float2 t0 = extrap2<false, true>(s_fbp, LXY, 0, lL, sL, 0, lR, sR, p2(0.f, 0.f), ky0);        // (A0, B0)
+        const float2 t1 = extrap2<true, true>(s_fbp, LXY, 1, lL, sL, 1, lR, sR, __fmul2_rn(p2(-dt, -dt), ax2), ky0);
+        const float2 t3 = extrap2<true, true>(s_fbp, LXY, 3, lL, sL, 3, lR, sR, __fmul2_rn(p2(dt, dt), ax2), ky0);
+        fbar[0] = 0.5f * (t0.x + t0.y); fbar[1] = 0.5f * (t1.x + t1.y); fbar[2] = v01.x;
+        fbar[3] = 0.5f * (t3.x + t3.y); fbar[4] = v01.y; fbar[5] = v23.x; fbar[6] = v23.y;
+        fbar[7] = v45.x; fbar[8] = v45.y;
+    }
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < NQ; a++) {
+        w0 += fbar[a];
+        if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
+        if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+    }
+    float ux, uy, feqb[NQ];
+    vel_of<float>(w0, w1, w2, ux, uy);
+    feq9f<float>(w0, ux, uy, feqb);
+    const float len = AX == 0 ? k.hy : k.hx;
+    const float2 bb = p2(k.b, k.b), cc = p2(k.c, k.c);
+    // slot pairs: AX 0 -> (1,3) (5,6) (7,8); AX 1 -> (2,4) (5,6) (7,8)
+    const float2 s01 = p2(len, -len);
+    const float2 s23 = AX == 0 ? p2(len, -len) : p2(len, len);
+    const float2 s45 = AX == 0 ? p2(-len, len) : p2(-len, -len);
+    const float2 e01 = AX == 0 ? p2(feqb[1], feqb[3]) : p2(feqb[2], feqb[4]);
+    const float2 f01 = __fmul2_rn(s01, __fmul2_rn(__ffma2_rn(bb, e01, v01), cc));
+    const float2 f23 = __fmul2_rn(s23, __fmul2_rn(__ffma2_rn(bb, p2(feqb[5], feqb[6]), v23), cc));
+    const float2 f45 = __fmul2_rn(s45, __fmul2_rn(__ffma2_rn(bb, p2(feqb[7], feqb[8]), v45), cc));
+    flux[0] = f01.x; flux[1] = f01.y; flux[2] = f23.x; flux[3] = f23.y; flux[4] = f45.x; flux[5] = f45.y;
+}
+
 // Boundary face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y) on grid side
 // `side`: adds the outward flux (xi . n l) f_b of every crossing velocity to F
 // (Sec. III rules).
@@ -322,7 +411,8 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         if (has_x(x0 + fi - 1) && has_x(x0 + fi) && has_y(y0 + fj)) {
             const int lL = (fj + 2) * S::LX + (fi + 1);
             R fl[6];
-            cart_interior_face<0, R>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
+            if constexpr (P == P_FP64) cart_interior_face<0, R>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
+            else cart_interior_face_f32x2<0>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
 #pragma unroll
             for (int r = 0; r < 6; r++) s_fx[r * S::NFX + tid] = fl[r];
         }
@@ -332,7 +422,8 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         if (has_y(y0 + fj - 1) && has_y(y0 + fj) && has_x(x0 + fi)) {
             const int lB = (fj + 1) * S::LX + (fi + 2);
             R fl[6];
-            cart_interior_face<1, R>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
+            if constexpr (P == P_FP64) cart_interior_face<1, R>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
+            else cart_interior_face_f32x2<1>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
 #pragma unroll
             for (int r = 0; r < 6; r++) s_fy[r * S::NFY + qq] = fl[r];
         }
