@@ -76,6 +76,31 @@ template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R ou
     }
 }
 
+// FP32: the same equilibrium with the four velocity pairs (1,2) (3,4) (5,6) (7,8)
+// evaluated by paired FP32 instructions (FFMA2/FMUL2; each lane rounds as the scalar
+// operation would): t = base + 4.5 rho e^2 and l = 3 rho e for e = (u_x, u_y) and for
+// e = (u_x + u_y, u_y - u_x), then w (t + l) and w (t - l).
+template <> __device__ __forceinline__ void feq9f<float>(float rho, float ux, float uy, float out[NQ]) {
+    const float base = rho - 1.5f * rho * (ux * ux + uy * uy);
+    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+    const float2 B = make_float2(base, base), R45 = make_float2(r45, r45), R3 = make_float2(r3, r3);
+    const float2 w1 = make_float2(1.0f / 9.0f, 1.0f / 9.0f), w5 = make_float2(1.0f / 36.0f, 1.0f / 36.0f);
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    out[0] = (4.0f / 9.0f) * base;
+    {
+        const float2 e = make_float2(ux, uy);
+        const float2 t = __ffma2_rn(__fmul2_rn(R45, e), e, B), l = __fmul2_rn(R3, e);
+        const float2 p = __fmul2_rn(w1, __fadd2_rn(t, l)), q = __fmul2_rn(w1, __ffma2_rn(l, m1, t));
+        out[1] = p.x; out[2] = p.y; out[3] = q.x; out[4] = q.y;
+    }
+    {
+        const float2 e = make_float2(ux + uy, uy - ux);
+        const float2 t = __ffma2_rn(__fmul2_rn(R45, e), e, B), l = __fmul2_rn(R3, e);
+        const float2 p = __fmul2_rn(w5, __fadd2_rn(t, l)), q = __fmul2_rn(w5, __ffma2_rn(l, m1, t));
+        out[5] = p.x; out[6] = p.y; out[7] = q.x; out[8] = q.y;
+    }
+}
+
 // (u_x, u_y) from rho, rho u in the compute precision (FP32: one correctly rounded
 // reciprocal; FP64: two IEEE divisions).
 template <class R> __device__ __forceinline__ void vel_of(R rho, R m1, R m2, R &ux, R &uy) {

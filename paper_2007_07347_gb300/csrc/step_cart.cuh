@@ -383,8 +383,21 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             for (int a = 0; a < NQ; a++)
                 if constexpr (P == P_BF16DEV) fv[a] += fe[a];       // decode the deviation
             if (mir == 0) {
+                if constexpr (P == P_FP64) {
 #pragma unroll
-                for (int a = 0; a < NQ; a++) s_fbp[a * LXY + ls] = k.a * fv[a] + k.b * fe[a];
+                    for (int a = 0; a < NQ; a++) s_fbp[a * LXY + ls] = k.a * fv[a] + k.b * fe[a];
+                } else {
+                    // paired: a f + b feq for the velocity pairs (1,2) (3,4) (5,6) (7,8)
+                    const float2 kb2 = make_float2(k.b, k.b), ka2 = make_float2(k.a, k.a);
+                    s_fbp[ls] = k.a * fv[0] + k.b * fe[0];
+#pragma unroll
+                    for (int a = 1; a < NQ; a += 2) {
+                        const float2 v = __ffma2_rn(ka2, make_float2(fv[a], fv[a + 1]),
+                                                    __fmul2_rn(kb2, make_float2(fe[a], fe[a + 1])));
+                        s_fbp[a * LXY + ls] = v.x;
+                        s_fbp[(a + 1) * LXY + ls] = v.y;
+                    }
+                }
             } else {
                 // mirror ghost: fbar+ of the mirrored velocity
                 R fb[NQ];
@@ -487,12 +500,22 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
         }
         feq9f<R>(rho1, ux1, uy1, feq1);
+        if constexpr (P == P_FP64) {
 #pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            R fnew;
-            if constexpr (P == P_FP64) fnew = (fn[a] - k.dtV * F[a] + k.r * feq1[a]) / (R(1) + k.r);
-            else fnew = (fn[a] - k.dtV * F[a] + k.r * feq1[a]) * m.finv1r;
-            fout[a * np + g] = SP::enc(fnew, feq1[a], a);
+            for (int a = 0; a < NQ; a++)
+                fout[a * np + g] = SP::enc((fn[a] - k.dtV * F[a] + k.r * feq1[a]) / (R(1) + k.r), feq1[a], a);
+        } else {
+            // paired: (f - dt/V F + r feq) / (1 + r) for the velocity pairs
+            const float2 mdv = make_float2(-k.dtV, -k.dtV), r2 = make_float2(k.r, k.r);
+            const float2 i2 = make_float2(m.finv1r, m.finv1r);
+            fout[g] = SP::enc((fn[0] - k.dtV * F[0] + k.r * feq1[0]) * m.finv1r, feq1[0], 0);
+#pragma unroll
+            for (int a = 1; a < NQ; a += 2) {
+                const float2 t = __ffma2_rn(mdv, make_float2(F[a], F[a + 1]), make_float2(fn[a], fn[a + 1]));
+                const float2 v = __fmul2_rn(__ffma2_rn(r2, make_float2(feq1[a], feq1[a + 1]), t), i2);
+                fout[a * np + g] = SP::enc(v.x, feq1[a], a);
+                fout[(a + 1) * np + g] = SP::enc(v.y, feq1[a + 1], a + 1);
+            }
         }
     }
 }
