@@ -53,12 +53,33 @@ __device__ __forceinline__ MaxP max_params(double rho, double mx, double my, dou
     return p;
 }
 
+template <class R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+// exp(-x) for the Maxwellian: FP64 exp; FP32 2^(-x log2 e) by the hardware base-2
+// exponential (relative error below 2^-22), with log2 e folded into sp[3].
+__device__ __forceinline__ float exp_neg(float x_log2e)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x_log2e));
+    return y;
+}
+__device__ __forceinline__ double exp_neg(double x) { return exp(-x); }
+
+// Maxwellian parameters in the compute precision: {pre, u_x, u_y, 1/(2RT)} (FP32:
+// 1/(2RT) times log2 e)
+template <class R> __device__ __forceinline__ void set_sp(R *sp, const MaxP &p)
+{
+    sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy);
+    sp[3] = sizeof(R) == 4 ? R(p.inv2RT * 1.4426950408889634) : R(p.inv2RT);
+}
+
 template <class R>
 __device__ __forceinline__ R maxwell(const R *sp, R x, R y, R w)
 {
-    // sp = {pre, ux, uy, inv2RT} in the compute precision
     const R cx = x - sp[1], cy = y - sp[2];
-    return w * sp[0] * dexp(-(cx * cx + cy * cy) * sp[3]);
+    return w * sp[0] * exp_neg((cx * cx + cy * cy) * sp[3]);
 }
 
 // Fixed-order block sum of NV per-thread values: warp sums by shuffles in the
@@ -90,18 +111,18 @@ __device__ __forceinline__ void block_sum(R v[NV], double *scratch, double out[N
     __syncthreads();
 }
 
-// fbar+ of the cell's velocity q plus (r - xi dt) . sigma, sigma its LLSR gradient
+// fbar+ of a cell's velocity q plus (r - xi dt) . sigma, sigma its LLSR gradient.
+// rows[0] is the cell's fbar+ row, rows[1..4] its neighbours' (a missing neighbour
+// repeats the cell's own row with a zero offset, which adds nothing).
 template <class R>
-__device__ __forceinline__ R reconstruct(const DvmMesh &m, const R *fbp, int64_t c, int64_t q, R rx, R ry, R xx,
-                                         R xy, R dt, const int32_t *nb, const R *d, const R *ai)
+__device__ __forceinline__ R reconstruct(const R *const *rows, const R *d, const R *ai, int q, R rx, R ry, R xx,
+                                         R xy, R dt)
 {
-    const int64_t Q = m.Q;
-    const R v0 = fbp[c * Q + q];
+    const R v0 = rows[0][q];
     R bx = R(0), by = R(0);
 #pragma unroll
     for (int sl = 0; sl < MAXF; sl++) {
-        if (nb[sl] < 0) continue;
-        const R dv = fbp[(int64_t)nb[sl] * Q + q] - v0;
+        const R dv = rows[1 + sl][q] - v0;
         bx += d[2 * sl] * dv;
         by += d[2 * sl + 1] * dv;
     }
@@ -115,78 +136,96 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const 
 {
     step_dependency_wait();
     __shared__ R sp[4];
-    const int64_t c = blockIdx.x, Q = m.Q;
-    if (threadIdx.x == 0) {
-        const MaxP p = max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]);
-        sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
-    }
+    const int64_t c = blockIdx.x;
+    const int Q = (int)m.Q;
+    if (threadIdx.x == 0) set_sp<R>(sp, max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]));
     __syncthreads();
     const DvmR<R> k(cf);
-    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
+    const typename V2<R>::T *xi = static_cast<const typename V2<R>::T *>(m.xi);
+    const R *wq = static_cast<const R *>(m.wq);
+    const R *fr = f + c * m.Q;
+    R *out = fbp + c * m.Q;
 #pragma unroll 2
-    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-        const R fe = maxwell<R>(sp, xi[2 * q], xi[2 * q + 1], wq[q]);
-        fbp[c * Q + q] = k.a * f[c * Q + q] + k.b * fe;
+    for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+        const typename V2<R>::T x = xi[q];
+        out[q] = k.a * fr[q] + k.b * maxwell<R>(sp, x.x, x.y, wq[q]);
+    }
+}
+
+// The rows and LLSR data of one side of a face, in shared memory.
+template <class R> struct SideData {
+    const R *rows[1 + MAXF];
+    R d[2 * MAXF], ai[3];
+};
+
+template <class R>
+__device__ __forceinline__ void load_side(SideData<R> &sd, const DvmMesh &m, const R *fbp, int64_t cc, int sl)
+{
+    // called by threads sl = 0..MAXF-1 (neighbours) and sl = MAXF (the cell itself)
+    if (sl < MAXF) {
+        const int32_t nb = m.cell_nb[cc * MAXF + sl];
+        sd.rows[1 + sl] = fbp + (nb >= 0 ? (int64_t)nb : cc) * m.Q;
+        const R *d = static_cast<const R *>(m.cell_d) + (cc * MAXF + sl) * 2;
+        sd.d[2 * sl] = nb >= 0 ? d[0] : R(0);
+        sd.d[2 * sl + 1] = nb >= 0 ? d[1] : R(0);
+        if (sl < 3) sd.ai[sl] = static_cast<const R *>(m.ainv)[cc * 3 + sl];
+    } else {
+        sd.rows[0] = fbp + cc * m.Q;
     }
 }
 
 // SMEM: the interface distribution of the face between the two passes over the
 // velocities stays in shared memory (Q values); otherwise in the flux array itself.
 template <class R, bool SMEM>
-__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 4 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
     step_dependency_wait();
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ double red[32 * 4];
     __shared__ R sp[4];
-    __shared__ int32_t nb[2][MAXF];
-    __shared__ R dd[2][2 * MAXF], ai[2][3];
-    const int64_t fc = blockIdx.x, Q = m.Q;
+    __shared__ SideData<R> sd[2];
+    const int64_t fc = blockIdx.x;
+    const int Q = (int)m.Q;
     const DvmR<R> k(cf);
-    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
+    const typename V2<R>::T *xi = static_cast<const typename V2<R>::T *>(m.xi);
+    const R *wq = static_cast<const R *>(m.wq);
     const R *G = static_cast<const R *>(m.face_geo) + 6 * fc;
     const R nx = G[0], ny = G[1], rox = G[2], roy = G[3], rkx = G[4], rky = G[5];
     const int64_t o = m.face_own[fc];
     const int32_t kn = m.face_nbr[fc];
     const bool interior = kn >= 0;
-    if (threadIdx.x < 2 * MAXF) {
-        const int side = threadIdx.x / MAXF, sl = threadIdx.x % MAXF;
-        const int64_t cc = side == 0 ? o : (interior ? (int64_t)kn : o);
-        nb[side][sl] = m.cell_nb[cc * MAXF + sl];
-        dd[side][2 * sl] = static_cast<const R *>(m.cell_d)[(cc * MAXF + sl) * 2];
-        dd[side][2 * sl + 1] = static_cast<const R *>(m.cell_d)[(cc * MAXF + sl) * 2 + 1];
-        if (sl < 3) ai[side][sl] = static_cast<const R *>(m.ainv)[cc * 3 + sl];
+    if (threadIdx.x < 2 * (MAXF + 1)) {
+        const int side = threadIdx.x / (MAXF + 1), sl = threadIdx.x % (MAXF + 1);
+        load_side<R>(sd[side], m, fbp, side == 0 ? o : (interior ? (int64_t)kn : o), sl);
     }
     __syncthreads();
-    R *out = flux + fc * Q;
+    R *out = flux + fc * m.Q;
     R *fbuf = SMEM ? reinterpret_cast<R *>(dyn) : out;
 
     if (interior) {
         R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
-        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-            const R x = xi[2 * q], y = xi[2 * q + 1];
+        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+            const typename V2<R>::T xv = xi[q];
+            const R x = xv.x, y = xv.y;
             const R s = x * nx + y * ny;
             R fb;
-            if (s > k.tie) fb = reconstruct<R>(m, fbp, o, q, rox, roy, x, y, k.dt, nb[0], dd[0], ai[0]);
-            else if (s < -k.tie) fb = reconstruct<R>(m, fbp, kn, q, rkx, rky, x, y, k.dt, nb[1], dd[1], ai[1]);
-            else fb = R(0.5) * (reconstruct<R>(m, fbp, o, q, rox, roy, x, y, k.dt, nb[0], dd[0], ai[0]) +
-                                reconstruct<R>(m, fbp, kn, q, rkx, rky, x, y, k.dt, nb[1], dd[1], ai[1]));
+            if (s > k.tie) fb = reconstruct<R>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt);
+            else if (s < -k.tie) fb = reconstruct<R>(sd[1].rows, sd[1].d, sd[1].ai, q, rkx, rky, x, y, k.dt);
+            else fb = R(0.5) * (reconstruct<R>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt) +
+                                reconstruct<R>(sd[1].rows, sd[1].d, sd[1].ai, q, rkx, rky, x, y, k.dt));
             fbuf[q] = fb;
             p0 += fb; p1 += x * fb; p2 += y * fb; p3 += R(0.5) * (x * x + y * y) * fb;
         }
         R part[4] = {p0, p1, p2, p3};
         double Wb[4];
         block_sum<4, R>(part, red, Wb);
-        if (threadIdx.x == 0) {
-            const MaxP p = max_params(Wb[0], Wb[1], Wb[2], Wb[3]);
-            sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
-        }
+        if (threadIdx.x == 0) set_sp<R>(sp, max_params(Wb[0], Wb[1], Wb[2], Wb[3]));
         __syncthreads();
-        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-            const R x = xi[2 * q], y = xi[2 * q + 1];
-            const R s = x * nx + y * ny;
-            const R g = maxwell<R>(sp, x, y, wq[q]);
+        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+            const typename V2<R>::T xv = xi[q];
+            const R s = xv.x * nx + xv.y * ny;
+            const R g = maxwell<R>(sp, xv.x, xv.y, wq[q]);
             out[q] = s * ((fbuf[q] + k.b * g) * k.c);
         }
     } else {
@@ -197,19 +236,21 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 4 : 1) k_dvm_fac
         const double uwx = bk == BK_MOVING_WALL ? cf.bc_par[p][0] : 0.0;
         const double uwy = bk == BK_MOVING_WALL ? cf.bc_par[p][1] : 0.0;
         if (threadIdx.x == 0) {
-            sp[0] = R(1.0 / (2.0 * 3.14159265358979323846 * RTw)); sp[1] = R(uwx); sp[2] = R(uwy);
-            sp[3] = R(1.0 / (2.0 * RTw));
+            MaxP pw;
+            pw.pre = 1.0 / (2.0 * 3.14159265358979323846 * RTw); pw.ux = uwx; pw.uy = uwy; pw.inv2RT = 1.0 / (2.0 * RTw);
+            set_sp<R>(sp, pw);
         }
         __syncthreads();
         R so = R(0), go = R(0), gi = R(0);
-        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-            const R x = xi[2 * q], y = xi[2 * q + 1];
+        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+            const typename V2<R>::T xv = xi[q];
+            const R x = xv.x, y = xv.y;
             const R s = x * nx + y * ny;
             const R g = maxwell<R>(sp, x, y, wq[q]);
             if (s < -k.tie) {
                 gi += s * g;
             } else {
-                const R fb = reconstruct<R>(m, fbp, o, q, rox, roy, x, y, k.dt, nb[0], dd[0], ai[0]);
+                const R fb = reconstruct<R>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt);
                 fbuf[q] = fb;
                 so += s * fb;
                 go += s * g;
@@ -220,10 +261,10 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 4 : 1) k_dvm_fac
         block_sum<3, R>(part, red, tot);
         const double rho_w = -double(k.c) * tot[0] / (double(k.c) * double(k.b) * tot[1] + tot[2]);
         const R rw = R(rho_w);
-        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-            const R x = xi[2 * q], y = xi[2 * q + 1];
-            const R s = x * nx + y * ny;
-            const R g = maxwell<R>(sp, x, y, wq[q]);
+        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+            const typename V2<R>::T xv = xi[q];
+            const R s = xv.x * nx + xv.y * ny;
+            const R g = maxwell<R>(sp, xv.x, xv.y, wq[q]);
             out[q] = s < -k.tie ? s * (rw * g) : s * ((fbuf[q] + k.b * (rw * g)) * k.c);
         }
     }
@@ -240,27 +281,33 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
     R *Fbuf = reinterpret_cast<R *>(dyn);
     __shared__ double red[32 * 4];
     __shared__ R sp[4];
-    __shared__ int32_t fid[MAXF];
-    const int64_t c = blockIdx.x, Q = m.Q;
+    __shared__ const R *frow[MAXF];
+    __shared__ R fsg[MAXF];
+    const int64_t c = blockIdx.x;
+    const int Q = (int)m.Q;
     const DvmR<R> k(cf);
-    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
-    if (threadIdx.x < MAXF) fid[threadIdx.x] = m.cell_face[c * MAXF + threadIdx.x];
+    const typename V2<R>::T *xi = static_cast<const typename V2<R>::T *>(m.xi);
+    const R *wq = static_cast<const R *>(m.wq);
+    if (threadIdx.x < MAXF) {
+        // the cell's faces in slot order: flux row and sign (a missing slot adds 0 x row 0)
+        const int32_t v = m.cell_face[c * MAXF + threadIdx.x];
+        const int32_t v0 = m.cell_face[c * MAXF];
+        const int32_t id = v >= 0 ? (v & (DVM_SECOND - 1)) : (v0 & (DVM_SECOND - 1));
+        frow[threadIdx.x] = flux + (int64_t)id * m.Q;
+        fsg[threadIdx.x] = v < 0 ? R(0) : ((v & DVM_SECOND) ? R(-1) : R(1));
+    }
     __syncthreads();
-    auto F_of = [&](int64_t q) {
+    auto F_of = [&](int q) {
         R F = R(0);
 #pragma unroll
-        for (int sl = 0; sl < MAXF; sl++) {
-            const int32_t v = fid[sl];
-            if (v < 0) continue;
-            const R x = flux[(int64_t)(v & (DVM_SECOND - 1)) * Q + q];
-            if (v & DVM_SECOND) F -= x; else F += x;
-        }
+        for (int sl = 0; sl < MAXF; sl++) F += fsg[sl] * frow[sl][q];
         return F;
     };
     R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
 #pragma unroll 2
-    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-        const R x = xi[2 * q], y = xi[2 * q + 1];
+    for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+        const typename V2<R>::T xv = xi[q];
+        const R x = xv.x, y = xv.y;
         const R F = F_of(q);
         if (SMEM) Fbuf[q] = F;
         p0 += F; p1 += x * F; p2 += y * F; p3 += R(0.5) * (x * x + y * y) * F;
@@ -275,18 +322,18 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
             Wn[d] = W[4 * c + d] - dtv * M[d];
             W[4 * c + d] = Wn[d];
         }
-        const MaxP p = max_params(Wn[0], Wn[1], Wn[2], Wn[3]);
-        sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
+        set_sp<R>(sp, max_params(Wn[0], Wn[1], Wn[2], Wn[3]));
     }
     __syncthreads();
     const R rdtv = R(dtv);
+    R *fr = f + c * m.Q;
 #pragma unroll 2
-    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) {
-        const R x = xi[2 * q], y = xi[2 * q + 1];
+    for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
+        const typename V2<R>::T xv = xi[q];
         const R F = SMEM ? Fbuf[q] : F_of(q);
-        const R fe = maxwell<R>(sp, x, y, wq[q]);
-        const R num = f[c * Q + q] - rdtv * F + k.r * fe;
-        f[c * Q + q] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
+        const R fe = maxwell<R>(sp, xv.x, xv.y, wq[q]);
+        const R num = fr[q] - rdtv * F + k.r * fe;
+        fr[q] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
     }
 }
 
@@ -297,10 +344,7 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_init(const DvmMesh m, const
 {
     __shared__ R sp[4];
     const int64_t c = blockIdx.x, Q = m.Q;
-    if (threadIdx.x == 0) {
-        const MaxP p = max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]);
-        sp[0] = R(p.pre); sp[1] = R(p.ux); sp[2] = R(p.uy); sp[3] = R(p.inv2RT);
-    }
+    if (threadIdx.x == 0) set_sp<R>(sp, max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]));
     __syncthreads();
     const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
     for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) f[c * Q + q] = maxwell<R>(sp, xi[2 * q], xi[2 * q + 1], wq[q]);
