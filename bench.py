@@ -183,14 +183,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ["d2q9.cuh", "sdugks_internal.h", "step_cart.cuh", "step_tiled.cuh", "k_cart.cu", "k_step_fp32.cu"]
+STEP_SOURCES = {
+    "k_step_cart": ["d2q9.cuh", "sdugks_internal.h", "step_cart.cuh", "k_cart.cu"],
+    "k_step_tiled": ["d2q9.cuh", "sdugks_internal.h", "step_tiled.cuh", "k_step_fp32.cu"],
+}
 
 
-def kernel_source_hash():
-    """Hash of the sources the step kernels are compiled from."""
+def kernel_source_hash(kernel: str = "k_step_cart"):
+    """Hash of the sources a step kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2007_07347_gb300", "csrc")
-    for name in STEP_SOURCES:
+    for name in STEP_SOURCES[kernel]:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -204,7 +207,8 @@ def profiled_traffic(kernel_key: str):
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(kernel_key)
-        if e and e.get("source_hash") == kernel_source_hash():
+        kernel = "k_step_tiled" if kernel_key.startswith("k_step_tiled") else "k_step_cart"
+        if e and e.get("source_hash") == kernel_source_hash(kernel):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass

@@ -798,6 +798,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     const int64_t npad = (n + 31) / 32 * 32;
     std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), tile_f0(nt + 1), halo;
     std::vector<uint16_t> sig_nb, cell_lf((size_t)MAXF * npad, LF_NONE);
+    std::vector<int32_t> sig_cell;   // internal cell of each gradient row
     std::vector<uint32_t> lf_ab;
     std::vector<double> lf_geo;   // [n_lf][6], transposed at upload
     std::vector<uint8_t> islk((size_t)MAXF * npad, SK_NONE);
@@ -862,6 +863,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                     }
                 }
                 sig_nb.insert(sig_nb.end(), row.begin(), row.end());
+                sig_cell.push_back(i);
             };
             for (int32_t i = 0; i < nint; i++) push_sig(c0 + i);
             for (int32_t c : r1) push_sig(c);
@@ -977,11 +979,11 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->tm.halo = A.take<int32_t>(std::max<size_t>(1, halo.size()));
         s->tm.sig_nb = A.take<uint16_t>(sig_nb.size());
         s->tm.tile_f0 = A.take<int32_t>(nt + 1);
-        s->tm.sl_d = A.take<char>(isld.size());
+        s->tm.sig_d = A.take<char>((size_t)MAXF * 2 * sig_cell.size() * rs);
+        s->tm.sig_ai = A.take<char>((size_t)3 * sig_cell.size() * rs);
         s->tm.cell_lf = A.take<uint16_t>(cell_lf.size());
         s->tm.lf_ab = A.take<uint32_t>(lf_ab.size());
         s->tm.lf_geo = A.take<char>(lf_geo.size() * rs);
-        s->tm.ainv = A.take<char>(3 * npad * rs);
         s->tm.dtV = A.take<char>(npad * rs);
         s->tm.vol = s->vol;
     };
@@ -1019,7 +1021,21 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         for (size_t q = 0; q < nlf; q++)
             for (int d = 0; d < 6; d++) lgeo_t[d * nlf + q] = lf_geo[q * 6 + d];
     }
-    const std::vector<char> ggeo = conv(lgeo_t), gainv = conv(iainv), gdtv = conv(idtv);
+    const std::vector<char> ggeo = conv(lgeo_t), gdtv = conv(idtv);
+    // gradient data per row (tile cells and ring 1 of every tile), SoA over the rows
+    const size_t nrow = sig_cell.size();
+    std::vector<char> gsd((size_t)MAXF * 2 * nrow * rs), gsa((size_t)3 * nrow * rs);
+    {
+        const std::vector<char> gainv = conv(iainv);
+        for (size_t r = 0; r < nrow; r++) {
+            const size_t i = (size_t)sig_cell[r];
+            for (int k = 0; k < 2 * MAXF; k++)
+                std::memcpy(&gsd[((size_t)k * nrow + r) * rs], &isld[((size_t)k * npad + i) * rs], rs);
+            for (int k = 0; k < 3; k++)
+                std::memcpy(&gsa[((size_t)k * nrow + r) * rs], &gainv[((size_t)k * npad + i) * rs], rs);
+        }
+    }
+    s->tm.n_sig = (int64_t)nrow;
     int rc2 = SDUGKS_OK;
     auto chk = [&](cudaError_t ee, const char *what) {
         if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
@@ -1034,11 +1050,11 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     if (!halo.empty()) chk(up(s->tm.halo, halo.data(), halo.size() * 4), "upload halo");
     chk(up(s->tm.sig_nb, sig_nb.data(), sig_nb.size() * 2), "upload sig_nb");
     chk(up(s->tm.tile_f0, tile_f0.data(), (nt + 1) * 4), "upload tiles");
-    chk(up(s->tm.sl_d, isld.data(), isld.size()), "upload slot offsets");
+    chk(up(s->tm.sig_d, gsd.data(), gsd.size()), "upload gradient offsets");
+    chk(up(s->tm.sig_ai, gsa.data(), gsa.size()), "upload LLSR inverse");
     chk(up(s->tm.cell_lf, cell_lf.data(), cell_lf.size() * 2), "upload cell faces");
     chk(up(s->tm.lf_ab, lf_ab.data(), lf_ab.size() * 4), "upload face sides");
     chk(up(s->tm.lf_geo, ggeo.data(), ggeo.size()), "upload face geometry");
-    chk(up(s->tm.ainv, gainv.data(), gainv.size()), "upload ainv");
     chk(up(s->tm.dtV, gdtv.data(), gdtv.size()), "upload dtV");
     chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
     chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");

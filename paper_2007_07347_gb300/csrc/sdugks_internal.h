@@ -61,15 +61,16 @@ struct TiledMesh {
     const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb
     const int32_t *tile_f0;   // [n_tiles+1] range of local faces
     const int32_t *halo;      // internal ids of ring 1 then ring 2 of each tile
-    const uint16_t *sig_nb;   // [sum n_sig][MAXF] tile-local index of the cell across each slot
-    const void *sl_d;         // [MAXF][2][npad] x_k - x_j across each interior slot
+    int64_t n_sig;            // gradient rows of all tiles (stride of sig_d and sig_ai)
+    const uint16_t *sig_nb;   // [n_sig][MAXF] tile-local index of the cell across each slot
+    const void *sig_d;        // [MAXF][2][n_sig] x_k - x_j across each slot of each gradient row
+    const void *sig_ai;       // [3][n_sig] LLSR inverse (xx, xy, yy) of each gradient row
     const uint16_t *cell_lf;  // [MAXF][npad] local face of each slot, | LF_SECOND when the cell
                               //   is the face's second side; LF_NONE for no face
     const uint32_t *lf_ab;    // [n_lf] tile-local first side | second side << 16; a boundary
                               //   face's second side is LF_BOUNDARY | patch
     const void *lf_geo;       // [6][n_lf] n l from the first side to the second (2),
                               //   x_f - x_first (2), x_f - x_second (2)
-    const void *ainv;         // [3][npad] LLSR inverse (xx, xy, yy)
     const void *dtV;          // [npad] dt / V (compute precision)
     const double *vol;        // [npad] V
     double *force;            // nullptr, or [MAXPATCH][2]: momentum flux out of the fluid per boundary patch

@@ -37,6 +37,16 @@ template <> struct CoefR<float> {
 };
 
 // fbar+ = a f^n + b feq(W^n) of one cell (Eq. fbarplus), with f^n and feq(W^n) returned.
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes) of read-only data.
+template <int B> __device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int P>
 __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict__ fin, const double *__restrict__ Wn,
                                          int64_t g, int64_t np, const CoefR<typename Store<P>::R> &k,
@@ -65,7 +75,8 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LOC_MAX]
     R *s_sig = s_fbp + NQ * LOC_MAX;                 // [2 NQ][SIG_MAX]
     R *s_flux = s_sig + 2 * NQ * SIG_MAX;            // [NQ][LF_MAX]
-    step_dependency_wait();
+    R *s_geo = s_flux + NQ * LF_MAX;                 // [6][LF_MAX] face geometry of the tile
+    uint32_t *s_lfab = reinterpret_cast<uint32_t *>(s_geo + 6 * LF_MAX);   // [LF_MAX] face sides
 
     const int t = blockIdx.x, tid = threadIdx.x;
     const int c0 = m.tile_c0[t];
@@ -78,9 +89,23 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int n_lf = m.tile_f0[t + 1] - f0;
     const int64_t np = m.npad, nlf = m.n_lf;
     const CoefR<R> k(c);
-    const R *sld = static_cast<const R *>(m.sl_d);
-    const R *geo = static_cast<const R *>(m.lf_geo);
-    const R *ainv = static_cast<const R *>(m.ainv);
+    // the tile's face list (read-only mesh data) travels to shared memory while the
+    // previous step finishes and the cells are staged
+    {
+        const R *gsrc = static_cast<const R *>(m.lf_geo);
+        for (int j = tid; j < n_lf; j += TILED_THREADS) {
+            cp_async<4>(&s_lfab[j], &m.lf_ab[f0 + j]);
+#pragma unroll
+            for (int q = 0; q < 6; q++) cp_async<sizeof(R)>(&s_geo[q * LF_MAX + j], &gsrc[q * nlf + f0 + j]);
+        }
+        cp_async_commit();
+    }
+    // cells this thread stages (read-only halo ids: looked up before the wait as well)
+    const int64_t gs0 = tid < n_int ? (int64_t)c0 + tid : (tid < n_loc ? (int64_t)m.halo[h0 + tid - n_int] : 0);
+    step_dependency_wait();
+    const R *sgd = static_cast<const R *>(m.sig_d);
+    const R *sga = static_cast<const R *>(m.sig_ai);
+    const int64_t nrow = m.n_sig;
 
     // ---- phase 1: fbar+ of the tile's cells and both halo rings; a thread keeps f^n of
     // its own cell (cell tid) in registers for the update
@@ -88,7 +113,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int64_t g = c0 + tid;
     R fn[NQ];
     for (int i = tid; i < n_loc; i += TILED_THREADS) {
-        const int64_t gi = i < n_int ? (int64_t)c0 + i : (int64_t)m.halo[h0 + i - n_int];
+        const int64_t gi = i == tid ? gs0 : (int64_t)m.halo[h0 + i - n_int];   // i > tid is always a halo cell
         R fx[NQ], fe[NQ], fb[NQ];
         cell_fbp<P>(fin, Wn, gi, np, k, fx, fe, fb);
 #pragma unroll
@@ -102,7 +127,6 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 
     // ---- phase 2: LLSR gradient sigma = A^{-1} sum_k d_k (fbar+_k - fbar+_j), d = x_k - x_j
     for (int i = tid; i < n_sig; i += TILED_THREADS) {
-        const int64_t gi = i < n_int ? (int64_t)c0 + i : (int64_t)m.halo[h0 + i - n_int];
         const uint16_t *nb = m.sig_nb + (int64_t)(s0 + i) * MAXF;
         R bx[NQ], by[NQ];
 #pragma unroll
@@ -111,7 +135,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         for (int sl = 0; sl < MAXF; sl++) {
             const int kk = nb[sl];
             if (kk == NO_LOCAL) continue;
-            const R dx = sld[(2 * sl) * np + gi], dy = sld[(2 * sl + 1) * np + gi];
+            const R dx = sgd[(2 * sl) * nrow + s0 + i], dy = sgd[(2 * sl + 1) * nrow + s0 + i];
             if (kk < SYM_X) {
 #pragma unroll
                 for (int a = 0; a < NQ; a++) {
@@ -130,23 +154,32 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 }
             }
         }
-        const R axx = ainv[gi], axy = ainv[np + gi], ayy = ainv[2 * np + gi];
+        const R axx = sga[s0 + i], axy = sga[nrow + s0 + i], ayy = sga[2 * nrow + s0 + i];
 #pragma unroll
         for (int a = 0; a < NQ; a++) {
             s_sig[(2 * a) * SIG_MAX + i] = axx * bx[a] + axy * by[a];
             s_sig[(2 * a + 1) * SIG_MAX + i] = axy * bx[a] + ayy * by[a];
         }
     }
+    cp_async_wait_all();        // the face list has arrived
     __syncthreads();
+    // inputs of the cell update, loaded now so that they arrive during the face phase
+    uint16_t my_lf[MAXF] = {LF_NONE, LF_NONE, LF_NONE, LF_NONE};
+    R dtv = R(0);
+    if (active) {
+#pragma unroll
+        for (int sl = 0; sl < MAXF; sl++) my_lf[sl] = m.cell_lf[sl * np + g];
+        dtv = static_cast<const R *>(m.dtV)[g];
+    }
 
     // ---- phase 3: every local face once; flux s f_b from the first side to the second
     for (int lf = tid; lf < n_lf; lf += TILED_THREADS) {
-        const uint32_t ab = m.lf_ab[f0 + lf];
+        const uint32_t ab = s_lfab[lf];
         const int A = (int)(ab & 0xFFFFu), B = (int)(ab >> 16);
-        const R *G = geo + f0 + lf;
-        const R nx = G[0], ny = G[nlf], rax = G[2 * nlf], ray = G[3 * nlf];
+        const R *G = s_geo + lf;
+        const R nx = G[0], ny = G[LF_MAX], rax = G[2 * LF_MAX], ray = G[3 * LF_MAX];
         if (!(B & LF_SECOND)) {
-            const R rbx = G[4 * nlf], rby = G[5 * nlf];
+            const R rbx = G[4 * LF_MAX], rby = G[5 * LF_MAX];
             R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
@@ -250,7 +283,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     for (int a = 0; a < NQ; a++) F[a] = R(0);
 #pragma unroll
     for (int sl = 0; sl < MAXF; sl++) {
-        const unsigned v = m.cell_lf[sl * np + g];
+        const unsigned v = my_lf[sl];
         if (v == LF_NONE) continue;
         const int lf = (int)(v & (LF_SECOND - 1u));
         if (v & LF_SECOND) {
@@ -264,7 +297,6 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 
     // ---- macroscopic flux (moments of F) -> W^{n+1} in FP64; cell update f^{n+1} (Eq. fn+1)
     const double w0n = Wn[g], w1n = Wn[np + g], w2n = Wn[2 * np + g];
-    const R dtv = static_cast<const R *>(m.dtV)[g];
     R M0 = R(0), M1 = R(0), M2 = R(0);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
@@ -296,7 +328,8 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 }
 
 template <int P> constexpr size_t tiled_smem() {
-    return sizeof(typename Store<P>::R) * (size_t)(NQ * LOC_MAX + 2 * NQ * SIG_MAX + NQ * LF_MAX);
+    return sizeof(typename Store<P>::R) * (size_t)(NQ * LOC_MAX + 2 * NQ * SIG_MAX + NQ * LF_MAX + 6 * LF_MAX) +
+           sizeof(uint32_t) * LF_MAX;
 }
 
 template <int P> cudaError_t prepare_tiled_p() {
