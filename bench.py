@@ -496,6 +496,21 @@ def run_rarefied(args):
         d.macros()
     e2e_s = time.perf_counter() - t0
     rho, u, RT = d.macros()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        threads = O.set_threads(0)
+        mt = case.meta
+        xi, wq = O.dvm_grid(mt["nv"], mt["vmax"])
+        st = O.dvm_init(n, xi, wq, RT0=mt["RT0"])
+        O.dvm_run(case.mesh, case.bcs, st, xi, wq, mt["RT0"], case.tau, case.dt, 1)     # warm-up, untimed
+        steps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+            O.dvm_run(case.mesh, case.bcs, st, xi, wq, mt["RT0"], case.tau, case.dt, 1)
+            steps += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": n * Q * steps / el / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": f"{steps} time steps of the same micro cavity ({el:.1f} s, {threads} OpenMP threads, FP64)"}
     line = {"metric": "MLUPS", "value": value, "unit": "MLUPS (cell-velocity updates, Q = 10^4)", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -517,6 +532,8 @@ def run_rarefied(args):
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
+    if cpu:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line))
 
 
