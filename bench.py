@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 from paper_2007_07347_gb300 import meshes as M  # noqa: E402
 
 INTERVAL = 1000
-STATE_BYTES = {"fp64": 192, "fp32": 120, "bf16dev": 84}    # f and W (FP64) each read and written once
+STATE_BYTES = {"fp64": 192, "fp32": 120, "bf16dev": 84, "fp16dev": 84}    # f and W (FP64) each read and written once
 
 
 def parse():
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=17)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16dev"],
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16dev", "fp16dev"],
                     help="storage of f (default: fp32; bf16dev for the cylinder)")
     ap.add_argument("--n", type=int, default=256, help="cavity cells per side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -357,7 +357,7 @@ def run_ours(args):
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "bf16dev": "f32 (bf16 storage)"}[args.precision],
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16dev": "f32 (bf16 storage)", "fp16dev": "f32 (fp16 storage)"}[args.precision],
         "data": "synthetic", "config": config(args, case),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(key),

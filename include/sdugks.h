@@ -60,6 +60,7 @@ extern "C" {
 #define SDUGKS_FP64 0          /* f stored and computed in FP64                          */
 #define SDUGKS_FP32 1          /* f stored and computed in FP32                          */
 #define SDUGKS_FP32_BF16DEV 2  /* f stored as bf16 d = (f - feq(W)) / w, computed in FP32 */
+#define SDUGKS_FP32_FP16DEV 3  /* f stored as fp16 d / s with s = 2^-10, computed in FP32  */
 /* W (and the macroscopic-flux accumulation, residual and mass) is FP64 in every mode. */
 
 /* ---- kernel selection ---------------------------------------------------------- */
@@ -75,10 +76,10 @@ typedef struct sdugks_solver sdugks_solver;
 typedef struct sdugks_params {
     double tau;          /* relaxation time, > 0                                   */
     double dt;           /* time step, > 0                                         */
-    int32_t precision;   /* SDUGKS_FP64 | SDUGKS_FP32 | SDUGKS_FP32_BF16DEV         */
+    int32_t precision;   /* SDUGKS_FP64 | SDUGKS_FP32 | SDUGKS_FP32_BF16DEV | _FP16DEV */
     int32_t kernel;      /* SDUGKS_KERNEL_*                                        */
-    int32_t tile_cells;  /* tiled kernel: cells per tile (16..128); Cartesian kernel (FP32 and
-                            bf16 storage): 256, 224 or 128 for 16x16, 16x14 or 16x8 blocks;
+    int32_t tile_cells;  /* tiled kernel: cells per tile (16..128); Cartesian kernel (FP32,
+                            bf16 and fp16 storage): 256, 224 or 128 for 16x16, 16x14 or 16x8 blocks;
                             0 = chosen from the grid size (Cartesian) or 128 (tiled) */
     int32_t graph_steps; /* steps per captured CUDA graph in sdugks_step, 0 = auto, <0 = off */
 } sdugks_params;
@@ -242,7 +243,7 @@ typedef struct sdugks_batch_status {
 } sdugks_batch_status;
 
 /* Create a batch with a device pool of pool_bytes and room for max_instances
- * instances.  precision: SDUGKS_FP32 or SDUGKS_FP32_BF16DEV.  stream as for
+ * instances.  precision: SDUGKS_FP32, SDUGKS_FP32_BF16DEV or SDUGKS_FP32_FP16DEV.  stream as for
  * solvers.  Errors: INVALID_ARG, OOM, CUDA. */
 int sdugks_batch_create(int64_t pool_bytes, int32_t precision, int32_t max_instances, void *stream,
                         sdugks_batch **out);

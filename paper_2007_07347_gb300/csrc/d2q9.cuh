@@ -2,6 +2,7 @@
 // codecs of f shared by the CUDA translation units.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include "sdugks_internal.h"
 
@@ -130,6 +131,18 @@ template <> struct Store<P_BF16DEV> {
     using T = __nv_bfloat16; using R = float;
     static __device__ __forceinline__ R dec(T v, R feq, int a) { return feq + wq<R>(a) * __bfloat162float(v); }
     static __device__ __forceinline__ T enc(R f, R feq, int a) { return __float2bfloat16_rn((f - feq) * inv_wq<R>(a)); }
+};
+// FP16DEV stores d / s with the power of two s = 2^-10: binary16 keeps 11 significant
+// bits over [6.1e-5, 65504], so scaled deviations |d| from 6e-8 to 64 stay normal.
+constexpr float FP16DEV_SCALE = 1.0f / 1024.0f;
+template <> struct Store<P_FP16DEV> {
+    using T = __half; using R = float;
+    static __device__ __forceinline__ R dec(T v, R feq, int a) {
+        return feq + (wq<R>(a) * FP16DEV_SCALE) * __half2float(v);
+    }
+    static __device__ __forceinline__ T enc(R f, R feq, int a) {
+        return __float2half_rn((f - feq) * (inv_wq<R>(a) * (1.0f / FP16DEV_SCALE)));
+    }
 };
 
 // IEEE-754 format conversions by field arithmetic on the integer pipe (the FP64 unit of

@@ -131,10 +131,15 @@ int grid_of(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (
 
 cudaError_t prepare_batch(int prec)
 {
+    if (prec == P_FP16DEV) return prep_p<P_FP16DEV>();
     return prec == P_BF16DEV ? prep_p<P_BF16DEV>() : prep_p<P_FP32>();
 }
 
-int batch_ctas_per_sm(int prec) { return prec == P_BF16DEV ? occ_p<P_BF16DEV>() : occ_p<P_FP32>(); }
+int batch_ctas_per_sm(int prec)
+{
+    if (prec == P_FP16DEV) return occ_p<P_FP16DEV>();
+    return prec == P_BF16DEV ? occ_p<P_BF16DEV>() : occ_p<P_FP32>();
+}
 
 cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,
                               int parity, cudaStream_t st)
@@ -142,6 +147,9 @@ cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items
     if (prec == P_BF16DEV)
         return launch_step_kernel(k_step_batch<P_BF16DEV, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
                                   cart_smem<P_BF16DEV, BTX, BTY>(), st, insts, items, n_items, parity);
+    if (prec == P_FP16DEV)
+        return launch_step_kernel(k_step_batch<P_FP16DEV, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
+                                  cart_smem<P_FP16DEV, BTX, BTY>(), st, insts, items, n_items, parity);
     return launch_step_kernel(k_step_batch<P_FP32, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
                               cart_smem<P_FP32, BTX, BTY>(), st, insts, items, n_items, parity);
 }
@@ -159,6 +167,7 @@ cudaError_t launch_batch_init(int prec, const CartInst *inst_host, const CartIns
 {
     const int g = grid_of((int64_t)inst_host->nx * inst_host->ny);
     if (prec == P_BF16DEV) k_binit<P_BF16DEV><<<g, 256, 0, st>>>(inst_dev, parity, rho, u);
+    else if (prec == P_FP16DEV) k_binit<P_FP16DEV><<<g, 256, 0, st>>>(inst_dev, parity, rho, u);
     else k_binit<P_FP32><<<g, 256, 0, st>>>(inst_dev, parity, rho, u);
     return cudaGetLastError();
 }

@@ -21,6 +21,7 @@ template <int P> cudaError_t prepare_shapes()
 cudaError_t prepare_cart(int prec)
 {
     if (prec == P_FP64) return prepare_cart_fp64();
+    if (prec == P_FP16DEV) return prepare_shapes<P_FP16DEV>();
     return prec == P_BF16DEV ? prepare_shapes<P_BF16DEV>() : prepare_shapes<P_FP32>();
 }
 
@@ -35,6 +36,7 @@ cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, int parity,
 {
     if (prec == P_FP64) return launch_cart_fp64(m, parity, st);
     if (prec == P_BF16DEV) return launch_shape<P_BF16DEV>(shape, m, parity, st);
+    if (prec == P_FP16DEV) return launch_shape<P_FP16DEV>(shape, m, parity, st);
     return launch_shape<P_FP32>(shape, m, parity, st);
 }
 
@@ -52,6 +54,8 @@ int cart_shape_occupancy(int prec, int shape)
     if (prec == P_FP64) return occ_shape<P_FP64, 16, 16>();
     if (prec == P_BF16DEV)
         return shape == 1 ? occ_shape<P_BF16DEV, 16, 14>() : shape == 2 ? occ_shape<P_BF16DEV, 16, 8>() : occ_shape<P_BF16DEV, 16, 16>();
+    if (prec == P_FP16DEV)
+        return shape == 1 ? occ_shape<P_FP16DEV, 16, 14>() : shape == 2 ? occ_shape<P_FP16DEV, 16, 8>() : occ_shape<P_FP16DEV, 16, 16>();
     return shape == 1 ? occ_shape<P_FP32, 16, 14>() : shape == 2 ? occ_shape<P_FP32, 16, 8>() : occ_shape<P_FP32, 16, 16>();
 }
 

@@ -151,6 +151,7 @@ cudaError_t launch_init_state(int prec, int64_t n, int64_t npad, const int32_t *
     const int g = grid_for(n);
     if (prec == P_FP64) k_init<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (double *)f, W);
     else if (prec == P_FP32) k_init<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (float *)f, W);
+    else if (prec == P_FP16DEV) k_init<P_FP16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (__half *)f, W);
     else k_init<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, rho, u, (__nv_bfloat16 *)f, W);
     return cudaGetLastError();
 }
@@ -163,6 +164,8 @@ cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *
         k_pack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, loc, (const double *)f, W, f_out, W_out);
     else if (prec == P_FP32)
         k_pack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, loc, (const float *)f, W, f_out, W_out);
+    else if (prec == P_FP16DEV)
+        k_pack<P_FP16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, (const __half *)f, W, f_out, W_out);
     else
         k_pack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, (const __nv_bfloat16 *)f, W, f_out, W_out);
     return cudaGetLastError();
@@ -176,6 +179,8 @@ cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t
         k_unpack<P_FP64><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (double *)f, W);
     else if (prec == P_FP32)
         k_unpack<P_FP32><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (float *)f, W);
+    else if (prec == P_FP16DEV)
+        k_unpack<P_FP16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (__half *)f, W);
     else
         k_unpack<P_BF16DEV><<<g, UT, 0, st>>>(n, npad, perm, loc, f_in, W_in, (__nv_bfloat16 *)f, W);
     return cudaGetLastError();

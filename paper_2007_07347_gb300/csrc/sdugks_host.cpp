@@ -657,7 +657,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     if (!m || !prm) return fail(SDUGKS_ERR_INVALID_ARG, "mesh or params is NULL");
     if (!(prm->tau > 0) || !(prm->dt > 0) || !std::isfinite(prm->tau) || !std::isfinite(prm->dt))
         return fail(SDUGKS_ERR_INVALID_ARG, "tau and dt must be finite and > 0");
-    if (prm->precision < SDUGKS_FP64 || prm->precision > SDUGKS_FP32_BF16DEV)
+    if (prm->precision < SDUGKS_FP64 || prm->precision > SDUGKS_FP32_FP16DEV)
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown precision %d", prm->precision);
     if (prm->kernel < SDUGKS_KERNEL_AUTO || prm->kernel > SDUGKS_KERNEL_CARTESIAN)
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown kernel %d", prm->kernel);
@@ -1365,7 +1365,7 @@ int64_t cart_npad(int32_t pitch, int32_t ny) { return ((int64_t)pitch * ny + 31)
 
 size_t inst_bytes(int prec, int64_t npad)
 {
-    const size_t fs = prec == P_BF16DEV ? 2 : 4;
+    const size_t fs = (prec == P_BF16DEV || prec == P_FP16DEV) ? 2 : 4;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     return 2 * up(NQ * npad * fs) + 2 * up(3 * npad * 8) + up(2 * npad * 8);
 }
@@ -1428,7 +1428,7 @@ extern "C" int sdugks_batch_create(int64_t pool_bytes, int32_t precision, int32_
     *out = nullptr;
     if (pool_bytes <= 0 || max_instances <= 0 || max_instances > (1 << 20))
         return fail(SDUGKS_ERR_INVALID_ARG, "pool_bytes must be > 0 and max_instances in [1, 2^20]");
-    if (precision != SDUGKS_FP32 && precision != SDUGKS_FP32_BF16DEV)
+    if (precision != SDUGKS_FP32 && precision != SDUGKS_FP32_BF16DEV && precision != SDUGKS_FP32_FP16DEV)
         return fail(SDUGKS_ERR_INVALID_ARG, "batches run in FP32 or FP32_BF16DEV");
     sdugks_batch *b = new (std::nothrow) sdugks_batch;
     if (!b) return fail(SDUGKS_ERR_OOM, "host allocation failed");
@@ -1497,7 +1497,7 @@ extern "C" int sdugks_batch_add(sdugks_batch *b, const sdugks_mesh *m, double ta
     fill_cart_inst(bi.ci, *m, g, tau, dt, pitch, npad);
     {
         auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-        const size_t fs = b->prec == P_BF16DEV ? 2 : 4;
+        const size_t fs = (b->prec == P_BF16DEV || b->prec == P_FP16DEV) ? 2 : 4;
         char *p = b->pool + off;
         for (int k = 0; k < 2; k++) { bi.ci.f[k] = p; p += up(NQ * npad * fs); }
         for (int k = 0; k < 2; k++) { bi.ci.W[k] = reinterpret_cast<double *>(p); p += up(3 * npad * 8); }

@@ -21,7 +21,7 @@ constexpr int LOC_MAX = 416;    // interior + two halo rings
 constexpr int SIG_MAX = 272;    // interior + first halo ring (cells whose gradient is needed)
 constexpr int LF_MAX = 320;     // faces with at least one interior cell of the tile
 
-enum Prec : int32_t { P_FP64 = 0, P_FP32 = 1, P_BF16DEV = 2 };
+enum Prec : int32_t { P_FP64 = 0, P_FP32 = 1, P_BF16DEV = 2, P_FP16DEV = 3 };
 
 enum BcKind : int32_t { BK_UNSET = 0, BK_PERIODIC = 1, BK_WALL = 2, BK_MOVING_WALL = 3,
                         BK_FARFIELD = 4, BK_OUTLET = 5, BK_SYMMETRY = 6 };

@@ -381,7 +381,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             feq9f<R>(rho, ux, uy, fe);
 #pragma unroll
             for (int a = 0; a < NQ; a++)
-                if constexpr (P == P_BF16DEV) fv[a] += fe[a];       // decode the deviation
+                if constexpr (P == P_BF16DEV || P == P_FP16DEV) fv[a] += fe[a];       // decode the deviation
             if (mir == 0) {
                 if constexpr (P == P_FP64) {
 #pragma unroll

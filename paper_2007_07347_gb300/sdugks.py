@@ -20,9 +20,9 @@ from . import meshes as _meshes
 _lock = threading.Lock()
 _lib = None
 
-FP64, FP32, FP32_BF16DEV = 0, 1, 2
+FP64, FP32, FP32_BF16DEV, FP32_FP16DEV = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_TILED, KERNEL_CARTESIAN = 0, 1, 2
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16dev": FP32_BF16DEV}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16dev": FP32_BF16DEV, "fp16dev": FP32_FP16DEV}
 ERRORS = {-1: "INVALID_ARG", -2: "INVALID_MESH", -3: "BAD_BC", -4: "OOM", -5: "DIVERGED", -6: "TIMEOUT",
           -7: "CUDA", -8: "STATE", -9: "FULL"}
 

@@ -42,7 +42,7 @@ MIX = [lambda: M.cavity(40, Re=400.0), lambda: M.cavity(100, Re=1000.0), lambda:
        lambda: M.cavity(64, Re=100.0)]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16dev"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev", "fp16dev"])
 def test_batch_instances_equal_single_solvers(precision):
     S = _S()
     b = S.Batch(256 << 20, precision, max_instances=16)
@@ -52,7 +52,7 @@ def test_batch_instances_equal_single_solvers(precision):
     for ident, case in zip(ids, cases):
         rho, u = b.macros(ident)
         rho1, u1 = _single(case, 300, precision)
-        _close_to_single(rho, u, rho1, u1, *((1e-4, 1e-5) if precision == "fp32" else (1e-3, 1e-4)))
+        _close_to_single(rho, u, rho1, u1, *{"fp32": (1e-4, 1e-5), "bf16dev": (1e-3, 1e-4), "fp16dev": (1e-3, 1e-4)}[precision])
 
 
 def test_result_same_alone_and_in_the_mix_and_late_admission():

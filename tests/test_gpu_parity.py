@@ -243,6 +243,20 @@ def test_bf16dev_cylinder_against_oracle():
     assert rel_l2(u, st.u) <= 1e-2
 
 
+@pytest.mark.parametrize("kernel", ["auto", "tiled"])
+def test_fp16dev_storage_against_oracle(kernel):
+    """fp16 scaled-deviation storage (d / 2^-10 in binary16, 11 significant bits; 3 more
+    than bf16): the cavity on the Cartesian and the tiled kernel and the cylinder
+    against the FP64 oracle, relative L2 of u <= 2e-3 (bf16: 1e-2)."""
+    S = _S()
+    for case, steps in ((M.cavity(64, Re=400.0), 1500), (M.cylinder(128, 64, first=0.01, r_far=20.0), 1500)):
+        u0 = None if case.u0 == (0.0, 0.0) else np.tile(case.u0, (case.mesh.n_cells, 1))
+        s, (f, W), st = run_both(case, steps, "fp16dev", None, u0, kernel=KERNELS[kernel])
+        rho, u = s.macros()
+        assert rel_l2(u, st.u) <= 2e-3
+        assert np.abs(rho - st.rho).max() <= 1e-4
+
+
 def test_residual_matches_oracle():
     S = _S()
     case = M.cavity(32, Re=100.0)
@@ -307,7 +321,7 @@ def test_cylinder_full_size_fp32_and_bf16dev():
     u0 = np.tile(case.u0, (case.mesh.n_cells, 1))
     st = O.init(case.mesh.n_cells, u=u0)
     O.run(case, st, 300)
-    for prec, tol, tol_d in (("fp32", 1e-4, 1e-3), ("bf16dev", 1e-2, 5e-2)):
+    for prec, tol, tol_d in (("fp32", 1e-4, 1e-3), ("bf16dev", 1e-2, 5e-2), ("fp16dev", 2e-3, 1e-2)):
         s = S.Solver.from_case(case, prec).init(None, u0)
         assert s.info()["kernel"] == S.KERNEL_TILED
         s.step(300)
