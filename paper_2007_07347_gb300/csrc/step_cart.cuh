@@ -22,25 +22,43 @@
 
 namespace sdugks {
 
+// Rows of cells or faces are dealt to warps two at a time, each half-warp one row of 16:
+// rows 4g + k pair as (4g, 4g + 2) and (4g + 1, 4g + 3), so that with the staging row
+// stride SX = 24 (48 = 16 mod 32 words between the two rows of a warp) every shared
+// access of a warp at a common offset from its positions hits 32 distinct banks.
+// Slot s of a row set: warp s / 32, half s / 16 % 2, column s % 16.
+__host__ __device__ constexpr int slot_row(int s) { return 4 * (s >> 6) + ((s >> 5) & 1) + 2 * ((s >> 4) & 1); }
+__host__ __device__ constexpr int row_slot(int r, int col) {
+    return 32 * (2 * (r >> 2) + (r & 1)) + 16 * ((r >> 1) & 1) + col;
+}
+// warps that hold rows 0 .. nr-1
+__host__ __device__ constexpr int row_warps(int nr) { return 2 * (nr / 4) + (nr % 4 < 2 ? nr % 4 : 2); }
+
 template <int TX, int TY> struct CartShape {
+    static_assert(TX == 16 && TY % 2 == 0 && TY <= 16, "blocks are 16 wide with an even height of at most 16");
     static constexpr int LX = TX + 4, LY = TY + 4;   // staged block with a two-cell halo
-    static constexpr int GX = TX + 2, GY = TY + 2;   // cells whose gradient is needed
+    static constexpr int SX = 24;                    // row stride of the staged planes (>= LX)
+    static constexpr int PLANE = SX * LY;            // plane stride (one velocity)
     static constexpr int NT = TX * TY;
-    static constexpr int NFX = (TX + 1) * TY;        // faces of constant x inside/around the block
-    static constexpr int NFY = TX * (TY + 1);        // faces of constant y
+    static constexpr int WX = row_warps(TY);         // warps of the cell rows / constant-x face rows
+    static constexpr int WY = row_warps(TY + 1);     // warps of the constant-y face rows
+    // face slots: constant-x faces left of each block cell (32 WX slots), then the TY faces on
+    // the block's right edge; constant-y faces below each block cell and above the top row
+    static constexpr int NSX = 32 * WX + TY;
+    static constexpr int NSY = 32 * WY;
 };
 
-// Threads per CTA: one per interior face of the block (>= cells, >= staged positions).
+// Threads per CTA: one per face slot (>= cell slots + ring positions of the staging).
 template <int TX, int TY> __host__ __device__ constexpr int cart_threads() {
-    constexpr int nf = CartShape<TX, TY>::NFX + CartShape<TX, TY>::NFY;
-    constexpr int nl = CartShape<TX, TY>::LX * CartShape<TX, TY>::LY;
-    constexpr int m = nf > nl ? nf : nl;
-    return (m + 31) / 32 * 32;
+    using S = CartShape<TX, TY>;
+    constexpr int nf = 32 * (S::WX + S::WY);
+    constexpr int nl = 32 * S::WX + S::LX * S::LY - S::NT;
+    return nf > nl ? nf : nl;
 }
 
 template <int P, int TX, int TY> constexpr size_t cart_smem() {
     using S = CartShape<TX, TY>;
-    return sizeof(typename Store<P>::R) * (size_t)(NQ * S::LX * S::LY + 6 * (S::NFX + S::NFY));
+    return sizeof(typename Store<P>::R) * (size_t)(NQ * S::PLANE + 6 * (S::NSX + S::NSY));
 }
 
 // Velocities crossing a face of constant x (xi_x != 0) and of constant y, in slot order.
@@ -275,10 +293,10 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     using T = typename Store<P>::T;
     using SP = Store<P>;
     using S = CartShape<TX, TY>;
-    constexpr int LXY = S::LX * S::LY;
-    R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][LX]
-    R *s_fx = s_fbp + NQ * LXY;                      // [6][NFX] fluxes through faces of constant x
-    R *s_fy = s_fx + 6 * S::NFX;                     // [6][NFY]
+    constexpr int LXY = S::PLANE;
+    R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][SX]
+    R *s_fx = s_fbp + NQ * LXY;                      // [6][NSX] fluxes through faces of constant x, by slot
+    R *s_fy = s_fx + 6 * S::NSX;                     // [6][NSY] constant y
 
     const T *__restrict__ fin = static_cast<const T *>(m.f[par]);
     T *__restrict__ fout = static_cast<T *>(m.f[1 - par]);
@@ -328,12 +346,12 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     };
     // gradient stencil of the staged cell at block position (bi, bj)
     auto sten = [&](int bi, int bj) {
-        if (INTERIOR) return Sten<R>{1, -1, S::LX, -S::LX, R(0.5) * k.ihx, R(0.5) * k.ihy};
+        if (INTERIOR) return Sten<R>{1, -1, S::SX, -S::SX, R(0.5) * k.ihx, R(0.5) * k.ihy};
         const int ci = x0 + bi, cj = y0 + bj;
         const bool hE = has_x(ci + 1), hW = has_x(ci - 1);
         const bool hN = has_y(cj + 1), hS = has_y(cj - 1);
         Sten<R> st;
-        st.oE = hE ? 1 : 0; st.oW = hW ? -1 : 0; st.oN = hN ? S::LX : 0; st.oS = hS ? -S::LX : 0;
+        st.oE = hE ? 1 : 0; st.oW = hW ? -1 : 0; st.oN = hN ? S::SX : 0; st.oS = hS ? -S::SX : 0;
         st.ax = (hE && hW) ? R(0.5) * k.ihx : k.ihx;
         st.ay = (hN && hS) ? R(0.5) * k.ihy : k.ihy;
         return st;
@@ -345,14 +363,14 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     };
 
     // ---- phase 1: fbar+ = a f^n + b feq(W^n) of every staged position, one round.
-    // Threads 0..NT-1 take the block (their own cell, kept in registers), the others
-    // the two-cell ring.
-    const bool cell_thread = tid < S::NT;
-    const int ti = tid % TX, tj = tid / TX;
+    // The cell slots (threads 0 .. 32 WX - 1) take the block (their own cell, kept in
+    // registers), the next LX LY - NT threads the two-cell ring.
+    const int ti = tid & 15, tj = slot_row(tid);
+    const bool cell_thread = tid < 32 * S::WX && tj < TY;
     const int gi = x0 + ti, gj = y0 + tj;
     const bool active = cell_thread && gi < nx && gj < ny;
     const int64_t g = (int64_t)gi + pitch * gj;
-    const int lme = (tj + 2) * S::LX + (ti + 2);
+    const int lme = (tj + 2) * S::SX + (ti + 2);
     R fn[NQ];
     R rho_n = R(1), ux_n = R(0), uy_n = R(0);
     double w0n = 1.0, w1n = 0.0, w2n = 0.0;
@@ -362,14 +380,14 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         if (cell_thread) {
             ls = lme;
             gs = active ? g : cell_of(ti, tj, mir);     // past the grid edge: a wrapped cell, a ghost or none
-        } else if (tid < LXY) {
+        } else if (tid >= 32 * S::WX && tid < 32 * S::WX + S::LX * S::LY - S::NT) {
             // ring position r: two rows below, two above, then two columns left and right
-            const int r = tid - S::NT;
+            const int r = tid - 32 * S::WX;
             int li, lj;
             if (r < 2 * S::LX) { li = r % S::LX; lj = r / S::LX; }
             else if (r < 4 * S::LX) { li = (r - 2 * S::LX) % S::LX; lj = S::LY - 2 + (r - 2 * S::LX) / S::LX; }
             else { const int q = r - 4 * S::LX; lj = 2 + q / 4; const int cc = q % 4; li = cc < 2 ? cc : S::LX - 4 + cc; }
-            ls = lj * S::LX + li;
+            ls = lj * S::SX + li;
             gs = cell_of(li - 2, lj - 2, mir);
         }
         if (gs >= 0) {
@@ -417,28 +435,36 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     }
     __syncthreads();
 
-    // ---- phase 2: every interior face of the block once, one per thread
-    if (tid < S::NFX) {
-        // face of constant x between block columns fi-1 (L) and fi (R), row fj
-        const int fi = tid % (TX + 1), fj = tid / (TX + 1);
+    // ---- phase 2: every interior face of the block once, one per thread.  Faces of
+    // constant x: slot s < 32 WX is the face left of block cell (s % 16, row of s); the
+    // free upper half of the last constant-y warp takes the TY faces on the right edge.
+    // A constant-x face between block columns fi-1 (L) and fi (R) in row fj:
+    auto x_face = [&](int fi, int fj, int slot) {
         if (has_x(x0 + fi - 1) && has_x(x0 + fi) && has_y(y0 + fj)) {
-            const int lL = (fj + 2) * S::LX + (fi + 1);
+            const int lL = (fj + 2) * S::SX + (fi + 1);
             R fl[6];
             if constexpr (P == P_FP64) cart_interior_face<0, R>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
             else cart_interior_face_f32x2<0>(fl, s_fbp, lL, lL + 1, sten(fi - 1, fj), sten(fi, fj), k, LXY);
 #pragma unroll
-            for (int r = 0; r < 6; r++) s_fx[r * S::NFX + tid] = fl[r];
+            for (int r = 0; r < 6; r++) s_fx[r * S::NSX + slot] = fl[r];
         }
-    } else if (tid < S::NFX + S::NFY) {
+    };
+    if (tid < 32 * S::WX) {
+        if (tj < TY) x_face(ti, tj, tid);
+    } else if (tid < 32 * (S::WX + S::WY)) {
         // face of constant y between block rows fj-1 (below) and fj (above), column fi
-        const int qq = tid - S::NFX, fi = qq % TX, fj = qq / TX;
-        if (has_y(y0 + fj - 1) && has_y(y0 + fj) && has_x(x0 + fi)) {
-            const int lB = (fj + 1) * S::LX + (fi + 2);
-            R fl[6];
-            if constexpr (P == P_FP64) cart_interior_face<1, R>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
-            else cart_interior_face_f32x2<1>(fl, s_fbp, lB, lB + S::LX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
+        const int qq = tid - 32 * S::WX, fi = qq & 15, fj = slot_row(qq);
+        if (fj <= TY) {
+            if (has_y(y0 + fj - 1) && has_y(y0 + fj) && has_x(x0 + fi)) {
+                const int lB = (fj + 1) * S::SX + (fi + 2);
+                R fl[6];
+                if constexpr (P == P_FP64) cart_interior_face<1, R>(fl, s_fbp, lB, lB + S::SX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
+                else cart_interior_face_f32x2<1>(fl, s_fbp, lB, lB + S::SX, sten(fi, fj - 1), sten(fi, fj), k, LXY);
 #pragma unroll
-            for (int r = 0; r < 6; r++) s_fy[r * S::NFY + qq] = fl[r];
+                for (int r = 0; r < 6; r++) s_fy[r * S::NSY + qq] = fl[r];
+            }
+        } else if ((qq >> 5) == S::WY - 1 && fi < TY) {
+            x_face(TX, fi, 32 * S::WX + fi);           // right edge of the block, row fi
         }
     }
     __syncthreads();
@@ -448,32 +474,35 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         R F[NQ];
 #pragma unroll
         for (int a = 0; a < NQ; a++) F[a] = R(0);
-        const int fW = tj * (TX + 1) + ti, fS = tj * TX + ti;
+        // face slots: left = own slot, right = next slot (or the right-edge slot of the
+        // row), below / above by row_slot
+        const int fW = tid, fE = ti + 1 < TX ? tid + 1 : 32 * S::WX + tj;
+        const int fS = row_slot(tj, ti), fN = row_slot(tj + 1, ti);
         const bool inW = has_x(gi - 1), inE = has_x(gi + 1);
         const bool inS = has_y(gj - 1), inN = has_y(gj + 1);
         R feqn[NQ];
         if (!(inW && inE && inS && inN)) feq9f<R>(rho_n, ux_n, uy_n, feqn);   // boundary cells only
         if (inW) {
 #pragma unroll
-            for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NFX + fW];
+            for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NSX + fW];
         } else {
             cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inE) {
 #pragma unroll
-            for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NFX + fW + 1];
+            for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NSX + fE];
         } else {
             cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inS) {
 #pragma unroll
-            for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NFY + fS];
+            for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NSY + fS];
         } else {
             cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inN) {
 #pragma unroll
-            for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NFY + fS + TX];
+            for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NSY + fN];
         } else {
             cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
