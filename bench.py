@@ -60,6 +60,9 @@ def parse():
                          "40x40 micro cavity on a 100x100 velocity grid (Kn 1)")
     ap.add_argument("--tile-cells", type=int, default=0,
                     help="block / tile size of the solver (0: the solver's own choice)")
+    ap.add_argument("--staging", default="loads", choices=["loads", "tma"],
+                    help="cavity: how the Cartesian kernel stages its interior blocks (per-thread loads or "
+                         "TMA tensor copies)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
     args = ap.parse_args()
@@ -99,7 +102,8 @@ def config(args, case):
             "storage": args.precision, "tau": case.tau, "dt": case.dt,
             "l2": f"flushed (256 MB rewrite) before each timed step; the {state_mb:.1f} MB state is L2-resident "
                   f"within a step",
-            "parallelism": f"replicas x{args.gpus}"}
+            "parallelism": f"replicas x{args.gpus}",
+            **({"staging": args.staging} if args.workload == "cavity" else {})}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -289,7 +293,8 @@ def run_ours(args):
     case = workload(args)
     n = case.mesh.n_cells
     stream = torch.cuda.Stream()
-    s = S.Solver.from_case(case, args.precision, stream=stream, tile_cells=args.tile_cells)
+    s = S.Solver.from_case(case, args.precision, stream=stream, tile_cells=args.tile_cells,
+                           staging=args.staging if args.workload == "cavity" else "loads")
     s.init(None, initial_u(case))
     info = s.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

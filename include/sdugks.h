@@ -68,6 +68,11 @@ extern "C" {
 #define SDUGKS_KERNEL_TILED 1     /* unstructured tiled kernel on any quad mesh        */
 #define SDUGKS_KERNEL_CARTESIAN 2 /* structured kernel; INVALID_ARG if not a grid      */
 
+/* ---- staging of the Cartesian kernel's interior blocks --------------------------- */
+#define SDUGKS_STAGING_LOADS 0    /* every thread loads its staged position (default)  */
+#define SDUGKS_STAGING_TMA 1      /* two TMA tensor copies per block (Cartesian only;  */
+                                  /* the same results; 1-6 % slower on GB300)          */
+
 typedef struct sdugks_mesh sdugks_mesh;
 typedef struct sdugks_solver sdugks_solver;
 
@@ -82,6 +87,10 @@ typedef struct sdugks_params {
                             bf16 and fp16 storage): 256, 224 or 128 for 16x16, 16x14 or 16x8 blocks;
                             0 = chosen from the grid size (Cartesian) or 128 (tiled) */
     int32_t graph_steps; /* steps per captured CUDA graph in sdugks_step, 0 = auto, <0 = off */
+    int32_t staging;     /* SDUGKS_STAGING_*; TMA requires the Cartesian kernel (else
+                            INVALID_ARG).  A TMA copy that does not land within 0.2 s
+                            makes the block give up and the next sdugks_residual
+                            report SDUGKS_ERR_TIMEOUT */
 } sdugks_params;
 
 /* What a solver chose and holds (sdugks_solver_info). */
@@ -97,6 +106,7 @@ typedef struct sdugks_info {
     int32_t precision;
     int32_t tile_cells;
     int32_t nx, ny;               /* Cartesian kernel: grid size, else 0               */
+    int32_t staging;              /* SDUGKS_STAGING_* in use                           */
 } sdugks_info;
 
 /* ---- mesh ---------------------------------------------------------------------- */

@@ -5,9 +5,11 @@ namespace sdugks {
 
 cudaError_t prepare_cart_fp64() { return prepare_cart_p<P_FP64, 16, 16>(); }
 
-cudaError_t launch_cart_fp64(const CartInst &m, int parity, cudaStream_t st)
+cudaError_t launch_cart_fp64(const CartInst &m, const CartTma *tma, int parity, cudaStream_t st)
 {
-    return launch_cart_p<P_FP64, 16, 16>(m, parity, st);
+    return launch_cart_p<P_FP64, 16, 16>(m, tma, parity, st);
 }
+
+int occ_cart_fp64(bool tma) { return tma ? occ_cart_p<P_FP64, 16, 16, true>() : occ_cart_p<P_FP64, 16, 16, false>(); }
 
 }  // namespace sdugks

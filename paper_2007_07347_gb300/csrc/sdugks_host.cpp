@@ -366,11 +366,12 @@ struct sdugks_solver {
     int32_t *loc = nullptr;         // q-th listed cell -> internal offset (nullptr: q)
     CartInst ci{};
     int cart_shape = 0;             // Cartesian block shape (CART_TY)
+    CartTma *tma = nullptr;         // Cartesian: tensor maps of the TMA staging (nullptr: plain loads)
     double *vol = nullptr, *snap = nullptr, *partial = nullptr, *red = nullptr;
     State st{};
     int n_red_blocks = 1;
     double *staging = nullptr;      // [n][15] FP64, allocated on first use
-    double *h_red = nullptr;        // pinned [4]
+    double *h_red = nullptr;        // pinned [5]: red[0..3], then the error flag (int32 in red[4])
     bool initialised = false;
     int cur = 0;                    // buffer (f and W) holding the state at t_n
     int64_t steps_done = 0;
@@ -392,7 +393,7 @@ static cudaError_t launch_one(sdugks_solver *s, cudaStream_t st)
     const int a = s->cur;
     cudaError_t e;
     if (s->kernel == SDUGKS_KERNEL_CARTESIAN)
-        e = launch_step_cart(s->p.precision, s->cart_shape, s->ci, a, st);
+        e = launch_step_cart(s->p.precision, s->cart_shape, s->ci, s->tma, a, st);
     else if (s->p.precision == P_FP64)
         e = launch_step_tiled_fp64(s->tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], st);
     else
@@ -580,7 +581,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
         s->vol = A.take<double>(npad);
         s->snap = A.take<double>(2 * npad);
         s->partial = A.take<double>(4 * (size_t)s->n_red_blocks);
-        s->red = A.take<double>(4);
+        s->red = A.take<double>(5);
         for (int b = 0; b < 2; b++) s->st.f[b] = A.take<char>(NQ * npad * fs);
         for (int b = 0; b < 2; b++) s->st.W[b] = A.take<double>(3 * npad);
     };
@@ -598,6 +599,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     layout(A);
     for (int b = 0; b < 2; b++) { s->ci.f[b] = s->st.f[b]; s->ci.W[b] = s->st.W[b]; }
     s->ci.snap = s->snap;
+    s->ci.err = reinterpret_cast<int32_t *>(s->red + 4);
     std::vector<int32_t> perm(n), loc(n);
     std::vector<double> vol(npad, 1.0);
     for (int64_t c = 0; c < n; c++) {
@@ -613,7 +615,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     chk(cudaMemcpy(s->perm, perm.data(), n * 4, cudaMemcpyHostToDevice), "upload perm");
     chk(cudaMemcpy(s->loc, loc.data(), n * 4, cudaMemcpyHostToDevice), "upload loc");
     chk(cudaMemcpy(s->vol, vol.data(), npad * 8, cudaMemcpyHostToDevice), "upload vol");
-    chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
+    chk(cudaMallocHost(&s->h_red, 5 * sizeof(double)), "cudaMallocHost");
     chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     chk((cudaError_t)prepare(prec, SDUGKS_KERNEL_CARTESIAN), "kernel attributes");
     if (rc2) { sdugks_solver_destroy(s); return rc2; }
@@ -624,6 +626,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     // shapes that fit four blocks per SM credited 1.21x for hiding latency better (the
     // ratio measured on GB300 between the 16x8 and 16x16 shapes on a 1024^2 grid).
     // The choice depends only on the grid size and the device, never on timings.
+    const bool use_tma = prm->staging == SDUGKS_STAGING_TMA;
     {
         int n_sm = 1;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -633,7 +636,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
             for (int sh = 0; sh < CART_SHAPES; sh++) {
                 const int ty = CART_TY[sh];
                 if (prm->tile_cells && prm->tile_cells != 16 * ty) continue;
-                const int occ = std::max(1, cart_shape_occupancy(prec, sh));
+                const int occ = std::max(1, cart_shape_occupancy(prec, sh, use_tma));
                 const int64_t tiles = (int64_t)((g.nx + 15) / 16) * ((g.ny + ty - 1) / ty);
                 const int64_t slots = (int64_t)n_sm * occ;
                 const double work = (20.0 * (ty + 4) + 17.0 * ty + 16.0 * (ty + 1));
@@ -645,6 +648,17 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
         const int ty = CART_TY[s->cart_shape];
         s->n_tiles = ((g.nx + 15) / 16) * ((g.ny + ty - 1) / ty);
         s->halo_cells = (int64_t)s->n_tiles * (20 * (ty + 4) - 16 * ty);
+    }
+    // interior blocks staged by tensor copies; the maps hold the fixed addresses of the
+    // two state buffers
+    if (use_tma) {
+        s->tma = new (std::nothrow) CartTma;
+        if (!s->tma) { sdugks_solver_destroy(s); return fail(SDUGKS_ERR_OOM, "host allocation failed"); }
+        const cudaError_t te = make_cart_tma(prec, s->cart_shape, s->ci, *s->tma);
+        if (te != cudaSuccess) {
+            sdugks_solver_destroy(s);
+            return fail(SDUGKS_ERR_CUDA, "tensor maps of the Cartesian state: %s", cudaGetErrorString(te));
+        }
     }
     *out = s;
     return SDUGKS_OK;
@@ -661,6 +675,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown precision %d", prm->precision);
     if (prm->kernel < SDUGKS_KERNEL_AUTO || prm->kernel > SDUGKS_KERNEL_CARTESIAN)
         return fail(SDUGKS_ERR_INVALID_ARG, "unknown kernel %d", prm->kernel);
+    if (prm->staging != SDUGKS_STAGING_LOADS && prm->staging != SDUGKS_STAGING_TMA)
+        return fail(SDUGKS_ERR_INVALID_ARG, "unknown staging %d", prm->staging);
 
     Faces F;
     int rc = merge_periodic(*m, F);
@@ -678,6 +694,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         if (prm->kernel == SDUGKS_KERNEL_CARTESIAN)
             return fail(SDUGKS_ERR_INVALID_ARG, "not a uniform Cartesian grid: %s", cg.why.c_str());
     }
+    if (prm->staging == SDUGKS_STAGING_TMA)
+        return fail(SDUGKS_ERR_INVALID_ARG, "TMA staging needs the Cartesian kernel (a uniform grid)");
     if (prm->tile_cells != 0 && (prm->tile_cells < 16 || prm->tile_cells > TILE_MAX))
         return fail(SDUGKS_ERR_INVALID_ARG, "tile_cells must be 0 or in [16, %d]", TILE_MAX);
 
@@ -969,7 +987,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->vol = A.take<double>(npad);
         s->snap = A.take<double>(2 * npad);
         s->partial = A.take<double>(4 * (size_t)s->n_red_blocks);
-        s->red = A.take<double>(4);
+        s->red = A.take<double>(5);
         for (int b = 0; b < 2; b++) s->st.f[b] = A.take<char>(NQ * npad * fs);
         for (int b = 0; b < 2; b++) s->st.W[b] = A.take<double>(3 * npad);
         s->tm.tile_c0 = A.take<int32_t>(nt + 1);
@@ -1056,7 +1074,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     chk(up(s->tm.lf_ab, lf_ab.data(), lf_ab.size() * 4), "upload face sides");
     chk(up(s->tm.lf_geo, ggeo.data(), ggeo.size()), "upload face geometry");
     chk(up(s->tm.dtV, gdtv.data(), gdtv.size()), "upload dtV");
-    chk(cudaMallocHost(&s->h_red, 4 * sizeof(double)), "cudaMallocHost");
+    chk(cudaMallocHost(&s->h_red, 5 * sizeof(double)), "cudaMallocHost");
     chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     chk((cudaError_t)prepare(prec, SDUGKS_KERNEL_TILED), "kernel attributes");
     if (rc2) { sdugks_solver_destroy(s); return rc2; }
@@ -1087,8 +1105,12 @@ static int snapshot(sdugks_solver *s, double *eps, double *mass)
 {
     CUDA_TRY(launch_residual(s->n, s->npad, s->loc, s->st.W[s->cur], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
                              s->stream));
-    CUDA_TRY(cudaMemcpyAsync(s->h_red, s->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(s->h_red, s->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
+    int32_t err_flag;
+    std::memcpy(&err_flag, &s->h_red[4], sizeof err_flag);
+    if (err_flag != 0)
+        return fail(SDUGKS_ERR_TIMEOUT, "a TMA staging copy of the Cartesian step did not complete within its wait limit");
     const double num = s->h_red[0], den = s->h_red[1];
     if (mass) *mass = s->h_red[2];
     if (s->h_red[3] != 0.0) {
@@ -1176,7 +1198,7 @@ extern "C" int sdugks_step_forces(sdugks_solver *s, double *force)
     if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
         CartInst ci = s->ci;
         ci.force = s->d_force;                 // per grid side
-        e = launch_step_cart(s->p.precision, s->cart_shape, ci, s->cur, s->stream);
+        e = launch_step_cart(s->p.precision, s->cart_shape, ci, s->tma, s->cur, s->stream);
     } else {
         TiledMesh tm = s->tm;
         tm.force = s->d_force;                 // per patch
@@ -1287,6 +1309,7 @@ extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
     o->tile_cells = s->kernel == SDUGKS_KERNEL_CARTESIAN ? 16 * CART_TY[s->cart_shape] : (s->p.tile_cells ? s->p.tile_cells : TILE_MAX);
     o->nx = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.nx : 0;
     o->ny = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.ny : 0;
+    o->staging = s->tma ? SDUGKS_STAGING_TMA : SDUGKS_STAGING_LOADS;
     return SDUGKS_OK;
 }
 
@@ -1300,6 +1323,7 @@ extern "C" void sdugks_solver_destroy(sdugks_solver *s)
     if (s->d_force) cudaFree(s->d_force);
     if (s->h_red) cudaFreeHost(s->h_red);
     if (s->dmem) cudaFree(s->dmem);
+    delete s->tma;
     delete s;
 }
 

@@ -2,6 +2,7 @@
 // and the CUDA translation units.  Plain structs of device pointers and sizes.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace sdugks {
@@ -97,6 +98,7 @@ struct CartInst {
     double *W[2];
     double *snap;             // [2][npad] residual snapshot (U0, V0)
     double *force;            // nullptr, or [4][2]: momentum flux out of the fluid per grid side
+    int32_t *err;             // nullptr, or a device flag set to 1 when a bounded staging wait gave up
 };
 
 // Device state of one solver, ping-pong: f [2][NQ][npad] (element type by
@@ -116,8 +118,16 @@ cudaError_t prepare_cart(int prec);
 // block shapes of the Cartesian kernel: 0 = 16x16, 1 = 16x14, 2 = 16x8 (FP64: 16x16 only)
 constexpr int CART_SHAPES = 3;
 constexpr int CART_TY[CART_SHAPES] = {16, 14, 8};
-cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, int parity, cudaStream_t st);
-int cart_shape_occupancy(int prec, int shape);   // resident CTAs per SM
+// Tensor maps of one Cartesian state for the TMA staging of interior blocks:
+// f[b] views f buffer b as (x, y, velocity), W[b] views W buffer b as (x, y, component);
+// the boxes are the block with its two-cell halo, widened in x to 16-byte boundaries.
+struct CartTma {
+    CUtensorMap f[2], W[2];
+};
+cudaError_t make_cart_tma(int prec, int shape, const CartInst &m, CartTma &out);
+// tma: nullptr stages every block with plain loads
+cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, const CartTma *tma, int parity, cudaStream_t st);
+int cart_shape_occupancy(int prec, int shape, bool tma);   // resident CTAs per SM
 // batched: every (instance, tile) item of the list, grid-stride over a fixed grid
 cudaError_t prepare_batch(int prec);
 cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,

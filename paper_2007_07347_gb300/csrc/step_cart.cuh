@@ -61,6 +61,84 @@ template <int P, int TX, int TY> constexpr size_t cart_smem() {
     return sizeof(typename Store<P>::R) * (size_t)(NQ * S::PLANE + 6 * (S::NSX + S::NSY));
 }
 
+// TMA staging of an interior block: two tensor copies bring f^n and W^n of the block
+// and its two-cell halo into shared memory, boxes of (x, y, plane) whose first column
+// lies OFF columns left of the block so that it starts on a 16-byte boundary (x0 is a
+// multiple of 16): f box BW x (TY + 4) x NQ, W box WBW x (TY + 4) x 3.  The boxes
+// overlay the face-flux arrays (written only after phase 1 has read the boxes) and an
+// mbarrier follows; offsets from a 128-byte aligned base.
+template <class T> __host__ __device__ constexpr int tma_off() { return sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? 4 : 8); }
+template <int P, int TX, int TY> struct CartTmaBox {
+    using T = typename Store<P>::T;
+    using R = typename Store<P>::R;
+    using S = CartShape<TX, TY>;
+    static constexpr int OFF = tma_off<T>(), BW = TX + 2 * OFF;
+    static constexpr int WOFF = 2, WBW = TX + 4;
+    static constexpr size_t F_BYTES = sizeof(T) * (size_t)NQ * S::LY * BW;
+    static constexpr size_t W_BYTES = sizeof(double) * (size_t)3 * S::LY * WBW;
+    static constexpr size_t FBP_BYTES = sizeof(R) * (size_t)NQ * S::PLANE;
+    static constexpr size_t FLUX_BYTES = sizeof(R) * (size_t)6 * (S::NSX + S::NSY);
+    static constexpr size_t F_OFF = (FBP_BYTES + 127) / 128 * 128;
+    static constexpr size_t W_OFF = F_OFF + (F_BYTES + 127) / 128 * 128;
+    static constexpr size_t END = (FBP_BYTES + FLUX_BYTES > W_OFF + W_BYTES) ? FBP_BYTES + FLUX_BYTES : W_OFF + W_BYTES;
+    static constexpr size_t BAR_OFF = (END + 15) / 16 * 16;
+    static constexpr size_t SMEM = BAR_OFF + 16 + 128;   // 128 bytes of slack align the base
+    static_assert((BW * sizeof(T)) % 16 == 0 && (WBW * sizeof(double)) % 16 == 0, "TMA box rows must be 16-byte multiples");
+    static_assert(BW <= 256 && WBW <= 256 && S::LY <= 256, "TMA box dimensions are at most 256");
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase `parity` of the mbarrier at shared address `bar` to complete;
+// gives up after `limit_ns` nanoseconds and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: arm the barrier at `bar` for the two boxes of the block at (x0, y0) and
+// start the tensor copies into dst_f / dst_w (shared addresses): the f box from
+// column x0 - OFF, the W box from x0 - 2, both from row y0 - 2.
+template <int P, int TX, int TY>
+__device__ __forceinline__ void tma_issue_block(uint32_t bar, uint32_t dst_f, uint32_t dst_w, const CUtensorMap *tf,
+                                                const CUtensorMap *tw, int x0, int y0)
+{
+    using B = CartTmaBox<P, TX, TY>;
+    const uint32_t bytes = (uint32_t)(B::F_BYTES + B::W_BYTES);
+    const int xf = x0 - B::OFF, xw = x0 - B::WOFF, y = y0 - 2;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst_f), "l"(reinterpret_cast<uint64_t>(tf)), "r"(xf), "r"(y), "r"(0), "r"(bar)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst_w), "l"(reinterpret_cast<uint64_t>(tw)), "r"(xw), "r"(y), "r"(0), "r"(bar)
+                 : "memory");
+}
+
+// Longest wait for a staging copy before the block reports SDUGKS_ERR_TIMEOUT through
+// the error flag (a copy normally lands within microseconds).
+constexpr uint64_t TMA_WAIT_NS = 200000000ull;
+
 // Velocities crossing a face of constant x (xi_x != 0) and of constant y, in slot order.
 __device__ constexpr int XSLOT_A(int k) { return k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
 __device__ constexpr int YSLOT_A(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 2 ? 5 : k == 3 ? 6 : k == 4 ? 7 : 8; }
@@ -285,14 +363,20 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int 
 // DIAG compiles in the optional wall-force accumulation.  INTERIOR: the block and its
 // two-cell halo lie inside the grid (no side, wrap or ghost within reach), so every
 // stencil is the central difference and every face of a cell is interior; the
-// existence tests and stencil choices are compile-time constants.
-template <int P, int TX, int TY, bool DIAG, bool INTERIOR>
-__device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, int tby, unsigned char *smem_raw)
+// existence tests and stencil choices are compile-time constants.  BOX (interior
+// blocks only): f^n and W^n of the staged block are read from the boxes a tensor copy
+// has already brought into shared memory (box_f, box_w; CartTmaBox layout) instead of
+// from global memory.
+template <int P, int TX, int TY, bool DIAG, bool INTERIOR, bool BOX = false>
+__device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, int tby, unsigned char *smem_raw,
+                                          const typename Store<P>::T *box_f = nullptr, const double *box_w = nullptr)
 {
+    static_assert(!BOX || INTERIOR, "box staging covers interior blocks");
     using R = typename Store<P>::R;
     using T = typename Store<P>::T;
     using SP = Store<P>;
     using S = CartShape<TX, TY>;
+    using B = CartTmaBox<P, TX, TY>;
     constexpr int LXY = S::PLANE;
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LY][SX]
     R *s_fx = s_fbp + NQ * LXY;                      // [6][NSX] fluxes through faces of constant x, by slot
@@ -376,14 +460,14 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     double w0n = 1.0, w1n = 0.0, w2n = 0.0;
     {
         int64_t gs = -1;
-        int ls = 0, mir = 0;
+        int ls = 0, mir = 0, li = 0, lj = 0;
         if (cell_thread) {
             ls = lme;
+            li = ti + 2; lj = tj + 2;
             gs = active ? g : cell_of(ti, tj, mir);     // past the grid edge: a wrapped cell, a ghost or none
         } else if (tid >= 32 * S::WX && tid < 32 * S::WX + S::LX * S::LY - S::NT) {
             // ring position r: two rows below, two above, then two columns left and right
             const int r = tid - 32 * S::WX;
-            int li, lj;
             if (r < 2 * S::LX) { li = r % S::LX; lj = r / S::LX; }
             else if (r < 4 * S::LX) { li = (r - 2 * S::LX) % S::LX; lj = S::LY - 2 + (r - 2 * S::LX) / S::LX; }
             else { const int q = r - 4 * S::LX; lj = 2 + q / 4; const int cc = q % 4; li = cc < 2 ? cc : S::LX - 4 + cc; }
@@ -391,10 +475,19 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             gs = cell_of(li - 2, lj - 2, mir);
         }
         if (gs >= 0) {
-            const double a0 = Wn[gs], a1 = Wn[np + gs], a2 = Wn[2 * np + gs];
+            double a0, a1, a2;
             R rho, ux, uy, fe[NQ], fv[NQ];
+            if constexpr (BOX) {
+                const double *w = box_w + lj * B::WBW + li;
+                a0 = w[0]; a1 = w[S::LY * B::WBW]; a2 = w[2 * S::LY * B::WBW];
+                const T *fb = box_f + lj * B::BW + li + (B::OFF - 2);
 #pragma unroll
-            for (int a = 0; a < NQ; a++) fv[a] = SP::dec(fin[a * np + gs], R(0), a);
+                for (int a = 0; a < NQ; a++) fv[a] = SP::dec(fb[a * S::LY * B::BW], R(0), a);
+            } else {
+                a0 = Wn[gs]; a1 = Wn[np + gs]; a2 = Wn[2 * np + gs];
+#pragma unroll
+                for (int a = 0; a < NQ; a++) fv[a] = SP::dec(fin[a * np + gs], R(0), a);
+            }
             macro(a0, a1, a2, rho, ux, uy);
             feq9f<R>(rho, ux, uy, fe);
 #pragma unroll
@@ -557,16 +650,64 @@ __device__ __forceinline__ bool cart_block_interior(const CartInst &m, int tbx, 
     return x0 >= 2 && x0 + TX + 2 <= m.nx && y0 >= 2 && y0 + TY + 2 <= m.ny;
 }
 
-template <int P, int TX, int TY>
-__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : (cart_threads<TX, TY>() <= 320 ? 4 : 2))
-k_step_cart(const CartInst m, int par)
+// 128-byte aligned start of the dynamic shared memory (the allocation has 128 bytes of
+// slack) and its shared-space address
+__device__ __forceinline__ unsigned char *aligned_smem(unsigned char *raw, uint32_t &sa)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t r = (uint32_t)__cvta_generic_to_shared(raw);
+    sa = (r + 127u) & ~127u;
+    return raw + (sa - r);
+}
+
+// Every thread waits for the barrier phase; false (for the whole CTA) if any thread
+// gave up, after the error flag is set and a late copy has had time to land.
+__device__ __forceinline__ bool cta_wait_staged(const CartInst &m, uint32_t bar, uint32_t parity)
+{
+    const bool ok = mbar_wait_bounded(bar, parity, TMA_WAIT_NS);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            if (m.err) atomicExch(m.err, 1);
+            mbar_wait_bounded(bar, parity, TMA_WAIT_NS);
+        }
+        return false;
+    }
+    return true;
+}
+
+// One block per CTA.  TMA: interior blocks are staged by two tensor copies (tf, tw: the
+// maps of buffer par) into boxes that overlay the face-flux arrays.
+template <int P, int TX, int TY, bool TMA>
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : (cart_threads<TX, TY>() <= 320 ? 4 : 2))
+k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tw)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     step_dependency_wait();
     const int ntx = (m.nx + TX - 1) / TX;
     const int tbx = blockIdx.x % ntx, tby = blockIdx.x / ntx;
-    if (cart_block_interior<TX, TY>(m, tbx, tby)) cart_tile<P, TX, TY, false, true>(m, par, tbx, tby, smem_raw);
-    else cart_tile<P, TX, TY, true, false>(m, par, tbx, tby, smem_raw);
+    if (cart_block_interior<TX, TY>(m, tbx, tby)) {
+        if constexpr (TMA) {
+            using B = CartTmaBox<P, TX, TY>;
+            uint32_t sa;
+            unsigned char *sm = aligned_smem(smem_raw, sa);
+            const uint32_t bar = sa + (uint32_t)B::BAR_OFF;
+            if (threadIdx.x == 0) mbar_init(bar);
+            __syncthreads();
+            if (threadIdx.x == 0)
+                tma_issue_block<P, TX, TY>(bar, sa + (uint32_t)B::F_OFF, sa + (uint32_t)B::W_OFF, &tf, &tw, tbx * TX, tby * TY);
+            if (!cta_wait_staged(m, bar, 0)) return;
+            cart_tile<P, TX, TY, false, true, true>(m, par, tbx, tby, sm,
+                                                    reinterpret_cast<const typename Store<P>::T *>(sm + B::F_OFF),
+                                                    reinterpret_cast<const double *>(sm + B::W_OFF));
+        } else {
+            cart_tile<P, TX, TY, false, true>(m, par, tbx, tby, smem_raw);
+        }
+    } else {
+        cart_tile<P, TX, TY, true, false>(m, par, tbx, tby, smem_raw);
+    }
+}
+
+template <int P, int TX, int TY, bool TMA> constexpr size_t cart_step_smem() {
+    return TMA ? CartTmaBox<P, TX, TY>::SMEM : cart_smem<P, TX, TY>();
 }
 
 // Batched: a fixed grid walks the (instance, block) work list; the item count is in
@@ -589,16 +730,33 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
 }
 
 template <int P, int TX, int TY> cudaError_t prepare_cart_p() {
-    return cudaFuncSetAttribute(k_step_cart<P, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)cart_smem<P, TX, TY>());
+    cudaError_t e = cudaFuncSetAttribute(k_step_cart<P, TX, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cart_step_smem<P, TX, TY, false>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step_cart<P, TX, TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cart_step_smem<P, TX, TY, true>());
+    return e;
 }
 
 template <int P, int TX, int TY>
-cudaError_t launch_cart_p(const CartInst &m, int par, cudaStream_t st)
+cudaError_t launch_cart_p(const CartInst &m, const CartTma *tma, int par, cudaStream_t st)
 {
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
-    return launch_step_kernel(k_step_cart<P, TX, TY>, dim3(ntx * nty), dim3(cart_threads<TX, TY>()),
-                              cart_smem<P, TX, TY>(), st, m, par);
+    if (tma)
+        return launch_step_kernel(k_step_cart<P, TX, TY, true>, dim3(ntx * nty), dim3(cart_threads<TX, TY>()),
+                                  cart_step_smem<P, TX, TY, true>(), st, m, par, tma->f[par], tma->W[par]);
+    static const CUtensorMap none{};
+    return launch_step_kernel(k_step_cart<P, TX, TY, false>, dim3(ntx * nty), dim3(cart_threads<TX, TY>()),
+                              cart_step_smem<P, TX, TY, false>(), st, m, par, none, none);
+}
+
+template <int P, int TX, int TY, bool TMA> int occ_cart_p()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_cart<P, TX, TY, TMA>, cart_threads<TX, TY>(),
+                                                      cart_step_smem<P, TX, TY, TMA>()) != cudaSuccess || n < 1)
+        return 1;
+    return n;
 }
 
 }  // namespace sdugks

@@ -22,6 +22,8 @@ _lib = None
 
 FP64, FP32, FP32_BF16DEV, FP32_FP16DEV = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_TILED, KERNEL_CARTESIAN = 0, 1, 2
+STAGING_LOADS, STAGING_TMA = 0, 1
+STAGINGS = {"loads": STAGING_LOADS, "tma": STAGING_TMA}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16dev": FP32_BF16DEV, "fp16dev": FP32_FP16DEV}
 ERRORS = {-1: "INVALID_ARG", -2: "INVALID_MESH", -3: "BAD_BC", -4: "OOM", -5: "DIVERGED", -6: "TIMEOUT",
           -7: "CUDA", -8: "STATE", -9: "FULL"}
@@ -36,14 +38,14 @@ class SdugksError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("tau", C.c_double), ("dt", C.c_double), ("precision", C.c_int32), ("kernel", C.c_int32),
-                ("tile_cells", C.c_int32), ("graph_steps", C.c_int32)]
+                ("tile_cells", C.c_int32), ("graph_steps", C.c_int32), ("staging", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_tiles", C.c_int64), ("halo_cells", C.c_int64),
                 ("steps_done", C.c_int64), ("device_bytes", C.c_int64), ("state_bytes_per_cell_step", C.c_double),
                 ("mesh_bytes_per_cell_step", C.c_double), ("kernel", C.c_int32), ("precision", C.c_int32),
-                ("tile_cells", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32)]
+                ("tile_cells", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("staging", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -170,13 +172,15 @@ class Mesh:
 
 class Solver:
     """sdugks_solver on the current CUDA device; ``stream`` is a torch.cuda.Stream,
-    a raw cudaStream_t integer, or None for the default stream."""
+    a raw cudaStream_t integer, or None for the default stream.  ``staging`` ("loads" or
+    "tma") picks how the Cartesian kernel stages its interior blocks."""
 
     def __init__(self, mesh: Mesh, tau: float, dt: float, precision="fp32", *, kernel=KERNEL_AUTO,
-                 tile_cells=0, graph_steps=0, stream=None):
+                 tile_cells=0, graph_steps=0, staging="loads", stream=None):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        self.params = Params(float(tau), float(dt), prec, int(kernel), int(tile_cells), int(graph_steps))
+        stg = STAGINGS[staging] if isinstance(staging, str) else int(staging)
+        self.params = Params(float(tau), float(dt), prec, int(kernel), int(tile_cells), int(graph_steps), stg)
         sh = getattr(stream, "cuda_stream", stream)
         self._h = C.c_void_p()
         _ck(L.sdugks_solver_create(mesh._h, C.byref(self.params), C.c_void_p(sh or 0), C.byref(self._h)),

@@ -85,6 +85,48 @@ def test_solver_create_validates_before_touching_the_device():
     assert e.value.name == "BAD_BC"
 
 
+def test_tma_staging_is_validated_on_the_host():
+    """TMA staging exists only in the Cartesian kernel; unknown values are rejected."""
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver.from_case(M.cylinder(32, 16), "fp32", staging="tma")
+    assert e.value.name == "INVALID_ARG" and "Cartesian" in str(e.value)
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver.from_case(M.cavity(48), "fp32", kernel=S.KERNEL_TILED, staging="tma")
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(S.SdugksError) as e:
+        S.Solver.from_case(M.cavity(48), "fp32", staging=7)
+    assert e.value.name == "INVALID_ARG"
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """The binding's Params and Info have the sizes and field offsets the C compiler
+    gives sdugks_params and sdugks_info."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    fields = {"sdugks_params": S.Params, "sdugks_info": S.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sdugks.h"', "int main(void) {"]
+    for cname, py in fields.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run([gcc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = []
+    for py in fields.values():
+        want.append(C.sizeof(py))
+        want += [getattr(py, f).offset for f, _ in py._fields_]
+    assert got == want
+
+
 def test_last_error_message_is_set():
     with pytest.raises(S.SdugksError) as e:
         S.Mesh(M.Mesh(np.zeros((0, 2)), np.zeros((0, 2), np.int64), np.zeros(0, np.int64),

@@ -365,3 +365,51 @@ def test_cartesian_block_shapes_agree(tile):
     assert rel_l2(u1, u0) <= 1e-5
     assert S.Solver.from_case(M.cavity(256), "fp32").info()["tile_cells"] == 224   # 304 blocks = 2 per SM
     assert S.Solver.from_case(M.cavity(1024), "fp32").info()["tile_cells"] == 128  # many waves: 4 blocks per SM
+
+
+def _periodic_channel_52x40():
+    """Periodic in x, walls below and above: interior blocks of both the 16x16 and the
+    16x8 Cartesian shapes exist (those are the blocks TMA staging covers)."""
+    mesh = M.cartesian(52, 40, 52.0, 40.0)
+    bcs = [(3, M.BC_PERIODIC, (1, 52.0, 0.0)), (1, M.BC_PERIODIC, (3, -52.0, 0.0)),
+           (0, M.BC_WALL, (0, 0, 0)), (2, M.BC_MOVING_WALL, (0.05, 0.0, 0.0))]
+    return M.Case("periodic_channel", mesh, bcs, tau=0.05, dt=0.25)
+
+
+@pytest.mark.parametrize("name", ["cavity_48", "periodic_channel_52x40"])
+def test_fp64_tma_staging_matches_oracle(name):
+    """TMA staging of the interior blocks (two tensor copies per block instead of
+    per-thread loads) keeps the FP64 step within 1e-12 of the oracle."""
+    S = _S()
+    if name == "cavity_48":
+        case, steps, rho, u = M.cavity(48, Re=400.0), 600, None, None
+    else:
+        case, steps = _periodic_channel_52x40(), 300
+        rho, u = _random_state(case, 21)
+    s, (f, W), st = run_both(case, steps, "fp64", rho, u, staging="tma")
+    assert s.info()["staging"] == S.STAGING_TMA and s.info()["kernel"] == S.KERNEL_CARTESIAN
+    assert relmax(f, st.f) <= 1e-12
+    assert relmax(W, st.W) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev", "fp16dev"])
+@pytest.mark.parametrize("tile", [256, 224, 128])
+def test_tma_staging_matches_loads(precision, tile):
+    """Both stagings feed the same values to the same arithmetic: after 150 steps the
+    state agrees to FP32 round-off (relative max 1e-6 on W and f) for every block
+    shape and storage."""
+    S = _S()
+    case = _periodic_channel_52x40()
+    rho, u = _random_state(case, 22)
+    out = []
+    for staging in ("loads", "tma"):
+        s = S.Solver.from_case(case, precision, tile_cells=tile, staging=staging).init(rho, u)
+        assert s.info()["staging"] == S.STAGINGS[staging]
+        s.step(150)
+        out.append(s.get_state())
+        eps, _ = s.residual()
+        assert np.isfinite(eps)
+    (f0, W0), (f1, W1) = out
+    assert relmax(W1, W0) <= 1e-6
+    assert relmax(f1, f0) <= 1e-6
+
