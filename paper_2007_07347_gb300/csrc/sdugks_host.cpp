@@ -804,6 +804,32 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         halos.push_back(std::move(h));
     }
     const int32_t nt = (int32_t)final_tiles.size();
+    // within a tile, cells along a Morton curve of their centroids (16 bits per axis over
+    // the tile's bounding box): faces, which are listed in the order of their cells,
+    // then read nearby local indices from one warp to the next lane
+    for (const auto &t : final_tiles) {
+        double mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+        for (size_t i = t.first; i < t.second; i++)
+            for (int d = 0; d < 2; d++) {
+                mn[d] = std::min(mn[d], m->xc[2 * ids[i] + d]);
+                mx[d] = std::max(mx[d], m->xc[2 * ids[i] + d]);
+            }
+        auto key = [&](int32_t c) {
+            uint32_t q[2];
+            for (int d = 0; d < 2; d++) {
+                const double w = mx[d] - mn[d];
+                const double u = w > 0 ? (m->xc[2 * c + d] - mn[d]) / w : 0.0;
+                q[d] = (uint32_t)std::min(65535.0, std::max(0.0, std::floor(u * 65536.0)));
+            }
+            uint64_t k = 0;
+            for (int b = 15; b >= 0; b--) k = (k << 2) | (((q[1] >> b) & 1u) << 1) | ((q[0] >> b) & 1u);
+            return k;
+        };
+        std::sort(ids.begin() + t.first, ids.begin() + t.second, [&](int32_t a, int32_t b) {
+            const uint64_t ka = key(a), kb = key(b);
+            return ka != kb ? ka < kb : a < b;
+        });
+    }
     // internal order: tiles in RCB order
     std::vector<int32_t> perm(n), iperm(n);
     {

@@ -102,6 +102,8 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     }
     // cells this thread stages (read-only halo ids: looked up before the wait as well)
     const int64_t gs0 = tid < n_int ? (int64_t)c0 + tid : (tid < n_loc ? (int64_t)m.halo[h0 + tid - n_int] : 0);
+    const int i1 = tid + TILED_THREADS;            // a second staged position (always a halo cell)
+    const int64_t gs1 = i1 < n_loc ? (int64_t)m.halo[h0 + i1 - n_int] : 0;
     step_dependency_wait();
     const R *sgd = static_cast<const R *>(m.sig_d);
     const R *sga = static_cast<const R *>(m.sig_ai);
@@ -113,7 +115,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int64_t g = c0 + tid;
     R fn[NQ];
     for (int i = tid; i < n_loc; i += TILED_THREADS) {
-        const int64_t gi = i == tid ? gs0 : (int64_t)m.halo[h0 + i - n_int];   // i > tid is always a halo cell
+        const int64_t gi = i == tid ? gs0 : (i == i1 ? gs1 : (int64_t)m.halo[h0 + i - n_int]);
         R fx[NQ], fe[NQ], fb[NQ];
         cell_fbp<P>(fin, Wn, gi, np, k, fx, fe, fb);
 #pragma unroll
