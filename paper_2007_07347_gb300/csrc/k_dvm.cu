@@ -14,7 +14,9 @@
 //   k_dvm_cell  per cell: F = sum of its faces' fluxes (Eq. MesoFlux), its moments
 //               (Eq. MacroFlux) update W in FP64 (Eq. MacroUpdate), then f (Eq. fn+1)
 // W = (rho, rho u, rho E) per cell in FP64; f and the scratch arrays in the compute
-// precision.  The Maxwellian is that of Eq. Feq with exponent |xi - u|^2 / (2 R T),
+// precision.  When Q is a multiple of 4 every thread takes 4 consecutive velocities at a
+// time with 16-byte vector loads and stores (V = 4); otherwise one (V = 1).  The
+// arithmetic of a velocity is the same either way.  The Maxwellian is that of Eq. Feq with exponent |xi - u|^2 / (2 R T),
 // D = 2, sampled at the nodes and multiplied by the node weights.
 #include "sdugks_internal.h"
 
@@ -52,10 +54,6 @@ __device__ __forceinline__ MaxP max_params(double rho, double mx, double my, dou
     p.inv2RT = 1.0 / (2.0 * RT);
     return p;
 }
-
-template <class R> struct V2;
-template <> struct V2<float> { using T = float2; };
-template <> struct V2<double> { using T = double2; };
 
 // exp(-x) for the Maxwellian: FP64 exp; FP32 2^(-x log2 e) by the hardware base-2
 // exponential (relative error below 2^-22), with log2 e folded into sp[3].
@@ -111,26 +109,78 @@ __device__ __forceinline__ void block_sum(R v[NV], double *scratch, double out[N
     __syncthreads();
 }
 
-// fbar+ of a cell's velocity q plus (r - xi dt) . sigma, sigma its LLSR gradient.
-// rows[0] is the cell's fbar+ row, rows[1..4] its neighbours' (a missing neighbour
-// repeats the cell's own row with a zero offset, which adds nothing).
-template <class R>
-__device__ __forceinline__ R reconstruct(const R *const *rows, const R *d, const R *ai, int q, R rx, R ry, R xx,
-                                         R xy, R dt)
+// V consecutive values (V = 4: 16-byte vector accesses; the address is 16-byte aligned
+// because rows start at multiples of Q values and Q is a multiple of 4).
+template <class R, int V> struct VIO;
+template <class R> struct VIO<R, 1> {
+    static __device__ __forceinline__ void ld(const R *p, R v[1]) { v[0] = *p; }
+    static __device__ __forceinline__ void st(R *p, const R v[1]) { *p = v[0]; }
+    static __device__ __forceinline__ void xi(const R *p, R x[1], R y[1]) { x[0] = p[0]; y[0] = p[1]; }
+};
+template <> struct VIO<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float v[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float v[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    // xi of 4 velocities: (x, y) pairs, 32 bytes
+    static __device__ __forceinline__ void xi(const float *p, float x[4], float y[4]) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+        x[0] = a.x; y[0] = a.y; x[1] = a.z; y[1] = a.w; x[2] = b.x; y[2] = b.y; x[3] = b.z; y[3] = b.w;
+    }
+};
+template <> struct VIO<double, 4> {
+    static __device__ __forceinline__ void ld(const double *p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double v[4]) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+    static __device__ __forceinline__ void xi(const double *p, double x[4], double y[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const double2 t = reinterpret_cast<const double2 *>(p)[j];
+            x[j] = t.x; y[j] = t.y;
+        }
+    }
+};
+
+// fbar+ of a cell's velocities q .. q+V-1 plus (r - xi dt) . sigma, sigma the cell's LLSR
+// gradient.  rows[0] is the cell's fbar+ row, rows[1..4] its neighbours' (a missing
+// neighbour repeats the cell's own row with a zero offset, which adds nothing); one
+// vector load per row.
+template <class R, int V>
+__device__ __forceinline__ void reconstruct_v(const R *const *rows, const R *d, const R *ai, int q, R rx, R ry,
+                                              const R *xx, const R *xy, R dt, R out[V])
 {
-    const R v0 = rows[0][q];
-    R bx = R(0), by = R(0);
+    R v0[V], bx[V], by[V];
+    VIO<R, V>::ld(rows[0] + q, v0);
+#pragma unroll
+    for (int j = 0; j < V; j++) { bx[j] = R(0); by[j] = R(0); }
 #pragma unroll
     for (int sl = 0; sl < MAXF; sl++) {
-        const R dv = rows[1 + sl][q] - v0;
-        bx += d[2 * sl] * dv;
-        by += d[2 * sl + 1] * dv;
+        R vn[V];
+        VIO<R, V>::ld(rows[1 + sl] + q, vn);
+        const R dx = d[2 * sl], dy = d[2 * sl + 1];
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            const R dv = vn[j] - v0[j];
+            bx[j] += dx * dv;
+            by[j] += dy * dv;
+        }
     }
-    const R sx = ai[0] * bx + ai[1] * by, sy = ai[1] * bx + ai[2] * by;
-    return v0 + (rx - xx * dt) * sx + (ry - xy * dt) * sy;
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        const R sx = ai[0] * bx[j] + ai[1] * by[j], sy = ai[1] * bx[j] + ai[2] * by[j];
+        out[j] = v0[j] + (rx - xx[j] * dt) * sx + (ry - xy[j] * dt) * sy;
+    }
 }
 
-template <class R>
+template <class R, int V>
 __global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
                                                          const double *__restrict__ W, R *__restrict__ fbp)
 {
@@ -141,14 +191,20 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const 
     if (threadIdx.x == 0) set_sp<R>(sp, max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]));
     __syncthreads();
     const DvmR<R> k(cf);
-    const typename V2<R>::T *xi = static_cast<const typename V2<R>::T *>(m.xi);
+    const R *xi = static_cast<const R *>(m.xi);
     const R *wq = static_cast<const R *>(m.wq);
     const R *fr = f + c * m.Q;
     R *out = fbp + c * m.Q;
 #pragma unroll 2
-    for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-        const typename V2<R>::T x = xi[q];
-        out[q] = k.a * fr[q] + k.b * maxwell<R>(sp, x.x, x.y, wq[q]);
+    for (int g = threadIdx.x; g < Q / V; g += DVM_THREADS) {
+        const int q = g * V;
+        R x[V], y[V], w[V], fv[V], o[V];
+        VIO<R, V>::xi(xi + 2 * q, x, y);
+        VIO<R, V>::ld(wq + q, w);
+        VIO<R, V>::ld(fr + q, fv);
+#pragma unroll
+        for (int j = 0; j < V; j++) o[j] = k.a * fv[j] + k.b * maxwell<R>(sp, x[j], y[j], w[j]);
+        VIO<R, V>::st(out + q, o);
     }
 }
 
@@ -176,8 +232,8 @@ __device__ __forceinline__ void load_side(SideData<R> &sd, const DvmMesh &m, con
 
 // SMEM: the interface distribution of the face between the two passes over the
 // velocities stays in shared memory (Q values); otherwise in the flux array itself.
-template <class R, bool SMEM>
-__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+template <class R, bool SMEM, int V>
+__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? (V == 1 ? 3 : 2) : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
     step_dependency_wait();
@@ -188,7 +244,7 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
     const int64_t fc = blockIdx.x;
     const int Q = (int)m.Q;
     const DvmR<R> k(cf);
-    const typename V2<R>::T *xi = static_cast<const typename V2<R>::T *>(m.xi);
+    const R *xi = static_cast<const R *>(m.xi);
     const R *wq = static_cast<const R *>(m.wq);
     const R *G = static_cast<const R *>(m.face_geo) + 6 * fc;
     const R nx = G[0], ny = G[1], rox = G[2], roy = G[3], rkx = G[4], rky = G[5];
@@ -205,28 +261,45 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
 
     if (interior) {
         R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
-        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-            const typename V2<R>::T xv = xi[q];
-            const R x = xv.x, y = xv.y;
-            const R s = x * nx + y * ny;
-            R fb;
-            if (s > k.tie) fb = reconstruct<R>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt);
-            else if (s < -k.tie) fb = reconstruct<R>(sd[1].rows, sd[1].d, sd[1].ai, q, rkx, rky, x, y, k.dt);
-            else fb = R(0.5) * (reconstruct<R>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt) +
-                                reconstruct<R>(sd[1].rows, sd[1].d, sd[1].ai, q, rkx, rky, x, y, k.dt));
-            fbuf[q] = fb;
-            p0 += fb; p1 += x * fb; p2 += y * fb; p3 += R(0.5) * (x * x + y * y) * fb;
+        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+            const int q = gi * V;
+            R x[V], y[V], s[V], fa[V], fo[V], fb[V];
+            VIO<R, V>::xi(xi + 2 * q, x, y);
+            bool needA = false, needB = false;        // some velocity takes the owner's / the neighbour's side
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                s[j] = x[j] * nx + y[j] * ny;
+                needA |= !(s[j] < -k.tie);
+                needB |= !(s[j] > k.tie);
+                fa[j] = R(0); fo[j] = R(0);
+            }
+            if (needA) reconstruct_v<R, V>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt, fa);
+            if (needB) reconstruct_v<R, V>(sd[1].rows, sd[1].d, sd[1].ai, q, rkx, rky, x, y, k.dt, fo);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                fb[j] = s[j] > k.tie ? fa[j] : (s[j] < -k.tie ? fo[j] : R(0.5) * (fa[j] + fo[j]));
+                p0 += fb[j]; p1 += x[j] * fb[j]; p2 += y[j] * fb[j]; p3 += R(0.5) * (x[j] * x[j] + y[j] * y[j]) * fb[j];
+            }
+            VIO<R, V>::st(fbuf + q, fb);
         }
         R part[4] = {p0, p1, p2, p3};
         double Wb[4];
         block_sum<4, R>(part, red, Wb);
         if (threadIdx.x == 0) set_sp<R>(sp, max_params(Wb[0], Wb[1], Wb[2], Wb[3]));
         __syncthreads();
-        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-            const typename V2<R>::T xv = xi[q];
-            const R s = xv.x * nx + xv.y * ny;
-            const R g = maxwell<R>(sp, xv.x, xv.y, wq[q]);
-            out[q] = s * ((fbuf[q] + k.b * g) * k.c);
+        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+            const int q = gi * V;
+            R x[V], y[V], w[V], fb[V], o[V];
+            VIO<R, V>::xi(xi + 2 * q, x, y);
+            VIO<R, V>::ld(wq + q, w);
+            VIO<R, V>::ld(fbuf + q, fb);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                const R s = x[j] * nx + y[j] * ny;
+                const R g = maxwell<R>(sp, x[j], y[j], w[j]);
+                o[j] = s * ((fb[j] + k.b * g) * k.c);
+            }
+            VIO<R, V>::st(out + q, o);
         }
     } else {
         // diffuse wall (Sec. III): entering velocities take rho_w g(u_w, R T_w), leaving
@@ -241,38 +314,57 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
             set_sp<R>(sp, pw);
         }
         __syncthreads();
-        R so = R(0), go = R(0), gi = R(0);
-        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-            const typename V2<R>::T xv = xi[q];
-            const R x = xv.x, y = xv.y;
-            const R s = x * nx + y * ny;
-            const R g = maxwell<R>(sp, x, y, wq[q]);
-            if (s < -k.tie) {
-                gi += s * g;
-            } else {
-                const R fb = reconstruct<R>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt);
-                fbuf[q] = fb;
-                so += s * fb;
-                go += s * g;
+        R so = R(0), go = R(0), gin = R(0);
+        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+            const int q = gi * V;
+            R x[V], y[V], w[V], s[V], fb[V];
+            VIO<R, V>::xi(xi + 2 * q, x, y);
+            VIO<R, V>::ld(wq + q, w);
+            bool leaving = false;                     // some velocity leaves the fluid through the wall
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                s[j] = x[j] * nx + y[j] * ny;
+                leaving |= !(s[j] < -k.tie);
+                fb[j] = R(0);
             }
+            if (leaving) reconstruct_v<R, V>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt, fb);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                const R g = maxwell<R>(sp, x[j], y[j], w[j]);
+                if (s[j] < -k.tie) {
+                    gin += s[j] * g;
+                } else {
+                    so += s[j] * fb[j];
+                    go += s[j] * g;
+                }
+            }
+            if (leaving) VIO<R, V>::st(fbuf + q, fb);
         }
-        R part[3] = {so, go, gi};
+        R part[3] = {so, go, gin};
         double tot[3];
         block_sum<3, R>(part, red, tot);
         const double rho_w = -double(k.c) * tot[0] / (double(k.c) * double(k.b) * tot[1] + tot[2]);
         const R rw = R(rho_w);
-        for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-            const typename V2<R>::T xv = xi[q];
-            const R s = xv.x * nx + xv.y * ny;
-            const R g = maxwell<R>(sp, xv.x, xv.y, wq[q]);
-            out[q] = s < -k.tie ? s * (rw * g) : s * ((fbuf[q] + k.b * (rw * g)) * k.c);
+        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+            const int q = gi * V;
+            R x[V], y[V], w[V], fb[V], o[V];
+            VIO<R, V>::xi(xi + 2 * q, x, y);
+            VIO<R, V>::ld(wq + q, w);
+            VIO<R, V>::ld(fbuf + q, fb);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                const R s = x[j] * nx + y[j] * ny;
+                const R g = maxwell<R>(sp, x[j], y[j], w[j]);
+                o[j] = s < -k.tie ? s * (rw * g) : s * ((fb[j] + k.b * (rw * g)) * k.c);
+            }
+            VIO<R, V>::st(out + q, o);
         }
     }
 }
 
 // SMEM: the cell's flux sum F (Q values) is kept in shared memory between the two
 // passes; otherwise it is summed again from the face fluxes.
-template <class R, bool SMEM>
+template <class R, bool SMEM, int V>
 __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
                                                           double *__restrict__ W, const R *__restrict__ flux)
 {
@@ -286,7 +378,7 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
     const int64_t c = blockIdx.x;
     const int Q = (int)m.Q;
     const DvmR<R> k(cf);
-    const typename V2<R>::T *xi = static_cast<const typename V2<R>::T *>(m.xi);
+    const R *xi = static_cast<const R *>(m.xi);
     const R *wq = static_cast<const R *>(m.wq);
     if (threadIdx.x < MAXF) {
         // the cell's faces in slot order: flux row and sign (a missing slot adds 0 x row 0)
@@ -297,20 +389,29 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
         fsg[threadIdx.x] = v < 0 ? R(0) : ((v & DVM_SECOND) ? R(-1) : R(1));
     }
     __syncthreads();
-    auto F_of = [&](int q) {
-        R F = R(0);
+    auto F_of = [&](int q, R F[V]) {
 #pragma unroll
-        for (int sl = 0; sl < MAXF; sl++) F += fsg[sl] * frow[sl][q];
-        return F;
+        for (int j = 0; j < V; j++) F[j] = R(0);
+#pragma unroll
+        for (int sl = 0; sl < MAXF; sl++) {
+            R r[V];
+            VIO<R, V>::ld(frow[sl] + q, r);
+#pragma unroll
+            for (int j = 0; j < V; j++) F[j] += fsg[sl] * r[j];
+        }
     };
     R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
 #pragma unroll 2
-    for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-        const typename V2<R>::T xv = xi[q];
-        const R x = xv.x, y = xv.y;
-        const R F = F_of(q);
-        if (SMEM) Fbuf[q] = F;
-        p0 += F; p1 += x * F; p2 += y * F; p3 += R(0.5) * (x * x + y * y) * F;
+    for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+        const int q = gi * V;
+        R x[V], y[V], F[V];
+        VIO<R, V>::xi(xi + 2 * q, x, y);
+        F_of(q, F);
+        if (SMEM) VIO<R, V>::st(Fbuf + q, F);
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            p0 += F[j]; p1 += x[j] * F[j]; p2 += y[j] * F[j]; p3 += R(0.5) * (x[j] * x[j] + y[j] * y[j]) * F[j];
+        }
     }
     R part[4] = {p0, p1, p2, p3};
     double M[4];
@@ -328,12 +429,21 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
     const R rdtv = R(dtv);
     R *fr = f + c * m.Q;
 #pragma unroll 2
-    for (int q = threadIdx.x; q < Q; q += DVM_THREADS) {
-        const typename V2<R>::T xv = xi[q];
-        const R F = SMEM ? Fbuf[q] : F_of(q);
-        const R fe = maxwell<R>(sp, xv.x, xv.y, wq[q]);
-        const R num = fr[q] - rdtv * F + k.r * fe;
-        fr[q] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
+    for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+        const int q = gi * V;
+        R x[V], y[V], w[V], F[V], fv[V];
+        VIO<R, V>::xi(xi + 2 * q, x, y);
+        VIO<R, V>::ld(wq + q, w);
+        VIO<R, V>::ld(fr + q, fv);
+        if (SMEM) VIO<R, V>::ld(Fbuf + q, F);
+        else F_of(q, F);
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            const R fe = maxwell<R>(sp, x[j], y[j], w[j]);
+            const R num = fv[j] - rdtv * F[j] + k.r * fe;
+            fv[j] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
+        }
+        VIO<R, V>::st(fr + q, fv);
     }
 }
 
@@ -355,20 +465,43 @@ constexpr size_t DVM_SMEM_MAX = 160 * 1024;
 
 template <class R> bool dvm_use_smem(int64_t Q) { return (size_t)Q * sizeof(R) <= DVM_SMEM_MAX; }
 
-template <class R>
-cudaError_t prepare_p(int64_t Q)
+template <class R, int V>
+cudaError_t prepare_pv(int64_t Q)
 {
     if (!dvm_use_smem<R>(Q)) return cudaSuccess;
     const int bytes = (int)((size_t)Q * sizeof(R));
-    cudaError_t e = cudaFuncSetAttribute(k_dvm_face<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_dvm_face<R, true, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dvm_cell<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(k_dvm_cell<R, true, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dvm_face<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_dvm_face<R, true, V>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dvm_cell<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_dvm_cell<R, true, V>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <class R> cudaError_t prepare_p(int64_t Q) { return Q % 4 == 0 ? prepare_pv<R, 4>(Q) : prepare_pv<R, 1>(Q); }
+
+template <class R, int V>
+cudaError_t step_pv(const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp, void *flux,
+                    cudaStream_t st)
+{
+    const dim3 cells((unsigned)m.nc), faces((unsigned)m.nf), blk(DVM_THREADS);
+    const R *cf = static_cast<const R *>(f);
+    R *pf = static_cast<R *>(f), *pfbp = static_cast<R *>(fbp), *pflux = static_cast<R *>(flux);
+    const R *cfbp = pfbp, *cflux = pflux;
+    cudaError_t e = launch_step_kernel(k_dvm_fbp<R, V>, cells, blk, 0, st, m, c, cf, (const double *)W, pfbp);
+    if (e != cudaSuccess) return e;
+    if (dvm_use_smem<R>(m.Q)) {
+        const size_t bytes = (size_t)m.Q * sizeof(R);
+        e = launch_step_kernel(k_dvm_face<R, true, V>, faces, blk, bytes, st, m, c, RTw, cfbp, pflux);
+        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, true, V>, cells, blk, bytes, st, m, c, pf, W, cflux);
+    } else {
+        e = launch_step_kernel(k_dvm_face<R, false, V>, faces, blk, 0, st, m, c, RTw, cfbp, pflux);
+        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, false, V>, cells, blk, 0, st, m, c, pf, W, cflux);
+    }
     return e;
 }
 
@@ -377,21 +510,7 @@ cudaError_t step_p(const DvmMesh &m, const Coefs &c, double RTw, void *f, double
                    cudaStream_t st)
 {
     if (m.nc <= 0) return cudaSuccess;
-    const dim3 cells((unsigned)m.nc), faces((unsigned)m.nf), blk(DVM_THREADS);
-    const R *cf = static_cast<const R *>(f);
-    R *pf = static_cast<R *>(f), *pfbp = static_cast<R *>(fbp), *pflux = static_cast<R *>(flux);
-    const R *cfbp = pfbp, *cflux = pflux;
-    cudaError_t e = launch_step_kernel(k_dvm_fbp<R>, cells, blk, 0, st, m, c, cf, (const double *)W, pfbp);
-    if (e != cudaSuccess) return e;
-    if (dvm_use_smem<R>(m.Q)) {
-        const size_t bytes = (size_t)m.Q * sizeof(R);
-        e = launch_step_kernel(k_dvm_face<R, true>, faces, blk, bytes, st, m, c, RTw, cfbp, pflux);
-        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, true>, cells, blk, bytes, st, m, c, pf, W, cflux);
-    } else {
-        e = launch_step_kernel(k_dvm_face<R, false>, faces, blk, 0, st, m, c, RTw, cfbp, pflux);
-        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, false>, cells, blk, 0, st, m, c, pf, W, cflux);
-    }
-    return e;
+    return m.Q % 4 == 0 ? step_pv<R, 4>(m, c, RTw, f, W, fbp, flux, st) : step_pv<R, 1>(m, c, RTw, f, W, fbp, flux, st);
 }
 
 }  // namespace

@@ -59,6 +59,17 @@ def test_fp64_cavity_matches_oracle(tau):
     assert np.abs(st.u).max() > 1e-3
 
 
+@pytest.mark.parametrize("nv", [9, 11])
+def test_fp64_odd_velocity_grid_matches_oracle(nv):
+    """Q = nv^2 not a multiple of 4: the kernels take one velocity per thread at a time
+    (even grids use 16-byte vectors of 4)."""
+    m, bcs = _cavity_jittered(5)
+    d, st = _run(m, bcs, nv, 2.0, 0.5, 0.1, 0.01, 40, "fp64")
+    f, W = d.get_state()
+    assert relmax(f, st.f) <= 1e-12
+    assert relmax(W, st.W) <= 1e-12
+
+
 def test_fp64_periodic_hybrid_channel_matches_oracle():
     m, bcs = _channel()
     rng = np.random.default_rng(3)
