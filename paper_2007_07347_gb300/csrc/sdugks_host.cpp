@@ -911,6 +911,13 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
             };
             for (int32_t i = 0; i < nint; i++) push_sig(c0 + i);
             for (int32_t c : r1) push_sig(c);
+            // pad the tile's rows to a multiple of 4 so that every tile's gradient data
+            // starts 16-byte aligned (the kernel copies it in 16-byte pieces)
+            const int32_t nsig_t = nint + (int32_t)r1.size(), npad_t = (nsig_t + 3) / 4 * 4;
+            for (int32_t q = nsig_t; q < npad_t; q++) {
+                for (int sl = 0; sl < MAXF; sl++) sig_nb.push_back(NO_LOCAL);
+                sig_cell.push_back(-1);
+            }
             // local faces, in order of first appearance over the tile's cells and slots;
             // oriented from the merged face's owner to its neighbour (or boundary)
             tile_f0[t] = (int32_t)lf_ab.size();
@@ -935,7 +942,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
             }
             c0 += nint;
             hoff += (int32_t)(r1.size() + r2.size());
-            soff += nint + (int32_t)r1.size();
+            soff += (nint + (int32_t)r1.size() + 3) / 4 * 4;
             halo_total += (int64_t)(r1.size() + r2.size());
             sig_total += nint + (int64_t)r1.size();
         }
@@ -947,7 +954,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         const int32_t nint = tile_c0[t + 1] - tile_c0[t];
         const int32_t nloc = nint + (tile_h0[t + 1] - tile_h0[t]);
         const int32_t nsig = nint + tile_nh1[t];
-        if (nint < 1 || nint > TILE_MAX || nloc > LOC_MAX || nsig > SIG_MAX || tile_s0[t + 1] - tile_s0[t] != nsig)
+        if (nint < 1 || nint > TILE_MAX || nloc > LOC_MAX || nsig > SIG_MAX || tile_s0[t] % 4 != 0 ||
+            tile_s0[t + 1] - tile_s0[t] != (nsig + 3) / 4 * 4)
             return fail(SDUGKS_ERR_INVALID_MESH, "internal: tile %d sizes out of range", t);
         for (int32_t q = tile_h0[t]; q < tile_h0[t + 1]; q++)
             if (halo[q] < 0 || halo[q] >= n) return fail(SDUGKS_ERR_INVALID_MESH, "internal: halo id out of range");
@@ -1072,6 +1080,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     {
         const std::vector<char> gainv = conv(iainv);
         for (size_t r = 0; r < nrow; r++) {
+            if (sig_cell[r] < 0) continue;             // padding row: zeros
             const size_t i = (size_t)sig_cell[r];
             for (int k = 0; k < 2 * MAXF; k++)
                 std::memcpy(&gsd[((size_t)k * nrow + r) * rs], &isld[((size_t)k * npad + i) * rs], rs);

@@ -59,7 +59,7 @@ struct TiledMesh {
     const int32_t *tile_c0;   // [n_tiles+1] interior cell range of each tile
     const int32_t *tile_h0;   // [n_tiles+1] range into halo
     const int32_t *tile_nh1;  // [n_tiles]   cells of ring 1 (first in the tile's halo)
-    const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb
+    const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb (each tile's rows padded to a multiple of 4)
     const int32_t *tile_f0;   // [n_tiles+1] range of local faces
     const int32_t *halo;      // internal ids of ring 1 then ring 2 of each tile
     int64_t n_sig;            // gradient rows of all tiles (stride of sig_d and sig_ai)

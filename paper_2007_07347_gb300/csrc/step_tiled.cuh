@@ -24,6 +24,10 @@
 
 namespace sdugks {
 
+// shared region of the face fluxes, which first holds the tile's gradient data
+constexpr int TILED_FLUX_REGION = NQ * LF_MAX > (2 * MAXF + 3) * SIG_MAX ? NQ * LF_MAX : (2 * MAXF + 3) * SIG_MAX;
+static_assert(SIG_MAX % 4 == 0 && (NQ * LOC_MAX + 2 * NQ * SIG_MAX) % 4 == 0, "16-byte aligned gradient planes");
+
 template <class R> struct CoefR;
 template <> struct CoefR<double> {
     double a, b, c, r, dt, tie;
@@ -44,8 +48,15 @@ template <int B> __device__ __forceinline__ void cp_async(void *smem, const void
     if (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
     else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// all committed groups but the most recent one
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int P>
 __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict__ fin, const double *__restrict__ Wn,
@@ -74,8 +85,10 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_fbp = reinterpret_cast<R *>(smem_raw);     // [NQ][LOC_MAX]
     R *s_sig = s_fbp + NQ * LOC_MAX;                 // [2 NQ][SIG_MAX]
-    R *s_flux = s_sig + 2 * NQ * SIG_MAX;            // [NQ][LF_MAX]
-    R *s_geo = s_flux + NQ * LF_MAX;                 // [6][LF_MAX] face geometry of the tile
+    R *s_flux = s_sig + 2 * NQ * SIG_MAX;            // [NQ][LF_MAX]; before phase 3:
+    R *s_sd = s_flux;                                //   [2 MAXF][SIG_MAX] gradient offsets of the rows
+    R *s_sa = s_flux + 2 * MAXF * SIG_MAX;           //   [3][SIG_MAX] LLSR inverses
+    R *s_geo = s_flux + TILED_FLUX_REGION;           // [6][LF_MAX] face geometry of the tile
     uint32_t *s_lfab = reinterpret_cast<uint32_t *>(s_geo + 6 * LF_MAX);   // [LF_MAX] face sides
 
     const int t = blockIdx.x, tid = threadIdx.x;
@@ -89,8 +102,21 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int n_lf = m.tile_f0[t + 1] - f0;
     const int64_t np = m.npad, nlf = m.n_lf;
     const CoefR<R> k(c);
-    // the tile's face list (read-only mesh data) travels to shared memory while the
-    // previous step finishes and the cells are staged
+    // the gradient data of the tile's rows (read-only mesh data, needed in phase 2) travels
+    // to shared memory while the previous step finishes: 16-byte pieces of each of the 11
+    // planes (tile_s0 and the plane stride are multiples of 4 rows)
+    {
+        constexpr int E = 16 / (int)sizeof(R);
+        const int nch = (n_sig + E - 1) / E;
+        const R *sgd = static_cast<const R *>(m.sig_d), *sga = static_cast<const R *>(m.sig_ai);
+        for (int u = tid; u < (2 * MAXF + 3) * nch; u += TILED_THREADS) {
+            const int pl = u / nch, j = u - pl * nch;
+            const R *src = pl < 2 * MAXF ? sgd + pl * m.n_sig : sga + (pl - 2 * MAXF) * m.n_sig;
+            cp_async16(&s_sd[pl * SIG_MAX + j * E], src + s0 + j * E);
+        }
+        cp_async_commit();
+    }
+    // then the tile's face list (needed in phase 3)
     {
         const R *gsrc = static_cast<const R *>(m.lf_geo);
         for (int j = tid; j < n_lf; j += TILED_THREADS) {
@@ -100,14 +126,14 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         }
         cp_async_commit();
     }
+    // the first gradient row's neighbour list
+    uint2 nb0 = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+    if (tid < n_sig) nb0 = *reinterpret_cast<const uint2 *>(m.sig_nb + (int64_t)(s0 + tid) * MAXF);
     // cells this thread stages (read-only halo ids: looked up before the wait as well)
     const int64_t gs0 = tid < n_int ? (int64_t)c0 + tid : (tid < n_loc ? (int64_t)m.halo[h0 + tid - n_int] : 0);
     const int i1 = tid + TILED_THREADS;            // a second staged position (always a halo cell)
     const int64_t gs1 = i1 < n_loc ? (int64_t)m.halo[h0 + i1 - n_int] : 0;
     step_dependency_wait();
-    const R *sgd = static_cast<const R *>(m.sig_d);
-    const R *sga = static_cast<const R *>(m.sig_ai);
-    const int64_t nrow = m.n_sig;
 
     // ---- phase 1: fbar+ of the tile's cells and both halo rings; a thread keeps f^n of
     // its own cell (cell tid) in registers for the update
@@ -125,11 +151,14 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
             for (int a = 0; a < NQ; a++) fn[a] = fx[a];
         }
     }
+    cp_async_wait_prior();      // the gradient data has arrived (the face list may be in flight)
     __syncthreads();
 
     // ---- phase 2: LLSR gradient sigma = A^{-1} sum_k d_k (fbar+_k - fbar+_j), d = x_k - x_j
     for (int i = tid; i < n_sig; i += TILED_THREADS) {
-        const uint16_t *nb = m.sig_nb + (int64_t)(s0 + i) * MAXF;
+        const uint2 nbv = i == tid ? nb0 : *reinterpret_cast<const uint2 *>(m.sig_nb + (int64_t)(s0 + i) * MAXF);
+        const uint16_t nb[MAXF] = {(uint16_t)(nbv.x & 0xFFFFu), (uint16_t)(nbv.x >> 16), (uint16_t)(nbv.y & 0xFFFFu),
+                                   (uint16_t)(nbv.y >> 16)};
         R bx[NQ], by[NQ];
 #pragma unroll
         for (int a = 0; a < NQ; a++) { bx[a] = R(0); by[a] = R(0); }
@@ -137,7 +166,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         for (int sl = 0; sl < MAXF; sl++) {
             const int kk = nb[sl];
             if (kk == NO_LOCAL) continue;
-            const R dx = sgd[(2 * sl) * nrow + s0 + i], dy = sgd[(2 * sl + 1) * nrow + s0 + i];
+            const R dx = s_sd[(2 * sl) * SIG_MAX + i], dy = s_sd[(2 * sl + 1) * SIG_MAX + i];
             if (kk < SYM_X) {
 #pragma unroll
                 for (int a = 0; a < NQ; a++) {
@@ -156,7 +185,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 }
             }
         }
-        const R axx = sga[s0 + i], axy = sga[nrow + s0 + i], ayy = sga[2 * nrow + s0 + i];
+        const R axx = s_sa[i], axy = s_sa[SIG_MAX + i], ayy = s_sa[2 * SIG_MAX + i];
 #pragma unroll
         for (int a = 0; a < NQ; a++) {
             s_sig[(2 * a) * SIG_MAX + i] = axx * bx[a] + axy * by[a];
@@ -330,7 +359,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 }
 
 template <int P> constexpr size_t tiled_smem() {
-    return sizeof(typename Store<P>::R) * (size_t)(NQ * LOC_MAX + 2 * NQ * SIG_MAX + NQ * LF_MAX + 6 * LF_MAX) +
+    return sizeof(typename Store<P>::R) * (size_t)(NQ * LOC_MAX + 2 * NQ * SIG_MAX + TILED_FLUX_REGION + 6 * LF_MAX) +
            sizeof(uint32_t) * LF_MAX;
 }
 
