@@ -180,6 +180,36 @@ __device__ __forceinline__ void reconstruct_v(const R *const *rows, const R *d, 
     }
 }
 
+// FP32, four velocities: the same operations two velocities at a time by paired FP32
+// instructions (FFMA2/FMUL2, each lane rounded as the scalar operation; differences as
+// FFMA2 with -1).
+template <>
+__device__ __forceinline__ void reconstruct_v<float, 4>(const float *const *rows, const float *d, const float *ai, int q,
+                                                        float rx, float ry, const float *xx, const float *xy, float dt,
+                                                        float out[4])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(rows[0] + q);
+    const float2 v01 = make_float2(a.x, a.y), v23 = make_float2(a.z, a.w), m1 = make_float2(-1.0f, -1.0f);
+    float2 bx01 = make_float2(0.f, 0.f), bx23 = bx01, by01 = bx01, by23 = bx01;
+#pragma unroll
+    for (int sl = 0; sl < MAXF; sl++) {
+        const float4 b = *reinterpret_cast<const float4 *>(rows[1 + sl] + q);
+        const float2 dx = make_float2(d[2 * sl], d[2 * sl]), dy = make_float2(d[2 * sl + 1], d[2 * sl + 1]);
+        const float2 dv01 = __ffma2_rn(v01, m1, make_float2(b.x, b.y)), dv23 = __ffma2_rn(v23, m1, make_float2(b.z, b.w));
+        bx01 = __ffma2_rn(dx, dv01, bx01); bx23 = __ffma2_rn(dx, dv23, bx23);
+        by01 = __ffma2_rn(dy, dv01, by01); by23 = __ffma2_rn(dy, dv23, by23);
+    }
+    const float2 a0 = make_float2(ai[0], ai[0]), a1 = make_float2(ai[1], ai[1]), a2 = make_float2(ai[2], ai[2]);
+    const float2 mdt = make_float2(-dt, -dt), rx2 = make_float2(rx, rx), ry2 = make_float2(ry, ry);
+    const float2 sx01 = __ffma2_rn(a1, by01, __fmul2_rn(a0, bx01)), sx23 = __ffma2_rn(a1, by23, __fmul2_rn(a0, bx23));
+    const float2 sy01 = __ffma2_rn(a2, by01, __fmul2_rn(a1, bx01)), sy23 = __ffma2_rn(a2, by23, __fmul2_rn(a1, bx23));
+    const float2 ex01 = __ffma2_rn(make_float2(xx[0], xx[1]), mdt, rx2), ex23 = __ffma2_rn(make_float2(xx[2], xx[3]), mdt, rx2);
+    const float2 ey01 = __ffma2_rn(make_float2(xy[0], xy[1]), mdt, ry2), ey23 = __ffma2_rn(make_float2(xy[2], xy[3]), mdt, ry2);
+    const float2 o01 = __ffma2_rn(ey01, sy01, __ffma2_rn(ex01, sx01, v01));
+    const float2 o23 = __ffma2_rn(ey23, sy23, __ffma2_rn(ex23, sx23, v23));
+    out[0] = o01.x; out[1] = o01.y; out[2] = o23.x; out[3] = o23.y;
+}
+
 template <class R, int V>
 __global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
                                                          const double *__restrict__ W, R *__restrict__ fbp)
@@ -233,7 +263,7 @@ __device__ __forceinline__ void load_side(SideData<R> &sd, const DvmMesh &m, con
 // SMEM: the interface distribution of the face between the two passes over the
 // velocities stays in shared memory (Q values); otherwise in the flux array itself.
 template <class R, bool SMEM, int V>
-__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? (V == 1 ? 3 : 2) : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
     step_dependency_wait();

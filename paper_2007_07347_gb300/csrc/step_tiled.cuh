@@ -197,10 +197,12 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     // inputs of the cell update, loaded now so that they arrive during the face phase
     uint16_t my_lf[MAXF] = {LF_NONE, LF_NONE, LF_NONE, LF_NONE};
     R dtv = R(0);
+    double w0n = 0.0, w1n = 0.0, w2n = 0.0;
     if (active) {
 #pragma unroll
         for (int sl = 0; sl < MAXF; sl++) my_lf[sl] = m.cell_lf[sl * np + g];
         dtv = static_cast<const R *>(m.dtV)[g];
+        w0n = Wn[g]; w1n = Wn[np + g]; w2n = Wn[2 * np + g];
     }
 
     // ---- phase 3: every local face once; flux s f_b from the first side to the second
@@ -327,7 +329,6 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     }
 
     // ---- macroscopic flux (moments of F) -> W^{n+1} in FP64; cell update f^{n+1} (Eq. fn+1)
-    const double w0n = Wn[g], w1n = Wn[np + g], w2n = Wn[2 * np + g];
     R M0 = R(0), M1 = R(0), M2 = R(0);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
