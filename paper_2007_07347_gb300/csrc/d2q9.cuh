@@ -52,7 +52,14 @@ template <class R> __device__ __forceinline__ void feq9(R rho, R ux, R uy, R out
 // (opposite velocities share w rho [1 - 1.5 |u|^2 + 4.5 (xi.u)^2] and differ in the
 // sign of 3 w rho xi.u).  Used by the hot kernels.
 template <class R> __device__ __forceinline__ R recip(R x) { return R(1) / x; }
-template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+// FP32: the hardware reciprocal (rcp.approx, at most 1 ulp from 1/x; subnormals flush
+// to zero, which the densities here never are)
+template <> __device__ __forceinline__ float recip<float>(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R out[NQ]) {
     const R base = rho - R(1.5) * rho * (ux * ux + uy * uy);
@@ -102,8 +109,8 @@ template <> __device__ __forceinline__ void feq9f<float>(float rho, float ux, fl
     }
 }
 
-// (u_x, u_y) from rho, rho u in the compute precision (FP32: one correctly rounded
-// reciprocal; FP64: two IEEE divisions).
+// (u_x, u_y) from rho, rho u in the compute precision (FP32: one hardware reciprocal;
+// FP64: two IEEE divisions).
 template <class R> __device__ __forceinline__ void vel_of(R rho, R m1, R m2, R &ux, R &uy) {
     const R inv = recip<R>(rho);
     ux = m1 * inv;

@@ -529,8 +529,8 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     __syncthreads();
 
     // ---- phase 2: every interior face of the block once, one per thread.  Faces of
-    // constant x: slot s < 32 WX is the face left of block cell (s % 16, row of s); the
-    // free upper half of the last constant-y warp takes the TY faces on the right edge.
+    // constant x: slot s < 32 WX is the face left of block cell (s % 16, row of s); the TY
+    // faces on the right edge take slots 32 WX + row.
     // A constant-x face between block columns fi-1 (L) and fi (R) in row fj:
     auto x_face = [&](int fi, int fj, int slot) {
         if (has_x(x0 + fi - 1) && has_x(x0 + fi) && has_y(y0 + fj)) {
@@ -542,8 +542,13 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             for (int r = 0; r < 6; r++) s_fx[r * S::NSX + slot] = fl[r];
         }
     };
+    // where the right-edge faces go: when TY = 2 (mod 4) the upper half of constant-x
+    // warp WX - 2 holds no row, and they run there with the same code as the rest of the
+    // warp; otherwise in the free upper half of the last constant-y warp
+    constexpr bool EDGE_IN_X = TY % 4 == 2;
     if (tid < 32 * S::WX) {
         if (tj < TY) x_face(ti, tj, tid);
+        else if (EDGE_IN_X && (tid >> 5) == S::WX - 2 && ti < TY) x_face(TX, ti, 32 * S::WX + ti);
     } else if (tid < 32 * (S::WX + S::WY)) {
         // face of constant y between block rows fj-1 (below) and fj (above), column fi
         const int qq = tid - 32 * S::WX, fi = qq & 15, fj = slot_row(qq);
@@ -556,7 +561,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 #pragma unroll
                 for (int r = 0; r < 6; r++) s_fy[r * S::NSY + qq] = fl[r];
             }
-        } else if ((qq >> 5) == S::WY - 1 && fi < TY) {
+        } else if (!EDGE_IN_X && (qq >> 5) == S::WY - 1 && fi < TY) {
             x_face(TX, fi, 32 * S::WX + fi);           // right edge of the block, row fi
         }
     }
