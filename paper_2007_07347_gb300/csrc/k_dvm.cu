@@ -25,6 +25,12 @@
 namespace sdugks {
 namespace {
 
+// threads per CTA of the three step kernels (a CTA walks its cell's or face's
+// velocities).  On the 40 x 40 x 100^2 micro cavity (GB300) 384 or 512 threads for the
+// cell kernel, 512 or 1024 for fbar+ and 384 for the face kernel measured the same or
+// slower than 256.
+constexpr int FBP_THREADS = 256, FACE_THREADS = 256, CELL_THREADS = 256;
+
 template <class R> struct DvmR;
 template <> struct DvmR<double> {
     double a, b, c, r, dt, tie, inv1r;
@@ -211,7 +217,7 @@ __device__ __forceinline__ void reconstruct_v<float, 4>(const float *const *rows
 }
 
 template <class R, int V>
-__global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
+__global__ void __launch_bounds__(FBP_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
                                                          const double *__restrict__ W, R *__restrict__ fbp)
 {
     step_dependency_wait();
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_fbp(const DvmMesh m, const 
     const R *fr = f + c * m.Q;
     R *out = fbp + c * m.Q;
 #pragma unroll 2
-    for (int g = threadIdx.x; g < Q / V; g += DVM_THREADS) {
+    for (int g = threadIdx.x; g < Q / V; g += FBP_THREADS) {
         const int q = g * V;
         R x[V], y[V], w[V], fv[V], o[V];
         VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -263,7 +269,7 @@ __device__ __forceinline__ void load_side(SideData<R> &sd, const DvmMesh &m, con
 // SMEM: the interface distribution of the face between the two passes over the
 // velocities stays in shared memory (Q values); otherwise in the flux array itself.
 template <class R, bool SMEM, int V>
-__global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+__global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
     step_dependency_wait();
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
 
     if (interior) {
         R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
-        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
             const int q = gi * V;
             R x[V], y[V], s[V], fa[V], fo[V], fb[V];
             VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
         block_sum<4, R>(part, red, Wb);
         if (threadIdx.x == 0) set_sp<R>(sp, max_params(Wb[0], Wb[1], Wb[2], Wb[3]));
         __syncthreads();
-        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
             const int q = gi * V;
             R x[V], y[V], w[V], fb[V], o[V];
             VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
         }
         __syncthreads();
         R so = R(0), go = R(0), gin = R(0);
-        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
             const int q = gi * V;
             R x[V], y[V], w[V], s[V], fb[V];
             VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
         block_sum<3, R>(part, red, tot);
         const double rho_w = -double(k.c) * tot[0] / (double(k.c) * double(k.b) * tot[1] + tot[2]);
         const R rw = R(rho_w);
-        for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
             const int q = gi * V;
             R x[V], y[V], w[V], fb[V], o[V];
             VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(DVM_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fac
 // SMEM: the cell's flux sum F (Q values) is kept in shared memory between the two
 // passes; otherwise it is summed again from the face fluxes.
 template <class R, bool SMEM, int V>
-__global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
+__global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
                                                           double *__restrict__ W, const R *__restrict__ flux)
 {
     step_dependency_wait();
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
     };
     R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
 #pragma unroll 2
-    for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+    for (int gi = threadIdx.x; gi < Q / V; gi += CELL_THREADS) {
         const int q = gi * V;
         R x[V], y[V], F[V];
         VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -459,7 +465,7 @@ __global__ void __launch_bounds__(DVM_THREADS) k_dvm_cell(const DvmMesh m, const
     const R rdtv = R(dtv);
     R *fr = f + c * m.Q;
 #pragma unroll 2
-    for (int gi = threadIdx.x; gi < Q / V; gi += DVM_THREADS) {
+    for (int gi = threadIdx.x; gi < Q / V; gi += CELL_THREADS) {
         const int q = gi * V;
         R x[V], y[V], w[V], F[V], fv[V];
         VIO<R, V>::xi(xi + 2 * q, x, y);
@@ -518,19 +524,19 @@ template <class R, int V>
 cudaError_t step_pv(const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp, void *flux,
                     cudaStream_t st)
 {
-    const dim3 cells((unsigned)m.nc), faces((unsigned)m.nf), blk(DVM_THREADS);
+    const dim3 cells((unsigned)m.nc), faces((unsigned)m.nf);
     const R *cf = static_cast<const R *>(f);
     R *pf = static_cast<R *>(f), *pfbp = static_cast<R *>(fbp), *pflux = static_cast<R *>(flux);
     const R *cfbp = pfbp, *cflux = pflux;
-    cudaError_t e = launch_step_kernel(k_dvm_fbp<R, V>, cells, blk, 0, st, m, c, cf, (const double *)W, pfbp);
+    cudaError_t e = launch_step_kernel(k_dvm_fbp<R, V>, cells, dim3(FBP_THREADS), 0, st, m, c, cf, (const double *)W, pfbp);
     if (e != cudaSuccess) return e;
     if (dvm_use_smem<R>(m.Q)) {
         const size_t bytes = (size_t)m.Q * sizeof(R);
-        e = launch_step_kernel(k_dvm_face<R, true, V>, faces, blk, bytes, st, m, c, RTw, cfbp, pflux);
-        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, true, V>, cells, blk, bytes, st, m, c, pf, W, cflux);
+        e = launch_step_kernel(k_dvm_face<R, true, V>, faces, dim3(FACE_THREADS), bytes, st, m, c, RTw, cfbp, pflux);
+        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, true, V>, cells, dim3(CELL_THREADS), bytes, st, m, c, pf, W, cflux);
     } else {
-        e = launch_step_kernel(k_dvm_face<R, false, V>, faces, blk, 0, st, m, c, RTw, cfbp, pflux);
-        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, false, V>, cells, blk, 0, st, m, c, pf, W, cflux);
+        e = launch_step_kernel(k_dvm_face<R, false, V>, faces, dim3(FACE_THREADS), 0, st, m, c, RTw, cfbp, pflux);
+        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, false, V>, cells, dim3(CELL_THREADS), 0, st, m, c, pf, W, cflux);
     }
     return e;
 }
