@@ -85,6 +85,42 @@ def test_batch_against_oracle():
     assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
 
 
+def test_batch_workload_sample_against_oracle_and_single_solves():
+    """The batch workload itself (256 cavities, N ~ logU[32, 512], Re ~ logU[100, 5000],
+    seed 1), 60 steps in one batch.  Every instance is checked against its own
+    single-solver run, and a seeded sample of 8 (the smallest, the largest and 6 drawn
+    with seed 7) against the FP64 oracle.  Sixty steps from rest is an early transient:
+    far from the lid u is near zero, so a relative norm of u measures FP32 rounding
+    against a vanishing signal.  The criterion is therefore the FP32 profile
+    tolerance, max |u - u_ref| <= 1e-4 U (lid speed U = 0.1), with
+    max |rho - rho_ref| <= 1e-5."""
+    S = _S()
+    cases = [M.cavity(n, Re=re) for n, re in M.batch_cavities(256, seed=1)]
+    probe = S.Batch(1 << 20, "fp32", 4)
+    need = sum(probe.footprint(S.Mesh(c.mesh, c.bcs)) for c in cases)
+    b = S.Batch(need + (64 << 20), "fp32", 512)
+    ids = [b.add_case(c) for c in cases]
+    steps, U = 60, 0.1
+    b.step(steps)
+    sizes = [c.mesh.n_cells for c in cases]
+    lo, hi = int(np.argmin(sizes)), int(np.argmax(sizes))
+    rng = np.random.default_rng(7)
+    sample = {lo, hi} | {int(i) for i in rng.choice([i for i in range(len(cases)) if i not in (lo, hi)], 6,
+                                                   replace=False)}
+    assert len(sample) == 8
+    for i, (c, ident) in enumerate(zip(cases, ids)):
+        rho, u = b.macros(ident)
+        rho1, u1 = _single(c, steps)
+        assert np.abs(u - u1).max() <= 1e-4 * U
+        assert np.abs(rho - rho1).max() <= 1e-5
+        if i in sample:
+            st = O.init(c.mesh.n_cells)
+            O.run(c, st, steps)
+            assert np.abs(st.u).max() > 1e-3                 # the lid has set the fluid moving
+            assert np.abs(u - st.u).max() <= 1e-4 * U
+            assert np.abs(rho - st.W[:, 0]).max() <= 1e-5
+
+
 def test_batch_residual_matches_single_solver():
     S = _S()
     case = M.cavity(64, Re=100.0)
