@@ -3,6 +3,7 @@ scope stated beside each measured number.
 
     python -m paper_2007_07347_gb300.validate cavity   # 256^2 Re 1000, 20k FP32 steps vs the FP64 oracle
     python -m paper_2007_07347_gb300.validate cylinder # 512x256 O-mesh Re 40 to steady state, FP64/FP32/bf16
+    python -m paper_2007_07347_gb300.validate cylinder fp16dev   # the same for the listed storages only
     python -m paper_2007_07347_gb300.validate shedding # 512x256 O-mesh Re 60/80/100: St and mean Cd
     python -m paper_2007_07347_gb300.validate plate    # laminar flat plate Re_L 1e5: Cd against Blasius
 
@@ -216,5 +217,7 @@ if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "cavity"
     if what == "shedding" and len(sys.argv) > 2:
         shedding(tuple(float(x) for x in sys.argv[2:]))
+    elif what == "cylinder" and len(sys.argv) > 2:
+        cylinder(precisions=tuple(sys.argv[2:]))           # e.g. cylinder fp16dev bf16dev
     else:
         {"cavity": cavity, "cylinder": cylinder, "shedding": shedding, "plate": plate}[what]()
