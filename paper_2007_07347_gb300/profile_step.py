@@ -1,11 +1,11 @@
 """Profiling driver: N separate step launches (no graph) of one case.
 
-    python -m paper_2007_07347_gb300.profile_step CASE [PRECISION] [STEPS] [TILE]
+    python -m paper_2007_07347_gb300.profile_step CASE [PRECISION] [STEPS] [TILE] [STAGING]
 
 CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh), or
 microcavity (the rarefied solver: 40 x 40 cells, 100 x 100 velocities, Kn 1).  Used
 under ncu with ``-k regex:k_step`` (``regex:k_dvm`` for the rarefied kernels) to
-capture single step launches.
+capture single step launches.  STAGING (Cartesian kernel): loads (default) or tma.
 """
 import sys
 
@@ -28,6 +28,7 @@ def main(argv):
     prec = argv[2] if len(argv) > 2 else "fp32"
     nsteps = int(argv[3]) if len(argv) > 3 else 10
     tile = int(argv[4]) if len(argv) > 4 else 0
+    staging = argv[5] if len(argv) > 5 else "loads"
     torch.cuda.set_device(0)
     if name == "microcavity":
         d = S.Dvm.from_case(M.micro_cavity(40, Kn=1.0), "fp64" if prec == "fp64" else "fp32", graph_steps=-1).init()
@@ -36,7 +37,7 @@ def main(argv):
         print("sizes", d.sizes())
         return
     case = CASES[name]()
-    s = S.Solver.from_case(case, prec, graph_steps=-1, tile_cells=tile)
+    s = S.Solver.from_case(case, prec, graph_steps=-1, tile_cells=tile, staging=staging)
     u = None if case.u0 == (0.0, 0.0) else np.tile(case.u0, (case.mesh.n_cells, 1))
     s.init(None, u)
     s.step(nsteps)
