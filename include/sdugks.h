@@ -107,6 +107,9 @@ typedef struct sdugks_info {
     int32_t tile_cells;
     int32_t nx, ny;               /* Cartesian kernel: grid size, else 0               */
     int32_t staging;              /* SDUGKS_STAGING_* in use                           */
+    int32_t one_code_path;        /* Cartesian kernel: 1 when the grid runs in one wave and
+                                     every block takes the general code path; 0 when interior
+                                     blocks take the compile-time interior variant      */
 } sdugks_info;
 
 /* ---- mesh ---------------------------------------------------------------------- */

@@ -8,7 +8,7 @@ namespace sdugks {
 // (shape index 0, 1, 2).  FP64 uses 16 x 16 only.
 
 cudaError_t prepare_cart_fp64();
-cudaError_t launch_cart_fp64(const CartInst &m, const CartTma *tma, int parity, cudaStream_t st);
+cudaError_t launch_cart_fp64(const CartInst &m, const CartTma *tma, bool general, int parity, cudaStream_t st);
 int occ_cart_fp64(bool tma);
 
 template <int P> cudaError_t prepare_shapes()
@@ -26,24 +26,26 @@ cudaError_t prepare_cart(int prec)
     return prec == P_BF16DEV ? prepare_shapes<P_BF16DEV>() : prepare_shapes<P_FP32>();
 }
 
-template <int P> cudaError_t launch_shape(int shape, const CartInst &m, const CartTma *tma, int parity, cudaStream_t st)
+template <int P>
+cudaError_t launch_shape(int shape, const CartInst &m, const CartTma *tma, bool general, int parity, cudaStream_t st)
 {
-    if (shape == 1) return launch_cart_p<P, 16, 14>(m, tma, parity, st);
-    if (shape == 2) return launch_cart_p<P, 16, 8>(m, tma, parity, st);
-    return launch_cart_p<P, 16, 16>(m, tma, parity, st);
+    if (shape == 1) return launch_cart_p<P, 16, 14>(m, tma, general, parity, st);
+    if (shape == 2) return launch_cart_p<P, 16, 8>(m, tma, general, parity, st);
+    return launch_cart_p<P, 16, 16>(m, tma, general, parity, st);
 }
 
-cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, const CartTma *tma, int parity, cudaStream_t st)
+cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, const CartTma *tma, bool general, int parity,
+                             cudaStream_t st)
 {
-    if (prec == P_FP64) return launch_cart_fp64(m, tma, parity, st);
-    if (prec == P_BF16DEV) return launch_shape<P_BF16DEV>(shape, m, tma, parity, st);
-    if (prec == P_FP16DEV) return launch_shape<P_FP16DEV>(shape, m, tma, parity, st);
-    return launch_shape<P_FP32>(shape, m, tma, parity, st);
+    if (prec == P_FP64) return launch_cart_fp64(m, tma, general, parity, st);
+    if (prec == P_BF16DEV) return launch_shape<P_BF16DEV>(shape, m, tma, general, parity, st);
+    if (prec == P_FP16DEV) return launch_shape<P_FP16DEV>(shape, m, tma, general, parity, st);
+    return launch_shape<P_FP32>(shape, m, tma, general, parity, st);
 }
 
 template <int P, int TX, int TY> int occ_shape(bool tma)
 {
-    return tma ? occ_cart_p<P, TX, TY, true>() : occ_cart_p<P, TX, TY, false>();
+    return tma ? occ_cart_p<P, TX, TY, CART_SPECIALISED_TMA>() : occ_cart_p<P, TX, TY, CART_SPECIALISED>();
 }
 
 int cart_shape_occupancy(int prec, int shape, bool tma)

@@ -125,8 +125,10 @@ struct CartTma {
     CUtensorMap f[2], W[2];
 };
 cudaError_t make_cart_tma(int prec, int shape, const CartInst &m, CartTma &out);
-// tma: nullptr stages every block with plain loads
-cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, const CartTma *tma, int parity, cudaStream_t st);
+// tma: nullptr stages every block with plain loads; general: every block on the general
+// code path (no interior variant; ignored with TMA staging)
+cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, const CartTma *tma, bool general, int parity,
+                             cudaStream_t st);
 int cart_shape_occupancy(int prec, int shape, bool tma);   // resident CTAs per SM
 // batched: every (instance, tile) item of the list, grid-stride over a fixed grid
 cudaError_t prepare_batch(int prec);

@@ -679,9 +679,16 @@ __device__ __forceinline__ bool cta_wait_staged(const CartInst &m, uint32_t bar,
     return true;
 }
 
-// One block per CTA.  TMA: interior blocks are staged by two tensor copies (tf, tw: the
-// maps of buffer par) into boxes that overlay the face-flux arrays.
-template <int P, int TX, int TY, bool TMA>
+// One block per CTA.  MODE (CartMode): CART_SPECIALISED runs interior blocks with the
+// compile-time interior variant of cart_tile and the others with the general one;
+// CART_SPECIALISED_TMA does the same with the interior blocks staged by two tensor copies
+// (tf, tw: the maps of buffer par) into boxes that overlay the face-flux arrays;
+// CART_GENERAL runs every block with the general variant.  One code path serves a grid
+// whose blocks all run in one wave better, where the slowest (edge) blocks set the time:
+// there the edge blocks' general code is not displaced by the interior variant's.
+enum CartMode { CART_SPECIALISED = 0, CART_SPECIALISED_TMA = 1, CART_GENERAL = 2 };
+
+template <int P, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : (cart_threads<TX, TY>() <= 320 ? 4 : 2))
 k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tw)
 {
@@ -689,8 +696,8 @@ k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, c
     step_dependency_wait();
     const int ntx = (m.nx + TX - 1) / TX;
     const int tbx = blockIdx.x % ntx, tby = blockIdx.x / ntx;
-    if (cart_block_interior<TX, TY>(m, tbx, tby)) {
-        if constexpr (TMA) {
+    if (MODE != CART_GENERAL && cart_block_interior<TX, TY>(m, tbx, tby)) {
+        if constexpr (MODE == CART_SPECIALISED_TMA) {
             using B = CartTmaBox<P, TX, TY>;
             uint32_t sa;
             unsigned char *sm = aligned_smem(smem_raw, sa);
@@ -711,8 +718,8 @@ k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, c
     }
 }
 
-template <int P, int TX, int TY, bool TMA> constexpr size_t cart_step_smem() {
-    return TMA ? CartTmaBox<P, TX, TY>::SMEM : cart_smem<P, TX, TY>();
+template <int P, int TX, int TY, int MODE> constexpr size_t cart_step_smem() {
+    return MODE == CART_SPECIALISED_TMA ? CartTmaBox<P, TX, TY>::SMEM : cart_smem<P, TX, TY>();
 }
 
 // Batched: a fixed grid walks the (instance, block) work list; the item count is in
@@ -734,32 +741,41 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
     }
 }
 
+template <int P, int TX, int TY, int MODE> cudaError_t prepare_mode_p() {
+    return cudaFuncSetAttribute(k_step_cart<P, TX, TY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cart_step_smem<P, TX, TY, MODE>());
+}
+
 template <int P, int TX, int TY> cudaError_t prepare_cart_p() {
-    cudaError_t e = cudaFuncSetAttribute(k_step_cart<P, TX, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cart_step_smem<P, TX, TY, false>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step_cart<P, TX, TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cart_step_smem<P, TX, TY, true>());
+    cudaError_t e = prepare_mode_p<P, TX, TY, CART_SPECIALISED>();
+    if (e == cudaSuccess) e = prepare_mode_p<P, TX, TY, CART_SPECIALISED_TMA>();
+    if (e == cudaSuccess) e = prepare_mode_p<P, TX, TY, CART_GENERAL>();
     return e;
 }
 
+// tma: the maps for TMA staging (nullptr: plain loads); general: every block on the
+// general path (ignored with TMA staging)
 template <int P, int TX, int TY>
-cudaError_t launch_cart_p(const CartInst &m, const CartTma *tma, int par, cudaStream_t st)
+cudaError_t launch_cart_p(const CartInst &m, const CartTma *tma, bool general, int par, cudaStream_t st)
 {
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
+    const dim3 grid(ntx * nty), block(cart_threads<TX, TY>());
     if (tma)
-        return launch_step_kernel(k_step_cart<P, TX, TY, true>, dim3(ntx * nty), dim3(cart_threads<TX, TY>()),
-                                  cart_step_smem<P, TX, TY, true>(), st, m, par, tma->f[par], tma->W[par]);
+        return launch_step_kernel(k_step_cart<P, TX, TY, CART_SPECIALISED_TMA>, grid, block,
+                                  cart_step_smem<P, TX, TY, CART_SPECIALISED_TMA>(), st, m, par, tma->f[par], tma->W[par]);
     static const CUtensorMap none{};
-    return launch_step_kernel(k_step_cart<P, TX, TY, false>, dim3(ntx * nty), dim3(cart_threads<TX, TY>()),
-                              cart_step_smem<P, TX, TY, false>(), st, m, par, none, none);
+    if (general)
+        return launch_step_kernel(k_step_cart<P, TX, TY, CART_GENERAL>, grid, block,
+                                  cart_step_smem<P, TX, TY, CART_GENERAL>(), st, m, par, none, none);
+    return launch_step_kernel(k_step_cart<P, TX, TY, CART_SPECIALISED>, grid, block,
+                              cart_step_smem<P, TX, TY, CART_SPECIALISED>(), st, m, par, none, none);
 }
 
-template <int P, int TX, int TY, bool TMA> int occ_cart_p()
+template <int P, int TX, int TY, int MODE> int occ_cart_p()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_cart<P, TX, TY, TMA>, cart_threads<TX, TY>(),
-                                                      cart_step_smem<P, TX, TY, TMA>()) != cudaSuccess || n < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_cart<P, TX, TY, MODE>, cart_threads<TX, TY>(),
+                                                      cart_step_smem<P, TX, TY, MODE>()) != cudaSuccess || n < 1)
         return 1;
     return n;
 }

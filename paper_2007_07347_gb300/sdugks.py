@@ -45,7 +45,8 @@ class Info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_tiles", C.c_int64), ("halo_cells", C.c_int64),
                 ("steps_done", C.c_int64), ("device_bytes", C.c_int64), ("state_bytes_per_cell_step", C.c_double),
                 ("mesh_bytes_per_cell_step", C.c_double), ("kernel", C.c_int32), ("precision", C.c_int32),
-                ("tile_cells", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("staging", C.c_int32)]
+                ("tile_cells", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("staging", C.c_int32),
+                ("one_code_path", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

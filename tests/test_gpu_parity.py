@@ -413,3 +413,46 @@ def test_tma_staging_matches_loads(precision, tile):
     assert relmax(W1, W0) <= 1e-6
     assert relmax(f1, f0) <= 1e-6
 
+
+
+def test_code_path_choice_by_waves():
+    """A Cartesian grid whose blocks all run in one wave takes the general code path for
+    every block; larger grids take the compile-time interior variant for interior
+    blocks."""
+    S = _S()
+    assert S.Solver.from_case(M.cavity(256), "fp32").info()["one_code_path"] == 1      # 304 blocks, 2 per SM
+    assert S.Solver.from_case(M.cavity(512), "fp32").info()["one_code_path"] == 0
+    assert S.Solver.from_case(M.cavity(1024), "fp32").info()["one_code_path"] == 0
+    assert S.Solver.from_case(M.cavity(256), "fp32", staging="tma").info()["one_code_path"] == 0
+
+
+def test_fp64_interior_variant_matches_oracle():
+    """A grid of more blocks than fit at once (FP64: 16x16 blocks, one per SM; 208^2 has
+    169) runs interior blocks with the compile-time interior variant: FP64 within 1e-12 of
+    the oracle, from a random state."""
+    S = _S()
+    case = M.cavity(208, Re=400.0)
+    rho, u = _random_state(case, 26)
+    s, (f, W), st = run_both(case, 200, "fp64", rho, u)
+    assert s.info()["one_code_path"] == 0
+    assert relmax(f, st.f) <= 1e-12
+    assert relmax(W, st.W) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol_u,tol_rho", [("fp32", 1e-4, 1e-5), ("fp16dev", 2e-3, 1e-4),
+                                                     ("bf16dev", 1e-2, 1e-3)])
+def test_interior_variant_fp32_modes_against_oracle(precision, tol_u, tol_rho):
+    """The interior variant in the FP32 modes (cavity 400^2, several waves of blocks)
+    against the FP64 oracle after 200 steps from a random state, with the FP32 /
+    fp16 / bf16 parity tolerances."""
+    S = _S()
+    case = M.cavity(400, Re=1000.0)
+    rho, u = _random_state(case, 27)
+    s = S.Solver.from_case(case, precision).init(rho, u)
+    assert s.info()["one_code_path"] == 0
+    s.step(200)
+    r, v = s.macros()
+    st = O.init(case.mesh.n_cells, rho=rho, u=u)
+    O.run(case, st, 200)
+    assert rel_l2(v, st.u) <= tol_u
+    assert np.abs(r - st.W[:, 0]).max() <= tol_rho
