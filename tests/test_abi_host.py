@@ -181,3 +181,25 @@ def test_rarefied_solver_checks_its_boundaries_on_the_host():
         S.Dvm.from_case(mc)
     except S.SdugksError as e:
         assert e.name == "CUDA" and not torch.cuda.is_available(), str(e)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the compiled library there is no fallback path: loading it, and so every
+    solver call, raises."""
+    saved = S._lib
+    try:
+        S._lib = None
+        monkeypatch.setattr(S._build, "build", lambda *a, **k: "/nonexistent/libsdugks.so")
+        with pytest.raises(OSError):
+            S.lib()
+        with pytest.raises(OSError):
+            S.Solver.from_case(M.cavity(8), "fp32")
+
+        def no_toolchain(*a, **k):
+            raise RuntimeError("nvcc failed")
+
+        monkeypatch.setattr(S._build, "build", no_toolchain)
+        with pytest.raises(RuntimeError):
+            S.lib()
+    finally:
+        S._lib = saved
