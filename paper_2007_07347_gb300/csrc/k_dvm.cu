@@ -402,7 +402,8 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
 // passes; otherwise it is summed again from the face fluxes.
 template <class R, bool SMEM, int V>
 __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
-                                                          double *__restrict__ W, const R *__restrict__ flux)
+                                                          double *__restrict__ W, const R *__restrict__ flux,
+                                                          R *__restrict__ fbp_next)
 {
     step_dependency_wait();
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -473,13 +474,16 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
         VIO<R, V>::ld(fr + q, fv);
         if (SMEM) VIO<R, V>::ld(Fbuf + q, F);
         else F_of(q, F);
+        R nb[V];
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const R fe = maxwell<R>(sp, x[j], y[j], w[j]);
             const R num = fv[j] - rdtv * F[j] + k.r * fe;
             fv[j] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
+            nb[j] = k.a * fv[j] + k.b * fe;       // the next step's fbar+ (Eq. fbarplus), as k_dvm_fbp forms it
         }
         VIO<R, V>::st(fr + q, fv);
+        if (fbp_next) VIO<R, V>::st(fbp_next + c * m.Q + q, nb);
     }
 }
 
@@ -522,40 +526,47 @@ template <class R> cudaError_t prepare_p(int64_t Q) { return Q % 4 == 0 ? prepar
 
 template <class R, int V>
 cudaError_t step_pv(const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp, void *flux,
-                    cudaStream_t st)
+                    bool fbp_ready, cudaStream_t st)
 {
     const dim3 cells((unsigned)m.nc), faces((unsigned)m.nf);
     const R *cf = static_cast<const R *>(f);
     R *pf = static_cast<R *>(f), *pfbp = static_cast<R *>(fbp), *pflux = static_cast<R *>(flux);
     const R *cfbp = pfbp, *cflux = pflux;
-    cudaError_t e = launch_step_kernel(k_dvm_fbp<R, V>, cells, dim3(FBP_THREADS), 0, st, m, c, cf, (const double *)W, pfbp);
+    cudaError_t e = cudaSuccess;
+    if (!fbp_ready)
+        e = launch_step_kernel(k_dvm_fbp<R, V>, cells, dim3(FBP_THREADS), 0, st, m, c, cf, (const double *)W, pfbp);
     if (e != cudaSuccess) return e;
+    // the cell kernel leaves the next step's fbar+ in fbp (read by this step's face kernel
+    // before the cell kernel starts)
     if (dvm_use_smem<R>(m.Q)) {
         const size_t bytes = (size_t)m.Q * sizeof(R);
         e = launch_step_kernel(k_dvm_face<R, true, V>, faces, dim3(FACE_THREADS), bytes, st, m, c, RTw, cfbp, pflux);
-        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, true, V>, cells, dim3(CELL_THREADS), bytes, st, m, c, pf, W, cflux);
+        if (e == cudaSuccess)
+            e = launch_step_kernel(k_dvm_cell<R, true, V>, cells, dim3(CELL_THREADS), bytes, st, m, c, pf, W, cflux, pfbp);
     } else {
         e = launch_step_kernel(k_dvm_face<R, false, V>, faces, dim3(FACE_THREADS), 0, st, m, c, RTw, cfbp, pflux);
-        if (e == cudaSuccess) e = launch_step_kernel(k_dvm_cell<R, false, V>, cells, dim3(CELL_THREADS), 0, st, m, c, pf, W, cflux);
+        if (e == cudaSuccess)
+            e = launch_step_kernel(k_dvm_cell<R, false, V>, cells, dim3(CELL_THREADS), 0, st, m, c, pf, W, cflux, pfbp);
     }
     return e;
 }
 
 template <class R>
 cudaError_t step_p(const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp, void *flux,
-                   cudaStream_t st)
+                   bool fbp_ready, cudaStream_t st)
 {
     if (m.nc <= 0) return cudaSuccess;
-    return m.Q % 4 == 0 ? step_pv<R, 4>(m, c, RTw, f, W, fbp, flux, st) : step_pv<R, 1>(m, c, RTw, f, W, fbp, flux, st);
+    return m.Q % 4 == 0 ? step_pv<R, 4>(m, c, RTw, f, W, fbp, flux, fbp_ready, st)
+                        : step_pv<R, 1>(m, c, RTw, f, W, fbp, flux, fbp_ready, st);
 }
 
 }  // namespace
 
 cudaError_t launch_dvm_step(int prec, const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp,
-                            void *flux, cudaStream_t st)
+                            void *flux, bool fbp_ready, cudaStream_t st)
 {
-    return prec == P_FP64 ? step_p<double>(m, c, RTw, f, W, fbp, flux, st)
-                          : step_p<float>(m, c, RTw, f, W, fbp, flux, st);
+    return prec == P_FP64 ? step_p<double>(m, c, RTw, f, W, fbp, flux, fbp_ready, st)
+                          : step_p<float>(m, c, RTw, f, W, fbp, flux, fbp_ready, st);
 }
 
 cudaError_t prepare_dvm(int prec, int64_t Q)

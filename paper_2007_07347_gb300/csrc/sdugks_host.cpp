@@ -1798,6 +1798,7 @@ struct sdugks_dvm {
     cudaGraphExec_t graph = nullptr;
     int graph_len = 0;
     bool initialised = false;
+    bool fbp_ready = false;         // fbp holds fbar+ of the current state (left by the last step)
 };
 
 extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *prm, void *stream, sdugks_dvm **out)
@@ -1968,6 +1969,7 @@ extern "C" int sdugks_dvm_init(sdugks_dvm *d, const double *rho, const double *u
     CUDA_TRY(launch_dvm_init(d->prec, d->dm, d->W, d->f, d->stream));
     CUDA_TRY(cudaStreamSynchronize(d->stream));
     d->initialised = true;
+    d->fbp_ready = false;
     return SDUGKS_OK;
 }
 
@@ -1978,8 +1980,8 @@ static int dvm_ensure_graph(sdugks_dvm *d)
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < G && e == cudaSuccess; k++)
-        e = launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, d->cap_stream);
+    for (int k = 0; k < G && e == cudaSuccess; k++)     // replayed only once fbp is ready
+        e = launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, true, d->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(d->cap_stream, &g);
     CUDA_TRY(e);
     CUDA_TRY(e2);
@@ -1998,13 +2000,18 @@ extern "C" int sdugks_dvm_step(sdugks_dvm *d, int64_t n)
     CUDA_TRY(cudaSetDevice(d->device));
     int64_t left = n;
     const int G = d->p.graph_steps;
+    if (left > 0 && !d->fbp_ready) {
+        CUDA_TRY(launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, false, d->stream));
+        d->fbp_ready = true;
+        left--;
+    }
     if (G > 0 && left >= G) {
         int rc = dvm_ensure_graph(d);
         if (rc) return rc;
         for (; left >= G; left -= G) CUDA_TRY(cudaGraphLaunch(d->graph, d->stream));
     }
     for (; left > 0; left--)
-        CUDA_TRY(launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, d->stream));
+        CUDA_TRY(launch_dvm_step(d->prec, d->dm, d->coefs, d->p.RT_wall, d->f, d->W, d->fbp, d->flux, true, d->stream));
     return SDUGKS_OK;
 }
 

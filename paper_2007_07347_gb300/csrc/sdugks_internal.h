@@ -193,8 +193,10 @@ struct DvmMesh {
 };
 constexpr int32_t DVM_SECOND = int32_t(0x40000000);
 constexpr int DVM_THREADS = 256;
+// one step; fbp_ready: fbp already holds this step's fbar+ (left there by the previous
+// step's cell kernel), else it is formed first.  The step leaves the next step's fbar+ in fbp.
 cudaError_t launch_dvm_step(int prec, const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp,
-                            void *flux, cudaStream_t st);
+                            void *flux, bool fbp_ready, cudaStream_t st);
 cudaError_t launch_dvm_init(int prec, const DvmMesh &m, const double *W, void *f, cudaStream_t st);
 cudaError_t prepare_dvm(int prec, int64_t Q);   // kernel attributes on the current device
 
