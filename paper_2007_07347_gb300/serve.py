@@ -35,6 +35,7 @@ class Request:
     status: str = "queued"   # queued | running | converged | capped
     handle: object = None
     result: tuple = None
+    mesh: object = None      # the library mesh (built once, while the GPU steps)
 
     def build(self):
         if self.case is None:
@@ -110,11 +111,23 @@ class Server:
         now = lambda: time.perf_counter() - t0  # noqa: E731
         idle_waits = 0
         while pending or running:
-            # admit every arrived request whose footprint fits (FIFO, skipping ahead)
+            # advance everything running by one residual interval (asynchronous; the two
+            # streams overlap), then prepare and admit arrivals while the GPU works
+            stepped = list(running)
+            for r in stepped:
+                if r.handle[0] == "solver":
+                    r.handle[1].step(self.check_every)
+            if stepped:
+                batch.step(self.check_every)
             arrived = [r for r in pending if r.arrival <= now()]
-            for r in arrived:
+            for r in arrived:                    # host-side mesh work, overlapping the steps
                 case = r.build()
-                m = S.Mesh(case.mesh, case.bcs)
+                if r.mesh is None:
+                    r.mesh = S.Mesh(case.mesh, case.bcs)
+            # admit every arrived request whose footprint fits (FIFO, skipping ahead);
+            # adding to the batch waits for the interval in flight on its stream
+            for r in arrived:
+                case, m = r.case, r.mesh
                 if r.kind == "cylinder":
                     need = 400 * case.mesh.n_cells          # state + mesh data, tiled FP32 path
                     if solver_bytes + need > self.solver_pool_bytes:
@@ -136,18 +149,14 @@ class Server:
                 r.status = "running"
                 pending.remove(r)
                 running.append(r)
-            if not running:
-                nxt = min(r.arrival for r in pending)
-                time.sleep(max(0.0, min(0.01, nxt - now())))
-                idle_waits += 1
+            if not stepped:
+                if not running:
+                    nxt = min(r.arrival for r in pending)
+                    time.sleep(max(0.0, min(0.01, nxt - now())))
+                    idle_waits += 1
                 continue
-            # advance everything by one residual interval; the two streams overlap
-            for r in running:
-                if r.handle[0] == "solver":
-                    r.handle[1].step(self.check_every)
-            batch.step(self.check_every)
             res = batch.residual()
-            for r in list(running):
+            for r in stepped:
                 if r.handle[0] == "solver":
                     try:
                         eps, _ = r.handle[1].residual()
@@ -170,6 +179,7 @@ class Server:
                     else:
                         batch.remove(r.handle[1])
                     r.handle = None
+                    r.mesh = None
                     r.done = now()
                     running.remove(r)
         wall = now()
