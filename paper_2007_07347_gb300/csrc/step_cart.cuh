@@ -735,8 +735,9 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int2 it = items[w];
         const CartInst &m = insts[it.x];
-        const int ntx = (m.nx + TX - 1) / TX;
-        cart_tile<P, TX, TY, false, false>(m, par, it.y % ntx, it.y / ntx, smem_raw);
+        const int ntx = (m.nx + TX - 1) / TX, bx = it.y % ntx, by = it.y / ntx;
+        if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
+        else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
         __syncthreads();                                 // shared memory is reused by the next item
     }
 }
