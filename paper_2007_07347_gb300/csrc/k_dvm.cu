@@ -14,10 +14,13 @@
 //   k_dvm_cell  per cell: F = sum of its faces' fluxes (Eq. MesoFlux), its moments
 //               (Eq. MacroFlux) update W in FP64 (Eq. MacroUpdate), then f (Eq. fn+1)
 // W = (rho, rho u, rho E) per cell in FP64; f and the scratch arrays in the compute
-// precision.  When Q is a multiple of 4 every thread takes 4 consecutive velocities at a
-// time with 16-byte vector loads and stores (V = 4); otherwise one (V = 1).  The
-// arithmetic of a velocity is the same either way.  The Maxwellian is that of Eq. Feq with exponent |xi - u|^2 / (2 R T),
-// D = 2, sampled at the nodes and multiplied by the node weights.
+// precision.  When nv is a multiple of 4 every thread takes 4 consecutive velocities at
+// a time with 16-byte vector loads and stores (V = 4); otherwise one (V = 1).  The
+// arithmetic of a velocity is the same either way.  The velocity grid is the tensor
+// product of one axis' nv nodes with one weight, so every CTA stages the nv nodes in
+// shared memory and reads a velocity's (x, y) from there.  The Maxwellian is that of
+// Eq. Feq with exponent |xi - u|^2 / (2 R T), D = 2, sampled at the nodes and multiplied
+// by the node weight.
 #include "sdugks_internal.h"
 
 #include <cuda_runtime.h>
@@ -121,7 +124,6 @@ template <class R, int V> struct VIO;
 template <class R> struct VIO<R, 1> {
     static __device__ __forceinline__ void ld(const R *p, R v[1]) { v[0] = *p; }
     static __device__ __forceinline__ void st(R *p, const R v[1]) { *p = v[0]; }
-    static __device__ __forceinline__ void xi(const R *p, R x[1], R y[1]) { x[0] = p[0]; y[0] = p[1]; }
 };
 template <> struct VIO<float, 4> {
     static __device__ __forceinline__ void ld(const float *p, float v[4]) {
@@ -130,11 +132,6 @@ template <> struct VIO<float, 4> {
     }
     static __device__ __forceinline__ void st(float *p, const float v[4]) {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-    // xi of 4 velocities: (x, y) pairs, 32 bytes
-    static __device__ __forceinline__ void xi(const float *p, float x[4], float y[4]) {
-        const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
-        x[0] = a.x; y[0] = a.y; x[1] = a.z; y[1] = a.w; x[2] = b.x; y[2] = b.y; x[3] = b.z; y[3] = b.w;
     }
 };
 template <> struct VIO<double, 4> {
@@ -146,12 +143,59 @@ template <> struct VIO<double, 4> {
         reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
         reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
     }
-    static __device__ __forceinline__ void xi(const double *p, double x[4], double y[4]) {
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const double2 t = reinterpret_cast<const double2 *>(p)[j];
-            x[j] = t.x; y[j] = t.y;
-        }
+};
+
+// Largest nv of the shared-memory node table (the API limit).
+constexpr int MAX_NV = 1024;
+
+// The nodes of one axis into shared memory.  They never change, so this runs before the
+// wait on the previous kernel; the caller synchronises before the first use.
+template <class R> __device__ __forceinline__ void load_nodes(R *vt, const DvmMesh &m)
+{
+    const R *g = static_cast<const R *>(m.vnode);
+    for (int k = threadIdx.x; k < m.nv; k += blockDim.x) vt[k] = g[k];
+}
+
+// Where a thread's velocity groups lie on the grid.  Group starts are a fixed stride
+// apart, so the grid position (j, i) of the first velocity, q = j + nv i, is stepped
+// rather than divided.  With V = 4, nv is a multiple of 4: a group lies in one grid row.
+struct VelWalk {
+    int j, i, dj, di, nv;
+    __device__ __forceinline__ VelWalk(int q0, int stride, int nv_) : nv(nv_)
+    {
+        j = q0 % nv_; i = q0 / nv_; dj = stride % nv_; di = stride / nv_;
+    }
+    __device__ __forceinline__ void next()
+    {
+        j += dj; i += di;
+        if (j >= nv) { j -= nv; i++; }
+    }
+};
+
+// (x, y) of the V velocities of a group from the node table.
+template <class R, int V> struct VNodes;
+template <class R> struct VNodes<R, 1> {
+    static __device__ __forceinline__ void get(const R *vt, const VelWalk &w, R x[1], R y[1])
+    {
+        x[0] = vt[w.j]; y[0] = vt[w.i];
+    }
+};
+template <> struct VNodes<float, 4> {
+    static __device__ __forceinline__ void get(const float *vt, const VelWalk &w, float x[4], float y[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(vt + w.j);
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+        const float yy = vt[w.i];
+        y[0] = yy; y[1] = yy; y[2] = yy; y[3] = yy;
+    }
+};
+template <> struct VNodes<double, 4> {
+    static __device__ __forceinline__ void get(const double *vt, const VelWalk &w, double x[4], double y[4])
+    {
+        const double2 a = reinterpret_cast<const double2 *>(vt + w.j)[0], b = reinterpret_cast<const double2 *>(vt + w.j)[1];
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+        const double yy = vt[w.i];
+        y[0] = yy; y[1] = yy; y[2] = yy; y[3] = yy;
     }
 };
 
@@ -220,26 +264,27 @@ template <class R, int V>
 __global__ void __launch_bounds__(FBP_THREADS) k_dvm_fbp(const DvmMesh m, const Coefs cf, const R *__restrict__ f,
                                                          const double *__restrict__ W, R *__restrict__ fbp)
 {
-    step_dependency_wait();
+    __shared__ __align__(16) R vt[MAX_NV];
     __shared__ R sp[4];
+    load_nodes<R>(vt, m);
+    step_dependency_wait();
     const int64_t c = blockIdx.x;
     const int Q = (int)m.Q;
     if (threadIdx.x == 0) set_sp<R>(sp, max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]));
     __syncthreads();
     const DvmR<R> k(cf);
-    const R *xi = static_cast<const R *>(m.xi);
-    const R *wq = static_cast<const R *>(m.wq);
+    const R w = R(m.w_node);
     const R *fr = f + c * m.Q;
     R *out = fbp + c * m.Q;
+    VelWalk vw(threadIdx.x * V, FBP_THREADS * V, m.nv);
 #pragma unroll 2
-    for (int g = threadIdx.x; g < Q / V; g += FBP_THREADS) {
+    for (int g = threadIdx.x; g < Q / V; g += FBP_THREADS, vw.next()) {
         const int q = g * V;
-        R x[V], y[V], w[V], fv[V], o[V];
-        VIO<R, V>::xi(xi + 2 * q, x, y);
-        VIO<R, V>::ld(wq + q, w);
+        R x[V], y[V], fv[V], o[V];
+        VNodes<R, V>::get(vt, vw, x, y);
         VIO<R, V>::ld(fr + q, fv);
 #pragma unroll
-        for (int j = 0; j < V; j++) o[j] = k.a * fv[j] + k.b * maxwell<R>(sp, x[j], y[j], w[j]);
+        for (int j = 0; j < V; j++) o[j] = k.a * fv[j] + k.b * maxwell<R>(sp, x[j], y[j], w);
         VIO<R, V>::st(out + q, o);
     }
 }
@@ -272,16 +317,17 @@ template <class R, bool SMEM, int V>
 __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
-    step_dependency_wait();
     extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ __align__(16) R vt[MAX_NV];
     __shared__ double red[32 * 4];
     __shared__ R sp[4];
     __shared__ SideData<R> sd[2];
+    load_nodes<R>(vt, m);
+    step_dependency_wait();
     const int64_t fc = blockIdx.x;
     const int Q = (int)m.Q;
     const DvmR<R> k(cf);
-    const R *xi = static_cast<const R *>(m.xi);
-    const R *wq = static_cast<const R *>(m.wq);
+    const R w = R(m.w_node);
     const R *G = static_cast<const R *>(m.face_geo) + 6 * fc;
     const R nx = G[0], ny = G[1], rox = G[2], roy = G[3], rkx = G[4], rky = G[5];
     const int64_t o = m.face_own[fc];
@@ -297,10 +343,11 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
 
     if (interior) {
         R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
-        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
+        VelWalk vw(threadIdx.x * V, FACE_THREADS * V, m.nv);
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS, vw.next()) {
             const int q = gi * V;
             R x[V], y[V], s[V], fa[V], fo[V], fb[V];
-            VIO<R, V>::xi(xi + 2 * q, x, y);
+            VNodes<R, V>::get(vt, vw, x, y);
             bool needA = false, needB = false;        // some velocity takes the owner's / the neighbour's side
 #pragma unroll
             for (int j = 0; j < V; j++) {
@@ -323,16 +370,16 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
         block_sum<4, R>(part, red, Wb);
         if (threadIdx.x == 0) set_sp<R>(sp, max_params(Wb[0], Wb[1], Wb[2], Wb[3]));
         __syncthreads();
-        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
+        VelWalk vw2(threadIdx.x * V, FACE_THREADS * V, m.nv);
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS, vw2.next()) {
             const int q = gi * V;
-            R x[V], y[V], w[V], fb[V], o[V];
-            VIO<R, V>::xi(xi + 2 * q, x, y);
-            VIO<R, V>::ld(wq + q, w);
+            R x[V], y[V], fb[V], o[V];
+            VNodes<R, V>::get(vt, vw2, x, y);
             VIO<R, V>::ld(fbuf + q, fb);
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 const R s = x[j] * nx + y[j] * ny;
-                const R g = maxwell<R>(sp, x[j], y[j], w[j]);
+                const R g = maxwell<R>(sp, x[j], y[j], w);
                 o[j] = s * ((fb[j] + k.b * g) * k.c);
             }
             VIO<R, V>::st(out + q, o);
@@ -351,11 +398,11 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
         }
         __syncthreads();
         R so = R(0), go = R(0), gin = R(0);
-        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
+        VelWalk vw(threadIdx.x * V, FACE_THREADS * V, m.nv);
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS, vw.next()) {
             const int q = gi * V;
-            R x[V], y[V], w[V], s[V], fb[V];
-            VIO<R, V>::xi(xi + 2 * q, x, y);
-            VIO<R, V>::ld(wq + q, w);
+            R x[V], y[V], s[V], fb[V];
+            VNodes<R, V>::get(vt, vw, x, y);
             bool leaving = false;                     // some velocity leaves the fluid through the wall
 #pragma unroll
             for (int j = 0; j < V; j++) {
@@ -366,7 +413,7 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
             if (leaving) reconstruct_v<R, V>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt, fb);
 #pragma unroll
             for (int j = 0; j < V; j++) {
-                const R g = maxwell<R>(sp, x[j], y[j], w[j]);
+                const R g = maxwell<R>(sp, x[j], y[j], w);
                 if (s[j] < -k.tie) {
                     gin += s[j] * g;
                 } else {
@@ -381,16 +428,16 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
         block_sum<3, R>(part, red, tot);
         const double rho_w = -double(k.c) * tot[0] / (double(k.c) * double(k.b) * tot[1] + tot[2]);
         const R rw = R(rho_w);
-        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS) {
+        VelWalk vw2(threadIdx.x * V, FACE_THREADS * V, m.nv);
+        for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS, vw2.next()) {
             const int q = gi * V;
-            R x[V], y[V], w[V], fb[V], o[V];
-            VIO<R, V>::xi(xi + 2 * q, x, y);
-            VIO<R, V>::ld(wq + q, w);
+            R x[V], y[V], fb[V], o[V];
+            VNodes<R, V>::get(vt, vw2, x, y);
             VIO<R, V>::ld(fbuf + q, fb);
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 const R s = x[j] * nx + y[j] * ny;
-                const R g = maxwell<R>(sp, x[j], y[j], w[j]);
+                const R g = maxwell<R>(sp, x[j], y[j], w);
                 o[j] = s < -k.tie ? s * (rw * g) : s * ((fb[j] + k.b * (rw * g)) * k.c);
             }
             VIO<R, V>::st(out + q, o);
@@ -405,18 +452,19 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
                                                           double *__restrict__ W, const R *__restrict__ flux,
                                                           R *__restrict__ fbp_next)
 {
-    step_dependency_wait();
     extern __shared__ __align__(16) unsigned char dyn[];
     R *Fbuf = reinterpret_cast<R *>(dyn);
+    __shared__ __align__(16) R vt[MAX_NV];
     __shared__ double red[32 * 4];
     __shared__ R sp[4];
     __shared__ const R *frow[MAXF];
     __shared__ R fsg[MAXF];
+    load_nodes<R>(vt, m);
+    step_dependency_wait();
     const int64_t c = blockIdx.x;
     const int Q = (int)m.Q;
     const DvmR<R> k(cf);
-    const R *xi = static_cast<const R *>(m.xi);
-    const R *wq = static_cast<const R *>(m.wq);
+    const R w = R(m.w_node);
     if (threadIdx.x < MAXF) {
         // the cell's faces in slot order: flux row and sign (a missing slot adds 0 x row 0)
         const int32_t v = m.cell_face[c * MAXF + threadIdx.x];
@@ -438,11 +486,12 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
         }
     };
     R p0 = R(0), p1 = R(0), p2 = R(0), p3 = R(0);
+    VelWalk vw(threadIdx.x * V, CELL_THREADS * V, m.nv);
 #pragma unroll 2
-    for (int gi = threadIdx.x; gi < Q / V; gi += CELL_THREADS) {
+    for (int gi = threadIdx.x; gi < Q / V; gi += CELL_THREADS, vw.next()) {
         const int q = gi * V;
         R x[V], y[V], F[V];
-        VIO<R, V>::xi(xi + 2 * q, x, y);
+        VNodes<R, V>::get(vt, vw, x, y);
         F_of(q, F);
         if (SMEM) VIO<R, V>::st(Fbuf + q, F);
 #pragma unroll
@@ -465,19 +514,19 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
     __syncthreads();
     const R rdtv = R(dtv);
     R *fr = f + c * m.Q;
+    VelWalk vw2(threadIdx.x * V, CELL_THREADS * V, m.nv);
 #pragma unroll 2
-    for (int gi = threadIdx.x; gi < Q / V; gi += CELL_THREADS) {
+    for (int gi = threadIdx.x; gi < Q / V; gi += CELL_THREADS, vw2.next()) {
         const int q = gi * V;
-        R x[V], y[V], w[V], F[V], fv[V];
-        VIO<R, V>::xi(xi + 2 * q, x, y);
-        VIO<R, V>::ld(wq + q, w);
+        R x[V], y[V], F[V], fv[V];
+        VNodes<R, V>::get(vt, vw2, x, y);
         VIO<R, V>::ld(fr + q, fv);
         if (SMEM) VIO<R, V>::ld(Fbuf + q, F);
         else F_of(q, F);
         R nb[V];
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            const R fe = maxwell<R>(sp, x[j], y[j], w[j]);
+            const R fe = maxwell<R>(sp, x[j], y[j], w);
             const R num = fv[j] - rdtv * F[j] + k.r * fe;
             fv[j] = sizeof(R) == 8 ? num / (R(1) + k.r) : num * k.inv1r;
             nb[j] = k.a * fv[j] + k.b * fe;       // the next step's fbar+ (Eq. fbarplus), as k_dvm_fbp forms it
@@ -492,12 +541,19 @@ template <class R>
 __global__ void __launch_bounds__(DVM_THREADS) k_dvm_init(const DvmMesh m, const double *__restrict__ W,
                                                           R *__restrict__ f)
 {
+    __shared__ __align__(16) R vt[MAX_NV];
     __shared__ R sp[4];
+    load_nodes<R>(vt, m);
     const int64_t c = blockIdx.x, Q = m.Q;
     if (threadIdx.x == 0) set_sp<R>(sp, max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]));
     __syncthreads();
-    const R *xi = static_cast<const R *>(m.xi), *wq = static_cast<const R *>(m.wq);
-    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) f[c * Q + q] = maxwell<R>(sp, xi[2 * q], xi[2 * q + 1], wq[q]);
+    const R w = R(m.w_node);
+    VelWalk vw(threadIdx.x, blockDim.x, m.nv);
+    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x, vw.next()) {
+        R x[1], y[1];
+        VNodes<R, 1>::get(vt, vw, x, y);
+        f[c * Q + q] = maxwell<R>(sp, x[0], y[0], w);
+    }
 }
 
 // Largest per-velocity buffer kept in shared memory (bytes).
@@ -522,7 +578,10 @@ cudaError_t prepare_pv(int64_t Q)
     return e;
 }
 
-template <class R> cudaError_t prepare_p(int64_t Q) { return Q % 4 == 0 ? prepare_pv<R, 4>(Q) : prepare_pv<R, 1>(Q); }
+template <class R> cudaError_t prepare_p(int64_t Q, int nv)
+{
+    return nv % 4 == 0 ? prepare_pv<R, 4>(Q) : prepare_pv<R, 1>(Q);
+}
 
 template <class R, int V>
 cudaError_t step_pv(const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp, void *flux,
@@ -556,8 +615,8 @@ cudaError_t step_p(const DvmMesh &m, const Coefs &c, double RTw, void *f, double
                    bool fbp_ready, cudaStream_t st)
 {
     if (m.nc <= 0) return cudaSuccess;
-    return m.Q % 4 == 0 ? step_pv<R, 4>(m, c, RTw, f, W, fbp, flux, fbp_ready, st)
-                        : step_pv<R, 1>(m, c, RTw, f, W, fbp, flux, fbp_ready, st);
+    return m.nv % 4 == 0 ? step_pv<R, 4>(m, c, RTw, f, W, fbp, flux, fbp_ready, st)
+                         : step_pv<R, 1>(m, c, RTw, f, W, fbp, flux, fbp_ready, st);
 }
 
 }  // namespace
@@ -569,9 +628,9 @@ cudaError_t launch_dvm_step(int prec, const DvmMesh &m, const Coefs &c, double R
                           : step_p<float>(m, c, RTw, f, W, fbp, flux, fbp_ready, st);
 }
 
-cudaError_t prepare_dvm(int prec, int64_t Q)
+cudaError_t prepare_dvm(int prec, int64_t Q, int nv)
 {
-    return prec == P_FP64 ? prepare_p<double>(Q) : prepare_p<float>(Q);
+    return prec == P_FP64 ? prepare_p<double>(Q, nv) : prepare_p<float>(Q, nv);
 }
 
 cudaError_t launch_dvm_init(int prec, const DvmMesh &m, const double *W, void *f, cudaStream_t st)

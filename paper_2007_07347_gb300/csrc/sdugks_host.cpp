@@ -1866,18 +1866,11 @@ extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *
         const double g6[6] = {F.nl[2 * f], F.nl[2 * f + 1], F.ro[2 * f], F.ro[2 * f + 1], F.rk[2 * f], F.rk[2 * f + 1]};
         std::copy(g6, g6 + 6, &fgeo[(size_t)f * 6]);
     }
-    // velocity nodes: midpoints of a uniform nv x nv partition of [-vmax, vmax]^2, x fastest
-    std::vector<double> xi((size_t)Q * 2), wq(Q);
-    {
-        const double h = 2.0 * prm->vmax / prm->nv;
-        for (int i = 0; i < prm->nv; i++)
-            for (int j = 0; j < prm->nv; j++) {
-                const size_t q = (size_t)j + (size_t)prm->nv * i;
-                xi[2 * q] = -prm->vmax + (j + 0.5) * h;
-                xi[2 * q + 1] = -prm->vmax + (i + 0.5) * h;
-                wq[q] = h * h;
-            }
-    }
+    // velocity nodes: midpoints of a uniform nv x nv partition of [-vmax, vmax]^2; node
+    // q = j + nv i (x fastest) is (vn[j], vn[i]) with weight h^2
+    const double h = 2.0 * prm->vmax / prm->nv;
+    std::vector<double> vn(prm->nv);
+    for (int j = 0; j < prm->nv; j++) vn[j] = -prm->vmax + (j + 0.5) * h;
 
     sdugks_dvm *d = new (std::nothrow) sdugks_dvm;
     if (!d) return fail(SDUGKS_ERR_OOM, "host allocation failed");
@@ -1901,8 +1894,7 @@ extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *
         d->dm.face_own = A.take<int32_t>(nf);
         d->dm.face_nbr = A.take<int32_t>(nf);
         d->dm.face_geo = A.take<char>(fgeo.size() * rs);
-        d->dm.xi = A.take<char>(xi.size() * rs);
-        d->dm.wq = A.take<char>(wq.size() * rs);
+        d->dm.vnode = A.take<char>(vn.size() * rs);
     };
     Arena A0;
     layout(A0);
@@ -1917,6 +1909,8 @@ extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *
     Arena A{d->dmem, 0, d->dbytes};
     layout(A);
     d->dm.nc = n; d->dm.nf = nf; d->dm.Q = Q;
+    d->dm.nv = prm->nv;
+    d->dm.w_node = h * h;
     auto conv = [&](const std::vector<double> &v) {
         std::vector<char> o(v.size() * rs);
         if (rs == 8) std::memcpy(o.data(), v.data(), o.size());
@@ -1931,7 +1925,7 @@ extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *
         const cudaError_t ee = cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
         if (ee != cudaSuccess && rc2 == SDUGKS_OK) rc2 = fail(SDUGKS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ee));
     };
-    const auto gcd = conv(cd), gai = conv(ainv), gfg = conv(fgeo), gxi = conv(xi), gwq = conv(wq);
+    const auto gcd = conv(cd), gai = conv(ainv), gfg = conv(fgeo), gvn = conv(vn);
     up(d->dm.cell_face, cface.data(), cface.size() * 4, "upload cell faces");
     up(d->dm.cell_nb, cnb.data(), cnb.size() * 4, "upload neighbours");
     up(d->dm.cell_d, gcd.data(), gcd.size(), "upload offsets");
@@ -1940,11 +1934,10 @@ extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *
     up(d->dm.face_own, fown.data(), fown.size() * 4, "upload owners");
     up(d->dm.face_nbr, fnbr.data(), fnbr.size() * 4, "upload neighbours");
     up(d->dm.face_geo, gfg.data(), gfg.size(), "upload face geometry");
-    up(d->dm.xi, gxi.data(), gxi.size(), "upload velocity nodes");
-    up(d->dm.wq, gwq.data(), gwq.size(), "upload weights");
+    up(d->dm.vnode, gvn.data(), gvn.size(), "upload velocity nodes");
     if (rc2 == SDUGKS_OK) {
         cudaError_t ee = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
-        if (ee == cudaSuccess) ee = prepare_dvm(d->prec, Q);
+        if (ee == cudaSuccess) ee = prepare_dvm(d->prec, Q, prm->nv);
         if (ee != cudaSuccess) rc2 = fail(SDUGKS_ERR_CUDA, "stream / kernel attributes: %s", cudaGetErrorString(ee));
     }
     if (rc2) { sdugks_dvm_destroy(d); return rc2; }

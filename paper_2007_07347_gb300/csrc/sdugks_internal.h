@@ -188,8 +188,10 @@ struct DvmMesh {
     const double *dtV;         // [nc] dt / V
     const int32_t *face_own, *face_nbr;   // face_nbr: cell, or -1 - patch
     const void *face_geo;      // [nf][6] n l (first -> second side), x_f - x_first, x_f - x_second
-    const void *xi;            // [Q][2] velocity nodes
-    const void *wq;            // [Q] quadrature weights
+    // velocity q = j + nv i (x fastest) sits at (vnode[j], vnode[i]) with weight w_node
+    const void *vnode;         // [nv] nodes of one axis (compute precision)
+    int32_t nv;
+    double w_node;
 };
 constexpr int32_t DVM_SECOND = int32_t(0x40000000);
 constexpr int DVM_THREADS = 256;
@@ -198,7 +200,7 @@ constexpr int DVM_THREADS = 256;
 cudaError_t launch_dvm_step(int prec, const DvmMesh &m, const Coefs &c, double RTw, void *f, double *W, void *fbp,
                             void *flux, bool fbp_ready, cudaStream_t st);
 cudaError_t launch_dvm_init(int prec, const DvmMesh &m, const double *W, void *f, cudaStream_t st);
-cudaError_t prepare_dvm(int prec, int64_t Q);   // kernel attributes on the current device
+cudaError_t prepare_dvm(int prec, int64_t Q, int nv);   // kernel attributes on the current device
 
 // state conversions between the caller's cell-major FP64 layout (user cell order)
 // and the internal SoA layout: the q-th listed cell is user cell perm[q] stored at
