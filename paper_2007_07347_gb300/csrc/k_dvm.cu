@@ -55,12 +55,15 @@ struct MaxP {
 };
 __device__ __forceinline__ MaxP max_params(double rho, double mx, double my, double rE)
 {
+    // two divisions (one thread runs this while its block waits)
     MaxP p;
-    p.ux = mx / rho;
-    p.uy = my / rho;
-    const double RT = rE / rho - 0.5 * (p.ux * p.ux + p.uy * p.uy);
-    p.pre = rho / (2.0 * 3.14159265358979323846 * RT);
-    p.inv2RT = 1.0 / (2.0 * RT);
+    const double ir = 1.0 / rho;
+    p.ux = mx * ir;
+    p.uy = my * ir;
+    const double RT = rE * ir - 0.5 * (p.ux * p.ux + p.uy * p.uy);
+    const double iRT = 1.0 / RT;
+    p.pre = rho * iRT * (0.5 / 3.14159265358979323846);
+    p.inv2RT = 0.5 * iRT;
     return p;
 }
 
@@ -445,8 +448,17 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
     }
 }
 
+// Ask L2 for a whole row at once (a hint; the row's start and length are multiples of 16
+// bytes).  Later iterations of the walk over the row then find it in L2.
+__device__ __forceinline__ void prefetch_row_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // SMEM: the cell's flux sum F (Q values) is kept in shared memory between the two
-// passes; otherwise it is summed again from the face fluxes.
+// passes; otherwise it is summed again from the face fluxes.  Cells are taken in
+// reverse order: the face kernel writes the fluxes in cell order, so the fluxes read
+// first were written last and are still in L2.
 template <class R, bool SMEM, int V>
 __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, const Coefs cf, R *__restrict__ f,
                                                           double *__restrict__ W, const R *__restrict__ flux,
@@ -461,7 +473,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
     __shared__ R fsg[MAXF];
     load_nodes<R>(vt, m);
     step_dependency_wait();
-    const int64_t c = blockIdx.x;
+    const int64_t c = m.nc - 1 - (int64_t)blockIdx.x;
     const int Q = (int)m.Q;
     const DvmR<R> k(cf);
     const R w = R(m.w_node);
@@ -472,6 +484,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
         const int32_t id = v >= 0 ? (v & (DVM_SECOND - 1)) : (v0 & (DVM_SECOND - 1));
         frow[threadIdx.x] = flux + (int64_t)id * m.Q;
         fsg[threadIdx.x] = v < 0 ? R(0) : ((v & DVM_SECOND) ? R(-1) : R(1));
+        if (V == 4 && v >= 0) prefetch_row_l2(flux + (int64_t)id * m.Q, (uint32_t)(m.Q * sizeof(R)));
+    } else if (V == 4 && threadIdx.x == 32) {
+        prefetch_row_l2(f + c * m.Q, (uint32_t)(m.Q * sizeof(R)));
     }
     __syncthreads();
     auto F_of = [&](int q, R F[V]) {

@@ -1824,6 +1824,25 @@ extern "C" int sdugks_dvm_create(const sdugks_mesh *m, const sdugks_dvm_params *
     const int64_t n = m->nc, nf = F.nf, Q = (int64_t)prm->nv * prm->nv;
     for (int64_t f = 0; f < nf; f++)
         if (F.own[f] == F.nbr[f]) return fail(SDUGKS_ERR_INVALID_MESH, "periodic pair joins a cell to itself");
+    {
+        // faces in the order of their first cell: the face kernel then writes the fluxes
+        // in cell order, and the cell kernel, which walks the cells backwards, first reads
+        // the fluxes written last (still in L2)
+        std::vector<int64_t> ord(nf);
+        std::iota(ord.begin(), ord.end(), int64_t(0));
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return F.own[a] < F.own[b]; });
+        Faces G;
+        G.nf = nf;
+        G.own.resize(nf); G.nbr.resize(nf); G.nl.resize(2 * nf); G.ro.resize(2 * nf); G.rk.resize(2 * nf);
+        for (int64_t i = 0; i < nf; i++) {
+            const int64_t f = ord[i];
+            G.own[i] = F.own[f]; G.nbr[i] = F.nbr[f];
+            for (int d = 0; d < 2; d++) {
+                G.nl[2 * i + d] = F.nl[2 * f + d]; G.ro[2 * i + d] = F.ro[2 * f + d]; G.rk[2 * i + d] = F.rk[2 * f + d];
+            }
+        }
+        F = std::move(G);
+    }
 
     // cell slots in ascending merged face id; LLSR neighbours, offsets and inverse
     std::vector<int32_t> cface((size_t)n * MAXF, -1), cnb((size_t)n * MAXF, -1);
