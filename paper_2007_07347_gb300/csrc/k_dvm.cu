@@ -202,26 +202,31 @@ template <> struct VNodes<double, 4> {
     }
 };
 
-// fbar+ of a cell's velocities q .. q+V-1 plus (r - xi dt) . sigma, sigma the cell's LLSR
-// gradient.  rows[0] is the cell's fbar+ row, rows[1..4] its neighbours' (a missing
-// neighbour repeats the cell's own row with a zero offset, which adds nothing); one
-// vector load per row.
+// The values at q .. q+V-1 of a side's 1 + MAXF rows: rows[0] is the cell's fbar+ row,
+// rows[1..4] its neighbours' (a missing neighbour repeats the cell's own row with a zero
+// offset, which adds nothing); one vector load per row.
 template <class R, int V>
-__device__ __forceinline__ void reconstruct_v(const R *const *rows, const R *d, const R *ai, int q, R rx, R ry,
-                                              const R *xx, const R *xy, R dt, R out[V])
+__device__ __forceinline__ void load_rows(const R *const *rows, int q, R v[1 + MAXF][V])
 {
-    R v0[V], bx[V], by[V];
-    VIO<R, V>::ld(rows[0] + q, v0);
+#pragma unroll
+    for (int k = 0; k < 1 + MAXF; k++) VIO<R, V>::ld(rows[k] + q, v[k]);
+}
+
+// fbar+ of a cell's velocities plus (r - xi dt) . sigma, sigma the cell's LLSR gradient,
+// from the row values of load_rows.
+template <class R, int V>
+__device__ __forceinline__ void reconstruct_vals(const R v[1 + MAXF][V], const R *d, const R *ai, R rx, R ry,
+                                                 const R *xx, const R *xy, R dt, R out[V])
+{
+    R bx[V], by[V];
 #pragma unroll
     for (int j = 0; j < V; j++) { bx[j] = R(0); by[j] = R(0); }
 #pragma unroll
     for (int sl = 0; sl < MAXF; sl++) {
-        R vn[V];
-        VIO<R, V>::ld(rows[1 + sl] + q, vn);
         const R dx = d[2 * sl], dy = d[2 * sl + 1];
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            const R dv = vn[j] - v0[j];
+            const R dv = v[1 + sl][j] - v[0][j];
             bx[j] += dx * dv;
             by[j] += dy * dv;
         }
@@ -229,7 +234,7 @@ __device__ __forceinline__ void reconstruct_v(const R *const *rows, const R *d, 
 #pragma unroll
     for (int j = 0; j < V; j++) {
         const R sx = ai[0] * bx[j] + ai[1] * by[j], sy = ai[1] * bx[j] + ai[2] * by[j];
-        out[j] = v0[j] + (rx - xx[j] * dt) * sx + (ry - xy[j] * dt) * sy;
+        out[j] = v[0][j] + (rx - xx[j] * dt) * sx + (ry - xy[j] * dt) * sy;
     }
 }
 
@@ -237,18 +242,17 @@ __device__ __forceinline__ void reconstruct_v(const R *const *rows, const R *d, 
 // instructions (FFMA2/FMUL2, each lane rounded as the scalar operation; differences as
 // FFMA2 with -1).
 template <>
-__device__ __forceinline__ void reconstruct_v<float, 4>(const float *const *rows, const float *d, const float *ai, int q,
-                                                        float rx, float ry, const float *xx, const float *xy, float dt,
-                                                        float out[4])
+__device__ __forceinline__ void reconstruct_vals<float, 4>(const float v[1 + MAXF][4], const float *d, const float *ai,
+                                                           float rx, float ry, const float *xx, const float *xy,
+                                                           float dt, float out[4])
 {
-    const float4 a = *reinterpret_cast<const float4 *>(rows[0] + q);
-    const float2 v01 = make_float2(a.x, a.y), v23 = make_float2(a.z, a.w), m1 = make_float2(-1.0f, -1.0f);
+    const float2 v01 = make_float2(v[0][0], v[0][1]), v23 = make_float2(v[0][2], v[0][3]), m1 = make_float2(-1.0f, -1.0f);
     float2 bx01 = make_float2(0.f, 0.f), bx23 = bx01, by01 = bx01, by23 = bx01;
 #pragma unroll
     for (int sl = 0; sl < MAXF; sl++) {
-        const float4 b = *reinterpret_cast<const float4 *>(rows[1 + sl] + q);
         const float2 dx = make_float2(d[2 * sl], d[2 * sl]), dy = make_float2(d[2 * sl + 1], d[2 * sl + 1]);
-        const float2 dv01 = __ffma2_rn(v01, m1, make_float2(b.x, b.y)), dv23 = __ffma2_rn(v23, m1, make_float2(b.z, b.w));
+        const float2 dv01 = __ffma2_rn(v01, m1, make_float2(v[1 + sl][0], v[1 + sl][1]));
+        const float2 dv23 = __ffma2_rn(v23, m1, make_float2(v[1 + sl][2], v[1 + sl][3]));
         bx01 = __ffma2_rn(dx, dv01, bx01); bx23 = __ffma2_rn(dx, dv23, bx23);
         by01 = __ffma2_rn(dy, dv01, by01); by23 = __ffma2_rn(dy, dv23, by23);
     }
@@ -261,6 +265,15 @@ __device__ __forceinline__ void reconstruct_v<float, 4>(const float *const *rows
     const float2 o01 = __ffma2_rn(ey01, sy01, __ffma2_rn(ex01, sx01, v01));
     const float2 o23 = __ffma2_rn(ey23, sy23, __ffma2_rn(ex23, sx23, v23));
     out[0] = o01.x; out[1] = o01.y; out[2] = o23.x; out[3] = o23.y;
+}
+
+template <class R, int V>
+__device__ __forceinline__ void reconstruct_v(const R *const *rows, const R *d, const R *ai, int q, R rx, R ry,
+                                              const R *xx, const R *xy, R dt, R out[V])
+{
+    R v[1 + MAXF][V];
+    load_rows<R, V>(rows, q, v);
+    reconstruct_vals<R, V>(v, d, ai, rx, ry, xx, xy, dt, out);
 }
 
 template <class R, int V>
@@ -317,7 +330,7 @@ __device__ __forceinline__ void load_side(SideData<R> &sd, const DvmMesh &m, con
 // SMEM: the interface distribution of the face between the two passes over the
 // velocities stays in shared memory (Q values); otherwise in the flux array itself.
 template <class R, bool SMEM, int V>
-__global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+__global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 2 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -359,8 +372,13 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 3 : 1) k_dvm_fa
                 needB |= !(s[j] > k.tie);
                 fa[j] = R(0); fo[j] = R(0);
             }
-            if (needA) reconstruct_v<R, V>(sd[0].rows, sd[0].d, sd[0].ai, q, rox, roy, x, y, k.dt, fa);
-            if (needB) reconstruct_v<R, V>(sd[1].rows, sd[1].d, sd[1].ai, q, rkx, rky, x, y, k.dt, fo);
+            // both sides' loads before either side's arithmetic: a warp whose lanes need
+            // different sides waits for memory once
+            R va[1 + MAXF][V], vb[1 + MAXF][V];
+            if (needA) load_rows<R, V>(sd[0].rows, q, va);
+            if (needB) load_rows<R, V>(sd[1].rows, q, vb);
+            if (needA) reconstruct_vals<R, V>(va, sd[0].d, sd[0].ai, rox, roy, x, y, k.dt, fa);
+            if (needB) reconstruct_vals<R, V>(vb, sd[1].d, sd[1].ai, rkx, rky, x, y, k.dt, fo);
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 fb[j] = s[j] > k.tie ? fa[j] : (s[j] < -k.tie ? fo[j] : R(0.5) * (fa[j] + fo[j]));
