@@ -503,8 +503,6 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
         frow[threadIdx.x] = flux + (int64_t)id * m.Q;
         fsg[threadIdx.x] = v < 0 ? R(0) : ((v & DVM_SECOND) ? R(-1) : R(1));
         if (V == 4 && v >= 0) prefetch_row_l2(flux + (int64_t)id * m.Q, (uint32_t)(m.Q * sizeof(R)));
-    } else if (V == 4 && threadIdx.x == 32) {
-        prefetch_row_l2(f + c * m.Q, (uint32_t)(m.Q * sizeof(R)));
     }
     __syncthreads();
     auto F_of = [&](int q, R F[V]) {
@@ -532,6 +530,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
             p0 += F[j]; p1 += x[j] * F[j]; p2 += y[j] * F[j]; p3 += R(0.5) * (x[j] * x[j] + y[j] * y[j]) * F[j];
         }
     }
+    if (V == 4 && threadIdx.x == 32) prefetch_row_l2(f + c * m.Q, (uint32_t)(m.Q * sizeof(R)));
     R part[4] = {p0, p1, p2, p3};
     double M[4];
     block_sum<4, R>(part, red, M);
