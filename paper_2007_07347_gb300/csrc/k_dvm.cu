@@ -30,9 +30,10 @@ namespace {
 
 // threads per CTA of the three step kernels (a CTA walks its cell's or face's
 // velocities).  On the 40 x 40 x 100^2 micro cavity (GB300) 384 or 512 threads for the
-// cell kernel, 512 or 1024 for fbar+ and 384 for the face kernel measured the same or
-// slower than 256.
-constexpr int FBP_THREADS = 256, FACE_THREADS = 256, CELL_THREADS = 256;
+// cell kernel and 512 or 1024 for fbar+ measured the same or slower than 256.  The face
+// kernel (128 registers) runs four CTAs of 128 threads per SM: 14 % faster than two of
+// 256, since a CTA waiting at the barrier before its second pass then holds fewer warps.
+constexpr int FBP_THREADS = 256, FACE_THREADS = 128, CELL_THREADS = 256;
 
 template <class R> struct DvmR;
 template <> struct DvmR<double> {
@@ -330,7 +331,7 @@ __device__ __forceinline__ void load_side(SideData<R> &sd, const DvmMesh &m, con
 // SMEM: the interface distribution of the face between the two passes over the
 // velocities stays in shared memory (Q values); otherwise in the flux array itself.
 template <class R, bool SMEM, int V>
-__global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 2 : 1) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
+__global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 4 : 2) k_dvm_face(const DvmMesh m, const Coefs cf, double RTw,
                                                           const R *__restrict__ fbp, R *__restrict__ flux)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
