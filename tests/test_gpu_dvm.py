@@ -61,8 +61,9 @@ def test_fp64_cavity_matches_oracle(tau):
 
 @pytest.mark.parametrize("nv", [9, 11])
 def test_fp64_odd_velocity_grid_matches_oracle(nv):
-    """Q = nv^2 not a multiple of 4: the kernels take one velocity per thread at a time
-    (even grids use 16-byte vectors of 4)."""
+    """Odd nv: the kernels take one velocity per thread at a time (nv a multiple of 4
+    takes 16-byte vectors of 4 velocities; the nv = 10 channel below is even but also
+    takes one at a time)."""
     m, bcs = _cavity_jittered(5)
     d, st = _run(m, bcs, nv, 2.0, 0.5, 0.1, 0.01, 40, "fp64")
     f, W = d.get_state()
