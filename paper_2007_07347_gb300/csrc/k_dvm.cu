@@ -4,8 +4,8 @@
 // The mesh is small and the velocity grid large (10^4 nodes), so the work is spread
 // over velocities: one CTA per cell or per face walks all Q velocities with its
 // threads, and the moments a step needs (the interface W of every face, the
-// macroscopic flux of every cell) are block reductions in a fixed order.  Three
-// launches per step:
+// macroscopic flux of every cell) are block reductions in a fixed order.  Two launches
+// per step (k_dvm_fbp only when the state is new):
 //   k_dvm_fbp   per cell: fbar+ = a f + b feq(W^n)                      (Eq. fbarplus)
 //   k_dvm_face  per face: characteristic reconstruction from the upwind cell with its
 //               LLSR gradient evaluated on the spot (Eqs. fbpsource, fbar), interface
@@ -13,6 +13,9 @@
 //               diffuse scattering; writes xi . n l f_b per face and velocity
 //   k_dvm_cell  per cell: F = sum of its faces' fluxes (Eq. MesoFlux), its moments
 //               (Eq. MacroFlux) update W in FP64 (Eq. MacroUpdate), then f (Eq. fn+1)
+//               and the next step's fbar+ (Eq. fbarplus with W^{n+1})
+// The faces are numbered in the order of their first cell and the cell kernel takes the
+// cells backwards, so each kernel first reads what the other wrote last (still in L2).
 // W = (rho, rho u, rho E) per cell in FP64; f and the scratch arrays in the compute
 // precision.  When nv is a multiple of 4 every thread takes 4 consecutive velocities at
 // a time with 16-byte vector loads and stores (V = 4); otherwise one (V = 1).  The
