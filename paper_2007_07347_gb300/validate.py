@@ -1,14 +1,13 @@
 """Full-length validation runs of the configurations, with the tolerances of the
 scope stated beside each measured number.
 
-    python -m paper_2007_07347_gb300.validate cavity   # 256^2 Re 1000, 20k FP32 steps vs the FP64 oracle
     python -m paper_2007_07347_gb300.validate cylinder # 512x256 O-mesh Re 40 to steady state, FP64/FP32/bf16
     python -m paper_2007_07347_gb300.validate cylinder fp16dev   # the same for the listed storages only
     python -m paper_2007_07347_gb300.validate shedding # 512x256 O-mesh Re 60/80/100: St and mean Cd
     python -m paper_2007_07347_gb300.validate plate    # laminar flat plate Re_L 1e5: Cd against Blasius
 
-Writes one JSON line per case to stdout.  The oracle (test infrastructure) is used
-only as the reference of the cavity comparison.
+Writes one JSON line per case to stdout.  The comparison of the 256^2 cavity with the
+FP64 oracle is test infrastructure and lives with the tests (tests/validate_cavity.py).
 """
 import json
 import math
@@ -16,46 +15,6 @@ import sys
 import time
 
 import numpy as np
-
-
-def cavity(steps=20000):
-    import torch
-    import oracle as O
-    from . import meshes as M
-    from . import sdugks as S
-    torch.cuda.set_device(0)
-    case = M.cavity(256)
-    s = S.Solver.from_case(case, "fp32").init()
-    _, m0 = s.residual()
-    t0 = time.perf_counter()
-    s.step(steps)
-    rho, u = s.macros()
-    t_gpu = time.perf_counter() - t0
-    _, m1 = s.residual()
-    st = O.init(case.mesh.n_cells)
-    vol = O.geometry(case.mesh, case.bcs)["vol"]
-    mo0 = float(vol @ st.W[:, 0])
-    t0 = time.perf_counter()
-    O.run(case, st, steps)
-    t_cpu = time.perf_counter() - t0
-    mo1 = float(vol @ st.W[:, 0])
-    U = case.meta["U"]
-    n = 256
-    ug, uo = u.reshape(n, n, 2), st.u.reshape(n, n, 2)
-    # vertical centreline u(y) at x = L/2 and horizontal centreline v(x) at y = L/2
-    # (mean of the two cell columns/rows either side of the centre line)
-    cu_g = 0.5 * (ug[:, n // 2 - 1, 0] + ug[:, n // 2, 0])
-    cu_o = 0.5 * (uo[:, n // 2 - 1, 0] + uo[:, n // 2, 0])
-    cv_g = 0.5 * (ug[n // 2 - 1, :, 1] + ug[n // 2, :, 1])
-    cv_o = 0.5 * (uo[n // 2 - 1, :, 1] + uo[n // 2, :, 1])
-    out = {"case": "cavity 256x256 Re 1000 lid 0.1, FP32 vs FP64 oracle", "steps": steps,
-           "rel_l2_u": float(np.sqrt(np.sum((u - st.u) ** 2) / np.sum(st.u ** 2))), "tol_rel_l2_u": 1e-4,
-           "centreline_max_err_over_U": float(max(np.abs(cu_g - cu_o).max(), np.abs(cv_g - cv_o).max()) / U),
-           "tol_centreline_over_U": 1e-4,
-           "mass_drift_gpu": (m1 - m0) / m0, "mass_drift_oracle": (mo1 - mo0) / mo0,
-           "max_rho_diff": float(np.abs(rho - st.W[:, 0]).max()),
-           "gpu_s": t_gpu, "oracle_s": t_cpu, "oracle_threads": O.set_threads(0)}
-    print(json.dumps(out), flush=True)
 
 
 def cylinder(max_steps=600000, interval=5000, target=1e-7, precisions=("fp64", "fp32", "bf16dev")):
@@ -214,10 +173,10 @@ def plate():
 
 
 if __name__ == "__main__":
-    what = sys.argv[1] if len(sys.argv) > 1 else "cavity"
+    what = sys.argv[1] if len(sys.argv) > 1 else "cylinder"
     if what == "shedding" and len(sys.argv) > 2:
         shedding(tuple(float(x) for x in sys.argv[2:]))
     elif what == "cylinder" and len(sys.argv) > 2:
         cylinder(precisions=tuple(sys.argv[2:]))           # e.g. cylinder fp16dev bf16dev
     else:
-        {"cavity": cavity, "cylinder": cylinder, "shedding": shedding, "plate": plate}[what]()
+        {"cylinder": cylinder, "shedding": shedding, "plate": plate}[what]()
