@@ -203,3 +203,23 @@ def test_missing_library_fails_loudly(monkeypatch):
             S.lib()
     finally:
         S._lib = saved
+
+
+def test_product_code_does_not_use_the_oracle():
+    """The package and its C/CUDA sources never import, link or call the oracle (only the
+    tests, smoke() and bench.py's CPU arms do)."""
+    import ast
+    import pathlib
+    root = pathlib.Path(__file__).resolve().parent.parent
+    pkg = root / "paper_2007_07347_gb300"
+    for py in pkg.rglob("*.py"):
+        for node in ast.walk(ast.parse(py.read_text())):
+            names = []
+            if isinstance(node, ast.Import):
+                names = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                names = [node.module or ""]
+            assert not any(n == "oracle" or n.startswith("oracle.") for n in names), py
+    for src in list((pkg / "csrc").iterdir()) + list((root / "include").iterdir()):
+        if src.suffix in (".h", ".cuh", ".cu", ".cpp"):
+            assert "oracle" not in src.read_text().lower(), src
