@@ -470,11 +470,13 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 4 : 2) k_dvm_fa
     }
 }
 
-// Ask L2 for a whole row at once (a hint; the row's start and length are multiples of 16
-// bytes).  Later iterations of the walk over the row then find it in L2.
+// Ask L2 for a row at once (a hint; the row's start and length are multiples of 16
+// bytes).  Later iterations of the walk over the row then find it in L2.  At most the
+// first 64 KB of a row, so that the rows of large velocity grids do not flood L2.
 __device__ __forceinline__ void prefetch_row_l2(const void *p, uint32_t bytes)
 {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+    const uint32_t n = bytes < 65536u ? bytes : 65536u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
 }
 
 // SMEM: the cell's flux sum F (Q values) is kept in shared memory between the two

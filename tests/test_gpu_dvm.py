@@ -71,6 +71,29 @@ def test_fp64_odd_velocity_grid_matches_oracle(nv):
     assert relmax(W, st.W) <= 1e-12
 
 
+@pytest.mark.parametrize("nv", [144, 145])
+def test_fp64_rows_beyond_the_shared_buffer_match_oracle(nv):
+    """Q x 8 bytes above the kernels' 160 KB shared-memory buffer: the face and cell
+    kernels keep the interface values and flux sums in global memory instead (nv = 144
+    with vectors of 4 velocities, 145 with one)."""
+    m, bcs = _cavity_jittered(4)
+    d, st = _run(m, bcs, nv, 2.0, 0.5, 0.1, 0.01, 12, "fp64")
+    f, W = d.get_state()
+    assert relmax(f, st.f) <= 1e-12
+    assert relmax(W, st.W) <= 1e-12
+    assert np.abs(st.u).max() > 1e-3
+
+
+def test_fp32_rows_beyond_the_shared_buffer_match_oracle():
+    """FP32 rows above the 160 KB buffer (nv = 204, Q x 4 bytes = 166 KB)."""
+    m, bcs = _cavity_jittered(4)
+    d, st = _run(m, bcs, 204, 2.0, 0.5, 0.1, 0.01, 30, "fp32")
+    rho, u, RT = d.macros()
+    assert np.sqrt(np.sum((u - st.u) ** 2) / np.sum(st.u ** 2)) <= 1e-4
+    assert np.abs(rho - st.rho).max() <= 1e-5
+    assert np.abs(RT - st.RT).max() <= 1e-5
+
+
 def test_fp64_periodic_hybrid_channel_matches_oracle():
     m, bcs = _channel()
     rng = np.random.default_rng(3)
