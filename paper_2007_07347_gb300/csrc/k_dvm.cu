@@ -50,9 +50,6 @@ template <> struct DvmR<float> {
                                                tie(k.ftie), inv1r(k.finv1r) {}
 };
 
-__device__ __forceinline__ double dexp(double x) { return exp(x); }
-__device__ __forceinline__ float dexp(float x) { return expf(x); }
-
 // Maxwellian parameters of one state, computed once per CTA in FP64.
 struct MaxP {
     double pre, ux, uy, inv2RT;
