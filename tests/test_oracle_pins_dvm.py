@@ -4,9 +4,11 @@ The rarefied variant runs the same scheme on a Q-node velocity grid with the
 Maxwellian of Eq. Feq and diffuse walls (Sec. III).  Pinned against: closed-form
 truncated Gaussian integrals of the grid (error bound of the midpoint rule), the
 uniform equilibrium as a fixed point, exact conservation of mass, momentum and
-energy on periodic meshes, the zero mass flux of a diffuse wall, and the
-collisionless Couette flow between diffuse plates, whose steady state is known in
-closed form on any velocity grid.
+energy on periodic meshes, the zero mass flux of a diffuse wall, the collisionless
+Couette flow between diffuse plates, whose steady state is known in closed form on any
+velocity grid, and one collisionless step of a quadratic field, which fixes the
+characteristic reconstruction (the sign of its xi dt term, the upwind side, the
+gradient) and the sign of the flux balance.
 """
 import math
 
@@ -117,3 +119,34 @@ def test_collisionless_couette_closed_form():
     np.testing.assert_allclose(st.W[:, 1], (xi[:, 0] * f_exact).sum(), rtol=1e-9)
     np.testing.assert_allclose(st.W[:, 2], 0.0, atol=1e-12)
     assert abs(st.W[:, 0].mean() - mass0) < 1e-12
+
+
+def test_one_collisionless_step_of_a_quadratic_field():
+    """Characteristic reconstruction (Eqs. fbpsource, fbar) and flux balance of one step
+    in the free-molecular limit (tau -> infinity: fbar+ = f, f_b = fbar, f^{n+1} = f^n -
+    dt/V F).  For f_q = w_q (x^2 + y^2) on a uniform mesh of unit cells, a cell two or
+    more cells from the walls sees only exact central LLSR gradients (2x, 2y), and the
+    upwind face values fbar = f_u + (x_f - x_u - xi dt) . sigma_u give, per axis,
+    F / V = xi_x (2 x - 2 xi_x dt): the step leaves
+        w_q [x^2 + y^2 - 2 dt (xi_x x + xi_y y) + 2 dt^2 (xi_x^2 + xi_y^2)]
+    (the exact transport f(x - xi dt) has dt^2 where the scheme has 2 dt^2).  A flipped
+    sign of xi dt in the reconstruction turns the last term into -2 dt^2; no gradient,
+    a downwind side or a flux sign error change the first-order term."""
+    nv, dt, n = 8, 0.1, 8
+    xi, w = O.dvm_grid(nv, 2.0)
+    m = M.cartesian(n, n, float(n), float(n))
+    bcs = [(0, M.BC_WALL, (0, 0, 0)), (1, M.BC_WALL, (0, 0, 0)), (3, M.BC_WALL, (0, 0, 0)),
+           (2, M.BC_MOVING_WALL, (0.1, 0, 0))]
+    st = O.dvm_init(m.n_cells, xi, w, RT0=0.5)
+    xy = m.meta["cell_xy_nominal"]
+    x, y = xy[:, 0], xy[:, 1]
+    st.f[:] = w[None, :] * (x * x + y * y)[:, None]
+    O.dvm_run(m, bcs, st, xi, w, 0.5, tau=1e12, dt=dt, n_steps=1)
+    i, j = m.meta["cell_i"], m.meta["cell_j"]
+    inner = (i >= 2) & (i <= n - 3) & (j >= 2) & (j <= n - 3)
+    ex = w[None, :] * ((x * x + y * y)[:, None]
+                       - 2 * dt * (xi[None, :, 0] * x[:, None] + xi[None, :, 1] * y[:, None])
+                       + 2 * dt * dt * (xi[None, :, 0] ** 2 + xi[None, :, 1] ** 2))
+    assert inner.sum() == (n - 4) ** 2
+    err = np.abs(st.f[inner] - ex[inner]).max() / np.abs(ex[inner]).max()
+    assert err <= 1e-12, err
