@@ -8,7 +8,8 @@ energy on periodic meshes, the zero mass flux of a diffuse wall, the collisionle
 Couette flow between diffuse plates, whose steady state is known in closed form on any
 velocity grid, and one collisionless step of a quadratic field, which fixes the
 characteristic reconstruction (the sign of its xi dt term, the upwind side, the
-gradient) and the sign of the flux balance.
+gradient) and the sign of the flux balance, and the BGK relaxation of a uniform state
+(the rate dt/tau of Eq. fn+1).
 """
 import math
 
@@ -150,3 +151,21 @@ def test_one_collisionless_step_of_a_quadratic_field():
     assert inner.sum() == (n - 4) ** 2
     err = np.abs(st.f[inner] - ex[inner]).max() / np.abs(ex[inner]).max()
     assert err <= 1e-12, err
+
+
+def test_uniform_state_relaxes_at_the_bgk_rate():
+    """Eq. fn+1 with no flux: a spatially uniform state on a periodic mesh has cancelling
+    face fluxes, so W keeps W0 and f relaxes geometrically to its Maxwellian,
+    f^n = feq(W0) + (f^0 - feq(W0)) / (1 + dt/tau)^n, whatever f^0 is."""
+    xi, w = O.dvm_grid(10, 2.5)
+    m = M.cartesian(4, 3, 1.0, 0.75, jitter=0.2, seed=5)
+    st = O.dvm_init(m.n_cells, xi, w, rho0=1.0, u0=(0.0, 0.0), RT0=0.5)
+    W0 = st.W.copy()
+    geq = O.dvm_maxwell(1.0, 0.0, 0.0, 0.5, xi, w)
+    g1 = O.dvm_maxwell(1.2, 0.15, -0.1, 0.65, xi, w)
+    st.f[:] = g1[None, :]
+    tau, dt, n = 0.05, 0.02, 7
+    O.dvm_run(m, _periodic(1.0, 0.75), st, xi, w, 0.5, tau=tau, dt=dt, n_steps=n)
+    ex = geq + (g1 - geq) / (1 + dt / tau) ** n
+    assert np.abs(st.f - ex[None, :]).max() <= 1e-13 * np.abs(ex).max()
+    assert np.abs(st.W - W0).max() <= 1e-13
