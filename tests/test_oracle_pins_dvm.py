@@ -10,7 +10,9 @@ velocity grid, and one collisionless step of a quadratic field, which fixes the
 characteristic reconstruction (the sign of its xi dt term, the upwind side, the
 gradient) and the sign of the flux balance, the BGK relaxation of a uniform state
 (the rate dt/tau of Eq. fn+1), and the decay of a shear wave at the Navier-Stokes rate
-nu k^2 with nu = tau R T (the interface distribution of Eq. f_t_n+1).
+nu k^2 with nu = tau R T (the interface distribution of Eq. f_t_n+1), and the mirror
+symmetry of a symmetric state on a grid with velocities tangential to the faces (the
+tie rule of reading A5).
 """
 import math
 
@@ -202,3 +204,28 @@ def test_shear_wave_decays_at_the_navier_stokes_rate():
     d32, d16 = r32 / e32 - 1, r16 / e16 - 1
     assert abs(d32) <= 0.01, d32
     assert 3 <= d16 / d32 <= 6, (d16, d32)
+
+
+def test_mirror_symmetric_state_stays_symmetric_with_tangential_nodes():
+    """Reading A5 for tangential velocities (xi . n = 0: the mean of both sides' values).
+    With odd nv the grid has a column xi_x = 0, tangential to every face of constant x;
+    such velocities carry no flux but enter the interface moments.  On a closed box of
+    walls at rest, a state symmetric under x -> L - x (rho and u_y even, u_x odd) stays
+    symmetric, to round-off, only if the tie rule treats the two sides alike."""
+    nx, ny, L = 6, 4, 6.0
+    xi, w = O.dvm_grid(9, 2.0)
+    m = M.cartesian(nx, ny, L, 4.0)
+    bcs = [(p, M.BC_WALL, (0, 0, 0)) for p in range(4)]
+    xy = m.meta["cell_xy_nominal"]
+    X, Y = 2 * np.pi * (xy[:, 0] - L / 2) / L, np.pi * xy[:, 1] / 4.0
+    st = O.dvm_init(m.n_cells, xi, w, rho=1 + 0.05 * np.cos(X),
+                    u=np.stack([0.05 * np.sin(X) * np.sin(Y), 0.02 * np.cos(X) * np.sin(Y)], 1),
+                    RT=0.5 + 0.02 * np.cos(X))
+    O.dvm_run(m, bcs, st, xi, w, 0.5, tau=0.1, dt=0.05, n_steps=20)
+    i, j = m.meta["cell_i"], m.meta["cell_j"]
+    mir = (nx - 1 - i) + nx * j
+    assert np.abs(st.rho - st.rho[mir]).max() <= 1e-12
+    assert np.abs(st.u[:, 0] + st.u[mir, 0]).max() <= 1e-12
+    assert np.abs(st.u[:, 1] - st.u[mir, 1]).max() <= 1e-12
+    assert np.abs(st.RT - st.RT[mir]).max() <= 1e-12
+    assert np.abs(st.u[:, 0]).max() > 1e-3
