@@ -27,15 +27,21 @@ NQ = 9
 XI = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], float)
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc with the oracle's flags (FP64, no contraction, OpenMP); returns ``out``."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-shared", "-fPIC", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library in-tree (idempotent)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
+        compile_library(_SRC, _SO)
     return _SO
 
 
@@ -43,7 +49,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
+            # SDUGKS_ORACLE_LIB: another build of this source (the planted-mistake sweep
+            # of tests/oracle_mutation_sweep.py); otherwise the in-tree build
+            lib = C.CDLL(os.environ.get("SDUGKS_ORACLE_LIB") or build())
             P = C.c_void_p
             i64, i32, dbl = C.c_int64, C.c_int, C.c_double
             mesh_args = [i64, P, i64, P, P, P, i64, i32, P, P]

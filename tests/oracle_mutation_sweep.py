@@ -1,0 +1,105 @@
+"""Planted-mistake sweep of the oracle's CPU pins (test infrastructure).
+
+Each entry plants one plausible mistake (a dropped term, a wrong sign, a wrong factor,
+the wrong side) in a copy of oracle/sdugks_oracle.c, compiles the copy in a temporary
+folder with the oracle's flags, and runs the pins against it (SDUGKS_ORACLE_LIB).  A
+mistake that no pin catches is a gap in the pins.  The in-tree oracle is never edited.
+Run from the repository root:
+
+    python tests/oracle_mutation_sweep.py        # exit status 1 if a mistake goes uncaught
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+
+D2Q9, DVM = "tests/test_oracle_pins.py", "tests/test_oracle_pins_dvm.py"
+
+# (what, pins, text in the oracle, replacement, which occurrence: 0 first, -1 last)
+MUTATIONS = [
+    ("D2Q9: sign of xi dt in the reconstruction", D2Q9,
+     "double px = xb[0] - XI[a][0] * dt, py = xb[1] - XI[a][1] * dt;",
+     "double px = xb[0] + XI[a][0] * dt, py = xb[1] + XI[a][1] * dt;", 0),
+    ("D2Q9: b feq_b dropped from f_b", D2Q9,
+     "fbf[a] = (fbar[a] + b_plus * feqb[a]) * c_face;", "fbf[a] = fbar[a] * c_face;", 0),
+    ("D2Q9: c dropped from f_b", D2Q9,
+     "fbf[a] = (fbar[a] + b_plus * feqb[a]) * c_face;", "fbf[a] = (fbar[a] + b_plus * feqb[a]);", 0),
+    ("D2Q9: relaxation rate dt/(2 tau)", D2Q9,
+     "const double r = dt / tau;", "const double r = dt / (2.0 * tau);", 0),
+    ("D2Q9: Hermite coefficient of (xi.u)^2", D2Q9,
+     "(eu * eu) / (2.0 * CS2 * CS2)", "(eu * eu) / (2.5 * CS2 * CS2)", 0),
+    ("D2Q9: sign of the W update", D2Q9,
+     "W[3 * j + d] - dt / m->vol[j] * Mj[d]", "W[3 * j + d] + dt / m->vol[j] * Mj[d]", 0),
+    ("LLSR: sign of the inverse's off-diagonal", D2Q9,
+     "m->ainv[3 * c + 1] = -axy / det;", "m->ainv[3 * c + 1] = axy / det;", 0),
+    ("D2Q9: downwind side", D2Q9,
+     "if (s > TIE) fbar[a] = from_o;\n                else if (s < -TIE) fbar[a] = from_k;",
+     "if (s > TIE) fbar[a] = from_k;\n                else if (s < -TIE) fbar[a] = from_o;", 0),
+    ("D2Q9: coefficient a of fbar+", D2Q9,
+     "(2.0 * tau - dt) / (2.0 * tau);  /* Eq. fbarplus */",
+     "(2.0 * tau - 0.5 * dt) / (2.0 * tau);  /* Eq. fbarplus */", 0),
+    ("D2Q9: wall's non-equilibrium part dropped", D2Q9,
+     "fbf[a] = feqb[a] + (f[NQ * o + a] - w->feqn[NQ * o + a]);", "fbf[a] = feqb[a];", 0),
+    ("rarefied: sign of the W update", DVM,
+     "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
+    ("rarefied: wall density without its b G_out term", DVM,
+     "double rho_w = -c_face * S_out / (c_face * b_plus * G_out + G_in);",
+     "double rho_w = -c_face * S_out / (G_in);", -1),
+    ("rarefied: wall's leaving values without b rho_w g", DVM,
+     "fbf[q] = s < -TIE ? rho_w * g[q] : (fbar[q] + b_plus * rho_w * g[q]) * c_face;",
+     "fbf[q] = s < -TIE ? rho_w * g[q] : fbar[q] * c_face;", -1),
+    ("rarefied: Maxwellian prefactor", DVM,
+     "const double pre = rho / (2.0 * M_PI * RT);", "const double pre = rho / (M_PI * RT);", -1),
+    ("rarefied: Maxwellian exponent", DVM,
+     "exp(-(cx * cx + cy * cy) / (2.0 * RT));", "exp(-(cx * cx + cy * cy) / (RT));", -1),
+    ("rarefied: a and b of fbar+ swapped", DVM,
+     "k->fbp[(size_t)Q * j + q] = a_plus * f[(size_t)Q * j + q] + b_plus * fe[q];",
+     "k->fbp[(size_t)Q * j + q] = b_plus * f[(size_t)Q * j + q] + a_plus * fe[q];", -1),
+    ("rarefied: tangential velocities take the owner's side", DVM,
+     "fbar[q] = s > TIE ? from_o : (s < -TIE ? from_k : 0.5 * (from_o + from_k));",
+     "fbar[q] = s > TIE ? from_o : (s < -TIE ? from_k : from_o);", -1),
+    ("rarefied: downwind side", DVM,
+     "fbar[q] = s > TIE ? from_o : (s < -TIE ? from_k : 0.5 * (from_o + from_k));",
+     "fbar[q] = s > TIE ? from_k : (s < -TIE ? from_o : 0.5 * (from_o + from_k));", -1),
+    ("rarefied: sign of xi dt in the reconstruction", DVM,
+     "double px = xb[0] - xi[2 * q] * dt, py = xb[1] - xi[2 * q + 1] * dt;\n                    const double *so = &k->sig[2 * ((size_t)Q * o + q)], *sk",
+     "double px = xb[0] + xi[2 * q] * dt, py = xb[1] + xi[2 * q + 1] * dt;\n                    const double *so = &k->sig[2 * ((size_t)Q * o + q)], *sk", -1),
+    ("rarefied: b feq_b dropped from f_b", DVM,
+     "fbf[q] = (fbar[q] + b_plus * g[q]) * c_face;   /* step 7 */", "fbf[q] = fbar[q] * c_face;   /* step 7 */", -1),
+    ("rarefied: relaxation rate dt/(2 tau)", DVM,
+     "    const double r = dt / tau;\n", "    const double r = dt / (2.0 * tau);\n", -1),
+]
+
+
+def main() -> int:
+    with open(os.path.join(ROOT, "oracle", "sdugks_oracle.c")) as fh:
+        src = fh.read()
+    missed = 0
+    with tempfile.TemporaryDirectory() as tmp:
+        for k, (what, pins, old, new, which) in enumerate(MUTATIONS):
+            if old not in src:
+                print(f"{what}: text not found in the oracle")
+                missed += 1
+                continue
+            i = src.index(old) if which == 0 else src.rindex(old)
+            c_path, so_path = os.path.join(tmp, f"m{k}.c"), os.path.join(tmp, f"m{k}.so")
+            with open(c_path, "w") as fh:
+                fh.write(src[:i] + new + src[i + len(old):])
+            oracle.compile_library(c_path, so_path)
+            r = subprocess.run([sys.executable, "-m", "pytest", pins, "-x", "-q", "-p", "no:cacheprovider"],
+                               cwd=ROOT, capture_output=True, text=True,
+                               env=dict(os.environ, SDUGKS_ORACLE_LIB=so_path))
+            caught = [ln.split("::")[1].split(" ")[0] for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
+            print(f"{what}: " + (f"caught by {caught[0]}" if caught else "NOT CAUGHT"), flush=True)
+            missed += not caught
+    print(f"{len(MUTATIONS) - missed} of {len(MUTATIONS)} planted mistakes caught")
+    return 1 if missed else 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
