@@ -45,6 +45,19 @@ MUTATIONS = [
      "(2.0 * tau - 0.5 * dt) / (2.0 * tau);  /* Eq. fbarplus */", 0),
     ("D2Q9: wall's non-equilibrium part dropped", D2Q9,
      "fbf[a] = feqb[a] + (f[NQ * o + a] - w->feqn[NQ * o + a]);", "fbf[a] = feqb[a];", 0),
+    ("D2Q9: far-field velocity components swapped", D2Q9,
+     "*rho = par[0]; *ux = par[1]; *uy = par[2]; break;", "*rho = par[0]; *ux = par[2]; *uy = par[1]; break;", 0),
+    ("D2Q9: sign of the outlet's tangential velocity", D2Q9,
+     "*rho = Wo[0]; *ux = Wo[1] / Wo[0]; *uy = Wo[2] / Wo[0]; break;",
+     "*rho = Wo[0]; *ux = Wo[1] / Wo[0]; *uy = -Wo[2] / Wo[0]; break;", 0),
+    ("D2Q9: sign of the moving wall's velocity", D2Q9,
+     "*rho = Wo[0]; *ux = par[0]; *uy = par[1]; break;", "*rho = Wo[0]; *ux = -par[0]; *uy = par[1]; break;", 0),
+    ("symmetry: mirror ghost's gradient not reflected", D2Q9,
+     "else if (mir == 2) { ak = MIRROR_Y[a]; gsy = -1.0; }", "else if (mir == 2) { ak = MIRROR_Y[a]; gsy = 1.0; }", 0),
+    ("geometry: centroid divisor", D2Q9,
+     "cen[0] = ox + cx / (3.0 * a2);", "cen[0] = ox + cx / (6.0 * a2);", 0),
+    ("residual: denominator without V0", D2Q9,
+     "den += U0 * U0 + V0 * V0;", "den += U0 * U0;", 0),
     ("rarefied: sign of the W update", DVM,
      "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
     ("rarefied: wall density without its b G_out term", DVM,
