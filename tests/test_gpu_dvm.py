@@ -116,6 +116,18 @@ def test_fp32_micro_cavity_matches_oracle():
     assert np.abs(RT - st.RT).max() <= 1e-5
 
 
+def test_fp32_one_velocity_per_thread_matches_oracle():
+    """FP32 with nv = 10 (not a multiple of 4): the kernels take one velocity per
+    thread at a time."""
+    case = M.micro_cavity(12, Kn=0.5, nv=10)
+    m, bcs = case.mesh, case.bcs
+    d, st = _run(m, bcs, 10, 2.0, 0.5, case.tau, case.dt, 200, "fp32")
+    rho, u, RT = d.macros()
+    assert np.sqrt(np.sum((u - st.u) ** 2) / np.sum(st.u ** 2)) <= 1e-4
+    assert np.abs(rho - st.rho).max() <= 1e-5
+    assert np.abs(RT - st.RT).max() <= 1e-5
+
+
 def test_diffuse_walls_conserve_mass_fp32():
     case = M.micro_cavity(20, Kn=1.0, nv=32)
     S = _S()
