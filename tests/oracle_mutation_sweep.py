@@ -58,6 +58,22 @@ MUTATIONS = [
      "cen[0] = ox + cx / (3.0 * a2);", "cen[0] = ox + cx / (6.0 * a2);", 0),
     ("residual: denominator without V0", D2Q9,
      "den += U0 * U0 + V0 * V0;", "den += U0 * U0;", 0),
+    ("D2Q9: tangential velocities take the owner's side", D2Q9,
+     "else fbar[a] = 0.5 * (from_o + from_k);", "else fbar[a] = from_o;", 0),
+    ("D2Q9: interface momentum from the wrong component", D2Q9,
+     "Wb[1] += XI[a][0] * fbar[a];", "Wb[1] += XI[a][1] * fbar[a];", 0),
+    ("D2Q9: wall's leaving values without b feq_b", D2Q9,
+     "fbf[a] = (fbar + b_plus * feqb[a]) * c_face;", "fbf[a] = fbar * c_face;", 0),
+    ("D2Q9: sign of the wall's non-equilibrium part", D2Q9,
+     "fbf[a] = feqb[a] + (f[NQ * o + a] - w->feqn[NQ * o + a]);", "fbf[a] = feqb[a] - (f[NQ * o + a] - w->feqn[NQ * o + a]);", 0),
+    ("D2Q9: coefficient of u^2 in feq", D2Q9,
+     "- uu / (2.0 * CS2));", "- uu / (3.0 * CS2));", 0),
+    ("D2Q9: a diagonal weight", D2Q9,
+     "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0};", 0),
+    ("LLSR: sign of the offset d = x_k - x_j", D2Q9,
+     "bx += (px - m->xc[2 * c]) * dphi;", "bx += (m->xc[2 * c] - px) * dphi;", 0),
+    ("D2Q9: neighbour side adds the face flux", D2Q9,
+     "double sg = (m->own[fc] == j) ? 1.0 : -1.0;", "double sg = 1.0;", 0),
     ("rarefied: sign of the W update", DVM,
      "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
     ("rarefied: wall density without its b G_out term", DVM,
