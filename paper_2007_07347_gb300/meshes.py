@@ -81,36 +81,62 @@ def cartesian(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, *, jitter: flo
     the quads convex for jitter < 0.25.
     """
     dx, dy = lx / nx, ly / ny
-    I, J = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
-    px = (I * dx).astype(np.float64).ravel()
-    py = (J * dy).astype(np.float64).ravel()
+    # arrays filled in place by broadcasting, row by row (row j of the points, faces
+    # and cells is contiguous), with the ids of the docstring
+    px = np.empty((ny + 1, nx + 1))
+    px[:] = np.arange(nx + 1) * dx
+    py = np.empty((ny + 1, nx + 1))
+    py[:] = (np.arange(ny + 1) * dy)[:, None]
+    px, py = px.ravel(), py.ravel()
     if jitter:
         rng = np.random.default_rng(seed)
-        inner = ((I > 0) & (I < nx) & (J > 0) & (J < ny)).ravel()
+        inner = np.zeros((ny + 1, nx + 1), bool)
+        inner[1:ny, 1:nx] = True
+        inner = inner.ravel()
         h = jitter * min(dx, dy)
         px[inner] += rng.uniform(-h, h, inner.sum())
         py[inner] += rng.uniform(-h, h, inner.sum())
-    points = np.stack([px, py], 1)
+    points = np.empty((px.size, 2))
+    points[:, 0], points[:, 1] = px, py
 
+    nfx, nfy = (nx + 1) * ny, nx * (ny + 1)
+    fp = np.empty((nfx + nfy, 2), np.int64)
+    own = np.empty(nfx + nfy, np.int64)
+    nbr = np.empty(nfx + nfy, np.int64)
     # faces of constant x (between cells (i-1, j) and (i, j)), row by row
-    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx + 1), indexing="ij")
-    ii, jj = ii.ravel(), jj.ravel()
-    fpx = np.stack([ii + (nx + 1) * jj, ii + (nx + 1) * (jj + 1)], 1)
-    ownx = np.where(ii == 0, jj * nx, ii - 1 + nx * jj)
-    nbrx = np.where(ii == 0, -1 - 3, np.where(ii == nx, -1 - 1, ii + nx * jj))
+    ii, jj = np.arange(nx + 1)[None, :], np.arange(ny)[:, None]
+    p0 = ii + (nx + 1) * jj
+    fp[:nfx, 0], fp[:nfx, 1] = p0.ravel(), (p0 + (nx + 1)).ravel()
+    o = np.empty((ny, nx + 1), np.int64)
+    o[:] = ii - 1 + nx * jj
+    o[:, 0] = nx * jj[:, 0]
+    own[:nfx] = o.ravel()
+    k = np.empty((ny, nx + 1), np.int64)
+    k[:] = ii + nx * jj
+    k[:, 0], k[:, nx] = -1 - 3, -1 - 1
+    nbr[:nfx] = k.ravel()
     # faces of constant y (between cells (i, j-1) and (i, j))
-    jj, ii = np.meshgrid(np.arange(ny + 1), np.arange(nx), indexing="ij")
-    ii, jj = ii.ravel(), jj.ravel()
-    fpy = np.stack([ii + (nx + 1) * jj, ii + 1 + (nx + 1) * jj], 1)
-    owny = np.where(jj == 0, ii, ii + nx * (jj - 1))
-    nbry = np.where(jj == 0, -1 - 0, np.where(jj == ny, -1 - 2, ii + nx * jj))
-    fp = np.concatenate([fpx, fpy]).astype(np.int64)
-    own = np.concatenate([ownx, owny]).astype(np.int64)
-    nbr = np.concatenate([nbrx, nbry]).astype(np.int64)
-    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ii, jj = np.arange(nx)[None, :], np.arange(ny + 1)[:, None]
+    p0 = ii + (nx + 1) * jj
+    fp[nfx:, 0], fp[nfx:, 1] = p0.ravel(), (p0 + 1).ravel()
+    o = np.empty((ny + 1, nx), np.int64)
+    o[:] = ii + nx * (jj - 1)
+    o[0, :] = ii[0]
+    own[nfx:] = o.ravel()
+    k = np.empty((ny + 1, nx), np.int64)
+    k[:] = ii + nx * jj
+    k[0, :], k[ny, :] = -1 - 0, -1 - 2
+    nbr[nfx:] = k.ravel()
+
+    ci = np.empty((ny, nx), np.int64)
+    ci[:] = np.arange(nx)
+    cj = np.empty((ny, nx), np.int64)
+    cj[:] = np.arange(ny)[:, None]
+    ci, cj = ci.ravel(), cj.ravel()
+    xyn = np.empty((nx * ny, 2))
+    xyn[:, 0], xyn[:, 1] = (ci + 0.5) * dx, (cj + 0.5) * dy
     meta = dict(kind="cartesian", nx=nx, ny=ny, lx=lx, ly=ly, dx=dx, dy=dy,
-                cell_i=ci.ravel(), cell_j=cj.ravel(),
-                cell_xy_nominal=np.stack([(ci.ravel() + 0.5) * dx, (cj.ravel() + 0.5) * dy], 1))
+                cell_i=ci, cell_j=cj, cell_xy_nominal=xyn)
     return Mesh(points, fp, own, nbr, nx * ny, dict(bottom=0, right=1, top=2, left=3), meta)
 
 
