@@ -74,6 +74,14 @@ MUTATIONS = [
      "bx += (px - m->xc[2 * c]) * dphi;", "bx += (m->xc[2 * c] - px) * dphi;", 0),
     ("D2Q9: neighbour side adds the face flux", D2Q9,
      "double sg = (m->own[fc] == j) ? 1.0 : -1.0;", "double sg = 1.0;", 0),
+    ("geometry: periodic image without its shift", D2Q9,
+     "m->gpos[2 * f] = m->xc[2 * other] - sx;", "m->gpos[2 * f] = m->xc[2 * other];", 0),
+    ("geometry: symmetry ghost at half its distance (lines of constant y)", D2Q9,
+     "m->gpos[2 * f + 1] = xo[1] + 2.0 * dn * Ny;", "m->gpos[2 * f + 1] = xo[1] + dn * Ny;", 0),
+    ("geometry: symmetry ghost at half its distance (lines of constant x)", D2Q9,
+     "m->gpos[2 * f] = xo[0] + 2.0 * dn * Nx;", "m->gpos[2 * f] = xo[0] + dn * Nx;", 0),
+    ("symmetry: ghost's x-gradient not reflected", D2Q9,
+     "if (mir == 1) { ak = MIRROR_X[a]; gsx = -1.0; }", "if (mir == 1) { ak = MIRROR_X[a]; gsx = 1.0; }", 0),
     ("rarefied: sign of the W update", DVM,
      "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
     ("rarefied: wall density without its b G_out term", DVM,

@@ -336,6 +336,46 @@ def test_symmetry_line_equals_the_mirrored_domain(jitter, seed):
     np.testing.assert_allclose(s_full.f[n:], s_full.f[:n][:, mx], rtol=0, atol=1e-13)
 
 
+def _transposed(mesh):
+    """The mesh with x and y exchanged (the same ids; a line of constant y becomes a
+    line of constant x)."""
+    meta = dict(mesh.meta)
+    if "cell_xy_nominal" in meta:
+        meta["cell_xy_nominal"] = meta["cell_xy_nominal"][:, ::-1].copy()
+    return M.Mesh(mesh.points[:, ::-1].copy(), mesh.face_pts, mesh.owner, mesh.neighbour, mesh.n_cells,
+                  mesh.patches, meta)
+
+
+@pytest.mark.parametrize("jitter,seed", [(0.0, None), (0.2, 3)])
+def test_symmetry_line_of_constant_x_equals_the_mirrored_domain(jitter, seed):
+    """The previous check with x and y exchanged: the symmetry line is a line of
+    constant x (the mirror of the other axis, its own ghost position and gradient
+    reflection), periodic in y, the moving wall at x = 0."""
+    half = _channel_half(jitter, seed)
+    full = M.mirror_y(half, half.patches["top"])
+    half, full = _transposed(half), _transposed(full)
+    n = half.n_cells
+    per = [(3, M.BC_PERIODIC, (1, 0.0, 8.0)), (1, M.BC_PERIODIC, (3, 0.0, -8.0))]
+    wall = [(0, M.BC_MOVING_WALL, (0.0, 0.05, 0.0))]
+    c_half = M.Case("half_t", half, per + wall + [(2, M.BC_SYMMETRY, (0.0, 0.0, 0.0))], tau=0.05, dt=0.2)
+    c_full = M.Case("full_t", full, per + wall, tau=0.05, dt=0.2)
+    xy = half.meta["cell_xy_nominal"]                         # (y, x) of the untransposed channel
+    X, Y = 2 * np.pi * xy[:, 1] / 8.0, np.pi * xy[:, 0] / 4.0
+    rho = 1.0 + 0.02 * np.cos(X) * np.cos(Y)
+    u = np.stack([0.02 * np.sin(X) * np.sin(0.5 * Y), 0.03 * np.sin(X) + 0.01 * Y], 1)
+    s_half = O.init(n, rho=rho, u=u)
+    u_m = u.copy()
+    u_m[:, 0] *= -1.0
+    s_full = O.init(2 * n, rho=np.concatenate([rho, rho]), u=np.concatenate([u, u_m]))
+    O.run(c_half, s_half, 40)
+    O.run(c_full, s_full, 40)
+    assert np.abs(s_half.W[:, 1]).max() > 1e-4                 # normal velocity near the line
+    np.testing.assert_allclose(s_half.f, s_full.f[:n], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s_half.W, s_full.W[:n], rtol=0, atol=1e-13)
+    my = np.array([0, 3, 2, 1, 4, 6, 5, 8, 7])                # mirror in x
+    np.testing.assert_allclose(s_full.f[n:], s_full.f[:n][:, my], rtol=0, atol=1e-13)
+
+
 def test_symmetry_uniform_stream_is_fixed_point():
     """A uniform stream along two symmetry lines (periodic in x) is a fixed point."""
     m = M.cartesian(6, 5, 6.0, 5.0, jitter=0.2, seed=8)
