@@ -88,9 +88,13 @@ typedef struct sdugks_params {
                             0 = chosen from the grid size (Cartesian) or 128 (tiled) */
     int32_t graph_steps; /* steps per captured CUDA graph in sdugks_step, 0 = auto, <0 = off */
     int32_t staging;     /* SDUGKS_STAGING_*; TMA requires the Cartesian kernel (else
-                            INVALID_ARG).  A TMA copy that does not land within 0.2 s
-                            makes the block give up and the next sdugks_residual
-                            report SDUGKS_ERR_TIMEOUT */
+                            INVALID_ARG).  A TMA copy that does not land within the wait
+                            limit below makes the block give up, and the next
+                            sdugks_residual reports SDUGKS_ERR_TIMEOUT */
+    int32_t tma_wait_us; /* wait limit of a TMA staging copy in microseconds:
+                            0 = 200000 (0.2 s); < 0 = give up at once without waiting,
+                            which exercises the timeout path (the block still waits, up
+                            to 0.2 s, for its copies to land before it exits) */
 } sdugks_params;
 
 /* What a solver chose and holds (sdugks_solver_info). */
@@ -189,7 +193,11 @@ int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double *d_u);
  *   eps = sqrt(sum_i (U_i - U0_i)^2 + (V_i - V0_i)^2) / sqrt(sum_i U0_i^2 + V0_i^2)
  * with U, V = rho u / rho; +inf when the snapshot is at rest.  *mass = sum_i V_i rho_i.
  * Then the snapshot is refreshed.  FP64 device reduction with a fixed order.
- * Synchronises.  Returns DIVERGED (with eps = NaN) if any W is not finite. */
+ * Synchronises.  Returns DIVERGED (with eps = NaN) if any W is not finite.
+ * Returns TIMEOUT if a bounded staging wait of a step since the previous call gave
+ * up: the blocks that gave up skipped their update, so the whole state is invalid;
+ * the solver then needs sdugks_init or sdugks_set_state before it steps again (STATE
+ * until then). */
 int sdugks_residual(sdugks_solver *s, double *eps, double *mass);
 
 /* Checkpoint of the state at t_n (host, FP64, caller's cell order):

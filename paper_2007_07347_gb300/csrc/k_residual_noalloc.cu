@@ -8,6 +8,7 @@
 // allocations).  The per-block partial sums live in `g_resid_scratch` below, a
 // file-scope device array that every GPU which loads this library holds until the
 // process exits; every call shares it.
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cuda_runtime.h>
@@ -27,8 +28,9 @@ constexpr int NA_MAX_DEVICES = 64;
 static __device__ __align__(256) double g_resid_scratch[NA_MAX_BLOCKS][4];
 
 // Device address of g_resid_scratch on each device, looked up on the first call made
-// with that device current.  Two threads racing on a first call store the same value.
-double *g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
+// with that device current.  Atomic, because host threads may make first calls at the
+// same time; they look up and store the same value.
+std::atomic<double *> g_scratch_ptr[NA_MAX_DEVICES];
 
 __device__ void na_block_sum4(double v[4], double *out)
 {
@@ -114,16 +116,16 @@ extern "C" int sdugks_residual_noalloc(int64_t n, const double *d_W, const doubl
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(SDUGKS_ERR_CUDA, "sdugks_residual_noalloc: cudaGetDevice", e);
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(SDUGKS_ERR_INVALID_ARG, "sdugks_residual_noalloc: device id >= 64");
-    if (!g_scratch_ptr[dev]) {
+    double *sp = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+    if (!sp) {
         // once per device, with that device current: the device address of the scratch
         // array (its host-side name is not a device address)
-        double *ptr = nullptr;
-        e = cudaGetSymbolAddress((void **)&ptr, g_resid_scratch);
-        if (e != cudaSuccess || !ptr)
+        e = cudaGetSymbolAddress((void **)&sp, g_resid_scratch);
+        if (e != cudaSuccess || !sp)
             return na_fail(SDUGKS_ERR_CUDA, "sdugks_residual_noalloc: cudaGetSymbolAddress", e);
-        g_scratch_ptr[dev] = ptr;
+        g_scratch_ptr[dev].store(sp, std::memory_order_relaxed);
     }
-    double (*scratch)[4] = reinterpret_cast<double (*)[4]>(g_scratch_ptr[dev]);
+    double (*scratch)[4] = reinterpret_cast<double (*)[4]>(sp);
     const int nb = (int)((n + NA_CELLS_PER_BLOCK - 1) / NA_CELLS_PER_BLOCK);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // every block writes its own partial row, so nothing has to be cleared first

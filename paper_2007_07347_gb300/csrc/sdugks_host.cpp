@@ -601,6 +601,8 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     for (int b = 0; b < 2; b++) { s->ci.f[b] = s->st.f[b]; s->ci.W[b] = s->st.W[b]; }
     s->ci.snap = s->snap;
     s->ci.err = reinterpret_cast<int32_t *>(s->red + 4);
+    s->ci.tma_wait_ns = prm->tma_wait_us == 0 ? 200000000ull
+                        : prm->tma_wait_us < 0 ? 0ull : 1000ull * (uint64_t)prm->tma_wait_us;
     std::vector<int32_t> perm(n), loc(n);
     std::vector<double> vol(npad, 1.0);
     for (int64_t c = 0; c < n; c++) {
@@ -1150,8 +1152,15 @@ static int snapshot(sdugks_solver *s, double *eps, double *mass)
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     int32_t err_flag;
     std::memcpy(&err_flag, &s->h_red[4], sizeof err_flag);
-    if (err_flag != 0)
-        return fail(SDUGKS_ERR_TIMEOUT, "a TMA staging copy of the Cartesian step did not complete within its wait limit");
+    if (err_flag != 0) {
+        // blocks of some launch since the last check skipped their update: no result of
+        // the state is usable until init or set_state; the flag is cleared for that
+        s->initialised = false;
+        CUDA_TRY(cudaMemsetAsync(s->red + 4, 0, sizeof(int32_t), s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return fail(SDUGKS_ERR_TIMEOUT, "a TMA staging copy of the Cartesian step did not complete within its wait "
+                                        "limit; the state is invalid until init or set_state");
+    }
     const double num = s->h_red[0], den = s->h_red[1];
     if (mass) *mass = s->h_red[2];
     if (s->h_red[3] != 0.0) {
@@ -1175,6 +1184,7 @@ extern "C" int sdugks_init(sdugks_solver *s, const double *rho, const double *u)
     if (u) CUDA_TRY(cudaMemcpyAsync(d_u, u, sizeof(double) * 2 * s->n, cudaMemcpyHostToDevice, s->stream));
     s->cur = 0; s->steps_done = 0;
     CUDA_TRY(launch_init_state(s->p.precision, s->n, s->npad, s->perm, s->loc, d_rho, d_u, s->st.f[0], s->st.W[0], s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->red + 4, 0, sizeof(int32_t), s->stream));   // a new state: no failed launch
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);
 }
@@ -1328,6 +1338,7 @@ extern "C" int sdugks_set_state(sdugks_solver *s, const double *f, const double 
     CUDA_TRY(cudaMemcpyAsync(dW, W, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
     s->cur = 0; s->steps_done = 0;
     CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, s->loc, df, dW, s->st.f[0], s->st.W[0], s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->red + 4, 0, sizeof(int32_t), s->stream));   // a new state: no failed launch
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);
 }

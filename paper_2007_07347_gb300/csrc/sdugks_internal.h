@@ -99,6 +99,7 @@ struct CartInst {
     double *snap;             // [2][npad] residual snapshot (U0, V0)
     double *force;            // nullptr, or [4][2]: momentum flux out of the fluid per grid side
     int32_t *err;             // nullptr, or a device flag set to 1 when a bounded staging wait gave up
+    uint64_t tma_wait_ns;     // TMA staging: wait limit of a block's copies (0: give up at once)
 };
 
 // Device state of one solver, ping-pong: f [2][NQ][npad] (element type by

@@ -95,9 +95,10 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Waits for the phase `parity` of the mbarrier at shared address `bar` to complete;
-// gives up after `limit_ns` nanoseconds and returns false.
+// gives up after `limit_ns` nanoseconds and returns false (at once when limit_ns is 0).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns)
 {
+    if (limit_ns == 0) return false;
     const uint64_t t0 = global_ns();
     for (;;) {
         uint32_t done;
@@ -135,8 +136,9 @@ __device__ __forceinline__ void tma_issue_block(uint32_t bar, uint32_t dst_f, ui
                  : "memory");
 }
 
-// Longest wait for a staging copy before the block reports SDUGKS_ERR_TIMEOUT through
-// the error flag (a copy normally lands within microseconds).
+// Default wait limit of a staging copy before the block reports SDUGKS_ERR_TIMEOUT
+// through the error flag (a copy normally lands within microseconds), and the limit of
+// the second wait, for copies still in flight, after a block has given up.
 constexpr uint64_t TMA_WAIT_NS = 200000000ull;
 
 // Velocities crossing a face of constant x (xi_x != 0) and of constant y, in slot order.
@@ -664,11 +666,16 @@ __device__ __forceinline__ unsigned char *aligned_smem(unsigned char *raw, uint3
     return raw + (sa - r);
 }
 
-// Every thread waits for the barrier phase; false (for the whole CTA) if any thread
-// gave up, after the error flag is set and a late copy has had time to land.
+// Every thread waits for the barrier phase, up to the solver's limit; false (for the
+// whole CTA) if any thread gave up.  Then the error flag is set (the host treats the
+// whole launch as failed) and thread 0 waits, up to TMA_WAIT_NS, for the copies to
+// land, so that the CTA's shared memory is not released while a copy still writes to it;
+// the other threads may exit meanwhile (the CTA's shared memory lives until its last
+// thread exits).  If that second wait gives up too, nothing more can be done: the copy
+// is reported but may still land after the CTA has exited.
 __device__ __forceinline__ bool cta_wait_staged(const CartInst &m, uint32_t bar, uint32_t parity)
 {
-    const bool ok = mbar_wait_bounded(bar, parity, TMA_WAIT_NS);
+    const bool ok = mbar_wait_bounded(bar, parity, m.tma_wait_ns);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
             if (m.err) atomicExch(m.err, 1);

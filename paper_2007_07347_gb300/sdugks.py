@@ -38,7 +38,8 @@ class SdugksError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("tau", C.c_double), ("dt", C.c_double), ("precision", C.c_int32), ("kernel", C.c_int32),
-                ("tile_cells", C.c_int32), ("graph_steps", C.c_int32), ("staging", C.c_int32)]
+                ("tile_cells", C.c_int32), ("graph_steps", C.c_int32), ("staging", C.c_int32),
+                ("tma_wait_us", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -177,11 +178,12 @@ class Solver:
     "tma") picks how the Cartesian kernel stages its interior blocks."""
 
     def __init__(self, mesh: Mesh, tau: float, dt: float, precision="fp32", *, kernel=KERNEL_AUTO,
-                 tile_cells=0, graph_steps=0, staging="loads", stream=None):
+                 tile_cells=0, graph_steps=0, staging="loads", tma_wait_us=0, stream=None):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         stg = STAGINGS[staging] if isinstance(staging, str) else int(staging)
-        self.params = Params(float(tau), float(dt), prec, int(kernel), int(tile_cells), int(graph_steps), stg)
+        self.params = Params(float(tau), float(dt), prec, int(kernel), int(tile_cells), int(graph_steps), stg,
+                             int(tma_wait_us))
         sh = getattr(stream, "cuda_stream", stream)
         self._h = C.c_void_p()
         _ck(L.sdugks_solver_create(mesh._h, C.byref(self.params), C.c_void_p(sh or 0), C.byref(self._h)),

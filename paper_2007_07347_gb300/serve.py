@@ -184,10 +184,20 @@ class Server:
                     running.remove(r)
         wall = now()
         torch.cuda.synchronize()
-        lat = np.array([r.done - r.arrival for r in requests])
-        conv = sum(r.status == "converged" for r in requests)
-        return {"requests": len(requests), "converged": int(conv), "capped": int(len(requests) - conv),
-                "wall_s": wall, "solves_per_s": len(requests) / wall,
-                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                "cell_steps": int(sum(r.steps * r.case.mesh.n_cells for r in requests)),
-                "batch": batch.info()}
+        return {**serve_stats(requests, wall), "batch": batch.info()}
+
+
+def serve_stats(requests: list, wall: float) -> dict:
+    """Throughput and latency of a finished run.  Only requests that reached the residual
+    target count as solves: solves/s and the p50/p99 latencies are taken over the
+    converged requests; requests stopped at the step cap (or diverged) are counted
+    beside them, and ``met_target`` is False when any request did not converge."""
+    conv = [r for r in requests if r.status == "converged"]
+    lat = np.array([r.done - r.arrival for r in conv])
+    out = {"requests": len(requests), "converged": len(conv), "capped": len(requests) - len(conv),
+           "met_target": len(conv) == len(requests),
+           "wall_s": wall, "solves_per_s": len(conv) / wall if wall > 0 else 0.0,
+           "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+           "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+           "cell_steps": int(sum(r.steps * r.case.mesh.n_cells for r in requests))}
+    return out

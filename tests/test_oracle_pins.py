@@ -246,7 +246,9 @@ def test_couette_linear_profile():
 
 def test_couette_second_order_on_distorted_meshes():
     """Sec. IV: the L2 error of u decays at second order on unstructured
-    (jittered) 4 x {8, 16, 32, 64} meshes."""
+    (jittered) 4 x {8, 16, 32, 64} meshes.  The fitted slope on these seeded meshes is
+    2.21 (local orders 2.06, 2.23, 2.34); the band is that value +- 0.15, so a first-order
+    term or an extra term that changes the rate fails it."""
     errs, hs = [], []
     for ny in (8, 16, 32, 64):
         base = M.couette(ny)
@@ -261,7 +263,7 @@ def test_couette_second_order_on_distorted_meshes():
         errs.append(np.sqrt(np.sum((st.u[:, 0] - U * y) ** 2) / np.sum((U * y) ** 2)))
         hs.append(dy)
     slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
-    assert 1.8 <= slope <= 2.6, (slope, errs)
+    assert 2.06 <= slope <= 2.36, (slope, errs)
 
 
 # ------------------------------------------------------------------ P7 mirror symmetry
@@ -476,8 +478,9 @@ def test_couette_second_order_on_triangles():
     """Sec. IV Couette flow on hybrid meshes 4 x {8, 16, 32, 64}: triangles everywhere
     but a layer of quads along the two walls; the L2 error of u decays at second
     order, approached from below on these coarse meshes (measured local orders 1.61
-    and 1.71 between 16, 32 and 64 rows; a first-order scheme would give 1).  dt
-    follows the CFL rule of the triangles (half the quads' step)."""
+    and 1.71 between 16, 32 and 64 rows, fitted slope 1.66; a first-order scheme would
+    give 1).  The band is the fitted slope +- 0.12.  dt follows the CFL rule of the
+    triangles (half the quads' step)."""
     errs, hs = [], []
     for ny in (8, 16, 32, 64):
         base = M.couette(ny)
@@ -492,5 +495,5 @@ def test_couette_second_order_on_triangles():
         errs.append(np.sqrt(np.sum((st.u[:, 0] - U * y) ** 2) / np.sum((U * y) ** 2)))
         hs.append(dy)
     slope = np.polyfit(np.log(hs[1:]), np.log(errs[1:]), 1)[0]
-    assert 1.55 <= slope <= 2.6, (slope, errs)
+    assert 1.54 <= slope <= 1.78, (slope, errs)
     assert errs[-1] < 1e-5

@@ -98,7 +98,8 @@ def test_every_request_finishes_and_the_pool_is_respected(fakes):
     first_remove = next(k for k, e in enumerate(FakeBatch.log) if e[0] == "remove")
     assert any(e[0] == "add" for e in FakeBatch.log[first_remove:])      # admitted once memory returned
     assert out["cell_steps"] == sum(3000 * r.case.mesh.n_cells for r in reqs)
-    assert 0 <= out["p50_latency_s"] <= out["p99_latency_s"]
+    # capped requests are not solves: no throughput, no latency, the target not met
+    assert out["solves_per_s"] == 0.0 and out["p50_latency_s"] is None and out["met_target"] is False
 
 
 def test_retirement_at_the_residual_target(fakes):
@@ -106,6 +107,22 @@ def test_retirement_at_the_residual_target(fakes):
     srv = V.Server(pool_bytes=1 << 40, check_every=500, step_cap=10 ** 6, target=0.5, solver_pool_bytes=1 << 40)
     out = srv.run(reqs)
     # eps = 1 / (1 + steps / 1000) falls below 0.5 after 1500 steps (three intervals)
-    assert out["converged"] == 12
+    assert out["converged"] == 12 and out["met_target"] is True
     assert all(r.status == "converged" and r.steps == 1500 and r.eps < 0.5 for r in reqs)
     assert all(math.isfinite(r.done) for r in reqs)
+    assert out["solves_per_s"] == pytest.approx(12 / out["wall_s"])
+    assert 0 <= out["p50_latency_s"] <= out["p99_latency_s"]
+
+
+def test_stats_count_converged_requests_only(fakes):
+    """Mixed outcome: solves/s and the latency percentiles come from the converged
+    requests alone; the capped ones are counted beside them."""
+    reqs = _requests(10)
+    for k, r in enumerate(reqs):
+        r.build()
+        r.status = "converged" if k < 6 else "capped"
+        r.arrival, r.done = 0.0, 1.0 + k
+    out = V.serve_stats(reqs, wall=4.0)
+    assert out["converged"] == 6 and out["capped"] == 4 and out["met_target"] is False
+    assert out["solves_per_s"] == pytest.approx(1.5)
+    assert out["p99_latency_s"] <= 6.0 + 1e-12          # the capped requests' latencies (7-10 s) are left out
