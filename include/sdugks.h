@@ -114,6 +114,8 @@ typedef struct sdugks_info {
     int32_t one_code_path;        /* Cartesian kernel: 1 when the grid runs in one wave and
                                      every block takes the general code path; 0 when interior
                                      blocks take the compile-time interior variant      */
+    int64_t n_boundary_faces;     /* faces on non-periodic patches: the rows of
+                                     sdugks_step_boundary_flux                          */
 } sdugks_info;
 
 /* ---- mesh ---------------------------------------------------------------------- */
@@ -180,6 +182,24 @@ int sdugks_step(sdugks_solver *s, int64_t n);
  * read 0.  Synchronises.  The FP64 sums use atomics, so the last bits can vary from
  * run to run; the state update itself is unchanged. */
 int sdugks_step_forces(sdugks_solver *s, double *force);
+
+/* One step (as sdugks_step(s, 1)) that also returns the momentum leaving the fluid
+ * through every boundary face, the face-by-face form of the forces of Sec. IV:
+ *   face_flux[2 i], face_flux[2 i + 1] (host, [n_boundary_faces][2], FP64) for the i-th
+ *   face of the mesh (in the caller's face order) whose neighbour is < 0 and whose
+ *   patch is not periodic (sdugks_info.n_boundary_faces rows):
+ *     F_i = sum_a xi_a (xi_a . n_i l_i) f_b,a,
+ *   n_i the unit normal out of the fluid, l_i the face length, f_b the interface
+ *   distribution of the step (Eq. f_t_n+1 with the rules of Sec. III).
+ * The patch sums of F_i are the forces of sdugks_step_forces; the normal part
+ * F_i . n_i / l_i is the normal momentum flux, i.e. the surface pressure at a no-slip
+ * wall (where the normal velocity and normal viscous stress vanish), from which
+ * C_p = (F_i . n_i / l_i - rho_inf c_s^2) / (0.5 rho_inf U^2) (Sec. IV); the tangential
+ * part over l_i is the wall shear stress.  Symmetry faces are included.
+ * force: NULL, or as in sdugks_step_forces (per patch, summed with atomics).
+ * face_flux: NULL, or the caller's buffer; each row is written once, in FP64 (FP32
+ * modes: the FP32 sum converted).  Synchronises.  Errors: INVALID_ARG, STATE. */
+int sdugks_step_boundary_flux(sdugks_solver *s, double *force, double *face_flux);
 
 /* Macroscopic fields at the current step: rho[n_cells], u[n_cells][2] (host;
  * synchronises).  Either pointer may be NULL. */

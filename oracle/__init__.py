@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 NQ = 9
+KIND_PERIODIC = 1          # boundary kind codes as the oracle's C source numbers them
 XI = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], float)
 
 
@@ -59,6 +60,7 @@ def _load():
             lib.oracle_geometry.argtypes = mesh_args + [P, P, P, P, P, P]
             lib.oracle_gradient.argtypes = mesh_args + [P, P]
             lib.oracle_run.argtypes = mesh_args + [dbl, dbl, i64, P, P]
+            lib.oracle_run_flux.argtypes = mesh_args + [dbl, dbl, i64, P, P, P]
             lib.oracle_init.argtypes = [i64, P, P, P, P]
             lib.oracle_residual.argtypes = [i64, P, P, P, P, P]
             lib.oracle_set_threads.argtypes = [i32]
@@ -66,7 +68,7 @@ def _load():
             lib.oracle_dvm_maxwell.argtypes = [dbl, dbl, dbl, dbl, i32, P, P, P]
             lib.oracle_dvm_init.argtypes = [i64, i32, P, P, P, P, P, P, P]
             lib.oracle_dvm_run.argtypes = mesh_args + [i32, P, P, dbl, dbl, dbl, i64, P, P]
-            for fn in ("oracle_feq", "oracle_geometry", "oracle_gradient", "oracle_run",
+            for fn in ("oracle_feq", "oracle_geometry", "oracle_gradient", "oracle_run", "oracle_run_flux",
                        "oracle_init", "oracle_residual", "oracle_set_threads", "oracle_dvm_grid",
                        "oracle_dvm_maxwell", "oracle_dvm_init", "oracle_dvm_run"):
                 getattr(lib, fn).restype = C.c_int
@@ -165,6 +167,29 @@ def run(case, state: State, n_steps: int, *, tau=None, dt=None) -> State:
                               float(case.dt if dt is None else dt), int(n_steps),
                               _p(state.f), _p(state.W)), "run")
     return state
+
+
+def boundary_faces(mesh, bcs) -> np.ndarray:
+    """Ids of the faces that get a row in run_flux: neighbour < 0 and a patch that is
+    not periodic, in ascending face id."""
+    kind = {p: k for p, k, _ in bcs}
+    nb = np.asarray(mesh.neighbour)
+    return np.array([f for f in range(len(nb)) if nb[f] < 0 and kind.get(int(-1 - nb[f])) != KIND_PERIODIC],
+                    np.int64)
+
+
+def run_flux(case, state: State, n_steps: int, *, tau=None, dt=None) -> np.ndarray:
+    """Advance ``state`` in place by n_steps >= 1 steps and return the momentum that
+    left the fluid through each non-periodic boundary face in the last step,
+    [len(boundary_faces), 2] (sum_a xi_a (xi_a . n l) f_b,a, n l out of the fluid)."""
+    m = _MeshArgs(case.mesh, case.bcs)
+    for a in (state.f, state.W):
+        assert a.flags.c_contiguous and a.dtype == np.float64
+    out = np.zeros((len(boundary_faces(case.mesh, case.bcs)), 2))
+    _check(_load().oracle_run_flux(*m.args(), float(case.tau if tau is None else tau),
+                                   float(case.dt if dt is None else dt), int(n_steps),
+                                   _p(state.f), _p(state.W), _p(out)), "run_flux")
+    return out
 
 
 def residual(W, Ws, vol=None):

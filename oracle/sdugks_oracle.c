@@ -509,10 +509,54 @@ static void one_step(const omesh *m, double tau, double dt, double *f, double *W
     }
 }
 
-/* Run n_steps steps in place on (f, W). */
+/* Momentum that leaves the fluid through each boundary face in the step just taken
+ * (the forces of Sec. IV: C_d and C_l are the wall patch's sums over 0.5 rho U^2 D):
+ * the psi = xi moment of the face's term of Eq. MesoFlux,
+ *   F_f = sum_a xi_a (xi_a . n_f l_f) f_b,a,
+ * with n_f l_f out of the fluid and f_b the interface distribution of step 7 of that
+ * step.  Every face with a neighbour < 0 whose patch is not periodic gets one row, in
+ * ascending face id: out[2 i], out[2 i + 1] for the i-th such face. */
+static void boundary_flux(const omesh *m, const double *fb, double *out)
+{
+    int64_t i = 0;
+    for (int64_t fc = 0; fc < m->nf; fc++) {
+        if (m->nbr[fc] >= 0 || m->bck[-1 - m->nbr[fc]] == KIND_PERIODIC) continue;
+        double px = 0.0, py = 0.0;
+        for (int a = 0; a < NQ; a++) {
+            double s = XI[a][0] * m->nl[2 * fc] + XI[a][1] * m->nl[2 * fc + 1];
+            px += XI[a][0] * s * fb[NQ * fc + a];
+            py += XI[a][1] * s * fb[NQ * fc + a];
+        }
+        out[2 * i] = px;
+        out[2 * i + 1] = py;
+        i++;
+    }
+}
+
+/* Run n_steps steps in place on (f, W); if bflux is given (n_steps >= 1), also the
+ * boundary momentum flux of the last step (boundary_flux). */
+static int run_steps(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, const int64_t *own,
+                     const int64_t *nbr, int64_t nc, int npatch, const int32_t *bck, const double *bcp,
+                     double tau, double dt, int64_t n_steps, double *f, double *W, double *bflux);
+
 int oracle_run(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, const int64_t *own,
                const int64_t *nbr, int64_t nc, int npatch, const int32_t *bck, const double *bcp,
                double tau, double dt, int64_t n_steps, double *f, double *W)
+{
+    return run_steps(np, xy, nf, fpts, own, nbr, nc, npatch, bck, bcp, tau, dt, n_steps, f, W, NULL);
+}
+
+int oracle_run_flux(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, const int64_t *own,
+                    const int64_t *nbr, int64_t nc, int npatch, const int32_t *bck, const double *bcp,
+                    double tau, double dt, int64_t n_steps, double *f, double *W, double *bflux)
+{
+    if (n_steps < 1 || !bflux) return OR_ERR_ARG;
+    return run_steps(np, xy, nf, fpts, own, nbr, nc, npatch, bck, bcp, tau, dt, n_steps, f, W, bflux);
+}
+
+static int run_steps(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, const int64_t *own,
+                     const int64_t *nbr, int64_t nc, int npatch, const int32_t *bck, const double *bcp,
+                     double tau, double dt, int64_t n_steps, double *f, double *W, double *bflux)
 {
     if (!(tau > 0) || !(dt > 0) || n_steps < 0 || !f || !W) return OR_ERR_ARG;
     omesh m;
@@ -526,6 +570,7 @@ int oracle_run(int64_t np, const double *xy, int64_t nf, const int64_t *fpts, co
     w.F = malloc(sizeof(double) * NQ * nc);
     if (!w.feqn || !w.fbp || !w.sig || !w.fb || !w.F) rc = OR_ERR_NOMEM;
     for (int64_t s = 0; s < n_steps && !rc; s++) one_step(&m, tau, dt, f, W, &w);
+    if (!rc && bflux) boundary_flux(&m, w.fb, bflux);
     free(w.feqn); free(w.fbp); free(w.sig); free(w.fb); free(w.F);
     omesh_free(&m);
     return rc;

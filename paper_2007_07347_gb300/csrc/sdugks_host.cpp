@@ -238,7 +238,20 @@ struct Faces {
     int64_t nf = 0;
     std::vector<int64_t> own, nbr;        // nbr: cell or -1 - patch
     std::vector<double> nl, ro, rk;       // [nf][2]
+    std::vector<int64_t> orig;            // the caller's id of each merged face
 };
+
+// Row of each caller face in the per-boundary-face outputs (sdugks_step_boundary_flux):
+// the faces on non-periodic patches, in the caller's face order; -1 for the others.
+// Returns the number of rows.
+int64_t boundary_rows(const sdugks_mesh &m, std::vector<int64_t> &row)
+{
+    row.assign(m.nf, -1);
+    int64_t n = 0;
+    for (int64_t f = 0; f < m.nf; f++)
+        if (m.nbr[f] < 0 && m.bc_kind[-1 - m.nbr[f]] != SDUGKS_BC_PERIODIC) row[f] = n++;
+    return n;
+}
 
 int merge_periodic(const sdugks_mesh &m, Faces &F)
 {
@@ -285,13 +298,14 @@ int merge_periodic(const sdugks_mesh &m, Faces &F)
         }
         newid[f] = F.nf++;
     }
-    F.own.resize(F.nf); F.nbr.resize(F.nf);
+    F.own.resize(F.nf); F.nbr.resize(F.nf); F.orig.resize(F.nf);
     F.nl.resize(2 * F.nf); F.ro.resize(2 * F.nf); F.rk.resize(2 * F.nf);
     for (int64_t f = 0; f < nf; f++) {
         const int64_t k = newid[f];
         if (k < 0) continue;
         const int64_t o = m.own[f];
         F.own[k] = o;
+        F.orig[k] = f;
         F.nl[2 * k] = m.nl[2 * f]; F.nl[2 * k + 1] = m.nl[2 * f + 1];
         F.ro[2 * k] = m.xf[2 * f] - m.xc[2 * o]; F.ro[2 * k + 1] = m.xf[2 * f + 1] - m.xc[2 * o + 1];
         if (m.nbr[f] >= 0) {
@@ -380,6 +394,8 @@ struct sdugks_solver {
     int graph_len = 0;
     double mesh_bytes = 0.0;
     double *d_force = nullptr;      // [MAXPATCH][2] (allocated on first force step)
+    int64_t n_bfaces = 0;           // rows of the per-boundary-face outputs
+    double *d_bface = nullptr;      // [n_bfaces][2] (allocated on first per-face flux step)
     int32_t side_patch[4] = {-1, -1, -1, -1};   // Cartesian: patch of each grid side
 };
 
@@ -583,6 +599,7 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
         s->snap = A.take<double>(2 * npad);
         s->partial = A.take<double>(4 * (size_t)s->n_red_blocks);
         s->red = A.take<double>(5);
+        s->ci.bidx = A.take<int32_t>(2 * ((size_t)g.nx + g.ny));
         for (int b = 0; b < 2; b++) s->st.f[b] = A.take<char>(NQ * npad * fs);
         for (int b = 0; b < 2; b++) s->st.W[b] = A.take<double>(3 * npad);
     };
@@ -598,6 +615,21 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     }
     Arena A{s->dmem, 0, s->dbytes};
     layout(A);
+    // boundary-face row of each side face, by side and position along the side
+    std::vector<int32_t> bidx(2 * ((size_t)g.nx + g.ny), -1);
+    {
+        std::vector<int64_t> row;
+        s->n_bfaces = boundary_rows(m, row);
+        for (int64_t f = 0; f < m.nf; f++) {
+            if (row[f] < 0) continue;
+            const int64_t o = m.own[f];
+            const double nx_ = m.nl[2 * f], ny_ = m.nl[2 * f + 1];
+            size_t q;
+            if (std::fabs(nx_) > std::fabs(ny_)) q = nx_ > 0 ? (size_t)g.nx + g.cj[o] : 2 * (size_t)g.nx + g.ny + g.cj[o];
+            else q = ny_ > 0 ? (size_t)g.nx + g.ny + g.ci[o] : (size_t)g.ci[o];
+            bidx[q] = (int32_t)row[f];
+        }
+    }
     for (int b = 0; b < 2; b++) { s->ci.f[b] = s->st.f[b]; s->ci.W[b] = s->st.W[b]; }
     s->ci.snap = s->snap;
     s->ci.err = reinterpret_cast<int32_t *>(s->red + 4);
@@ -618,6 +650,8 @@ static int create_cart(const sdugks_mesh &m, const CartGrid &g, const sdugks_par
     chk(cudaMemcpy(s->perm, perm.data(), n * 4, cudaMemcpyHostToDevice), "upload perm");
     chk(cudaMemcpy(s->loc, loc.data(), n * 4, cudaMemcpyHostToDevice), "upload loc");
     chk(cudaMemcpy(s->vol, vol.data(), npad * 8, cudaMemcpyHostToDevice), "upload vol");
+    chk(cudaMemcpy(const_cast<int32_t *>(s->ci.bidx), bidx.data(), bidx.size() * 4, cudaMemcpyHostToDevice),
+        "upload boundary rows");
     chk(cudaMallocHost(&s->h_red, 5 * sizeof(double)), "cudaMallocHost");
     chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     chk((cudaError_t)prepare(prec, SDUGKS_KERNEL_CARTESIAN), "kernel attributes");
@@ -852,6 +886,9 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     std::vector<uint16_t> sig_nb, cell_lf((size_t)MAXF * npad, LF_NONE);
     std::vector<int32_t> sig_cell;   // internal cell of each gradient row
     std::vector<uint32_t> lf_ab;
+    std::vector<int32_t> lf_bface;  // boundary-face row of each local face (-1: none)
+    std::vector<int64_t> brow;
+    const int64_t n_bfaces = boundary_rows(*m, brow);
     std::vector<double> lf_geo;   // [n_lf][6], transposed at upload
     std::vector<uint8_t> islk((size_t)MAXF * npad, SK_NONE);
     std::vector<double> iainv(3 * npad, 0.0), ivol(npad, 1.0), idtv(npad, 0.0);
@@ -940,6 +977,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                         const uint32_t b = F.nbr[f] >= 0 ? (uint32_t)local[iperm[F.nbr[f]]]
                                                          : (LF_BOUNDARY | (uint32_t)(-1 - F.nbr[f]));
                         lf_ab.push_back(a | (b << 16));
+                        lf_bface.push_back(F.nbr[f] >= 0 ? -1 : (int32_t)brow[F.orig[f]]);
                         const double q6[6] = {F.nl[2 * f], F.nl[2 * f + 1], F.ro[2 * f], F.ro[2 * f + 1],
                                               F.rk[2 * f], F.rk[2 * f + 1]};
                         lf_geo.insert(lf_geo.end(), q6, q6 + 6);
@@ -1018,6 +1056,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     s->p = *prm;
     if (s->p.graph_steps == 0) s->p.graph_steps = 64;
     if (s->p.graph_steps > 0) s->p.graph_steps = std::max(2, s->p.graph_steps / 2 * 2);
+    s->n_bfaces = n_bfaces;
     s->stream = static_cast<cudaStream_t>(stream);
     s->n = n; s->npad = npad; s->nf = F.nf; s->n_tiles = nt; s->halo_cells = halo_total;
     s->kernel = SDUGKS_KERNEL_TILED;
@@ -1043,6 +1082,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->tm.sig_ai = A.take<char>((size_t)3 * sig_cell.size() * rs);
         s->tm.cell_lf = A.take<uint16_t>(cell_lf.size());
         s->tm.lf_ab = A.take<uint32_t>(lf_ab.size());
+        s->tm.lf_bface = A.take<int32_t>(lf_bface.size());
         s->tm.lf_geo = A.take<char>(lf_geo.size() * rs);
         s->tm.dtV = A.take<char>(npad * rs);
         s->tm.vol = s->vol;
@@ -1115,6 +1155,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     chk(up(s->tm.sig_ai, gsa.data(), gsa.size()), "upload LLSR inverse");
     chk(up(s->tm.cell_lf, cell_lf.data(), cell_lf.size() * 2), "upload cell faces");
     chk(up(s->tm.lf_ab, lf_ab.data(), lf_ab.size() * 4), "upload face sides");
+    chk(up(s->tm.lf_bface, lf_bface.data(), lf_bface.size() * 4), "upload boundary rows");
     chk(up(s->tm.lf_geo, ggeo.data(), ggeo.size()), "upload face geometry");
     chk(up(s->tm.dtV, gdtv.data(), gdtv.size()), "upload dtV");
     chk(cudaMallocHost(&s->h_red, 5 * sizeof(double)), "cudaMallocHost");
@@ -1238,21 +1279,27 @@ extern "C" int sdugks_step(sdugks_solver *s, int64_t n)
     return SDUGKS_OK;
 }
 
-extern "C" int sdugks_step_forces(sdugks_solver *s, double *force)
+extern "C" int sdugks_step_boundary_flux(sdugks_solver *s, double *force, double *face_flux)
 {
-    if (!s || !force) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
     if (!s->initialised) return fail(SDUGKS_ERR_STATE, "step before init or set_state");
     CUDA_TRY(cudaSetDevice(s->device));
-    if (!s->d_force) CUDA_TRY(cudaMalloc(&s->d_force, sizeof(double) * 2 * MAXPATCH));
-    CUDA_TRY(cudaMemsetAsync(s->d_force, 0, sizeof(double) * 2 * MAXPATCH, s->stream));
+    if (force && !s->d_force) CUDA_TRY(cudaMalloc(&s->d_force, sizeof(double) * 2 * MAXPATCH));
+    if (face_flux && s->n_bfaces > 0 && !s->d_bface)
+        CUDA_TRY(cudaMalloc(&s->d_bface, sizeof(double) * 2 * (size_t)s->n_bfaces));
+    double *d_force = force ? s->d_force : nullptr;
+    double *d_bface = face_flux && s->n_bfaces > 0 ? s->d_bface : nullptr;
+    if (d_force) CUDA_TRY(cudaMemsetAsync(d_force, 0, sizeof(double) * 2 * MAXPATCH, s->stream));
     cudaError_t e;
     if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
         CartInst ci = s->ci;
-        ci.force = s->d_force;                 // per grid side
+        ci.force = d_force;                    // per grid side
+        ci.bface = d_bface;
         e = launch_step_cart(s->p.precision, s->cart_shape, ci, s->tma, s->cart_general, s->cur, s->stream);
     } else {
         TiledMesh tm = s->tm;
-        tm.force = s->d_force;                 // per patch
+        tm.force = d_force;                    // per patch
+        tm.bface = d_bface;
         const int a = s->cur;
         e = s->p.precision == P_FP64
                 ? launch_step_tiled_fp64(tm, s->coefs, s->st.f[a], s->st.f[1 - a], s->st.W[a], s->st.W[1 - a], s->stream)
@@ -1263,20 +1310,31 @@ extern "C" int sdugks_step_forces(sdugks_solver *s, double *force)
     s->cur = 1 - s->cur;
     s->steps_done++;
     double h[2 * MAXPATCH];
-    CUDA_TRY(cudaMemcpyAsync(h, s->d_force, sizeof h, cudaMemcpyDeviceToHost, s->stream));
+    if (d_force) CUDA_TRY(cudaMemcpyAsync(h, d_force, sizeof h, cudaMemcpyDeviceToHost, s->stream));
+    if (d_bface)
+        CUDA_TRY(cudaMemcpyAsync(face_flux, d_bface, sizeof(double) * 2 * (size_t)s->n_bfaces, cudaMemcpyDeviceToHost,
+                                 s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
-    for (int q = 0; q < 2 * MAXPATCH; q++) force[q] = 0.0;
-    if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
-        for (int side = 0; side < 4; side++) {
-            const int p = s->side_patch[side];
-            if (p < 0 || s->coefs.bc_kind[p] == SDUGKS_BC_PERIODIC) continue;
-            force[2 * p] += h[2 * side];
-            force[2 * p + 1] += h[2 * side + 1];
+    if (force) {
+        for (int q = 0; q < 2 * MAXPATCH; q++) force[q] = 0.0;
+        if (s->kernel == SDUGKS_KERNEL_CARTESIAN) {
+            for (int side = 0; side < 4; side++) {
+                const int p = s->side_patch[side];
+                if (p < 0 || s->coefs.bc_kind[p] == SDUGKS_BC_PERIODIC) continue;
+                force[2 * p] += h[2 * side];
+                force[2 * p + 1] += h[2 * side + 1];
+            }
+        } else {
+            for (int q = 0; q < 2 * MAXPATCH; q++) force[q] = h[q];
         }
-    } else {
-        for (int q = 0; q < 2 * MAXPATCH; q++) force[q] = h[q];
     }
     return SDUGKS_OK;
+}
+
+extern "C" int sdugks_step_forces(sdugks_solver *s, double *force)
+{
+    if (!s || !force) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    return sdugks_step_boundary_flux(s, force, nullptr);
 }
 
 extern "C" int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double *d_u)
@@ -1362,6 +1420,7 @@ extern "C" int sdugks_solver_info(const sdugks_solver *s, sdugks_info *o)
     o->nx = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.nx : 0;
     o->ny = s->kernel == SDUGKS_KERNEL_CARTESIAN ? s->ci.ny : 0;
     o->staging = s->tma ? SDUGKS_STAGING_TMA : SDUGKS_STAGING_LOADS;
+    o->n_boundary_faces = s->n_bfaces;
     o->one_code_path = s->cart_general ? 1 : 0;
     return SDUGKS_OK;
 }
@@ -1373,6 +1432,7 @@ extern "C" void sdugks_solver_destroy(sdugks_solver *s)
     if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->staging) cudaFree(s->staging);
+    if (s->d_bface) cudaFree(s->d_bface);
     if (s->d_force) cudaFree(s->d_force);
     if (s->h_red) cudaFreeHost(s->h_red);
     if (s->dmem) cudaFree(s->dmem);

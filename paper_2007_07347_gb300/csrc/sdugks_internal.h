@@ -75,6 +75,8 @@ struct TiledMesh {
     const void *dtV;          // [npad] dt / V (compute precision)
     const double *vol;        // [npad] V
     double *force;            // nullptr, or [MAXPATCH][2]: momentum flux out of the fluid per boundary patch
+    const int32_t *lf_bface;  // [n_lf] boundary-face row of each local face (-1: interior or periodic)
+    double *bface;            // nullptr, or [n_bfaces][2]: momentum flux out of the fluid per boundary face
 };
 constexpr uint16_t LF_SECOND = 0x8000, LF_NONE = 0xFFFF;
 constexpr uint32_t LF_BOUNDARY = 0xC000;
@@ -100,6 +102,9 @@ struct CartInst {
     double *force;            // nullptr, or [4][2]: momentum flux out of the fluid per grid side
     int32_t *err;             // nullptr, or a device flag set to 1 when a bounded staging wait gave up
     uint64_t tma_wait_ns;     // TMA staging: wait limit of a block's copies (0: give up at once)
+    const int32_t *bidx;      // [2 (nx + ny)] boundary-face row of each side face: bottom (by i), right
+                              //   (by j), top (by i), left (by j); -1 on periodic sides
+    double *bface;            // nullptr, or [n_bfaces][2]: momentum flux out of the fluid per boundary face
 };
 
 // Device state of one solver, ping-pong: f [2][NQ][npad] (element type by

@@ -315,10 +315,29 @@ __device__ __forceinline__ void cart_interior_face_f32x2(float flux[6], const fl
 // Boundary face of the own cell in direction D (0 +x, 1 -x, 2 +y, 3 -y) on grid side
 // `side`: adds the outward flux (xi . n l) f_b of every crossing velocity to F
 // (Sec. III rules).
+// Diagnostic steps: the momentum (px, py) leaving the fluid through the boundary face
+// at position pos (i on the bottom and top sides, j on the left and right) of a grid
+// side, added to the side's total and written to the face's row.
+__device__ __forceinline__ void cart_face_momentum(const CartInst &m, int side, int pos, double px, double py)
+{
+    if (m.force) {
+        atomicAdd(&m.force[2 * side], px);
+        atomicAdd(&m.force[2 * side + 1], py);
+    }
+    if (m.bface) {
+        const int base = side == 0 ? 0 : side == 1 ? m.nx : side == 2 ? m.nx + m.ny : 2 * m.nx + m.ny;
+        const int q = m.bidx[base + pos];
+        if (q >= 0) {
+            m.bface[2 * q] = px;
+            m.bface[2 * q + 1] = py;
+        }
+    }
+}
+
 template <int D, class R, bool DIAG>
 __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int lme, const Sten<R> &st,
-                                                   const CartInst &m, int side, const CartK<R> &k, const R fn[NQ],
-                                                   const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY)
+                                                   const CartInst &m, int side, int pos, const CartK<R> &k,
+                                                   const R fn[NQ], const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY)
 {
     const R nx = D == 0 ? k.hy : (D == 1 ? -k.hy : R(0));
     const R ny = D == 2 ? k.hx : (D == 3 ? -k.hx : R(0));
@@ -354,10 +373,7 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int 
     SDUGKS_BFACE_ALPHA(0) SDUGKS_BFACE_ALPHA(1) SDUGKS_BFACE_ALPHA(2) SDUGKS_BFACE_ALPHA(3) SDUGKS_BFACE_ALPHA(4)
     SDUGKS_BFACE_ALPHA(5) SDUGKS_BFACE_ALPHA(6) SDUGKS_BFACE_ALPHA(7) SDUGKS_BFACE_ALPHA(8)
 #undef SDUGKS_BFACE_ALPHA
-    if (DIAG && m.force) {       // diagnostic steps only: momentum leaving the fluid through this side
-        atomicAdd(&m.force[2 * side], to_f64<R>(px_));
-        atomicAdd(&m.force[2 * side + 1], to_f64<R>(py_));
-    }
+    if (DIAG) cart_face_momentum(m, side, pos, to_f64<R>(px_), to_f64<R>(py_));   // diagnostic steps only
 }
 
 // One TX x TY block (block coordinates tbx, tby) of one grid: reads buffer `par`,
@@ -586,25 +602,45 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NSX + fW];
         } else {
-            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, gj, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inE) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NSX + fE];
         } else {
-            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, gj, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inS) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NSY + fS];
         } else {
-            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, gi, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
         }
         if (inN) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NSY + fN];
         } else {
-            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, gi, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+        }
+
+        if (DIAG && (m.force || m.bface)) {
+            // symmetry sides are staged as mirror ghosts, so their faces are interior
+            // faces here: the momentum leaving the fluid through one is that face's flux
+            // moment (fluxes are oriented along +x / +y), with the outward sign
+            auto sym_face = [&](int side, int pos, const R *fl, int stride, bool y_face, R sgn) {
+                R px_ = R(0), py_ = R(0);
+#pragma unroll
+                for (int r = 0; r < 6; r++) {
+                    const int a = y_face ? YSLOT_A(r) : XSLOT_A(r);
+                    px_ += R(EX(a)) * fl[r * stride];
+                    py_ += R(EY(a)) * fl[r * stride];
+                }
+                cart_face_momentum(m, side, pos, to_f64<R>(sgn * px_), to_f64<R>(sgn * py_));
+            };
+            if (symL && gi == 0) sym_face(3, gj, s_fx + fW, S::NSX, false, R(-1));
+            if (symR && gi == nx - 1) sym_face(1, gj, s_fx + fE, S::NSX, false, R(1));
+            if (symB && gj == 0) sym_face(0, gi, s_fy + fS, S::NSY, true, R(-1));
+            if (symT && gj == ny - 1) sym_face(2, gi, s_fy + fN, S::NSY, true, R(1));
         }
 
         // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)

@@ -58,6 +58,24 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // all committed groups but the most recent one
 __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Diagnostic steps (m.force or m.bface set): the momentum (px, py) leaving the fluid
+// through boundary face `q` (index over all local faces) of patch p, added to the
+// patch total and written to the face's row.
+__device__ __forceinline__ void tiled_face_momentum(const TiledMesh &m, int p, int q, double px, double py)
+{
+    if (m.force) {
+        atomicAdd(&m.force[2 * p], px);
+        atomicAdd(&m.force[2 * p + 1], py);
+    }
+    if (m.bface) {
+        const int row = m.lf_bface[q];
+        if (row >= 0) {
+            m.bface[2 * row] = px;
+            m.bface[2 * row + 1] = py;
+        }
+    }
+}
+
 template <int P>
 __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict__ fin, const double *__restrict__ Wn,
                                          int64_t g, int64_t np, const CoefR<typename Store<P>::R> &k,
@@ -267,10 +285,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 px_ += R(EX(a)) * fl;
                 py_ += R(EY(a)) * fl;
             }
-            if (m.force) {
-                atomicAdd(&m.force[2 * (B & 0xFF)], to_f64<R>(px_));
-                atomicAdd(&m.force[2 * (B & 0xFF) + 1], to_f64<R>(py_));
-            }
+            tiled_face_momentum(m, B & 0xFF, f0 + lf, to_f64<R>(px_), to_f64<R>(py_));
         } else {
             // boundary face of cell A (an interior cell of the tile): Sec. III rules
             const int p = B & 0xFF;
@@ -301,10 +316,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 px_ += R(EX(a)) * (s * fb);
                 py_ += R(EY(a)) * (s * fb);
             }
-            if (m.force) {       // diagnostic steps only: momentum leaving the fluid through this patch
-                atomicAdd(&m.force[2 * p], to_f64<R>(px_));
-                atomicAdd(&m.force[2 * p + 1], to_f64<R>(py_));
-            }
+            tiled_face_momentum(m, p, f0 + lf, to_f64<R>(px_), to_f64<R>(py_));
         }
     }
     __syncthreads();

@@ -47,7 +47,7 @@ class Info(C.Structure):
                 ("steps_done", C.c_int64), ("device_bytes", C.c_int64), ("state_bytes_per_cell_step", C.c_double),
                 ("mesh_bytes_per_cell_step", C.c_double), ("kernel", C.c_int32), ("precision", C.c_int32),
                 ("tile_cells", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("staging", C.c_int32),
-                ("one_code_path", C.c_int32)]
+                ("one_code_path", C.c_int32), ("n_boundary_faces", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +84,7 @@ def lib():
                 "sdugks_set_state": [P, P, P],
                 "sdugks_solver_info": [P, P],
                 "sdugks_step_forces": [P, P],
+                "sdugks_step_boundary_flux": [P, P, P],
                 "sdugks_residual_noalloc": [i64, P, P, P, P, P],
                 "sdugks_batch_create": [i64, i32, i32, P, P],
                 "sdugks_batch_footprint": [P, P, P],
@@ -212,6 +213,15 @@ class Solver:
         out = np.zeros((64, 2))
         _ck(lib().sdugks_step_forces(self._h, _ptr(out)), "sdugks_step_forces")
         return out
+
+    def step_boundary_flux(self, forces: bool = False):
+        """One step; returns [n_boundary_faces, 2]: the momentum leaving the fluid through
+        each non-periodic boundary face (caller's face order), and with ``forces`` also
+        the [64, 2] patch sums of sdugks_step_forces."""
+        out = np.zeros((self.info()["n_boundary_faces"], 2))
+        frc = np.zeros((64, 2)) if forces else None
+        _ck(lib().sdugks_step_boundary_flux(self._h, _ptr(frc), _ptr(out)), "sdugks_step_boundary_flux")
+        return (out, frc) if forces else out
 
     def macros(self):
         rho = np.empty(self.n)
