@@ -1,20 +1,26 @@
 """Benchmark of the S-DUGKS D2Q9 step on one GB300 (or N replicas, one per GPU).
 
 Workload (default): the lid-driven cavity of 256 x 256 unit cells, Re 1000, lid
-U = 0.1, CFL 0.5, f stored in FP32, started from rest.  One benchmark step is one
-residual interval: 1000 fused S-DUGKS time steps (steps 1-11 of Sec. II, each one
-kernel launch, replayed from a captured CUDA graph) followed by the FP64 residual
-and mass reduction of Sec. IV.  The default --warmup 3 --steps 17 therefore runs
-exactly the 20,000 steps of that case.
+U = 0.1, CFL 0.5, f stored in FP32, started from rest (the configuration the metric is
+quoted on).  One benchmark step is five residual intervals: 5 x (1000 fused S-DUGKS
+time steps, steps 1-11 of Sec. II, each one kernel launch, replayed from captured CUDA
+graphs, then the FP64 residual and mass reduction of Sec. IV).  The launch
+configuration (block shape, staging, graph length) is the autotuner's choice.
 
 Metric: MLUPS = cells x 9 velocities x time steps / s / 1e6 ("cell-Q updates").
 The device-timed region starts with f, W resident in HBM; L2 is flushed (a 256 MB
 buffer is rewritten) before every timed step, outside its events.  The state of
-this case is 9.4 MB, so inside a step the 1000 launches run from L2.
+this case is 7.9 MB, so inside a step the launches run from L2 (the roofline object
+says so: "l2_resident").
+
+The same line carries the other single-GPU configurations, each timed the same way
+and with its own roofline ("configs"): the 512 x 256 cylinder O-mesh (bf16-deviation
+storage, unstructured tiled kernel) and the batch of 256 cavities (11.7 M cells,
+1.4 GB of state: HBM-resident).
 
 e2e: the same metric through the C-ABI from pinned host buffers: each step uploads
-the full state (f, W in FP64), advances 1000 steps, runs the residual and reads rho
-and u back.
+the full state (f, W in FP64), advances the time steps, runs the residual and reads
+rho and u back.
 
 --impl reference: the FP64 C oracle, as it stands, on the host cores, on bounded
 samples of the same workload (rank 0 only).
@@ -38,8 +44,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2007_07347_gb300 import meshes as M  # noqa: E402
 
-INTERVAL = 1000
+INTERVAL = 1000            # time steps per residual check (Sec. IV)
+INTERVALS_PER_STEP = 5     # residual intervals per benchmark step
 STATE_BYTES = {"fp64": 192, "fp32": 120, "bf16dev": 84, "fp16dev": 84}    # f and W (FP64) each read and written once
+L2_BYTES = 129e6
 
 
 def parse():
@@ -60,9 +68,13 @@ def parse():
                          "40x40 micro cavity on a 100x100 velocity grid (Kn 1)")
     ap.add_argument("--tile-cells", type=int, default=0,
                     help="block / tile size of the solver (0: the solver's own choice)")
-    ap.add_argument("--staging", default="loads", choices=["loads", "tma"],
+    ap.add_argument("--staging", default=None, choices=["loads", "tma"],
                     help="cavity: how the Cartesian kernel stages its interior blocks (per-thread loads or "
-                         "TMA tensor copies)")
+                         "TMA tensor copies; default: the autotuner's choice)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="the solver's own launch configuration instead of the autotuner's")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other single-GPU configurations (cylinder, batch) in the default line")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
     args = ap.parse_args()
@@ -98,18 +110,17 @@ def initial_u(case):
 def config(args, case):
     state_mb = STATE_BYTES[args.precision] * case.mesh.n_cells / 1e6
     return {"workload": workload_name(args),
-            "cells": case.mesh.n_cells, "velocities": 9, "time_steps_per_step": INTERVAL,
+            "cells": case.mesh.n_cells, "velocities": 9, "time_steps_per_step": INTERVAL * INTERVALS_PER_STEP,
             "storage": args.precision, "tau": case.tau, "dt": case.dt,
             "l2": f"flushed (256 MB rewrite) before each timed step; the {state_mb:.1f} MB state is L2-resident "
                   f"within a step",
-            "parallelism": f"replicas x{args.gpus}",
-            **({"staging": args.staging} if args.workload == "cavity" else {})}
+            "parallelism": f"replicas x{args.gpus}"}
 
 
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    """nvidia-smi clock/throttle samples every 50 ms while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -122,7 +133,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -277,6 +288,71 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def make_solver(S, case, args, precision, stream, cartesian_options=True):
+    """The solver of a workload: the autotuner's launch configuration, unless one was
+    given on the command line (or --no-autotune)."""
+    if args.no_autotune or args.tile_cells or (args.staging and cartesian_options):
+        kw = {"tile_cells": args.tile_cells}
+        if cartesian_options and args.staging:
+            kw["staging"] = args.staging
+        return S.Solver.from_case(case, precision, stream=stream, **kw), None
+    s = S.Solver.tuned(case, precision, stream=stream)
+    return s, s.tune
+
+
+def time_steps(s, steps, warmup, stream, flush, clk=None):
+    """Benchmark steps of INTERVALS_PER_STEP x (INTERVAL time steps + residual), L2
+    flushed before each: per-step ms, mean ms per step launch, last (eps, mass)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            for _ in range(INTERVALS_PER_STEP):
+                s.step(INTERVAL)
+                s.residual()
+        torch.cuda.synchronize()
+        E = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+        ev = [(E(), E(), [(E(), E()) for _ in range(INTERVALS_PER_STEP)]) for _ in range(steps)]
+        last = None
+        if clk:
+            clk.__enter__()
+        try:
+            for k in range(steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                for a, b in ev[k][2]:
+                    a.record(stream)
+                    s.step(INTERVAL)
+                    b.record(stream)
+                    last = s.residual()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        finally:
+            if clk:
+                clk.__exit__(None, None, None)
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    launch_ms = float(np.mean([a.elapsed_time(b) / INTERVAL for e in ev for a, b in e[2]]))
+    return step_ms, launch_ms, last
+
+
+def roofline_of(info, precision, n, launch_ms, key):
+    """Roofline of the step kernel: algorithmic bytes (state read and written once, plus
+    the mesh data an unstructured step must read) over the mean launch time."""
+    peak, peak_kind = measured_peaks()
+    mesh_b = info["mesh_bytes_per_cell_step"] if info["kernel"] == 1 else 0.0
+    alg_bytes = (STATE_BYTES[precision] + mesh_b) * n
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    kname = {1: "k_step_tiled", 2: "k_step_cart"}[info["kernel"]]
+    resident = (STATE_BYTES[precision] + mesh_b) * n < 0.8 * L2_BYTES
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(key), "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes,
+            "state_bytes_per_cell_step": STATE_BYTES[precision], "mesh_bytes_per_cell_step": mesh_b,
+            "avg_launch_us": launch_ms * 1e3, "peak_kind": f"{peak_kind} (hbm_gbs)",
+            "l2_resident": resident,
+            "note": ("state and mesh fit in L2 (129 MB) and stay there within a benchmark step: achieved counts "
+                     "algorithmic bytes, DRAM moves less (traffic)") if resident else
+                    "state larger than L2: every launch streams it from HBM"}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -293,8 +369,7 @@ def run_ours(args):
     case = workload(args)
     n = case.mesh.n_cells
     stream = torch.cuda.Stream()
-    s = S.Solver.from_case(case, args.precision, stream=stream, tile_cells=args.tile_cells,
-                           staging=args.staging if args.workload == "cavity" else "loads")
+    s, tune = make_solver(S, case, args, args.precision, stream, cartesian_options=args.workload == "cavity")
     s.init(None, initial_u(case))
     info = s.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -304,27 +379,13 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            s.step(INTERVAL)
-            s.residual()
-        barrier()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-        eps_hist = []
-        with ClockSampler(torch.cuda.current_device()) as clk:
-            for k in range(args.steps):
-                flush.fill_(float(k))
-                ev[k][0].record(stream)
-                s.step(INTERVAL)
-                ev[k][1].record(stream)
-                eps_hist.append(s.residual())
-                ev[k][2].record(stream)
-            barrier()
-        step_ms = [e[0].elapsed_time(e[2]) for e in ev]
-        kern_ms = [e[0].elapsed_time(e[1]) / INTERVAL for e in ev]
+    barrier()
+    clk = ClockSampler(torch.cuda.current_device())
+    step_ms, launch_ms, last = time_steps(s, args.steps, args.warmup, stream, flush, clk)
+    barrier()
     total_ms = max_over_ranks(sum(step_ms), world)
-    cells_q = n * 9 * INTERVAL * args.steps * world
-    value = cells_q / (total_ms / 1e3) / 1e6
+    tsteps = INTERVAL * INTERVALS_PER_STEP
+    value = n * 9 * tsteps * args.steps * world / (total_ms / 1e3) / 1e6
 
     # ---- e2e through the C-ABI with pinned host buffers
     f_h = torch.empty((n, 9), dtype=torch.float64).pin_memory().numpy()
@@ -340,47 +401,116 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         S._ck(L.sdugks_set_state(s._h, P(f_h), P(W_h)), "set_state")
-        S._ck(L.sdugks_step(s._h, INTERVAL), "step")
-        s.residual()
+        for _ in range(INTERVALS_PER_STEP):
+            S._ck(L.sdugks_step(s._h, INTERVAL), "step")
+            s.residual()
         S._ck(L.sdugks_get_macros(s._h, P(rho_h), P(u_h)), "get_macros")
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_val = n * 9 * INTERVAL * e2e_steps * world / e2e_s / 1e6
+    e2e_val = n * 9 * tsteps * e2e_steps * world / e2e_s / 1e6
 
+    configs = {}
+    if args.workload == "cavity" and not args.no_configs and args.n == 256 and args.precision == "fp32":
+        configs = other_configs(args, S, stream, flush)
     if rank != 0:
         return
-    peak, peak_kind = measured_peaks()
-    # algorithmic bytes per launch: the state (f and W read and written once) and, on
-    # an unstructured mesh, the mesh data the step must read
-    mesh_b = info["mesh_bytes_per_cell_step"] if info["kernel"] == 1 else 0.0
-    alg_bytes = (STATE_BYTES[args.precision] + mesh_b) * n
-    kern_avg_s = float(np.mean(kern_ms)) / 1e3
-    achieved = alg_bytes / kern_avg_s / 1e9
-    kname = {1: "k_step_tiled", 2: "k_step_cart"}[info["kernel"]]
-    key = f"{kname}_{args.precision}_{workload_tag(args)}"
+    key = f"{ {1: 'k_step_tiled', 2: 'k_step_cart'}[info['kernel']] }_{args.precision}_{workload_tag(args)}"
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16dev": "f32 (bf16 storage)", "fp16dev": "f32 (fp16 storage)"}[args.precision],
         "data": "synthetic", "config": config(args, case),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(key),
-                     "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes,
-                     "avg_launch_us": kern_avg_s * 1e6, "peak_kind": f"{peak_kind} (hbm_gbs)"},
+        "roofline": roofline_of(info, args.precision, n, launch_ms, key),
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": n * 12 * 8,
-                "d2h_bytes_per_step": n * 3 * 8 + 32, "steps": e2e_steps},
-        "gpu_launches": args.steps * (INTERVAL + 2),
-        "residual_last": eps_hist[-1][0], "mass_last": eps_hist[-1][1],
-        "solver": {k: info[k] for k in ("n_tiles", "halo_cells", "mesh_bytes_per_cell_step", "kernel")},
+                "d2h_bytes_per_step": n * 3 * 8 + 32 * INTERVALS_PER_STEP, "steps": e2e_steps},
+        "gpu_launches": args.steps * INTERVALS_PER_STEP * (INTERVAL + 2),
+        "residual_last": last[0], "mass_last": last[1],
+        "solver": {k: info[k] for k in ("n_tiles", "halo_cells", "mesh_bytes_per_cell_step", "kernel", "tile_cells",
+                                        "staging", "one_code_path")},
+        "autotune": tune,
         "mcell_steps_per_s": value / 9,
     }
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
+    if configs:
+        line["configs"] = configs
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds)
     print(json.dumps(line))
+
+
+def other_configs(args, S, stream, flush):
+    """The other single-GPU configurations, each timed like the headline (CUDA events on
+    the launching stream, L2 flushed before each timed step): the cylinder O-mesh in
+    bf16-deviation storage on the unstructured kernel, and the batch of 256 cavities."""
+    import torch
+    out = {}
+    # -- cylinder: 512 x 256 O-mesh, Re 40, far field at 50 D, ids shuffled, from the free stream
+    case = M.cylinder(512, 256)
+    n = case.mesh.n_cells
+    s, tune = make_solver(S, case, args, "bf16dev", stream, cartesian_options=False)
+    s.init(None, initial_u(case))
+    info = s.info()
+    steps = max(3, min(args.steps, 10))
+    clk = ClockSampler(torch.cuda.current_device())
+    step_ms, launch_ms, last = time_steps(s, steps, 2, stream, flush, clk)
+    tsteps = INTERVAL * INTERVALS_PER_STEP
+    out["cylinder_512x256_bf16dev"] = {
+        "workload": "cylinder O-mesh 512x256 (r 0.5-50, first cell 0.005), Re 40, U 0.1, far field + no-slip wall, "
+                    "cell ids shuffled (seed 0), from uniform flow; f as bf16 deviation, FP32 compute",
+        "value": n * 9 * tsteps * steps / (sum(step_ms) / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+        "time_steps_per_step": tsteps, "ms_per_step": sum(step_ms) / steps, "cells": n,
+        "roofline": roofline_of(info, "bf16dev", n, launch_ms, f"k_step_tiled_bf16dev_cylinder512x256"),
+        "autotune": tune, "residual_last": last[0], "clocks": clk.summary(),
+        "gpu_launches": steps * INTERVALS_PER_STEP * (INTERVAL + 2)}
+    s.close()
+    # -- batch: 256 cavities, N ~ logU[32, 512], Re ~ logU[100, 5000] (seed 1), FP32, 11.7 M cells
+    specs = M.batch_cavities(256, seed=1)
+    cases = [M.cavity(nn, Re=re) for nn, re in specs]
+    cells = sum(c.mesh.n_cells for c in cases)
+    probe = S.Batch(1 << 20, "fp32", 4)
+    meshes = [S.Mesh(c.mesh, c.bcs) for c in cases]
+    need = sum(probe.footprint(m) for m in meshes)
+    probe.close()
+    b = S.Batch(need + (64 << 20), "fp32", 512, stream=stream)
+    for c, m in zip(cases, meshes):
+        b.add(m, c.tau, c.dt)
+    b.autotune(2)
+    interval, bsteps = 100, 5
+    with torch.cuda.stream(stream):
+        b.step(2 * interval)
+        b.residual()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(torch.cuda.current_device())
+        with clk:
+            e0.record(stream)
+            for _ in range(bsteps):
+                b.step(interval)
+                b.residual()
+            e1.record(stream)
+            torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    peak, peak_kind = measured_peaks()
+    alg = 120.0 * cells
+    launch_s = t / (interval * bsteps)               # the residual reductions are included
+    out["batch_256_cavities_fp32"] = {
+        "workload": "batch of 256 lid-driven cavities, N~logU[32,512], Re~logU[100,5000], seed 1, lid 0.1, CFL 0.5, "
+                    "FP32, one batched launch per step over the (instance, 16x16 block) work list",
+        "value": cells * 9 * interval * bsteps / t / 1e6, "unit": "MLUPS", "steps": bsteps,
+        "time_steps_per_step": interval, "ms_per_step": 1e3 * t / bsteps, "cells": cells,
+        "roofline": {"bound": "hbm", "achieved": alg / launch_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / launch_s / 1e9 / peak, "traffic": None, "kernel": "k_step_batch",
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_us": launch_s * 1e6,
+                     "peak_kind": f"{peak_kind} (hbm_gbs)", "l2_resident": False,
+                     "note": "1.4 GB of state: every launch streams it from HBM; the launch time includes the share "
+                             "of the per-instance residual reductions (one per 100 steps)"},
+        "batch": b.info(), "clocks": clk.summary(),
+        "gpu_launches": bsteps * (interval + 2)}
+    b.close()
+    return out
 
 
 def run_batch(args):

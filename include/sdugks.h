@@ -258,6 +258,37 @@ int sdugks_residual_noalloc(int64_t n, const double *d_W, const double *d_vol, d
 
 int sdugks_solver_info(const sdugks_solver *s, sdugks_info *out);
 
+/* ---- autotuner ------------------------------------------------------------------ */
+/* A facility of this library (the paper has no counterpart): the launch configuration
+ * of a solve chosen by timing it on the current device. */
+typedef struct sdugks_tune_info {
+    double ns_per_step;   /* measured time of one step with the chosen configuration   */
+    int32_t candidates;   /* configurations timed (0 when the result came from the cache) */
+    int32_t from_cache;   /* 1: an earlier call tuned the same mesh on this device        */
+    int32_t kernel;       /* SDUGKS_KERNEL_TILED or SDUGKS_KERNEL_CARTESIAN                */
+    int32_t pad_;
+} sdugks_tune_info;
+
+/* Time the candidate launch configurations of a solve of mesh m with base's tau, dt,
+ * precision and kernel request, and return in *best a copy of *base with the fastest
+ * tile_cells, graph_steps and staging.  Candidates: on the Cartesian kernel the block
+ * shapes 16x16, 16x14, 16x8 (FP64: 16x16) with per-thread loads or TMA staging; on the
+ * tiled kernel tiles of 64, 96, 108, 120 and 128 cells; each with graphs of 32, 64 and
+ * 128 steps.  Each candidate is a temporary solver at rest (the work of a step does not
+ * depend on the state) timed over `steps` steps, rounded up to whole graphs, with CUDA
+ * events on `stream` (a cudaStream_t; NULL = default stream), after one graph of warm-up.
+ * The result is cached per (device, mesh and boundary rules, precision, kernel request)
+ * for the life of the process; later calls return it without timing.  Choosing among
+ * these does not change the method: every configuration runs the same sums per cell
+ * (FP64 results are bit-identical across tile sizes, graph lengths and stagings; FP32
+ * results agree to rounding across Cartesian block shapes).  Synchronises.  Allocates
+ * and frees the candidates' device memory.  Errors: INVALID_ARG, OOM, CUDA. */
+int sdugks_autotune(const sdugks_mesh *m, const sdugks_params *base, int64_t steps, void *stream,
+                    sdugks_params *best, sdugks_tune_info *info);
+
+/* Forget every cached autotuning result. */
+void sdugks_autotune_clear(void);
+
 /* ---- batched solves ----------------------------------------------------------- */
 /* Many independent uniform-grid solves (cavities, channels) of different sizes and
  * Reynolds numbers advanced together: every step is one launch of a fixed grid of

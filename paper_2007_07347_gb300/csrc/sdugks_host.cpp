@@ -10,9 +10,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 using namespace sdugks;
@@ -1438,6 +1441,153 @@ extern "C" void sdugks_solver_destroy(sdugks_solver *s)
     if (s->dmem) cudaFree(s->dmem);
     delete s->tma;
     delete s;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+namespace {
+
+// Fingerprint of a mesh and its boundary rules (FNV-1a over the caller's arrays): two
+// solves of the same mesh share a tuning result whatever their tau and dt, which do
+// not change the work of a step.
+uint64_t mesh_fingerprint(const sdugks_mesh &m)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; i++) { h ^= c[i]; h *= 1099511628211ull; }
+    };
+    mix(&m.nc, sizeof m.nc);
+    mix(&m.nf, sizeof m.nf);
+    mix(m.xy.data(), m.xy.size() * sizeof(double));
+    mix(m.own.data(), m.own.size() * sizeof(int64_t));
+    mix(m.nbr.data(), m.nbr.size() * sizeof(int64_t));
+    mix(m.bc_kind.data(), sizeof m.bc_kind);
+    return h;
+}
+
+using TuneKey = std::tuple<int, uint64_t, int32_t, int32_t>;   // device, mesh, precision, kernel request
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<sdugks_params, double>> g_tune_cache;
+
+// Per-step time of one candidate: a solver with these parameters, at rest, one graph of
+// warm-up, then `steps` steps (rounded up to whole graphs) between two events.
+int time_candidate(const sdugks_mesh *m, const sdugks_params &p, int64_t steps, cudaStream_t st, double *ns)
+{
+    sdugks_solver *s = nullptr;
+    int rc = sdugks_solver_create(m, &p, st, &s);
+    if (rc) return rc;
+    rc = sdugks_init(s, nullptr, nullptr);
+    const int64_t G = s->p.graph_steps > 0 ? 2 * (int64_t)s->p.graph_steps : 2;
+    const int64_t n = std::max<int64_t>(G, (steps + G - 1) / G * G);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    if (!rc) rc = sdugks_step(s, G);
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = fail(SDUGKS_ERR_CUDA, "autotune: cudaEventCreate");
+    if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = fail(SDUGKS_ERR_CUDA, "autotune: cudaEventRecord");
+    if (!rc) rc = sdugks_step(s, n);
+    if (!rc && cudaEventRecord(e1, st) != cudaSuccess) rc = fail(SDUGKS_ERR_CUDA, "autotune: cudaEventRecord");
+    if (!rc) {
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = fail(SDUGKS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    }
+    if (!rc) {
+        double eps = 0.0;
+        rc = sdugks_residual(s, &eps, nullptr);      // a candidate that failed (TIMEOUT, DIVERGED) is not taken
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    sdugks_solver_destroy(s);
+    if (!rc) *ns = 1e6 * (double)ms / (double)n;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int sdugks_autotune(const sdugks_mesh *m, const sdugks_params *base, int64_t steps, void *stream,
+                               sdugks_params *best, sdugks_tune_info *info)
+{
+    if (!m || !base || !best || steps <= 0) return fail(SDUGKS_ERR_INVALID_ARG, "bad argument");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    const TuneKey key{dev, mesh_fingerprint(*m), base->precision, base->kernel};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = *base;
+            best->tile_cells = it->second.first.tile_cells;
+            best->graph_steps = it->second.first.graph_steps;
+            best->staging = it->second.first.staging;
+            if (info) { std::memset(info, 0, sizeof *info); info->ns_per_step = it->second.second; info->from_cache = 1; }
+            return SDUGKS_OK;
+        }
+    }
+    // which kernel the solve takes decides the search space
+    sdugks_params p0 = *base;
+    p0.tile_cells = 0; p0.graph_steps = 0; p0.staging = SDUGKS_STAGING_LOADS;
+    int32_t kernel = 0;
+    {
+        sdugks_solver *s = nullptr;
+        int rc = sdugks_solver_create(m, &p0, stream, &s);
+        if (rc) return rc;
+        kernel = s->kernel;
+        sdugks_solver_destroy(s);
+    }
+    std::vector<int32_t> tiles, stagings{SDUGKS_STAGING_LOADS};
+    if (kernel == SDUGKS_KERNEL_CARTESIAN) {
+        stagings.push_back(SDUGKS_STAGING_TMA);
+        if (base->precision == P_FP64) tiles = {0};
+        else tiles = {256, 224, 128};
+    } else {
+        tiles = {64, 96, 108, 120, 128};
+    }
+    const int32_t graphs[3] = {32, 64, 128};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double best_ns = 1e300;
+    sdugks_params win = p0;
+    int32_t n_cand = 0;
+    for (int32_t t : tiles)
+        for (int32_t sg : stagings)
+            for (int32_t g : graphs) {
+                sdugks_params p = p0;
+                p.kernel = kernel;
+                p.tile_cells = t;
+                p.staging = sg;
+                p.graph_steps = g;
+                double ns = 0.0;
+                const int rc = time_candidate(m, p, steps, st, &ns);
+                if (rc == SDUGKS_ERR_OOM || rc == SDUGKS_ERR_CUDA) return rc;
+                if (rc) continue;                    // a combination this mesh does not take
+                n_cand++;
+                if (ns < best_ns) { best_ns = ns; win = p; }
+            }
+    if (n_cand == 0) return fail(SDUGKS_ERR_INVALID_ARG, "autotune: no candidate configuration runs on this mesh");
+    *best = *base;
+    best->kernel = base->kernel;
+    best->tile_cells = win.tile_cells;
+    best->graph_steps = win.graph_steps;
+    best->staging = win.staging;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {*best, best_ns};
+    }
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->ns_per_step = best_ns;
+        info->candidates = n_cand;
+        info->from_cache = 0;
+        info->kernel = kernel;
+    }
+    return SDUGKS_OK;
+}
+
+extern "C" void sdugks_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
 }
 
 extern "C" const char *sdugks_last_error(void) { return g_err.c_str(); }

@@ -42,6 +42,11 @@ class Params(C.Structure):
                 ("tma_wait_us", C.c_int32)]
 
 
+class TuneInfo(C.Structure):
+    _fields_ = [("ns_per_step", C.c_double), ("candidates", C.c_int32), ("from_cache", C.c_int32),
+                ("kernel", C.c_int32), ("pad_", C.c_int32)]
+
+
 class Info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_tiles", C.c_int64), ("halo_cells", C.c_int64),
                 ("steps_done", C.c_int64), ("device_bytes", C.c_int64), ("state_bytes_per_cell_step", C.c_double),
@@ -85,6 +90,7 @@ def lib():
                 "sdugks_solver_info": [P, P],
                 "sdugks_step_forces": [P, P],
                 "sdugks_step_boundary_flux": [P, P, P],
+                "sdugks_autotune": [P, P, i64, P, P, P],
                 "sdugks_residual_noalloc": [i64, P, P, P, P, P],
                 "sdugks_batch_create": [i64, i32, i32, P, P],
                 "sdugks_batch_footprint": [P, P, P],
@@ -114,6 +120,8 @@ def lib():
             L.sdugks_batch_destroy.restype = None
             L.sdugks_dvm_destroy.argtypes = [P]
             L.sdugks_dvm_destroy.restype = None
+            L.sdugks_autotune_clear.argtypes = []
+            L.sdugks_autotune_clear.restype = None
             L.sdugks_last_error.restype = C.c_char_p
             L.sdugks_version.restype = C.c_char_p
             _lib = L
@@ -198,6 +206,19 @@ class Solver:
         s._mesh = m
         return s
 
+    @classmethod
+    def tuned(cls, case: _meshes.Case, precision="fp32", *, kernel=KERNEL_AUTO, steps=256, stream=None):
+        """A solver of the case with the launch configuration sdugks_autotune picks (the
+        tuning result is cached per mesh, precision and kernel request); the chosen
+        configuration and its measured time are in ``.tune``."""
+        m = Mesh(case.mesh, case.bcs)
+        t = autotune(m, case.tau, case.dt, precision, kernel=kernel, steps=steps, stream=stream)
+        s = cls(m, case.tau, case.dt, precision, kernel=kernel, tile_cells=t["tile_cells"],
+                graph_steps=t["graph_steps"], staging=t["staging"], stream=stream)
+        s._mesh = m
+        s.tune = t
+        return s
+
     def init(self, rho=None, u=None):
         r = None if rho is None else _f64(rho, (self.n,))
         v = None if u is None else _f64(u, (self.n, 2))
@@ -269,6 +290,26 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def autotune(mesh: Mesh, tau: float, dt: float, precision="fp32", *, kernel=KERNEL_AUTO, steps=256,
+             stream=None) -> dict:
+    """sdugks_autotune: the fastest launch configuration of a solve on this device, as
+    {tile_cells, graph_steps, staging, ns_per_step, candidates, from_cache, kernel}."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    base = Params(float(tau), float(dt), prec, int(kernel), 0, 0, STAGINGS["loads"], 0)
+    best = Params()
+    info = TuneInfo()
+    sh = getattr(stream, "cuda_stream", stream)
+    _ck(lib().sdugks_autotune(mesh._h, C.byref(base), int(steps), C.c_void_p(sh or 0), C.byref(best),
+                              C.byref(info)), "sdugks_autotune")
+    return {"tile_cells": best.tile_cells, "graph_steps": best.graph_steps, "staging": best.staging,
+            "ns_per_step": info.ns_per_step, "candidates": info.candidates, "from_cache": info.from_cache,
+            "kernel": info.kernel}
+
+
+def autotune_clear():
+    lib().sdugks_autotune_clear()
 
 
 class BatchStatus(C.Structure):

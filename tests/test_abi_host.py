@@ -108,7 +108,7 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
     if gcc is None:
         pytest.skip("no C compiler")
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
-    fields = {"sdugks_params": S.Params, "sdugks_info": S.Info}
+    fields = {"sdugks_params": S.Params, "sdugks_info": S.Info, "sdugks_tune_info": S.TuneInfo}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sdugks.h"', "int main(void) {"]
     for cname, py in fields.items():
         lines.append(f'printf("%zu\\n", sizeof({cname}));')
