@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="cavity cells per side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "cylinder", "batch", "serve", "rarefied"],
+    ap.add_argument("--workload", default="cavity",
+                    choices=["cavity", "cylinder", "batch", "batch-solve", "serve", "rarefied"],
                     help="cavity: the headline single solve; cylinder: the 512 x 256 O-mesh (shuffled, "
                          "unstructured kernel); batch: 256 cavities in one batch against the plain "
                          "one-at-a-time path; serve: the continuous-batching request loop; rarefied: the "
@@ -75,6 +76,14 @@ def parse():
                     help="the solver's own launch configuration instead of the autotuner's")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other single-GPU configurations (cylinder, batch) in the default line")
+    ap.add_argument("--target", type=float, default=1e-6, help="batch-solve / serve: residual target")
+    ap.add_argument("--cap-steps", type=int, default=400000, help="batch-solve: steps before an instance is capped")
+    ap.add_argument("--stall-checks", type=int, default=50,
+                    help="batch-solve: residual checks without a 1 %% lower minimum before an instance is "
+                         "retired as stalled at its floor")
+    ap.add_argument("--plain-sample", type=int, default=16,
+                    help="batch-solve: converged instances solved again one at a time (plain path) and as "
+                         "their own batch, for the solves/s comparison")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
     args = ap.parse_args()
@@ -569,6 +578,138 @@ def run_batch(args):
                       "batch": info}))
 
 
+class Retire:
+    """Stopping rule of a batched or plain solve, checked every INTERVAL steps (Sec. IV
+    residual): converged below the target; stalled when `stall` checks in a row bring no
+    new minimum 1 % below the previous one (the FP32 state has reached the floor of its
+    rounding noise); capped at `cap` steps."""
+
+    def __init__(self, target, cap, stall):
+        self.target, self.cap, self.stall = target, cap, stall
+        self.best, self.since = math.inf, 0
+
+    def __call__(self, eps, steps):
+        if eps < self.target:
+            return "converged"
+        if not (eps == math.inf or eps == eps):        # NaN
+            return "diverged"
+        if eps < 0.99 * self.best:
+            self.best, self.since = eps, 0
+        else:
+            self.since += 1
+        if self.since >= self.stall:
+            return "stalled"
+        if steps >= self.cap:
+            return "capped"
+        return None
+
+
+def batch_to_target(S, cases, args, stream, label=""):
+    """Advance the cases as one batch until each retires (Retire); per instance: status,
+    steps, wall time at retirement, last and lowest residual."""
+    import torch
+    probe = S.Batch(1 << 20, "fp32", 4)
+    meshes = [S.Mesh(c.mesh, c.bcs) for c in cases]
+    need = sum(probe.footprint(m) for m in meshes)
+    probe.close()
+    b = S.Batch(need + (64 << 20), "fp32", max(512, len(cases)), stream=stream)
+    ids = {b.add(m, c.tau, c.dt): k for k, (c, m) in enumerate(zip(cases, meshes))}
+    b.autotune(2)
+    rules = {k: Retire(args.target, args.cap_steps, args.stall_checks) for k in range(len(cases))}
+    out = [None] * len(cases)
+    cell_steps = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while ids:
+            cell_steps += INTERVAL * sum(cases[k].mesh.n_cells for k in ids.values())
+            b.step(INTERVAL)
+            res = b.residual()
+            for i, (eps, _, st) in res.items():
+                k = ids[i]
+                why = rules[k](eps, st)
+                if why:
+                    out[k] = {"status": why, "steps": st, "wall_s": time.perf_counter() - t0, "eps": eps,
+                              "eps_min": min(rules[k].best, eps)}
+                    b.remove(i)
+                    del ids[i]
+    wall = time.perf_counter() - t0
+    b.close()
+    return out, wall, cell_steps
+
+
+def plain_to_target(S, case, args, stream):
+    """One instance alone on the plain FP32 path (its own solver, default launch
+    configuration), with the same stopping rule."""
+    import torch
+    s = S.Solver.from_case(case, "fp32", stream=stream).init()
+    rule = Retire(args.target, args.cap_steps, args.stall_checks)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        s.step(INTERVAL)
+        steps += INTERVAL
+        eps, _ = s.residual()
+        why = rule(eps, steps)
+        if why:
+            break
+    wall = time.perf_counter() - t0
+    s.close()
+    return {"status": why, "steps": steps, "wall_s": wall, "eps": eps}
+
+
+def run_batch_solve(args):
+    """The batch of 256 lid-driven cavities (N ~ logU[32, 512], Re ~ logU[100, 5000], seed 1,
+    FP32) run to the per-instance residual target with retirement, and, on a seeded sample
+    of the instances that converged, the same solves one at a time on the plain path and
+    as their own batch: solves/s at equal accuracy (the same stopping rule)."""
+    import torch
+    from paper_2007_07347_gb300 import sdugks as S
+    torch.cuda.set_device(0)
+    specs = M.batch_cavities(256, seed=1)
+    cases = [M.cavity(nn, Re=re) for nn, re in specs]
+    stream = torch.cuda.Stream()
+    res, wall, cell_steps = batch_to_target(S, cases, args, stream)
+    conv = [k for k, r in enumerate(res) if r["status"] == "converged"]
+    stalled = [k for k, r in enumerate(res) if r["status"] == "stalled"]
+    tts = np.array([res[k]["wall_s"] for k in conv])
+    full = {"instances": len(cases), "cells": sum(c.mesh.n_cells for c in cases), "wall_s": wall,
+            "converged": len(conv), "stalled": len(stalled),
+            "capped": sum(r["status"] == "capped" for r in res), "diverged": sum(r["status"] == "diverged" for r in res),
+            "solves_per_s": len(conv) / wall,
+            "p50_time_to_solution_s": float(np.percentile(tts, 50)) if len(tts) else None,
+            "p99_time_to_solution_s": float(np.percentile(tts, 99)) if len(tts) else None,
+            "mlups": 9 * cell_steps / wall / 1e6,
+            "stalled_floor": ({"eps_min_lo": min(res[k]["eps_min"] for k in stalled),
+                               "eps_min_hi": max(res[k]["eps_min"] for k in stalled)} if stalled else None),
+            "per_instance": [{"N": specs[k][0], "Re": round(specs[k][1], 1), **{kk: (round(v, 4) if isinstance(v, float)
+                              else v) for kk, v in res[k].items()}} for k in range(len(cases))]}
+    # equal-accuracy comparison on a seeded sample of the converged instances
+    rng = np.random.default_rng(7)
+    sample = sorted(rng.choice(conv, size=min(args.plain_sample, len(conv)), replace=False).tolist()) if conv else []
+    cmp = None
+    if sample:
+        sub = [cases[k] for k in sample]
+        bres, bwall, _ = batch_to_target(S, sub, args, stream)
+        pres = [plain_to_target(S, c, args, stream) for c in sub]
+        pwall = sum(r["wall_s"] for r in pres)
+        cmp = {"sample": [{"N": specs[k][0], "Re": round(specs[k][1], 1)} for k in sample],
+               "batched": {"wall_s": bwall, "converged": sum(r["status"] == "converged" for r in bres),
+                           "solves_per_s": sum(r["status"] == "converged" for r in bres) / bwall},
+               "plain": {"wall_s": pwall, "converged": sum(r["status"] == "converged" for r in pres),
+                         "solves_per_s": sum(r["status"] == "converged" for r in pres) / pwall},
+               "steps_batched": [r["steps"] for r in bres], "steps_plain": [r["steps"] for r in pres]}
+        cmp["batched_over_plain"] = cmp["batched"]["solves_per_s"] / max(cmp["plain"]["solves_per_s"], 1e-30)
+    print(json.dumps({"metric": "solves/s", "value": full["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                      "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+                      "config": {"workload": "batch of 256 lid-driven cavities, N~logU[32,512], Re~logU[100,5000], "
+                                             "seed 1, lid 0.1, CFL 0.5, FP32, to eps < target (check every 1000 steps)",
+                                 "target": args.target, "cap_steps": args.cap_steps,
+                                 "stall_checks": args.stall_checks},
+                      "batch": full, "equal_accuracy": cmp}))
+
+
 def run_serve(args):
     """Continuous-batching request loop on the config-shaped request mix (seed 2)."""
     import torch
@@ -677,6 +818,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch-solve":
+        run_batch_solve(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":

@@ -5,8 +5,11 @@ and cylinder O-meshes) are admitted while their device-memory footprint fits: un
 grids join one `Batch` (one kernel launch per step over every admitted instance) and
 cylinder O-meshes run as tiled single solvers on a second CUDA stream, so their work
 overlaps on the GPU.  Every `check_every` steps the residual of each running solve is
-read; solves whose residual is below `target`, or that reached `step_cap`, retire and
-free their memory for queued requests.  Latency is retire time minus arrival time.
+read; solves whose residual is below `target` retire as converged, and so do, as not
+converged, solves that reached `step_cap`, whose residual stopped falling (no new minimum
+1 % below the last one for `stall_checks` checks: the floor of the FP32 state's rounding
+noise, or an unsteady flow) or that diverged; each frees its memory for queued requests.
+Latency is retire time minus arrival time.
 """
 from __future__ import annotations
 
@@ -32,7 +35,9 @@ class Request:
     done: float = math.nan
     steps: int = 0
     eps: float = math.inf
-    status: str = "queued"   # queued | running | converged | capped
+    status: str = "queued"   # queued | running | converged | capped | stalled | diverged
+    eps_best: float = math.inf
+    stall: int = 0
     handle: object = None
     result: tuple = None
     mesh: object = None      # the library mesh (built once, while the GPU steps)
@@ -96,6 +101,7 @@ class Server:
     target: float = 1e-6
     check_every: int = 1000
     step_cap: int = 200000
+    stall_checks: int = 0    # 0: no stall rule
     solver_pool_bytes: int = 4 << 30
     keep_results: bool = False
     log: list = field(default_factory=list)
@@ -169,8 +175,14 @@ class Server:
                     eps, _, r.steps = res[r.handle[1]]
                 r.eps = eps
                 diverged = math.isnan(eps)
-                if eps < self.target or r.steps >= self.step_cap or diverged:
-                    r.status = "converged" if eps < self.target else "capped"
+                if eps < 0.99 * r.eps_best:
+                    r.eps_best, r.stall = eps, 0
+                else:
+                    r.stall += 1
+                stalled = self.stall_checks > 0 and r.stall >= self.stall_checks
+                if eps < self.target or r.steps >= self.step_cap or diverged or stalled:
+                    r.status = ("converged" if eps < self.target else "diverged" if diverged
+                                else "stalled" if stalled else "capped")
                     if self.keep_results:
                         r.result = (r.handle[1].macros() if r.handle[0] == "solver" else batch.macros(r.handle[1]))
                     if r.handle[0] == "solver":
@@ -194,7 +206,10 @@ def serve_stats(requests: list, wall: float) -> dict:
     beside them, and ``met_target`` is False when any request did not converge."""
     conv = [r for r in requests if r.status == "converged"]
     lat = np.array([r.done - r.arrival for r in conv])
-    out = {"requests": len(requests), "converged": len(conv), "capped": len(requests) - len(conv),
+    out = {"requests": len(requests), "converged": len(conv),
+           "capped": sum(r.status == "capped" for r in requests),
+           "stalled": sum(r.status == "stalled" for r in requests),
+           "diverged": sum(r.status == "diverged" for r in requests),
            "met_target": len(conv) == len(requests),
            "wall_s": wall, "solves_per_s": len(conv) / wall if wall > 0 else 0.0,
            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,

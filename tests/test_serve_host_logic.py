@@ -126,3 +126,18 @@ def test_stats_count_converged_requests_only(fakes):
     assert out["converged"] == 6 and out["capped"] == 4 and out["met_target"] is False
     assert out["solves_per_s"] == pytest.approx(1.5)
     assert out["p99_latency_s"] <= 6.0 + 1e-12          # the capped requests' latencies (7-10 s) are left out
+
+
+def test_a_residual_that_stops_falling_retires_as_stalled(fakes, monkeypatch):
+    """A residual floor (eps constant at 0.5 after the first check) retires the request as
+    stalled once `stall_checks` checks in a row bring no new minimum; it is not a solve."""
+    monkeypatch.setattr(FakeBatch, "residual",
+                        lambda self: {i: (0.5, 1.0, it[1]) for i, it in self.items.items()})
+    monkeypatch.setattr(FakeSolver, "residual", lambda self: (0.5, 1.0))
+    reqs = _requests(6)
+    srv = V.Server(pool_bytes=1 << 40, check_every=500, step_cap=10 ** 6, target=1e-9, stall_checks=3,
+                   solver_pool_bytes=1 << 40)
+    out = srv.run(reqs)
+    assert out["stalled"] == 6 and out["converged"] == 0 and out["met_target"] is False
+    assert all(r.status == "stalled" and r.steps == 4 * 500 for r in reqs)   # the first check sets the minimum
+    assert out["solves_per_s"] == 0.0
