@@ -61,7 +61,11 @@ extern "C" {
 #define SDUGKS_FP32 1          /* f stored and computed in FP32                          */
 #define SDUGKS_FP32_BF16DEV 2  /* f stored as bf16 d = (f - feq(W)) / w, computed in FP32 */
 #define SDUGKS_FP32_FP16DEV 3  /* f stored as fp16 d / s with s = 2^-10, computed in FP32  */
-/* W (and the macroscopic-flux accumulation, residual and mass) is FP64 in every mode. */
+/* W (and the macroscopic-flux accumulation, residual and mass) is FP64 in every mode.
+ * Inside the library the FP32-compute modes work in a deviation form: the distribution
+ * is handled as f - w (w the lattice weights: the rest equilibrium of unit density) and
+ * the density as rho - 1, so that face fluxes and their moments are sums of small
+ * terms.  Every call of this header takes and returns f and rho themselves. */
 
 /* ---- kernel selection ---------------------------------------------------------- */
 #define SDUGKS_KERNEL_AUTO 0      /* Cartesian kernel when the mesh is a uniform grid  */
@@ -228,6 +232,21 @@ int sdugks_residual(sdugks_solver *s, double *eps, double *mass);
  * uninterrupted run bit for bit with FP64 and FP32 storage. */
 int sdugks_get_state(sdugks_solver *s, double *f, double *W);
 int sdugks_set_state(sdugks_solver *s, const double *f, const double *W);
+
+/* Checkpoint in the solver's own storage: a 32-byte header (layout of the solver), then
+ * the distribution in the storage precision and W in FP64, both in the solver's internal
+ * cell order.  The FP32-compute precisions store f as its deviation from the lattice
+ * weights and W[0] as rho - 1 (see the precision notes above); the FP64 f and rho of
+ * sdugks_get_state can round those stored values in their last place, while this form
+ * restores bit for bit in every precision.
+ *   buf    host; get: NULL to query the size into *bytes; else *bytes is its capacity,
+ *          and receives the size written
+ *   bytes  set: the size of buf, which must be the size get reports for this solver
+ * set accepts only a state taken from a solver of the same layout (same mesh, precision,
+ * kernel and tile size: INVALID_ARG otherwise), replaces the state and refreshes the
+ * residual snapshot.  Both synchronise.  Errors: INVALID_ARG, STATE (get before init). */
+int sdugks_get_state_raw(sdugks_solver *s, void *buf, int64_t *bytes);
+int sdugks_set_state_raw(sdugks_solver *s, const void *buf, int64_t bytes);
 
 /* The residual and mass reduction of sdugks_residual, for callers that may not
  * allocate device memory: over caller-owned device arrays, with the reduction's

@@ -61,8 +61,12 @@ template <> __device__ __forceinline__ float recip<float>(float x)
     return y;
 }
 
-template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R out[NQ]) {
-    const R base = rho - R(1.5) * rho * (ux * ux + uy * uy);
+// feq9fd(b0, rho, u): w [b0 + rho (3 xi.u + 4.5 (xi.u)^2 - 1.5 |u|^2)].  With b0 = rho
+// this is the equilibrium itself (feq9f); with b0 = rho - 1 it is the equilibrium's
+// deviation from the rest equilibrium of unit density, feq(rho, u) - w, the form the
+// FP32 kernels compute in (each term then has the size of the deviation, not of f).
+template <class R> __device__ __forceinline__ void feq9fd(R b0, R rho, R ux, R uy, R out[NQ]) {
+    const R base = b0 - R(1.5) * rho * (ux * ux + uy * uy);
     const R r3 = R(3) * rho, r45 = R(4.5) * rho;
     const R w0 = R(4) / R(9), w1 = R(1) / R(9), w5 = R(1) / R(36);
     out[0] = w0 * base;
@@ -88,8 +92,8 @@ template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R ou
 // evaluated by paired FP32 instructions (FFMA2/FMUL2; each lane rounds as the scalar
 // operation would): t = base + 4.5 rho e^2 and l = 3 rho e for e = (u_x, u_y) and for
 // e = (u_x + u_y, u_y - u_x), then w (t + l) and w (t - l).
-template <> __device__ __forceinline__ void feq9f<float>(float rho, float ux, float uy, float out[NQ]) {
-    const float base = rho - 1.5f * rho * (ux * ux + uy * uy);
+template <> __device__ __forceinline__ void feq9fd<float>(float b0, float rho, float ux, float uy, float out[NQ]) {
+    const float base = b0 - 1.5f * rho * (ux * ux + uy * uy);
     const float r3 = 3.0f * rho, r45 = 4.5f * rho;
     const float2 B = make_float2(base, base), R45 = make_float2(r45, r45), R3 = make_float2(r3, r3);
     const float2 w1 = make_float2(1.0f / 9.0f, 1.0f / 9.0f), w5 = make_float2(1.0f / 36.0f, 1.0f / 36.0f);
@@ -109,6 +113,10 @@ template <> __device__ __forceinline__ void feq9f<float>(float rho, float ux, fl
     }
 }
 
+template <class R> __device__ __forceinline__ void feq9f(R rho, R ux, R uy, R out[NQ]) {
+    feq9fd<R>(rho, rho, ux, uy, out);
+}
+
 // (u_x, u_y) from rho, rho u in the compute precision (FP32: one hardware reciprocal;
 // FP64: two IEEE divisions).
 template <class R> __device__ __forceinline__ void vel_of(R rho, R m1, R m2, R &ux, R &uy) {
@@ -121,8 +129,23 @@ template <> __device__ __forceinline__ void vel_of<double>(double rho, double m1
     uy = m2 / rho;
 }
 
-// Storage codecs.  FP64/FP32 store f itself.  BF16DEV stores the scaled deviation
-// d = (f - feq(W)) / w from the equilibrium of the same time level.
+// Deviation form.  The FP32-compute kernels (FP32, bf16 and fp16 storage) store the
+// conserved variables as W = (rho - 1, rho u_x, rho u_y) (FP64) and work with g = f - w,
+// the distribution's deviation from the rest equilibrium of unit density, and with
+// equilibria in the same form (feq9fd with b0 = rho - 1).  FP64 keeps W = (rho, rho u)
+// and f itself.  Every step
+// of the update is linear in f or uses a moment of it, and a constant field has no
+// gradient and no net flux through a closed cell, so the update of g is the update of
+// f with w taken out; but the face fluxes and their moments are then sums of small
+// terms instead of differences of O(w) terms, and their FP32 rounding error shrinks in
+// proportion (it sets the floor of the FP32 residual).
+template <int P> struct Dev { static constexpr bool ON = P != P_FP64; };
+// the density the stored W[0] is measured from: rho = rho_ref + W[0]
+template <int P> __host__ __device__ constexpr double rho_ref() { return P == P_FP64 ? 0.0 : 1.0; }
+
+// Storage codecs.  FP64 stores f; FP32 stores g = f - w.  BF16DEV stores the scaled
+// deviation d = (f - feq(W)) / w from the equilibrium of the same time level (the feq
+// passed is in the kernel's form, so dec returns g and enc takes g).
 template <int P> struct Store;
 template <> struct Store<P_FP64> {
     using T = double; using R = double;
@@ -181,14 +204,20 @@ template <> __device__ __forceinline__ float from_f64<float>(double d) { return 
 template <class R> __device__ __forceinline__ double to_f64(R x) { return double(x); }
 template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_fields(x); }
 
-// Conserved variables (rho, rho u) -> (rho, u) in the compute precision.
-template <class R> __device__ __forceinline__ void macro_of(double w0, double w1, double w2, R &rho, R &ux, R &uy) {
-    rho = from_f64<R>(w0);
+// Stored conserved variables -> rho - 1, rho and u in the compute precision.  FP32
+// compute: W = (rho - 1, rho u); rho - 1 converted from FP64 keeps its own relative
+// precision.  FP64: W = (rho, rho u) (drho is then rho - 1 rounded, unused by the
+// FP64 kernels).
+template <class R> __device__ __forceinline__ void macro_of(double w0, double w1, double w2, R &drho, R &rho, R &ux,
+                                                           R &uy) {
+    drho = from_f64<R>(w0);
+    rho = R(1) + drho;
     vel_of<R>(rho, from_f64<R>(w1), from_f64<R>(w2), ux, uy);
 }
-template <> __device__ __forceinline__ void macro_of<double>(double w0, double w1, double w2, double &rho, double &ux,
-                                                             double &uy) {
+template <> __device__ __forceinline__ void macro_of<double>(double w0, double w1, double w2, double &drho,
+                                                             double &rho, double &ux, double &uy) {
     rho = w0;
+    drho = w0 - 1.0;
     ux = w1 / w0;
     uy = w2 / w0;
 }

@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(RT) k_bresid_partial(const CartInst *__restric
         if (i < m.nx && j < m.ny) {
             const int64_t g = i + (int64_t)m.pitch * j, np = m.npad;
             const double *W = m.W[par];
-            const double w0 = W[g], w1 = W[np + g], w2 = W[2 * np + g];
+            // batched precisions compute in the deviation form: W[0] = rho - 1
+            const double w0 = 1.0 + W[g], w1 = W[np + g], w2 = W[2 * np + g];
             const double U = w1 / w0, V = w2 / w0, U0 = m.snap[g], V0 = m.snap[np + g];
             v[0] = (U - U0) * (U - U0) + (V - V0) * (V - V0);
             v[1] = U0 * U0 + V0 * V0;
@@ -100,13 +101,15 @@ __global__ void k_binit(const CartInst *__restrict__ mp, int par, const double *
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = q % m.nx + (int64_t)m.pitch * (q / m.nx);
         const double r = rho ? rho[q] : 1.0, ux = u ? u[2 * q] : 0.0, uy = u ? u[2 * q + 1] : 0.0;
-        W[g] = r; W[np + g] = r * ux; W[2 * np + g] = r * uy;
+        // deviation form (every batched precision computes in FP32): W[0] = rho - 1 and
+        // f stored as g = f - w (FP32) or as the deviation from feq (bf16, fp16)
+        W[g] = r - 1.0; W[np + g] = r * ux; W[2 * np + g] = r * uy;
         m.snap[g] = ux; m.snap[np + g] = uy;
         double fe[NQ];
-        feq9<double>(r, ux, uy, fe);
-        R rr, x, y, feR[NQ];
-        macro_of<R>(r, r * ux, r * uy, rr, x, y);
-        feq9f<R>(rr, x, y, feR);
+        feq9fd<double>(r - 1.0, r, ux, uy, fe);
+        R drr, rr, x, y, feR[NQ];
+        macro_of<R>(r - 1.0, r * ux, r * uy, drr, rr, x, y);
+        feq9fd<R>(drr, rr, x, y, feR);
 #pragma unroll
         for (int a = 0; a < NQ; a++) f[a * np + g] = Store<P>::enc(R(fe[a]), feR[a], a);
     }
@@ -119,7 +122,7 @@ __global__ void k_bmacros(const CartInst *__restrict__ mp, int par, double *__re
     const double *W = m.W[par];
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = q % m.nx + (int64_t)m.pitch * (q / m.nx);
-        const double w0 = W[g];
+        const double w0 = 1.0 + W[g];      // deviation form: W[0] = rho - 1
         if (rho) rho[q] = w0;
         if (u) { u[2 * q] = W[np + g] / w0; u[2 * q + 1] = W[2 * np + g] / w0; }
     }

@@ -440,6 +440,7 @@ static void fill_coefs(Coefs &c, const sdugks_mesh &m, double tau, double dt)
             c.bc_par[q][d] = m.bc_par[q][d];
             c.fbc_par[q][d] = (float)m.bc_par[q][d];
         }
+        c.fbc_drho[q] = (float)(m.bc_par[q][0] - 1.0);
     }
 }
 
@@ -557,6 +558,7 @@ static void fill_cart_inst(CartInst &ci, const sdugks_mesh &m, const CartGrid &g
             ci.side_par[k][d] = m.bc_par[p][d];
             ci.fside_par[k][d] = (float)m.bc_par[p][d];
         }
+        ci.fside_drho[k] = (float)(m.bc_par[p][0] - 1.0);
     }
     ci.npad = npad;
     ci.dx = g.dx; ci.dy = g.dy; ci.dtV = dt / (g.dx * g.dy);
@@ -1190,7 +1192,8 @@ static int ensure_staging(sdugks_solver *s)
 
 static int snapshot(sdugks_solver *s, double *eps, double *mass)
 {
-    CUDA_TRY(launch_residual(s->n, s->npad, s->loc, s->st.W[s->cur], s->vol, s->snap, s->partial, s->n_red_blocks, s->red,
+    CUDA_TRY(launch_residual(s->n, s->npad, s->loc, s->st.W[s->cur], rho_ref_of(s->p.precision), s->vol, s->snap,
+                             s->partial, s->n_red_blocks, s->red,
                              s->stream));
     CUDA_TRY(cudaMemcpyAsync(s->h_red, s->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -1345,7 +1348,8 @@ extern "C" int sdugks_get_macros_device(sdugks_solver *s, double *d_rho, double 
     if (!s) return fail(SDUGKS_ERR_INVALID_ARG, "solver is NULL");
     if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_macros before init");
     CUDA_TRY(cudaSetDevice(s->device));
-    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->loc, s->st.W[s->cur], d_rho, d_u, s->stream));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->loc, s->st.W[s->cur], rho_ref_of(s->p.precision), d_rho, d_u,
+                           s->stream));
     return SDUGKS_OK;
 }
 
@@ -1356,7 +1360,8 @@ extern "C" int sdugks_get_macros(sdugks_solver *s, double *rho, double *u)
     CUDA_TRY(cudaSetDevice(s->device));
     int rc = ensure_staging(s);
     if (rc) return rc;
-    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->loc, s->st.W[s->cur], s->staging, s->staging + s->n, s->stream));
+    CUDA_TRY(launch_macros(s->n, s->npad, s->perm, s->loc, s->st.W[s->cur], rho_ref_of(s->p.precision), s->staging,
+                           s->staging + s->n, s->stream));
     if (rho) CUDA_TRY(cudaMemcpyAsync(rho, s->staging, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
     if (u) CUDA_TRY(cudaMemcpyAsync(u, s->staging + s->n, sizeof(double) * 2 * s->n, cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -1399,6 +1404,76 @@ extern "C" int sdugks_set_state(sdugks_solver *s, const double *f, const double 
     CUDA_TRY(cudaMemcpyAsync(dW, W, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
     s->cur = 0; s->steps_done = 0;
     CUDA_TRY(launch_unpack_state(s->p.precision, s->n, s->npad, s->perm, s->loc, df, dW, s->st.f[0], s->st.W[0], s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->red + 4, 0, sizeof(int32_t), s->stream));   // a new state: no failed launch
+    s->initialised = true;
+    return snapshot(s, nullptr, nullptr);
+}
+
+namespace {
+// Header of a raw checkpoint: the state is only meaningful to a solver of the same
+// layout (precision, cell count and padding, kernel, tile size).
+struct RawHeader {
+    uint32_t magic;
+    int32_t precision;
+    int64_t n, npad;
+    int32_t kernel, tile_cells;
+};
+constexpr uint32_t RAW_MAGIC = 0x31474453u;   // "SDG1"
+
+size_t raw_f_bytes(const sdugks_solver *s)
+{
+    const size_t fs = s->p.precision == P_FP64 ? 8 : (s->p.precision == P_FP32 ? 4 : 2);
+    return (size_t)NQ * (size_t)s->npad * fs;
+}
+RawHeader raw_header(const sdugks_solver *s)
+{
+    RawHeader h{};
+    h.magic = RAW_MAGIC;
+    h.precision = s->p.precision;
+    h.n = s->n;
+    h.npad = s->npad;
+    h.kernel = s->kernel;
+    h.tile_cells = s->kernel == SDUGKS_KERNEL_CARTESIAN ? 16 * CART_TY[s->cart_shape] : s->p.tile_cells;
+    return h;
+}
+}  // namespace
+
+extern "C" int sdugks_get_state_raw(sdugks_solver *s, void *buf, int64_t *bytes)
+{
+    if (!s || !bytes) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    const size_t fb = raw_f_bytes(s), wb = sizeof(double) * 3 * (size_t)s->npad;
+    const size_t total = sizeof(RawHeader) + fb + wb;
+    if (!buf) { *bytes = (int64_t)total; return SDUGKS_OK; }
+    if (*bytes < (int64_t)total) return fail(SDUGKS_ERR_INVALID_ARG, "raw state needs %zu bytes", total);
+    if (!s->initialised) return fail(SDUGKS_ERR_STATE, "get_state_raw before init");
+    CUDA_TRY(cudaSetDevice(s->device));
+    const RawHeader h = raw_header(s);
+    char *c = static_cast<char *>(buf);
+    std::memcpy(c, &h, sizeof h);
+    CUDA_TRY(cudaMemcpyAsync(c + sizeof h, s->st.f[s->cur], fb, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(c + sizeof h + fb, s->st.W[s->cur], wb, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    *bytes = (int64_t)total;
+    return SDUGKS_OK;
+}
+
+extern "C" int sdugks_set_state_raw(sdugks_solver *s, const void *buf, int64_t bytes)
+{
+    if (!s || !buf) return fail(SDUGKS_ERR_INVALID_ARG, "NULL argument");
+    const size_t fb = raw_f_bytes(s), wb = sizeof(double) * 3 * (size_t)s->npad;
+    const size_t total = sizeof(RawHeader) + fb + wb;
+    if (bytes != (int64_t)total) return fail(SDUGKS_ERR_INVALID_ARG, "raw state of %lld bytes, this solver's is %zu",
+                                             (long long)bytes, total);
+    RawHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    const RawHeader mine = raw_header(s);
+    if (std::memcmp(&h, &mine, sizeof h) != 0)
+        return fail(SDUGKS_ERR_INVALID_ARG, "raw state was taken from a solver of another layout");
+    CUDA_TRY(cudaSetDevice(s->device));
+    const char *c = static_cast<const char *>(buf);
+    s->cur = 0; s->steps_done = 0;
+    CUDA_TRY(cudaMemcpyAsync(s->st.f[0], c + sizeof h, fb, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(s->st.W[0], c + sizeof h + fb, wb, cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaMemsetAsync(s->red + 4, 0, sizeof(int32_t), s->stream));   // a new state: no failed launch
     s->initialised = true;
     return snapshot(s, nullptr, nullptr);

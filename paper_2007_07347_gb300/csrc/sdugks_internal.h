@@ -41,6 +41,7 @@ struct Coefs {
     int32_t bc_kind[MAXPATCH];
     double bc_par[MAXPATCH][3];
     float fbc_par[MAXPATCH][3];
+    float fbc_drho[MAXPATCH];     // rho_inf - 1 of far-field patches (FP32 compute works with rho - 1)
 };
 
 // Slot kinds of a cell's faces (slots in ascending face id).
@@ -96,6 +97,7 @@ struct CartInst {
     double side_par[4][3];
     float fdx, fdy, fdtV, fa, fb, fc, fr, finv1r, fdt, fihx, fihy;
     float fside_par[4][3];
+    float fside_drho[4];      // rho_inf - 1 of far-field sides (FP32 compute works with rho - 1)
     void *f[2];
     double *W[2];
     double *snap;             // [2][npad] residual snapshot (U0, V0)
@@ -217,12 +219,15 @@ cudaError_t launch_pack_state(int prec, int64_t n, int64_t npad, const int32_t *
                               const double *W, double *f_out, double *W_out, cudaStream_t st);
 cudaError_t launch_unpack_state(int prec, int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc,
                                 const double *f_in, const double *W_in, void *f, double *W, cudaStream_t st);
-cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc, const double *W, double *rho,
-                          double *u, cudaStream_t st);
+// rr: the density the stored W[0] is measured from (rho = rr + W[0]; 0 for FP64, 1 for
+// the FP32-compute precisions)
+cudaError_t launch_macros(int64_t n, int64_t npad, const int32_t *perm, const int32_t *loc, const double *W, double rr,
+                          double *rho, double *u, cudaStream_t st);
 // residual over the listed cells: snap [2][npad] (U0, V0); partial [blocks][4];
 // out[4] = (num, den, mass, non-finite count)
-cudaError_t launch_residual(int64_t n, int64_t npad, const int32_t *loc, const double *W, const double *vol, double *snap,
-                            double *partial, int n_blocks, double *out, cudaStream_t st);
+cudaError_t launch_residual(int64_t n, int64_t npad, const int32_t *loc, const double *W, double rr, const double *vol,
+                            double *snap, double *partial, int n_blocks, double *out, cudaStream_t st);
+inline double rho_ref_of(int prec) { return prec == P_FP64 ? 0.0 : 1.0; }
 int residual_blocks(int64_t n);
 
 // records msg as the calling thread's sdugks_last_error() and returns code

@@ -152,6 +152,7 @@ template <> struct CartK<double> {
     __device__ explicit CartK(const CartInst &m)
         : a(m.a), b(m.b), c(m.c), r(m.r), dt(m.dt), dtV(m.dtV), hx(m.dx), hy(m.dy), ihx(m.ihx), ihy(m.ihy) {}
     __device__ static double par(const CartInst &m, int side, int i) { return m.side_par[side][i]; }
+    __device__ static double drho_par(const CartInst &m, int side) { return m.side_par[side][0] - 1.0; }
 };
 template <> struct CartK<float> {
     float a, b, c, r, dt, dtV, hx, hy, ihx, ihy;
@@ -159,6 +160,7 @@ template <> struct CartK<float> {
         : a(m.fa), b(m.fb), c(m.fc), r(m.fr), dt(m.fdt), dtV(m.fdtV), hx(m.fdx), hy(m.fdy),
           ihx(m.fihx), ihy(m.fihy) {}
     __device__ static float par(const CartInst &m, int side, int i) { return m.fside_par[side][i]; }
+    __device__ static float drho_par(const CartInst &m, int side) { return m.fside_drho[side]; }
 };
 
 // LLSR gradient stencil of one staged cell on a uniform grid.  Over the face
@@ -296,9 +298,11 @@ __device__ __forceinline__ void cart_interior_face_f32x2(float flux[6], const fl
         if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
         if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
     }
+    // deviation form: w0 = sum of g = rho_b - 1
     float ux, uy, feqb[NQ];
-    vel_of<float>(w0, w1, w2, ux, uy);
-    feq9f<float>(w0, ux, uy, feqb);
+    const float rb = 1.0f + w0;
+    vel_of<float>(rb, w1, w2, ux, uy);
+    feq9fd<float>(w0, rb, ux, uy, feqb);
     const float len = AX == 0 ? k.hy : k.hx;
     const float2 bb = p2(k.b, k.b), cc = p2(k.c, k.c);
     // slot pairs: AX 0 -> (1,3) (5,6) (7,8); AX 1 -> (2,4) (5,6) (7,8)
@@ -337,20 +341,23 @@ __device__ __forceinline__ void cart_face_momentum(const CartInst &m, int side, 
 template <int D, class R, bool DIAG>
 __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int lme, const Sten<R> &st,
                                                    const CartInst &m, int side, int pos, const CartK<R> &k,
-                                                   const R fn[NQ], const R feqn[NQ], R rho_n, R ux_n, R uy_n, int LXY)
+                                                   const R fn[NQ], const R feqn[NQ], R drho_n, R rho_n, R ux_n,
+                                                   R uy_n, int LXY)
 {
+    constexpr bool DEV = sizeof(R) == 4;           // FP32 compute: deviation form
     const R nx = D == 0 ? k.hy : (D == 1 ? -k.hy : R(0));
     const R ny = D == 2 ? k.hx : (D == 3 ? -k.hx : R(0));
     const R rx = D == 0 ? R(0.5) * k.hx : (D == 1 ? R(-0.5) * k.hx : R(0));
     const R ry = D == 2 ? R(0.5) * k.hy : (D == 3 ? R(-0.5) * k.hy : R(0));
     const int bk = m.side_kind[side];
-    R rb = rho_n, ubx = R(0), uby = R(0);
+    R rb = rho_n, drb = drho_n, ubx = R(0), uby = R(0);
     if (bk == BK_MOVING_WALL) { ubx = CartK<R>::par(m, side, 0); uby = CartK<R>::par(m, side, 1); }
     else if (bk == BK_FARFIELD) {
-        rb = CartK<R>::par(m, side, 0); ubx = CartK<R>::par(m, side, 1); uby = CartK<R>::par(m, side, 2);
+        rb = CartK<R>::par(m, side, 0); drb = CartK<R>::drho_par(m, side);
+        ubx = CartK<R>::par(m, side, 1); uby = CartK<R>::par(m, side, 2);
     } else if (bk == BK_OUTLET) { ubx = ux_n; uby = uy_n; }
     R feqb[NQ];
-    feq9f<R>(rb, ubx, uby, feqb);
+    feq9fd<R>(DEV ? drb : rb, rb, ubx, uby, feqb);
     R px_ = R(0), py_ = R(0);
 #define SDUGKS_BFACE_ALPHA(a)                                                                       \
     {                                                                                               \
@@ -373,7 +380,12 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int 
     SDUGKS_BFACE_ALPHA(0) SDUGKS_BFACE_ALPHA(1) SDUGKS_BFACE_ALPHA(2) SDUGKS_BFACE_ALPHA(3) SDUGKS_BFACE_ALPHA(4)
     SDUGKS_BFACE_ALPHA(5) SDUGKS_BFACE_ALPHA(6) SDUGKS_BFACE_ALPHA(7) SDUGKS_BFACE_ALPHA(8)
 #undef SDUGKS_BFACE_ALPHA
-    if (DIAG) cart_face_momentum(m, side, pos, to_f64<R>(px_), to_f64<R>(py_));   // diagnostic steps only
+    if (DIAG) {       // diagnostic steps only; in the deviation form the rest equilibrium's
+                      // momentum flux c_s^2 n l is added back
+        const double rfx = DEV ? (D == 0 ? m.dy : (D == 1 ? -m.dy : 0.0)) / 3.0 : 0.0;
+        const double rfy = DEV ? (D == 2 ? m.dx : (D == 3 ? -m.dx : 0.0)) / 3.0 : 0.0;
+        cart_face_momentum(m, side, pos, to_f64<R>(px_) + rfx, to_f64<R>(py_) + rfy);
+    }
 }
 
 // One TX x TY block (block coordinates tbx, tby) of one grid: reads buffer `par`,
@@ -458,10 +470,9 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         st.ay = (hN && hS) ? R(0.5) * k.ihy : k.ihy;
         return st;
     };
-    auto macro = [&](double w0, double w1, double w2, R &rho, R &ux, R &uy) {
-        rho = from_f64<R>(w0);
-        if constexpr (P == P_FP64) vel_of<R>(w0, w1, w2, ux, uy);
-        else vel_of<R>(rho, from_f64<R>(w1), from_f64<R>(w2), ux, uy);
+    constexpr bool DEV = Dev<P>::ON;      // FP32 compute: g = f - w, W[0] = rho - 1
+    auto macro = [&](double w0, double w1, double w2, R &drho, R &rho, R &ux, R &uy) {
+        macro_of<R>(w0, w1, w2, drho, rho, ux, uy);
     };
 
     // ---- phase 1: fbar+ = a f^n + b feq(W^n) of every staged position, one round.
@@ -474,8 +485,8 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     const int64_t g = (int64_t)gi + pitch * gj;
     const int lme = (tj + 2) * S::SX + (ti + 2);
     R fn[NQ];
-    R rho_n = R(1), ux_n = R(0), uy_n = R(0);
-    double w0n = 1.0, w1n = 0.0, w2n = 0.0;
+    R rho_n = R(1), drho_n = R(0), ux_n = R(0), uy_n = R(0);
+    double w0n = 1.0 - rho_ref<P>(), w1n = 0.0, w2n = 0.0;
     {
         int64_t gs = -1;
         int ls = 0, mir = 0, li = 0, lj = 0;
@@ -506,8 +517,9 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 #pragma unroll
                 for (int a = 0; a < NQ; a++) fv[a] = SP::dec(fin[a * np + gs], R(0), a);
             }
-            macro(a0, a1, a2, rho, ux, uy);
-            feq9f<R>(rho, ux, uy, fe);
+            R drho;
+            macro(a0, a1, a2, drho, rho, ux, uy);
+            feq9fd<R>(DEV ? drho : rho, rho, ux, uy, fe);
 #pragma unroll
             for (int a = 0; a < NQ; a++)
                 if constexpr (P == P_BF16DEV || P == P_FP16DEV) fv[a] += fe[a];       // decode the deviation
@@ -539,7 +551,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             if (active) {
 #pragma unroll
                 for (int a = 0; a < NQ; a++) fn[a] = fv[a];
-                rho_n = rho; ux_n = ux; uy_n = uy;
+                rho_n = rho; drho_n = drho; ux_n = ux; uy_n = uy;
                 w0n = a0; w1n = a1; w2n = a2;
             }
         }
@@ -597,30 +609,30 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         const bool inW = has_x(gi - 1), inE = has_x(gi + 1);
         const bool inS = has_y(gj - 1), inN = has_y(gj + 1);
         R feqn[NQ];
-        if (!(inW && inE && inS && inN)) feq9f<R>(rho_n, ux_n, uy_n, feqn);   // boundary cells only
+        if (!(inW && inE && inS && inN)) feq9fd<R>(DEV ? drho_n : rho_n, rho_n, ux_n, uy_n, feqn);   // boundary cells only
         if (inW) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NSX + fW];
         } else {
-            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, gj, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, gj, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
         }
         if (inE) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NSX + fE];
         } else {
-            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, gj, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, gj, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
         }
         if (inS) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NSY + fS];
         } else {
-            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, gi, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, gi, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
         }
         if (inN) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NSY + fN];
         } else {
-            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, gi, k, fn, feqn, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, gi, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
         }
 
         if (DIAG && (m.force || m.bface)) {
@@ -635,7 +647,10 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
                     px_ += R(EX(a)) * fl[r * stride];
                     py_ += R(EY(a)) * fl[r * stride];
                 }
-                cart_face_momentum(m, side, pos, to_f64<R>(sgn * px_), to_f64<R>(sgn * py_));
+                // deviation form: plus the rest equilibrium's flux c_s^2 n l (n out of the fluid)
+                const double rf = DEV ? (double)sgn * (y_face ? m.dx : m.dy) / 3.0 : 0.0;
+                cart_face_momentum(m, side, pos, to_f64<R>(sgn * px_) + (y_face ? 0.0 : rf),
+                                   to_f64<R>(sgn * py_) + (y_face ? rf : 0.0));
             };
             if (symL && gi == 0) sym_face(3, gj, s_fx + fW, S::NSX, false, R(-1));
             if (symR && gi == nx - 1) sym_face(1, gj, s_fx + fE, S::NSX, false, R(1));
@@ -660,11 +675,13 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         if constexpr (P == P_FP64) {
             rho1 = W0;
             vel_of<R>(W0, W1, W2, ux1, uy1);
+            feq9f<R>(rho1, ux1, uy1, feq1);
         } else {
-            rho1 = rho_n - d0;
+            const R drho1 = drho_n - d0;
+            rho1 = R(1) + drho1;
             vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
+            feq9fd<R>(drho1, rho1, ux1, uy1, feq1);
         }
-        feq9f<R>(rho1, ux1, uy1, feq1);
         if constexpr (P == P_FP64) {
 #pragma unroll
             for (int a = 0; a < NQ; a++)

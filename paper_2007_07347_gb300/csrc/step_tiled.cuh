@@ -33,11 +33,13 @@ template <> struct CoefR<double> {
     double a, b, c, r, dt, tie;
     __device__ CoefR(const Coefs &k) : a(k.a_plus), b(k.b_plus), c(k.c_face), r(k.r), dt(k.dt), tie(k.tie) {}
     __device__ static double par(const Coefs &k, int p, int i) { return k.bc_par[p][i]; }
+    __device__ static double drho_par(const Coefs &k, int p) { return k.bc_par[p][0] - 1.0; }
 };
 template <> struct CoefR<float> {
     float a, b, c, r, dt, tie;
     __device__ CoefR(const Coefs &k) : a(k.fa_plus), b(k.fb_plus), c(k.fc_face), r(k.fr), dt(k.fdt), tie(k.ftie) {}
     __device__ static float par(const Coefs &k, int p, int i) { return k.fbc_par[p][i]; }
+    __device__ static float drho_par(const Coefs &k, int p) { return k.fbc_drho[p]; }
 };
 
 // fbar+ = a f^n + b feq(W^n) of one cell (Eq. fbarplus), with f^n and feq(W^n) returned.
@@ -76,6 +78,32 @@ __device__ __forceinline__ void tiled_face_momentum(const TiledMesh &m, int p, i
     }
 }
 
+// Interface velocity and equilibrium from the moments (w0, w1, w2) of the interface
+// distribution: FP64, w0 = rho_b; FP32 compute (deviation form), w0 = rho_b - 1 and the
+// equilibrium is returned as its deviation from w.
+template <int P>
+__device__ __forceinline__ void interface_feq(typename Store<P>::R w0, typename Store<P>::R w1, typename Store<P>::R w2,
+                                              typename Store<P>::R &ux, typename Store<P>::R &uy,
+                                              typename Store<P>::R feqb[NQ])
+{
+    using R = typename Store<P>::R;
+    if constexpr (Dev<P>::ON) {
+        const R rb = R(1) + w0;
+        vel_of<R>(rb, w1, w2, ux, uy);
+        feq9fd<R>(w0, rb, ux, uy, feqb);
+    } else {
+        vel_of<R>(w0, w1, w2, ux, uy);
+        feq9f<R>(w0, ux, uy, feqb);
+    }
+}
+
+// The rest equilibrium's momentum flux c_s^2 n l through a face (component nl of n l),
+// which the deviation form leaves out of its face fluxes; 0 in FP64.
+template <int P> __device__ __forceinline__ double ref_momentum(typename Store<P>::R nl)
+{
+    return Dev<P>::ON ? to_f64<typename Store<P>::R>(nl) / 3.0 : 0.0;
+}
+
 template <int P>
 __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict__ fin, const double *__restrict__ Wn,
                                          int64_t g, int64_t np, const CoefR<typename Store<P>::R> &k,
@@ -83,9 +111,9 @@ __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict_
                                          typename Store<P>::R fbp[NQ])
 {
     using R = typename Store<P>::R;
-    R rho, ux, uy;
-    macro_of<R>(Wn[g], Wn[np + g], Wn[2 * np + g], rho, ux, uy);
-    feq9f<R>(rho, ux, uy, fe);
+    R drho, rho, ux, uy;
+    macro_of<R>(Wn[g], Wn[np + g], Wn[2 * np + g], drho, rho, ux, uy);
+    feq9fd<R>(Dev<P>::ON ? drho : rho, rho, ux, uy, fe);      // FP32 compute: deviation form (g = f - w)
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         fn[a] = Store<P>::dec(fin[a * np + g], fe[a], a);
@@ -246,8 +274,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
             }
             R ux, uy, feqb[NQ];
-            vel_of<R>(w0, w1, w2, ux, uy);
-            feq9f<R>(w0, ux, uy, feqb);
+            interface_feq<P>(w0, w1, w2, ux, uy, feqb);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
@@ -274,8 +301,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
             }
             R ux, uy, feqb[NQ];
-            vel_of<R>(w0, w1, w2, ux, uy);
-            feq9f<R>(w0, ux, uy, feqb);
+            interface_feq<P>(w0, w1, w2, ux, uy, feqb);
             R px_ = R(0), py_ = R(0);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
@@ -285,21 +311,24 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 px_ += R(EX(a)) * fl;
                 py_ += R(EY(a)) * fl;
             }
-            tiled_face_momentum(m, B & 0xFF, f0 + lf, to_f64<R>(px_), to_f64<R>(py_));
+            tiled_face_momentum(m, B & 0xFF, f0 + lf, to_f64<R>(px_) + ref_momentum<P>(nx),
+                                to_f64<R>(py_) + ref_momentum<P>(ny));
         } else {
             // boundary face of cell A (an interior cell of the tile): Sec. III rules
             const int p = B & 0xFF;
             const int bk = c.bc_kind[p];
             const int64_t gA = (int64_t)c0 + A;
-            R fnA[NQ], feqA[NQ], fbA[NQ], rhoA, uxA, uyA;
+            R fnA[NQ], feqA[NQ], fbA[NQ], drhoA, rhoA, uxA, uyA;
             cell_fbp<P>(fin, Wn, gA, np, k, fnA, feqA, fbA);
-            macro_of<R>(Wn[gA], Wn[np + gA], Wn[2 * np + gA], rhoA, uxA, uyA);
-            R rb = rhoA, ubx = R(0), uby = R(0);
+            macro_of<R>(Wn[gA], Wn[np + gA], Wn[2 * np + gA], drhoA, rhoA, uxA, uyA);
+            R rb = rhoA, drb = drhoA, ubx = R(0), uby = R(0);
             if (bk == BK_MOVING_WALL) { ubx = CoefR<R>::par(c, p, 0); uby = CoefR<R>::par(c, p, 1); }
-            else if (bk == BK_FARFIELD) { rb = CoefR<R>::par(c, p, 0); ubx = CoefR<R>::par(c, p, 1); uby = CoefR<R>::par(c, p, 2); }
-            else if (bk == BK_OUTLET) { ubx = uxA; uby = uyA; }
+            else if (bk == BK_FARFIELD) {
+                rb = CoefR<R>::par(c, p, 0); drb = CoefR<R>::drho_par(c, p);
+                ubx = CoefR<R>::par(c, p, 1); uby = CoefR<R>::par(c, p, 2);
+            } else if (bk == BK_OUTLET) { ubx = uxA; uby = uyA; }
             R feqb[NQ];
-            feq9f<R>(rb, ubx, uby, feqb);
+            feq9fd<R>(Dev<P>::ON ? drb : rb, rb, ubx, uby, feqb);
             R px_ = R(0), py_ = R(0);
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
@@ -316,7 +345,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 px_ += R(EX(a)) * (s * fb);
                 py_ += R(EY(a)) * (s * fb);
             }
-            tiled_face_momentum(m, p, f0 + lf, to_f64<R>(px_), to_f64<R>(py_));
+            tiled_face_momentum(m, p, f0 + lf, to_f64<R>(px_) + ref_momentum<P>(nx), to_f64<R>(py_) + ref_momentum<P>(ny));
         }
     }
     __syncthreads();
@@ -355,13 +384,16 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     Wout[2 * np + g] = W2;
     R rho1, ux1, uy1, feq1[NQ];
     if constexpr (P == P_FP64) {
-        macro_of<R>(W0, W1, W2, rho1, ux1, uy1);
+        R drho1;
+        macro_of<R>(W0, W1, W2, drho1, rho1, ux1, uy1);
+        feq9f<R>(rho1, ux1, uy1, feq1);
     } else {
-        // FP32 compute: W^{n+1} in FP32 from the FP32 copies of W^n
-        rho1 = from_f64<R>(w0n) - d0;
+        // FP32 compute: W^{n+1} in FP32 from the FP32 copies of W^n (W[0] = rho - 1)
+        const R drho1 = from_f64<R>(w0n) - d0;
+        rho1 = R(1) + drho1;
         vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
+        feq9fd<R>(drho1, rho1, ux1, uy1, feq1);
     }
-    feq9f<R>(rho1, ux1, uy1, feq1);
 #pragma unroll
     for (int a = 0; a < NQ; a++) {
         R fnew;

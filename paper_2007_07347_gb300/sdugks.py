@@ -87,6 +87,8 @@ def lib():
                 "sdugks_residual": [P, P, P],
                 "sdugks_get_state": [P, P, P],
                 "sdugks_set_state": [P, P, P],
+                "sdugks_get_state_raw": [P, P, P],
+                "sdugks_set_state_raw": [P, P, i64],
                 "sdugks_solver_info": [P, P],
                 "sdugks_step_forces": [P, P],
                 "sdugks_step_boundary_flux": [P, P, P],
@@ -269,6 +271,19 @@ class Solver:
     def get_state_into(self, f, W):
         """Like get_state into caller-provided (e.g. pinned) float64 arrays."""
         _ck(lib().sdugks_get_state(self._h, _ptr(f), _ptr(W)), "sdugks_get_state")
+
+    def get_state_raw(self) -> np.ndarray:
+        """The state in the solver's own storage (bytes): restores bit for bit."""
+        n = C.c_int64(0)
+        _ck(lib().sdugks_get_state_raw(self._h, None, C.byref(n)), "sdugks_get_state_raw")
+        buf = np.empty(n.value, np.uint8)
+        _ck(lib().sdugks_get_state_raw(self._h, _ptr(buf), C.byref(n)), "sdugks_get_state_raw")
+        return buf
+
+    def set_state_raw(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _ck(lib().sdugks_set_state_raw(self._h, _ptr(buf), int(buf.size)), "sdugks_set_state_raw")
+        return self
 
     def set_state(self, f, W):
         f = _f64(f, (self.n, 9)); W = _f64(W, (self.n, 3))
