@@ -85,7 +85,9 @@ def parse():
                     help="batch-solve: converged instances solved again one at a time (plain path) and as "
                          "their own batch, for the solves/s comparison")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
-    ap.add_argument("--step-cap", type=int, default=5000, help="serve: steps before a request is reported capped")
+    ap.add_argument("--step-cap", type=int, default=400000, help="serve: steps before a request is reported capped")
+    ap.add_argument("--serve-sizes", default="config", choices=["config", "small"],
+                    help="serve: the configuration's size ranges, or smaller ones the box finishes in minutes")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "bf16dev" if args.workload == "cylinder" else "fp32"
@@ -642,7 +644,7 @@ def plain_to_target(S, case, args, stream):
     """One instance alone on the plain FP32 path (its own solver, default launch
     configuration), with the same stopping rule."""
     import torch
-    s = S.Solver.from_case(case, "fp32", stream=stream).init()
+    s = S.Solver.from_case(case, "fp32", stream=stream).init(None, initial_u(case))
     rule = Retire(args.target, args.cap_steps, args.stall_checks)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -711,21 +713,54 @@ def run_batch_solve(args):
 
 
 def run_serve(args):
-    """Continuous-batching request loop on the config-shaped request mix (seed 2)."""
+    """Continuous-batching request loop on the config-shaped request mix (seed 2): Poisson
+    arrivals at 200/s of 60/30/10 cavities / Couette channels / cylinder O-meshes, each run
+    to the residual target (stopping rule of Retire: converged, stalled, capped).  With
+    --serve-sizes small the size ranges are those the box finishes in minutes (cavities
+    32^2-128^2, Couette 4x32-4x256, cylinders 128x64; Re ranges unchanged).  A seeded
+    sample of the requests is then solved one at a time on the plain FP32 path with the
+    same stopping rule (solves/s at equal accuracy)."""
     import torch
     from paper_2007_07347_gb300 import serve as V
+    from paper_2007_07347_gb300 import sdugks as S
     torch.cuda.set_device(0)
-    wl = V.Workload(n_requests=args.requests)
+    if args.serve_sizes == "small":
+        wl = V.Workload(n_requests=args.requests, cavity_n=(32, 128), couette_ny=(32, 256),
+                        cylinder=((128, 64), (128, 64)))
+        sizes = "cavities 32^2-128^2 Re 100-5000 / Couette 4x32-4x256 Re 10 / cylinders 128x64 Re 10-100"
+    else:
+        wl = V.Workload(n_requests=args.requests)
+        sizes = "cavities 64^2-1024^2 Re 100-5000 / Couette 4x64-4x1024 Re 10 / cylinders 128x64-512x256 Re 10-100"
     reqs = wl.requests()
-    srv = V.Server(pool_bytes=16 << 30, precision=args.precision, target=1e-6, check_every=500,
-                   step_cap=args.step_cap)
+    srv = V.Server(pool_bytes=16 << 30, precision=args.precision, target=args.target, check_every=INTERVAL,
+                   step_cap=args.step_cap, stall_checks=args.stall_checks)
     sb, ss = torch.cuda.Stream(), torch.cuda.Stream()
     out = srv.run(reqs, stream_batch=sb, stream_solvers=ss)
     out["cell_steps_per_s"] = out["cell_steps"] / out["wall_s"]
     out["mlups"] = 9 * out["cell_steps_per_s"] / 1e6
-    out["config"] = {"workload": f"{args.requests} Poisson requests (200/s, seed 2), 60/30/10 cavities 64^2-1024^2 "
-                                 f"Re 100-5000 / Couette 4x64-4x1024 Re 10 / cylinders 128x64-512x256 Re 10-100, "
-                                 f"target 1e-6, cap {args.step_cap} steps", "precision": args.precision}
+    out["by_kind"] = {k: {st: sum(r.kind == k and r.status == st for r in reqs)
+                          for st in ("converged", "stalled", "capped", "diverged")}
+                      for k in ("cavity", "couette", "cylinder")}
+    # equal accuracy: a seeded sample of the converged requests, each alone on the plain path
+    conv = [r for r in reqs if r.status == "converged"]
+    rng = np.random.default_rng(11)
+    pick = sorted(rng.choice(len(conv), size=min(args.plain_sample, len(conv)), replace=False).tolist()) if conv else []
+    if pick:
+        stream = torch.cuda.Stream()
+        plain = [plain_to_target(S, conv[i].build(), args, stream) for i in pick]
+        served_t = [conv[i].done - conv[i].admitted for i in pick]
+        n_ok = sum(p["status"] == "converged" for p in plain)
+        out["equal_accuracy"] = {
+            "sample": [{"kind": conv[i].kind, "size": list(conv[i].size), "Re": round(conv[i].re, 1)} for i in pick],
+            "plain": {"wall_s": sum(p["wall_s"] for p in plain), "converged": n_ok,
+                      "solves_per_s": n_ok / sum(p["wall_s"] for p in plain)},
+            "steps_served": [conv[i].steps for i in pick], "steps_plain": [p["steps"] for p in plain],
+            "served_time_in_system_s": served_t,
+            "served_over_plain_solves_per_s": out["solves_per_s"] / max(n_ok / sum(p["wall_s"] for p in plain), 1e-30)}
+    out["config"] = {"workload": f"{args.requests} Poisson requests (200/s, seed 2), 60/30/10 {sizes}, target "
+                                 f"{args.target}, residual checked every {INTERVAL} steps, cap {args.step_cap} steps, "
+                                 f"stalled after {args.stall_checks} checks without a 1 % lower minimum",
+                     "precision": args.precision}
     print(json.dumps(out))
 
 

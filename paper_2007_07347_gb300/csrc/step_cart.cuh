@@ -341,10 +341,12 @@ __device__ __forceinline__ void cart_face_momentum(const CartInst &m, int side, 
 template <int D, class R, bool DIAG>
 __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int lme, const Sten<R> &st,
                                                    const CartInst &m, int side, int pos, const CartK<R> &k,
-                                                   const R fn[NQ], const R feqn[NQ], R drho_n, R rho_n, R ux_n,
-                                                   R uy_n, int LXY)
+                                                   const R fn[NQ], const R feqn[NQ], R b0_n, R ux_n, R uy_n,
+                                                   int LXY)
 {
     constexpr bool DEV = sizeof(R) == 4;           // FP32 compute: deviation form
+    // b0_n: the cell's rho - 1 (deviation form) or rho (FP64)
+    const R rho_n = DEV ? R(1) + b0_n : b0_n, drho_n = b0_n;
     const R nx = D == 0 ? k.hy : (D == 1 ? -k.hy : R(0));
     const R ny = D == 2 ? k.hx : (D == 3 ? -k.hx : R(0));
     const R rx = D == 0 ? R(0.5) * k.hx : (D == 1 ? R(-0.5) * k.hx : R(0));
@@ -380,10 +382,11 @@ __device__ __forceinline__ void cart_boundary_face(R F[NQ], const R *s_fbp, int 
     SDUGKS_BFACE_ALPHA(0) SDUGKS_BFACE_ALPHA(1) SDUGKS_BFACE_ALPHA(2) SDUGKS_BFACE_ALPHA(3) SDUGKS_BFACE_ALPHA(4)
     SDUGKS_BFACE_ALPHA(5) SDUGKS_BFACE_ALPHA(6) SDUGKS_BFACE_ALPHA(7) SDUGKS_BFACE_ALPHA(8)
 #undef SDUGKS_BFACE_ALPHA
-    if (DIAG) {       // diagnostic steps only; in the deviation form the rest equilibrium's
-                      // momentum flux c_s^2 n l is added back
-        const double rfx = DEV ? (D == 0 ? m.dy : (D == 1 ? -m.dy : 0.0)) / 3.0 : 0.0;
-        const double rfy = DEV ? (D == 2 ? m.dx : (D == 3 ? -m.dx : 0.0)) / 3.0 : 0.0;
+    if (DIAG && (m.force || m.bface)) {   // diagnostic steps only; in the deviation form the
+                                          // rest equilibrium's momentum flux c_s^2 n l is added back
+        constexpr double third = 1.0 / 3.0;
+        const double rfx = DEV ? third * (D == 0 ? m.dy : (D == 1 ? -m.dy : 0.0)) : 0.0;
+        const double rfy = DEV ? third * (D == 2 ? m.dx : (D == 3 ? -m.dx : 0.0)) : 0.0;
         cart_face_momentum(m, side, pos, to_f64<R>(px_) + rfx, to_f64<R>(py_) + rfy);
     }
 }
@@ -485,7 +488,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
     const int64_t g = (int64_t)gi + pitch * gj;
     const int lme = (tj + 2) * S::SX + (ti + 2);
     R fn[NQ];
-    R rho_n = R(1), drho_n = R(0), ux_n = R(0), uy_n = R(0);
+    R b0_n = DEV ? R(0) : R(1), ux_n = R(0), uy_n = R(0);   // b0_n: rho - 1 (deviation form) or rho (FP64)
     double w0n = 1.0 - rho_ref<P>(), w1n = 0.0, w2n = 0.0;
     {
         int64_t gs = -1;
@@ -551,7 +554,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             if (active) {
 #pragma unroll
                 for (int a = 0; a < NQ; a++) fn[a] = fv[a];
-                rho_n = rho; drho_n = drho; ux_n = ux; uy_n = uy;
+                b0_n = DEV ? drho : rho; ux_n = ux; uy_n = uy;
                 w0n = a0; w1n = a1; w2n = a2;
             }
         }
@@ -609,30 +612,30 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
         const bool inW = has_x(gi - 1), inE = has_x(gi + 1);
         const bool inS = has_y(gj - 1), inN = has_y(gj + 1);
         R feqn[NQ];
-        if (!(inW && inE && inS && inN)) feq9fd<R>(DEV ? drho_n : rho_n, rho_n, ux_n, uy_n, feqn);   // boundary cells only
+        if (!(inW && inE && inS && inN)) feq9fd<R>(b0_n, DEV ? R(1) + b0_n : b0_n, ux_n, uy_n, feqn);   // boundary cells only
         if (inW) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] -= s_fx[r * S::NSX + fW];
         } else {
-            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, gj, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<1, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 3, gj, k, fn, feqn, b0_n, ux_n, uy_n, LXY);
         }
         if (inE) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[XSLOT_A(r)] += s_fx[r * S::NSX + fE];
         } else {
-            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, gj, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<0, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 1, gj, k, fn, feqn, b0_n, ux_n, uy_n, LXY);
         }
         if (inS) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] -= s_fy[r * S::NSY + fS];
         } else {
-            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, gi, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<3, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 0, gi, k, fn, feqn, b0_n, ux_n, uy_n, LXY);
         }
         if (inN) {
 #pragma unroll
             for (int r = 0; r < 6; r++) F[YSLOT_A(r)] += s_fy[r * S::NSY + fN];
         } else {
-            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, gi, k, fn, feqn, drho_n, rho_n, ux_n, uy_n, LXY);
+            cart_boundary_face<2, R, DIAG>(F, s_fbp, lme, sten(ti, tj), m, 2, gi, k, fn, feqn, b0_n, ux_n, uy_n, LXY);
         }
 
         if (DIAG && (m.force || m.bface)) {
@@ -648,7 +651,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
                     py_ += R(EY(a)) * fl[r * stride];
                 }
                 // deviation form: plus the rest equilibrium's flux c_s^2 n l (n out of the fluid)
-                const double rf = DEV ? (double)sgn * (y_face ? m.dx : m.dy) / 3.0 : 0.0;
+                const double rf = DEV ? (1.0 / 3.0) * (double)sgn * (y_face ? m.dx : m.dy) : 0.0;
                 cart_face_momentum(m, side, pos, to_f64<R>(sgn * px_) + (y_face ? 0.0 : rf),
                                    to_f64<R>(sgn * py_) + (y_face ? rf : 0.0));
             };
@@ -677,7 +680,7 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
             vel_of<R>(W0, W1, W2, ux1, uy1);
             feq9f<R>(rho1, ux1, uy1, feq1);
         } else {
-            const R drho1 = drho_n - d0;
+            const R drho1 = b0_n - d0;
             rho1 = R(1) + drho1;
             vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
             feq9fd<R>(drho1, rho1, ux1, uy1, feq1);
@@ -746,12 +749,15 @@ __device__ __forceinline__ bool cta_wait_staged(const CartInst &m, uint32_t bar,
 // CART_GENERAL runs every block with the general variant.  One code path serves a grid
 // whose blocks all run in one wave better, where the slowest (edge) blocks set the time:
 // there the edge blocks' general code is not displaced by the interior variant's.
+// DIAG: the diagnostic step (CART_GENERAL only), which also reports the momentum leaving
+// the fluid through the boundary faces; ordinary steps carry none of that code.
 enum CartMode { CART_SPECIALISED = 0, CART_SPECIALISED_TMA = 1, CART_GENERAL = 2 };
 
-template <int P, int TX, int TY, int MODE>
+template <int P, int TX, int TY, int MODE, bool DIAG = false>
 __global__ void __launch_bounds__(cart_threads<TX, TY>(), P == P_FP64 ? 1 : (cart_threads<TX, TY>() <= 320 ? 4 : 2))
 k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tw)
 {
+    static_assert(!DIAG || MODE == CART_GENERAL, "diagnostic steps run every block on the general variant");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     step_dependency_wait();
     const int ntx = (m.nx + TX - 1) / TX;
@@ -774,11 +780,11 @@ k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, c
             cart_tile<P, TX, TY, false, true>(m, par, tbx, tby, smem_raw);
         }
     } else {
-        cart_tile<P, TX, TY, true, false>(m, par, tbx, tby, smem_raw);
+        cart_tile<P, TX, TY, DIAG, false>(m, par, tbx, tby, smem_raw);
     }
 }
 
-template <int P, int TX, int TY, int MODE> constexpr size_t cart_step_smem() {
+template <int P, int TX, int TY, int MODE, bool DIAG = false> constexpr size_t cart_step_smem() {
     return MODE == CART_SPECIALISED_TMA ? CartTmaBox<P, TX, TY>::SMEM : cart_smem<P, TX, TY>();
 }
 
@@ -802,8 +808,8 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
     }
 }
 
-template <int P, int TX, int TY, int MODE> cudaError_t prepare_mode_p() {
-    return cudaFuncSetAttribute(k_step_cart<P, TX, TY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int P, int TX, int TY, int MODE, bool DIAG = false> cudaError_t prepare_mode_p() {
+    return cudaFuncSetAttribute(k_step_cart<P, TX, TY, MODE, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)cart_step_smem<P, TX, TY, MODE>());
 }
 
@@ -811,16 +817,22 @@ template <int P, int TX, int TY> cudaError_t prepare_cart_p() {
     cudaError_t e = prepare_mode_p<P, TX, TY, CART_SPECIALISED>();
     if (e == cudaSuccess) e = prepare_mode_p<P, TX, TY, CART_SPECIALISED_TMA>();
     if (e == cudaSuccess) e = prepare_mode_p<P, TX, TY, CART_GENERAL>();
+    if (e == cudaSuccess) e = prepare_mode_p<P, TX, TY, CART_GENERAL, true>();
     return e;
 }
 
 // tma: the maps for TMA staging (nullptr: plain loads); general: every block on the
-// general path (ignored with TMA staging)
+// general path (ignored with TMA staging).  A diagnostic step (m.force or m.bface set)
+// runs the diagnostic instance, every block on the general path with plain loads.
 template <int P, int TX, int TY>
 cudaError_t launch_cart_p(const CartInst &m, const CartTma *tma, bool general, int par, cudaStream_t st)
 {
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
     const dim3 grid(ntx * nty), block(cart_threads<TX, TY>());
+    static const CUtensorMap none0{};
+    if (m.force || m.bface)
+        return launch_step_kernel(k_step_cart<P, TX, TY, CART_GENERAL, true>, grid, block,
+                                  cart_step_smem<P, TX, TY, CART_GENERAL>(), st, m, par, none0, none0);
     if (tma)
         return launch_step_kernel(k_step_cart<P, TX, TY, CART_SPECIALISED_TMA>, grid, block,
                                   cart_step_smem<P, TX, TY, CART_SPECIALISED_TMA>(), st, m, par, tma->f[par], tma->W[par]);

@@ -101,7 +101,7 @@ __device__ __forceinline__ void interface_feq(typename Store<P>::R w0, typename 
 // which the deviation form leaves out of its face fluxes; 0 in FP64.
 template <int P> __device__ __forceinline__ double ref_momentum(typename Store<P>::R nl)
 {
-    return Dev<P>::ON ? to_f64<typename Store<P>::R>(nl) / 3.0 : 0.0;
+    return Dev<P>::ON ? (1.0 / 3.0) * to_f64<typename Store<P>::R>(nl) : 0.0;
 }
 
 template <int P>
@@ -121,7 +121,9 @@ __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict_
     }
 }
 
-template <int P>
+// DIAG: the diagnostic step, which also reports the momentum leaving the fluid through
+// the boundary faces (m.force, m.bface); ordinary steps carry none of that code.
+template <int P, bool DIAG = false>
 __global__ void __launch_bounds__(TILED_THREADS, P == P_FP64 ? 1 : 4)
 k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__restrict__ fin,
              typename Store<P>::T *__restrict__ fout, const double *__restrict__ Wn, double *__restrict__ Wout)
@@ -308,11 +310,14 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 const R s = xdot<R>(a, nx, ny);
                 const R fl = s * ((fbar[a] + k.b * feqb[a]) * k.c);
                 s_flux[a * LF_MAX + lf] = fl;
-                px_ += R(EX(a)) * fl;
-                py_ += R(EY(a)) * fl;
+                if constexpr (DIAG) {
+                    px_ += R(EX(a)) * fl;
+                    py_ += R(EY(a)) * fl;
+                }
             }
-            tiled_face_momentum(m, B & 0xFF, f0 + lf, to_f64<R>(px_) + ref_momentum<P>(nx),
-                                to_f64<R>(py_) + ref_momentum<P>(ny));
+            if constexpr (DIAG)
+                tiled_face_momentum(m, B & 0xFF, f0 + lf, to_f64<R>(px_) + ref_momentum<P>(nx),
+                                    to_f64<R>(py_) + ref_momentum<P>(ny));
         } else {
             // boundary face of cell A (an interior cell of the tile): Sec. III rules
             const int p = B & 0xFF;
@@ -342,10 +347,14 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                     fb = (FA + k.b * feqb[a]) * k.c;
                 }
                 s_flux[a * LF_MAX + lf] = s * fb;
-                px_ += R(EX(a)) * (s * fb);
-                py_ += R(EY(a)) * (s * fb);
+                if constexpr (DIAG) {
+                    px_ += R(EX(a)) * (s * fb);
+                    py_ += R(EY(a)) * (s * fb);
+                }
             }
-            tiled_face_momentum(m, p, f0 + lf, to_f64<R>(px_) + ref_momentum<P>(nx), to_f64<R>(py_) + ref_momentum<P>(ny));
+            if constexpr (DIAG)
+                tiled_face_momentum(m, p, f0 + lf, to_f64<R>(px_) + ref_momentum<P>(nx),
+                                    to_f64<R>(py_) + ref_momentum<P>(ny));
         }
     }
     __syncthreads();
@@ -408,13 +417,18 @@ template <int P> constexpr size_t tiled_smem() {
            sizeof(uint32_t) * LF_MAX;
 }
 
-template <int P> cudaError_t prepare_tiled_p() {
-    cudaError_t e = cudaFuncSetAttribute(k_step_tiled<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_smem<P>());
+template <int P, bool DIAG> cudaError_t prepare_tiled_pd() {
+    cudaError_t e = cudaFuncSetAttribute(k_step_tiled<P, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tiled_smem<P>());
     // all of the unified L1/shared array as shared memory: four FP32 tiles per SM
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step_tiled<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_step_tiled<P, DIAG>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     return e;
+}
+template <int P> cudaError_t prepare_tiled_p() {
+    cudaError_t e = prepare_tiled_pd<P, false>();
+    return e == cudaSuccess ? prepare_tiled_pd<P, true>() : e;
 }
 
 template <int P>
@@ -423,7 +437,10 @@ cudaError_t launch_tiled_p(const TiledMesh &m, const Coefs &c, const void *fin, 
 {
     using T = typename Store<P>::T;
     if (m.n_tiles <= 0) return cudaSuccess;
-    return launch_step_kernel(k_step_tiled<P>, dim3(m.n_tiles), dim3(TILED_THREADS), tiled_smem<P>(), st, m, c,
+    if (m.force || m.bface)     // the diagnostic step
+        return launch_step_kernel(k_step_tiled<P, true>, dim3(m.n_tiles), dim3(TILED_THREADS), tiled_smem<P>(), st, m,
+                                  c, static_cast<const T *>(fin), static_cast<T *>(fout), Wn, Wout);
+    return launch_step_kernel(k_step_tiled<P, false>, dim3(m.n_tiles), dim3(TILED_THREADS), tiled_smem<P>(), st, m, c,
                               static_cast<const T *>(fin), static_cast<T *>(fout), Wn, Wout);
 }
 

@@ -2,8 +2,9 @@
 
     python -m paper_2007_07347_gb300.profile_step CASE [PRECISION] [STEPS] [TILE] [STAGING]
 
-CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh), or
-microcavity (the rarefied solver: 40 x 40 cells, 100 x 100 velocities, Kn 1).  Used
+CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh),
+microcavity (the rarefied solver: 40 x 40 cells, 100 x 100 velocities, Kn 1), or batch
+(the 256 cavities of the batched configuration, N ~ logU[32, 512], seed 1).  Used
 under ncu with ``-k regex:k_step`` (``regex:k_dvm`` for the rarefied kernels) to
 capture single step launches.  STAGING (Cartesian kernel): loads (default) or tma.
 """
@@ -30,6 +31,19 @@ def main(argv):
     tile = int(argv[4]) if len(argv) > 4 else 0
     staging = argv[5] if len(argv) > 5 else "loads"
     torch.cuda.set_device(0)
+    if name == "batch":
+        cases = [M.cavity(n, Re=re) for n, re in M.batch_cavities(256, seed=1)]
+        meshes = [S.Mesh(c.mesh, c.bcs) for c in cases]
+        probe = S.Batch(1 << 20, prec, 4)
+        need = sum(probe.footprint(m) for m in meshes)
+        probe.close()
+        b = S.Batch(need + (64 << 20), prec, 512)
+        for c, m in zip(cases, meshes):
+            b.add(m, c.tau, c.dt)
+        b.step(nsteps)
+        torch.cuda.synchronize()
+        print("batch", b.info())
+        return
     if name == "microcavity":
         d = S.Dvm.from_case(M.micro_cavity(40, Kn=1.0), "fp64" if prec == "fp64" else "fp32", graph_steps=-1).init()
         d.step(nsteps)

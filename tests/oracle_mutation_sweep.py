@@ -19,6 +19,7 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 
 D2Q9, DVM = "tests/test_oracle_pins.py", "tests/test_oracle_pins_dvm.py"
+FORCES = "tests/test_oracle_pins_forces.py"
 
 # (what, pins, text in the oracle, replacement, which occurrence: 0 first, -1 last)
 MUTATIONS = [
@@ -82,6 +83,16 @@ MUTATIONS = [
      "m->gpos[2 * f] = xo[0] + 2.0 * dn * Nx;", "m->gpos[2 * f] = xo[0] + dn * Nx;", 0),
     ("symmetry: ghost's x-gradient not reflected", D2Q9,
      "if (mir == 1) { ak = MIRROR_X[a]; gsx = -1.0; }", "if (mir == 1) { ak = MIRROR_X[a]; gsx = 1.0; }", 0),
+    ("forces: x-momentum flux from the y component of xi", FORCES,
+     "px += XI[a][0] * s * fb[NQ * fc + a];", "px += XI[a][1] * s * fb[NQ * fc + a];", 0),
+    ("forces: flux without the normal velocity s", FORCES,
+     "py += XI[a][1] * s * fb[NQ * fc + a];", "py += XI[a][1] * fb[NQ * fc + a];", 0),
+    ("forces: rows for periodic faces too", FORCES,
+     "if (m->nbr[fc] >= 0 || m->bck[-1 - m->nbr[fc]] == KIND_PERIODIC) continue;",
+     "if (m->nbr[fc] >= 0) continue;", 0),
+    ("forces: the previous step's interface values", FORCES,
+     "    if (!rc && bflux) boundary_flux(&m, w.fb, bflux);\n",
+     "    if (!rc && bflux) { one_step(&m, tau, dt, f, W, &w); boundary_flux(&m, w.fb, bflux); }\n", 0),
     ("rarefied: sign of the W update", DVM,
      "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
     ("rarefied: wall density without its b G_out term", DVM,
