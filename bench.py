@@ -83,7 +83,8 @@ def parse():
                          "retired as stalled at its floor")
     ap.add_argument("--plain-sample", type=int, default=16,
                     help="batch-solve: converged instances solved again one at a time (plain path) and as "
-                         "their own batch, for the solves/s comparison")
+                         "their own batch, for the solves/s comparison; serve: requests solved one at a time "
+                         "(0: every request)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--step-cap", type=int, default=400000, help="serve: steps before a request is reported capped")
     ap.add_argument("--serve-sizes", default="config", choices=["config", "small"],
@@ -734,29 +735,29 @@ def run_serve(args):
     reqs = wl.requests()
     srv = V.Server(pool_bytes=16 << 30, precision=args.precision, target=args.target, check_every=INTERVAL,
                    step_cap=args.step_cap, stall_checks=args.stall_checks)
-    sb, ss = torch.cuda.Stream(), torch.cuda.Stream()
+    sb = torch.cuda.Stream()
+    ss = [torch.cuda.Stream() for _ in range(8)]          # single (tiled) solvers take these in turn
     out = srv.run(reqs, stream_batch=sb, stream_solvers=ss)
     out["cell_steps_per_s"] = out["cell_steps"] / out["wall_s"]
     out["mlups"] = 9 * out["cell_steps_per_s"] / 1e6
     out["by_kind"] = {k: {st: sum(r.kind == k and r.status == st for r in reqs)
                           for st in ("converged", "stalled", "capped", "diverged")}
                       for k in ("cavity", "couette", "cylinder")}
-    # equal accuracy: a seeded sample of the converged requests, each alone on the plain path
-    conv = [r for r in reqs if r.status == "converged"]
+    # equal accuracy: the same requests solved one at a time on the plain FP32 path with the
+    # same stopping rule (every request, or a seeded sample with --plain-sample > 0)
     rng = np.random.default_rng(11)
-    pick = sorted(rng.choice(len(conv), size=min(args.plain_sample, len(conv)), replace=False).tolist()) if conv else []
-    if pick:
-        stream = torch.cuda.Stream()
-        plain = [plain_to_target(S, conv[i].build(), args, stream) for i in pick]
-        served_t = [conv[i].done - conv[i].admitted for i in pick]
-        n_ok = sum(p["status"] == "converged" for p in plain)
-        out["equal_accuracy"] = {
-            "sample": [{"kind": conv[i].kind, "size": list(conv[i].size), "Re": round(conv[i].re, 1)} for i in pick],
-            "plain": {"wall_s": sum(p["wall_s"] for p in plain), "converged": n_ok,
-                      "solves_per_s": n_ok / sum(p["wall_s"] for p in plain)},
-            "steps_served": [conv[i].steps for i in pick], "steps_plain": [p["steps"] for p in plain],
-            "served_time_in_system_s": served_t,
-            "served_over_plain_solves_per_s": out["solves_per_s"] / max(n_ok / sum(p["wall_s"] for p in plain), 1e-30)}
+    pick = (list(range(len(reqs))) if args.plain_sample <= 0 else
+            sorted(rng.choice(len(reqs), size=min(args.plain_sample, len(reqs)), replace=False).tolist()))
+    stream = torch.cuda.Stream()
+    plain = [plain_to_target(S, reqs[i].build(), args, stream) for i in pick]
+    p_wall = sum(p["wall_s"] for p in plain)
+    n_ok = sum(p["status"] == "converged" for p in plain)
+    same = sum(p["status"] == reqs[i].status for p, i in zip(plain, pick))
+    out["equal_accuracy"] = {
+        "requests": len(pick), "same_outcome": same,
+        "plain": {"wall_s": p_wall, "converged": n_ok, "solves_per_s": n_ok / p_wall if p_wall > 0 else 0.0},
+        "served_over_plain_solves_per_s": (out["solves_per_s"] / (n_ok / p_wall)) if n_ok else None,
+        "steps_differ": sum(p["steps"] != reqs[i].steps for p, i in zip(plain, pick))}
     out["config"] = {"workload": f"{args.requests} Poisson requests (200/s, seed 2), 60/30/10 {sizes}, target "
                                  f"{args.target}, residual checked every {INTERVAL} steps, cap {args.step_cap} steps, "
                                  f"stalled after {args.stall_checks} checks without a 1 % lower minimum",

@@ -7,8 +7,8 @@ namespace sdugks {
 
 namespace {
 
-constexpr int BTX = 16, BTY = 16;
-constexpr int RT = 256;                    // residual block = one 16x16 block of cells
+constexpr int BTX = 16, BTY = BATCH_TY;
+constexpr int RT = BTX * BTY;              // residual block = one block of cells
 
 template <int P> cudaError_t prep_p() {
     return cudaFuncSetAttribute(k_step_batch<P, BTX, BTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,

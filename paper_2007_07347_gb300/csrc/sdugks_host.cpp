@@ -1855,7 +1855,7 @@ extern "C" int sdugks_batch_add(sdugks_batch *b, const sdugks_mesh *m, double ta
     bi.off = off;
     bi.bytes = bytes;
     bi.admitted_at = b->steps;
-    bi.ntiles = (int64_t)((g.nx + 15) / 16) * ((g.ny + 15) / 16);
+    bi.ntiles = (int64_t)((g.nx + 15) / 16) * ((g.ny + BATCH_TY - 1) / BATCH_TY);
     fill_cart_inst(bi.ci, *m, g, tau, dt, pitch, npad);
     {
         auto up = [](size_t x) { return (x + 255) & ~size_t(255); };

@@ -125,6 +125,10 @@ cudaError_t prepare_tiled_fp32(int prec);
 cudaError_t prepare_cart(int prec);
 // block shapes of the Cartesian kernel: 0 = 16x16, 1 = 16x14, 2 = 16x8 (FP64: 16x16 only)
 constexpr int CART_SHAPES = 3;
+// block of the batched kernel: 16 x BATCH_TY cells per (instance, block) work item (the
+// 16x8 shape fits four CTAs per SM, the fastest shape of the single-solve kernel on
+// grids of many waves)
+constexpr int BATCH_TY = 8;
 constexpr int CART_TY[CART_SHAPES] = {16, 14, 8};
 // Tensor maps of one Cartesian state for the TMA staging of interior blocks:
 // f[b] views f buffer b as (x, y, velocity), W[b] views W buffer b as (x, y, component);

@@ -791,16 +791,24 @@ template <int P, int TX, int TY, int MODE, bool DIAG = false> constexpr size_t c
 // Batched: a fixed grid walks the (instance, block) work list; the item count is in
 // device memory so that a captured graph stays valid while instances come and go.
 template <int P, int TX, int TY>
-__global__ void __launch_bounds__(cart_threads<TX, TY>(), 2)
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), cart_threads<TX, TY>() <= 320 ? 4 : 2)
 k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items, const int *__restrict__ n_items,
              int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step_dependency_wait();
+    // the item's instance record is copied to shared memory once per item, so that the
+    // block routine reads its fields there instead of from global memory
+    static_assert(sizeof(CartInst) % 4 == 0, "CartInst copies in 4-byte words");
+    __shared__ __align__(16) CartInst s_inst;
+    constexpr int NW = (int)(sizeof(CartInst) / 4);
     const int n = *n_items;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int2 it = items[w];
-        const CartInst &m = insts[it.x];
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + it.x);
+        for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst)[q] = src[q];
+        __syncthreads();
+        const CartInst &m = s_inst;
         const int ntx = (m.nx + TX - 1) / TX, bx = it.y % ntx, by = it.y / ntx;
         if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
         else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);

@@ -102,14 +102,28 @@ class Server:
     check_every: int = 1000
     step_cap: int = 200000
     stall_checks: int = 0    # 0: no stall rule
+    prep_threads: int = 4    # host threads that build the arrivals' meshes (0: in the loop)
     solver_pool_bytes: int = 4 << 30
     keep_results: bool = False
     log: list = field(default_factory=list)
 
     def run(self, requests: list, stream_batch=None, stream_solvers=None) -> dict:
+        """stream_solvers: one stream, or a list of streams that the single (tiled) solvers
+        take in turn, so that the steps of several small solves run at the same time."""
         import torch
+        from concurrent.futures import ThreadPoolExecutor
         batch = S.Batch(self.pool_bytes, self.precision, self.max_instances, stream=stream_batch)
         solver_bytes = 0
+        # mesh building of the arrivals (the case's arrays, then sdugks_mesh_create, which
+        # runs without the interpreter lock) on worker threads, off the loop's path
+        workers = ThreadPoolExecutor(self.prep_threads) if self.prep_threads > 0 else None
+        prep = {}
+
+        def prepare(r):
+            case = r.build()
+            if r.mesh is None:
+                r.mesh = S.Mesh(case.mesh, case.bcs)
+            return r
         queue = sorted(requests, key=lambda r: r.arrival)
         pending = list(queue)
         running = []
@@ -127,18 +141,25 @@ class Server:
                 batch.step(self.check_every)
             arrived = [r for r in pending if r.arrival <= now()]
             for r in arrived:                    # host-side mesh work, overlapping the steps
-                case = r.build()
-                if r.mesh is None:
-                    r.mesh = S.Mesh(case.mesh, case.bcs)
-            # admit every arrived request whose footprint fits (FIFO, skipping ahead);
-            # adding to the batch waits for the interval in flight on its stream
+                if workers is None:
+                    prepare(r)
+                elif r.rid not in prep:
+                    prep[r.rid] = workers.submit(prepare, r)
+            # admit every arrived request that is prepared and whose footprint fits (FIFO,
+            # skipping ahead); adding to the batch waits for the interval in flight on its stream
             for r in arrived:
+                if workers is not None:
+                    fu = prep[r.rid]
+                    if not fu.done():
+                        continue
+                    fu.result()                  # re-raises a failure of the mesh set-up
                 case, m = r.case, r.mesh
                 if r.kind == "cylinder":
                     need = 400 * case.mesh.n_cells          # state + mesh data, tiled FP32 path
                     if solver_bytes + need > self.solver_pool_bytes:
                         continue
-                    s = S.Solver(m, case.tau, case.dt, self.precision, stream=stream_solvers)
+                    pool = stream_solvers if isinstance(stream_solvers, (list, tuple)) else [stream_solvers]
+                    s = S.Solver(m, case.tau, case.dt, self.precision, stream=pool[r.rid % len(pool)])
                     s._mesh = m
                     s.init(None, np.tile(case.u0, (case.mesh.n_cells, 1)))
                     r.handle = ("solver", s, need)
@@ -158,7 +179,7 @@ class Server:
             if not stepped:
                 if not running:
                     nxt = min(r.arrival for r in pending)
-                    time.sleep(max(0.0, min(0.01, nxt - now())))
+                    time.sleep(max(0.0, min(0.01, nxt - now())) if nxt > now() else 0.001)
                     idle_waits += 1
                 continue
             res = batch.residual()
@@ -196,6 +217,8 @@ class Server:
                     running.remove(r)
         wall = now()
         torch.cuda.synchronize()
+        if workers is not None:
+            workers.shutdown()
         return {**serve_stats(requests, wall), "batch": batch.info()}
 
 

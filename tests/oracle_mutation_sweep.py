@@ -143,6 +143,8 @@ def main() -> int:
                                cwd=ROOT, capture_output=True, text=True,
                                env=dict(os.environ, SDUGKS_ORACLE_LIB=so_path))
             caught = [ln.split("::")[1].split(" ")[0] for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
+            if not caught and r.returncode not in (0, 1):       # the pins' process died: the mistake showed
+                caught = [f"a crash of the pins (exit status {r.returncode})"]
             print(f"{what}: " + (f"caught by {caught[0]}" if caught else "NOT CAUGHT"), flush=True)
             missed += not caught
     print(f"{len(MUTATIONS) - missed} of {len(MUTATIONS)} planted mistakes caught")

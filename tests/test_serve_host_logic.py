@@ -13,8 +13,12 @@ FULL = next(code for code, name in S.ERRORS.items() if name == "FULL")
 
 
 class FakeMesh:
+    threads = set()
+
     def __init__(self, mesh, bcs):
+        import threading
         self.n_cells = mesh.n_cells
+        FakeMesh.threads.add(threading.get_ident())
 
 
 class FakeBatch:
@@ -141,3 +145,18 @@ def test_a_residual_that_stops_falling_retires_as_stalled(fakes, monkeypatch):
     assert out["stalled"] == 6 and out["converged"] == 0 and out["met_target"] is False
     assert all(r.status == "stalled" and r.steps == 4 * 500 for r in reqs)   # the first check sets the minimum
     assert out["solves_per_s"] == 0.0
+
+
+def test_meshes_are_built_off_the_loop_thread(fakes):
+    """The arrivals' meshes are built on the worker threads (prep_threads > 0), and in the
+    loop itself with prep_threads = 0; every request finishes either way."""
+    import threading
+    for workers in (4, 0):
+        FakeMesh.threads = set()
+        reqs = _requests(10)
+        out = V.Server(pool_bytes=1 << 40, check_every=500, step_cap=3000, target=1e-9, prep_threads=workers,
+                       solver_pool_bytes=1 << 40).run(reqs)
+        assert out["capped"] == 10
+        main = threading.get_ident() in FakeMesh.threads
+        assert (not main) if workers else (FakeMesh.threads == {threading.get_ident()})
+
