@@ -266,11 +266,19 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
             for (int a = 0; a < NQ; a++) {
                 const R s = xdot<R>(a, nx, ny);
                 const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
-                const R FA = s_fbp[a * LOC_MAX + A] + (rax - ex) * s_sig[(2 * a) * SIG_MAX + A] +
-                             (ray - ey) * s_sig[(2 * a + 1) * SIG_MAX + A];
-                const R FB = s_fbp[a * LOC_MAX + B] + (rbx - ex) * s_sig[(2 * a) * SIG_MAX + B] +
-                             (rby - ey) * s_sig[(2 * a + 1) * SIG_MAX + B];
-                fbar[a] = s > k.tie ? FA : (s < -k.tie ? FB : R(0.5) * (FA + FB));
+                // the upwind side's reconstruction only (side B when the velocity leaves
+                // it, else side A); a tangential velocity takes the mean of both sides
+                const bool from_b = s < -k.tie;
+                const int U = from_b ? B : A;
+                const R rux = from_b ? rbx : rax, ruy = from_b ? rby : ray;
+                R v = s_fbp[a * LOC_MAX + U] + (rux - ex) * s_sig[(2 * a) * SIG_MAX + U] +
+                      (ruy - ey) * s_sig[(2 * a + 1) * SIG_MAX + U];
+                if (!from_b && !(s > k.tie)) {
+                    const R FB = s_fbp[a * LOC_MAX + B] + (rbx - ex) * s_sig[(2 * a) * SIG_MAX + B] +
+                                 (rby - ey) * s_sig[(2 * a + 1) * SIG_MAX + B];
+                    v = R(0.5) * (v + FB);
+                }
+                fbar[a] = v;
                 w0 += fbar[a];
                 if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
