@@ -3,6 +3,7 @@ scope stated beside each measured number.
 
     python -m paper_2007_07347_gb300.validate cylinder # 512x256 O-mesh Re 40 to steady state, FP64/FP32/bf16
     python -m paper_2007_07347_gb300.validate cylinder fp16dev   # the same for the listed storages only
+    python -m paper_2007_07347_gb300.validate cylinder fp32 --max-steps 3000000   # a longer cap (default 600,000)
     python -m paper_2007_07347_gb300.validate shedding # 512x256 O-mesh Re 60/80/100: St and mean Cd
     python -m paper_2007_07347_gb300.validate plate    # laminar flat plate Re_L 1e5: Cd against Blasius
 
@@ -173,10 +174,17 @@ def plate():
 
 
 if __name__ == "__main__":
-    what = sys.argv[1] if len(sys.argv) > 1 else "cylinder"
-    if what == "shedding" and len(sys.argv) > 2:
-        shedding(tuple(float(x) for x in sys.argv[2:]))
-    elif what == "cylinder" and len(sys.argv) > 2:
-        cylinder(precisions=tuple(sys.argv[2:]))           # e.g. cylinder fp16dev bf16dev
+    argv = sys.argv[1:]
+    max_steps = 600000
+    if "--max-steps" in argv:                              # e.g. cylinder fp32 --max-steps 3000000
+        i = argv.index("--max-steps")
+        max_steps = int(argv[i + 1])
+        argv = argv[:i] + argv[i + 2:]
+    what = argv[0] if argv else "cylinder"
+    if what == "shedding" and len(argv) > 1:
+        shedding(tuple(float(x) for x in argv[1:]))
+    elif what == "cylinder":
+        precisions = tuple(argv[1:]) or ("fp64", "fp32", "bf16dev")   # e.g. cylinder fp16dev bf16dev
+        cylinder(max_steps=max_steps, precisions=precisions)
     else:
-        {"cylinder": cylinder, "shedding": shedding, "plate": plate}[what]()
+        {"shedding": shedding, "plate": plate}[what]()
