@@ -213,6 +213,7 @@ def measured_peaks():
 STEP_SOURCES = {
     "k_step_cart": ["d2q9.cuh", "sdugks_internal.h", "step_cart.cuh", "k_cart.cu"],
     "k_step_tiled": ["d2q9.cuh", "sdugks_internal.h", "step_tiled.cuh", "k_step_fp32.cu"],
+    "k_step_batch": ["d2q9.cuh", "sdugks_internal.h", "step_cart.cuh", "k_batch.cu"],
 }
 
 
@@ -234,7 +235,7 @@ def profiled_traffic(kernel_key: str):
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(kernel_key)
-        kernel = "k_step_tiled" if kernel_key.startswith("k_step_tiled") else "k_step_cart"
+        kernel = next(k for k in STEP_SOURCES if kernel_key.startswith(k))
         if e and e.get("source_hash") == kernel_source_hash(kernel):
             return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -514,7 +515,8 @@ def other_configs(args, S, stream, flush):
         "value": cells * 9 * interval * bsteps / t / 1e6, "unit": "MLUPS", "steps": bsteps,
         "time_steps_per_step": interval, "ms_per_step": 1e3 * t / bsteps, "cells": cells,
         "roofline": {"bound": "hbm", "achieved": alg / launch_s / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": alg / launch_s / 1e9 / peak, "traffic": None, "kernel": "k_step_batch",
+                     "frac": alg / launch_s / 1e9 / peak, "traffic": profiled_traffic("k_step_batch_fp32_batch256"),
+                     "kernel": "k_step_batch",
                      "algorithmic_bytes_per_launch": alg, "avg_launch_us": launch_s * 1e6,
                      "peak_kind": f"{peak_kind} (hbm_gbs)", "l2_resident": False,
                      "note": "1.4 GB of state: every launch streams it from HBM; the launch time includes the share "
