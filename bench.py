@@ -511,7 +511,7 @@ def other_configs(args, S, stream, flush):
     launch_s = t / (interval * bsteps)               # the residual reductions are included
     out["batch_256_cavities_fp32"] = {
         "workload": "batch of 256 lid-driven cavities, N~logU[32,512], Re~logU[100,5000], seed 1, lid 0.1, CFL 0.5, "
-                    "FP32, one batched launch per step over the (instance, 16x16 block) work list",
+                    "FP32, one batched launch per step over the (instance, 16x8 block) work list",
         "value": cells * 9 * interval * bsteps / t / 1e6, "unit": "MLUPS", "steps": bsteps,
         "time_steps_per_step": interval, "ms_per_step": 1e3 * t / bsteps, "cells": cells,
         "roofline": {"bound": "hbm", "achieved": alg / launch_s / 1e9, "peak": peak, "unit": "GB/s",
