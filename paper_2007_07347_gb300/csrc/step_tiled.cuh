@@ -60,6 +60,43 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // all committed groups but the most recent one
 __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// FP32 compute: one FFMA2/FMUL2/FADD2 instruction does two independent FP32 operations
+// (each lane rounded as the scalar operation), so the per-velocity arithmetic of the
+// phases below runs two velocities at a time, paired (1,2) (3,4) (5,6) (7,8).
+__device__ __forceinline__ float2 pr2(float a, float b) { return make_float2(a, b); }
+
+// FP32 reconstruction of velocity a at a face from staged cell U (Eqs. fbpsource, fbar):
+// fbar+_U + (r_U - xi_a dt) . sigma_U, with r_U = x_f - x_U = (rx, ry)
+template <int a>
+__device__ __forceinline__ float rec1(const float *s_fbp, const float *s_sig, int U, float rx, float ry, float dt)
+{
+    return s_fbp[a * LOC_MAX + U] + (rx - float(EX(a)) * dt) * s_sig[(2 * a) * SIG_MAX + U] +
+           (ry - float(EY(a)) * dt) * s_sig[(2 * a + 1) * SIG_MAX + U];
+}
+
+// The interface values of the velocity pair (a, a+1) at an interior face from the
+// upwind side of each (side B when the velocity leaves B, else side A); a tangential
+// velocity takes the mean of both sides.
+template <int a>
+__device__ __forceinline__ void face_pair(float fbar[NQ], const float *s_fbp, const float *s_sig, int A, int B,
+                                          float nx, float ny, float rax, float ray, float rbx, float rby, float dt,
+                                          float tie)
+{
+    constexpr int b = a + 1;
+    const float sa = xdot<float>(a, nx, ny), sb = xdot<float>(b, nx, ny);
+    const bool ba = sa < -tie, bb = sb < -tie;
+    const int Ua = ba ? B : A, Ub = bb ? B : A;
+    const float2 cx = __fadd2_rn(pr2(ba ? rbx : rax, bb ? rbx : rax), pr2(-float(EX(a)) * dt, -float(EX(b)) * dt));
+    const float2 cy = __fadd2_rn(pr2(ba ? rby : ray, bb ? rby : ray), pr2(-float(EY(a)) * dt, -float(EY(b)) * dt));
+    float2 v = __ffma2_rn(cx, pr2(s_sig[(2 * a) * SIG_MAX + Ua], s_sig[(2 * b) * SIG_MAX + Ub]),
+                          pr2(s_fbp[a * LOC_MAX + Ua], s_fbp[b * LOC_MAX + Ub]));
+    v = __ffma2_rn(cy, pr2(s_sig[(2 * a + 1) * SIG_MAX + Ua], s_sig[(2 * b + 1) * SIG_MAX + Ub]), v);
+    fbar[a] = v.x;
+    fbar[b] = v.y;
+    if (!ba && !(sa > tie)) fbar[a] = 0.5f * (fbar[a] + rec1<a>(s_fbp, s_sig, B, rbx, rby, dt));
+    if (!bb && !(sb > tie)) fbar[b] = 0.5f * (fbar[b] + rec1<b>(s_fbp, s_sig, B, rbx, rby, dt));
+}
+
 // Diagnostic steps (m.force or m.bface set): the momentum (px, py) leaving the fluid
 // through boundary face `q` (index over all local faces) of patch p, added to the
 // patch total and written to the face's row.
@@ -115,9 +152,19 @@ __device__ __forceinline__ void cell_fbp(const typename Store<P>::T *__restrict_
     macro_of<R>(Wn[g], Wn[np + g], Wn[2 * np + g], drho, rho, ux, uy);
     feq9fd<R>(Dev<P>::ON ? drho : rho, rho, ux, uy, fe);      // FP32 compute: deviation form (g = f - w)
 #pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        fn[a] = Store<P>::dec(fin[a * np + g], fe[a], a);
-        fbp[a] = k.a * fn[a] + k.b * fe[a];
+    for (int a = 0; a < NQ; a++) fn[a] = Store<P>::dec(fin[a * np + g], fe[a], a);
+    if constexpr (P == P_FP64) {
+#pragma unroll
+        for (int a = 0; a < NQ; a++) fbp[a] = k.a * fn[a] + k.b * fe[a];
+    } else {
+        const float2 ka = pr2(k.a, k.a), kb = pr2(k.b, k.b);
+        fbp[0] = k.a * fn[0] + k.b * fe[0];
+#pragma unroll
+        for (int a = 1; a < NQ; a += 2) {
+            const float2 v = __ffma2_rn(ka, pr2(fn[a], fn[a + 1]), __fmul2_rn(kb, pr2(fe[a], fe[a + 1])));
+            fbp[a] = v.x;
+            fbp[a + 1] = v.y;
+        }
     }
 }
 
@@ -207,37 +254,90 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         const uint2 nbv = i == tid ? nb0 : *reinterpret_cast<const uint2 *>(m.sig_nb + (int64_t)(s0 + i) * MAXF);
         const uint16_t nb[MAXF] = {(uint16_t)(nbv.x & 0xFFFFu), (uint16_t)(nbv.x >> 16), (uint16_t)(nbv.y & 0xFFFFu),
                                    (uint16_t)(nbv.y >> 16)};
-        R bx[NQ], by[NQ];
+        if constexpr (P == P_FP64) {
+            R bx[NQ], by[NQ];
 #pragma unroll
-        for (int a = 0; a < NQ; a++) { bx[a] = R(0); by[a] = R(0); }
+            for (int a = 0; a < NQ; a++) { bx[a] = R(0); by[a] = R(0); }
 #pragma unroll
-        for (int sl = 0; sl < MAXF; sl++) {
-            const int kk = nb[sl];
-            if (kk == NO_LOCAL) continue;
-            const R dx = s_sd[(2 * sl) * SIG_MAX + i], dy = s_sd[(2 * sl + 1) * SIG_MAX + i];
-            if (kk < SYM_X) {
+            for (int sl = 0; sl < MAXF; sl++) {
+                const int kk = nb[sl];
+                if (kk == NO_LOCAL) continue;
+                const R dx = s_sd[(2 * sl) * SIG_MAX + i], dy = s_sd[(2 * sl + 1) * SIG_MAX + i];
+                if (kk < SYM_X) {
 #pragma unroll
-                for (int a = 0; a < NQ; a++) {
-                    const R d = s_fbp[a * LOC_MAX + kk] - s_fbp[a * LOC_MAX + i];
-                    bx[a] += dx * d;
-                    by[a] += dy * d;
-                }
-            } else {
-                // symmetry ghost: the cell's own fbar+ of the mirrored velocity (Sec. III)
-                const bool mx = kk == SYM_X;
+                    for (int a = 0; a < NQ; a++) {
+                        const R d = s_fbp[a * LOC_MAX + kk] - s_fbp[a * LOC_MAX + i];
+                        bx[a] += dx * d;
+                        by[a] += dy * d;
+                    }
+                } else {
+                    // symmetry ghost: the cell's own fbar+ of the mirrored velocity (Sec. III)
+                    const bool mx = kk == SYM_X;
 #pragma unroll
-                for (int a = 0; a < NQ; a++) {
-                    const R d = s_fbp[(mx ? MIRROR_X(a) : MIRROR_Y(a)) * LOC_MAX + i] - s_fbp[a * LOC_MAX + i];
-                    bx[a] += dx * d;
-                    by[a] += dy * d;
+                    for (int a = 0; a < NQ; a++) {
+                        const R d = s_fbp[(mx ? MIRROR_X(a) : MIRROR_Y(a)) * LOC_MAX + i] - s_fbp[a * LOC_MAX + i];
+                        bx[a] += dx * d;
+                        by[a] += dy * d;
+                    }
                 }
             }
-        }
-        const R axx = s_sa[i], axy = s_sa[SIG_MAX + i], ayy = s_sa[2 * SIG_MAX + i];
+            const R axx = s_sa[i], axy = s_sa[SIG_MAX + i], ayy = s_sa[2 * SIG_MAX + i];
 #pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            s_sig[(2 * a) * SIG_MAX + i] = axx * bx[a] + axy * by[a];
-            s_sig[(2 * a + 1) * SIG_MAX + i] = axy * bx[a] + ayy * by[a];
+            for (int a = 0; a < NQ; a++) {
+                s_sig[(2 * a) * SIG_MAX + i] = axx * bx[a] + axy * by[a];
+                s_sig[(2 * a + 1) * SIG_MAX + i] = axy * bx[a] + ayy * by[a];
+            }
+        } else {
+            // the same sums, paired; the differences f_k - f_j as FFMA2 with -1
+            float fi[NQ];
+#pragma unroll
+            for (int a = 0; a < NQ; a++) fi[a] = s_fbp[a * LOC_MAX + i];
+            const float2 m1 = pr2(-1.0f, -1.0f);
+            float bx0 = 0.0f, by0 = 0.0f;
+            float2 bx[4], by[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) { bx[q] = pr2(0.0f, 0.0f); by[q] = pr2(0.0f, 0.0f); }
+#pragma unroll
+            for (int sl = 0; sl < MAXF; sl++) {
+                const int kk = nb[sl];
+                if (kk == NO_LOCAL) continue;
+                const float dx = s_sd[(2 * sl) * SIG_MAX + i], dy = s_sd[(2 * sl + 1) * SIG_MAX + i];
+                float fk[NQ];
+                if (kk < SYM_X) {
+#pragma unroll
+                    for (int a = 0; a < NQ; a++) fk[a] = s_fbp[a * LOC_MAX + kk];
+                } else {
+                    // symmetry ghost: the cell's own fbar+ of the mirrored velocity (Sec. III)
+                    const bool mx = kk == SYM_X;
+#pragma unroll
+                    for (int a = 0; a < NQ; a++) fk[a] = fi[mx ? MIRROR_X(a) : MIRROR_Y(a)];
+                }
+                const float d0 = fk[0] - fi[0];
+                bx0 += dx * d0;
+                by0 += dy * d0;
+                const float2 dx2 = pr2(dx, dx), dy2 = pr2(dy, dy);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int a = 1 + 2 * q;
+                    const float2 d = __ffma2_rn(pr2(fi[a], fi[a + 1]), m1, pr2(fk[a], fk[a + 1]));
+                    bx[q] = __ffma2_rn(dx2, d, bx[q]);
+                    by[q] = __ffma2_rn(dy2, d, by[q]);
+                }
+            }
+            const float axx = s_sa[i], axy = s_sa[SIG_MAX + i], ayy = s_sa[2 * SIG_MAX + i];
+            s_sig[i] = axx * bx0 + axy * by0;
+            s_sig[SIG_MAX + i] = axy * bx0 + ayy * by0;
+            const float2 xx = pr2(axx, axx), xy = pr2(axy, axy), yy = pr2(ayy, ayy);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int a = 1 + 2 * q;
+                const float2 sx = __ffma2_rn(xx, bx[q], __fmul2_rn(xy, by[q]));
+                const float2 sy = __ffma2_rn(xy, bx[q], __fmul2_rn(yy, by[q]));
+                s_sig[(2 * a) * SIG_MAX + i] = sx.x;
+                s_sig[(2 * a + 1) * SIG_MAX + i] = sy.x;
+                s_sig[(2 * a + 2) * SIG_MAX + i] = sx.y;
+                s_sig[(2 * a + 3) * SIG_MAX + i] = sy.y;
+            }
         }
     }
     cp_async_wait_all();        // the face list has arrived
@@ -262,33 +362,58 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         if (!(B & LF_SECOND)) {
             const R rbx = G[4 * LF_MAX], rby = G[5 * LF_MAX];
             R fbar[NQ], w0 = R(0), w1 = R(0), w2 = R(0);
+            if constexpr (P == P_FP64) {
+#pragma unroll
+                for (int a = 0; a < NQ; a++) {
+                    const R s = xdot<R>(a, nx, ny);
+                    const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
+                    // the upwind side's reconstruction only (side B when the velocity leaves
+                    // it, else side A); a tangential velocity takes the mean of both sides
+                    const bool from_b = s < -k.tie;
+                    const int U = from_b ? B : A;
+                    const R rux = from_b ? rbx : rax, ruy = from_b ? rby : ray;
+                    R v = s_fbp[a * LOC_MAX + U] + (rux - ex) * s_sig[(2 * a) * SIG_MAX + U] +
+                          (ruy - ey) * s_sig[(2 * a + 1) * SIG_MAX + U];
+                    if (!from_b && !(s > k.tie)) {
+                        const R FB = s_fbp[a * LOC_MAX + B] + (rbx - ex) * s_sig[(2 * a) * SIG_MAX + B] +
+                                     (rby - ey) * s_sig[(2 * a + 1) * SIG_MAX + B];
+                        v = R(0.5) * (v + FB);
+                    }
+                    fbar[a] = v;
+                }
+            } else {
+                // the rest velocity is tangential to every face
+                fbar[0] = 0.5f * (rec1<0>(s_fbp, s_sig, A, rax, ray, k.dt) + rec1<0>(s_fbp, s_sig, B, rbx, rby, k.dt));
+                face_pair<1>(fbar, s_fbp, s_sig, A, B, nx, ny, rax, ray, rbx, rby, k.dt, k.tie);
+                face_pair<3>(fbar, s_fbp, s_sig, A, B, nx, ny, rax, ray, rbx, rby, k.dt, k.tie);
+                face_pair<5>(fbar, s_fbp, s_sig, A, B, nx, ny, rax, ray, rbx, rby, k.dt, k.tie);
+                face_pair<7>(fbar, s_fbp, s_sig, A, B, nx, ny, rax, ray, rbx, rby, k.dt, k.tie);
+            }
 #pragma unroll
             for (int a = 0; a < NQ; a++) {
-                const R s = xdot<R>(a, nx, ny);
-                const R ex = R(EX(a)) * k.dt, ey = R(EY(a)) * k.dt;
-                // the upwind side's reconstruction only (side B when the velocity leaves
-                // it, else side A); a tangential velocity takes the mean of both sides
-                const bool from_b = s < -k.tie;
-                const int U = from_b ? B : A;
-                const R rux = from_b ? rbx : rax, ruy = from_b ? rby : ray;
-                R v = s_fbp[a * LOC_MAX + U] + (rux - ex) * s_sig[(2 * a) * SIG_MAX + U] +
-                      (ruy - ey) * s_sig[(2 * a + 1) * SIG_MAX + U];
-                if (!from_b && !(s > k.tie)) {
-                    const R FB = s_fbp[a * LOC_MAX + B] + (rbx - ex) * s_sig[(2 * a) * SIG_MAX + B] +
-                                 (rby - ey) * s_sig[(2 * a + 1) * SIG_MAX + B];
-                    v = R(0.5) * (v + FB);
-                }
-                fbar[a] = v;
                 w0 += fbar[a];
                 if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
                 if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
             }
             R ux, uy, feqb[NQ];
             interface_feq<P>(w0, w1, w2, ux, uy, feqb);
+            if constexpr (P == P_FP64) {
 #pragma unroll
-            for (int a = 0; a < NQ; a++) {
-                const R s = xdot<R>(a, nx, ny);
-                s_flux[a * LF_MAX + lf] = s * ((fbar[a] + k.b * feqb[a]) * k.c);
+                for (int a = 0; a < NQ; a++) {
+                    const R s = xdot<R>(a, nx, ny);
+                    s_flux[a * LF_MAX + lf] = s * ((fbar[a] + k.b * feqb[a]) * k.c);
+                }
+            } else {
+                const float2 bb = pr2(k.b, k.b), cc = pr2(k.c, k.c);
+                s_flux[lf] = 0.0f * ((fbar[0] + k.b * feqb[0]) * k.c);
+#pragma unroll
+                for (int a = 1; a < NQ; a += 2) {
+                    const float2 sv = pr2(xdot<float>(a, nx, ny), xdot<float>(a + 1, nx, ny));
+                    const float2 t = __fmul2_rn(__ffma2_rn(bb, pr2(feqb[a], feqb[a + 1]), pr2(fbar[a], fbar[a + 1])), cc);
+                    const float2 fl = __fmul2_rn(sv, t);
+                    s_flux[a * LF_MAX + lf] = fl.x;
+                    s_flux[(a + 1) * LF_MAX + lf] = fl.y;
+                }
             }
         } else if (c.bc_kind[B & 0xFF] == BK_SYMMETRY) {
             // symmetry face of cell A: the far side is A's mirror ghost, whose
@@ -377,12 +502,26 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         const unsigned v = my_lf[sl];
         if (v == LF_NONE) continue;
         const int lf = (int)(v & (LF_SECOND - 1u));
-        if (v & LF_SECOND) {
+        if constexpr (P == P_FP64) {
+            if (v & LF_SECOND) {
 #pragma unroll
-            for (int a = 0; a < NQ; a++) F[a] -= s_flux[a * LF_MAX + lf];
+                for (int a = 0; a < NQ; a++) F[a] -= s_flux[a * LF_MAX + lf];
+            } else {
+#pragma unroll
+                for (int a = 0; a < NQ; a++) F[a] += s_flux[a * LF_MAX + lf];
+            }
         } else {
+            // F +- flux as FFMA2 with +-1 (exactly the sum or difference)
+            const float sg = (v & LF_SECOND) ? -1.0f : 1.0f;
+            const float2 sg2 = pr2(sg, sg);
+            F[0] = F[0] + sg * s_flux[lf];
 #pragma unroll
-            for (int a = 0; a < NQ; a++) F[a] += s_flux[a * LF_MAX + lf];
+            for (int a = 1; a < NQ; a += 2) {
+                const float2 t = __ffma2_rn(pr2(s_flux[a * LF_MAX + lf], s_flux[(a + 1) * LF_MAX + lf]), sg2,
+                                            pr2(F[a], F[a + 1]));
+                F[a] = t.x;
+                F[a + 1] = t.y;
+            }
         }
     }
 
@@ -411,12 +550,21 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         vel_of<R>(rho1, from_f64<R>(w1n) - d1, from_f64<R>(w2n) - d2, ux1, uy1);
         feq9fd<R>(drho1, rho1, ux1, uy1, feq1);
     }
+    if constexpr (P == P_FP64) {
 #pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        R fnew;
-        if constexpr (P == P_FP64) fnew = (fn[a] - dtv * F[a] + k.r * feq1[a]) / (R(1) + k.r);
-        else fnew = (fn[a] - dtv * F[a] + k.r * feq1[a]) * c.finv1r;
-        fout[a * np + g] = SP::enc(fnew, feq1[a], a);
+        for (int a = 0; a < NQ; a++)
+            fout[a * np + g] = SP::enc((fn[a] - dtv * F[a] + k.r * feq1[a]) / (R(1) + k.r), feq1[a], a);
+    } else {
+        // paired: (f - dt/V F + r feq) / (1 + r)
+        const float2 mdv = pr2(-dtv, -dtv), r2 = pr2(k.r, k.r), i2 = pr2(c.finv1r, c.finv1r);
+        fout[g] = SP::enc((fn[0] - dtv * F[0] + k.r * feq1[0]) * c.finv1r, feq1[0], 0);
+#pragma unroll
+        for (int a = 1; a < NQ; a += 2) {
+            const float2 t = __ffma2_rn(mdv, pr2(F[a], F[a + 1]), pr2(fn[a], fn[a + 1]));
+            const float2 u = __fmul2_rn(__ffma2_rn(r2, pr2(feq1[a], feq1[a + 1]), t), i2);
+            fout[a * np + g] = SP::enc(u.x, feq1[a], a);
+            fout[(a + 1) * np + g] = SP::enc(u.y, feq1[a + 1], a + 1);
+        }
     }
 }
 
