@@ -65,6 +65,19 @@ __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.w
 // phases below runs two velocities at a time, paired (1,2) (3,4) (5,6) (7,8).
 __device__ __forceinline__ float2 pr2(float a, float b) { return make_float2(a, b); }
 
+// (sum v, sum xi_x v, sum xi_y v) of nine per-velocity values, paired:
+// sum xi_x v = (v1 - v3) + (v5 - v7) - (v6 - v8), sum xi_y v = (v2 - v4) + (v5 - v7) + (v6 - v8)
+__device__ __forceinline__ void moments9(const float v[NQ], float &m0, float &m1, float &m2)
+{
+    const float2 m1x2 = pr2(-1.0f, -1.0f);
+    const float2 p1 = pr2(v[1], v[2]), p3 = pr2(v[3], v[4]), p5 = pr2(v[5], v[6]), p7 = pr2(v[7], v[8]);
+    const float2 sum = __fadd2_rn(__fadd2_rn(p1, p3), __fadd2_rn(p5, p7));
+    const float2 d13 = __ffma2_rn(p3, m1x2, p1), d57 = __ffma2_rn(p7, m1x2, p5);
+    m0 = v[0] + (sum.x + sum.y);
+    m1 = d13.x + (d57.x - d57.y);
+    m2 = d13.y + (d57.x + d57.y);
+}
+
 // FP32 reconstruction of velocity a at a face from staged cell U (Eqs. fbpsource, fbar):
 // fbar+_U + (r_U - xi_a dt) . sigma_U, with r_U = x_f - x_U = (rx, ry)
 template <int a>
@@ -389,11 +402,15 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
                 face_pair<5>(fbar, s_fbp, s_sig, A, B, nx, ny, rax, ray, rbx, rby, k.dt, k.tie);
                 face_pair<7>(fbar, s_fbp, s_sig, A, B, nx, ny, rax, ray, rbx, rby, k.dt, k.tie);
             }
+            if constexpr (P == P_FP64) {
 #pragma unroll
-            for (int a = 0; a < NQ; a++) {
-                w0 += fbar[a];
-                if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
-                if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+                for (int a = 0; a < NQ; a++) {
+                    w0 += fbar[a];
+                    if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
+                    if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
+                }
+            } else {
+                moments9(fbar, w0, w1, w2);
             }
             R ux, uy, feqb[NQ];
             interface_feq<P>(w0, w1, w2, ux, uy, feqb);
@@ -527,11 +544,15 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
 
     // ---- macroscopic flux (moments of F) -> W^{n+1} in FP64; cell update f^{n+1} (Eq. fn+1)
     R M0 = R(0), M1 = R(0), M2 = R(0);
+    if constexpr (P == P_FP64) {
 #pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        M0 += F[a];
-        if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
-        if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
+        for (int a = 0; a < NQ; a++) {
+            M0 += F[a];
+            if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
+            if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
+        }
+    } else {
+        moments9(F, M0, M1, M2);
     }
     const R d0 = dtv * M0, d1 = dtv * M1, d2 = dtv * M2;
     const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
