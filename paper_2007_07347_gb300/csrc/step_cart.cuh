@@ -291,13 +291,15 @@ __device__ __forceinline__ void cart_interior_face_f32x2(float flux[6], const fl
         fbar[3] = 0.5f * (t3.x + t3.y); fbar[4] = v01.y; fbar[5] = v23.x; fbar[6] = v23.y;
         fbar[7] = v45.x; fbar[8] = v45.y;
     }
-    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-#pragma unroll
-    for (int a = 0; a < NQ; a++) {
-        w0 += fbar[a];
-        if (EX(a) == 1) w1 += fbar[a]; else if (EX(a) == -1) w1 -= fbar[a];
-        if (EY(a) == 1) w2 += fbar[a]; else if (EY(a) == -1) w2 -= fbar[a];
-    }
+    // moments from the pairs: with d = (f5 - f7, f6 - f8), sum xi_x f = (f1 - f3) + d.x - d.y and
+    // sum xi_y f = (f2 - f4) + d.x + d.y
+    const float2 d57 = __ffma2_rn(v45, p2(-1.f, -1.f), v23), s57 = __fadd2_rn(v23, v45);
+    const float t13 = AX == 0 ? v01.x - v01.y : fbar[1] - fbar[3];
+    const float t24 = AX == 0 ? fbar[2] - fbar[4] : v01.x - v01.y;
+    const float tan2 = AX == 0 ? fbar[2] + fbar[4] : fbar[1] + fbar[3];
+    const float w0 = fbar[0] + (v01.x + v01.y) + tan2 + (s57.x + s57.y);
+    const float w1 = t13 + (d57.x - d57.y);
+    const float w2 = t24 + (d57.x + d57.y);
     // deviation form: w0 = sum of g = rho_b - 1
     float ux, uy, feqb[NQ];
     const float rb = 1.0f + w0;
@@ -663,11 +665,22 @@ __device__ __forceinline__ void cart_tile(const CartInst &m, int par, int tbx, i
 
         // ---- macroscopic flux -> W^{n+1} (FP64); cell update f^{n+1} (Eq. fn+1)
         R M0 = R(0), M1 = R(0), M2 = R(0);
+        if constexpr (P == P_FP64) {
 #pragma unroll
-        for (int a = 0; a < NQ; a++) {
-            M0 += F[a];
-            if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
-            if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
+            for (int a = 0; a < NQ; a++) {
+                M0 += F[a];
+                if (EX(a) == 1) M1 += F[a]; else if (EX(a) == -1) M1 -= F[a];
+                if (EY(a) == 1) M2 += F[a]; else if (EY(a) == -1) M2 -= F[a];
+            }
+        } else {
+            // paired: sum xi_x F = (F1 - F3) + (F5 - F7) - (F6 - F8), sum xi_y F = (F2 - F4) + (F5 - F7) + (F6 - F8)
+            const float2 m1 = p2(-1.f, -1.f);
+            const float2 q1 = p2(F[1], F[2]), q3 = p2(F[3], F[4]), q5 = p2(F[5], F[6]), q7 = p2(F[7], F[8]);
+            const float2 sm = __fadd2_rn(__fadd2_rn(q1, q3), __fadd2_rn(q5, q7));
+            const float2 d13 = __ffma2_rn(q3, m1, q1), d57 = __ffma2_rn(q7, m1, q5);
+            M0 = F[0] + (sm.x + sm.y);
+            M1 = d13.x + (d57.x - d57.y);
+            M2 = d13.y + (d57.x + d57.y);
         }
         const R d0 = k.dtV * M0, d1 = k.dtV * M1, d2 = k.dtV * M2;
         const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
