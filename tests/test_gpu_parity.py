@@ -128,6 +128,28 @@ def test_fp64_matches_oracle(name, kernel):
     assert np.abs(st.W[:, 1:]).max() > 0
 
 
+@pytest.mark.parametrize("name", list(FP64_CASES))
+def test_fp32_tiled_matches_oracle(name):
+    """FP32 compute (deviation form, per-velocity arithmetic paired in FFMA2/FMUL2/FADD2)
+    on the tiled kernel, for every case above: mirror ghosts in the gradient (symmetry
+    lines), three-face cells, periodic partners, outlets, far field and moving walls.
+    FP32 tolerances: relative L2 of u <= 1e-4, max |rho - rho_oracle| <= 1e-5."""
+    make, steps, init = FP64_CASES[name]
+    case = make()
+    rho = u = None
+    if init == "smooth":
+        rho, u = M.smooth_field(case, seed=3)
+    elif isinstance(init, int):
+        rho, u = _random_state(case, init)
+    elif case.u0 != (0.0, 0.0):
+        u = np.tile(case.u0, (case.mesh.n_cells, 1))
+    s, _, st = run_both(case, steps, "fp32", rho, u, kernel=KERNELS["tiled"])
+    rg, ug = s.macros()
+    assert rel_l2(ug, st.u) <= 1e-4
+    assert np.abs(rg - st.rho).max() <= 1e-5
+    assert np.abs(st.u).max() > 1e-4
+
+
 def test_kernel_selection():
     S = _S()
     assert S.Solver.from_case(M.cavity(64), "fp32").info()["kernel"] == S.KERNEL_CARTESIAN
