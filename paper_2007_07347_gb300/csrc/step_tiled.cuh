@@ -214,13 +214,18 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     // to shared memory while the previous step finishes: 16-byte pieces of each of the 11
     // planes (tile_s0 and the plane stride are multiples of 4 rows)
     {
+        // one 16-byte piece of each plane per thread: a tile has at most SIG_MAX / E
+        // pieces per plane, fewer than the threads, so only the first warps copy
         constexpr int E = 16 / (int)sizeof(R);
+        static_assert(SIG_MAX / E <= TILED_THREADS, "one piece per thread and plane");
         const int nch = (n_sig + E - 1) / E;
-        const R *sgd = static_cast<const R *>(m.sig_d), *sga = static_cast<const R *>(m.sig_ai);
-        for (int u = tid; u < (2 * MAXF + 3) * nch; u += TILED_THREADS) {
-            const int pl = u / nch, j = u - pl * nch;
-            const R *src = pl < 2 * MAXF ? sgd + pl * m.n_sig : sga + (pl - 2 * MAXF) * m.n_sig;
-            cp_async16(&s_sd[pl * SIG_MAX + j * E], src + s0 + j * E);
+        if (tid < nch) {
+            const R *sgd = static_cast<const R *>(m.sig_d) + s0 + tid * E;
+            const R *sga = static_cast<const R *>(m.sig_ai) + s0 + tid * E;
+#pragma unroll
+            for (int pl = 0; pl < 2 * MAXF; pl++) cp_async16(&s_sd[pl * SIG_MAX + tid * E], sgd + pl * m.n_sig);
+#pragma unroll
+            for (int pl = 0; pl < 3; pl++) cp_async16(&s_sa[pl * SIG_MAX + tid * E], sga + pl * m.n_sig);
         }
         cp_async_commit();
     }
