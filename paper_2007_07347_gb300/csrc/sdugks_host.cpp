@@ -887,7 +887,8 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     }
 
     const int64_t npad = (n + 31) / 32 * 32;
-    std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), tile_f0(nt + 1), halo;
+    std::vector<int32_t> tile_c0(nt + 1), tile_h0(nt + 1), tile_nh1(nt), tile_s0(nt + 1), tile_f0(nt + 1), tile_nlf(nt), halo;
+    int64_t lf_total = 0;            // local faces of all tiles without the padding
     std::vector<uint16_t> sig_nb, cell_lf((size_t)MAXF * npad, LF_NONE);
     std::vector<int32_t> sig_cell;   // internal cell of each gradient row
     std::vector<uint32_t> lf_ab;
@@ -991,6 +992,15 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                     cell_lf[(size_t)sl * npad + c0 + i] = (uint16_t)(flocal[f] | (second ? LF_SECOND : 0));
                 }
             }
+            // the next tile's faces start at a multiple of 4 (16-byte pieces of every
+            // face array); padding entries are never read as faces
+            tile_nlf[t] = (int32_t)lf_ab.size() - tile_f0[t];
+            lf_total += tile_nlf[t];
+            while (lf_ab.size() % 4 != 0) {
+                lf_ab.push_back(0u);
+                lf_bface.push_back(-1);
+                lf_geo.insert(lf_geo.end(), 6, 0.0);
+            }
             c0 += nint;
             hoff += (int32_t)(r1.size() + r2.size());
             soff += (nint + (int32_t)r1.size() + 3) / 4 * 4;
@@ -1027,9 +1037,10 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
                     return fail(SDUGKS_ERR_INVALID_MESH, "internal: face neighbour outside ring 1");
             }
         }
-        const int32_t nlf = tile_f0[t + 1] - tile_f0[t];
-        if (nlf < 1 || nlf > LF_MAX) return fail(SDUGKS_ERR_INVALID_MESH, "internal: tile %d face count out of range", t);
-        for (int32_t q = tile_f0[t]; q < tile_f0[t + 1]; q++) {
+        const int32_t nlf = tile_nlf[t];
+        if (nlf < 1 || nlf > LF_MAX || tile_f0[t] % 4 != 0 || tile_f0[t + 1] - tile_f0[t] != (nlf + 3) / 4 * 4)
+            return fail(SDUGKS_ERR_INVALID_MESH, "internal: tile %d face count out of range", t);
+        for (int32_t q = tile_f0[t]; q < tile_f0[t] + nlf; q++) {
             const uint32_t a = lf_ab[q] & 0xFFFFu, b = lf_ab[q] >> 16;
             if ((b & LF_SECOND) == 0) {
                 if (a >= (uint32_t)nsig || b >= (uint32_t)nsig || (a >= (uint32_t)nint && b >= (uint32_t)nint))
@@ -1083,6 +1094,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
         s->tm.halo = A.take<int32_t>(std::max<size_t>(1, halo.size()));
         s->tm.sig_nb = A.take<uint16_t>(sig_nb.size());
         s->tm.tile_f0 = A.take<int32_t>(nt + 1);
+        s->tm.tile_nlf = A.take<int32_t>(nt);
         s->tm.sig_d = A.take<char>((size_t)MAXF * 2 * sig_cell.size() * rs);
         s->tm.sig_ai = A.take<char>((size_t)3 * sig_cell.size() * rs);
         s->tm.cell_lf = A.take<uint16_t>(cell_lf.size());
@@ -1156,6 +1168,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     if (!halo.empty()) chk(up(s->tm.halo, halo.data(), halo.size() * 4), "upload halo");
     chk(up(s->tm.sig_nb, sig_nb.data(), sig_nb.size() * 2), "upload sig_nb");
     chk(up(s->tm.tile_f0, tile_f0.data(), (nt + 1) * 4), "upload tiles");
+    chk(up(s->tm.tile_nlf, tile_nlf.data(), nt * 4), "upload tiles");
     chk(up(s->tm.sig_d, gsd.data(), gsd.size()), "upload gradient offsets");
     chk(up(s->tm.sig_ai, gsa.data(), gsa.size()), "upload LLSR inverse");
     chk(up(s->tm.cell_lf, cell_lf.data(), cell_lf.size() * 2), "upload cell faces");
@@ -1174,7 +1187,7 @@ extern "C" int sdugks_solver_create(const sdugks_mesh *m, const sdugks_params *p
     // data (d vectors, inverse, neighbour indices) of interior and ring-1 cells, halo
     // ids and dt/V
     {
-        const double sigc = (double)sig_total / n, lfc = (double)lf_ab.size() / n;
+        const double sigc = (double)sig_total / n, lfc = (double)lf_total / n;
         s->mesh_bytes = MAXF * 2 + lfc * (4 + 6 * rs) + sigc * (MAXF * (2 + 2 * rs) + 3 * rs) +
                         (double)halo_total / n * 4 + rs;
     }

@@ -56,12 +56,14 @@ constexpr uint8_t SK_INTERIOR = 0xFF;  // face shared with another cell (periodi
 struct TiledMesh {
     int32_t n_tiles;
     int64_t n, npad;
-    int64_t n_lf;             // local faces of all tiles (stride of lf_geo)
+    int64_t n_lf;             // local faces of all tiles with the padding (stride of lf_geo, a multiple of 4)
     const int32_t *tile_c0;   // [n_tiles+1] interior cell range of each tile
     const int32_t *tile_h0;   // [n_tiles+1] range into halo
     const int32_t *tile_nh1;  // [n_tiles]   cells of ring 1 (first in the tile's halo)
     const int32_t *tile_s0;   // [n_tiles+1] range into sig_nb (each tile's rows padded to a multiple of 4)
-    const int32_t *tile_f0;   // [n_tiles+1] range of local faces
+    const int32_t *tile_f0;   // [n_tiles+1] first local face of each tile, a multiple of 4 (the
+                              //   ranges are padded so that each starts 16-byte aligned)
+    const int32_t *tile_nlf;  // [n_tiles] local faces of each tile (the rest of its range is padding)
     const int32_t *halo;      // internal ids of ring 1 then ring 2 of each tile
     int64_t n_sig;            // gradient rows of all tiles (stride of sig_d and sig_ai)
     const uint16_t *sig_nb;   // [n_sig][MAXF] tile-local index of the cell across each slot

@@ -207,7 +207,7 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     const int n_sig = n_int + m.tile_nh1[t];
     const int s0 = m.tile_s0[t];
     const int f0 = m.tile_f0[t];
-    const int n_lf = m.tile_f0[t + 1] - f0;
+    const int n_lf = m.tile_nlf[t];
     const int64_t np = m.npad, nlf = m.n_lf;
     const CoefR<R> k(c);
     // the gradient data of the tile's rows (read-only mesh data, needed in phase 2) travels
@@ -229,13 +229,17 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
         }
         cp_async_commit();
     }
-    // then the tile's face list (needed in phase 3)
+    // then the tile's face list (needed in phase 3), in 16-byte pieces: the tile's range
+    // starts at a multiple of 4 faces in every face array (the pieces past its last face
+    // read the range's padding)
     {
-        const R *gsrc = static_cast<const R *>(m.lf_geo);
-        for (int j = tid; j < n_lf; j += TILED_THREADS) {
-            cp_async<4>(&s_lfab[j], &m.lf_ab[f0 + j]);
+        constexpr int E = 16 / (int)sizeof(R);
+        static_assert(LF_MAX % 4 == 0 && LF_MAX / E <= TILED_THREADS, "one piece per thread and plane");
+        if (tid < (n_lf + 3) / 4) cp_async16(&s_lfab[tid * 4], &m.lf_ab[f0 + tid * 4]);
+        if (tid < (n_lf + E - 1) / E) {
+            const R *gsrc = static_cast<const R *>(m.lf_geo) + f0 + tid * E;
 #pragma unroll
-            for (int q = 0; q < 6; q++) cp_async<sizeof(R)>(&s_geo[q * LF_MAX + j], &gsrc[q * nlf + f0 + j]);
+            for (int q = 0; q < 6; q++) cp_async16(&s_geo[q * LF_MAX + tid * E], gsrc + q * nlf);
         }
         cp_async_commit();
     }
