@@ -54,8 +54,7 @@ __global__ void __launch_bounds__(RT) k_bresid_partial(const CartInst *__restric
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int2 it = items[w];
         const CartInst &m = insts[it.x];
-        const int ntx = (m.nx + BTX - 1) / BTX;
-        const int i = (it.y % ntx) * BTX + threadIdx.x % BTX, j = (it.y / ntx) * BTY + threadIdx.x / BTX;
+        const int i = (it.y & 0xFFFF) * BTX + threadIdx.x % BTX, j = (it.y >> 16) * BTY + threadIdx.x / BTX;
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         if (i < m.nx && j < m.ny) {
             const int64_t g = i + (int64_t)m.pitch * j, np = m.npad;

@@ -487,6 +487,8 @@ bool detect_cart(const sdugks_mesh &m, CartGrid &g)
     }
     const int64_t nx = mi + 1, ny = mj + 1;
     if (nx * ny != m.nc || nx < 2 || ny < 2) { g.why = "cells do not fill an nx x ny grid (nx, ny >= 2)"; return false; }
+    // the kernel's grid of blocks is two-dimensional: at most 65535 rows of blocks of >= 8 rows
+    if (ny > 8 * 65535) { g.why = "more than 524,280 rows of cells"; return false; }
     {
         std::vector<char> seen(m.nc, 0);
         for (int64_t c = 0; c < m.nc; c++) {
@@ -1781,7 +1783,10 @@ static int batch_upload_tables(sdugks_batch *b)
         CartInst ci = b->inst[q].ci;
         ci.item0 = (int32_t)items.size();
         ci.n_items = (int32_t)b->inst[q].ntiles;
-        for (int64_t t = 0; t < b->inst[q].ntiles; t++) items.push_back(make_int2((int)q, (int)t));
+        // item: (instance, block x | block y << 16)
+        const int ntx = (ci.nx + 15) / 16;
+        for (int64_t t = 0; t < b->inst[q].ntiles; t++)
+            items.push_back(make_int2((int)q, (int)(t % ntx) | ((int)(t / ntx) << 16)));
         b->inst[q].ci.item0 = ci.item0;
         b->inst[q].ci.n_items = ci.n_items;
         h.push_back(ci);
@@ -1857,6 +1862,8 @@ extern "C" int sdugks_batch_add(sdugks_batch *b, const sdugks_mesh *m, double ta
     CartGrid g;
     if (!detect_cart(*m, g)) return fail(SDUGKS_ERR_INVALID_ARG, "not a uniform Cartesian grid: %s", g.why.c_str());
     if ((int32_t)b->inst.size() >= b->max_inst) return fail(SDUGKS_ERR_FULL, "batch instance table full");
+    if ((g.nx + 15) / 16 > 0xFFFF || (g.ny + BATCH_TY - 1) / BATCH_TY > 0x7FFF)
+        return fail(SDUGKS_ERR_INVALID_ARG, "grid of %d x %d cells too large for a batch instance", g.nx, g.ny);
     const int32_t pitch = (g.nx + 31) / 32 * 32;
     const int64_t npad = cart_npad(pitch, g.ny);
     const size_t bytes = inst_bytes(b->prec, npad);

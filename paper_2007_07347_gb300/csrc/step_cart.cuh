@@ -773,8 +773,7 @@ k_step_cart(const CartInst m, int par, const __grid_constant__ CUtensorMap tf, c
     static_assert(!DIAG || MODE == CART_GENERAL, "diagnostic steps run every block on the general variant");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     step_dependency_wait();
-    const int ntx = (m.nx + TX - 1) / TX;
-    const int tbx = blockIdx.x % ntx, tby = blockIdx.x / ntx;
+    const int tbx = blockIdx.x, tby = blockIdx.y;     // a two-dimensional grid of blocks
     if (MODE != CART_GENERAL && cart_block_interior<TX, TY>(m, tbx, tby)) {
         if constexpr (MODE == CART_SPECIALISED_TMA) {
             using B = CartTmaBox<P, TX, TY>;
@@ -822,7 +821,7 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
         for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst)[q] = src[q];
         __syncthreads();
         const CartInst &m = s_inst;
-        const int ntx = (m.nx + TX - 1) / TX, bx = it.y % ntx, by = it.y / ntx;
+        const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
         if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
         else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
         __syncthreads();                                 // shared memory is reused by the next item
@@ -849,7 +848,7 @@ template <int P, int TX, int TY>
 cudaError_t launch_cart_p(const CartInst &m, const CartTma *tma, bool general, int par, cudaStream_t st)
 {
     const int ntx = (m.nx + TX - 1) / TX, nty = (m.ny + TY - 1) / TY;
-    const dim3 grid(ntx * nty), block(cart_threads<TX, TY>());
+    const dim3 grid(ntx, nty), block(cart_threads<TX, TY>());
     static const CUtensorMap none0{};
     if (m.force || m.bface)
         return launch_step_kernel(k_step_cart<P, TX, TY, CART_GENERAL, true>, grid, block,
