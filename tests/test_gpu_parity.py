@@ -236,6 +236,25 @@ def test_tile_size_and_graphs_do_not_change_results():
             np.testing.assert_array_equal(a, b)
 
 
+def test_remainder_graphs_replay_the_same_steps():
+    """A call of n steps runs full graphs, then the remainder as graphs of 2^k steps and
+    at most one single launch (203 = 12 x 16 + 8 + 2 + 1): bit-identical to single
+    launches on the Cartesian kernel in FP32, and across several calls."""
+    S = _S()
+    case = M.cavity(48, Re=400.0)
+    a = S.Solver.from_case(case, "fp32", graph_steps=-1).init()
+    b = S.Solver.from_case(case, "fp32", graph_steps=16).init()
+    a.step(203)
+    b.step(203)
+    for x, y in zip(a.get_state(), b.get_state()):
+        np.testing.assert_array_equal(x, y)
+    a.step(97)
+    b.step(40)
+    b.step(57)
+    for x, y in zip(a.get_state(), b.get_state()):
+        np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16dev"])
 def test_checkpoint_resume_is_bitwise(precision):
     """A run resumed from a checkpoint equals the uninterrupted run bit for bit: through
