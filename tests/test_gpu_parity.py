@@ -150,6 +150,26 @@ def test_fp32_tiled_matches_oracle(name):
     assert np.abs(st.u).max() > 1e-4
 
 
+@pytest.mark.parametrize("name", [n for n in FP64_CASES if n.startswith(("symmetry_channel", "symmetry_box",
+                                                                          "couette", "cavity", "mixed"))])
+def test_fp32_cartesian_matches_oracle(name):
+    """FP32 compute on the Cartesian kernel (one code path on these one-wave grids) for
+    the uniform-grid cases above: symmetry sides staged as mirror ghosts, outlet, far
+    field, moving wall and plain walls.  FP32 tolerances as above."""
+    S = _S()
+    make, steps, init = FP64_CASES[name]
+    case = make()
+    rho = u = None
+    if isinstance(init, int):
+        rho, u = _random_state(case, init)
+    s, _, st = run_both(case, steps, "fp32", rho, u)
+    assert s.info()["kernel"] == S.KERNEL_CARTESIAN
+    rg, ug = s.macros()
+    assert rel_l2(ug, st.u) <= 1e-4
+    assert np.abs(rg - st.rho).max() <= 1e-5
+    assert np.abs(st.u).max() > 1e-4
+
+
 def test_kernel_selection():
     S = _S()
     assert S.Solver.from_case(M.cavity(64), "fp32").info()["kernel"] == S.KERNEL_CARTESIAN
