@@ -86,6 +86,28 @@ template <class R> __device__ __forceinline__ void set_sp(R *sp, const MaxP &p)
     sp[3] = sizeof(R) == 4 ? R(p.inv2RT * 1.4426950408889634) : R(p.inv2RT);
 }
 
+// The parameters of the state with moments (rho, rho u, rho E), in the compute
+// precision.  FP64: by max_params.  FP32: the moments rounded to FP32 and the same
+// formulas in FP32, so that the thread that forms them does not hold its block for the
+// FP64 divisions of this GPU's narrow FP64 unit (the parameters were rounded to FP32
+// before either way).
+template <class R> __device__ __forceinline__ void state_sp(R *sp, double rho, double mx, double my, double rE);
+template <> __device__ __forceinline__ void state_sp<double>(double *sp, double rho, double mx, double my, double rE)
+{
+    set_sp<double>(sp, max_params(rho, mx, my, rE));
+}
+template <> __device__ __forceinline__ void state_sp<float>(float *sp, double rho_d, double mx, double my, double rE)
+{
+    const float rho = (float)rho_d, ir = 1.0f / rho;
+    const float ux = (float)mx * ir, uy = (float)my * ir;
+    const float RT = (float)rE * ir - 0.5f * (ux * ux + uy * uy);
+    const float iRT = 1.0f / RT;
+    sp[0] = rho * iRT * (float)(0.5 / 3.14159265358979323846);
+    sp[1] = ux;
+    sp[2] = uy;
+    sp[3] = 0.5f * iRT * 1.4426950408889634f;
+}
+
 template <class R>
 __device__ __forceinline__ R maxwell(const R *sp, R x, R y, R w)
 {
@@ -287,7 +309,7 @@ __global__ void __launch_bounds__(FBP_THREADS) k_dvm_fbp(const DvmMesh m, const 
     step_dependency_wait();
     const int64_t c = blockIdx.x;
     const int Q = (int)m.Q;
-    if (threadIdx.x == 0) set_sp<R>(sp, max_params(W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]));
+    if (threadIdx.x == 0) state_sp<R>(sp, W[4 * c], W[4 * c + 1], W[4 * c + 2], W[4 * c + 3]);
     __syncthreads();
     const DvmR<R> k(cf);
     const R w = R(m.w_node);
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 4 : 2) k_dvm_fa
         R part[4] = {p0, p1, p2, p3};
         double Wb[4];
         block_sum<4, R>(part, red, Wb);
-        if (threadIdx.x == 0) set_sp<R>(sp, max_params(Wb[0], Wb[1], Wb[2], Wb[3]));
+        if (threadIdx.x == 0) state_sp<R>(sp, Wb[0], Wb[1], Wb[2], Wb[3]);
         __syncthreads();
         VelWalk vw2(threadIdx.x * V, FACE_THREADS * V, m.nv);
         for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS, vw2.next()) {
@@ -448,8 +470,11 @@ __global__ void __launch_bounds__(FACE_THREADS, sizeof(R) == 4 ? 4 : 2) k_dvm_fa
         R part[3] = {so, go, gin};
         double tot[3];
         block_sum<3, R>(part, red, tot);
-        const double rho_w = -double(k.c) * tot[0] / (double(k.c) * double(k.b) * tot[1] + tot[2]);
-        const R rw = R(rho_w);
+        // every thread forms rho_w: in FP32 compute by an FP32 division (FP64 divisions
+        // are slow on this GPU), from the FP64 sums rounded to FP32
+        R rw;
+        if constexpr (sizeof(R) == 8) rw = -k.c * tot[0] / (k.c * k.b * tot[1] + tot[2]);
+        else rw = -k.c * float(tot[0]) / (k.c * k.b * float(tot[1]) + float(tot[2]));
         VelWalk vw2(threadIdx.x * V, FACE_THREADS * V, m.nv);
         for (int gi = threadIdx.x; gi < Q / V; gi += FACE_THREADS, vw2.next()) {
             const int q = gi * V;
@@ -544,7 +569,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_dvm_cell(const DvmMesh m, cons
             Wn[d] = W[4 * c + d] - dtv * M[d];
             W[4 * c + d] = Wn[d];
         }
-        set_sp<R>(sp, max_params(Wn[0], Wn[1], Wn[2], Wn[3]));
+        state_sp<R>(sp, Wn[0], Wn[1], Wn[2], Wn[3]);
     }
     __syncthreads();
     const R rdtv = R(dtv);
