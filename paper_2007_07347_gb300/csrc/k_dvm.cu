@@ -116,8 +116,9 @@ __device__ __forceinline__ R maxwell(const R *sp, R x, R y, R w)
 }
 
 // Fixed-order block sum of NV per-thread values: warp sums by shuffles in the
-// compute precision, the per-warp results combined in FP64 by one thread; the result
-// in out[] on every thread.  Uses scratch[32 * NV] shared doubles.
+// compute precision, the per-warp results of value k combined in FP64 by thread k (in
+// warp order); the result in out[] on every thread.  Uses scratch[32 * NV] shared
+// doubles.
 template <int NV, class R>
 __device__ __forceinline__ void block_sum(R v[NV], double *scratch, double out[NV])
 {
@@ -130,13 +131,11 @@ __device__ __forceinline__ void block_sum(R v[NV], double *scratch, double out[N
         if (lane == 0) scratch[k * 32 + warp] = double(x);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            double t = 0.0;
-            for (int w = 0; w < nw; w++) t += scratch[k * 32 + w];
-            scratch[k * 32] = t;
-        }
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double t = 0.0;
+        for (int w = 0; w < nw; w++) t += scratch[k * 32 + w];
+        scratch[k * 32] = t;
     }
     __syncthreads();
 #pragma unroll
