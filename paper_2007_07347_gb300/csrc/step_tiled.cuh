@@ -565,9 +565,13 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
     }
     const R d0 = dtv * M0, d1 = dtv * M1, d2 = dtv * M2;
     const double W0 = w0n - to_f64<R>(d0), W1 = w1n - to_f64<R>(d1), W2 = w2n - to_f64<R>(d2);
-    Wout[g] = W0;
-    Wout[np + g] = W1;
-    Wout[2 * np + g] = W2;
+    // FP32 compute: the FP64 sums are stored last, after the f update, which does not wait
+    // for them (the FP64 unit of this GPU is narrow)
+    if constexpr (P == P_FP64) {
+        Wout[g] = W0;
+        Wout[np + g] = W1;
+        Wout[2 * np + g] = W2;
+    }
     R rho1, ux1, uy1, feq1[NQ];
     if constexpr (P == P_FP64) {
         R drho1;
@@ -595,6 +599,9 @@ k_step_tiled(const TiledMesh m, const Coefs c, const typename Store<P>::T *__res
             fout[a * np + g] = SP::enc(u.x, feq1[a], a);
             fout[(a + 1) * np + g] = SP::enc(u.y, feq1[a + 1], a + 1);
         }
+        Wout[g] = W0;
+        Wout[np + g] = W1;
+        Wout[2 * np + g] = W2;
     }
 }
 
