@@ -816,22 +816,29 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step_dependency_wait();
-    // the item's instance record is copied to shared memory once per item, so that the
-    // block routine reads its fields there instead of from global memory
+    // each item's instance record is copied to shared memory, so that the block routine
+    // reads its fields there instead of from global memory: two buffers, the next item's
+    // record copied while the current item ends, so that one barrier between items both
+    // publishes it and separates the items' use of the staging memory
     static_assert(sizeof(CartInst) % 4 == 0, "CartInst copies in 4-byte words");
-    __shared__ __align__(16) CartInst s_inst;
+    __shared__ __align__(16) CartInst s_inst[2];
     constexpr int NW = (int)(sizeof(CartInst) / 4);
     const int n = *n_items;
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    auto fetch = [&](int w, int b) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + items[w].x);
+        for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst[b])[q] = src[q];
+    };
+    if ((int)blockIdx.x < n) fetch(blockIdx.x, 0);
+    __syncthreads();
+    int b = 0;
+    for (int w = blockIdx.x; w < n; w += gridDim.x, b ^= 1) {
         const int2 it = items[w];
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + it.x);
-        for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst)[q] = src[q];
-        __syncthreads();
-        const CartInst &m = s_inst;
+        const CartInst &m = s_inst[b];
         const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
         if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
         else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
-        __syncthreads();                                 // shared memory is reused by the next item
+        if (w + (int)gridDim.x < n) fetch(w + gridDim.x, b ^ 1);
+        __syncthreads();
     }
 }
 

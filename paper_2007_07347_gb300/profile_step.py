@@ -3,8 +3,9 @@
     python -m paper_2007_07347_gb300.profile_step CASE [PRECISION] [STEPS] [TILE] [STAGING]
 
 CASE is one of cavity128, cavity256, cavity1024, cylinder (512 x 256 O-mesh),
-microcavity (the rarefied solver: 40 x 40 cells, 100 x 100 velocities, Kn 1), or batch
-(the 256 cavities of the batched configuration, N ~ logU[32, 512], seed 1).  Used
+microcavity (the rarefied solver: 40 x 40 cells, 100 x 100 velocities, Kn 1), batch
+(the 256 cavities of the batched configuration, N ~ logU[32, 512], seed 1) or batchK
+(the first K of those 256, e.g. batch32 for a capture that holds less device memory).  Used
 under ncu with ``-k regex:k_step`` (``regex:k_dvm`` for the rarefied kernels) to
 capture single step launches.  STAGING (Cartesian kernel): loads (default) or tma.
 """
@@ -31,8 +32,9 @@ def main(argv):
     tile = int(argv[4]) if len(argv) > 4 else 0
     staging = argv[5] if len(argv) > 5 else "loads"
     torch.cuda.set_device(0)
-    if name == "batch":
-        cases = [M.cavity(n, Re=re) for n, re in M.batch_cavities(256, seed=1)]
+    if name.startswith("batch"):
+        count = int(name[5:]) if len(name) > 5 else 256
+        cases = [M.cavity(n, Re=re) for n, re in M.batch_cavities(256, seed=1)[:count]]
         meshes = [S.Mesh(c.mesh, c.bcs) for c in cases]
         probe = S.Batch(1 << 20, prec, 4)
         need = sum(probe.footprint(m) for m in meshes)
