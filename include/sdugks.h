@@ -327,10 +327,12 @@ typedef struct sdugks_batch_status {
     int64_t pool_bytes;      /* device pool size                                    */
     int64_t pool_used;       /* bytes held by active instances                      */
     int64_t steps;           /* batch steps since creation                          */
-    int32_t grid;            /* CTAs per step launch                                */
+    int32_t grid;            /* CTAs per step launch (the item count if per_item)   */
     int32_t ctas_per_sm;     /* resident CTAs per SM of the batched kernel          */
     int32_t graph_steps;     /* steps per captured graph                            */
     int32_t precision;
+    int32_t per_item;        /* 1: one CTA per work item; 0: a fixed grid walks the
+                                work list                                           */
 } sdugks_batch_status;
 
 /* Create a batch with a device pool of pool_bytes and room for max_instances
@@ -367,9 +369,11 @@ int sdugks_batch_residual(sdugks_batch *b, int64_t *ids, double *eps, double *ma
 /* rho[nx*ny], u[nx*ny][2] of one instance (host; synchronises). */
 int sdugks_batch_get_macros(sdugks_batch *b, int64_t id, double *rho, double *u);
 
-/* Time `steps` steps at each candidate grid (1, 2 and 4 times the resident CTAs
- * per step) and keep the fastest (see sdugks_batch_status.grid).  Call with instances
- * admitted. */
+/* Time `steps` steps of each candidate launch form and keep the fastest: one CTA per
+ * work item (the default), or a fixed grid of 1, 2 or 4 times the resident CTAs that
+ * walks the work list (see sdugks_batch_status.per_item and .grid).  Call with
+ * instances admitted.  With one CTA per item, the step graph is captured again after
+ * the item count changes (instances admitted or removed). */
 int sdugks_batch_autotune(sdugks_batch *b, int64_t steps);
 
 int sdugks_batch_info(const sdugks_batch *b, sdugks_batch_status *out);

@@ -11,16 +11,31 @@ constexpr int BTX = 16, BTY = BATCH_TY;
 constexpr int RT = BTX * BTY;              // residual block = one block of cells
 
 template <int P> cudaError_t prep_p() {
-    return cudaFuncSetAttribute(k_step_batch<P, BTX, BTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)cart_smem<P, BTX, BTY>());
+    cudaError_t e = cudaFuncSetAttribute(k_step_batch<P, BTX, BTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cart_smem<P, BTX, BTY>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step_batch<P, BTX, BTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cart_smem<P, BTX, BTY>());
+    return e;
 }
 
 template <int P> int occ_p() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<P, BTX, BTY>, cart_threads<BTX, BTY>(),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<P, BTX, BTY, false>, cart_threads<BTX, BTY>(),
                                                       cart_smem<P, BTX, BTY>()) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+template <int P>
+cudaError_t launch_batch_p(const CartInst *insts, const int2 *items, const int *n_items, int grid, bool per_item,
+                           int parity, cudaStream_t st)
+{
+    if (per_item)
+        return launch_step_kernel(k_step_batch<P, BTX, BTY, true>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
+                                  cart_smem<P, BTX, BTY>(), st, insts, items, n_items, parity);
+    return launch_step_kernel(k_step_batch<P, BTX, BTY, false>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
+                              cart_smem<P, BTX, BTY>(), st, insts, items, n_items, parity);
 }
 
 __device__ void bsum4(double v[4], double *out)
@@ -144,16 +159,11 @@ int batch_ctas_per_sm(int prec)
 }
 
 cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,
-                              int parity, cudaStream_t st)
+                              bool per_item, int parity, cudaStream_t st)
 {
-    if (prec == P_BF16DEV)
-        return launch_step_kernel(k_step_batch<P_BF16DEV, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
-                                  cart_smem<P_BF16DEV, BTX, BTY>(), st, insts, items, n_items, parity);
-    if (prec == P_FP16DEV)
-        return launch_step_kernel(k_step_batch<P_FP16DEV, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
-                                  cart_smem<P_FP16DEV, BTX, BTY>(), st, insts, items, n_items, parity);
-    return launch_step_kernel(k_step_batch<P_FP32, BTX, BTY>, dim3(grid), dim3(cart_threads<BTX, BTY>()),
-                              cart_smem<P_FP32, BTX, BTY>(), st, insts, items, n_items, parity);
+    if (prec == P_BF16DEV) return launch_batch_p<P_BF16DEV>(insts, items, n_items, grid, per_item, parity, st);
+    if (prec == P_FP16DEV) return launch_batch_p<P_FP16DEV>(insts, items, n_items, grid, per_item, parity, st);
+    return launch_batch_p<P_FP32>(insts, items, n_items, grid, per_item, parity, st);
 }
 
 cudaError_t launch_batch_residual(const CartInst *insts, int n_inst, const int2 *items, const int *n_items, int grid,

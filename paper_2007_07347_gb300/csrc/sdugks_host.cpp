@@ -1791,10 +1791,18 @@ struct sdugks_batch {
     double *d_stage = nullptr;          // [max_cells_one][3] staging for add/get
     int64_t stage_cells = 0;
     int64_t max_items = 0, n_items = 0;
-    int grid = 0, ctas_per_sm = 1, n_sm = 1;
+    int grid = 0, ctas_per_sm = 1, n_sm = 1;   // grid: CTAs of the walking form
+    bool per_item = true;                       // one CTA per work item (the grid follows the list)
     int graph_steps = 64;
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_items = -1;                   // the item count the graph's per-item grids were sized for
 };
+
+// CTAs of a step launch: one per work item (at least one), or the walking form's grid
+static int batch_launch_grid(const sdugks_batch *b)
+{
+    return b->per_item ? (int)(b->n_items > 0 ? b->n_items : 1) : b->grid;
+}
 
 static int batch_upload_tables(sdugks_batch *b)
 {
@@ -1816,6 +1824,11 @@ static int batch_upload_tables(sdugks_batch *b)
     if ((int64_t)items.size() > b->max_items) return fail(SDUGKS_ERR_FULL, "batch work list full");
     b->n_items = (int64_t)items.size();
     const int ni = (int)b->n_items;
+    // a graph of per-item launches has grids of the old item count
+    if (b->graph && b->per_item && b->graph_items != b->n_items) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(b->d_inst, h.data(), h.size() * sizeof(CartInst), cudaMemcpyHostToDevice, b->stream));
     if (!items.empty()) CUDA_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
     CUDA_TRY(cudaMemcpyAsync(b->d_nitems, &ni, sizeof(int), cudaMemcpyHostToDevice, b->stream));
@@ -1969,14 +1982,16 @@ static int batch_ensure_graph(sdugks_batch *b)
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
+    const int grid = batch_launch_grid(b);
     for (int k = 0; k < b->graph_steps && e == cudaSuccess; k++)
-        e = launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, b->grid, k & 1, b->cap_stream);
+        e = launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, b->per_item, k & 1, b->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
     CUDA_TRY(e);
     CUDA_TRY(e2);
     e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     CUDA_TRY(e);
+    b->graph_items = b->n_items;
     return SDUGKS_OK;
 }
 
@@ -1988,7 +2003,8 @@ extern "C" int sdugks_batch_step(sdugks_batch *b, int64_t n)
     int64_t left = n;
     if (left >= 2 * b->graph_steps) {
         if (b->cur != 0) {
-            CUDA_TRY(launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, b->grid, b->cur, b->stream));
+            CUDA_TRY(launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, batch_launch_grid(b),
+                                       b->per_item, b->cur, b->stream));
             b->cur ^= 1; b->steps++; left--;
         }
         int rc = batch_ensure_graph(b);
@@ -1999,7 +2015,8 @@ extern "C" int sdugks_batch_step(sdugks_batch *b, int64_t n)
         }
     }
     while (left > 0) {
-        CUDA_TRY(launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, b->grid, b->cur, b->stream));
+        CUDA_TRY(launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, batch_launch_grid(b), b->per_item,
+                                   b->cur, b->stream));
         b->cur ^= 1; b->steps++; left--;
     }
     return SDUGKS_OK;
@@ -2057,28 +2074,36 @@ extern "C" int sdugks_batch_autotune(sdugks_batch *b, int64_t steps)
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    // candidates: one CTA per item (mult 0), then the walking form at 1, 2 and 4 times
+    // the resident CTAs
     const int base = b->n_sm * b->ctas_per_sm;
-    int best = base;
+    const int item_grid = (int)(b->n_items > 0 ? b->n_items : 1);
+    int best = 0;
     float best_ms = 1e30f;
-    for (int mult : {1, 2, 4}) {
-        const int grid = base * mult;
+    for (int mult : {0, 1, 2, 4}) {
+        const bool per_item = mult == 0;
+        const int grid = per_item ? item_grid : base * mult;
         // steps in pairs so that the buffer parity is unchanged
-        for (int64_t k = 0; k < 2; k++) launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, (b->cur + k) & 1, b->stream);
+        for (int64_t k = 0; k < 2; k++)
+            launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, per_item, (b->cur + k) & 1, b->stream);
         cudaEventRecord(e0, b->stream);
         for (int64_t k = 0; k < 2 * steps; k++)
-            launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, (b->cur + k) & 1, b->stream);
+            launch_step_batch(b->prec, b->d_inst, b->d_items, b->d_nitems, grid, per_item, (b->cur + k) & 1, b->stream);
         cudaEventRecord(e1, b->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         float ms = 0;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return fail(SDUGKS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e)); }
         b->steps += 2 + 2 * steps;
-        if (ms < best_ms) { best_ms = ms; best = grid; }
+        if (ms < best_ms) { best_ms = ms; best = mult; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best != b->grid) {
-        b->grid = best;
+    const bool per_item = best == 0;
+    const int grid = per_item ? b->grid : base * best;
+    if (per_item != b->per_item || grid != b->grid) {
+        b->per_item = per_item;
+        b->grid = grid;
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     }
     return SDUGKS_OK;
@@ -2094,10 +2119,11 @@ extern "C" int sdugks_batch_info(const sdugks_batch *b, sdugks_batch_status *o)
     o->pool_bytes = (int64_t)b->alloc.cap();
     o->pool_used = (int64_t)b->alloc.used();
     o->steps = b->steps;
-    o->grid = b->grid;
+    o->grid = batch_launch_grid(b);
     o->ctas_per_sm = b->ctas_per_sm;
     o->graph_steps = b->graph_steps;
     o->precision = b->prec;
+    o->per_item = b->per_item ? 1 : 0;
     return SDUGKS_OK;
 }
 

@@ -144,10 +144,11 @@ cudaError_t make_cart_tma(int prec, int shape, const CartInst &m, CartTma &out);
 cudaError_t launch_step_cart(int prec, int shape, const CartInst &m, const CartTma *tma, bool general, int parity,
                              cudaStream_t st);
 int cart_shape_occupancy(int prec, int shape, bool tma);   // resident CTAs per SM
-// batched: every (instance, tile) item of the list, grid-stride over a fixed grid
+// batched: every (instance, tile) item of the list, one per CTA (per_item: grid >= the
+// item count) or grid-stride over a fixed grid
 cudaError_t prepare_batch(int prec);
 cudaError_t launch_step_batch(int prec, const CartInst *insts, const int2 *items, const int *n_items, int grid,
-                              int parity, cudaStream_t st);
+                              bool per_item, int parity, cudaStream_t st);
 int batch_ctas_per_sm(int prec);
 // batched residual: partial [max_items][4] per tile, out [n_inst][4] = (num, den, mass, non-finite)
 cudaError_t launch_batch_residual(const CartInst *insts, int n_inst, const int2 *items, const int *n_items, int grid,

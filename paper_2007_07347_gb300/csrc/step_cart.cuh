@@ -807,15 +807,27 @@ template <int P, int TX, int TY, int MODE, bool DIAG = false> constexpr size_t c
     return MODE == CART_SPECIALISED_TMA ? CartTmaBox<P, TX, TY>::SMEM : cart_smem<P, TX, TY>();
 }
 
-// Batched: a fixed grid walks the (instance, block) work list; the item count is in
-// device memory so that a captured graph stays valid while instances come and go.
-template <int P, int TX, int TY>
+// Batched: the (instance, block) work list, one item per CTA (PER_ITEM: the grid has a
+// CTA for every item, and CTAs past the item count in device memory return) or walked
+// by a fixed grid (a captured graph then stays valid while instances come and go).
+// One item per CTA keeps the block routine free of the walk's loop-carried state: the
+// walking form spills registers at four CTAs per SM, the per-item form does not.
+template <int P, int TX, int TY, bool PER_ITEM>
 __global__ void __launch_bounds__(cart_threads<TX, TY>(), cart_threads<TX, TY>() <= 320 ? 4 : 2)
 k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items, const int *__restrict__ n_items,
              int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step_dependency_wait();
+    if constexpr (PER_ITEM) {
+        if ((int)blockIdx.x >= *n_items) return;
+        const int2 it = items[blockIdx.x];
+        const CartInst &m = insts[it.x];
+        const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
+        if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
+        else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
+        return;
+    }
     // each item's instance record is copied to shared memory, so that the block routine
     // reads its fields there instead of from global memory: two buffers, the next item's
     // record copied while the current item ends, so that one barrier between items both

@@ -330,7 +330,7 @@ def autotune_clear():
 class BatchStatus(C.Structure):
     _fields_ = [("instances", C.c_int64), ("cells", C.c_int64), ("items", C.c_int64), ("pool_bytes", C.c_int64),
                 ("pool_used", C.c_int64), ("steps", C.c_int64), ("grid", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("graph_steps", C.c_int32), ("precision", C.c_int32)]
+                ("graph_steps", C.c_int32), ("precision", C.c_int32), ("per_item", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -72,6 +72,34 @@ def test_result_same_alone_and_in_the_mix_and_late_admission():
     assert res[late][2] == 201 and res[others[0]][2] == 238
 
 
+def test_step_graph_follows_the_work_list():
+    """With one CTA per work item, the step graph's grids have the item count it was
+    captured with; an admission or a removal captures it again.  An instance admitted
+    after the capture (its items lie past the old grid) and one whose items move in the
+    list after a removal give bit for bit the results they give alone."""
+    S = _S()
+    case, extra = M.cavity(48, Re=400.0), MIX[1]()
+    alone = S.Batch(64 << 20, "fp32", max_instances=4)
+    a = alone.add_case(case)
+    alone.step(3 * 130)
+    alone_x = S.Batch(64 << 20, "fp32", max_instances=4)
+    ax = alone_x.add_case(extra)
+    alone_x.step(130)
+    mix = S.Batch(256 << 20, "fp32", max_instances=8)
+    first = mix.add_case(MIX[0]())
+    mine = mix.add_case(case)
+    mix.step(130)                                 # a graph of 64 steps for these items
+    assert mix.info()["per_item"] == 1
+    late = mix.add_case(extra)                    # more items than the graph's grids
+    mix.step(130)
+    np.testing.assert_array_equal(alone_x.macros(ax)[1], mix.macros(late)[1])
+    mix.remove(first)                             # the others' items move forward
+    mix.remove(late)
+    mix.step(130)
+    np.testing.assert_array_equal(alone.macros(a)[1], mix.macros(mine)[1])
+    assert mix.info()["items"] == alone.info()["items"]
+
+
 def test_batch_against_oracle():
     S = _S()
     case = M.cavity(32, Re=100.0)
