@@ -818,39 +818,48 @@ k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items,
              int par)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_dependency_wait();
+    static_assert(sizeof(CartInst) % 4 == 0, "CartInst copies in 4-byte words");
+    constexpr int NW = (int)(sizeof(CartInst) / 4);
     if constexpr (PER_ITEM) {
+        // The work list and the instance records are written by the host only (stream
+        // ordered before the launch), so the item and its record are read before the
+        // wait on the previous step: the record goes to shared memory while that step
+        // ends, and the block routine reads its fields there.
+        __shared__ __align__(16) CartInst s_one;
         if ((int)blockIdx.x >= *n_items) return;
         const int2 it = items[blockIdx.x];
-        const CartInst &m = insts[it.x];
-        const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
-        if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
-        else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
-        return;
-    }
-    // each item's instance record is copied to shared memory, so that the block routine
-    // reads its fields there instead of from global memory: two buffers, the next item's
-    // record copied while the current item ends, so that one barrier between items both
-    // publishes it and separates the items' use of the staging memory
-    static_assert(sizeof(CartInst) % 4 == 0, "CartInst copies in 4-byte words");
-    __shared__ __align__(16) CartInst s_inst[2];
-    constexpr int NW = (int)(sizeof(CartInst) / 4);
-    const int n = *n_items;
-    auto fetch = [&](int w, int b) {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + items[w].x);
-        for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst[b])[q] = src[q];
-    };
-    if ((int)blockIdx.x < n) fetch(blockIdx.x, 0);
-    __syncthreads();
-    int b = 0;
-    for (int w = blockIdx.x; w < n; w += gridDim.x, b ^= 1) {
-        const int2 it = items[w];
-        const CartInst &m = s_inst[b];
-        const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
-        if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
-        else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
-        if (w + (int)gridDim.x < n) fetch(w + gridDim.x, b ^ 1);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + it.x);
+        for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_one)[q] = src[q];
+        step_dependency_wait();
         __syncthreads();
+        const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
+        if (cart_block_interior<TX, TY>(s_one, bx, by)) cart_tile<P, TX, TY, false, true>(s_one, par, bx, by, smem_raw);
+        else cart_tile<P, TX, TY, false, false>(s_one, par, bx, by, smem_raw);
+    } else {
+        step_dependency_wait();
+        // each item's instance record is copied to shared memory, so that the block
+        // routine reads its fields there instead of from global memory: two buffers,
+        // the next item's record copied while the current item ends, so that one
+        // barrier between items both publishes it and separates the items' use of the
+        // staging memory
+        __shared__ __align__(16) CartInst s_inst[2];
+        const int n = *n_items;
+        auto fetch = [&](int w, int b) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + items[w].x);
+            for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst[b])[q] = src[q];
+        };
+        if ((int)blockIdx.x < n) fetch(blockIdx.x, 0);
+        __syncthreads();
+        int b = 0;
+        for (int w = blockIdx.x; w < n; w += gridDim.x, b ^= 1) {
+            const int2 it = items[w];
+            const CartInst &m = s_inst[b];
+            const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
+            if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
+            else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
+            if (w + (int)gridDim.x < n) fetch(w + gridDim.x, b ^ 1);
+            __syncthreads();
+        }
     }
 }
 
