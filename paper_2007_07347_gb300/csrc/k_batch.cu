@@ -5,6 +5,69 @@
 
 namespace sdugks {
 
+// Batched: the (instance, block) work list, one item per CTA (PER_ITEM: the grid has a
+// CTA for every item, and CTAs past the item count in device memory return) or walked
+// by a fixed grid (a captured graph then stays valid while instances come and go).
+// One item per CTA keeps the block routine free of the walk's loop-carried state: the
+// walking form spills registers at four CTAs per SM, the per-item form does not.
+template <int P, int TX, int TY, bool PER_ITEM>
+__global__ void __launch_bounds__(cart_threads<TX, TY>(), cart_threads<TX, TY>() <= 320 ? 4 : 2)
+k_step_batch(const CartInst *__restrict__ insts, const int2 *__restrict__ items, const int *__restrict__ n_items,
+             int par)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    static_assert(sizeof(CartInst) % 4 == 0, "CartInst copies in 4-byte words");
+    constexpr int NW = (int)(sizeof(CartInst) / 4);
+    if constexpr (PER_ITEM) {
+        // The work list and the instance records are written by the host only (stream
+        // ordered before the launch), so the item and its record are read before the
+        // wait on the previous step: the record goes to shared memory while that step
+        // ends, and the block routine reads its fields there.  Every 16th CTA asks L2
+        // for the 128-byte line of the items ITEM_AHEAD places on (an in-bounds hint),
+        // so that the CTAs of later waves find their item in L2 although the step's
+        // state streams through it.
+        constexpr int ITEM_AHEAD = 2048;
+        __shared__ __align__(16) CartInst s_one;
+        const int n = *n_items;
+        if ((int)blockIdx.x >= n) return;
+        if (threadIdx.x == 0 && (blockIdx.x & 15) == 0 && (int)blockIdx.x + ITEM_AHEAD < n)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(items + blockIdx.x + ITEM_AHEAD));
+        const int2 it = items[blockIdx.x];
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + it.x);
+        for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_one)[q] = src[q];
+        step_dependency_wait();
+        __syncthreads();
+        const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
+        if (cart_block_interior<TX, TY>(s_one, bx, by)) cart_tile<P, TX, TY, false, true>(s_one, par, bx, by, smem_raw);
+        else cart_tile<P, TX, TY, false, false>(s_one, par, bx, by, smem_raw);
+    } else {
+        step_dependency_wait();
+        // each item's instance record is copied to shared memory, so that the block
+        // routine reads its fields there instead of from global memory: two buffers,
+        // the next item's record copied while the current item ends, so that one
+        // barrier between items both publishes it and separates the items' use of the
+        // staging memory
+        __shared__ __align__(16) CartInst s_inst[2];
+        const int n = *n_items;
+        auto fetch = [&](int w, int b) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + items[w].x);
+            for (int q = threadIdx.x; q < NW; q += blockDim.x) reinterpret_cast<uint32_t *>(&s_inst[b])[q] = src[q];
+        };
+        if ((int)blockIdx.x < n) fetch(blockIdx.x, 0);
+        __syncthreads();
+        int b = 0;
+        for (int w = blockIdx.x; w < n; w += gridDim.x, b ^= 1) {
+            const int2 it = items[w];
+            const CartInst &m = s_inst[b];
+            const int bx = it.y & 0xFFFF, by = it.y >> 16;   // the block's coordinates, packed on the host
+            if (cart_block_interior<TX, TY>(m, bx, by)) cart_tile<P, TX, TY, false, true>(m, par, bx, by, smem_raw);
+            else cart_tile<P, TX, TY, false, false>(m, par, bx, by, smem_raw);
+            if (w + (int)gridDim.x < n) fetch(w + gridDim.x, b ^ 1);
+            __syncthreads();
+        }
+    }
+}
+
 namespace {
 
 constexpr int BTX = 16, BTY = BATCH_TY;
