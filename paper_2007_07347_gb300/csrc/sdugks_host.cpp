@@ -1824,15 +1824,16 @@ static int batch_upload_tables(sdugks_batch *b)
     if ((int64_t)items.size() > b->max_items) return fail(SDUGKS_ERR_FULL, "batch work list full");
     b->n_items = (int64_t)items.size();
     const int ni = (int)b->n_items;
-    // a graph of per-item launches has grids of the old item count
-    if (b->graph && b->per_item && b->graph_items != b->n_items) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
     if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(b->d_inst, h.data(), h.size() * sizeof(CartInst), cudaMemcpyHostToDevice, b->stream));
     if (!items.empty()) CUDA_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
     CUDA_TRY(cudaMemcpyAsync(b->d_nitems, &ni, sizeof(int), cudaMemcpyHostToDevice, b->stream));
     CUDA_TRY(cudaStreamSynchronize(b->stream));   // the host vectors go out of scope
+    // a graph of per-item launches has grids of the old item count (destroyed after the
+    // synchronisation, so no launch of it is still running)
+    if (b->graph && b->per_item && b->graph_items != b->n_items) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     return SDUGKS_OK;
 }
 
