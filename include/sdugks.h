@@ -310,9 +310,10 @@ void sdugks_autotune_clear(void);
 
 /* ---- batched solves ----------------------------------------------------------- */
 /* Many independent uniform-grid solves (cavities, channels) of different sizes and
- * Reynolds numbers advanced together: every step is one launch of a fixed grid of
- * CTAs walking the (instance, 16x16 block) work list of all instances, with the
- * S-DUGKS update of Sec. II per block; steps replay a captured CUDA graph.  Each
+ * Reynolds numbers advanced together: every step is one launch over the (instance,
+ * 16x8 block) work list of all instances, one CTA per item (or, if the autotuner
+ * prefers it, a fixed grid of CTAs walking the list), with the S-DUGKS update of
+ * Sec. II per block; steps replay a captured CUDA graph.  Each
  * instance's arithmetic is the same as a single solver's Cartesian kernel on the
  * same mesh, so its results do not depend on what else is in the batch.  Instances
  * are admitted while the batch's device pool has room for their state (admission
