@@ -121,6 +121,24 @@ MUTATIONS = [
      "fbf[q] = (fbar[q] + b_plus * g[q]) * c_face;   /* step 7 */", "fbf[q] = fbar[q] * c_face;   /* step 7 */", -1),
     ("rarefied: relaxation rate dt/(2 tau)", DVM,
      "    const double r = dt / tau;\n", "    const double r = dt / (2.0 * tau);\n", -1),
+    ("rarefied: temperature from the total energy", DVM,
+     "double RT = W[3] / rho - 0.5 * (ux * ux + uy * uy);", "double RT = W[3] / rho;", -1),
+    ("rarefied: energy moment without its 1/2", DVM,
+     "W[3] += 0.5 * (x * x + y * y) * g[q];", "W[3] += (x * x + y * y) * g[q];", -1),
+    ("rarefied: moving wall's velocity reversed", DVM,
+     "if (m->bck[p] == KIND_MOVING_WALL) { uwx = m->bcp[3 * p]; uwy = m->bcp[3 * p + 1]; }",
+     "if (m->bck[p] == KIND_MOVING_WALL) { uwx = -m->bcp[3 * p]; uwy = -m->bcp[3 * p + 1]; }", -1),
+    ("rarefied: wall Maxwellian at twice the wall temperature", DVM,
+     "dvm_maxwell(1.0, uwx, uwy, RTw, Q, xi, w, g);", "dvm_maxwell(1.0, uwx, uwy, 2.0 * RTw, Q, xi, w, g);", -1),
+    ("rarefied: wall density without c", DVM,
+     "double rho_w = -c_face * S_out / (c_face * b_plus * G_out + G_in);",
+     "double rho_w = -S_out / (c_face * b_plus * G_out + G_in);", -1),
+    ("rarefied: first-order reconstruction (no gradient term)", DVM,
+     "double from_o = k->fbp[(size_t)Q * o + q] + (px - xo[0]) * so[0] + (py - xo[1]) * so[1];",
+     "double from_o = k->fbp[(size_t)Q * o + q];", -1),
+    ("rarefied: cell update without the 1/(1 + r)", DVM,
+     "f[(size_t)Q * j + q] = (f[(size_t)Q * j + q] - dt / m->vol[j] * Fj[q] + r * fe[q]) / (1.0 + r);",
+     "f[(size_t)Q * j + q] = (f[(size_t)Q * j + q] - dt / m->vol[j] * Fj[q] + r * fe[q]);", -1),
 ]
 
 

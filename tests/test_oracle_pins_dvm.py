@@ -12,7 +12,8 @@ gradient) and the sign of the flux balance, the BGK relaxation of a uniform stat
 (the rate dt/tau of Eq. fn+1), and the decay of a shear wave at the Navier-Stokes rate
 nu k^2 with nu = tau R T (the interface distribution of Eq. f_t_n+1), and the mirror
 symmetry of a symmetric state on a grid with velocities tangential to the faces (the
-tie rule of reading A5).
+tie rule of reading A5), and the equilibrium of the conserved moments (its temperature
+and its moments).
 """
 import math
 
@@ -48,6 +49,27 @@ def test_grid_and_maxwellian_against_truncated_gaussian(nv, vmax, ux, uy, RT):
     nb = math.exp(-(vmax - ux) ** 2 / (2 * RT)) / (s * math.sqrt(2 * math.pi))
     mx = ux * Ix + RT * (na - nb)
     assert abs((xi[:, 0] * g).sum() / 1.3 - mx * Iy) <= 2.5 * bound * (vmax + 2)
+
+
+def test_maxwellian_of_the_conserved_moments():
+    """The equilibrium a step builds from the conserved moments W = (rho, rho u,
+    rho (|u|^2/2 + R T)) (Eqs. Macro, Feq: the temperature is the energy per unit mass
+    less the kinetic part) is the Maxwellian of (rho, u, R T) sampled directly, and on a
+    grid wide enough for the truncation to be small its moments return W.  The
+    midpoint rule on a Gaussian has an error far below the truncation's; the tolerance
+    is the truncated tails' share of moments up to second order, 4 t rho (1 + vmax^2)
+    with t the larger one-sided tail mass of the two axes."""
+    nv, vmax = 100, 4.0
+    xi, w = O.dvm_grid(nv, vmax)
+    rho, ux, uy, RT = 1.2, 0.3, -0.2, 0.4
+    st = O.dvm_init(1, xi, w, rho0=rho, u0=(ux, uy), RT0=RT)
+    g = O.dvm_maxwell(rho, ux, uy, RT, xi, w)
+    assert np.abs(st.f[0] - g).max() <= 1e-13 * g.max()
+    E = 0.5 * (xi ** 2).sum(1)
+    mom = np.array([st.f[0].sum(), (xi[:, 0] * st.f[0]).sum(), (xi[:, 1] * st.f[0]).sum(), (E * st.f[0]).sum()])
+    assert np.allclose(st.W[0], [rho, rho * ux, rho * uy, rho * (0.5 * (ux * ux + uy * uy) + RT)], rtol=1e-15)
+    t = max(0.5 * math.erfc((vmax - abs(u)) / math.sqrt(2 * RT)) for u in (ux, uy))
+    assert np.abs(mom - st.W[0]).max() <= 4 * t * rho * (1 + vmax ** 2)
 
 
 def _periodic(lx, ly):
