@@ -93,6 +93,42 @@ MUTATIONS = [
     ("forces: the previous step's interface values", FORCES,
      "    if (!rc && bflux) boundary_flux(&m, w.fb, bflux);\n",
      "    if (!rc && bflux) { one_step(&m, tau, dt, f, W, &w); boundary_flux(&m, w.fb, bflux); }\n", 0),
+    ("D2Q9: cell update without the 1/(1 + r)", D2Q9,
+     "f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * w->F[NQ * j + a] + r * feq1[a]) / (1.0 + r);",
+     "f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * w->F[NQ * j + a] + r * feq1[a]);", 0),
+    ("D2Q9: sign of the flux in the f update", D2Q9,
+     "f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * w->F[NQ * j + a] + r * feq1[a]) / (1.0 + r);",
+     "f[NQ * j + a] = (f[NQ * j + a] + dt / m->vol[j] * w->F[NQ * j + a] + r * feq1[a]) / (1.0 + r);", 0),
+    ("D2Q9: f update with the old equilibrium", D2Q9,
+     "f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * w->F[NQ * j + a] + r * feq1[a]) / (1.0 + r);",
+     "f[NQ * j + a] = (f[NQ * j + a] - dt / m->vol[j] * w->F[NQ * j + a] + r * w->feqn[NQ * j + a]) / (1.0 + r);", 0),
+    ("D2Q9: c = 2 tau / (2 tau - dt)", D2Q9,
+     "const double c_face = 2.0 * tau / (2.0 * tau + dt);    /* Eq. f_t_n+1 */",
+     "const double c_face = 2.0 * tau / (2.0 * tau - dt);    /* Eq. f_t_n+1 */", 0),
+    ("D2Q9: b feq_b doubled in f_b", D2Q9,
+     "fbf[a] = (fbar[a] + b_plus * feqb[a]) * c_face;", "fbf[a] = (fbar[a] + 2.0 * b_plus * feqb[a]) * c_face;", 0),
+    ("D2Q9: tangential velocities take the neighbour's side", D2Q9,
+     "else fbar[a] = 0.5 * (from_o + from_k);", "else fbar[a] = from_k;", 0),
+    ("D2Q9: interface density without the rest velocity", D2Q9,
+     "                Wb[0] += fbar[a];\n", "                Wb[0] += a ? fbar[a] : 0.0;\n", 0),
+    ("equilibrium: velocity not divided by rho", D2Q9,
+     "feq_of(W[0], W[1] / W[0], W[2] / W[0], out);", "feq_of(W[0], W[1], W[2], out);", 0),
+    ("walls: incoming values from fbar+ instead of f", D2Q9,
+     "fbf[a] = feqb[a] + (f[NQ * o + a] - w->feqn[NQ * o + a]);",
+     "fbf[a] = feqb[a] + (w->fbp[NQ * o + a] - w->feqn[NQ * o + a]);", 0),
+    ("walls: leaving values without the gradient term", D2Q9,
+     "double fbar = w->fbp[NQ * o + a] + (px - xo[0]) * w->sig[2 * (NQ * o + a)] +\n"
+     "                                  (py - xo[1]) * w->sig[2 * (NQ * o + a) + 1];",
+     "double fbar = w->fbp[NQ * o + a];", 0),
+    ("walls: moving wall's density fixed at 1", D2Q9,
+     "*rho = Wo[0]; *ux = par[0]; *uy = par[1]; break;", "*rho = 1.0; *ux = par[0]; *uy = par[1]; break;", 0),
+    ("outlet: velocity not divided by rho", D2Q9,
+     "*rho = Wo[0]; *ux = Wo[1] / Wo[0]; *uy = Wo[2] / Wo[0]; break;",
+     "*rho = Wo[0]; *ux = Wo[1]; *uy = Wo[2]; break;", 0),
+    ("symmetry: ghost velocity not mirrored (lines of constant x)", D2Q9,
+     "if (mir == 1) { ak = MIRROR_X[a]; gsx = -1.0; }", "if (mir == 1) { gsx = -1.0; }", 0),
+    ("LLSR: diagonal entries of the inverse swapped", D2Q9,
+     "m->ainv[3 * c] = ayy / det;", "m->ainv[3 * c] = axx / det;", 0),
     ("rarefied: sign of the W update", DVM,
      "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
     ("rarefied: wall density without its b G_out term", DVM,
