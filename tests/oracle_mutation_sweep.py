@@ -129,6 +129,14 @@ MUTATIONS = [
      "if (mir == 1) { ak = MIRROR_X[a]; gsx = -1.0; }", "if (mir == 1) { gsx = -1.0; }", 0),
     ("LLSR: diagonal entries of the inverse swapped", D2Q9,
      "m->ainv[3 * c] = ayy / det;", "m->ainv[3 * c] = axx / det;", 0),
+    ("forces: y-momentum from the x component of xi", FORCES,
+     "py += XI[a][1] * s * fb[NQ * fc + a];", "py += XI[a][0] * s * fb[NQ * fc + a];", 0),
+    ("forces: sign of the face normal", FORCES,
+     "double s = XI[a][0] * m->nl[2 * fc] + XI[a][1] * m->nl[2 * fc + 1];\n            px +=",
+     "double s = -(XI[a][0] * m->nl[2 * fc] + XI[a][1] * m->nl[2 * fc + 1]);\n            px +=", 0),
+    ("forces: the flux halved", FORCES,
+     "px += XI[a][0] * s * fb[NQ * fc + a];\n            py += XI[a][1] * s * fb[NQ * fc + a];",
+     "px += XI[a][0] * s * fb[NQ * fc + a] * 0.5;\n            py += XI[a][1] * s * fb[NQ * fc + a] * 0.5;", 0),
     ("rarefied: sign of the W update", DVM,
      "W[4 * j + d] -= dt / m->vol[j] * Mj[d];", "W[4 * j + d] += dt / m->vol[j] * Mj[d];", -1),
     ("rarefied: wall density without its b G_out term", DVM,
