@@ -12,8 +12,10 @@ gradient) and the sign of the flux balance, the BGK relaxation of a uniform stat
 (the rate dt/tau of Eq. fn+1), and the decay of a shear wave at the Navier-Stokes rate
 nu k^2 with nu = tau R T (the interface distribution of Eq. f_t_n+1), and the mirror
 symmetry of a symmetric state on a grid with velocities tangential to the faces (the
-tie rule of reading A5), and the equilibrium of the conserved moments (its temperature
-and its moments).
+tie rule of reading A5), the equilibrium of the conserved moments (its temperature
+and its moments), and by brute force: three steps on 3 x 3 grids (periodic, between
+diffuse walls, in a closed box) against an independent 40-digit restatement of the step
+(``oracle/handstep_dvm.py``).
 """
 import math
 
@@ -251,3 +253,47 @@ def test_mirror_symmetric_state_stays_symmetric_with_tangential_nodes():
     assert np.abs(st.u[:, 1] - st.u[mir, 1]).max() <= 1e-12
     assert np.abs(st.RT - st.RT[mir]).max() <= 1e-12
     assert np.abs(st.u[:, 0]).max() > 1e-3
+
+
+_SIDES = {
+    "periodic": ({"bottom": ("periodic",), "top": ("periodic",), "left": ("periodic",), "right": ("periodic",)},
+                 lambda lx, ly: _periodic(lx, ly)),
+    "channel": ({"bottom": ("wall", 0.0, 0.0), "top": ("wall", 0.1, 0.0), "left": ("periodic",),
+                 "right": ("periodic",)},
+                lambda lx, ly: [(3, M.BC_PERIODIC, (1, lx, 0.0)), (1, M.BC_PERIODIC, (3, -lx, 0.0)),
+                                (0, M.BC_WALL, (0, 0, 0)), (2, M.BC_MOVING_WALL, (0.1, 0, 0))]),
+    "box": ({"bottom": ("wall", 0.0, 0.0), "top": ("wall", 0.1, 0.0), "left": ("wall", 0.0, 0.0),
+             "right": ("wall", 0.0, 0.0)},
+            lambda lx, ly: [(0, M.BC_WALL, (0, 0, 0)), (1, M.BC_WALL, (0, 0, 0)), (3, M.BC_WALL, (0, 0, 0)),
+                            (2, M.BC_MOVING_WALL, (0.1, 0, 0))]),
+}
+
+
+@pytest.mark.parametrize("kind", ["periodic", "channel", "box"])
+def test_hand_stepped_against_a_40_digit_restatement(kind):
+    """Three steps on a 3 x 3 grid of 1/3 x 1/4 cells with a 4 x 4 velocity grid, from a
+    non-uniform state (density, velocity and temperature vary from cell to cell),
+    against ``oracle/handstep_dvm.py``: the same step written cell by cell with explicit
+    neighbours and faces in 40-digit arithmetic.  Periodic sides, a channel between a
+    resting and a moving diffuse wall, and a closed box (corner cells with two LLSR
+    neighbours).  The FP64 oracle agrees to FP64 rounding: about 4e-16 of the largest
+    value measured, 1e-14 asserted, while the state changes by about 5 % over the three
+    steps."""
+    mp = pytest.importorskip("mpmath")
+    from oracle import handstep_dvm as H
+    nx, ny, lx, ly, nv, vmax = 3, 3, 1.0, 0.75, 4, 2.0
+    tau, dt, RTw, steps = 0.05, 0.02, 0.5, 3
+    sides, bcs = _SIDES[kind]
+    xi, w = O.dvm_grid(nv, vmax)
+    m = M.cartesian(nx, ny, lx, ly)
+    rng = np.random.default_rng(11)
+    st = O.dvm_init(m.n_cells, xi, w, rho=1 + 0.1 * rng.uniform(-1, 1, m.n_cells),
+                    u=0.1 * rng.uniform(-1, 1, (m.n_cells, 2)), RT=0.5 + 0.05 * rng.uniform(-1, 1, m.n_cells))
+    g = H.Grid(nx, ny, lx / nx, ly / ny, sides, nv, vmax)
+    fh, Wh = H.run(g, st.f, st.W, tau, dt, RTw, steps)
+    O.dvm_run(m, bcs(lx, ly), st, xi, w, RTw, tau=tau, dt=dt, n_steps=steps)
+    fh = np.array([[float(v) for v in row] for row in fh])
+    Wh = np.array([[float(v) for v in row] for row in Wh])
+    assert np.abs(st.f - fh).max() <= 1e-14 * np.abs(fh).max()
+    assert np.abs(st.W - Wh).max() <= 1e-14 * np.abs(Wh).max()
+    assert np.abs(Wh[:, 1:3]).max() > 1e-3                  # the state is not at rest
