@@ -14,10 +14,12 @@ q = j + nv i with j along x; the distributions are weighted (moments are plain s
 psi = (1, xi, |xi|^2/2) and R T = E / rho - |u|^2 / 2 with E the energy per unit mass;
 the macroscopic flux of Eq. MacroUpdate is the moment of the same step's mesoscopic
 flux; the LLSR neighbours are the face neighbours (periodic images at shifted
-positions, none across a wall); upwind by the sign of xi . n; a diffuse wall sends
-back rho_w times its Maxwellian (rho 1, wall velocity, R T_w) into the fluid and takes
-the leaving velocities from the inner reconstruction with rho_w times the wall
-Maxwellian as their equilibrium, rho_w such that no mass crosses the wall.
+positions, none across a wall); upwind by the sign of xi . n, the mean of both sides'
+reconstructions for a velocity tangential to the face (at a wall, the inner side's); a
+diffuse wall sends back rho_w times its Maxwellian (rho 1, wall velocity, R T_w) into
+the fluid and takes the leaving velocities from the inner reconstruction with rho_w
+times the wall Maxwellian as their equilibrium, rho_w such that no mass crosses the
+wall.
 """
 from __future__ import annotations
 
@@ -159,7 +161,8 @@ def step(g: Grid, f, W, tau, dt, RTw):
 
         if k is not None:
             xk = (xo[0] + off[0], xo[1] + off[1])      # the neighbour's (image) centre
-            fbar = [recon(o, xo, q) if s[q] > 0 else recon(k, xk, q) for q in range(Q)]
+            fbar = [recon(o, xo, q) if s[q] > 0 else
+                    (recon(k, xk, q) if s[q] < 0 else (recon(o, xo, q) + recon(k, xk, q)) / 2) for q in range(Q)]
             gb = maxwell_W(g, moments(g, fbar))
             fb = [cf * (fbar[q] + b * gb[q]) for q in range(Q)]
         else:
