@@ -162,9 +162,10 @@ cudaError_t launch_step_tiled_fp32(int prec, const TiledMesh &m, const Coefs &c,
 
 // Programmatic dependent launch of the step kernels: each step kernel lets the next
 // launch in its stream be scheduled as soon as all of its CTAs are running
-// (griddepcontrol.launch_dependents) and, before it touches global memory, waits
-// until the previous grid has completed and its writes are visible
-// (griddepcontrol.wait; a no-op when the launch did not allow an early start).  The
+// (griddepcontrol.launch_dependents) and, before it touches memory that a step
+// writes, waits until the previous grid has completed and its writes are visible
+// (griddepcontrol.wait; a no-op when the launch did not allow an early start); what
+// only the host writes (mesh data, work items) may be read before the wait.  The
 // next step's CTAs therefore take the SM slots the moment the current step's CTAs
 // retire, instead of after the launch latency.
 #ifdef __CUDACC__
