@@ -50,3 +50,24 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
                        cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0
     assert not any(ln.lstrip().startswith("{") for ln in r.stdout.splitlines())
+
+
+def test_stopping_rule_of_the_batched_solves():
+    """The retirement rule of `--workload batch-solve` (Sec. IV residual checked every
+    interval): converged below the target; diverged on a NaN residual; stalled when
+    `stall` checks in a row bring no minimum 1 % below the last one; capped at the step
+    cap.  An infinite residual (no snapshot motion yet) is none of these."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.Retire(target=1e-6, cap=10_000, stall=3)
+    assert r(float("inf"), 1000) is None
+    assert r(1e-3, 2000) is None
+    assert r(0.995e-3, 3000) is None              # less than 1 % lower: no new minimum
+    assert r(0.994e-3, 4000) is None
+    assert r(0.5e-3, 5000) is None                # a new minimum resets the count
+    assert r(0.5e-3, 6000) is None
+    assert r(0.5e-3, 7000) is None
+    assert r(0.5e-3, 8000) == "stalled"
+    assert bench.Retire(1e-6, 10_000, 3)(0.9e-6, 1000) == "converged"
+    assert bench.Retire(1e-6, 10_000, 3)(float("nan"), 1000) == "diverged"
+    assert bench.Retire(1e-6, 2000, 50)(1e-3, 2000) == "capped"
